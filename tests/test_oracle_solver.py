@@ -1,0 +1,94 @@
+"""Pins of the oracle's solver pieces: Steihaug CG against direct solves and the
+trust-region geometry, CGLS against the exact rho, and Gauss-Newton against
+quadratic local convergence and noiseless recovery of ground-truth maps."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import model, solver, metrics
+
+
+def _spd(n, seed, cond=100.0):
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return (q * np.geomspace(1, cond, n)) @ q.T
+
+
+def test_steihaug_interior_solution_equals_direct_solve():
+    B = _spd(12, 0)
+    g = np.random.default_rng(1).standard_normal(12)
+    p, mval, it, why = solver.steihaug_cg(lambda v: B @ v, g, 1e9, 100, rel_tol=1e-13)
+    ref = np.linalg.solve(B, -g)
+    assert np.allclose(p, ref, rtol=1e-9)
+    assert np.isclose(mval, g @ ref + 0.5 * ref @ B @ ref, rtol=1e-9)
+    assert why == "converged"
+
+
+def test_steihaug_stops_on_the_trust_boundary():
+    B = _spd(12, 2)
+    g = np.random.default_rng(3).standard_normal(12)
+    p, mval, it, why = solver.steihaug_cg(lambda v: B @ v, g, 0.05, 100)
+    assert why == "boundary"
+    assert np.isclose(np.linalg.norm(p), 0.05, rtol=1e-12)
+    assert np.isclose(mval, g @ p + 0.5 * p @ B @ p, rtol=1e-10)
+    assert mval < 0
+
+
+def test_steihaug_negative_curvature_goes_to_the_boundary():
+    B = np.diag([1.0, -2.0, 3.0])
+    g = np.array([0.0, 1.0, 0.0])
+    p, mval, it, why = solver.steihaug_cg(lambda v: B @ v, g, 2.0, 10)
+    assert why == "negative_curvature"
+    assert np.isclose(np.linalg.norm(p), 2.0)
+    assert np.isclose(mval, g @ p + 0.5 * p @ B @ p)
+
+
+def test_cgls_recovers_rho_at_the_true_relaxation_times():
+    seq, ph = synth.config("quad16")
+    alpha = np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(), ph.rho.imag.ravel()])
+    lin = model.linearize(seq, alpha)
+    d = model.signal(lin)
+    rho = solver.cgls_rho(lin, d, iters=60)
+    assert metrics.nrmse(rho, ph.rho.ravel()) < 1e-8
+
+
+def test_gauss_newton_converges_quadratically_near_the_solution():
+    seq, ph = synth.config("quad16")
+    truth = np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(), ph.rho.imag.ravel()])
+    d = model.forward(seq, truth)
+    a1 = truth + 0.1 * synth.random_params(seq.nv, 5)
+    a, rep = solver.gauss_newton(seq, d, a1, opts=solver.GNOptions(outer_iters=6, inner_iters=40))
+    assert all(np.diff(rep.f) < 0)
+    assert rep.f_final < 1e-12 * rep.f[0]
+    assert metrics.nrmse(np.exp(a[0]), ph.t1_ms.ravel()) < 1e-7
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("seed", [0, 2])
+def test_noiseless_recovery_from_the_papers_initial_guess(seed):
+    """Start at T1 = 1000 ms, T2 = 100 ms with CGLS rho and a drawn mask (Methods) on a
+    16x16 four-region phantom scanned with 24 fills (384 TRs, 3 s)."""
+    seq = synth.make_sequence(16, 16, 24, 7.8, 3.9, seed=seed)
+    ph = synth.quadrant_phantom(16, seed)
+    truth = np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(), ph.rho.imag.ravel()])
+    d = model.forward(seq, truth)
+    a0, mask = solver.initial_alpha(seq, d, seq.nv)
+    a, rep = solver.gauss_newton(seq, d, a0, mask=mask, opts=solver.GNOptions(outer_iters=10, inner_iters=20))
+    assert rep.f_final < 1e-6 * rep.f[0]
+    assert metrics.nrmse(np.exp(a[0]), ph.t1_ms.ravel()) < 1e-3
+    assert metrics.nrmse(np.exp(a[1]), ph.t2_ms.ravel()) < 1e-3
+    assert metrics.nrmse(a[2] + 1j * a[3], ph.rho.ravel()) < 1e-3
+
+
+def test_noisy_fit_reaches_the_noise_floor():
+    """With SNR 50 noise the final objective sits at about 1/2 ||noise||^2 (Results)."""
+    seq = synth.make_sequence(16, 16, 24, 7.8, 3.9, seed=0)
+    ph = synth.quadrant_phantom(16, 0)
+    truth = np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(), ph.rho.imag.ravel()])
+    s = model.forward(seq, truth)
+    d = synth.add_noise(s, 50.0, 9)
+    floor = 0.5 * np.linalg.norm(d - s) ** 2
+    a, rep = solver.gauss_newton(seq, d, truth, opts=solver.GNOptions(outer_iters=4, inner_iters=30))
+    # the fit absorbs about N of the 2 Nt real noise components: f_final ~ floor * (1 - N / (2 Nt))
+    expected = floor * (1 - truth.size / (2 * d.size))
+    assert 0.8 * expected < rep.f_final < 1.05 * floor
