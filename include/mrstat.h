@@ -1,0 +1,217 @@
+/*
+ * mrstat.h -- C ABI of the GB300 MR-STAT hot path (libmrstat.so).
+ *
+ * MR-STAT (van der Heide et al., arXiv 1904.13244) fits T1, T2 and complex proton
+ * density maps directly to time-domain k-space data by an inexact Gauss-Newton
+ * method whose inner CG solve only needs the signal s(alpha) and the Jacobian
+ * products J.v and Re(J^H w) (Theory, Eq. 4; Algorithms 2, 4 and 6).  This library
+ * evaluates those products on one GPU with hand-written sm_103a kernels.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Image grid nx (readout, x) by ny (phase encode, y); nv = nx * ny voxels; voxel
+ *    j = iy * nx + ix (ix fastest).
+ *  - Parameter maps alpha are float32 [4][nv] in DEVICE memory, parameter-major
+ *    (Theory: index j + k Nv): k = 0 ln(T1/ms), 1 ln(T2/ms), 2 Re rho, 3 Im rho
+ *    (log scaling of T1 and T2: Methods, "Reconstructions").
+ *  - k-space vectors (s, d, J.v, w) are interleaved complex float32 [ntr][nkx][2]
+ *    in DEVICE memory; TR n samples the phase-encode line ky[n] and readout points
+ *    kx = k - nkx/2, k = 0..nkx-1; the encoding phase is exp(-2 pi i (kx ix/nx +
+ *    ky iy/ny)) (Theory, Eqs. 1-2 with the gradient encoding of Supporting
+ *    Information S2).
+ *  - J denotes the SIGNAL Jacobian J_s = ds/dalpha.  The paper's J = dr/dalpha is
+ *    -J_s (Theory, "Computing the gradient g"), so the gradient of
+ *    f = 1/2 ||d - s||^2 is -Re(J_s^H (d - s)).
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).  Every
+ *    call only enqueues work on that stream and returns; no call synchronises the
+ *    device unless its comment says so.  Buffers belong to the caller and must stay
+ *    valid until the enqueued work has finished.
+ *  - A plan is bound to the CUDA device that was current when it was created; calls
+ *    switch to that device and restore the caller's device before returning.
+ *  - Every call returns an mrstat_status; mrstat_last_error() gives a message for
+ *    the last failure on the calling thread.  A failed call leaves outputs
+ *    undefined but the plan usable.
+ *  - Calls on the same plan must not overlap in time on different host threads or
+ *    different streams: the plan's work buffers are shared.
+ */
+#ifndef MRSTAT_H
+#define MRSTAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mrstat_status {
+  MRSTAT_OK = 0,
+  MRSTAT_ERR_INVALID_ARG = 1,     /* null pointer, bad enum, bad option value          */
+  MRSTAT_ERR_SHAPE = 2,           /* sizes out of range (see mrstat_plan_create)        */
+  MRSTAT_ERR_NOT_LINEARIZED = 3,  /* jvp/jhw/timecourses before mrstat_linearize        */
+  MRSTAT_ERR_CUDA = 4,            /* a CUDA runtime call or kernel launch failed        */
+  MRSTAT_ERR_NONFINITE = 5,       /* NaN or Inf found where a finite value is required */
+  MRSTAT_ERR_TIMEOUT = 6,         /* an iteration budget ran out                        */
+  MRSTAT_ERR_UNSUPPORTED = 7,     /* valid request this build does not implement        */
+  MRSTAT_ERR_OUT_OF_MEMORY = 8    /* device allocation failed                            */
+} mrstat_status;
+
+/* Numerical forms of the encoding contraction. */
+typedef enum mrstat_form {
+  MRSTAT_FORM_PLAIN_FP32 = 0,     /* every step in FP32 on the CUDA cores               */
+  MRSTAT_FORM_SPLIT_BF16 = 1      /* x-DFT as split-BF16 tensor-core products, FP32 acc */
+} mrstat_form;
+
+/*
+ * Pulse-sequence description (Methods, "Pulse Sequence"; Supporting Information S1).
+ * Balanced gradient echo with one phase-encode line per TR; the RF pulse of TR n is
+ * an instantaneous rotation by flip_rad[n] * B1 about -x (RF phase 0) or +x (RF
+ * phase 180 degrees; the phase alternates 0/180 between TRs when alternate_phase is
+ * nonzero).  inversion != 0 applies an ideal non-selective inversion before TR 0.
+ * The magnetisation is sampled at te_ms after each pulse and held constant across
+ * the nkx readout samples of its TR.  flip_rad and ky are HOST arrays read only
+ * during mrstat_plan_create.
+ */
+typedef struct mrstat_seq {
+  int32_t nx, ny;          /* image grid, 1..2048 each                             */
+  int32_t nkx;             /* readout samples per TR, 1..4096                       */
+  int32_t ntr;             /* number of TRs, 1..65536                               */
+  double tr_ms, te_ms;     /* 0 < te_ms < tr_ms                                    */
+  int32_t inversion;       /* 0 or 1                                                */
+  int32_t alternate_phase; /* 0 or 1                                                */
+  const float* flip_rad;   /* host [ntr], finite, >= 0                              */
+  const int32_t* ky;       /* host [ntr], each in [-(ny/2), ny - ny/2)              */
+} mrstat_seq;
+
+typedef struct mrstat_plan mrstat_plan;
+
+/* Static description of a plan (host struct filled by mrstat_plan_info). */
+typedef struct mrstat_plan_info_t {
+  int32_t nx, ny, nkx, ntr, nv, form;
+  int32_t ntr_padded;          /* ntr rounded up to a multiple of 4 (TR quads)      */
+  int64_t device_bytes;        /* device memory owned by the plan                   */
+  int64_t timecourse_bytes;    /* of which the cached time courses D                */
+} mrstat_plan_info_t;
+
+/*
+ * Create a plan: validates the sequence, builds the per-TR rotation and phase
+ * tables and allocates every work buffer (the cached magnetisation time courses
+ * D of 3 x ntr_padded x nv float32, the forward scratch, the x-DFT matrices and the
+ * reduction scratch).  Synchronises the current device once.  On failure *out is
+ * set to NULL.  Errors: INVALID_ARG (null seq/out/arrays, bad form, non-finite or
+ * negative flips, te/tr), SHAPE (sizes outside the ranges above, ky out of range),
+ * OUT_OF_MEMORY, CUDA.
+ */
+int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out);
+
+/* Free a plan and its device memory (synchronises the plan's device). NULL is a no-op. */
+int mrstat_plan_destroy(mrstat_plan* plan);
+
+int mrstat_plan_info(const mrstat_plan* plan, mrstat_plan_info_t* info);
+
+/*
+ * Linearise the model at alpha (Algorithm 2 step 1 for every voxel, with the
+ * forward-mode derivatives of Supporting Information S2): runs the Bloch recursion
+ * of every voxel and caches m_y and dm_y/dln T1, dm_y/dln T2 at every echo, plus
+ * rho and the mask, for later mrstat_jvp / mrstat_jhw / mrstat_timecourses calls.
+ *   alpha: device float [4][nv] (see top).
+ *   b1:    device float [nv] relative transmit field, or NULL for B1 = 1.
+ *   mask:  device uint8 [nv], nonzero = voxel takes part, or NULL for all voxels
+ *          (Methods: voxels without significant proton density are excluded; a
+ *          masked-out voxel contributes nothing to s and gets zero gradient).
+ * Errors: INVALID_ARG (null plan/alpha), CUDA.
+ */
+int mrstat_linearize(mrstat_plan* plan, const float* alpha, const float* b1,
+                     const uint8_t* mask, void* stream);
+
+/*
+ * s = sum_j rho_j m_j(theta_j) exp(-i k.r_j) (Algorithm 2; Eqs. 1-2) at alpha.
+ *   s: device float [ntr][nkx][2] output.  Does not change the cached linearisation.
+ * Errors: INVALID_ARG, CUDA.
+ */
+int mrstat_forward(mrstat_plan* plan, const float* alpha, const float* b1,
+                   const uint8_t* mask, float* s, void* stream);
+
+/*
+ * jv = J_s v at the cached linearisation ("Similar techniques ... J v", text before
+ * Eq. 4): jv = encode(rho (v0 dm/dlnT1 + v1 dm/dlnT2) + (v2 + i v3) m).
+ *   v: device float [4][nv];  jv: device float [ntr][nkx][2].
+ * Errors: INVALID_ARG, NOT_LINEARIZED, CUDA.
+ */
+int mrstat_jvp(mrstat_plan* plan, const float* v, float* jv, void* stream);
+
+/*
+ * g = Re(J_s^H w) at the cached linearisation (Algorithm 4 with J_s = -J):
+ * g[k][j] = Re sum_{n,kx} conj(d(rho_j m_j[n])/dalpha_k exp(-i k.r_j)) w[n][kx].
+ *   w: device float [ntr][nkx][2];  g: device float [4][nv] (zero outside the mask).
+ * Errors: INVALID_ARG, NOT_LINEARIZED, CUDA.
+ */
+int mrstat_jhw(mrstat_plan* plan, const float* w, float* g, void* stream);
+
+/*
+ * Copy one cached time course channel out of the plan: channel 0 = m_y, 1 =
+ * dm_y/dln T1, 2 = dm_y/dln T2 at every echo (the echo signal is i * m_y because
+ * the RF phases 0/180 keep m_x = 0; Supporting Information S2).
+ *   out: device float [ntr][nv].  Masked-out voxels read as 0.
+ * Errors: INVALID_ARG (bad channel), NOT_LINEARIZED, CUDA.
+ */
+int mrstat_timecourses(mrstat_plan* plan, int32_t channel, float* out, void* stream);
+
+/*
+ * *out = sum_i a[i] * b[i] accumulated in float64 (the CG inner products of the
+ * inner Gauss-Newton loop, Algorithm 6).  a, b: device float [n]; out: device double.
+ * Uses the plan's reduction scratch.  n may be 0 (result 0).
+ * Errors: INVALID_ARG (null pointer, n < 0), CUDA.
+ */
+int mrstat_dot(mrstat_plan* plan, const float* a, const float* b, int64_t n,
+               double* out, void* stream);
+
+/*
+ * Fixed-count conjugate gradients on Re(J_s^H J_s) x = rhs at the cached
+ * linearisation (the inner CG of Algorithm 6 without trust-region exits): x_0 = 0,
+ * then exactly `iters` iterations, each one J^H J v product (mrstat_jvp followed by
+ * mrstat_jhw) plus float64 inner products; every scalar stays on the device.  An
+ * iteration whose curvature p.Hp is not positive, or whose residual is exactly
+ * zero, freezes x for the remaining iterations.
+ *   rhs, x: device float [4][nv].  iters >= 0.
+ * Errors: INVALID_ARG, NOT_LINEARIZED, CUDA.
+ */
+int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters,
+                    void* stream);
+
+/*
+ * Tracing of the plan's own kernel launches.  Launch counts are always kept; while
+ * profiling is on, every launch of a kernel whose bit is set in kernel_mask is
+ * bracketed by two CUDA events on its stream.  mrstat_profile_start clears the
+ * counters and turns profiling on; mrstat_profile_stop waits for the recorded events,
+ * fills *out (launches and summed event time per kernel) and turns profiling off.
+ * Instrumentation for roofline reporting; it does not change any result.
+ */
+typedef enum mrstat_kernel_id {
+  MRSTAT_K_BLOCH = 0,        /* Bloch recursion + tangents (K1)                    */
+  MRSTAT_K_YCONTRACT = 1,    /* phase-encode contraction of s and J.v (K2)         */
+  MRSTAT_K_XDFT = 2,         /* readout DFT (K3)                                   */
+  MRSTAT_K_XDFT_ADJ = 3,     /* readout DFT adjoint (K3^H)                         */
+  MRSTAT_K_JHW_DOT = 4,      /* phase-encode adjoint + tangent inner products (K4) */
+  MRSTAT_K_VECTOR = 5,       /* coefficient preparation, reductions, CG updates    */
+  MRSTAT_K_COUNT = 6
+} mrstat_kernel_id;
+
+typedef struct mrstat_kernel_stats {
+  int64_t launches[8];       /* indexed by mrstat_kernel_id                          */
+  double ms[8];              /* summed event time of the profiled launches           */
+  int64_t timed[8];          /* launches that were bracketed by events               */
+} mrstat_kernel_stats;
+
+int mrstat_profile_start(mrstat_plan* plan, uint32_t kernel_mask);
+int mrstat_profile_stop(mrstat_plan* plan, mrstat_kernel_stats* out);
+
+const char* mrstat_status_string(int status);
+
+/* Message of the last failed call on the calling thread ("" if none). */
+const char* mrstat_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRSTAT_H */

@@ -69,13 +69,14 @@ def scale(dm, e1, e2):
     return np.stack([dm[0] * e2, dm[1] * e2, dm[2] * e1])
 
 
-def simulate(seq, t1_ms, t2_ms, b1=None, tangents=True, b1_tangent=False):
+def simulate(seq, t1_ms, t2_ms, b1=None, tangents=True, b1_tangent=False, rows=None):
     """Simulate the transverse magnetisation at every echo.
 
     Parameters are flat arrays over voxels (length nv).  ``t1_ms``/``t2_ms`` may
     be complex (complex-step checks).  Returns a dict with ``m`` [ntr, nv] and,
     when requested, ``dm_dlnT1``, ``dm_dlnT2`` and ``dm_dB1`` of the same shape,
-    plus the full 3-component state ``mxyz`` at every echo [ntr, 3, nv].
+    plus the full 3-component state ``mxyz`` at every echo [ntr, 3, nv].  With
+    ``rows`` (sorted TR indices) only those echoes are kept, in that order.
     """
     t1 = np.asarray(t1_ms)
     t2 = np.asarray(t2_ms)
@@ -97,8 +98,11 @@ def simulate(seq, t1_ms, t2_ms, b1=None, tangents=True, b1_tangent=False):
     d2 = np.zeros((3, nv), dtype)
     db = np.zeros((3, nv), dtype)
 
-    out_m = np.zeros((seq.ntr, nv), np.result_type(dtype, np.complex128))
-    out_xyz = np.zeros((seq.ntr, 3, nv), dtype)
+    keep = np.arange(seq.ntr) if rows is None else np.asarray(rows)
+    slot = np.full(seq.ntr, -1)
+    slot[keep] = np.arange(keep.shape[0])
+    out_m = np.zeros((keep.shape[0], nv), np.result_type(dtype, np.complex128))
+    out_xyz = np.zeros((keep.shape[0], 3, nv), dtype)
     if tangents:
         out_d1 = np.zeros_like(out_m)
         out_d2 = np.zeros_like(out_m)
@@ -127,13 +131,15 @@ def simulate(seq, t1_ms, t2_ms, b1=None, tangents=True, b1_tangent=False):
             d2 = rodrigues(d2, k, theta)
             m = rodrigues(m, k, theta)
         m, d1, d2, db = decay(m, d1, d2, db, e1a, e2a, te)
-        out_m[n] = m[0] + 1j * m[1]
-        out_xyz[n] = m
-        if tangents:
-            out_d1[n] = d1[0] + 1j * d1[1]
-            out_d2[n] = d2[0] + 1j * d2[1]
-        if b1_tangent:
-            out_db[n] = db[0] + 1j * db[1]
+        i = slot[n]
+        if i >= 0:
+            out_m[i] = m[0] + 1j * m[1]
+            out_xyz[i] = m
+            if tangents:
+                out_d1[i] = d1[0] + 1j * d1[1]
+                out_d2[i] = d2[0] + 1j * d2[1]
+            if b1_tangent:
+                out_db[i] = db[0] + 1j * db[1]
         m, d1, d2, db = decay(m, d1, d2, db, e1b, e2b, tr - te)
 
     res = {"m": out_m, "mxyz": out_xyz}

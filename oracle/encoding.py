@@ -29,32 +29,37 @@ def voxel_coords(nx: int, ny: int):
     return j % nx, j // nx  # ix, iy
 
 
-def phase_matrix(seq, ky: int) -> np.ndarray:
-    """E[kx, j] = exp(-2 pi i (kx ix_j / nx + ky iy_j / ny)), shape [nkx, nv]."""
+def phase_matrix(seq, ky: int, voxels=None) -> np.ndarray:
+    """E[kx, j] = exp(-2 pi i (kx ix_j / nx + ky iy_j / ny)), shape [nkx, nv] (or only the
+    columns of the listed voxels)."""
     ix, iy = voxel_coords(seq.nx, seq.ny)
+    if voxels is not None:
+        ix, iy = ix[voxels], iy[voxels]
     kx = kx_values(seq.nkx)
     ph = kx[:, None] * ix[None, :] / seq.nx + ky * iy[None, :] / seq.ny
     return np.exp(-2j * np.pi * ph)
 
 
 def encode(seq, q: np.ndarray, rows=None) -> np.ndarray:
-    """s[n] = E_{ky(n)} q[n] for every TR n (or only the TRs in ``rows``)."""
+    """s[n] = E_{ky(n)} q[n] for every TR n.  With ``rows``, only those TRs are encoded
+    and q[i] holds the voxel values of TR rows[i]."""
     rows = np.arange(seq.ntr) if rows is None else np.asarray(rows)
     s = np.zeros((rows.shape[0], seq.nkx), np.complex128)
     ky = np.asarray(seq.ky)[rows]
     for u in np.unique(ky):
         sel = np.nonzero(ky == u)[0]
         e = phase_matrix(seq, int(u))
-        s[sel] = q[rows[sel]] @ e.T
+        s[sel] = q[sel] @ e.T
     return s
 
 
-def encode_adjoint(seq, w: np.ndarray) -> np.ndarray:
-    """W[n] = E_{ky(n)}^H w[n], shape [ntr, nv]."""
-    out = np.zeros((seq.ntr, seq.nv), np.complex128)
+def encode_adjoint(seq, w: np.ndarray, voxels=None) -> np.ndarray:
+    """W[n] = E_{ky(n)}^H w[n], shape [ntr, nv] (or [ntr, len(voxels)])."""
+    nv = seq.nv if voxels is None else len(voxels)
+    out = np.zeros((seq.ntr, nv), np.complex128)
     ky = np.asarray(seq.ky)
     for u in np.unique(ky):
         sel = np.nonzero(ky == u)[0]
-        e = phase_matrix(seq, int(u))
+        e = phase_matrix(seq, int(u), voxels)
         out[sel] = w[sel] @ np.conj(e)
     return out

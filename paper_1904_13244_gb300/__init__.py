@@ -1,0 +1,117 @@
+"""GB300-native MR-STAT hot path: the signal model and its Jacobian products.
+
+MR-STAT (van der Heide et al., arXiv 1904.13244) reconstructs T1, T2 and complex
+proton density maps by an inexact Gauss-Newton method whose inner CG solve only
+needs s(alpha), J.v and Re(J^H w) (Theory, Eq. 4; Algorithms 2, 4 and 6).  These
+run in libmrstat.so (hand-written sm_103a CUDA behind a C ABI, include/mrstat.h);
+this package only marshals torch tensors into that ABI.
+
+    plan = Plan(seq)                 # seq: nx, ny, nkx, tr_ms, te_ms, flip_rad, ky, ...
+    plan.linearize(alpha)            # alpha: cuda float32 [4, nv]
+    jv = plan.jvp(v)                 # cuda complex64 [ntr, nkx]
+    g = plan.jhw(w)                  # cuda float32 [4, nv]
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _binding as _b
+from ._binding import (MrstatError, MRSTAT_FORM_PLAIN_FP32, MRSTAT_FORM_SPLIT_BF16,  # noqa: F401
+                       mrstat_plan_create, mrstat_plan_destroy, mrstat_plan_info, mrstat_linearize,
+                       mrstat_forward, mrstat_jvp, mrstat_jhw, mrstat_timecourses, mrstat_dot,
+                       mrstat_cg_fixed, mrstat_status_string, mrstat_last_error,
+                       mrstat_profile_start, mrstat_profile_stop)
+
+__all__ = ["Plan", "MrstatError", "load"]
+
+
+def load():
+    """Load libmrstat.so; raises if it has not been built."""
+    return _b.load()
+
+
+class Plan:
+    """Owns one mrstat_plan (device tables and the cached linearisation)."""
+
+    def __init__(self, seq, form: int = MRSTAT_FORM_PLAIN_FP32):
+        self.nx, self.ny, self.nkx = int(seq.nx), int(seq.ny), int(seq.nkx)
+        self.ntr = int(len(seq.flip_rad))
+        self.nv = self.nx * self.ny
+        self._h = mrstat_plan_create(seq, form)
+
+    # -- life cycle --
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value is not None:
+            mrstat_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        return mrstat_plan_info(self._h)
+
+    # -- products --
+    def _kspace(self, out):
+        if out is None:
+            out = torch.empty((self.ntr, self.nkx), dtype=torch.complex64, device="cuda")
+        return out
+
+    def _params(self, out):
+        if out is None:
+            out = torch.empty((4, self.nv), dtype=torch.float32, device="cuda")
+        return out
+
+    def linearize(self, alpha, b1=None, mask=None, stream=None):
+        mrstat_linearize(self._h, alpha, b1, mask, stream)
+
+    def forward(self, alpha, b1=None, mask=None, out=None, stream=None):
+        out = self._kspace(out)
+        mrstat_forward(self._h, alpha, b1, mask, out, stream)
+        return out
+
+    def jvp(self, v, out=None, stream=None):
+        out = self._kspace(out)
+        mrstat_jvp(self._h, v, out, stream)
+        return out
+
+    def jhw(self, w, out=None, stream=None):
+        out = self._params(out)
+        mrstat_jhw(self._h, w, out, stream)
+        return out
+
+    def timecourses(self, channel: int, out=None, stream=None):
+        if out is None:
+            out = torch.empty((self.ntr, self.nv), dtype=torch.float32, device="cuda")
+        mrstat_timecourses(self._h, channel, out, stream)
+        return out
+
+    def dot(self, a, b, out=None, stream=None):
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device="cuda")
+        mrstat_dot(self._h, a, b, a.numel(), out, stream)
+        return out
+
+    def profile_start(self, kernels=("ycontract", "jhw_dot")):
+        mrstat_profile_start(self._h, kernels)
+
+    def profile_stop(self) -> dict:
+        return mrstat_profile_stop(self._h)
+
+    def cg_fixed(self, rhs, iters: int, out=None, stream=None):
+        out = self._params(out)
+        mrstat_cg_fixed(self._h, rhs, out, iters, stream)
+        return out

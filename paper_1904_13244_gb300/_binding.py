@@ -1,0 +1,225 @@
+"""ctypes binding of libmrstat.so: argument marshalling only.
+
+Every function here has the name of the C entry point it wraps (include/mrstat.h)
+and forwards raw device pointers taken from torch tensors plus the current CUDA
+stream; all arithmetic runs in the library's kernels.  Loading fails loudly if the
+library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmrstat.so")
+
+MRSTAT_OK = 0
+MRSTAT_FORM_PLAIN_FP32 = 0
+MRSTAT_FORM_SPLIT_BF16 = 1
+
+
+class MrstatError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {message} (status {status})")
+        self.status = status
+
+
+class mrstat_seq(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nkx", ctypes.c_int32),
+                ("ntr", ctypes.c_int32), ("tr_ms", ctypes.c_double), ("te_ms", ctypes.c_double),
+                ("inversion", ctypes.c_int32), ("alternate_phase", ctypes.c_int32),
+                ("flip_rad", ctypes.POINTER(ctypes.c_float)), ("ky", ctypes.POINTER(ctypes.c_int32))]
+
+
+class mrstat_plan_info_t(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nkx", ctypes.c_int32),
+                ("ntr", ctypes.c_int32), ("nv", ctypes.c_int32), ("form", ctypes.c_int32),
+                ("ntr_padded", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("timecourse_bytes", ctypes.c_int64)]
+
+
+class mrstat_kernel_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8), ("timed", ctypes.c_int64 * 8)]
+
+
+KERNEL_IDS = {"bloch": 0, "ycontract": 1, "xdft": 2, "xdft_adj": 3, "jhw_dot": 4, "vector": 5}
+
+_lib = None
+
+_SIGS = {
+    "mrstat_plan_create": [ctypes.POINTER(mrstat_seq), ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
+    "mrstat_plan_destroy": [ctypes.c_void_p],
+    "mrstat_plan_info": [ctypes.c_void_p, ctypes.POINTER(mrstat_plan_info_t)],
+    "mrstat_linearize": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_forward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                       ctypes.c_void_p],
+    "mrstat_jvp": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_jhw": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_timecourses": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_dot": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                   ctypes.c_void_p],
+    "mrstat_cg_fixed": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
+    "mrstat_profile_start": [ctypes.c_void_p, ctypes.c_uint32],
+    "mrstat_profile_stop": [ctypes.c_void_p, ctypes.POINTER(mrstat_kernel_stats)],
+    "mrstat_status_string": [ctypes.c_int],
+    "mrstat_last_error": [],
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libmrstat.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmrstat.so not built ({path}); run paper_1904_13244_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, args in _SIGS.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name in ("mrstat_status_string", "mrstat_last_error") else ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status: int, where: str):
+    if status != MRSTAT_OK:
+        lib = load()
+        raise MrstatError(status, where, lib.mrstat_last_error().decode() or
+                          lib.mrstat_status_string(status).decode())
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+_dims_cache = {}
+
+
+def _dims(plan):
+    """(nv, ntr, nkx) of a plan, from mrstat_plan_info (cached per handle)."""
+    key = plan.value if isinstance(plan, ctypes.c_void_p) else plan
+    if key not in _dims_cache:
+        info = mrstat_plan_info(plan)
+        _dims_cache[key] = (info["nv"], info["ntr"], info["nkx"])
+    return _dims_cache[key]
+
+
+def _ptr(t, dtype, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# same-name wrappers of the C entry points
+# ---------------------------------------------------------------------------
+def mrstat_plan_create(seq, form: int = MRSTAT_FORM_PLAIN_FP32) -> ctypes.c_void_p:
+    lib = load()
+    import numpy as np
+    flips = np.ascontiguousarray(np.asarray(seq.flip_rad, dtype=np.float32))
+    ky = np.ascontiguousarray(np.asarray(seq.ky, dtype=np.int32))
+    s = mrstat_seq(int(seq.nx), int(seq.ny), int(seq.nkx), int(flips.shape[0]), float(seq.tr_ms),
+                   float(seq.te_ms), int(bool(seq.inversion)), int(bool(seq.alternate_phase)),
+                   flips.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                   ky.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    h = ctypes.c_void_p()
+    _check(lib.mrstat_plan_create(ctypes.byref(s), int(form), ctypes.byref(h)), "mrstat_plan_create")
+    return h
+
+
+def mrstat_plan_destroy(plan):
+    _dims_cache.pop(plan.value if isinstance(plan, ctypes.c_void_p) else plan, None)
+    _check(load().mrstat_plan_destroy(plan), "mrstat_plan_destroy")
+
+
+def mrstat_plan_info(plan) -> dict:
+    info = mrstat_plan_info_t()
+    _check(load().mrstat_plan_info(plan, ctypes.byref(info)), "mrstat_plan_info")
+    return {f: getattr(info, f) for f, _ in mrstat_plan_info_t._fields_}
+
+
+def mrstat_linearize(plan, alpha, b1=None, mask=None, stream=None):
+    nv, _, _ = _dims(plan)
+    _check(load().mrstat_linearize(plan, _ptr(alpha, torch.float32, (4, nv), "alpha"),
+                                   _ptr(b1, torch.float32, (nv,), "b1"),
+                                   _ptr(mask, torch.uint8, (nv,), "mask"), _stream(stream)),
+           "mrstat_linearize")
+
+
+def mrstat_forward(plan, alpha, b1, mask, s, stream=None):
+    nv, ntr, nkx = _dims(plan)
+    _check(load().mrstat_forward(plan, _ptr(alpha, torch.float32, (4, nv), "alpha"),
+                                 _ptr(b1, torch.float32, (nv,), "b1"), _ptr(mask, torch.uint8, (nv,), "mask"),
+                                 _ptr(s, torch.complex64, (ntr, nkx), "s"), _stream(stream)), "mrstat_forward")
+
+
+def mrstat_jvp(plan, v, jv, stream=None):
+    nv, ntr, nkx = _dims(plan)
+    _check(load().mrstat_jvp(plan, _ptr(v, torch.float32, (4, nv), "v"),
+                             _ptr(jv, torch.complex64, (ntr, nkx), "jv"), _stream(stream)), "mrstat_jvp")
+
+
+def mrstat_jhw(plan, w, g, stream=None):
+    nv, ntr, nkx = _dims(plan)
+    _check(load().mrstat_jhw(plan, _ptr(w, torch.complex64, (ntr, nkx), "w"),
+                             _ptr(g, torch.float32, (4, nv), "g"), _stream(stream)), "mrstat_jhw")
+
+
+def mrstat_timecourses(plan, channel, out, stream=None):
+    nv, ntr, _ = _dims(plan)
+    _check(load().mrstat_timecourses(plan, int(channel), _ptr(out, torch.float32, (ntr, nv), "out"),
+                                     _stream(stream)), "mrstat_timecourses")
+
+
+def mrstat_dot(plan, a, b, n, out, stream=None):
+    if a.numel() < n or b.numel() < n:
+        raise ValueError("a and b must hold at least n elements")
+    _check(load().mrstat_dot(plan, _ptr(a, torch.float32, name="a"), _ptr(b, torch.float32, name="b"),
+                             int(n), _ptr(out, torch.float64, (), "out"), _stream(stream)), "mrstat_dot")
+
+
+def mrstat_cg_fixed(plan, rhs, x, iters, stream=None):
+    nv, _, _ = _dims(plan)
+    _check(load().mrstat_cg_fixed(plan, _ptr(rhs, torch.float32, (4, nv), "rhs"),
+                                  _ptr(x, torch.float32, (4, nv), "x"), int(iters), _stream(stream)),
+           "mrstat_cg_fixed")
+
+
+def mrstat_profile_start(plan, kernels=("ycontract", "jhw_dot")):
+    mask = 0
+    for k in kernels:
+        mask |= 1 << KERNEL_IDS[k]
+    _check(load().mrstat_profile_start(plan, mask), "mrstat_profile_start")
+
+
+def mrstat_profile_stop(plan) -> dict:
+    st = mrstat_kernel_stats()
+    _check(load().mrstat_profile_stop(plan, ctypes.byref(st)), "mrstat_profile_stop")
+    return {name: {"launches": st.launches[i], "ms": st.ms[i], "timed": st.timed[i]}
+            for name, i in KERNEL_IDS.items()}
+
+
+def mrstat_status_string(status: int) -> str:
+    return load().mrstat_status_string(int(status)).decode()
+
+
+def mrstat_last_error() -> str:
+    return load().mrstat_last_error().decode()

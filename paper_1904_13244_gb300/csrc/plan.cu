@@ -1,0 +1,490 @@
+// Host side of libmrstat: plan life cycle, per-TR tables and the C entry points.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace mrstat {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+int fail(int status, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? MRSTAT_ERR_OUT_OF_MEMORY : MRSTAT_ERR_CUDA;
+}
+
+namespace {
+
+// Makes the plan's device current for the lifetime of the guard.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+cudaError_t dalloc(Plan* p, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+  if (e == cudaSuccess) p->bytes += (int64_t)(count * sizeof(T));
+  return e;
+}
+
+void free_plan(Plan* p) {
+  if (p == nullptr) return;
+  void* ptrs[] = {p->cs, p->phi, p->kyi, p->roots, p->ft, p->fh, p->D, p->rho, p->maskf,
+                  p->dfwd, p->cf, p->A, p->wt, p->red, p->cg_r, p->cg_p, p->cg_q, p->cg_jv,
+                  p->cg_s, p->cg_frozen};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+  delete p;
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+cudaEvent_t pool_event(Plan* p) {
+  if (p->pool_used == p->event_pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    p->event_pool.push_back(e);
+  }
+  return p->event_pool[p->pool_used++];
+}
+
+// Counts the launches of one kernel class and, while profiling it, brackets them with events.
+struct Span {
+  Plan* p;
+  int kid;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Span(Plan* plan, int k, cudaStream_t s, int nlaunch = 1) : p(plan), kid(k), st(s) {
+    p->launches[kid] += nlaunch;
+    if (p->prof_on && ((p->prof_mask >> kid) & 1u)) {
+      a = pool_event(p);
+      b = pool_event(p);
+      if (a && b) cudaEventRecord(a, st);
+    }
+  }
+  ~Span() {
+    if (a && b) {
+      cudaEventRecord(b, st);
+      p->marks.push_back({kid, a, b});
+    }
+  }
+};
+
+// exp(-2 pi i a / n) for an integer phase a, reduced exactly modulo n first
+inline void unit_root(long long a, long long n, float2* out, bool conj) {
+  long long r = a % n;
+  if (r < 0) r += n;
+  const double ang = -2.0 * M_PI * (double)r / (double)n;
+  out->x = (float)std::cos(ang);
+  out->y = (float)(conj ? -std::sin(ang) : std::sin(ang));
+}
+
+// J^H J building blocks on the plan's cached linearisation
+int do_jvp(Plan* p, const float* v, float2* jv, cudaStream_t st) {
+  cudaError_t e;
+  {
+    Span sp(p, MRSTAT_K_VECTOR, st);
+    e = launch_prep_jvp(*p, v, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "prep_jvp launch");
+  {
+    Span sp(p, MRSTAT_K_YCONTRACT, st);
+    e = launch_ycontract(*p, p->D, kChannels, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
+  {
+    Span sp(p, MRSTAT_K_XDFT, st);
+    e = launch_cgemm(p->A, p->ft, jv, p->ntr, p->nkx, p->nx, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "x-DFT launch");
+  return MRSTAT_OK;
+}
+
+int do_jhw(Plan* p, const float2* w, float* g, cudaStream_t st) {
+  cudaError_t e;
+  {
+    Span sp(p, MRSTAT_K_XDFT_ADJ, st);
+    e = launch_cgemm(w, p->fh, p->wt, p->ntr, p->nx, p->nkx, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "x-DFT adjoint launch");
+  {
+    Span sp(p, MRSTAT_K_JHW_DOT, st);
+    e = launch_jhw_dot(*p, g, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "jhw_dot launch");
+  return MRSTAT_OK;
+}
+
+cudaError_t do_dot(Plan* p, const float* a, const float* b, int64_t n, double* out, cudaStream_t st) {
+  Span sp(p, MRSTAT_K_VECTOR, st, 2);
+  return launch_dot(a, b, n, p->red, out, st);
+}
+
+}  // namespace
+}  // namespace mrstat
+
+using namespace mrstat;
+
+struct mrstat_plan : public Plan {};
+
+extern "C" {
+
+const char* mrstat_status_string(int status) {
+  switch (status) {
+    case MRSTAT_OK: return "ok";
+    case MRSTAT_ERR_INVALID_ARG: return "invalid argument";
+    case MRSTAT_ERR_SHAPE: return "invalid shape";
+    case MRSTAT_ERR_NOT_LINEARIZED: return "plan not linearised";
+    case MRSTAT_ERR_CUDA: return "CUDA error";
+    case MRSTAT_ERR_NONFINITE: return "non-finite value";
+    case MRSTAT_ERR_TIMEOUT: return "iteration budget exhausted";
+    case MRSTAT_ERR_UNSUPPORTED: return "unsupported";
+    case MRSTAT_ERR_OUT_OF_MEMORY: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+const char* mrstat_last_error(void) { return g_last_error.c_str(); }
+
+int mrstat_profile_start(mrstat_plan* plan, uint32_t kernel_mask) {
+  if (plan == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan");
+  for (int64_t& c : plan->launches) c = 0;
+  plan->marks.clear();
+  plan->pool_used = 0;
+  plan->prof_mask = kernel_mask;
+  plan->prof_on = true;
+  return MRSTAT_OK;
+}
+
+int mrstat_profile_stop(mrstat_plan* plan, mrstat_kernel_stats* out) {
+  if (plan == nullptr || out == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(plan->device);
+  std::memset(out, 0, sizeof(*out));
+  for (int k = 0; k < 8; ++k) out->launches[k] = plan->launches[k];
+  for (const Plan::Mark& m : plan->marks) {
+    cudaError_t e = cudaEventSynchronize(m.b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, m.a, m.b);
+    if (e != cudaSuccess) {
+      plan->prof_on = false;
+      return cuda_fail(e, "profile events");
+    }
+    out->ms[m.kid] += ms;
+    out->timed[m.kid] += 1;
+  }
+  plan->marks.clear();
+  plan->pool_used = 0;
+  plan->prof_on = false;
+  return MRSTAT_OK;
+}
+
+int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
+  g_last_error.clear();
+  if (out == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (seq == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "seq is NULL");
+  if (form != MRSTAT_FORM_PLAIN_FP32)
+    return fail(form == MRSTAT_FORM_SPLIT_BF16 ? MRSTAT_ERR_UNSUPPORTED : MRSTAT_ERR_INVALID_ARG,
+                "form %d not available", form);
+  if (seq->nx < 1 || seq->nx > 2048 || seq->ny < 1 || seq->ny > 2048 || seq->nkx < 1 ||
+      seq->nkx > 4096 || seq->ntr < 1 || seq->ntr > 65536)
+    return fail(MRSTAT_ERR_SHAPE, "sizes out of range: nx=%d ny=%d nkx=%d ntr=%d", seq->nx, seq->ny,
+                seq->nkx, seq->ntr);
+  if (seq->flip_rad == nullptr || seq->ky == nullptr)
+    return fail(MRSTAT_ERR_INVALID_ARG, "flip_rad or ky is NULL");
+  if (!(seq->tr_ms > 0.0) || !(seq->te_ms > 0.0) || !(seq->te_ms < seq->tr_ms) ||
+      !std::isfinite(seq->tr_ms))
+    return fail(MRSTAT_ERR_INVALID_ARG, "need 0 < te_ms < tr_ms (te=%g tr=%g)", seq->te_ms, seq->tr_ms);
+  const int lo = -(seq->ny / 2), hi = seq->ny - seq->ny / 2;
+  for (int n = 0; n < seq->ntr; ++n) {
+    if (!std::isfinite(seq->flip_rad[n]) || seq->flip_rad[n] < 0.f)
+      return fail(MRSTAT_ERR_INVALID_ARG, "flip_rad[%d] = %g is not a finite non-negative angle", n,
+                  (double)seq->flip_rad[n]);
+    if (seq->ky[n] < lo || seq->ky[n] >= hi)
+      return fail(MRSTAT_ERR_SHAPE, "ky[%d] = %d outside [%d, %d)", n, seq->ky[n], lo, hi);
+  }
+
+  mrstat_plan* p = new mrstat_plan();
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return fail(MRSTAT_ERR_CUDA, "no CUDA device");
+  }
+  p->nx = seq->nx;
+  p->ny = seq->ny;
+  p->nkx = seq->nkx;
+  p->ntr = seq->ntr;
+  p->ntr_pad = (seq->ntr + 3) / 4 * 4;
+  p->nq = p->ntr_pad / 4;
+  p->nv = seq->nx * seq->ny;
+  p->form = form;
+  p->tr_ms = seq->tr_ms;
+  p->te_ms = seq->te_ms;
+  p->inversion = seq->inversion != 0;
+  p->alternate = seq->alternate_phase != 0;
+
+  // host tables (float64, rounded once)
+  std::vector<float2> cs(p->ntr_pad);
+  std::vector<float> phi(p->ntr_pad, 0.f);
+  std::vector<int> kyi(p->ntr_pad, 0);
+  for (int n = 0; n < p->ntr_pad; ++n) {
+    double ph = 0.0;
+    if (n < p->ntr) {
+      ph = (double)seq->flip_rad[n];
+      if (p->alternate && (n & 1)) ph = -ph;  // RF phase 180 degrees rotates about +x
+      kyi[n] = ((seq->ky[n] % p->ny) + p->ny) % p->ny;
+    }
+    phi[n] = (float)ph;
+    cs[n] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+  }
+  std::vector<float2> roots(p->ny), ft((size_t)p->nx * p->nkx), fh((size_t)p->nkx * p->nx);
+  for (int k = 0; k < p->ny; ++k) unit_root(k, p->ny, &roots[k], false);
+  for (int ix = 0; ix < p->nx; ++ix)
+    for (int k = 0; k < p->nkx; ++k) {
+      const long long kx = k - p->nkx / 2;
+      unit_root(kx * ix, p->nx, &ft[(size_t)ix * p->nkx + k], false);
+      unit_root(kx * ix, p->nx, &fh[(size_t)k * p->nx + ix], true);
+    }
+
+  const size_t nv = p->nv, nq = p->nq;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  chk(dalloc(p, &p->cs, p->ntr_pad));
+  chk(dalloc(p, &p->phi, p->ntr_pad));
+  chk(dalloc(p, &p->kyi, p->ntr_pad));
+  chk(dalloc(p, &p->roots, p->ny));
+  chk(dalloc(p, &p->ft, ft.size()));
+  chk(dalloc(p, &p->fh, fh.size()));
+  const int64_t before = p->bytes;
+  chk(dalloc(p, &p->D, (size_t)kChannels * nq * nv));
+  p->d_bytes = p->bytes - before;
+  chk(dalloc(p, &p->rho, nv));
+  chk(dalloc(p, &p->maskf, nv));
+  chk(dalloc(p, &p->dfwd, nq * nv));
+  chk(dalloc(p, &p->cf, (size_t)kChannels * nv));
+  chk(dalloc(p, &p->A, (size_t)p->ntr * p->nx));
+  chk(dalloc(p, &p->wt, (size_t)p->ntr_pad * p->nx));
+  chk(dalloc(p, &p->red, kRedBlocks));
+  chk(dalloc(p, &p->cg_r, 4 * nv));
+  chk(dalloc(p, &p->cg_p, 4 * nv));
+  chk(dalloc(p, &p->cg_q, 4 * nv));
+  chk(dalloc(p, &p->cg_jv, (size_t)p->ntr * p->nkx));
+  chk(dalloc(p, &p->cg_frozen, 1));
+  if (e != cudaSuccess) {
+    int st = cuda_fail(e, "plan allocation");
+    free_plan(p);
+    return st;
+  }
+  chk(cudaMemcpy(p->cs, cs.data(), cs.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(p->phi, phi.data(), phi.size() * sizeof(float), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(p->kyi, kyi.data(), kyi.size() * sizeof(int), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(p->roots, roots.data(), roots.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(p->ft, ft.data(), ft.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(p->fh, fh.data(), fh.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  chk(cudaMemset(p->wt, 0, (size_t)p->ntr_pad * p->nx * sizeof(float2)));
+  chk(cudaDeviceSynchronize());
+  if (e != cudaSuccess) {
+    int st = cuda_fail(e, "plan tables");
+    free_plan(p);
+    return st;
+  }
+  *out = p;
+  return MRSTAT_OK;
+}
+
+int mrstat_plan_destroy(mrstat_plan* plan) {
+  if (plan == nullptr) return MRSTAT_OK;
+  DeviceGuard g(plan->device);
+  cudaDeviceSynchronize();
+  free_plan(plan);
+  return MRSTAT_OK;
+}
+
+int mrstat_plan_info(const mrstat_plan* plan, mrstat_plan_info_t* info) {
+  if (plan == nullptr || info == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL argument");
+  info->nx = plan->nx;
+  info->ny = plan->ny;
+  info->nkx = plan->nkx;
+  info->ntr = plan->ntr;
+  info->nv = plan->nv;
+  info->form = plan->form;
+  info->ntr_padded = plan->ntr_pad;
+  info->device_bytes = plan->bytes;
+  info->timecourse_bytes = plan->d_bytes;
+  return MRSTAT_OK;
+}
+
+int mrstat_linearize(mrstat_plan* plan, const float* alpha, const float* b1, const uint8_t* mask,
+                     void* stream) {
+  if (plan == nullptr || alpha == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or alpha");
+  DeviceGuard g(plan->device);
+  cudaStream_t st = as_stream(stream);
+  plan->linearized = false;
+  cudaError_t e;
+  {
+    Span sp(plan, MRSTAT_K_VECTOR, st);
+    e = launch_prep_linearize(*plan, alpha, mask, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "prep_linearize launch");
+  {
+    Span sp(plan, MRSTAT_K_BLOCH, st);
+    e = launch_bloch(*plan, alpha, b1, mask, plan->D, kChannels, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "bloch launch");
+  plan->linearized = true;
+  return MRSTAT_OK;
+}
+
+int mrstat_forward(mrstat_plan* plan, const float* alpha, const float* b1, const uint8_t* mask,
+                   float* s, void* stream) {
+  if (plan == nullptr || alpha == nullptr || s == nullptr)
+    return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, alpha or s");
+  DeviceGuard g(plan->device);
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e;
+  {
+    Span sp(plan, MRSTAT_K_BLOCH, st);
+    e = launch_bloch(*plan, alpha, b1, mask, plan->dfwd, 1, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "bloch launch");
+  {
+    Span sp(plan, MRSTAT_K_VECTOR, st);
+    e = launch_prep_forward(*plan, alpha, mask, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "prep_forward launch");
+  {
+    Span sp(plan, MRSTAT_K_YCONTRACT, st);
+    e = launch_ycontract(*plan, plan->dfwd, 1, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
+  {
+    Span sp(plan, MRSTAT_K_XDFT, st);
+    e = launch_cgemm(plan->A, plan->ft, reinterpret_cast<float2*>(s), plan->ntr, plan->nkx, plan->nx, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "x-DFT launch");
+  return MRSTAT_OK;
+}
+
+int mrstat_jvp(mrstat_plan* plan, const float* v, float* jv, void* stream) {
+  if (plan == nullptr || v == nullptr || jv == nullptr)
+    return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, v or jv");
+  if (!plan->linearized) return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_jvp before mrstat_linearize");
+  DeviceGuard g(plan->device);
+  return do_jvp(plan, v, reinterpret_cast<float2*>(jv), as_stream(stream));
+}
+
+int mrstat_jhw(mrstat_plan* plan, const float* w, float* gout, void* stream) {
+  if (plan == nullptr || w == nullptr || gout == nullptr)
+    return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, w or g");
+  if (!plan->linearized) return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_jhw before mrstat_linearize");
+  DeviceGuard g(plan->device);
+  return do_jhw(plan, reinterpret_cast<const float2*>(w), gout, as_stream(stream));
+}
+
+int mrstat_timecourses(mrstat_plan* plan, int32_t channel, float* out, void* stream) {
+  if (plan == nullptr || out == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or out");
+  if (channel < 0 || channel >= kChannels)
+    return fail(MRSTAT_ERR_INVALID_ARG, "channel %d not in [0, %d)", channel, kChannels);
+  if (!plan->linearized) return fail(MRSTAT_ERR_NOT_LINEARIZED, "timecourses before mrstat_linearize");
+  DeviceGuard g(plan->device);
+  Span sp(plan, MRSTAT_K_VECTOR, as_stream(stream));
+  cudaError_t e = launch_timecourse(*plan, channel, out, as_stream(stream));
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "timecourse launch");
+}
+
+int mrstat_dot(mrstat_plan* plan, const float* a, const float* b, int64_t n, double* out,
+               void* stream) {
+  if (plan == nullptr || out == nullptr || n < 0 || (n > 0 && (a == nullptr || b == nullptr)))
+    return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_dot");
+  DeviceGuard g(plan->device);
+  cudaError_t e = do_dot(plan, a, b, n, out, as_stream(stream));
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "dot launch");
+}
+
+int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters, void* stream) {
+  if (plan == nullptr || rhs == nullptr || x == nullptr || iters < 0)
+    return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_cg_fixed");
+  if (!plan->linearized) return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_cg_fixed before mrstat_linearize");
+  DeviceGuard g(plan->device);
+  cudaStream_t st = as_stream(stream);
+  if (plan->cg_s_cap < iters + 1) {
+    if (plan->cg_s) {
+      cudaStreamSynchronize(st);
+      cudaFree(plan->cg_s);
+      plan->bytes -= (int64_t)plan->cg_s_cap * 4 * sizeof(double);
+      plan->cg_s = nullptr;
+      plan->cg_s_cap = 0;
+    }
+    const int cap = iters + 1 < 64 ? 64 : iters + 1;
+    cudaError_t e = dalloc(plan, &plan->cg_s, (size_t)cap * 4);
+    if (e != cudaSuccess) return cuda_fail(e, "CG scalar allocation");
+    plan->cg_s_cap = cap;
+  }
+  const int64_t n = 4 * (int64_t)plan->nv;
+  double* sc = plan->cg_s;
+  cudaError_t e = cudaMemsetAsync(plan->cg_frozen, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    Span sp(plan, MRSTAT_K_VECTOR, st);
+    e = launch_cg_init(rhs, x, plan->cg_r, plan->cg_p, n, st);
+  }
+  if (e == cudaSuccess) e = do_dot(plan, plan->cg_r, plan->cg_r, n, sc + 0, st);
+  if (e != cudaSuccess) return cuda_fail(e, "CG init");
+  for (int it = 0; it < iters; ++it) {
+    double* rr = sc + 4 * it;
+    double* pq = rr + 1;
+    double* rr_next = sc + 4 * (it + 1);
+    int s = do_jvp(plan, plan->cg_p, plan->cg_jv, st);
+    if (s != MRSTAT_OK) return s;
+    s = do_jhw(plan, plan->cg_jv, plan->cg_q, st);
+    if (s != MRSTAT_OK) return s;
+    e = do_dot(plan, plan->cg_p, plan->cg_q, n, pq, st);
+    if (e == cudaSuccess) {
+      Span sp(plan, MRSTAT_K_VECTOR, st);
+      e = launch_cg_update_xr(x, plan->cg_r, plan->cg_p, plan->cg_q, n, rr, pq, plan->cg_frozen, st);
+    }
+    if (e == cudaSuccess) e = do_dot(plan, plan->cg_r, plan->cg_r, n, rr_next, st);
+    if (e == cudaSuccess) {
+      Span sp(plan, MRSTAT_K_VECTOR, st);
+      e = launch_cg_update_p(plan->cg_p, plan->cg_r, n, rr, rr_next, plan->cg_frozen, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "CG iteration");
+  }
+  return MRSTAT_OK;
+}
+
+}  // extern "C"
