@@ -179,6 +179,81 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
                     void* stream);
 
 /*
+ * Inexact Gauss-Newton reconstruction (Algorithm 6) with a trust region.
+ *
+ * Minimises f(alpha) = 1/2 ||d - s(alpha)||^2 (Theory, Eq. argmin) by outer
+ * iterations, each of which linearises the model, forms g = grad f = -Re(J_s^H (d - s))
+ * and solves Re(J_s^H J_s) p = -g approximately by Steihaug's truncated CG inside the
+ * trust region ||p|| <= Delta (Eq. 4; Methods: trust-region framework of Steihaug and
+ * Nocedal & Wright Alg. 7.2).  A trial point alpha + p, reflected into the T1/T2 box
+ * (Methods: reflection at feasible boundaries), is accepted when the actual reduction
+ * exceeds eta times the CG model's predicted reduction; Delta shrinks by 4 when the
+ * ratio is below 1/4 and doubles (up to delta_max) when it is above 3/4 with the step
+ * on the boundary.  With rho_init_iters > 0 the complex proton density is first
+ * initialised as the least-squares solution of M(alpha_0) rho = d by CGLS at
+ * T1 = t1_init_ms, T2 = t2_init_ms (Methods), and with mask_threshold > 0 the mask
+ * |rho| > mask_threshold * max |rho| is drawn and written to `mask`.
+ *
+ * Every CG scalar lives on the device in float64; the host synchronises once per
+ * outer iteration to evaluate the trust-region ratio.  On return the plan holds the
+ * linearisation at the returned alpha.
+ *   d:      device float [ntr][nkx][2] measured k-space data.
+ *   alpha:  device float [4][nv], initial guess in, estimate out.
+ *   b1:     device float [nv] or NULL (B1 = 1); a known map, not estimated.
+ *   mask:   device uint8 [nv]: in, the voxels to fit (NULL = all), unless a mask is
+ *           drawn, in which case it is written (must then be non-NULL).
+ *   report: host struct filled with the per-iteration history (may be NULL).
+ * Errors: INVALID_ARG (bad pointers or options), OUT_OF_MEMORY (the solver's work
+ * space: a second set of time courses plus a few vectors), CUDA.
+ */
+#define MRSTAT_GN_MAX_OUTER 64
+
+typedef enum mrstat_cg_exit {
+  MRSTAT_CG_MAX_ITER = 0,
+  MRSTAT_CG_BOUNDARY = 1,
+  MRSTAT_CG_NEGATIVE_CURVATURE = 2,
+  MRSTAT_CG_CONVERGED = 3,
+  MRSTAT_CG_ZERO_GRADIENT = 4
+} mrstat_cg_exit;
+
+typedef struct mrstat_gn_opts {
+  int32_t outer_iters;         /* 0..MRSTAT_GN_MAX_OUTER                               */
+  int32_t inner_iters;         /* CG iterations per outer iteration, >= 1              */
+  double delta0;               /* initial radius; <= 0: 0.1 ||alpha_0|| over the mask  */
+  double delta_max;            /* <= 0: unbounded                                      */
+  double eta;                  /* acceptance threshold on the reduction ratio          */
+  double cg_rel_tol;           /* CG stops when ||res|| <= cg_rel_tol ||g|| (0: never) */
+  double t1_min_ms, t1_max_ms; /* T1 box                                               */
+  double t2_min_ms, t2_max_ms; /* T2 box                                               */
+  int32_t rho_init_iters;      /* CGLS iterations of the rho initialisation (0: none)  */
+  double t1_init_ms, t2_init_ms;
+  double mask_threshold;       /* > 0: draw the mask after the rho initialisation       */
+} mrstat_gn_opts;
+
+typedef struct mrstat_gn_report {
+  int32_t iterations;                      /* outer iterations run                  */
+  int32_t mask_voxels;                     /* voxels inside the mask                */
+  int32_t cg_steps[MRSTAT_GN_MAX_OUTER];
+  int32_t cg_exit[MRSTAT_GN_MAX_OUTER];    /* mrstat_cg_exit                         */
+  int32_t accepted[MRSTAT_GN_MAX_OUTER];
+  double f[MRSTAT_GN_MAX_OUTER];           /* objective at the start of iteration   */
+  double gnorm[MRSTAT_GN_MAX_OUTER];
+  double delta[MRSTAT_GN_MAX_OUTER];
+  double ratio[MRSTAT_GN_MAX_OUTER];
+  double f_final;
+  double seconds;                          /* wall time of the call                 */
+} mrstat_gn_report;
+
+/* Fill opts with the defaults: 10 x 20 iterations, delta0 from alpha_0, eta = 1e-4,
+   no CG tolerance, T1 in [50, 6000] ms, T2 in [5, 3000] ms, no rho initialisation
+   (t1_init 1000 ms, t2_init 100 ms, 50 CGLS steps and threshold 0.1 when enabled). */
+void mrstat_gn_default_opts(mrstat_gn_opts* opts);
+
+int mrstat_gn_solve(mrstat_plan* plan, const float* d, float* alpha, const float* b1,
+                    uint8_t* mask, const mrstat_gn_opts* opts, mrstat_gn_report* report,
+                    void* stream);
+
+/*
  * Tracing of the plan's own kernel launches.  Launch counts are always kept; while
  * profiling is on, every launch of a kernel whose bit is set in kernel_mask is
  * bracketed by two CUDA events on its stream.  mrstat_profile_start clears the

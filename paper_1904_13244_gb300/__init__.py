@@ -20,7 +20,8 @@ from ._binding import (MrstatError, MRSTAT_FORM_PLAIN_FP32, MRSTAT_FORM_SPLIT_BF
                        mrstat_plan_create, mrstat_plan_destroy, mrstat_plan_info, mrstat_linearize,
                        mrstat_forward, mrstat_jvp, mrstat_jhw, mrstat_timecourses, mrstat_dot,
                        mrstat_cg_fixed, mrstat_status_string, mrstat_last_error,
-                       mrstat_profile_start, mrstat_profile_stop)
+                       mrstat_profile_start, mrstat_profile_stop, mrstat_gn_default_opts,
+                       mrstat_gn_solve)
 
 __all__ = ["Plan", "MrstatError", "load"]
 
@@ -104,6 +105,10 @@ class Plan:
             out = torch.empty((), dtype=torch.float64, device="cuda")
         mrstat_dot(self._h, a, b, a.numel(), out, stream)
         return out
+
+    def gn_solve(self, d, alpha, b1=None, mask=None, stream=None, **opts) -> dict:
+        """Algorithm 6 on the device; alpha (cuda float32 [4, nv]) is updated in place."""
+        return mrstat_gn_solve(self._h, d, alpha, b1, mask, mrstat_gn_default_opts(**opts), stream)
 
     def profile_start(self, kernels=("ycontract", "jhw_dot")):
         mrstat_profile_start(self._h, kernels)

@@ -44,6 +44,28 @@ class mrstat_kernel_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8), ("timed", ctypes.c_int64 * 8)]
 
 
+GN_MAX_OUTER = 64
+CG_EXIT = {0: "max_iter", 1: "boundary", 2: "negative_curvature", 3: "converged", 4: "zero_gradient"}
+
+
+class mrstat_gn_opts(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
+                ("delta0", ctypes.c_double), ("delta_max", ctypes.c_double), ("eta", ctypes.c_double),
+                ("cg_rel_tol", ctypes.c_double), ("t1_min_ms", ctypes.c_double), ("t1_max_ms", ctypes.c_double),
+                ("t2_min_ms", ctypes.c_double), ("t2_max_ms", ctypes.c_double),
+                ("rho_init_iters", ctypes.c_int32), ("t1_init_ms", ctypes.c_double),
+                ("t2_init_ms", ctypes.c_double), ("mask_threshold", ctypes.c_double)]
+
+
+class mrstat_gn_report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("mask_voxels", ctypes.c_int32),
+                ("cg_steps", ctypes.c_int32 * GN_MAX_OUTER), ("cg_exit", ctypes.c_int32 * GN_MAX_OUTER),
+                ("accepted", ctypes.c_int32 * GN_MAX_OUTER), ("f", ctypes.c_double * GN_MAX_OUTER),
+                ("gnorm", ctypes.c_double * GN_MAX_OUTER), ("delta", ctypes.c_double * GN_MAX_OUTER),
+                ("ratio", ctypes.c_double * GN_MAX_OUTER), ("f_final", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
 KERNEL_IDS = {"bloch": 0, "ycontract": 1, "xdft": 2, "xdft_adj": 3, "jhw_dot": 4, "vector": 5}
 
 _lib = None
@@ -61,6 +83,9 @@ _SIGS = {
     "mrstat_dot": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                    ctypes.c_void_p],
     "mrstat_cg_fixed": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
+    "mrstat_gn_default_opts": [ctypes.POINTER(mrstat_gn_opts)],
+    "mrstat_gn_solve": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                        ctypes.POINTER(mrstat_gn_opts), ctypes.POINTER(mrstat_gn_report), ctypes.c_void_p],
     "mrstat_profile_start": [ctypes.c_void_p, ctypes.c_uint32],
     "mrstat_profile_stop": [ctypes.c_void_p, ctypes.POINTER(mrstat_kernel_stats)],
     "mrstat_status_string": [ctypes.c_int],
@@ -78,7 +103,12 @@ def load(path: str = LIB_PATH):
         for name, args in _SIGS.items():
             f = getattr(lib, name)
             f.argtypes = args
-            f.restype = ctypes.c_char_p if name in ("mrstat_status_string", "mrstat_last_error") else ctypes.c_int
+            if name in ("mrstat_status_string", "mrstat_last_error"):
+                f.restype = ctypes.c_char_p
+            elif name == "mrstat_gn_default_opts":
+                f.restype = None
+            else:
+                f.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -201,6 +231,31 @@ def mrstat_cg_fixed(plan, rhs, x, iters, stream=None):
     _check(load().mrstat_cg_fixed(plan, _ptr(rhs, torch.float32, (4, nv), "rhs"),
                                   _ptr(x, torch.float32, (4, nv), "x"), int(iters), _stream(stream)),
            "mrstat_cg_fixed")
+
+
+def mrstat_gn_default_opts(**overrides) -> mrstat_gn_opts:
+    o = mrstat_gn_opts()
+    load().mrstat_gn_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"unknown Gauss-Newton option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def mrstat_gn_solve(plan, d, alpha, b1=None, mask=None, opts=None, stream=None) -> dict:
+    nv, ntr, nkx = _dims(plan)
+    opts = opts if opts is not None else mrstat_gn_default_opts()
+    rep = mrstat_gn_report()
+    _check(load().mrstat_gn_solve(plan, _ptr(d, torch.complex64, (ntr, nkx), "d"),
+                                  _ptr(alpha, torch.float32, (4, nv), "alpha"), _ptr(b1, torch.float32, (nv,), "b1"),
+                                  _ptr(mask, torch.uint8, (nv,), "mask"), ctypes.byref(opts), ctypes.byref(rep),
+                                  _stream(stream)), "mrstat_gn_solve")
+    k = rep.iterations
+    return {"iterations": k, "mask_voxels": rep.mask_voxels, "f": list(rep.f[:k]), "gnorm": list(rep.gnorm[:k]),
+            "delta": list(rep.delta[:k]), "ratio": list(rep.ratio[:k]), "cg_steps": list(rep.cg_steps[:k]),
+            "cg_exit": [CG_EXIT.get(x, str(x)) for x in rep.cg_exit[:k]],
+            "accepted": [bool(x) for x in rep.accepted[:k]], "f_final": rep.f_final, "seconds": rep.seconds}
 
 
 def mrstat_profile_start(plan, kernels=("ycontract", "jhw_dot")):

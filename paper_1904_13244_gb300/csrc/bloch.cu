@@ -8,6 +8,7 @@
 // phi_n = (+-1) alpha_n B1:
 //     (m_y, m_z) <- (cos phi m_y + sin phi m_z, cos phi m_z - sin phi m_y)   (Rodrigues)
 //     relax over TE:       m_y <- E2 m_y,  m_z <- 1 + E1 (m_z - 1)           (S2 decay)
+//                          (evaluated as m += (E - 1)(m - m_eq) with E - 1 from expm1f)
 //     store m_y (and the tangents) at the echo
 //     relax over TR - TE.
 // Tangents with respect to ln T1 and ln T2 (T1 and T2 times the S2 d/dT form):
@@ -41,10 +42,14 @@ bloch_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
 
   const float t1 = expf(alpha[j]);
   const float t2 = expf(alpha[nv + j]);
-  // decay factors over TE (a) and TR - TE (b), and their ln T derivatives
+  // Decay over TE (a) and TR - TE (b).  E = exp(-dt/T) is within a few 1e-4 of 1 for
+  // long T1/T2, where a float32 E would keep only ~4 significant digits of the rate
+  // 1 - E and bias every TR the same way; x = E - 1 from expm1f keeps it to 1 ulp and
+  // the updates take the form m += x * (m - m_eq).  d = (dt/T) E = dE/dln T.
   const float ra1 = te / t1, ra2 = te / t2, rb1 = tb / t1, rb2 = tb / t2;
-  const float e1a = expf(-ra1), e2a = expf(-ra2), e1b = expf(-rb1), e2b = expf(-rb2);
-  const float d1a = ra1 * e1a, d2a = ra2 * e2a, d1b = rb1 * e1b, d2b = rb2 * e2b;
+  const float x1a = expm1f(-ra1), x2a = expm1f(-ra2), x1b = expm1f(-rb1), x2b = expm1f(-rb2);
+  const float d1a = ra1 * (1.f + x1a), d2a = ra2 * (1.f + x2a);
+  const float d1b = rb1 * (1.f + x1b), d2b = rb2 * (1.f + x2b);
   const float bj = B1MAP ? b1[j] : 1.f;
 
   float my = 0.f, mz = m0z;   // magnetisation
@@ -76,16 +81,16 @@ bloch_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
         bz = c * bz - s * by;
         by = ty;
       }
-      // decay and regrowth over TE
+      // decay and regrowth over TE: m += (E - 1) o (m - m_eq), tangents gain their source terms
       float zm1 = mz - 1.f;
       if (NCH > 1) {
-        ay = e2a * ay;
-        az = fmaf(e1a, az, d1a * zm1);
-        by = fmaf(e2a, by, d2a * my);
-        bz = e1a * bz;
+        ay = fmaf(x2a, ay, ay);
+        az = fmaf(x1a, az, fmaf(d1a, zm1, az));
+        by = fmaf(x2a, by, fmaf(d2a, my, by));
+        bz = fmaf(x1a, bz, bz);
       }
-      my = e2a * my;
-      mz = fmaf(e1a, zm1, 1.f);
+      my = fmaf(x2a, my, my);
+      mz = fmaf(x1a, zm1, mz);
       o0[k] = my;
       if (NCH > 1) {
         o1[k] = ay;
@@ -94,13 +99,13 @@ bloch_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
       // decay and regrowth over TR - TE
       zm1 = mz - 1.f;
       if (NCH > 1) {
-        ay = e2b * ay;
-        az = fmaf(e1b, az, d1b * zm1);
-        by = fmaf(e2b, by, d2b * my);
-        bz = e1b * bz;
+        ay = fmaf(x2b, ay, ay);
+        az = fmaf(x1b, az, fmaf(d1b, zm1, az));
+        by = fmaf(x2b, by, fmaf(d2b, my, by));
+        bz = fmaf(x1b, bz, bz);
       }
-      my = e2b * my;
-      mz = fmaf(e1b, zm1, 1.f);
+      my = fmaf(x2b, my, my);
+      mz = fmaf(x1b, zm1, mz);
     }
     __stcs(out + (size_t)q * nv, make_float4(o0[0], o0[1], o0[2], o0[3]));
     if (NCH > 1) {

@@ -41,8 +41,15 @@ __global__ void prep_linearize_kernel(const float* __restrict__ alpha, const uin
   maskf[j] = m;
 }
 
+__global__ void prep_rho_kernel(const float2* __restrict__ rho, int nv, float2* __restrict__ cf) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nv) cf[j] = rho[j];
+}
+
 __global__ void prep_jvp_kernel(const float* __restrict__ v, const float2* __restrict__ rho,
-                                const float* __restrict__ maskf, int nv, float2* __restrict__ cf) {
+                                const float* __restrict__ maskf, int nv, float2* __restrict__ cf,
+                                const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nv) return;
   const float2 r = rho[j];  // already zero outside the mask
@@ -75,7 +82,9 @@ template <int NCH, int QB>
 __global__ void __launch_bounds__(256)
 ycontract_kernel(const float4* __restrict__ D, const float2* __restrict__ cf,
                  const int* __restrict__ kyi, const float2* __restrict__ roots, int nx, int ny,
-                 int nv, int nq, int ntr, float inv_ny, float2* __restrict__ A) {
+                 int nv, int nq, int ntr, float inv_ny, float2* __restrict__ A,
+                 const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
   extern __shared__ float2 smem[];
   constexpr int T = 4 * QB;  // TRs per block
   float2* ey = smem;         // [T][ny]
@@ -164,7 +173,8 @@ __global__ void __launch_bounds__(256)
 jhw_dot_kernel(const float4* __restrict__ D, const float2* __restrict__ wt,
                const int* __restrict__ kyi, const float2* __restrict__ roots_g,
                const float2* __restrict__ rho, const float* __restrict__ maskf, int nx, int ny,
-               int nv, int nq, float inv_ny, float* __restrict__ g) {
+               int nv, int nq, float inv_ny, float* __restrict__ g, const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
   extern __shared__ float2 smem[];
   float2* roots = smem;                                  // [ny]
   float* red = reinterpret_cast<float*>(smem + ny);      // [8][6][32]
@@ -246,15 +256,22 @@ cudaError_t launch_prep_forward(const Plan& p, const float* alpha, const uint8_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep_linearize(const Plan& p, const float* alpha, const uint8_t* mask, cudaStream_t st) {
+cudaError_t launch_prep_linearize(const Plan& p, const float* alpha, const uint8_t* mask, float2* rho,
+                                  cudaStream_t st) {
   if (p.nv == 0) return cudaSuccess;
-  prep_linearize_kernel<<<(p.nv + 255) / 256, 256, 0, st>>>(alpha, mask, p.nv, p.rho, p.maskf);
+  prep_linearize_kernel<<<(p.nv + 255) / 256, 256, 0, st>>>(alpha, mask, p.nv, rho, p.maskf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_rho(const Plan& p, const float2* rho, cudaStream_t st) {
+  if (p.nv == 0) return cudaSuccess;
+  prep_rho_kernel<<<(p.nv + 255) / 256, 256, 0, st>>>(rho, p.nv, p.cf);
   return cudaGetLastError();
 }
 
 cudaError_t launch_prep_jvp(const Plan& p, const float* v, cudaStream_t st) {
   if (p.nv == 0) return cudaSuccess;
-  prep_jvp_kernel<<<(p.nv + 255) / 256, 256, 0, st>>>(v, p.rho, p.maskf, p.nv, p.cf);
+  prep_jvp_kernel<<<(p.nv + 255) / 256, 256, 0, st>>>(v, p.rho, p.maskf, p.nv, p.cf, p.gate);
   return cudaGetLastError();
 }
 
@@ -268,13 +285,13 @@ cudaError_t launch_ycontract(const Plan& p, const float4* D, int nch, cudaStream
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(ycontract_kernel<1, kQB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     ycontract_kernel<1, kQB><<<grid, block, sm, st>>>(D, p.cf, p.kyi, p.roots, p.nx, p.ny, p.nv,
-                                                      p.nq, p.ntr, inv_ny, p.A);
+                                                      p.nq, p.ntr, inv_ny, p.A, p.gate);
   } else {
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(ycontract_kernel<kChannels, kQB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sm);
     ycontract_kernel<kChannels, kQB><<<grid, block, sm, st>>>(D, p.cf, p.kyi, p.roots, p.nx, p.ny,
-                                                              p.nv, p.nq, p.ntr, inv_ny, p.A);
+                                                              p.nv, p.nq, p.ntr, inv_ny, p.A, p.gate);
   }
   return cudaGetLastError();
 }
@@ -287,7 +304,7 @@ cudaError_t launch_jhw_dot(const Plan& p, float* g, cudaStream_t st) {
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(jhw_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   jhw_dot_kernel<<<grid, block, sm, st>>>(p.D, p.wt, p.kyi, p.roots, p.rho, p.maskf, p.nx, p.ny,
-                                          p.nv, p.nq, 1.0f / (float)p.ny, g);
+                                          p.nv, p.nq, 1.0f / (float)p.ny, g, p.gate);
   return cudaGetLastError();
 }
 

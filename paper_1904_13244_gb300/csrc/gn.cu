@@ -1,0 +1,734 @@
+// Inexact Gauss-Newton reconstruction (Algorithm 6) with a Steihaug trust region,
+// the CGLS proton-density initialisation and the mask (Methods, "Reconstructions").
+//
+// The truncated CG runs entirely on the device: its float64 scalars live in a small
+// device block, tiny single-thread kernels take the Steihaug decisions (negative
+// curvature, trust boundary, tolerance, iteration count), and once CG has stopped
+// the product kernels return at once through the plan's gate flag.  The host waits
+// once per outer iteration, to evaluate the trust-region ratio in float64.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace mrstat {
+namespace {
+
+// float64 scalar slots (gn_sc)
+enum {
+  S_F = 0,       // objective at the trial point / current point
+  S_RR,          // res . res
+  S_RR_NEW,
+  S_GNORM,
+  S_MVAL,        // CG model value m(z) - f
+  S_COEF,        // step applied to z (alpha_j or tau)
+  S_BETA,
+  S_DBD, S_RD, S_DD, S_ZD, S_ZZ,  // multidot outputs (contiguous)
+  S_ANORM2,      // ||alpha * mask||^2
+  S_GAMMA, S_GAMMA_NEW, S_QQ,     // CGLS
+  S_RHOMAX,      // max |rho| (as float bits in a double slot is not needed: stored as double)
+  S_PNORM2,      // z . z after CG
+  S_COUNT
+};
+// integer slots (gn_si)
+enum { I_ACTIVE = 0, I_CONT, I_EXIT, I_STEPS, I_FROZEN, I_MASKCOUNT, I_COUNT };
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum_n(double (&v)[NV], double* ws /* [NV][8] */) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = warp_sum(v[k]);
+    if (lane == 0) ws[k * 8 + w] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = (threadIdx.x < 8) ? ws[k * 8 + threadIdx.x] : 0.0;
+    if (w == 0) x = warp_sum(x);
+    v[k] = x;
+  }
+  __syncthreads();
+}
+
+// After thread 0 of every block stored its NV partials in part[k * gridDim.x + block], the
+// last block sums them in block order into out[0..NV) and resets the ticket.
+template <int NV>
+__device__ __forceinline__ void finish_n(double* part, unsigned* ticket, double* out, double* ws) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kT) s += ((volatile double*)part)[k * gridDim.x + i];
+    v[k] = s;
+  }
+  block_sum_n<NV>(v, ws);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = v[k];
+    *ticket = 0u;
+  }
+}
+
+int grid_for(int64_t n) {
+  int64_t b = (n + kT - 1) / kT;
+  if (b > kRedBlocks / 5) b = kRedBlocks / 5;  // room for five partial vectors
+  return (int)(b > 0 ? b : 1);
+}
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kT)
+
+// r = s - d (complex as float pairs, n floats) and f = 1/2 ||r||^2
+__global__ void __launch_bounds__(kT)
+residual_kernel(const float* __restrict__ s, const float* __restrict__ d, float* __restrict__ r,
+                int64_t n, double* part, unsigned* ticket, double* f) {
+  __shared__ double ws[8];
+  double acc[1] = {0.0};
+  GRID_STRIDE(i, n) {
+    const float v = s[i] - d[i];
+    r[i] = v;
+    acc[0] = fma((double)v, (double)v, acc[0]);
+  }
+  block_sum_n<1>(acc, ws);
+  if (threadIdx.x == 0) part[blockIdx.x] = 0.5 * acc[0];
+  finish_n<1>(part, ticket, f, ws);
+}
+
+// ||alpha * mask||^2 over all four parameter rows
+__global__ void __launch_bounds__(kT)
+masked_norm_kernel(const float* __restrict__ alpha, const uint8_t* __restrict__ mask, int nv,
+                   double* part, unsigned* ticket, double* out) {
+  __shared__ double ws[8];
+  double acc[1] = {0.0};
+  GRID_STRIDE(j, nv) {
+    if (mask[j]) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double a = alpha[k * (int64_t)nv + j];
+        acc[0] = fma(a, a, acc[0]);
+      }
+    }
+  }
+  block_sum_n<1>(acc, ws);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+  finish_n<1>(part, ticket, out, ws);
+}
+
+// Steihaug initialisation: z = 0, res = g, dir = -g, rr = g.g
+__global__ void __launch_bounds__(kT)
+st_init_kernel(const float* __restrict__ g, float* __restrict__ z, float* __restrict__ res,
+               float* __restrict__ dir, int64_t n, double* part, unsigned* ticket, double* rr) {
+  __shared__ double ws[8];
+  double acc[1] = {0.0};
+  GRID_STRIDE(i, n) {
+    const float v = g[i];
+    z[i] = 0.f;
+    res[i] = v;
+    dir[i] = -v;
+    acc[0] = fma((double)v, (double)v, acc[0]);
+  }
+  block_sum_n<1>(acc, ws);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+  finish_n<1>(part, ticket, rr, ws);
+}
+
+__global__ void st_start_kernel(double* sc, int* si) {
+  const double rr = sc[S_RR];
+  sc[S_GNORM] = sqrt(rr);
+  sc[S_MVAL] = 0.0;
+  sc[S_COEF] = 0.0;
+  sc[S_BETA] = 0.0;
+  si[I_STEPS] = 0;
+  si[I_CONT] = 0;
+  si[I_ACTIVE] = rr > 0.0 ? 1 : 0;
+  si[I_EXIT] = rr > 0.0 ? MRSTAT_CG_MAX_ITER : MRSTAT_CG_ZERO_GRADIENT;
+}
+
+// dir.q, res.dir, dir.dir, z.dir, z.z in one pass
+__global__ void __launch_bounds__(kT)
+multidot_kernel(const float* __restrict__ dir, const float* __restrict__ q, const float* __restrict__ res,
+                const float* __restrict__ z, int64_t n, const int* __restrict__ si, double* part,
+                unsigned* ticket, double* out) {
+  if (si[I_ACTIVE] == 0) return;
+  __shared__ double ws[5 * 8];
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  GRID_STRIDE(i, n) {
+    const double d = dir[i], qq = q[i], r = res[i], zz = z[i];
+    acc[0] = fma(d, qq, acc[0]);
+    acc[1] = fma(r, d, acc[1]);
+    acc[2] = fma(d, d, acc[2]);
+    acc[3] = fma(zz, d, acc[3]);
+    acc[4] = fma(zz, zz, acc[4]);
+  }
+  block_sum_n<5>(acc, ws);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) part[k * gridDim.x + blockIdx.x] = acc[k];
+  }
+  finish_n<5>(part, ticket, out, ws);
+}
+
+__device__ double to_boundary(double zz, double zd, double dd, double delta) {
+  const double disc = fmax(zd * zd + dd * (delta * delta - zz), 0.0);
+  return (-zd + sqrt(disc)) / dd;
+}
+
+// One Steihaug decision (Nocedal & Wright Alg. 7.2): choose the step along dir.
+__global__ void st_step_kernel(double* sc, int* si, double delta) {
+  if (si[I_ACTIVE] == 0) {
+    sc[S_COEF] = 0.0;
+    si[I_CONT] = 0;
+    return;
+  }
+  const double dBd = sc[S_DBD], rd = sc[S_RD], dd = sc[S_DD], zd = sc[S_ZD], zz = sc[S_ZZ];
+  si[I_STEPS] += 1;
+  if (!(dBd > 0.0)) {
+    const double tau = to_boundary(zz, zd, dd, delta);
+    sc[S_MVAL] += tau * rd + 0.5 * tau * tau * dBd;
+    sc[S_COEF] = tau;
+    si[I_CONT] = 0;
+    si[I_ACTIVE] = 0;
+    si[I_EXIT] = MRSTAT_CG_NEGATIVE_CURVATURE;
+    return;
+  }
+  const double a = sc[S_RR] / dBd;
+  const double zn2 = zz + 2.0 * a * zd + a * a * dd;
+  if (sqrt(fmax(zn2, 0.0)) >= delta) {
+    const double tau = to_boundary(zz, zd, dd, delta);
+    sc[S_MVAL] += tau * rd + 0.5 * tau * tau * dBd;
+    sc[S_COEF] = tau;
+    si[I_CONT] = 0;
+    si[I_ACTIVE] = 0;
+    si[I_EXIT] = MRSTAT_CG_BOUNDARY;
+    return;
+  }
+  sc[S_MVAL] += a * rd + 0.5 * a * a * dBd;
+  sc[S_COEF] = a;
+  si[I_CONT] = 1;
+}
+
+// z += coef dir; while continuing also res += coef q and rr_new = res.res
+__global__ void __launch_bounds__(kT)
+st_update_kernel(float* __restrict__ z, float* __restrict__ res, const float* __restrict__ dir,
+                 const float* __restrict__ q, int64_t n, const double* __restrict__ sc,
+                 const int* __restrict__ si, double* part, unsigned* ticket, double* rr_new) {
+  const double coef = sc[S_COEF];
+  const int cont = si[I_CONT];
+  if (coef == 0.0 && !cont) return;
+  __shared__ double ws[8];
+  const float c = (float)coef;
+  double acc[1] = {0.0};
+  GRID_STRIDE(i, n) {
+    z[i] = fmaf(c, dir[i], z[i]);
+    if (cont) {
+      const float r = fmaf(c, q[i], res[i]);
+      res[i] = r;
+      acc[0] = fma((double)r, (double)r, acc[0]);
+    }
+  }
+  if (!cont) return;
+  block_sum_n<1>(acc, ws);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+  finish_n<1>(part, ticket, rr_new, ws);
+}
+
+__global__ void st_beta_kernel(double* sc, int* si, double rel_tol, int max_steps) {
+  if (si[I_CONT] == 0) return;
+  const double rr_new = sc[S_RR_NEW];
+  if (sqrt(rr_new) <= rel_tol * sc[S_GNORM]) {
+    si[I_ACTIVE] = 0;
+    si[I_CONT] = 0;
+    si[I_EXIT] = MRSTAT_CG_CONVERGED;
+    return;
+  }
+  sc[S_BETA] = rr_new / sc[S_RR];
+  sc[S_RR] = rr_new;
+  if (si[I_STEPS] >= max_steps) {
+    si[I_ACTIVE] = 0;
+    si[I_CONT] = 0;
+    si[I_EXIT] = MRSTAT_CG_MAX_ITER;
+  }
+}
+
+// dir = -res + beta dir
+__global__ void __launch_bounds__(kT)
+st_dir_kernel(float* __restrict__ dir, const float* __restrict__ res, int64_t n,
+              const double* __restrict__ sc, const int* __restrict__ si) {
+  if (si[I_CONT] == 0 || si[I_ACTIVE] == 0) return;
+  const float beta = (float)sc[S_BETA];
+  GRID_STRIDE(i, n) dir[i] = fmaf(beta, dir[i], -res[i]);
+}
+
+__device__ __forceinline__ float reflect(float x, float lo, float hi) {
+  if (x > hi) x = 2.f * hi - x;
+  if (x < lo) x = 2.f * lo - x;
+  return fminf(fmaxf(x, lo), hi);
+}
+
+// trial = alpha + z inside the mask, with ln T1 and ln T2 reflected into their box
+__global__ void trial_kernel(const float* __restrict__ alpha, const float* __restrict__ z,
+                             const uint8_t* __restrict__ mask, int nv, float lt1a, float lt1b,
+                             float lt2a, float lt2b, float* __restrict__ trial) {
+  GRID_STRIDE(j, nv) {
+    const bool on = mask[j] != 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = k * (int64_t)nv + j;
+      float v = alpha[i];
+      if (on) {
+        v += z[i];
+        if (k == 0) v = reflect(v, lt1a, lt1b);
+        if (k == 1) v = reflect(v, lt2a, lt2b);
+      }
+      trial[i] = v;
+    }
+  }
+}
+
+__global__ void z_norm_kernel(const float* __restrict__ z, int64_t n, double* part, unsigned* ticket,
+                              double* out) {
+  __shared__ double ws[8];
+  double acc[1] = {0.0};
+  GRID_STRIDE(i, n) acc[0] = fma((double)z[i], (double)z[i], acc[0]);
+  block_sum_n<1>(acc, ws);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+  finish_n<1>(part, ticket, out, ws);
+}
+
+// ---- rho initialisation (CGLS on the rho block) ----
+__global__ void fill_rows_kernel(float* __restrict__ alpha, int nv, float lt1, float lt2) {
+  GRID_STRIDE(j, nv) {
+    alpha[j] = lt1;
+    alpha[nv + j] = lt2;
+    alpha[2 * (int64_t)nv + j] = 0.f;
+    alpha[3 * (int64_t)nv + j] = 0.f;
+  }
+}
+
+__global__ void fill_u8_kernel(uint8_t* __restrict__ m, int nv, uint8_t v) {
+  GRID_STRIDE(j, nv) m[j] = v;
+}
+
+// y += sign * (num / den) * x, the coefficient formed once per block; a non-positive
+// denominator or numerator freezes the iteration (flag set by block 0)
+__global__ void __launch_bounds__(kT)
+scaled_axpy_kernel(float* __restrict__ y, const float* __restrict__ x, int64_t n, const double* num,
+                   const double* den, float sign, int* frozen, int may_freeze) {
+  __shared__ float s_coef;
+  __shared__ int s_apply;
+  if (threadIdx.x == 0) {
+    const bool ok = !*frozen && *den > 0.0 && *num > 0.0;
+    s_apply = ok;
+    s_coef = ok ? (float)(*num / *den) * sign : 0.f;
+    if (!ok && may_freeze && blockIdx.x == 0) *frozen = 1;
+  }
+  __syncthreads();
+  if (!s_apply) return;
+  const float c = s_coef;
+  GRID_STRIDE(i, n) y[i] = fmaf(c, x[i], y[i]);
+}
+
+// p = s + (num / den) * p unless frozen
+__global__ void __launch_bounds__(kT)
+xpby_kernel(float* __restrict__ p, const float* __restrict__ s, int64_t n, const double* num,
+            const double* den, const int* frozen) {
+  __shared__ float s_beta;
+  __shared__ int s_apply;
+  if (threadIdx.x == 0) {
+    s_apply = !*frozen && *den > 0.0;
+    s_beta = s_apply ? (float)(*num / *den) : 0.f;
+  }
+  __syncthreads();
+  if (!s_apply) return;
+  const float b = s_beta;
+  GRID_STRIDE(i, n) p[i] = fmaf(b, p[i], s[i]);
+}
+
+__global__ void copy_scalar_kernel(double* dst, const double* src) { *dst = *src; }
+
+__global__ void rho_max_kernel(const float* __restrict__ x, int nv, double* part, unsigned* ticket,
+                               double* out) {
+  // max |rho|^2 via the same deterministic two-level pattern (max instead of sum)
+  __shared__ double ws[8];
+  __shared__ bool last;
+  double m = 0.0;
+  GRID_STRIDE(j, nv) {
+    const double a = x[j], b = x[nv + j];
+    m = fmax(m, a * a + b * b);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < kT / 32; ++w) b = fmax(b, ws[w]);
+    part[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double b = 0.0;
+  for (int i = 0; i < (int)gridDim.x; ++i) b = fmax(b, ((volatile double*)part)[i]);
+  *out = b;
+  *ticket = 0u;
+}
+
+// mask = |rho|^2 > thr^2 max|rho|^2; rho rows of alpha set to the masked CGLS solution
+__global__ void draw_mask_kernel(const float* __restrict__ x, int nv, const double* rmax2, double thr,
+                                 uint8_t* __restrict__ mask, float* __restrict__ alpha, int* count) {
+  const double lim = thr * thr * (*rmax2);
+  int c = 0;
+  GRID_STRIDE(j, nv) {
+    const float a = x[j], b = x[nv + j];
+    const bool on = (double)a * a + (double)b * b > lim;
+    mask[j] = on ? 1 : 0;
+    alpha[2 * (int64_t)nv + j] = on ? a : 0.f;
+    alpha[3 * (int64_t)nv + j] = on ? b : 0.f;
+    c += on;
+  }
+  atomicAdd(count, c);
+}
+
+__global__ void set_rho_rows_kernel(const float* __restrict__ x, int nv, float* __restrict__ alpha) {
+  GRID_STRIDE(j, nv) {
+    alpha[2 * (int64_t)nv + j] = x[j];
+    alpha[3 * (int64_t)nv + j] = x[nv + j];
+  }
+}
+
+__global__ void count_mask_kernel(const uint8_t* __restrict__ mask, int nv, int* count) {
+  int c = 0;
+  GRID_STRIDE(j, nv) c += mask[j] != 0;
+  atomicAdd(count, c);
+}
+
+template <typename T>
+void swap_ptr(T*& a, T*& b) {
+  T* t = a;
+  a = b;
+  b = t;
+}
+
+cudaError_t ensure_workspace(Plan* p) {
+  if (p->gn_ready) return cudaSuccess;
+  const size_t nv = p->nv, nk = (size_t)p->ntr * p->nkx;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  chk(dalloc(p, &p->D2, (size_t)kChannels * p->nq * nv));
+  chk(dalloc(p, &p->rho2, nv));
+  chk(dalloc(p, &p->gn_g, 4 * nv));
+  chk(dalloc(p, &p->gn_z, 4 * nv));
+  chk(dalloc(p, &p->gn_res, 4 * nv));
+  chk(dalloc(p, &p->gn_dir, 4 * nv));
+  chk(dalloc(p, &p->gn_q, 4 * nv));
+  chk(dalloc(p, &p->gn_alpha, 4 * nv));
+  chk(dalloc(p, &p->gn_trial, 4 * nv));
+  chk(dalloc(p, &p->gn_s, nk));
+  chk(dalloc(p, &p->gn_r, nk));
+  chk(dalloc(p, &p->gn_st, nk));
+  chk(dalloc(p, &p->gn_rt, nk));
+  chk(dalloc(p, &p->gn_jv, nk));
+  chk(dalloc(p, &p->gn_mask, nv));
+  chk(dalloc(p, &p->gn_sc, S_COUNT));
+  chk(dalloc(p, &p->gn_si, I_COUNT));
+  if (e == cudaSuccess) p->gn_ready = true;
+  return e;
+}
+
+struct Solver {
+  Plan* p;
+  cudaStream_t st;
+  int64_t n4;    // 4 nv
+  int64_t nkf;   // k-space floats 2 ntr nkx
+  double* sc;
+  int* si;
+
+  cudaError_t last() { return cudaGetLastError(); }
+
+  // vector kernel launch bookkeeping
+  template <typename F>
+  cudaError_t vec(F&& launch, int nlaunch = 1) {
+    Span sp(p, MRSTAT_K_VECTOR, st, nlaunch);
+    launch();
+    return cudaGetLastError();
+  }
+
+  int residual(const float2* s, const float* d, float2* r, double* f) {
+    cudaError_t e = vec([&] {
+      residual_kernel<<<grid_for(nkf), kT, 0, st>>>(reinterpret_cast<const float*>(s), d,
+                                                      reinterpret_cast<float*>(r), nkf, p->red, p->ticket, f);
+    });
+    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "residual");
+  }
+
+  // Steihaug truncated CG on B = Re(J^H J) with gradient p->gn_g; result in p->gn_z
+  int steihaug(double delta, int inner, double rel_tol) {
+    cudaError_t e = vec([&] {
+      st_init_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_g, p->gn_z, p->gn_res, p->gn_dir, n4, p->red,
+                                                  p->ticket, sc + S_RR);
+    });
+    if (e == cudaSuccess) e = vec([&] { st_start_kernel<<<1, 1, 0, st>>>(sc, si); });
+    if (e != cudaSuccess) return cuda_fail(e, "Steihaug init");
+    p->gate = si + I_ACTIVE;
+    int status = MRSTAT_OK;
+    for (int it = 0; it < inner && status == MRSTAT_OK; ++it) {
+      status = do_jvp(p, p->gn_dir, p->gn_jv, st);
+      if (status == MRSTAT_OK) status = do_jhw(p, p->gn_jv, p->gn_q, st);
+      if (status != MRSTAT_OK) break;
+      e = vec([&] {
+        multidot_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_dir, p->gn_q, p->gn_res, p->gn_z, n4, si, p->red,
+                                                     p->ticket, sc + S_DBD);
+      });
+      if (e == cudaSuccess) e = vec([&] { st_step_kernel<<<1, 1, 0, st>>>(sc, si, delta); });
+      if (e == cudaSuccess)
+        e = vec([&] {
+          st_update_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_z, p->gn_res, p->gn_dir, p->gn_q, n4, sc, si,
+                                                        p->red, p->ticket, sc + S_RR_NEW);
+        });
+      if (e == cudaSuccess) e = vec([&] { st_beta_kernel<<<1, 1, 0, st>>>(sc, si, rel_tol, inner); });
+      if (e == cudaSuccess)
+        e = vec([&] { st_dir_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_dir, p->gn_res, n4, sc, si); });
+      if (e != cudaSuccess) status = cuda_fail(e, "Steihaug iteration");
+    }
+    p->gate = nullptr;
+    if (status != MRSTAT_OK) return status;
+    e = vec([&] { z_norm_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_z, n4, p->red, p->ticket, sc + S_PNORM2); });
+    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "step norm");
+  }
+
+  // CGLS for rho at the current linearisation (rho rows only); solution rows 2..3 of gn_z
+  int cgls_rho(const float* d, int iters) {
+    const int64_t n2 = 2 * (int64_t)p->nv;
+    float* x = p->gn_z + n2;       // rows 2..3 of the solution
+    float* pr = p->gn_dir;          // direction, rows 0..1 stay zero
+    float* s = p->gn_g;             // A^H r
+    float2* r = p->gn_r;            // k-space residual d - A x
+    float2* q = p->gn_jv;
+    cudaError_t e = cudaMemsetAsync(p->gn_z, 0, 4 * p->nv * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pr, 0, 4 * p->nv * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r, d, nkf * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(si + I_FROZEN, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "CGLS init");
+    int status = do_jhw(p, r, s, st);
+    if (status != MRSTAT_OK) return status;
+    e = cudaMemcpyAsync(pr + n2, s + n2, n2 * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = do_dot(p, s + n2, s + n2, n2, sc + S_GAMMA, st);
+    if (e != cudaSuccess) return cuda_fail(e, "CGLS init");
+    for (int it = 0; it < iters; ++it) {
+      status = do_jvp(p, pr, q, st);
+      if (status != MRSTAT_OK) return status;
+      e = do_dot(p, reinterpret_cast<const float*>(q), reinterpret_cast<const float*>(q), nkf, sc + S_QQ, st);
+      if (e == cudaSuccess)
+        e = vec([&] {
+          scaled_axpy_kernel<<<grid_for(n2), kT, 0, st>>>(x, pr + n2, n2, sc + S_GAMMA, sc + S_QQ, 1.f,
+                                                          si + I_FROZEN, 1);
+        });
+      if (e == cudaSuccess)
+        e = vec([&] {
+          scaled_axpy_kernel<<<grid_for(nkf), kT, 0, st>>>(reinterpret_cast<float*>(r),
+                                                           reinterpret_cast<const float*>(q), nkf,
+                                                           sc + S_GAMMA, sc + S_QQ, -1.f, si + I_FROZEN, 0);
+        });
+      if (e != cudaSuccess) return cuda_fail(e, "CGLS update");
+      status = do_jhw(p, r, s, st);
+      if (status != MRSTAT_OK) return status;
+      e = do_dot(p, s + n2, s + n2, n2, sc + S_GAMMA_NEW, st);
+      if (e == cudaSuccess)
+        e = vec([&] {
+          xpby_kernel<<<grid_for(n2), kT, 0, st>>>(pr + n2, s + n2, n2, sc + S_GAMMA_NEW, sc + S_GAMMA,
+                                                   si + I_FROZEN);
+        });
+      if (e == cudaSuccess) e = vec([&] { copy_scalar_kernel<<<1, 1, 0, st>>>(sc + S_GAMMA, sc + S_GAMMA_NEW); });
+      if (e != cudaSuccess) return cuda_fail(e, "CGLS direction");
+    }
+    return MRSTAT_OK;
+  }
+};
+
+}  // namespace
+}  // namespace mrstat
+
+using namespace mrstat;
+
+extern "C" {
+
+void mrstat_gn_default_opts(mrstat_gn_opts* o) {
+  if (o == nullptr) return;
+  std::memset(o, 0, sizeof(*o));
+  o->outer_iters = 10;
+  o->inner_iters = 20;
+  o->delta0 = 0.0;
+  o->delta_max = 0.0;
+  o->eta = 1e-4;
+  o->cg_rel_tol = 0.0;
+  o->t1_min_ms = 50.0;
+  o->t1_max_ms = 6000.0;
+  o->t2_min_ms = 5.0;
+  o->t2_max_ms = 3000.0;
+  o->rho_init_iters = 0;
+  o->t1_init_ms = 1000.0;
+  o->t2_init_ms = 100.0;
+  o->mask_threshold = 0.0;
+}
+
+int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const float* b1, uint8_t* mask,
+                    const mrstat_gn_opts* o, mrstat_gn_report* rep, void* stream) {
+  Plan* p = reinterpret_cast<Plan*>(plan_);
+  if (p == nullptr || d == nullptr || alpha == nullptr || o == nullptr)
+    return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, d, alpha or opts");
+  if (o->outer_iters < 0 || o->outer_iters > MRSTAT_GN_MAX_OUTER || o->inner_iters < 1 ||
+      o->rho_init_iters < 0 || !(o->t1_min_ms > 0) || !(o->t1_max_ms > o->t1_min_ms) ||
+      !(o->t2_min_ms > 0) || !(o->t2_max_ms > o->t2_min_ms) || !std::isfinite(o->eta))
+    return fail(MRSTAT_ERR_INVALID_ARG, "invalid Gauss-Newton options");
+  if (o->rho_init_iters > 0 && (!(o->t1_init_ms > 0) || !(o->t2_init_ms > 0)))
+    return fail(MRSTAT_ERR_INVALID_ARG, "invalid rho initialisation point");
+  if (o->rho_init_iters > 0 && o->mask_threshold > 0 && mask == nullptr)
+    return fail(MRSTAT_ERR_INVALID_ARG, "drawing a mask needs a mask buffer");
+  DeviceGuard guard(p->device);
+  const auto t_start = std::chrono::steady_clock::now();
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = ensure_workspace(p);
+  if (e != cudaSuccess) return cuda_fail(e, "Gauss-Newton work space");
+
+  Solver S{p, st, 4 * (int64_t)p->nv, 2 * (int64_t)p->ntr * p->nkx, p->gn_sc, p->gn_si};
+  const int nv = p->nv;
+  const int g = grid_for(nv);
+  mrstat_gn_report local;
+  std::memset(&local, 0, sizeof(local));
+  int status = MRSTAT_OK;
+
+  e = cudaMemcpyAsync(p->gn_alpha, alpha, 4 * (size_t)nv * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->gn_si, 0, I_COUNT * sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "Gauss-Newton setup");
+
+  // -- rho initialisation and mask (Methods, "Reconstructions") --
+  if (o->rho_init_iters > 0) {
+    e = S.vec([&] {
+      fill_rows_kernel<<<g, kT, 0, st>>>(p->gn_alpha, nv, (float)std::log(o->t1_init_ms),
+                                         (float)std::log(o->t2_init_ms));
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "rho init fill");
+    status = do_linearize(p, p->gn_alpha, b1, nullptr, p->D, p->rho, st);
+    if (status == MRSTAT_OK) status = S.cgls_rho(d, o->rho_init_iters);
+    if (status != MRSTAT_OK) return status;
+    const float* x = p->gn_z + 2 * (int64_t)nv;
+    if (o->mask_threshold > 0) {
+      e = S.vec([&] { rho_max_kernel<<<g, kT, 0, st>>>(x, nv, p->red, p->ticket, p->gn_sc + S_RHOMAX); });
+      if (e == cudaSuccess)
+        e = S.vec([&] {
+          draw_mask_kernel<<<g, kT, 0, st>>>(x, nv, p->gn_sc + S_RHOMAX, o->mask_threshold, p->gn_mask,
+                                             p->gn_alpha, p->gn_si + I_MASKCOUNT);
+        });
+      if (e == cudaSuccess) e = cudaMemcpyAsync(mask, p->gn_mask, nv, cudaMemcpyDeviceToDevice, st);
+    } else {
+      if (mask) e = cudaMemcpyAsync(p->gn_mask, mask, nv, cudaMemcpyDeviceToDevice, st);
+      else e = S.vec([&] { fill_u8_kernel<<<g, kT, 0, st>>>(p->gn_mask, nv, 1); });
+      if (e == cudaSuccess) e = S.vec([&] { set_rho_rows_kernel<<<g, kT, 0, st>>>(x, nv, p->gn_alpha); });
+      if (e == cudaSuccess) e = S.vec([&] { count_mask_kernel<<<g, kT, 0, st>>>(p->gn_mask, nv, p->gn_si + I_MASKCOUNT); });
+    }
+  } else {
+    if (mask) e = cudaMemcpyAsync(p->gn_mask, mask, nv, cudaMemcpyDeviceToDevice, st);
+    else e = S.vec([&] { fill_u8_kernel<<<g, kT, 0, st>>>(p->gn_mask, nv, 1); });
+    if (e == cudaSuccess) e = S.vec([&] { count_mask_kernel<<<g, kT, 0, st>>>(p->gn_mask, nv, p->gn_si + I_MASKCOUNT); });
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "mask");
+
+  // -- current point --
+  status = do_linearize(p, p->gn_alpha, b1, p->gn_mask, p->D, p->rho, st);
+  if (status == MRSTAT_OK) status = do_signal(p, p->D, p->rho, p->gn_s, st);
+  if (status == MRSTAT_OK) status = S.residual(p->gn_s, d, p->gn_r, p->gn_sc + S_F);
+  if (status != MRSTAT_OK) return status;
+  e = S.vec([&] {
+    masked_norm_kernel<<<g, kT, 0, st>>>(p->gn_alpha, p->gn_mask, nv, p->red, p->ticket, p->gn_sc + S_ANORM2);
+  });
+  if (e != cudaSuccess) return cuda_fail(e, "alpha norm");
+  double hs[S_COUNT];
+  int hi[I_COUNT];
+  auto fetch = [&]() -> int {
+    cudaError_t r = cudaMemcpyAsync(hs, p->gn_sc, sizeof hs, cudaMemcpyDeviceToHost, st);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(hi, p->gn_si, sizeof hi, cudaMemcpyDeviceToHost, st);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(st);
+    return r == cudaSuccess ? MRSTAT_OK : cuda_fail(r, "Gauss-Newton scalars");
+  };
+  if ((status = fetch()) != MRSTAT_OK) return status;
+  double f = hs[S_F];
+  local.mask_voxels = hi[I_MASKCOUNT];
+  if (!std::isfinite(f)) return fail(MRSTAT_ERR_NONFINITE, "objective is not finite at the initial point");
+  double delta = o->delta0 > 0 ? o->delta0 : 0.1 * std::sqrt(hs[S_ANORM2]);
+  const double delta_max = o->delta_max > 0 ? o->delta_max : INFINITY;
+  const float lt1a = (float)std::log(o->t1_min_ms), lt1b = (float)std::log(o->t1_max_ms);
+  const float lt2a = (float)std::log(o->t2_min_ms), lt2b = (float)std::log(o->t2_max_ms);
+
+  for (int k = 0; k < o->outer_iters; ++k) {
+    // gradient g = Re(J_s^H (s - d)) at the current point
+    status = do_jhw(p, p->gn_r, p->gn_g, st);
+    if (status == MRSTAT_OK) status = S.steihaug(delta, o->inner_iters, o->cg_rel_tol);
+    if (status != MRSTAT_OK) return status;
+    e = S.vec([&] {
+      trial_kernel<<<g, kT, 0, st>>>(p->gn_alpha, p->gn_z, p->gn_mask, nv, lt1a, lt1b, lt2a, lt2b, p->gn_trial);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "trial point");
+    status = do_linearize(p, p->gn_trial, b1, p->gn_mask, p->D2, p->rho2, st);
+    if (status == MRSTAT_OK) status = do_signal(p, p->D2, p->rho2, p->gn_st, st);
+    if (status == MRSTAT_OK) status = S.residual(p->gn_st, d, p->gn_rt, p->gn_sc + S_F);
+    if (status == MRSTAT_OK) status = fetch();
+    if (status != MRSTAT_OK) return status;
+    const double ft = hs[S_F];
+    const double pred = -hs[S_MVAL];
+    const double ratio = (pred > 0 && std::isfinite(ft)) ? (f - ft) / pred : -INFINITY;
+    const double pnorm = std::sqrt(hs[S_PNORM2]);
+    local.f[k] = f;
+    local.gnorm[k] = hs[S_GNORM];
+    local.delta[k] = delta;
+    local.cg_steps[k] = hi[I_STEPS];
+    local.cg_exit[k] = hi[I_EXIT];
+    local.ratio[k] = ratio;
+    if (ratio < 0.25) delta *= 0.25;
+    else if (ratio > 0.75 && pnorm >= 0.99 * delta) delta = std::fmin(2.0 * delta, delta_max);
+    const bool acc = ratio > o->eta;
+    local.accepted[k] = acc;
+    local.iterations = k + 1;
+    if (acc) {
+      swap_ptr(p->D, p->D2);
+      swap_ptr(p->rho, p->rho2);
+      swap_ptr(p->gn_alpha, p->gn_trial);
+      swap_ptr(p->gn_s, p->gn_st);
+      swap_ptr(p->gn_r, p->gn_rt);
+      f = ft;
+    }
+  }
+  local.f_final = f;
+  // the plan's cached linearisation is the one at the returned alpha (mask gn_mask)
+  e = cudaMemcpyAsync(alpha, p->gn_alpha, 4 * (size_t)nv * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "Gauss-Newton result");
+  p->linearized = true;
+  local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  if (rep) *rep = local;
+  return MRSTAT_OK;
+}
+
+}  // extern "C"

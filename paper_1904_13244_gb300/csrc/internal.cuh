@@ -12,7 +12,7 @@ namespace mrstat {
 
 // Number of channels of the cached time courses: m_y, dm_y/dlnT1, dm_y/dlnT2.
 constexpr int kChannels = 3;
-// Blocks of the first stage of the float64 reductions.
+// Maximum number of blocks of a float64 reduction (partials buffer size).
 constexpr int kRedBlocks = 608;
 
 struct Plan {
@@ -45,6 +45,7 @@ struct Plan {
   float2* A = nullptr;      // [ntr][nx] y-contracted image rows
   float2* wt = nullptr;     // [ntr_pad][nx] x-adjoint of a k-space vector (rows >= ntr zero)
   double* red = nullptr;    // [kRedBlocks] reduction partials
+  unsigned* ticket = nullptr;  // last-block ticket of the reductions (0 between launches)
   float* cg_r = nullptr;    // [4][nv]
   float* cg_p = nullptr;    // [4][nv]
   float* cg_q = nullptr;    // [4][nv]
@@ -52,6 +53,20 @@ struct Plan {
   double* cg_s = nullptr;   // CG scalars, 4 per iteration
   int* cg_frozen = nullptr; // CG stop flag
   int cg_s_cap = 0;         // iterations the scalar buffer holds
+
+  // Gauss-Newton work space (allocated by the first mrstat_gn_solve)
+  bool gn_ready = false;
+  float4* D2 = nullptr;     // trial-point time courses
+  float2* rho2 = nullptr;   // trial-point rho * mask
+  float *gn_g = nullptr, *gn_z = nullptr, *gn_res = nullptr, *gn_dir = nullptr, *gn_q = nullptr;
+  float *gn_alpha = nullptr, *gn_trial = nullptr;
+  float2 *gn_s = nullptr, *gn_r = nullptr, *gn_st = nullptr, *gn_rt = nullptr, *gn_jv = nullptr;
+  uint8_t* gn_mask = nullptr;
+  double* gn_sc = nullptr;  // scalar block
+  int* gn_si = nullptr;     // integer state block
+
+  // kernels of the products return at once while *gate == 0 (nullptr: always run)
+  const int* gate = nullptr;
 
   int64_t bytes = 0;
   int64_t d_bytes = 0;
@@ -74,25 +89,82 @@ void set_error(const char* fmt, ...);
 int fail(int status, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 
+// Makes the plan's device current for the lifetime of the guard.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+inline cudaError_t dalloc(Plan* p, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+  if (e == cudaSuccess) p->bytes += (int64_t)(count * sizeof(T));
+  return e;
+}
+
+cudaEvent_t pool_event(Plan* p);
+
+// Counts the launches of one kernel class and, while profiling it, brackets them with events.
+struct Span {
+  Plan* p;
+  int kid;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Span(Plan* plan, int k, cudaStream_t s, int nlaunch = 1) : p(plan), kid(k), st(s) {
+    p->launches[kid] += nlaunch;
+    if (p->prof_on && ((p->prof_mask >> kid) & 1u)) {
+      a = pool_event(p);
+      b = pool_event(p);
+      if (a && b) cudaEventRecord(a, st);
+    }
+  }
+  ~Span() {
+    if (a && b) {
+      cudaEventRecord(b, st);
+      p->marks.push_back({kid, a, b});
+    }
+  }
+};
+
+// product building blocks on a plan (plan.cu); they return an mrstat_status
+int do_jvp(Plan* p, const float* v, float2* jv, cudaStream_t st);
+int do_jhw(Plan* p, const float2* w, float* g, cudaStream_t st);
+int do_signal(Plan* p, const float4* D, const float2* rho_masked, float2* s, cudaStream_t st);
+int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* mask, float4* D,
+                 float2* rho, cudaStream_t st);
+cudaError_t do_dot(Plan* p, const float* a, const float* b, int64_t n, double* out, cudaStream_t st);
+
 // ---- launchers (each returns the launch's cudaError_t) ----
 // bloch.cu
 cudaError_t launch_bloch(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,
                          float4* D, int nch, cudaStream_t st);
 // encode.cu
 cudaError_t launch_prep_forward(const Plan& p, const float* alpha, const uint8_t* mask, cudaStream_t st);
-cudaError_t launch_prep_linearize(const Plan& p, const float* alpha, const uint8_t* mask, cudaStream_t st);
+cudaError_t launch_prep_rho(const Plan& p, const float2* rho, cudaStream_t st);
+cudaError_t launch_prep_linearize(const Plan& p, const float* alpha, const uint8_t* mask, float2* rho,
+                                  cudaStream_t st);
 cudaError_t launch_prep_jvp(const Plan& p, const float* v, cudaStream_t st);
 cudaError_t launch_ycontract(const Plan& p, const float4* D, int nch, cudaStream_t st);
 cudaError_t launch_jhw_dot(const Plan& p, float* g, cudaStream_t st);
 cudaError_t launch_timecourse(const Plan& p, int channel, float* out, cudaStream_t st);
 // dft.cu
-cudaError_t launch_cgemm(const float2* A, const float2* B, float2* C, int M, int N, int K, cudaStream_t st);
+cudaError_t launch_cgemm(const float2* A, const float2* B, float2* C, int M, int N, int K,
+                         const int* gate, cudaStream_t st);
 // reduce.cu
-cudaError_t launch_dot(const float* a, const float* b, int64_t n, double* partials, double* out,
-                       cudaStream_t st);
+cudaError_t launch_dot(const float* a, const float* b, int64_t n, double* partials, unsigned* ticket,
+                       double* out, cudaStream_t st);
 cudaError_t launch_cg_init(const float* rhs, float* x, float* r, float* p, int64_t n, cudaStream_t st);
 cudaError_t launch_cg_update_xr(float* x, float* r, const float* p, const float* q, int64_t n,
-                                const double* rr, const double* pq, int* frozen, cudaStream_t st);
+                                const double* rr, const double* pq, int* frozen, double* partials,
+                                unsigned* ticket, double* rr_new, cudaStream_t st);
 cudaError_t launch_cg_update_p(float* p, const float* r, int64_t n, const double* rr_old,
                                const double* rr_new, const int* frozen, cudaStream_t st);
 

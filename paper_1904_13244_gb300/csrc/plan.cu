@@ -37,34 +37,13 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 namespace {
 
-// Makes the plan's device current for the lifetime of the guard.
-struct DeviceGuard {
-  int prev = -1;
-  bool changed = false;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
-      changed = cudaSetDevice(dev) == cudaSuccess;
-    }
-  }
-  ~DeviceGuard() {
-    if (changed) cudaSetDevice(prev);
-  }
-};
-
-template <typename T>
-cudaError_t dalloc(Plan* p, T** ptr, size_t count) {
-  *ptr = nullptr;
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
-  if (e == cudaSuccess) p->bytes += (int64_t)(count * sizeof(T));
-  return e;
-}
-
 void free_plan(Plan* p) {
   if (p == nullptr) return;
   void* ptrs[] = {p->cs, p->phi, p->kyi, p->roots, p->ft, p->fh, p->D, p->rho, p->maskf,
-                  p->dfwd, p->cf, p->A, p->wt, p->red, p->cg_r, p->cg_p, p->cg_q, p->cg_jv,
-                  p->cg_s, p->cg_frozen};
+                  p->dfwd, p->cf, p->A, p->wt, p->red, p->ticket, p->cg_r, p->cg_p, p->cg_q,
+                  p->cg_jv, p->cg_s, p->cg_frozen, p->D2, p->rho2, p->gn_g, p->gn_z, p->gn_res,
+                  p->gn_dir, p->gn_q, p->gn_alpha, p->gn_trial, p->gn_s, p->gn_r, p->gn_st,
+                  p->gn_rt, p->gn_jv, p->gn_mask, p->gn_sc, p->gn_si};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
@@ -72,37 +51,6 @@ void free_plan(Plan* p) {
 }
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
-
-cudaEvent_t pool_event(Plan* p) {
-  if (p->pool_used == p->event_pool.size()) {
-    cudaEvent_t e = nullptr;
-    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-    p->event_pool.push_back(e);
-  }
-  return p->event_pool[p->pool_used++];
-}
-
-// Counts the launches of one kernel class and, while profiling it, brackets them with events.
-struct Span {
-  Plan* p;
-  int kid;
-  cudaStream_t st;
-  cudaEvent_t a = nullptr, b = nullptr;
-  Span(Plan* plan, int k, cudaStream_t s, int nlaunch = 1) : p(plan), kid(k), st(s) {
-    p->launches[kid] += nlaunch;
-    if (p->prof_on && ((p->prof_mask >> kid) & 1u)) {
-      a = pool_event(p);
-      b = pool_event(p);
-      if (a && b) cudaEventRecord(a, st);
-    }
-  }
-  ~Span() {
-    if (a && b) {
-      cudaEventRecord(b, st);
-      p->marks.push_back({kid, a, b});
-    }
-  }
-};
 
 // exp(-2 pi i a / n) for an integer phase a, reduced exactly modulo n first
 inline void unit_root(long long a, long long n, float2* out, bool conj) {
@@ -113,7 +61,17 @@ inline void unit_root(long long a, long long n, float2* out, bool conj) {
   out->y = (float)(conj ? -std::sin(ang) : std::sin(ang));
 }
 
-// J^H J building blocks on the plan's cached linearisation
+}  // namespace
+
+cudaEvent_t pool_event(Plan* p) {
+  if (p->pool_used == p->event_pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    p->event_pool.push_back(e);
+  }
+  return p->event_pool[p->pool_used++];
+}
+
 int do_jvp(Plan* p, const float* v, float2* jv, cudaStream_t st) {
   cudaError_t e;
   {
@@ -128,7 +86,7 @@ int do_jvp(Plan* p, const float* v, float2* jv, cudaStream_t st) {
   if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
   {
     Span sp(p, MRSTAT_K_XDFT, st);
-    e = launch_cgemm(p->A, p->ft, jv, p->ntr, p->nkx, p->nx, st);
+    e = launch_cgemm(p->A, p->ft, jv, p->ntr, p->nkx, p->nx, p->gate, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "x-DFT launch");
   return MRSTAT_OK;
@@ -138,7 +96,7 @@ int do_jhw(Plan* p, const float2* w, float* g, cudaStream_t st) {
   cudaError_t e;
   {
     Span sp(p, MRSTAT_K_XDFT_ADJ, st);
-    e = launch_cgemm(w, p->fh, p->wt, p->ntr, p->nx, p->nkx, st);
+    e = launch_cgemm(w, p->fh, p->wt, p->ntr, p->nx, p->nkx, p->gate, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "x-DFT adjoint launch");
   {
@@ -149,12 +107,47 @@ int do_jhw(Plan* p, const float2* w, float* g, cudaStream_t st) {
   return MRSTAT_OK;
 }
 
-cudaError_t do_dot(Plan* p, const float* a, const float* b, int64_t n, double* out, cudaStream_t st) {
-  Span sp(p, MRSTAT_K_VECTOR, st, 2);
-  return launch_dot(a, b, n, p->red, out, st);
+int do_signal(Plan* p, const float4* D, const float2* rho_masked, float2* s, cudaStream_t st) {
+  cudaError_t e;
+  {
+    Span sp(p, MRSTAT_K_VECTOR, st);
+    e = launch_prep_rho(*p, rho_masked, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "prep_rho launch");
+  {
+    Span sp(p, MRSTAT_K_YCONTRACT, st);
+    e = launch_ycontract(*p, D, kChannels, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
+  {
+    Span sp(p, MRSTAT_K_XDFT, st);
+    e = launch_cgemm(p->A, p->ft, s, p->ntr, p->nkx, p->nx, nullptr, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "x-DFT launch");
+  return MRSTAT_OK;
 }
 
-}  // namespace
+int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* mask, float4* D,
+                 float2* rho, cudaStream_t st) {
+  cudaError_t e;
+  {
+    Span sp(p, MRSTAT_K_VECTOR, st);
+    e = launch_prep_linearize(*p, alpha, mask, rho, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "prep_linearize launch");
+  {
+    Span sp(p, MRSTAT_K_BLOCH, st);
+    e = launch_bloch(*p, alpha, b1, mask, D, kChannels, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "bloch launch");
+  return MRSTAT_OK;
+}
+
+cudaError_t do_dot(Plan* p, const float* a, const float* b, int64_t n, double* out, cudaStream_t st) {
+  Span sp(p, MRSTAT_K_VECTOR, st);
+  return launch_dot(a, b, n, p->red, p->ticket, out, st);
+}
+
 }  // namespace mrstat
 
 using namespace mrstat;
@@ -300,6 +293,7 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(dalloc(p, &p->A, (size_t)p->ntr * p->nx));
   chk(dalloc(p, &p->wt, (size_t)p->ntr_pad * p->nx));
   chk(dalloc(p, &p->red, kRedBlocks));
+  chk(dalloc(p, &p->ticket, 1));
   chk(dalloc(p, &p->cg_r, 4 * nv));
   chk(dalloc(p, &p->cg_p, 4 * nv));
   chk(dalloc(p, &p->cg_q, 4 * nv));
@@ -317,6 +311,7 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(cudaMemcpy(p->ft, ft.data(), ft.size() * sizeof(float2), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(p->fh, fh.data(), fh.size() * sizeof(float2), cudaMemcpyHostToDevice));
   chk(cudaMemset(p->wt, 0, (size_t)p->ntr_pad * p->nx * sizeof(float2)));
+  chk(cudaMemset(p->ticket, 0, sizeof(unsigned)));
   chk(cudaDeviceSynchronize());
   if (e != cudaSuccess) {
     int st = cuda_fail(e, "plan tables");
@@ -355,17 +350,8 @@ int mrstat_linearize(mrstat_plan* plan, const float* alpha, const float* b1, con
   DeviceGuard g(plan->device);
   cudaStream_t st = as_stream(stream);
   plan->linearized = false;
-  cudaError_t e;
-  {
-    Span sp(plan, MRSTAT_K_VECTOR, st);
-    e = launch_prep_linearize(*plan, alpha, mask, st);
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "prep_linearize launch");
-  {
-    Span sp(plan, MRSTAT_K_BLOCH, st);
-    e = launch_bloch(*plan, alpha, b1, mask, plan->D, kChannels, st);
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "bloch launch");
+  const int status = do_linearize(plan, alpha, b1, mask, plan->D, plan->rho, st);
+  if (status != MRSTAT_OK) return status;
   plan->linearized = true;
   return MRSTAT_OK;
 }
@@ -394,7 +380,8 @@ int mrstat_forward(mrstat_plan* plan, const float* alpha, const float* b1, const
   if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
   {
     Span sp(plan, MRSTAT_K_XDFT, st);
-    e = launch_cgemm(plan->A, plan->ft, reinterpret_cast<float2*>(s), plan->ntr, plan->nkx, plan->nx, st);
+    e = launch_cgemm(plan->A, plan->ft, reinterpret_cast<float2*>(s), plan->ntr, plan->nkx, plan->nx,
+                     nullptr, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "x-DFT launch");
   return MRSTAT_OK;
@@ -475,9 +462,9 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
     e = do_dot(plan, plan->cg_p, plan->cg_q, n, pq, st);
     if (e == cudaSuccess) {
       Span sp(plan, MRSTAT_K_VECTOR, st);
-      e = launch_cg_update_xr(x, plan->cg_r, plan->cg_p, plan->cg_q, n, rr, pq, plan->cg_frozen, st);
+      e = launch_cg_update_xr(x, plan->cg_r, plan->cg_p, plan->cg_q, n, rr, pq, plan->cg_frozen, plan->red,
+                              plan->ticket, rr_next, st);
     }
-    if (e == cudaSuccess) e = do_dot(plan, plan->cg_r, plan->cg_r, n, rr_next, st);
     if (e == cudaSuccess) {
       Span sp(plan, MRSTAT_K_VECTOR, st);
       e = launch_cg_update_p(plan->cg_p, plan->cg_r, n, rr, rr_next, plan->cg_frozen, st);

@@ -1,8 +1,12 @@
 // K5: float64-accumulated inner products and the vector updates of the inner CG
-// solve (Algorithm 6; Eq. 4 solved by CG).  Reductions are deterministic: a fixed
-// grid of partial sums (warp shuffles, then shared memory), then one block that sums
-// the partials in a fixed order.  CG scalars never leave the device: each update
-// kernel reads the float64 inner products it needs and forms alpha or beta itself.
+// solve (Algorithm 6; Eq. 4 solved by CG).
+//
+// Reductions are deterministic and single-pass: every block writes its partial sum,
+// and the last block to finish (a release fence plus an atomic ticket) adds the
+// partials in block order and resets the ticket for the next launch.  CG scalars
+// never leave the device: each update kernel reads the float64 inner products it
+// needs, forms alpha or beta once per block (GB300's float64 rate makes a per-thread
+// division visible) and the x/r update also produces the partial sums of r.r.
 #include "internal.cuh"
 
 namespace mrstat {
@@ -14,35 +18,52 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Block-wide sum; the result is valid in thread 0.  Uses `ws` (>= THREADS/32 doubles).
 template <int THREADS>
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double ws[THREADS / 32];
+__device__ __forceinline__ double block_sum(double v, double* ws) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) ws[w] = v;
   __syncthreads();
   v = (threadIdx.x < THREADS / 32) ? ws[threadIdx.x] : 0.0;
   if (w == 0) v = warp_sum(v);
-  return v;  // valid in thread 0
+  __syncthreads();
+  return v;
 }
 
-__global__ void __launch_bounds__(256)
-dot_partial_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
-                   double* __restrict__ part) {
+// Called by every thread after thread 0 of each block stored its partial in part[blockIdx.x].
+// The last block sums all partials in order into *out.
+template <int THREADS>
+__device__ __forceinline__ void finish_reduction(double* part, unsigned* ticket, double* out, double* ws) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
   double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += THREADS) s += ((volatile double*)part)[i];
+  s = block_sum<THREADS>(s, ws);
+  if (threadIdx.x == 0) {
+    *out = s;
+    *ticket = 0u;
+  }
+}
+
+constexpr int kT = 256;
+
+__global__ void __launch_bounds__(kT)
+dot_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n, double* part,
+           unsigned* ticket, double* __restrict__ out) {
+  __shared__ double ws[kT / 32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
     s = fma((double)a[i], (double)b[i], s);
-  s = block_sum<256>(s);
+  s = block_sum<kT>(s, ws);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-__global__ void __launch_bounds__(256)
-dot_final_kernel(const double* __restrict__ part, int np, double* __restrict__ out) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < np; i += 256) s += part[i];
-  s = block_sum<256>(s);
-  if (threadIdx.x == 0) *out = s;
+  finish_reduction<kT>(part, ticket, out, ws);
 }
 
 __global__ void cg_init_kernel(const float* __restrict__ rhs, float* __restrict__ x,
@@ -56,68 +77,86 @@ __global__ void cg_init_kernel(const float* __restrict__ rhs, float* __restrict_
   }
 }
 
-// alpha = rr / pq, or 0 once the iteration is frozen (pq <= 0 or rr == 0)
-__device__ __forceinline__ double cg_alpha(double rr, double pq, int frozen) {
-  return (frozen || !(pq > 0.0) || !(rr > 0.0)) ? 0.0 : rr / pq;
-}
-
-__global__ void cg_update_xr_kernel(float* __restrict__ x, float* __restrict__ r,
-                                    const float* __restrict__ p, const float* __restrict__ q,
-                                    int64_t n, const double* __restrict__ rr,
-                                    const double* __restrict__ pq, int* __restrict__ frozen) {
-  const int fz = *frozen;
-  const double al = cg_alpha(*rr, *pq, fz);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && al == 0.0) *frozen = 1;
-  if (al == 0.0) return;
-  const float a = (float)al;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fmaf(a, p[i], x[i]);
-    r[i] = fmaf(-a, q[i], r[i]);
+// x += alpha p, r -= alpha q with alpha = rr / pq (0 once frozen: pq <= 0 or rr == 0),
+// then rr_new = r.r.  When alpha is 0 the vectors are left alone and rr_new = rr.
+__global__ void __launch_bounds__(kT)
+cg_update_xr_kernel(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p,
+                    const float* __restrict__ q, int64_t n, const double* __restrict__ rr,
+                    const double* __restrict__ pq, int* __restrict__ frozen, double* part,
+                    unsigned* ticket, double* __restrict__ rr_new) {
+  __shared__ double ws[kT / 32];
+  __shared__ float s_alpha;
+  __shared__ int s_apply;
+  if (threadIdx.x == 0) {
+    const double rrv = *rr, pqv = *pq;
+    const bool ok = !*frozen && pqv > 0.0 && rrv > 0.0;
+    s_alpha = ok ? (float)(rrv / pqv) : 0.f;
+    s_apply = ok;
+    if (!ok && blockIdx.x == 0) *frozen = 1;
   }
+  __syncthreads();
+  const float al = s_alpha;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    float ri = r[i];
+    if (s_apply) {
+      x[i] = fmaf(al, p[i], x[i]);
+      ri = fmaf(-al, q[i], ri);
+      r[i] = ri;
+    }
+    s = fma((double)ri, (double)ri, s);
+  }
+  s = block_sum<kT>(s, ws);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  finish_reduction<kT>(part, ticket, rr_new, ws);
 }
 
-__global__ void cg_update_p_kernel(float* __restrict__ p, const float* __restrict__ r, int64_t n,
-                                   const double* __restrict__ rr_old,
-                                   const double* __restrict__ rr_new, const int* __restrict__ frozen) {
-  if (*frozen) return;
-  const float beta = (float)(*rr_new / *rr_old);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
+__global__ void __launch_bounds__(kT)
+cg_update_p_kernel(float* __restrict__ p, const float* __restrict__ r, int64_t n,
+                   const double* __restrict__ rr_old, const double* __restrict__ rr_new,
+                   const int* __restrict__ frozen) {
+  __shared__ float s_beta;
+  __shared__ int s_apply;
+  if (threadIdx.x == 0) {
+    s_apply = !*frozen;
+    s_beta = s_apply ? (float)(*rr_new / *rr_old) : 0.f;
+  }
+  __syncthreads();
+  if (!s_apply) return;
+  const float beta = s_beta;
+  for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
     p[i] = fmaf(beta, p[i], r[i]);
 }
 
 int grid_for(int64_t n) {
-  int64_t b = (n + 255) / 256;
-  return (int)(b < 2 * kRedBlocks ? (b > 0 ? b : 1) : 2 * kRedBlocks);
+  int64_t b = (n + kT - 1) / kT;
+  if (b > kRedBlocks) b = kRedBlocks;
+  return (int)(b > 0 ? b : 1);
 }
 
 }  // namespace
 
-cudaError_t launch_dot(const float* a, const float* b, int64_t n, double* partials, double* out,
-                       cudaStream_t st) {
-  int64_t blocks = (n + 255) / 256;
-  if (blocks > kRedBlocks) blocks = kRedBlocks;
-  if (blocks < 1) blocks = 1;
-  dot_partial_kernel<<<(int)blocks, 256, 0, st>>>(a, b, n, partials);
-  dot_final_kernel<<<1, 256, 0, st>>>(partials, (int)blocks, out);
+cudaError_t launch_dot(const float* a, const float* b, int64_t n, double* partials, unsigned* ticket,
+                       double* out, cudaStream_t st) {
+  dot_kernel<<<grid_for(n), kT, 0, st>>>(a, b, n, partials, ticket, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_init(const float* rhs, float* x, float* r, float* p, int64_t n, cudaStream_t st) {
-  cg_init_kernel<<<grid_for(n), 256, 0, st>>>(rhs, x, r, p, n);
+  cg_init_kernel<<<grid_for(n), kT, 0, st>>>(rhs, x, r, p, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update_xr(float* x, float* r, const float* p, const float* q, int64_t n,
-                                const double* rr, const double* pq, int* frozen, cudaStream_t st) {
-  cg_update_xr_kernel<<<grid_for(n), 256, 0, st>>>(x, r, p, q, n, rr, pq, frozen);
+                                const double* rr, const double* pq, int* frozen, double* partials,
+                                unsigned* ticket, double* rr_new, cudaStream_t st) {
+  cg_update_xr_kernel<<<grid_for(n), kT, 0, st>>>(x, r, p, q, n, rr, pq, frozen, partials, ticket, rr_new);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update_p(float* p, const float* r, int64_t n, const double* rr_old,
                                const double* rr_new, const int* frozen, cudaStream_t st) {
-  cg_update_p_kernel<<<grid_for(n), 256, 0, st>>>(p, r, n, rr_old, rr_new, frozen);
+  cg_update_p_kernel<<<grid_for(n), kT, 0, st>>>(p, r, n, rr_old, rr_new, frozen);
   return cudaGetLastError();
 }
 

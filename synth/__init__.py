@@ -95,8 +95,10 @@ def make_sequence(nx: int, ny: int, fills: int, tr_ms: float, te_ms: float, seed
                   nkx: int | None = None, extra_trs: int = 0, inversion: bool = True,
                   alternate_phase: bool = True, max_deg: float = 60.0) -> Sequence:
     ntr = fills * ny + extra_trs
+    # flips are rounded to float32 so that a float32 consumer sees exactly these values
+    flips = flip_train(ntr, fills + extra_trs / max(ny, 1), seed, max_deg).astype(np.float32)
     return Sequence(nx=nx, ny=ny, nkx=nx if nkx is None else nkx, tr_ms=tr_ms, te_ms=te_ms,
-                    flip_rad=flip_train(ntr, fills + extra_trs / max(ny, 1), seed, max_deg),
+                    flip_rad=flips.astype(np.float64),
                     ky=cartesian_ky(ntr, ny), inversion=inversion,
                     alternate_phase=alternate_phase)
 

@@ -1,0 +1,139 @@
+"""GPU Gauss-Newton (mrstat_gn_solve) against the oracle's trust-region solver.
+
+Both run Algorithm 6 with the same Steihaug truncated CG and trust-region rules; the
+GPU keeps vectors in float32 and scalars in float64, so trajectories agree closely
+at first and drift slowly.  Bars: objective and gradient norm at the start 1e-5
+(single products), CG exit reasons and step counts equal, the first step 1e-3
+(ten float32 CG iterations), objective history 1e-3 over four outer iterations,
+noiseless recovery NRMSE < 1e-3.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import model, solver, metrics
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mr():
+    import paper_1904_13244_gb300 as mr
+    from paper_1904_13244_gb300 import build
+    build.build()
+    return mr
+
+
+def f32(x):
+    return np.asarray(x).astype(np.float32).astype(np.float64)
+
+
+def truth_of(ph):
+    return f32(np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(),
+                         ph.rho.imag.ravel()]))
+
+
+def cuda(x, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def noisy_quad():
+    seq, ph = synth.config("quad16")
+    truth = truth_of(ph)
+    d = synth.add_noise(model.forward(seq, truth), 50.0, 3)
+    d = d.astype(np.complex64).astype(np.complex128)
+    a0 = f32(truth + 0.05 * synth.random_params(seq.nv, 4))
+    return seq, ph, truth, d, a0
+
+
+def test_first_outer_iteration_matches_oracle(mr, noisy_quad):
+    seq, ph, truth, d, a0 = noisy_quad
+    opts = solver.GNOptions(outer_iters=1, inner_iters=10)
+    a_ref, rep_ref = solver.gauss_newton(seq, d, a0, opts=opts)
+    with mr.Plan(seq) as plan:
+        a = cuda(a0)
+        rep = plan.gn_solve(cuda(d, torch.complex64), a, outer_iters=1, inner_iters=10)
+        a_gpu = a.cpu().numpy()
+    assert abs(rep["f"][0] - rep_ref.f[0]) / rep_ref.f[0] < 1e-5
+    assert abs(rep["gnorm"][0] - rep_ref.gnorm[0]) / rep_ref.gnorm[0] < 1e-5
+    assert rep["cg_exit"][0] == rep_ref.exit[0]
+    assert rep["cg_steps"][0] == rep_ref.cg_steps[0]
+    assert abs(rep["delta"][0] - rep_ref.delta[0]) / rep_ref.delta[0] < 1e-6
+    assert rep["accepted"][0] == rep_ref.accepted[0]
+    assert metrics.relerr(a_gpu - a0, a_ref - a0) < 1e-3
+
+
+def test_objective_history_matches_oracle(mr, noisy_quad):
+    seq, ph, truth, d, a0 = noisy_quad
+    opts = solver.GNOptions(outer_iters=4, inner_iters=20)
+    a_ref, rep_ref = solver.gauss_newton(seq, d, a0, opts=opts)
+    with mr.Plan(seq) as plan:
+        a = cuda(a0)
+        rep = plan.gn_solve(cuda(d, torch.complex64), a, outer_iters=4, inner_iters=20)
+    assert rep["accepted"] == rep_ref.accepted
+    assert np.allclose(rep["f"], rep_ref.f, rtol=1e-3)
+    assert abs(rep["f_final"] - rep_ref.f_final) / rep_ref.f_final < 1e-3
+
+
+def test_rho_initialisation_and_mask_match_oracle(mr):
+    seq, ph = synth.config("ellipse64")
+    truth = truth_of(ph)
+    d = model.forward(seq, truth).astype(np.complex64).astype(np.complex128)
+    a0_ref, mask_ref = solver.initial_alpha(seq, d, seq.nv, rho_iters=30)
+    with mr.Plan(seq) as plan:
+        a = cuda(np.zeros((4, seq.nv)))
+        mask = torch.zeros(seq.nv, dtype=torch.uint8, device="cuda")
+        rep = plan.gn_solve(cuda(d, torch.complex64), a, mask=mask, outer_iters=0, rho_init_iters=30,
+                            mask_threshold=0.1)
+        a_gpu = a.cpu().numpy()
+        m_gpu = mask.cpu().numpy().astype(bool)
+    # the masks may only differ where |rho| sits at the threshold
+    rho_ref = a0_ref[2] + 1j * a0_ref[3]
+    diff = m_gpu != mask_ref
+    thr = 0.1 * np.abs(rho_ref).max()
+    assert np.all(np.abs(np.abs(rho_ref[diff]) - thr) < 1e-3 * thr)
+    assert rep["mask_voxels"] == int(m_gpu.sum())
+    both = m_gpu & mask_ref
+    assert metrics.relerr((a_gpu[2] + 1j * a_gpu[3])[both], rho_ref[both]) < 1e-4
+    assert np.allclose(a_gpu[0], np.log(1000.0)) and np.allclose(a_gpu[1], np.log(100.0))
+
+
+@pytest.mark.parametrize("seed", [0, 2])
+def test_noiseless_recovery_from_the_papers_initial_guess(mr, seed):
+    seq = synth.make_sequence(16, 16, 24, 7.8, 3.9, seed=seed)
+    ph = synth.quadrant_phantom(16, seed)
+    truth = truth_of(ph)
+    d = model.forward(seq, truth)
+    with mr.Plan(seq) as plan:
+        a = cuda(np.zeros((4, seq.nv)))
+        mask = torch.zeros(seq.nv, dtype=torch.uint8, device="cuda")
+        rep = plan.gn_solve(cuda(d, torch.complex64), a, mask=mask, outer_iters=10, inner_iters=20,
+                            rho_init_iters=50, mask_threshold=0.1)
+        a_gpu = a.cpu().numpy().astype(np.float64)
+    assert rep["mask_voxels"] == seq.nv
+    assert rep["f_final"] < 1e-5 * rep["f"][0]
+    assert metrics.nrmse(np.exp(a_gpu[0]), ph.t1_ms.ravel()) < 1e-3
+    assert metrics.nrmse(np.exp(a_gpu[1]), ph.t2_ms.ravel()) < 1e-3
+    assert metrics.nrmse(a_gpu[2] + 1j * a_gpu[3], ph.rho.ravel()) < 1e-3
+
+
+def test_plan_holds_the_final_linearisation(mr, noisy_quad):
+    seq, ph, truth, d, a0 = noisy_quad
+    with mr.Plan(seq) as plan:
+        a = cuda(a0)
+        plan.gn_solve(cuda(d, torch.complex64), a, outer_iters=2, inner_iters=5)
+        lin = model.linearize(seq, a.cpu().numpy().astype(np.float64))
+        tc = plan.timecourses(0).cpu().numpy()
+    assert metrics.relerr(tc, lin.m.imag) < 1e-5
+
+
+def test_invalid_options_are_rejected(mr, noisy_quad):
+    seq, ph, truth, d, a0 = noisy_quad
+    with mr.Plan(seq) as plan:
+        for bad in [dict(outer_iters=-1), dict(outer_iters=65), dict(inner_iters=0),
+                    dict(t1_min_ms=0.0), dict(t2_max_ms=1.0), dict(rho_init_iters=5, mask_threshold=0.1)]:
+            with pytest.raises(mr.MrstatError) as e:
+                plan.gn_solve(cuda(d, torch.complex64), cuda(a0), **bad)
+            assert e.value.status == 1, bad

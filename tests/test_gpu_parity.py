@@ -30,8 +30,9 @@ def mr():
 
 
 def alpha_of(ph):
+    """Parameter maps rounded to float32 (the ABI's input type), held in float64 for the oracle."""
     return np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(),
-                     ph.rho.imag.ravel()])
+                     ph.rho.imag.ravel()]).astype(np.float32).astype(np.float64)
 
 
 def random_phantom(nx, ny, seed):
@@ -102,7 +103,7 @@ def test_mask_b1_and_shuffled_ky(mr):
     seq = synth.make_sequence(nx, ny, 3, 7.6, 3.8, seed=4, extra_trs=6)
     seq.ky = np.random.default_rng(3).permutation(seq.ky).astype(np.int32)
     ph = random_phantom(nx, ny, 9)
-    b1 = synth.smooth_b1(nx, ny, 5).ravel()
+    b1 = synth.smooth_b1(nx, ny, 5).ravel().astype(np.float32).astype(np.float64)
     mask = np.random.default_rng(1).random(seq.nv) > 0.3
     alpha = alpha_of(ph)
     lin = model.linearize(seq, alpha, b1=b1, mask=mask)
