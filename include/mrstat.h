@@ -58,7 +58,9 @@ typedef enum mrstat_status {
 /* Numerical forms of the encoding contraction. */
 typedef enum mrstat_form {
   MRSTAT_FORM_PLAIN_FP32 = 0,     /* every step in FP32 on the CUDA cores               */
-  MRSTAT_FORM_SPLIT_BF16 = 1      /* x-DFT as split-BF16 tensor-core products, FP32 acc */
+  MRSTAT_FORM_SPLIT_BF16 = 1      /* readout DFT on tcgen05 tensor cores as split-BF16
+                                     products (hi*hi + hi*lo + lo*hi), FP32 accumulation;
+                                     everything else as in the plain form              */
 } mrstat_form;
 
 /*
@@ -107,6 +109,14 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out);
 int mrstat_plan_destroy(mrstat_plan* plan);
 
 int mrstat_plan_info(const mrstat_plan* plan, mrstat_plan_info_t* info);
+
+/*
+ * Wait for the plan's device work and report device-side failures: returns
+ * MRSTAT_ERR_TIMEOUT (and clears the flag) when a tensor-core kernel stopped because a
+ * bounded wait on its pipeline barriers ran out; its outputs are then undefined.
+ * Synchronises the plan's device.
+ */
+int mrstat_plan_check(mrstat_plan* plan);
 
 /*
  * Linearise the model at alpha (Algorithm 2 step 1 for every voxel, with the

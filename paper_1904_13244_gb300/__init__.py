@@ -21,7 +21,7 @@ from ._binding import (MrstatError, MRSTAT_FORM_PLAIN_FP32, MRSTAT_FORM_SPLIT_BF
                        mrstat_forward, mrstat_jvp, mrstat_jhw, mrstat_timecourses, mrstat_dot,
                        mrstat_cg_fixed, mrstat_status_string, mrstat_last_error,
                        mrstat_profile_start, mrstat_profile_stop, mrstat_gn_default_opts,
-                       mrstat_gn_solve)
+                       mrstat_gn_solve, mrstat_plan_check)
 
 __all__ = ["Plan", "MrstatError", "load"]
 
@@ -64,6 +64,10 @@ class Plan:
 
     def info(self) -> dict:
         return mrstat_plan_info(self._h)
+
+    def check(self):
+        """Synchronise and raise if a device-side bounded wait gave up."""
+        mrstat_plan_check(self._h)
 
     # -- products --
     def _kspace(self, out):

@@ -74,6 +74,7 @@ _SIGS = {
     "mrstat_plan_create": [ctypes.POINTER(mrstat_seq), ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
     "mrstat_plan_destroy": [ctypes.c_void_p],
     "mrstat_plan_info": [ctypes.c_void_p, ctypes.POINTER(mrstat_plan_info_t)],
+    "mrstat_plan_check": [ctypes.c_void_p],
     "mrstat_linearize": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_forward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                        ctypes.c_void_p],
@@ -184,6 +185,10 @@ def mrstat_plan_info(plan) -> dict:
     info = mrstat_plan_info_t()
     _check(load().mrstat_plan_info(plan, ctypes.byref(info)), "mrstat_plan_info")
     return {f: getattr(info, f) for f, _ in mrstat_plan_info_t._fields_}
+
+
+def mrstat_plan_check(plan):
+    _check(load().mrstat_plan_check(plan), "mrstat_plan_check")
 
 
 def mrstat_linearize(plan, alpha, b1=None, mask=None, stream=None):

@@ -667,11 +667,18 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   if (e != cudaSuccess) return cuda_fail(e, "alpha norm");
   double hs[S_COUNT];
   int hi[I_COUNT];
+  int herr = 0;
   auto fetch = [&]() -> int {
     cudaError_t r = cudaMemcpyAsync(hs, p->gn_sc, sizeof hs, cudaMemcpyDeviceToHost, st);
     if (r == cudaSuccess) r = cudaMemcpyAsync(hi, p->gn_si, sizeof hi, cudaMemcpyDeviceToHost, st);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(&herr, p->dev_err, sizeof herr, cudaMemcpyDeviceToHost, st);
     if (r == cudaSuccess) r = cudaStreamSynchronize(st);
-    return r == cudaSuccess ? MRSTAT_OK : cuda_fail(r, "Gauss-Newton scalars");
+    if (r != cudaSuccess) return cuda_fail(r, "Gauss-Newton scalars");
+    if (herr) {
+      cudaMemsetAsync(p->dev_err, 0, sizeof(int), st);
+      return fail(MRSTAT_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on its pipeline barriers");
+    }
+    return MRSTAT_OK;
   };
   if ((status = fetch()) != MRSTAT_OK) return status;
   double f = hs[S_F];

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/mrstat.h"
+#include "tc_gemm.cuh"
 
 namespace mrstat {
 
@@ -64,6 +65,15 @@ struct Plan {
   uint8_t* gn_mask = nullptr;
   double* gn_sc = nullptr;  // scalar block
   int* gn_si = nullptr;     // integer state block
+
+  // split-BF16 readout DFT (form MRSTAT_FORM_SPLIT_BF16)
+  int kf_pad = 0, ka_pad = 0;       // padded K of the forward (2 nx) and adjoint (2 nkx) GEMMs
+  void *bf_ft_hi = nullptr, *bf_ft_lo = nullptr;  // [2 nkx][kf_pad] forward DFT, K-major
+  void *bf_fh_hi = nullptr, *bf_fh_lo = nullptr;  // [2 nx][ka_pad] adjoint DFT, K-major
+  void *bf_a_hi = nullptr, *bf_a_lo = nullptr;    // [ntr][kf_pad] split rows A
+  void *bf_w_hi = nullptr, *bf_w_lo = nullptr;    // [ntr][ka_pad] split k-space rows
+  TcOperand* tc = nullptr;          // [4]: A rows, forward B, k-space rows, adjoint B
+  int* dev_err = nullptr;           // set by a kernel whose bounded wait ran out
 
   // kernels of the products return at once while *gate == 0 (nullptr: always run)
   const int* gate = nullptr;
@@ -141,6 +151,9 @@ int do_signal(Plan* p, const float4* D, const float2* rho_masked, float2* s, cud
 int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* mask, float4* D,
                  float2* rho, cudaStream_t st);
 cudaError_t do_dot(Plan* p, const float* a, const float* b, int64_t n, double* out, cudaStream_t st);
+// readout DFT of rows A [ntr][nx] (complex) into out [ntr][nkx], and its adjoint
+int do_xdft(Plan* p, const float2* A, float2* out, const int* gate, cudaStream_t st);
+int do_xdft_adj(Plan* p, const float2* w, float2* out, const int* gate, cudaStream_t st);
 
 // ---- launchers (each returns the launch's cudaError_t) ----
 // bloch.cu

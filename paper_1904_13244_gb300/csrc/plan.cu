@@ -43,10 +43,12 @@ void free_plan(Plan* p) {
                   p->dfwd, p->cf, p->A, p->wt, p->red, p->ticket, p->cg_r, p->cg_p, p->cg_q,
                   p->cg_jv, p->cg_s, p->cg_frozen, p->D2, p->rho2, p->gn_g, p->gn_z, p->gn_res,
                   p->gn_dir, p->gn_q, p->gn_alpha, p->gn_trial, p->gn_s, p->gn_r, p->gn_st,
-                  p->gn_rt, p->gn_jv, p->gn_mask, p->gn_sc, p->gn_si};
+                  p->gn_rt, p->gn_jv, p->gn_mask, p->gn_sc, p->gn_si, p->bf_ft_hi, p->bf_ft_lo,
+                  p->bf_fh_hi, p->bf_fh_lo, p->bf_a_hi, p->bf_a_lo, p->bf_w_hi, p->bf_w_lo, p->dev_err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+  delete[] p->tc;
   delete p;
 }
 
@@ -84,21 +86,13 @@ int do_jvp(Plan* p, const float* v, float2* jv, cudaStream_t st) {
     e = launch_ycontract(*p, p->D, kChannels, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
-  {
-    Span sp(p, MRSTAT_K_XDFT, st);
-    e = launch_cgemm(p->A, p->ft, jv, p->ntr, p->nkx, p->nx, p->gate, st);
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "x-DFT launch");
-  return MRSTAT_OK;
+  return do_xdft(p, p->A, jv, p->gate, st);
 }
 
 int do_jhw(Plan* p, const float2* w, float* g, cudaStream_t st) {
+  const int status = do_xdft_adj(p, w, p->wt, p->gate, st);
+  if (status != MRSTAT_OK) return status;
   cudaError_t e;
-  {
-    Span sp(p, MRSTAT_K_XDFT_ADJ, st);
-    e = launch_cgemm(w, p->fh, p->wt, p->ntr, p->nx, p->nkx, p->gate, st);
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "x-DFT adjoint launch");
   {
     Span sp(p, MRSTAT_K_JHW_DOT, st);
     e = launch_jhw_dot(*p, g, st);
@@ -119,12 +113,45 @@ int do_signal(Plan* p, const float4* D, const float2* rho_masked, float2* s, cud
     e = launch_ycontract(*p, D, kChannels, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
-  {
+  return do_xdft(p, p->A, s, nullptr, st);
+}
+
+int do_xdft(Plan* p, const float2* A, float2* out, const int* gate, cudaStream_t st) {
+  cudaError_t e;
+  if (p->form == MRSTAT_FORM_SPLIT_BF16) {
+    {
+      Span sp(p, MRSTAT_K_VECTOR, st);
+      e = launch_split_bf16(reinterpret_cast<const float*>(A), p->ntr, 2 * p->nx, 2 * p->nx, p->bf_a_hi,
+                            p->bf_a_lo, p->kf_pad, gate, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "split launch");
     Span sp(p, MRSTAT_K_XDFT, st);
-    e = launch_cgemm(p->A, p->ft, s, p->ntr, p->nkx, p->nx, nullptr, st);
+    e = launch_tc_gemm(p->tc[0], p->tc[1], reinterpret_cast<float*>(out), p->ntr, 2 * p->nkx, 2 * p->nx,
+                       2 * p->nkx, 3, gate, p->dev_err, st);
+  } else {
+    Span sp(p, MRSTAT_K_XDFT, st);
+    e = launch_cgemm(A, p->ft, out, p->ntr, p->nkx, p->nx, gate, st);
   }
-  if (e != cudaSuccess) return cuda_fail(e, "x-DFT launch");
-  return MRSTAT_OK;
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "x-DFT launch");
+}
+
+int do_xdft_adj(Plan* p, const float2* w, float2* out, const int* gate, cudaStream_t st) {
+  cudaError_t e;
+  if (p->form == MRSTAT_FORM_SPLIT_BF16) {
+    {
+      Span sp(p, MRSTAT_K_VECTOR, st);
+      e = launch_split_bf16(reinterpret_cast<const float*>(w), p->ntr, 2 * p->nkx, 2 * p->nkx, p->bf_w_hi,
+                            p->bf_w_lo, p->ka_pad, gate, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "split launch");
+    Span sp(p, MRSTAT_K_XDFT_ADJ, st);
+    e = launch_tc_gemm(p->tc[2], p->tc[3], reinterpret_cast<float*>(out), p->ntr, 2 * p->nx, 2 * p->nkx,
+                       2 * p->nx, 3, gate, p->dev_err, st);
+  } else {
+    Span sp(p, MRSTAT_K_XDFT_ADJ, st);
+    e = launch_cgemm(w, p->fh, out, p->ntr, p->nx, p->nkx, gate, st);
+  }
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "x-DFT adjoint launch");
 }
 
 int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* mask, float4* D,
@@ -173,6 +200,20 @@ const char* mrstat_status_string(int status) {
 
 const char* mrstat_last_error(void) { return g_last_error.c_str(); }
 
+int mrstat_plan_check(mrstat_plan* plan) {
+  if (plan == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan");
+  DeviceGuard g(plan->device);
+  int flag = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "plan check");
+  if (flag) {
+    cudaMemset(plan->dev_err, 0, sizeof(int));
+    return fail(MRSTAT_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on its pipeline barriers");
+  }
+  return MRSTAT_OK;
+}
+
 int mrstat_profile_start(mrstat_plan* plan, uint32_t kernel_mask) {
   if (plan == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan");
   for (int64_t& c : plan->launches) c = 0;
@@ -210,9 +251,8 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   if (out == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (seq == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "seq is NULL");
-  if (form != MRSTAT_FORM_PLAIN_FP32)
-    return fail(form == MRSTAT_FORM_SPLIT_BF16 ? MRSTAT_ERR_UNSUPPORTED : MRSTAT_ERR_INVALID_ARG,
-                "form %d not available", form);
+  if (form != MRSTAT_FORM_PLAIN_FP32 && form != MRSTAT_FORM_SPLIT_BF16)
+    return fail(MRSTAT_ERR_INVALID_ARG, "form %d not available", form);
   if (seq->nx < 1 || seq->nx > 2048 || seq->ny < 1 || seq->ny > 2048 || seq->nkx < 1 ||
       seq->nkx > 4096 || seq->ntr < 1 || seq->ntr > 65536)
     return fail(MRSTAT_ERR_SHAPE, "sizes out of range: nx=%d ny=%d nkx=%d ntr=%d", seq->nx, seq->ny,
@@ -299,6 +339,51 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(dalloc(p, &p->cg_q, 4 * nv));
   chk(dalloc(p, &p->cg_jv, (size_t)p->ntr * p->nkx));
   chk(dalloc(p, &p->cg_frozen, 1));
+  chk(dalloc(p, &p->dev_err, 1));
+  std::vector<uint16_t> bfh_f, bfl_f, bfh_a, bfl_a;
+  if (form == MRSTAT_FORM_SPLIT_BF16) {
+    p->kf_pad = (2 * p->nx + 7) / 8 * 8;
+    p->ka_pad = (2 * p->nkx + 7) / 8 * 8;
+    const size_t nf = (size_t)2 * p->nkx * p->kf_pad, na = (size_t)2 * p->nx * p->ka_pad;
+    chk(cudaMalloc(&p->bf_ft_hi, nf * 2));
+    chk(cudaMalloc(&p->bf_ft_lo, nf * 2));
+    chk(cudaMalloc(&p->bf_fh_hi, na * 2));
+    chk(cudaMalloc(&p->bf_fh_lo, na * 2));
+    chk(cudaMalloc(&p->bf_a_hi, (size_t)p->ntr * p->kf_pad * 2));
+    chk(cudaMalloc(&p->bf_a_lo, (size_t)p->ntr * p->kf_pad * 2));
+    chk(cudaMalloc(&p->bf_w_hi, (size_t)p->ntr * p->ka_pad * 2));
+    chk(cudaMalloc(&p->bf_w_lo, (size_t)p->ntr * p->ka_pad * 2));
+    p->bytes += (int64_t)(2 * (nf + na) * 2 + 2 * (size_t)p->ntr * (p->kf_pad + p->ka_pad) * 2);
+    // real embeddings of the complex DFT matrices (K-major), split into bf16 hi + lo
+    bfh_f.assign(nf, 0);
+    bfl_f.assign(nf, 0);
+    bfh_a.assign(na, 0);
+    bfl_a.assign(na, 0);
+    auto put = [](std::vector<uint16_t>& hi, std::vector<uint16_t>& lo, size_t idx, double v) {
+      const float f = (float)v;
+      const uint16_t h = host_bf16(f);
+      hi[idx] = h;
+      lo[idx] = host_bf16((float)(v - (double)host_bf16_to_float(h)));
+    };
+    for (int k = 0; k < p->nkx; ++k)
+      for (int ix = 0; ix < p->nx; ++ix) {
+        const long long kx = k - p->nkx / 2;
+        long long r = (kx * ix) % p->nx;
+        if (r < 0) r += p->nx;
+        const double ang = -2.0 * M_PI * (double)r / (double)p->nx;
+        const double fr = std::cos(ang), fi = std::sin(ang);  // F = exp(-2 pi i kx ix / nx)
+        // forward: rows 2k (re), 2k+1 (im) of the output; columns 2ix (re A), 2ix+1 (im A)
+        put(bfh_f, bfl_f, (size_t)(2 * k) * p->kf_pad + 2 * ix, fr);
+        put(bfh_f, bfl_f, (size_t)(2 * k) * p->kf_pad + 2 * ix + 1, -fi);
+        put(bfh_f, bfl_f, (size_t)(2 * k + 1) * p->kf_pad + 2 * ix, fi);
+        put(bfh_f, bfl_f, (size_t)(2 * k + 1) * p->kf_pad + 2 * ix + 1, fr);
+        // adjoint with G = conj(F): rows 2ix, 2ix+1 of the output; columns 2k, 2k+1 of w
+        put(bfh_a, bfl_a, (size_t)(2 * ix) * p->ka_pad + 2 * k, fr);
+        put(bfh_a, bfl_a, (size_t)(2 * ix) * p->ka_pad + 2 * k + 1, fi);
+        put(bfh_a, bfl_a, (size_t)(2 * ix + 1) * p->ka_pad + 2 * k, -fi);
+        put(bfh_a, bfl_a, (size_t)(2 * ix + 1) * p->ka_pad + 2 * k + 1, fr);
+      }
+  }
   if (e != cudaSuccess) {
     int st = cuda_fail(e, "plan allocation");
     free_plan(p);
@@ -312,6 +397,22 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(cudaMemcpy(p->fh, fh.data(), fh.size() * sizeof(float2), cudaMemcpyHostToDevice));
   chk(cudaMemset(p->wt, 0, (size_t)p->ntr_pad * p->nx * sizeof(float2)));
   chk(cudaMemset(p->ticket, 0, sizeof(unsigned)));
+  chk(cudaMemset(p->dev_err, 0, sizeof(int)));
+  if (form == MRSTAT_FORM_SPLIT_BF16) {
+    chk(cudaMemcpy(p->bf_ft_hi, bfh_f.data(), bfh_f.size() * 2, cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(p->bf_ft_lo, bfl_f.data(), bfl_f.size() * 2, cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(p->bf_fh_hi, bfh_a.data(), bfh_a.size() * 2, cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(p->bf_fh_lo, bfl_a.data(), bfl_a.size() * 2, cudaMemcpyHostToDevice));
+    chk(cudaMemset(p->bf_a_hi, 0, (size_t)p->ntr * p->kf_pad * 2));
+    chk(cudaMemset(p->bf_a_lo, 0, (size_t)p->ntr * p->kf_pad * 2));
+    chk(cudaMemset(p->bf_w_hi, 0, (size_t)p->ntr * p->ka_pad * 2));
+    chk(cudaMemset(p->bf_w_lo, 0, (size_t)p->ntr * p->ka_pad * 2));
+    p->tc = new TcOperand[4];
+    chk(make_split_operand(&p->tc[0], p->bf_a_hi, p->bf_a_lo, p->ntr, 2 * p->nx, p->kf_pad, true));
+    chk(make_split_operand(&p->tc[1], p->bf_ft_hi, p->bf_ft_lo, 2 * p->nkx, 2 * p->nx, p->kf_pad, false));
+    chk(make_split_operand(&p->tc[2], p->bf_w_hi, p->bf_w_lo, p->ntr, 2 * p->nkx, p->ka_pad, true));
+    chk(make_split_operand(&p->tc[3], p->bf_fh_hi, p->bf_fh_lo, 2 * p->nx, 2 * p->nkx, p->ka_pad, false));
+  }
   chk(cudaDeviceSynchronize());
   if (e != cudaSuccess) {
     int st = cuda_fail(e, "plan tables");
@@ -378,13 +479,7 @@ int mrstat_forward(mrstat_plan* plan, const float* alpha, const float* b1, const
     e = launch_ycontract(*plan, plan->dfwd, 1, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
-  {
-    Span sp(plan, MRSTAT_K_XDFT, st);
-    e = launch_cgemm(plan->A, plan->ft, reinterpret_cast<float2*>(s), plan->ntr, plan->nkx, plan->nx,
-                     nullptr, st);
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "x-DFT launch");
-  return MRSTAT_OK;
+  return do_xdft(plan, plan->A, reinterpret_cast<float2*>(s), nullptr, st);
 }
 
 int mrstat_jvp(mrstat_plan* plan, const float* v, float* jv, void* stream) {

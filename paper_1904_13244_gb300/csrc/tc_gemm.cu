@@ -1,0 +1,381 @@
+// Tensor-core GEMM for sm_103a: C[M][N] (float32) = sum_p A_p[M][K] B_p[N][K]^T with
+// BF16 operands, float32 accumulation in tensor memory.
+//
+// Used for the split-BF16 form of the readout DFT: an FP32 operand x is carried as
+// x_hi + x_lo with x_hi = bf16(x) and x_lo = bf16(x - x_hi), and the product keeps
+// the three leading terms A_hi B_hi + A_hi B_lo + A_lo B_hi (about 16 significant
+// bits per operand; the dropped A_lo B_lo term is ~2^-18 relative).
+//
+// Structure (one 128 x BN output tile per CTA, 128 threads):
+//   warp 0 lane 0   TMA producer: 128B-swizzled K-major tiles of 64 K elements into
+//                   a STAGES-deep shared-memory ring (mbarrier expect-tx per stage);
+//   warp 1 lane 0   MMA issuer: tcgen05.mma.kind::f16 M=128 N=BN K=16, accumulating
+//                   in TMEM; tcgen05.commit frees each stage and finally signals done;
+//   warps 0..3      epilogue: tcgen05.ld 32 lanes x 16 columns per warp, float32 stores.
+// Every mbarrier wait is bounded; on timeout the CTA records an error code, skips the
+// rest of its work, releases its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cstring>
+
+#include "internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace mrstat {
+namespace {
+
+constexpr int BM = 128, BK = 64;
+constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase: false after kWaitNs of wall time (or kSpinLimit
+// polls), or as soon as another thread of the CTA has given up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 255u) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > kWaitNs) break;
+    }
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of 64 BF16
+// (128 B), 8-row swizzle atoms 1024 B apart (stride byte offset), SM100 version 1.
+__device__ __forceinline__ uint64_t sdesc_sw128(const void* tile) {
+  const uint64_t a = smem_u32(tile);
+  uint64_t d = (a >> 4) & 0x3FFFull;   // start address
+  d |= 1ull << 16;                      // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+  d |= 1ull << 46;                      // descriptor version
+  d |= 2ull << 61;                      // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t make_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN, int STAGES>
+struct TileShape {
+  static constexpr uint32_t kA = BM * BK * 2;            // bytes of one A tile
+  static constexpr uint32_t kB = BN * BK * 2;            // bytes of one B tile
+  static constexpr uint32_t kStage = 2 * kA + 2 * kB;    // hi and lo of both
+  static constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
+  static constexpr size_t kSmem = (size_t)STAGES * kStage + 1024 /* align */ + 256 /* barriers */;
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(128, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
+               const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
+               float* __restrict__ C, int M, int N, int K, int ldc, int nprod, const int* __restrict__ gate,
+               int* __restrict__ err) {
+  using TS = TileShape<BN, STAGES>;
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
+  if (gate != nullptr && *gate == 0) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * TS::kStage);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int nk = (K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, TS::kTmemCols);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;  // chunks whose loads the producer issued
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    for (int c = 0; c < nk; ++c) {
+      const int s = c % STAGES;
+      const uint32_t use = (uint32_t)(c / STAGES);
+      if (c >= STAGES && !mbar_wait(&empty[s], (use - 1) & 1u, abort_flag)) break;
+      uint8_t* a_hi = smem + s * TS::kStage;
+      uint8_t* a_lo = a_hi + TS::kA;
+      uint8_t* b_hi = a_lo + TS::kA;
+      uint8_t* b_lo = b_hi + TS::kB;
+      mbar_expect_tx(&full[s], nprod == 3 ? TS::kStage : TS::kA + TS::kB);
+      tma_load_2d(&ta_hi, &full[s], a_hi, c * BK, m0);
+      tma_load_2d(&tb_hi, &full[s], b_hi, c * BK, n0);
+      if (nprod == 3) {
+        tma_load_2d(&ta_lo, &full[s], a_lo, c * BK, m0);
+        tma_load_2d(&tb_lo, &full[s], b_lo, c * BK, n0);
+      }
+      issued = c + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t idesc = make_idesc(BM, BN);
+    for (int c = 0; c < nk; ++c) {
+      const int s = c % STAGES;
+      if (!mbar_wait(&full[s], (uint32_t)(c / STAGES) & 1u, abort_flag)) break;
+      fence_after();
+      const uint8_t* a_hi = smem + s * TS::kStage;
+      const uint8_t* a_lo = a_hi + TS::kA;
+      const uint8_t* b_hi = a_lo + TS::kA;
+      const uint8_t* b_lo = b_hi + TS::kB;
+      const uint64_t dah = sdesc_sw128(a_hi), dal = sdesc_sw128(a_lo);
+      const uint64_t dbh = sdesc_sw128(b_hi), dbl = sdesc_sw128(b_lo);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k) {
+        const uint64_t off = 2ull * k;  // 16 BF16 = 32 B along K, in 16-byte units
+        mma_bf16(tmem, dah + off, dbh + off, idesc, (c > 0 || k > 0) ? 1u : 0u);
+        if (nprod == 3) {
+          mma_bf16(tmem, dah + off, dbl + off, idesc, 1u);
+          mma_bf16(tmem, dal + off, dbh + off, idesc, 1u);
+        }
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+
+  // ---------------- epilogue ----------------
+  const bool ok = mbar_wait(done, 0, abort_flag) && *abort_flag == 0;
+  __syncwarp();
+  fence_after();
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    float* crow = C + (size_t)row * ldc;
+#pragma unroll
+    for (int cb = 0; cb < BN; cb += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + cb + j;
+          if (col < N) crow[col] = v[j];
+        }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicExch(err, 1);
+    // let the copies this thread issued land before the CTA's shared memory goes away
+    for (int c = issued > STAGES ? issued - STAGES : 0; c < issued; ++c) {
+      int spins = 0;
+      while (!mbar_try_wait(&full[c % STAGES], (uint32_t)(c / STAGES) & 1u) && ++spins < (1 << 16)) {
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TS::kTmemCols);
+}
+
+// x (float, rows x cols, row stride ld_src) -> hi, lo (bf16, rows x ldk, zero padded)
+__global__ void split_bf16_kernel(const float* __restrict__ x, int rows, int cols, int ld_src,
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int ldk,
+                                  const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  const int64_t total = (int64_t)rows * ldk;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / ldk;
+    const int c = (int)(e - r * ldk);
+    const float v = c < cols ? x[r * ld_src + c] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  }
+  return fn;
+}
+
+constexpr int kBN = 64, kStages = 4;
+
+}  // namespace
+
+// A K-major BF16 matrix [rows][ldk] (ldk a multiple of 8 elements = 16 bytes), K valid
+// columns; box = 64 K elements x box_rows rows, 128-byte swizzle, zero fill out of bounds.
+cudaError_t make_bf16_tmap(CUtensorMap* map, const void* base, int rows, int k, int ldk, int box_rows) {
+  EncodeFn fn = encode_fn();
+  if (fn == nullptr) return cudaErrorNotSupported;
+  if ((ldk % 8) != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return cudaErrorInvalidValue;
+  const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ldk * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t make_split_operand(TcOperand* op, const void* hi, const void* lo, int rows, int k, int ldk,
+                               bool is_a) {
+  op->rows = rows;
+  op->k = k;
+  op->ldk = ldk;
+  cudaError_t e = make_bf16_tmap(&op->hi, hi, rows, k, ldk, is_a ? BM : kBN);
+  if (e == cudaSuccess) e = make_bf16_tmap(&op->lo, lo, rows, k, ldk, is_a ? BM : kBN);
+  return e;
+}
+
+size_t tc_gemm_smem_bytes() { return TileShape<kBN, kStages>::kSmem; }
+
+cudaError_t launch_tc_gemm(const TcOperand& a, const TcOperand& b, float* C, int M, int N, int K, int ldc,
+                           int nprod, const int* gate, int* err, cudaStream_t st) {
+  if (M == 0 || N == 0) return cudaSuccess;
+  const size_t sm = TileShape<kBN, kStages>::kSmem;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kBN, kStages>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((M + BM - 1) / BM, (N + kBN - 1) / kBN);
+  tc_gemm_kernel<kBN, kStages><<<grid, 128, sm, st>>>(a.hi, a.lo, b.hi, b.lo, C, M, N, K, ldc, nprod, gate, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16(const float* x, int rows, int cols, int ld_src, void* hi, void* lo, int ldk,
+                              const int* gate, cudaStream_t st) {
+  const int64_t total = (int64_t)rows * ldk;
+  if (total == 0) return cudaSuccess;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 2048) blocks = 2048;
+  split_bf16_kernel<<<blocks, 256, 0, st>>>(x, rows, cols, ld_src, reinterpret_cast<__nv_bfloat16*>(hi),
+                                            reinterpret_cast<__nv_bfloat16*>(lo), ldk, gate);
+  return cudaGetLastError();
+}
+
+// host-side round-to-nearest-even float -> bf16 bits, and back
+uint16_t host_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+float host_bf16_to_float(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+}  // namespace mrstat

@@ -260,3 +260,44 @@ def test_full_size_jhw_sampled_voxels(brain):
         np.real(np.sum(np.conj(sim["m"]) * W, 0)),
         np.real(np.sum(np.conj(1j * sim["m"]) * W, 0))])
     assert metrics.relerr(out["g"], ref) < TOL
+
+
+# ---------------------------------------------------------------------------
+# split-BF16 form: readout DFT on tcgen05 tensor cores
+# ---------------------------------------------------------------------------
+# Each operand keeps ~16 significant bits (hi + lo), the dropped lo*lo term is
+# ~2^-18 relative per product; summed over the 2*nx (or 2*nkx) real terms of a
+# DFT row the normwise error stays near 1e-5.  Bar: 3e-5 normwise per output.
+SPLIT_TOL = 3e-5
+
+
+@pytest.mark.parametrize("name", ["quad16", "ragged_40x24", "odd_33x7", "ellipse64", "one_line"])
+def test_split_bf16_products_match_oracle(mr, name):
+    seq, ph = make_case(name)
+    alpha = alpha_of(ph)
+    lin = model.linearize(seq, alpha)
+    v = synth.random_params(seq.nv, 11)
+    w = synth.random_kspace(seq.ntr, seq.nkx, 12)
+    with mr.Plan(seq, form=mr.MRSTAT_FORM_SPLIT_BF16) as plan:
+        a = cuda(alpha)
+        plan.linearize(a)
+        s = plan.forward(a).cpu().numpy()
+        jv = plan.jvp(cuda(v)).cpu().numpy()
+        g = plan.jhw(cuda(w, torch.complex64)).cpu().numpy()
+        plan.check()
+    e = [metrics.relerr(s, model.signal(lin)), metrics.relerr(jv, model.jvp(lin, v)),
+         metrics.relerr(g, model.jhw(lin, w))]
+    assert max(e) < SPLIT_TOL, e
+
+
+def test_split_bf16_full_size_sampled(mr, brain):
+    seq, ph, alpha, v, w, rows, vox, out = brain
+    with mr.Plan(seq, form=mr.MRSTAT_FORM_SPLIT_BF16) as plan:
+        a = cuda(alpha)
+        plan.linearize(a)
+        jv = plan.jvp(cuda(v)).cpu().numpy()[rows]
+        g = plan.jhw(cuda(w, torch.complex64)).cpu().numpy()[:, vox]
+        plan.check()
+    # against the plain FP32 outputs of the same inputs (themselves pinned to the oracle)
+    assert metrics.relerr(jv, out["jv"]) < SPLIT_TOL
+    assert metrics.relerr(g, out["g"]) < SPLIT_TOL
