@@ -96,9 +96,10 @@ typedef struct mrstat_plan_info_t {
 
 /*
  * Create a plan: validates the sequence, builds the per-TR rotation and phase
- * tables and allocates every work buffer (the cached magnetisation time courses
- * D of 3 x ntr_padded x nv float32, the forward scratch, the x-DFT matrices and the
- * reduction scratch).  Synchronises the current device once.  On failure *out is
+ * tables and allocates the small work buffers (x-DFT matrices, reduction scratch,
+ * CG vectors).  The large buffers are allocated by the first call that needs them:
+ * the cached time courses D (3 x ntr_padded x nv float32) by mrstat_linearize, the
+ * m_y scratch (ntr_padded x nv float32) by mrstat_forward / mrstat_forward_ckpt.  Synchronises the current device once.  On failure *out is
  * set to NULL.  Errors: INVALID_ARG (null seq/out/arrays, bad form, non-finite or
  * negative flips, te/tr), SHAPE (sizes outside the ranges above, ky out of range),
  * OUT_OF_MEMORY, CUDA.
@@ -165,6 +166,24 @@ int mrstat_jhw(mrstat_plan* plan, const float* w, float* g, void* stream);
  * Errors: INVALID_ARG (bad channel), NOT_LINEARIZED, CUDA.
  */
 int mrstat_timecourses(mrstat_plan* plan, int32_t channel, float* out, void* stream);
+
+/*
+ * Checkpointed signal and gradient (differentiation by recomputation).
+ *
+ * mrstat_forward_ckpt computes s like mrstat_forward and keeps, instead of the time
+ * courses, the full Bloch state of every voxel (m_y, m_z and their ln T1 / ln T2
+ * tangents) before every `interval`-th TR: 6 * ceil(ntr / interval) floats per voxel.
+ * mrstat_jhw_ckpt then returns Re(J_s^H w) at that point by re-running each segment of
+ * the recursion from its checkpoint (Supporting Information S2), all segments in
+ * parallel, fused with the inner products of Algorithm 4; no time course is stored.
+ * mrstat_jhw_ckpt reads alpha, b1 and mask from the caller's buffers given to the last
+ * mrstat_forward_ckpt, which must still hold the same values.
+ *   interval: positive multiple of 4 (64 is the usual choice).
+ * Errors: INVALID_ARG, NOT_LINEARIZED (jhw_ckpt before forward_ckpt), OUT_OF_MEMORY, CUDA.
+ */
+int mrstat_forward_ckpt(mrstat_plan* plan, const float* alpha, const float* b1,
+                        const uint8_t* mask, int32_t interval, float* s, void* stream);
+int mrstat_jhw_ckpt(mrstat_plan* plan, const float* w, float* g, void* stream);
 
 /*
  * *out = sum_i a[i] * b[i] accumulated in float64 (the CG inner products of the

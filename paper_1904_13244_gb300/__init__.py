@@ -21,9 +21,9 @@ from ._binding import (MrstatError, MRSTAT_FORM_PLAIN_FP32, MRSTAT_FORM_SPLIT_BF
                        mrstat_forward, mrstat_jvp, mrstat_jhw, mrstat_timecourses, mrstat_dot,
                        mrstat_cg_fixed, mrstat_status_string, mrstat_last_error,
                        mrstat_profile_start, mrstat_profile_stop, mrstat_gn_default_opts,
-                       mrstat_gn_solve, mrstat_plan_check)
+                       mrstat_gn_solve, mrstat_plan_check, mrstat_forward_ckpt, mrstat_jhw_ckpt)
 
-__all__ = ["Plan", "MrstatError", "load"]
+__all__ = ["Plan", "MrstatError", "load", "Signal", "signal"]
 
 
 def load():
@@ -88,6 +88,16 @@ class Plan:
         mrstat_forward(self._h, alpha, b1, mask, out, stream)
         return out
 
+    def forward_ckpt(self, alpha, b1=None, mask=None, interval: int = 64, out=None, stream=None):
+        out = self._kspace(out)
+        mrstat_forward_ckpt(self._h, alpha, b1, mask, interval, out, stream)
+        return out
+
+    def jhw_ckpt(self, w, out=None, stream=None):
+        out = self._params(out)
+        mrstat_jhw_ckpt(self._h, w, out, stream)
+        return out
+
     def jvp(self, v, out=None, stream=None):
         out = self._kspace(out)
         mrstat_jvp(self._h, v, out, stream)
@@ -124,3 +134,6 @@ class Plan:
         out = self._params(out)
         mrstat_cg_fixed(self._h, rhs, out, iters, stream)
         return out
+
+
+from .autograd import Signal, signal  # noqa: E402

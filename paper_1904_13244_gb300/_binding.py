@@ -81,6 +81,9 @@ _SIGS = {
     "mrstat_jvp": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_jhw": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_timecourses": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_forward_ckpt": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                            ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_jhw_ckpt": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_dot": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                    ctypes.c_void_p],
     "mrstat_cg_fixed": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
@@ -216,6 +219,20 @@ def mrstat_jhw(plan, w, g, stream=None):
     nv, ntr, nkx = _dims(plan)
     _check(load().mrstat_jhw(plan, _ptr(w, torch.complex64, (ntr, nkx), "w"),
                              _ptr(g, torch.float32, (4, nv), "g"), _stream(stream)), "mrstat_jhw")
+
+
+def mrstat_forward_ckpt(plan, alpha, b1, mask, interval, s, stream=None):
+    nv, ntr, nkx = _dims(plan)
+    _check(load().mrstat_forward_ckpt(plan, _ptr(alpha, torch.float32, (4, nv), "alpha"),
+                                      _ptr(b1, torch.float32, (nv,), "b1"), _ptr(mask, torch.uint8, (nv,), "mask"),
+                                      int(interval), _ptr(s, torch.complex64, (ntr, nkx), "s"), _stream(stream)),
+           "mrstat_forward_ckpt")
+
+
+def mrstat_jhw_ckpt(plan, w, g, stream=None):
+    nv, ntr, nkx = _dims(plan)
+    _check(load().mrstat_jhw_ckpt(plan, _ptr(w, torch.complex64, (ntr, nkx), "w"),
+                                  _ptr(g, torch.float32, (4, nv), "g"), _stream(stream)), "mrstat_jhw_ckpt")
 
 
 def mrstat_timecourses(plan, channel, out, stream=None):

@@ -432,6 +432,7 @@ void swap_ptr(T*& a, T*& b) {
 
 cudaError_t ensure_workspace(Plan* p) {
   if (p->gn_ready) return cudaSuccess;
+  if (ensure_timecourses(p) != cudaSuccess) return cudaErrorMemoryAllocation;
   const size_t nv = p->nv, nk = (size_t)p->ntr * p->nkx;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) {

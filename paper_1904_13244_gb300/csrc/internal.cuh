@@ -75,6 +75,15 @@ struct Plan {
   TcOperand* tc = nullptr;          // [4]: A rows, forward B, k-space rows, adjoint B
   int* dev_err = nullptr;           // set by a kernel whose bounded wait ran out
 
+  // checkpointed form
+  float* ckpt = nullptr;        // [nseg][6][nv] Bloch states at segment starts
+  float* zpart = nullptr;       // [nseg][6][nv] per-segment partial inner products
+  int ckpt_interval = 0, ckpt_nseg = 0, ckpt_cap = 0;
+  const float* ckpt_alpha = nullptr;   // caller's alpha/b1/mask of the last checkpointed forward
+  const float* ckpt_b1 = nullptr;
+  const uint8_t* ckpt_mask = nullptr;
+  bool ckpt_ready = false;
+
   // kernels of the products return at once while *gate == 0 (nullptr: always run)
   const int* gate = nullptr;
 
@@ -155,10 +164,18 @@ cudaError_t do_dot(Plan* p, const float* a, const float* b, int64_t n, double* o
 int do_xdft(Plan* p, const float2* A, float2* out, const int* gate, cudaStream_t st);
 int do_xdft_adj(Plan* p, const float2* w, float2* out, const int* gate, cudaStream_t st);
 
+cudaError_t ensure_timecourses(Plan* p);   // allocates D on first use
+cudaError_t ensure_forward_scratch(Plan* p);
+
 // ---- launchers (each returns the launch's cudaError_t) ----
 // bloch.cu
 cudaError_t launch_bloch(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,
                          float4* D, int nch, cudaStream_t st);
+cudaError_t launch_bloch_ckpt(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,
+                              int interval, int nseg, float* ckpt, cudaStream_t st);
+cudaError_t launch_segment_jhw(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,
+                               int interval, int nseg, const float* ckpt, float* zpart, float* g,
+                               cudaStream_t st);
 // encode.cu
 cudaError_t launch_prep_forward(const Plan& p, const float* alpha, const uint8_t* mask, cudaStream_t st);
 cudaError_t launch_prep_rho(const Plan& p, const float2* rho, cudaStream_t st);

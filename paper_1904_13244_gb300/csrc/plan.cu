@@ -44,7 +44,7 @@ void free_plan(Plan* p) {
                   p->cg_jv, p->cg_s, p->cg_frozen, p->D2, p->rho2, p->gn_g, p->gn_z, p->gn_res,
                   p->gn_dir, p->gn_q, p->gn_alpha, p->gn_trial, p->gn_s, p->gn_r, p->gn_st,
                   p->gn_rt, p->gn_jv, p->gn_mask, p->gn_sc, p->gn_si, p->bf_ft_hi, p->bf_ft_lo,
-                  p->bf_fh_hi, p->bf_fh_lo, p->bf_a_hi, p->bf_a_lo, p->bf_w_hi, p->bf_w_lo, p->dev_err};
+                  p->bf_fh_hi, p->bf_fh_lo, p->bf_a_hi, p->bf_a_lo, p->bf_w_hi, p->bf_w_lo, p->dev_err, p->ckpt, p->zpart};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
@@ -64,6 +64,19 @@ inline void unit_root(long long a, long long n, float2* out, bool conj) {
 }
 
 }  // namespace
+
+cudaError_t ensure_timecourses(Plan* p) {
+  if (p->D != nullptr) return cudaSuccess;
+  const int64_t before = p->bytes;
+  cudaError_t e = dalloc(p, &p->D, (size_t)kChannels * p->nq * p->nv);
+  p->d_bytes = p->bytes - before;
+  return e;
+}
+
+cudaError_t ensure_forward_scratch(Plan* p) {
+  if (p->dfwd != nullptr) return cudaSuccess;
+  return dalloc(p, &p->dfwd, (size_t)p->nq * p->nv);
+}
 
 cudaEvent_t pool_event(Plan* p) {
   if (p->pool_used == p->event_pool.size()) {
@@ -109,8 +122,9 @@ int do_signal(Plan* p, const float4* D, const float2* rho_masked, float2* s, cud
   }
   if (e != cudaSuccess) return cuda_fail(e, "prep_rho launch");
   {
+    // the signal only needs channel 0 (m_y) and coefficient 0 (rho)
     Span sp(p, MRSTAT_K_YCONTRACT, st);
-    e = launch_ycontract(*p, D, kChannels, st);
+    e = launch_ycontract(*p, D, 1, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
   return do_xdft(p, p->A, s, nullptr, st);
@@ -323,12 +337,8 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(dalloc(p, &p->roots, p->ny));
   chk(dalloc(p, &p->ft, ft.size()));
   chk(dalloc(p, &p->fh, fh.size()));
-  const int64_t before = p->bytes;
-  chk(dalloc(p, &p->D, (size_t)kChannels * nq * nv));
-  p->d_bytes = p->bytes - before;
   chk(dalloc(p, &p->rho, nv));
   chk(dalloc(p, &p->maskf, nv));
-  chk(dalloc(p, &p->dfwd, nq * nv));
   chk(dalloc(p, &p->cf, (size_t)kChannels * nv));
   chk(dalloc(p, &p->A, (size_t)p->ntr * p->nx));
   chk(dalloc(p, &p->wt, (size_t)p->ntr_pad * p->nx));
@@ -451,6 +461,8 @@ int mrstat_linearize(mrstat_plan* plan, const float* alpha, const float* b1, con
   DeviceGuard g(plan->device);
   cudaStream_t st = as_stream(stream);
   plan->linearized = false;
+  cudaError_t ea = ensure_timecourses(plan);
+  if (ea != cudaSuccess) return cuda_fail(ea, "time-course allocation");
   const int status = do_linearize(plan, alpha, b1, mask, plan->D, plan->rho, st);
   if (status != MRSTAT_OK) return status;
   plan->linearized = true;
@@ -463,7 +475,8 @@ int mrstat_forward(mrstat_plan* plan, const float* alpha, const float* b1, const
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, alpha or s");
   DeviceGuard g(plan->device);
   cudaStream_t st = as_stream(stream);
-  cudaError_t e;
+  cudaError_t e = ensure_forward_scratch(plan);
+  if (e != cudaSuccess) return cuda_fail(e, "forward scratch allocation");
   {
     Span sp(plan, MRSTAT_K_BLOCH, st);
     e = launch_bloch(*plan, alpha, b1, mask, plan->dfwd, 1, st);
@@ -516,6 +529,76 @@ int mrstat_dot(mrstat_plan* plan, const float* a, const float* b, int64_t n, dou
   DeviceGuard g(plan->device);
   cudaError_t e = do_dot(plan, a, b, n, out, as_stream(stream));
   return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "dot launch");
+}
+
+int mrstat_forward_ckpt(mrstat_plan* plan, const float* alpha, const float* b1, const uint8_t* mask,
+                        int32_t interval, float* s, void* stream) {
+  if (plan == nullptr || alpha == nullptr || s == nullptr)
+    return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, alpha or s");
+  if (interval < 4 || interval % 4 != 0)
+    return fail(MRSTAT_ERR_INVALID_ARG, "checkpoint interval %d is not a positive multiple of 4", interval);
+  DeviceGuard g(plan->device);
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = ensure_forward_scratch(plan);
+  if (e != cudaSuccess) return cuda_fail(e, "forward scratch allocation");
+  const int nseg = (plan->ntr + interval - 1) / interval;
+  if (nseg > plan->ckpt_cap) {
+    cudaStreamSynchronize(st);
+    if (plan->ckpt) {
+      cudaFree(plan->ckpt);
+      cudaFree(plan->zpart);
+      plan->bytes -= 2 * (int64_t)plan->ckpt_cap * 6 * plan->nv * (int64_t)sizeof(float);
+      plan->ckpt = plan->zpart = nullptr;
+      plan->ckpt_cap = 0;
+    }
+    e = dalloc(plan, &plan->ckpt, (size_t)nseg * 6 * plan->nv);
+    if (e == cudaSuccess) e = dalloc(plan, &plan->zpart, (size_t)nseg * 6 * plan->nv);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint allocation");
+    plan->ckpt_cap = nseg;
+  }
+  plan->ckpt_ready = false;
+  {
+    Span sp(plan, MRSTAT_K_BLOCH, st);
+    e = launch_bloch_ckpt(*plan, alpha, b1, mask, interval, nseg, plan->ckpt, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "checkpointed Bloch launch");
+  {
+    Span sp(plan, MRSTAT_K_VECTOR, st);
+    e = launch_prep_forward(*plan, alpha, mask, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "prep_forward launch");
+  {
+    Span sp(plan, MRSTAT_K_YCONTRACT, st);
+    e = launch_ycontract(*plan, plan->dfwd, 1, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
+  const int status = do_xdft(plan, plan->A, reinterpret_cast<float2*>(s), nullptr, st);
+  if (status != MRSTAT_OK) return status;
+  plan->ckpt_interval = interval;
+  plan->ckpt_nseg = nseg;
+  plan->ckpt_alpha = alpha;
+  plan->ckpt_b1 = b1;
+  plan->ckpt_mask = mask;
+  plan->ckpt_ready = true;
+  return MRSTAT_OK;
+}
+
+int mrstat_jhw_ckpt(mrstat_plan* plan, const float* w, float* gout, void* stream) {
+  if (plan == nullptr || w == nullptr || gout == nullptr)
+    return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, w or g");
+  if (!plan->ckpt_ready)
+    return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_jhw_ckpt before mrstat_forward_ckpt");
+  DeviceGuard g(plan->device);
+  cudaStream_t st = as_stream(stream);
+  int status = do_xdft_adj(plan, reinterpret_cast<const float2*>(w), plan->wt, nullptr, st);
+  if (status != MRSTAT_OK) return status;
+  cudaError_t e;
+  {
+    Span sp(plan, MRSTAT_K_JHW_DOT, st, 2);
+    e = launch_segment_jhw(*plan, plan->ckpt_alpha, plan->ckpt_b1, plan->ckpt_mask, plan->ckpt_interval,
+                           plan->ckpt_nseg, plan->ckpt, plan->zpart, gout, st);
+  }
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "segment recompute launch");
 }
 
 int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters, void* stream) {
