@@ -186,8 +186,56 @@ int mrstat_forward_ckpt(mrstat_plan* plan, const float* alpha, const float* b1,
 int mrstat_jhw_ckpt(mrstat_plan* plan, const float* w, float* g, void* stream);
 
 /*
- * *out = sum_i a[i] * b[i] accumulated in float64 (the CG inner products of the
- * inner Gauss-Newton loop, Algorithm 6).  a, b: device float [n]; out: device double.
+ * out = Re(J_s^H J_s) v, the Gauss-Newton matrix-vector product of the inner CG
+ * (Eq. 4: first y = J v, then Re(J^H y)), with the plan's current linearisation:
+ * mrstat_jvp then mrstat_jhw after mrstat_linearize, or the per-ky Gram product of the
+ * low-rank form after mrstat_lowrank_linearize.
+ *   v, out: device float [4][nv].
+ * Errors: INVALID_ARG, NOT_LINEARIZED, CUDA.
+ */
+int mrstat_jhjv(mrstat_plan* plan, const float* v, float* out, void* stream);
+
+/*
+ * Low-rank (compressed) form.  Every echo time course is represented in a real time
+ * basis U [ntr][R]: m_j[n] ~ i sum_r U[n][r] c_r,j, and likewise dm_j/dln T1 and
+ * dm_j/dln T2 with coefficients dc1, dc2.  This is the SVD compression the paper's
+ * comparison pipeline applies to its dictionary (Methods, "Numerical Brain
+ * Simulation"), applied to the signal model itself; the encoding sum of Eqs. 1-2 then
+ * becomes R two-dimensional DFTs, and Re(J^H J) v uses the per-ky Gram matrices
+ * M_ky = sum_{n: ky(n) = ky} U[n]^T U[n] so that it never touches the TR axis.  All
+ * DFTs run as split-BF16 tcgen05 products with float32 accumulation.
+ *
+ * mrstat_lowrank_basis: U = leading R left singular vectors of the training time courses
+ *   [m_y | dm_y/dlnT1 | dm_y/dlnT2] of ns voxels (Bloch recursion on the device, then
+ *   subspace iteration Q <- orth(Y (Y^T Q)) with float32 products on the device and
+ *   float64 orthonormalisation and Rayleigh-Ritz on the host).
+ *   train: device float [2][ns] (ln T1, ln T2 in ms); train_b1: device float [ns] or
+ *   NULL; U_out: device float [ntr][R]; sv_out: host double [R] singular values or NULL.
+ *   1 <= R <= 32.  Allocates and frees its own work space; synchronises.
+ * mrstat_lowrank_set_basis: adopts U (device float [ntr][R], R in {8, 16, 24, 32},
+ *   orthonormal columns) and allocates the form's work space; synchronises.
+ * mrstat_lowrank_linearize: makes the low-rank model at alpha the plan's linearisation
+ *   for mrstat_jvp, mrstat_jhw, mrstat_jhjv and mrstat_cg_fixed.  coef = NULL projects
+ *   the exact Bloch recursion onto U on the fly (no time course is stored); otherwise
+ *   coef is device float [3][R][nv] (c, dc1, dc2), e.g. from a learned surrogate.  A
+ *   later mrstat_linearize switches the plan back to the exact model.
+ * mrstat_lowrank_coefficients: copies the current coefficients to device [3][R][nv].
+ * mrstat_lowrank_rank: R of the adopted basis (0 if none).
+ * Errors: INVALID_ARG, NOT_LINEARIZED (no basis / no low-rank linearisation),
+ * OUT_OF_MEMORY, TIMEOUT (a tensor-core kernel's bounded wait ran out), CUDA.
+ */
+int mrstat_lowrank_basis(mrstat_plan* plan, const float* train, const float* train_b1, int32_t ns,
+                         int32_t rank, float* U_out, double* sv_out, void* stream);
+int mrstat_lowrank_set_basis(mrstat_plan* plan, const float* U, int32_t rank, void* stream);
+int mrstat_lowrank_linearize(mrstat_plan* plan, const float* alpha, const float* b1,
+                             const uint8_t* mask, const float* coef, void* stream);
+int mrstat_lowrank_coefficients(mrstat_plan* plan, float* coef, void* stream);
+int mrstat_lowrank_rank(const mrstat_plan* plan);
+
+/*
+ * *out = sum_i a[i] * b[i] (the CG inner products of the inner Gauss-Newton loop,
+ * Algorithm 6): each thread adds its few products (a grid-stride handful) in float32,
+ * all partial sums are added in float64; the relative error is ~1e-7 of sum |a b|.  a, b: device float [n]; out: device double.
  * Uses the plan's reduction scratch.  n may be 0 (result 0).
  * Errors: INVALID_ARG (null pointer, n < 0), CUDA.
  */
@@ -223,6 +271,12 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
  * T1 = t1_init_ms, T2 = t2_init_ms (Methods), and with mask_threshold > 0 the mask
  * |rho| > mask_threshold * max |rho| is drawn and written to `mask`.
  *
+ * With opts->hessian = 1 the CG uses the low-rank Gauss-Newton matrix of the plan's
+ * time basis (the compressed model's Re(J^H J), recomputed at every accepted point by
+ * projecting the exact recursion onto the basis), while gradient, objective and the
+ * trust-region ratio stay exact, so the iteration converges to the exact model's
+ * solution.
+ *
  * Every CG scalar lives on the device in float64; the host synchronises once per
  * outer iteration to evaluate the trust-region ratio.  On return the plan holds the
  * linearisation at the returned alpha.
@@ -257,6 +311,9 @@ typedef struct mrstat_gn_opts {
   int32_t rho_init_iters;      /* CGLS iterations of the rho initialisation (0: none)  */
   double t1_init_ms, t2_init_ms;
   double mask_threshold;       /* > 0: draw the mask after the rho initialisation       */
+  int32_t hessian;             /* 0: exact Re(J^H J); 1: low-rank per-ky Gram product of
+                                  the plan's time basis (mrstat_lowrank_set_basis) for the
+                                  CG, with the exact gradient and objective              */
 } mrstat_gn_opts;
 
 typedef struct mrstat_gn_report {

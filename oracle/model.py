@@ -118,3 +118,28 @@ def gradient(lin: Linearization, d) -> np.ndarray:
 def gauss_newton_product(lin: Linearization, v) -> np.ndarray:
     """Re(J^H J) v = Re(J_s^H (J_s v)) (Eq. 4: first y = J v, then Re(J^H y))."""
     return jhw(lin, jvp(lin, v))
+
+
+def project_onto_basis(lin: Linearization, U) -> Linearization:
+    """Low-rank model: every time course replaced by its orthogonal projection onto the
+    columns of the real time basis U [ntr, R] (m_j ~ U U^T m_j, and the same for each
+    tangent).  The basis comes from an SVD of simulated time courses, the compression the
+    paper's comparison pipeline applies to its dictionary (Methods, "Numerical Brain
+    Simulation": rank-5 SVD compression); here it compresses the model itself."""
+    U = np.asarray(U, np.float64)
+
+    def proj(x):
+        return U @ (U.T @ x)
+
+    return Linearization(lin.seq, lin.alpha, lin.b1, lin.mask, proj(lin.m), proj(lin.dm1), proj(lin.dm2),
+                         None if lin.dmb is None else proj(lin.dmb))
+
+
+def time_basis(seq, t1_ms, t2_ms, rank, b1=None):
+    """Leading left singular vectors of the simulated training time courses [m_y, dm_y/dlnT1,
+    dm_y/dlnT2] (columns over the training samples); returns (U [ntr, rank], singular values)."""
+    from . import bloch
+    sim = bloch.simulate(seq, np.asarray(t1_ms), np.asarray(t2_ms), b1)
+    Y = np.concatenate([sim["m"].imag, sim["dm_dlnT1"].imag, sim["dm_dlnT2"].imag], axis=1)
+    u, s, _ = np.linalg.svd(Y, full_matrices=False)
+    return u[:, :rank], s[:rank]

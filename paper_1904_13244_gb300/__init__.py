@@ -21,7 +21,9 @@ from ._binding import (MrstatError, MRSTAT_FORM_PLAIN_FP32, MRSTAT_FORM_SPLIT_BF
                        mrstat_forward, mrstat_jvp, mrstat_jhw, mrstat_timecourses, mrstat_dot,
                        mrstat_cg_fixed, mrstat_status_string, mrstat_last_error,
                        mrstat_profile_start, mrstat_profile_stop, mrstat_gn_default_opts,
-                       mrstat_gn_solve, mrstat_plan_check, mrstat_forward_ckpt, mrstat_jhw_ckpt)
+                       mrstat_gn_solve, mrstat_plan_check, mrstat_forward_ckpt, mrstat_jhw_ckpt,
+                       mrstat_jhjv, mrstat_lowrank_basis, mrstat_lowrank_set_basis, mrstat_lowrank_linearize,
+                       mrstat_lowrank_coefficients, mrstat_lowrank_rank)
 
 __all__ = ["Plan", "MrstatError", "load", "Signal", "signal"]
 
@@ -96,6 +98,31 @@ class Plan:
     def jhw_ckpt(self, w, out=None, stream=None):
         out = self._params(out)
         mrstat_jhw_ckpt(self._h, w, out, stream)
+        return out
+
+    def jhjv(self, v, out=None, stream=None):
+        out = self._params(out)
+        mrstat_jhjv(self._h, v, out, stream)
+        return out
+
+    # -- low-rank form --
+    def lowrank_basis(self, train, rank: int, train_b1=None, stream=None):
+        """Time basis U [ntr, rank] from training parameters train [2, ns] (ln T1, ln T2)."""
+        U = torch.empty((self.ntr, rank), dtype=torch.float32, device="cuda")
+        sv = mrstat_lowrank_basis(self._h, train, train_b1, rank, U, stream)
+        return U, sv
+
+    def lowrank_set_basis(self, U, stream=None):
+        mrstat_lowrank_set_basis(self._h, U, stream)
+
+    def lowrank_linearize(self, alpha, b1=None, mask=None, coef=None, stream=None):
+        mrstat_lowrank_linearize(self._h, alpha, b1, mask, coef, stream)
+
+    def lowrank_coefficients(self, out=None, stream=None):
+        R = mrstat_lowrank_rank(self._h)
+        if out is None:
+            out = torch.empty((3, R, self.nv), dtype=torch.float32, device="cuda")
+        mrstat_lowrank_coefficients(self._h, out, stream)
         return out
 
     def jvp(self, v, out=None, stream=None):

@@ -54,7 +54,8 @@ class mrstat_gn_opts(ctypes.Structure):
                 ("cg_rel_tol", ctypes.c_double), ("t1_min_ms", ctypes.c_double), ("t1_max_ms", ctypes.c_double),
                 ("t2_min_ms", ctypes.c_double), ("t2_max_ms", ctypes.c_double),
                 ("rho_init_iters", ctypes.c_int32), ("t1_init_ms", ctypes.c_double),
-                ("t2_init_ms", ctypes.c_double), ("mask_threshold", ctypes.c_double)]
+                ("t2_init_ms", ctypes.c_double), ("mask_threshold", ctypes.c_double),
+                ("hessian", ctypes.c_int32)]
 
 
 class mrstat_gn_report(ctypes.Structure):
@@ -84,6 +85,14 @@ _SIGS = {
     "mrstat_forward_ckpt": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                             ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_jhw_ckpt": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_jhjv": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_lowrank_basis": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p],
+    "mrstat_lowrank_set_basis": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
+    "mrstat_lowrank_linearize": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_lowrank_coefficients": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_lowrank_rank": [ctypes.c_void_p],
     "mrstat_dot": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                    ctypes.c_void_p],
     "mrstat_cg_fixed": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
@@ -233,6 +242,50 @@ def mrstat_jhw_ckpt(plan, w, g, stream=None):
     nv, ntr, nkx = _dims(plan)
     _check(load().mrstat_jhw_ckpt(plan, _ptr(w, torch.complex64, (ntr, nkx), "w"),
                                   _ptr(g, torch.float32, (4, nv), "g"), _stream(stream)), "mrstat_jhw_ckpt")
+
+
+def mrstat_jhjv(plan, v, out, stream=None):
+    nv, _, _ = _dims(plan)
+    _check(load().mrstat_jhjv(plan, _ptr(v, torch.float32, (4, nv), "v"), _ptr(out, torch.float32, (4, nv), "out"),
+                              _stream(stream)), "mrstat_jhjv")
+
+
+def mrstat_lowrank_basis(plan, train, train_b1, rank, U_out, stream=None):
+    ns = int(train.shape[1])
+    nv, ntr, _ = _dims(plan)
+    sv = (ctypes.c_double * rank)()
+    _check(load().mrstat_lowrank_basis(plan, _ptr(train, torch.float32, (2, ns), "train"),
+                                       _ptr(train_b1, torch.float32, (ns,), "train_b1"), ns, int(rank),
+                                       _ptr(U_out, torch.float32, (ntr, rank), "U"), sv, _stream(stream)),
+           "mrstat_lowrank_basis")
+    return list(sv)
+
+
+def mrstat_lowrank_set_basis(plan, U, stream=None):
+    nv, ntr, _ = _dims(plan)
+    rank = int(U.shape[1])
+    _check(load().mrstat_lowrank_set_basis(plan, _ptr(U, torch.float32, (ntr, rank), "U"), rank, _stream(stream)),
+           "mrstat_lowrank_set_basis")
+
+
+def mrstat_lowrank_linearize(plan, alpha, b1=None, mask=None, coef=None, stream=None):
+    nv, _, _ = _dims(plan)
+    R = load().mrstat_lowrank_rank(plan)
+    _check(load().mrstat_lowrank_linearize(plan, _ptr(alpha, torch.float32, (4, nv), "alpha"),
+                                           _ptr(b1, torch.float32, (nv,), "b1"), _ptr(mask, torch.uint8, (nv,), "mask"),
+                                           _ptr(coef, torch.float32, (3, R, nv), "coef"), _stream(stream)),
+           "mrstat_lowrank_linearize")
+
+
+def mrstat_lowrank_coefficients(plan, out, stream=None):
+    nv, _, _ = _dims(plan)
+    R = load().mrstat_lowrank_rank(plan)
+    _check(load().mrstat_lowrank_coefficients(plan, _ptr(out, torch.float32, (3, R, nv), "coef"), _stream(stream)),
+           "mrstat_lowrank_coefficients")
+
+
+def mrstat_lowrank_rank(plan) -> int:
+    return int(load().mrstat_lowrank_rank(plan))
 
 
 def mrstat_timecourses(plan, channel, out, stream=None):

@@ -140,6 +140,17 @@ cudaError_t launch_bloch(const Plan& p, const float* alpha, const float* b1, con
                   : launch_t<kChannels>(p, alpha, b1, mask, D, st);
 }
 
+cudaError_t launch_bloch_n(const Plan& p, const float* alpha, const float* b1, float4* D, int nv_override,
+                           cudaStream_t st) {
+  if (nv_override <= 0) return cudaSuccess;
+  Plan q = p;  // same sequence tables, different voxel count
+  q.nv = nv_override;
+  cudaError_t e = launch_t<kChannels>(q, alpha, b1, nullptr, D, st);
+  q.marks.clear();
+  q.event_pool.clear();
+  return e;
+}
+
 }  // namespace mrstat
 
 // ---------------------------------------------------------------------------

@@ -496,8 +496,7 @@ struct Solver {
     p->gate = si + I_ACTIVE;
     int status = MRSTAT_OK;
     for (int it = 0; it < inner && status == MRSTAT_OK; ++it) {
-      status = do_jvp(p, p->gn_dir, p->gn_jv, st);
-      if (status == MRSTAT_OK) status = do_jhw(p, p->gn_jv, p->gn_q, st);
+      status = do_jhjv(p, p->gn_dir, p->gn_q, st);
       if (status != MRSTAT_OK) break;
       e = vec([&] {
         multidot_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_dir, p->gn_q, p->gn_res, p->gn_z, n4, si, p->red,
@@ -608,6 +607,9 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
     return fail(MRSTAT_ERR_INVALID_ARG, "invalid rho initialisation point");
   if (o->rho_init_iters > 0 && o->mask_threshold > 0 && mask == nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "drawing a mask needs a mask buffer");
+  if (o->hessian != 0 && o->hessian != 1) return fail(MRSTAT_ERR_INVALID_ARG, "hessian must be 0 or 1");
+  if (o->hessian == 1 && p->lr == nullptr)
+    return fail(MRSTAT_ERR_NOT_LINEARIZED, "the low-rank Hessian needs mrstat_lowrank_set_basis first");
   DeviceGuard guard(p->device);
   const auto t_start = std::chrono::steady_clock::now();
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -615,6 +617,8 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   if (e != cudaSuccess) return cuda_fail(e, "Gauss-Newton work space");
 
   Solver S{p, st, 4 * (int64_t)p->nv, 2 * (int64_t)p->ntr * p->nkx, p->gn_sc, p->gn_si};
+  if (p->lr) p->lr->active = false;
+  bool coef_stale = true;  // low-rank coefficients of the current point
   const int nv = p->nv;
   const int g = grid_for(nv);
   mrstat_gn_report local;
@@ -693,7 +697,18 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   for (int k = 0; k < o->outer_iters; ++k) {
     // gradient g = Re(J_s^H (s - d)) at the current point
     status = do_jhw(p, p->gn_r, p->gn_g, st);
-    if (status == MRSTAT_OK) status = S.steihaug(delta, o->inner_iters, o->cg_rel_tol);
+    if (status != MRSTAT_OK) return status;
+    if (o->hessian == 1) {
+      if (coef_stale) {
+        Span sp(p, MRSTAT_K_BLOCH, st);
+        e = lowrank_project(*p, *p->lr, p->gn_alpha, b1, p->gn_mask, p->lr->coef, st);
+        if (e != cudaSuccess) return cuda_fail(e, "low-rank projection");
+        coef_stale = false;
+      }
+      p->lr->active = true;  // Steihaug's products use the per-ky Gram form
+    }
+    status = S.steihaug(delta, o->inner_iters, o->cg_rel_tol);
+    if (p->lr) p->lr->active = false;
     if (status != MRSTAT_OK) return status;
     e = S.vec([&] {
       trial_kernel<<<g, kT, 0, st>>>(p->gn_alpha, p->gn_z, p->gn_mask, nv, lt1a, lt1b, lt2a, lt2b, p->gn_trial);
@@ -726,6 +741,7 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
       swap_ptr(p->gn_s, p->gn_st);
       swap_ptr(p->gn_r, p->gn_rt);
       f = ft;
+      coef_stale = true;
     }
   }
   local.f_final = f;

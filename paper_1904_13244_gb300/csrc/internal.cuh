@@ -8,6 +8,7 @@
 
 #include "../../include/mrstat.h"
 #include "tc_gemm.cuh"
+#include "lowrank.cuh"
 
 namespace mrstat {
 
@@ -73,6 +74,7 @@ struct Plan {
   void *bf_a_hi = nullptr, *bf_a_lo = nullptr;    // [ntr][kf_pad] split rows A
   void *bf_w_hi = nullptr, *bf_w_lo = nullptr;    // [ntr][ka_pad] split k-space rows
   TcOperand* tc = nullptr;          // [4]: A rows, forward B, k-space rows, adjoint B
+  LowRank* lr = nullptr;            // low-rank form (after mrstat_lowrank_set_basis)
   int* dev_err = nullptr;           // set by a kernel whose bounded wait ran out
 
   // checkpointed form
@@ -160,17 +162,33 @@ int do_signal(Plan* p, const float4* D, const float2* rho_masked, float2* s, cud
 int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* mask, float4* D,
                  float2* rho, cudaStream_t st);
 cudaError_t do_dot(Plan* p, const float* a, const float* b, int64_t n, double* out, cudaStream_t st);
+// Re(J^H J) v with the plan's active linearisation (exact: J.v then J^H; low-rank: per-ky Gram)
+int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st);
 // readout DFT of rows A [ntr][nx] (complex) into out [ntr][nkx], and its adjoint
 int do_xdft(Plan* p, const float2* A, float2* out, const int* gate, cudaStream_t st);
 int do_xdft_adj(Plan* p, const float2* w, float2* out, const int* gate, cudaStream_t st);
 
 cudaError_t ensure_timecourses(Plan* p);   // allocates D on first use
+int build_split_tables(Plan* p);           // split-BF16 readout DFT operands (plan.cu)
+// low-rank form (lowrank.cu)
+int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st);
+void lowrank_free(LowRank* L);
+cudaError_t lowrank_project(const Plan& p, const LowRank& L, const float* alpha, const float* b1,
+                            const uint8_t* mask, float* coef, cudaStream_t st);
+int lowrank_jvp(Plan* p, const float* v, float2* jv, cudaStream_t st);
+int lowrank_jhw(Plan* p, const float2* w, float* g, cudaStream_t st);
+int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st);
+cudaError_t lowrank_train_matrix(const float4* D, int ns, int nq, int ntr, float2* Y, float2* Yt,
+                                 cudaStream_t st);
 cudaError_t ensure_forward_scratch(Plan* p);
 
 // ---- launchers (each returns the launch's cudaError_t) ----
 // bloch.cu
 cudaError_t launch_bloch(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,
                          float4* D, int nch, cudaStream_t st);
+// the same recursion for nv_override voxels laid out [2][nv_override] (ln T1, ln T2)
+cudaError_t launch_bloch_n(const Plan& p, const float* alpha, const float* b1, float4* D, int nv_override,
+                           cudaStream_t st);
 cudaError_t launch_bloch_ckpt(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,
                               int interval, int nseg, float* ckpt, cudaStream_t st);
 cudaError_t launch_segment_jhw(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,

@@ -1,0 +1,583 @@
+// Low-rank (compressed) form of the signal model and its Jacobian products.
+//
+// Every echo time course is represented in a real time basis U [ntr][R]:
+//     m_j[n] ~ i sum_r U[n][r] c_r,j   (and the same for dm/dlnT1, dm/dlnT2),
+// the SVD compression the paper's comparison pipeline applies to its dictionary
+// (Methods, "Numerical Brain Simulation"), applied here to the model itself.  Because
+// U does not depend on the voxel, the encoding sum of Eqs. 1-2 turns into R images
+// and R two-dimensional DFTs:
+//     J.v:  s[n][kx] = sum_r U[n][r] H_r[ky(n)][kx],   H_r = DFT2(h_r),
+//           h_r,j = i (rho_j (v0 dc1_r,j + v1 dc2_r,j) + (v2 + i v3) c_r,j) * mask_j,
+//     J^H w: g_k,j = Re sum_r conj(dh_r,j / dv_k) P_r,j,   P_r = DFT2^H(G_r),
+//           G_r[ky][kx] = sum_{n : ky(n) = ky} U[n][r] w[n][kx],
+// and for J^H J v the per-ky Gram matrices M_ky = sum_{n : ky(n) = ky} U[n]^T U[n]
+// give G_r = sum_r' M_ky[r][r'] H_r' without ever expanding to the TR axis.
+// Each DFT2 is two GEMMs (readout x, then phase encode y) on the tcgen05 tensor cores in
+// split-BF16 with float32 accumulation (tc_gemm.cu); between them a transpose kernel
+// writes the next GEMM's K-major BF16 hi/lo operand directly.
+//
+// The coefficients c, dc1, dc2 come either from the exact Bloch recursion projected onto
+// U on the fly (lr_project_kernel: no time course is ever stored) or from a caller (the
+// learned surrogate).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "lowrank.cuh"
+
+namespace mrstat {
+namespace {
+
+__device__ __forceinline__ void put_split(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t idx, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[idx] = h;
+  lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__device__ __forceinline__ int mod_small_l(int a, int n, float inv_n) {
+  int q = __float2int_rz(__int2float_rn(a) * inv_n);
+  int r = a - q * n;
+  r += (r < 0) ? n : 0;
+  r -= (r >= n) ? n : 0;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// exact linearisation projected onto U: Bloch recursion with tangents (as bloch.cu),
+// accumulating c_r += U[n][r] m_y, dc1_r += U[n][r] dm_y/dlnT1, dc2_r += U[n][r] dm_y/dlnT2
+// ---------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(128)
+lr_project_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
+                  const uint8_t* __restrict__ mask, const float2* __restrict__ cs, const float* __restrict__ phi,
+                  const float* __restrict__ U, int nv, int ntr, float te, float tb, float m0z,
+                  float* __restrict__ coef) {
+  constexpr int CH = 64;  // TRs of U staged per chunk
+  __shared__ __align__(16) float us[CH * R];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = j < nv;
+  const bool on = valid && (mask == nullptr || mask[j] != 0);
+  float t1 = 1000.f, t2 = 100.f, bj = 1.f;
+  if (valid) {
+    t1 = expf(alpha[j]);
+    t2 = expf(alpha[nv + j]);
+    if (b1 != nullptr) bj = b1[j];
+  }
+  const float ra1 = te / t1, ra2 = te / t2, rb1 = tb / t1, rb2 = tb / t2;
+  const float x1a = expm1f(-ra1), x2a = expm1f(-ra2), x1b = expm1f(-rb1), x2b = expm1f(-rb2);
+  const float d1a = ra1 * (1.f + x1a), d2a = ra2 * (1.f + x2a), d1b = rb1 * (1.f + x1b), d2b = rb2 * (1.f + x2b);
+  float my = 0.f, mz = m0z, ay = 0.f, az = 0.f, by = 0.f, bz = 0.f;
+  float c0[R], c1[R], c2[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) c0[r] = c1[r] = c2[r] = 0.f;
+
+  for (int n0 = 0; n0 < ntr; n0 += CH) {
+    const int cnt = min(CH, ntr - n0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * R; e += blockDim.x) us[e] = U[(size_t)n0 * R + e];
+    __syncthreads();
+    for (int t = 0; t < cnt; ++t) {
+      const int n = n0 + t;
+      float c, s;
+      if (b1 != nullptr) {
+        sincosf(__ldg(phi + n) * bj, &s, &c);
+      } else {
+        const float2 v = __ldg(cs + n);
+        c = v.x;
+        s = v.y;
+      }
+      float ty = c * my + s * mz;
+      mz = c * mz - s * my;
+      my = ty;
+      ty = c * ay + s * az;
+      az = c * az - s * ay;
+      ay = ty;
+      ty = c * by + s * bz;
+      bz = c * bz - s * by;
+      by = ty;
+      float zm1 = mz - 1.f;
+      ay = fmaf(x2a, ay, ay);
+      az = fmaf(x1a, az, fmaf(d1a, zm1, az));
+      by = fmaf(x2a, by, fmaf(d2a, my, by));
+      bz = fmaf(x1a, bz, bz);
+      my = fmaf(x2a, my, my);
+      mz = fmaf(x1a, zm1, mz);
+      const float4* u4 = reinterpret_cast<const float4*>(us + t * R);
+#pragma unroll
+      for (int r4 = 0; r4 < R / 4; ++r4) {
+        const float4 u = u4[r4];
+        c0[4 * r4 + 0] = fmaf(u.x, my, c0[4 * r4 + 0]);
+        c0[4 * r4 + 1] = fmaf(u.y, my, c0[4 * r4 + 1]);
+        c0[4 * r4 + 2] = fmaf(u.z, my, c0[4 * r4 + 2]);
+        c0[4 * r4 + 3] = fmaf(u.w, my, c0[4 * r4 + 3]);
+        c1[4 * r4 + 0] = fmaf(u.x, ay, c1[4 * r4 + 0]);
+        c1[4 * r4 + 1] = fmaf(u.y, ay, c1[4 * r4 + 1]);
+        c1[4 * r4 + 2] = fmaf(u.z, ay, c1[4 * r4 + 2]);
+        c1[4 * r4 + 3] = fmaf(u.w, ay, c1[4 * r4 + 3]);
+        c2[4 * r4 + 0] = fmaf(u.x, by, c2[4 * r4 + 0]);
+        c2[4 * r4 + 1] = fmaf(u.y, by, c2[4 * r4 + 1]);
+        c2[4 * r4 + 2] = fmaf(u.z, by, c2[4 * r4 + 2]);
+        c2[4 * r4 + 3] = fmaf(u.w, by, c2[4 * r4 + 3]);
+      }
+      zm1 = mz - 1.f;
+      ay = fmaf(x2b, ay, ay);
+      az = fmaf(x1b, az, fmaf(d1b, zm1, az));
+      by = fmaf(x2b, by, fmaf(d2b, my, by));
+      bz = fmaf(x1b, bz, bz);
+      my = fmaf(x2b, my, my);
+      mz = fmaf(x1b, zm1, mz);
+    }
+  }
+  if (!valid) return;
+  const float m = on ? 1.f : 0.f;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    coef[(size_t)r * nv + j] = c0[r] * m;
+    coef[(size_t)(R + r) * nv + j] = c1[r] * m;
+    coef[(size_t)(2 * R + r) * nv + j] = c2[r] * m;
+  }
+}
+
+// h_r,j for J.v, written as the K-major split-BF16 operand of the readout GEMM:
+// row r * ny + iy, columns 2 ix (re) and 2 ix + 1 (im)
+__global__ void lr_prep_jvp_kernel(const float* __restrict__ v, const float* __restrict__ coef,
+                                   const float2* __restrict__ rho, const float* __restrict__ maskf, int nx,
+                                   int ny, int nv, int R, __nv_bfloat16* __restrict__ hi,
+                                   __nv_bfloat16* __restrict__ lo, int ldk, const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nv) return;
+  const int iy = j / nx, ix = j - iy * nx;
+  const float m = maskf[j];
+  const float2 rh = rho[j];
+  const float v0 = v[j], v1 = v[nv + j], v2 = v[2 * (size_t)nv + j] * m, v3 = v[3 * (size_t)nv + j] * m;
+  for (int r = 0; r < R; ++r) {
+    const float c = coef[(size_t)r * nv + j];
+    const float t = fmaf(v0, coef[(size_t)(R + r) * nv + j], v1 * coef[(size_t)(2 * R + r) * nv + j]);
+    // q = rho t + (v2 + i v3) c ; h = i q
+    const float qr = rh.x * t + v2 * c, qi = rh.y * t + v3 * c;
+    const size_t row = (size_t)(r * ny + iy) * ldk;
+    put_split(hi, lo, row + 2 * ix, -qi);
+    put_split(hi, lo, row + 2 * ix + 1, qr);
+  }
+}
+
+// complex rows (r, a) x B columns of src (row stride 2B floats) -> split-BF16 rows (r, b)
+// x A complex columns of dst (row stride ldk); tiles of 32 x 32 through shared memory
+__global__ void lr_transpose_split_kernel(const float* __restrict__ src, int A, int B,
+                                          __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int ldk,
+                                          const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  __shared__ float2 tile[32][33];
+  const int r = blockIdx.z;
+  const int b0 = blockIdx.x * 32, a0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const float2* s2 = reinterpret_cast<const float2*>(src) + (size_t)r * A * B;
+  for (int k = ty; k < 32; k += 8) {
+    const int a = a0 + k, b = b0 + tx;
+    tile[k][tx] = (a < A && b < B) ? s2[(size_t)a * B + b] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int b = b0 + k, a = a0 + tx;
+    if (a < A && b < B) {
+      const float2 v = tile[tx][k];
+      const size_t row = ((size_t)r * B + b) * ldk;
+      put_split(hi, lo, row + 2 * a, v.x);
+      put_split(hi, lo, row + 2 * a + 1, v.y);
+    }
+  }
+}
+
+// s[n][kx] = sum_r U[n][r] H[(r nkx + kx)][ky(n)]   (H rows: ny complex values)
+__global__ void lr_expand_kernel(const float* __restrict__ H, const float* __restrict__ U,
+                                 const int* __restrict__ kyi, int ntr, int nkx, int ny, int R,
+                                 float2* __restrict__ s) {
+  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.y;
+  if (kx >= nkx || n >= ntr) return;
+  const int ky = kyi[n];
+  const float2* H2 = reinterpret_cast<const float2*>(H);
+  float sr = 0.f, si = 0.f;
+  for (int r = 0; r < R; ++r) {
+    const float u = __ldg(U + (size_t)n * R + r);
+    const float2 h = H2[((size_t)r * nkx + kx) * ny + ky];
+    sr = fmaf(u, h.x, sr);
+    si = fmaf(u, h.y, si);
+  }
+  s[(size_t)n * nkx + kx] = make_float2(sr, si);
+}
+
+// G_r[ky][kx] = sum_r' M_ky[r][r'] H_r'[ky][kx], written as the split operand of the
+// phase-encode adjoint GEMM (rows (r, kx), columns 2 ky + re/im).  One block per ky.
+__global__ void lr_gram_kernel(const float* __restrict__ H, const float* __restrict__ Mky, int nkx, int ny,
+                               int R, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int ldk,
+                               const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  extern __shared__ float msh[];  // R x R
+  const int ky = blockIdx.x;
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) msh[e] = Mky[(size_t)ky * R * R + e];
+  __syncthreads();
+  const float2* H2 = reinterpret_cast<const float2*>(H);
+  for (int kx = threadIdx.x; kx < nkx; kx += blockDim.x) {
+    float2 h[kMaxRank];
+    for (int r = 0; r < R; ++r) h[r] = H2[((size_t)r * nkx + kx) * ny + ky];
+    for (int r = 0; r < R; ++r) {
+      float gr = 0.f, gi = 0.f;
+      for (int q = 0; q < R; ++q) {
+        const float mm = msh[r * R + q];
+        gr = fmaf(mm, h[q].x, gr);
+        gi = fmaf(mm, h[q].y, gi);
+      }
+      const size_t row = ((size_t)r * nkx + kx) * ldk;
+      put_split(hi, lo, row + 2 * ky, gr);
+      put_split(hi, lo, row + 2 * ky + 1, gi);
+    }
+  }
+}
+
+// G_r[ky][kx] = sum_{n: ky(n) = ky} U[n][r] w[n][kx] into the same operand layout
+__global__ void lr_gather_kernel(const float2* __restrict__ w, const float* __restrict__ U,
+                                 const int* __restrict__ kyptr, const int* __restrict__ kytr, int nkx, int R,
+                                 __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int ldk) {
+  const int ky = blockIdx.x;
+  const int na = kyptr[ky], ne = kyptr[ky + 1];
+  for (int kx = threadIdx.x; kx < nkx; kx += blockDim.x) {
+    float2 g[kMaxRank];
+    for (int r = 0; r < R; ++r) g[r] = make_float2(0.f, 0.f);
+    for (int t = na; t < ne; ++t) {
+      const int n = kytr[t];
+      const float2 wv = w[(size_t)n * nkx + kx];
+      for (int r = 0; r < R; ++r) {
+        const float u = __ldg(U + (size_t)n * R + r);
+        g[r].x = fmaf(u, wv.x, g[r].x);
+        g[r].y = fmaf(u, wv.y, g[r].y);
+      }
+    }
+    for (int r = 0; r < R; ++r) {
+      const size_t row = ((size_t)r * nkx + kx) * ldk;
+      put_split(hi, lo, row + 2 * ky, g[r].x);
+      put_split(hi, lo, row + 2 * ky + 1, g[r].y);
+    }
+  }
+}
+
+// g_k,j = Re sum_r conj(dh_r,j/dv_k) P_r,j with P rows (r ny + iy), columns 2 ix + re/im
+__global__ void lr_final_kernel(const float* __restrict__ P, const float* __restrict__ coef,
+                                const float2* __restrict__ rho, const float* __restrict__ maskf, int nx, int ny,
+                                int nv, int R, float* __restrict__ g, const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nv) return;
+  const int iy = j / nx, ix = j - iy * nx;
+  const float2* P2 = reinterpret_cast<const float2*>(P);
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  const float2 rh = rho[j];
+  for (int r = 0; r < R; ++r) {
+    const float2 p = P2[(size_t)(r * ny + iy) * nx + ix];
+    const float c = coef[(size_t)r * nv + j];
+    const float t1 = coef[(size_t)(R + r) * nv + j], t2 = coef[(size_t)(2 * R + r) * nv + j];
+    const float imcp = rh.x * p.y - rh.y * p.x;  // Im(conj(rho) P)
+    a0 = fmaf(t1, imcp, a0);
+    a1 = fmaf(t2, imcp, a1);
+    a2 = fmaf(c, p.y, a2);
+    a3 = fmaf(-c, p.x, a3);
+  }
+  const float m = maskf[j];
+  g[j] = a0 * m;
+  g[nv + j] = a1 * m;
+  g[2 * (size_t)nv + j] = a2 * m;
+  g[3 * (size_t)nv + j] = a3 * m;
+}
+
+// training time courses [3][nq][ns] (quads) -> Y [ntr][3 ns] and Yt [3 ns][ntr] (complex
+// storage with zero imaginary part), columns c * ns + s
+__global__ void lr_train_matrix_kernel(const float4* __restrict__ D, int ns, int nq, int ntr,
+                                       float2* __restrict__ Y, float2* __restrict__ Yt) {
+  const int64_t K = 3 * (int64_t)ns;
+  const int64_t total = (int64_t)ntr * K;
+  const float* Df = reinterpret_cast<const float*>(D);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = e / K;
+    const int64_t col = e - n * K;
+    const int64_t c = col / ns, s = col - c * ns;
+    const float v = Df[(((size_t)c * nq + (n >> 2)) * ns + s) * 4 + (n & 3)];
+    Y[e] = make_float2(v, 0.f);
+    Yt[col * ntr + n] = make_float2(v, 0.f);
+  }
+}
+
+template <int R>
+cudaError_t launch_project_t(const Plan& p, const LowRank& L, const float* alpha, const float* b1,
+                             const uint8_t* mask, float* coef, cudaStream_t st) {
+  const int blocks = (p.nv + 127) / 128;
+  lr_project_kernel<R><<<blocks, 128, 0, st>>>(alpha, b1, mask, p.cs, p.phi, L.U, p.nv, p.ntr, (float)p.te_ms,
+                                               (float)(p.tr_ms - p.te_ms), p.inversion ? -1.f : 1.f, coef);
+  return cudaGetLastError();
+}
+
+inline int pad8(int k) { return (k + 7) / 8 * 8; }
+
+}  // namespace
+
+cudaError_t lowrank_project(const Plan& p, const LowRank& L, const float* alpha, const float* b1,
+                            const uint8_t* mask, float* coef, cudaStream_t st) {
+  if (p.nv == 0) return cudaSuccess;
+  switch (L.R) {
+    case 8: return launch_project_t<8>(p, L, alpha, b1, mask, coef, st);
+    case 16: return launch_project_t<16>(p, L, alpha, b1, mask, coef, st);
+    case 24: return launch_project_t<24>(p, L, alpha, b1, mask, coef, st);
+    case 32: return launch_project_t<32>(p, L, alpha, b1, mask, coef, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+void lowrank_free(LowRank* L) {
+  if (L == nullptr) return;
+  void* ptrs[] = {L->U, L->Mky, L->kyptr, L->kytr, L->coef, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
+                  L->a4_hi, L->a4_lo, L->by_hi, L->by_lo, L->bya_hi, L->bya_lo, L->X1, L->H, L->Y3, L->P};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete L;
+}
+
+// Allocates the low-rank work space and builds the phase-encode DFT operands and the
+// per-ky tables for basis U (device [ntr][R]); the readout DFT operands are the plan's
+// split-BF16 tables.
+int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
+  if (R != 8 && R != 16 && R != 24 && R != 32)
+    return fail(MRSTAT_ERR_INVALID_ARG, "rank %d not in {8, 16, 24, 32}", R);
+  if (!p->tc) {
+    const int s = build_split_tables(p);
+    if (s != MRSTAT_OK) return s;
+  }
+  if (p->lr) {
+    lowrank_free(p->lr);
+    p->lr = nullptr;
+  }
+  LowRank* L = new LowRank();
+  L->R = R;
+  const int nx = p->nx, ny = p->ny, nkx = p->nkx, ntr = p->ntr;
+  L->k1 = pad8(2 * nx);
+  L->k23 = pad8(2 * ny);
+  L->k4 = pad8(2 * nkx);
+  // host copies of U (float64 for the Gram tables)
+  std::vector<float> Uh((size_t)ntr * R);
+  cudaError_t e = cudaMemcpyAsync(Uh.data(), U_dev, Uh.size() * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    delete L;
+    return cuda_fail(e, "basis copy");
+  }
+  std::vector<int> kyi_h(p->ntr_pad);
+  e = cudaMemcpy(kyi_h.data(), p->kyi, kyi_h.size() * sizeof(int), cudaMemcpyDeviceToHost);
+  std::vector<int> ptr(ny + 1, 0), trs(ntr);
+  for (int n = 0; n < ntr; ++n) ptr[kyi_h[n] + 1]++;
+  for (int k = 0; k < ny; ++k) ptr[k + 1] += ptr[k];
+  {
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (int n = 0; n < ntr; ++n) trs[fill[kyi_h[n]]++] = n;
+  }
+  std::vector<float> M((size_t)ny * R * R, 0.f);
+  for (int k = 0; k < ny; ++k)
+    for (int a = 0; a < R; ++a)
+      for (int b = 0; b < R; ++b) {
+        double s = 0.0;
+        for (int t = ptr[k]; t < ptr[k + 1]; ++t) s += (double)Uh[(size_t)trs[t] * R + a] * Uh[(size_t)trs[t] * R + b];
+        M[((size_t)k * R + a) * R + b] = (float)s;
+      }
+  // phase-encode DFT operands (K-major real embeddings, split into bf16 hi + lo)
+  const size_t nby = (size_t)2 * ny * L->k23;
+  std::vector<uint16_t> byh(nby, 0), byl(nby, 0), bah(nby, 0), bal(nby, 0);
+  auto put = [](std::vector<uint16_t>& hi, std::vector<uint16_t>& lo, size_t idx, double v) {
+    const uint16_t h = host_bf16((float)v);
+    hi[idx] = h;
+    lo[idx] = host_bf16((float)(v - (double)host_bf16_to_float(h)));
+  };
+  for (int ky = 0; ky < ny; ++ky)
+    for (int iy = 0; iy < ny; ++iy) {
+      const long long r = ((long long)ky * iy) % ny;
+      const double ang = -2.0 * M_PI * (double)r / (double)ny;
+      const double er = std::cos(ang), ei = std::sin(ang);  // Ey = exp(-2 pi i ky iy / ny)
+      // forward: output rows 2 ky (+1), inputs 2 iy (+1)
+      put(byh, byl, (size_t)(2 * ky) * L->k23 + 2 * iy, er);
+      put(byh, byl, (size_t)(2 * ky) * L->k23 + 2 * iy + 1, -ei);
+      put(byh, byl, (size_t)(2 * ky + 1) * L->k23 + 2 * iy, ei);
+      put(byh, byl, (size_t)(2 * ky + 1) * L->k23 + 2 * iy + 1, er);
+      // adjoint (conj, transposed): output rows 2 iy (+1), inputs 2 ky (+1)
+      put(bah, bal, (size_t)(2 * iy) * L->k23 + 2 * ky, er);
+      put(bah, bal, (size_t)(2 * iy) * L->k23 + 2 * ky + 1, ei);
+      put(bah, bal, (size_t)(2 * iy + 1) * L->k23 + 2 * ky, -ei);
+      put(bah, bal, (size_t)(2 * iy + 1) * L->k23 + 2 * ky + 1, er);
+    }
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  const size_t rny = (size_t)R * ny, rnk = (size_t)R * nkx;
+  chk(cudaMalloc(&L->U, (size_t)ntr * R * sizeof(float)));
+  chk(cudaMalloc(&L->Mky, M.size() * sizeof(float)));
+  chk(cudaMalloc(&L->kyptr, ptr.size() * sizeof(int)));
+  chk(cudaMalloc(&L->kytr, trs.size() * sizeof(int)));
+  chk(cudaMalloc(&L->coef, (size_t)3 * R * p->nv * sizeof(float)));
+  chk(cudaMalloc(&L->a1_hi, rny * L->k1 * 2));
+  chk(cudaMalloc(&L->a1_lo, rny * L->k1 * 2));
+  chk(cudaMalloc(&L->a23_hi, rnk * L->k23 * 2));
+  chk(cudaMalloc(&L->a23_lo, rnk * L->k23 * 2));
+  chk(cudaMalloc(&L->a4_hi, rny * L->k4 * 2));
+  chk(cudaMalloc(&L->a4_lo, rny * L->k4 * 2));
+  chk(cudaMalloc(&L->by_hi, nby * 2));
+  chk(cudaMalloc(&L->by_lo, nby * 2));
+  chk(cudaMalloc(&L->bya_hi, nby * 2));
+  chk(cudaMalloc(&L->bya_lo, nby * 2));
+  chk(cudaMalloc(&L->X1, rny * 2 * nkx * sizeof(float)));
+  chk(cudaMalloc(&L->H, rnk * 2 * ny * sizeof(float)));
+  chk(cudaMalloc(&L->Y3, rnk * 2 * ny * sizeof(float)));
+  chk(cudaMalloc(&L->P, rny * 2 * nx * sizeof(float)));
+  if (e != cudaSuccess) {
+    lowrank_free(L);
+    return cuda_fail(e, "low-rank allocation");
+  }
+  chk(cudaMemcpyAsync(L->U, U_dev, (size_t)ntr * R * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  chk(cudaMemcpy(L->Mky, M.data(), M.size() * sizeof(float), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(L->kyptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(L->kytr, trs.data(), trs.size() * sizeof(int), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(L->by_hi, byh.data(), nby * 2, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(L->by_lo, byl.data(), nby * 2, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(L->bya_hi, bah.data(), nby * 2, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(L->bya_lo, bal.data(), nby * 2, cudaMemcpyHostToDevice));
+  // padding columns of the operands must read as zero
+  chk(cudaMemset(L->a1_hi, 0, rny * L->k1 * 2));
+  chk(cudaMemset(L->a1_lo, 0, rny * L->k1 * 2));
+  chk(cudaMemset(L->a23_hi, 0, rnk * L->k23 * 2));
+  chk(cudaMemset(L->a23_lo, 0, rnk * L->k23 * 2));
+  chk(cudaMemset(L->a4_hi, 0, rny * L->k4 * 2));
+  chk(cudaMemset(L->a4_lo, 0, rny * L->k4 * 2));
+  chk(make_split_operand(&L->op_a1, L->a1_hi, L->a1_lo, (int)rny, 2 * nx, L->k1, true));
+  chk(make_split_operand(&L->op_a23, L->a23_hi, L->a23_lo, (int)rnk, 2 * ny, L->k23, true));
+  chk(make_split_operand(&L->op_a4, L->a4_hi, L->a4_lo, (int)rny, 2 * nkx, L->k4, true));
+  chk(make_split_operand(&L->op_by, L->by_hi, L->by_lo, 2 * ny, 2 * ny, L->k23, false));
+  chk(make_split_operand(&L->op_bya, L->bya_hi, L->bya_lo, 2 * ny, 2 * ny, L->k23, false));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    lowrank_free(L);
+    return cuda_fail(e, "low-rank set-up");
+  }
+  p->bytes += (int64_t)((size_t)ntr * R * 4 + M.size() * 4 + (size_t)3 * R * p->nv * 4 +
+                        2 * 2 * (rny * L->k1 + rnk * L->k23 + rny * L->k4) + 4 * nby * 2 +
+                        (rny * 2 * nkx + 2 * rnk * 2 * ny + rny * 2 * nx) * 4);
+  p->lr = L;
+  return MRSTAT_OK;
+}
+
+// ---- the three stages shared by the products ----
+static int lr_forward_dft(Plan* p, const int* gate, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  const int R = L.R, nx = p->nx, ny = p->ny, nkx = p->nkx;
+  cudaError_t e;
+  {
+    Span sp(p, MRSTAT_K_XDFT, st);
+    e = launch_tc_gemm(L.op_a1, p->tc[1], L.X1, R * ny, 2 * nkx, 2 * nx, 2 * nkx, 3, gate, p->dev_err, st);
+  }
+  if (e == cudaSuccess) {
+    Span sp(p, MRSTAT_K_VECTOR, st);
+    dim3 grid((nkx + 31) / 32, (ny + 31) / 32, R);
+    lr_transpose_split_kernel<<<grid, dim3(32, 8), 0, st>>>(L.X1, ny, nkx, (__nv_bfloat16*)L.a23_hi,
+                                                            (__nv_bfloat16*)L.a23_lo, L.k23, gate);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    Span sp(p, MRSTAT_K_XDFT, st);
+    e = launch_tc_gemm(L.op_a23, L.op_by, L.H, R * nkx, 2 * ny, 2 * ny, 2 * ny, 3, gate, p->dev_err, st);
+  }
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank DFT");
+}
+
+static int lr_adjoint_dft_and_final(Plan* p, float* g, const int* gate, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  const int R = L.R, nx = p->nx, ny = p->ny, nkx = p->nkx;
+  cudaError_t e;
+  {
+    Span sp(p, MRSTAT_K_XDFT_ADJ, st);
+    e = launch_tc_gemm(L.op_a23, L.op_bya, L.Y3, R * nkx, 2 * ny, 2 * ny, 2 * ny, 3, gate, p->dev_err, st);
+  }
+  if (e == cudaSuccess) {
+    Span sp(p, MRSTAT_K_VECTOR, st);
+    dim3 grid((ny + 31) / 32, (nkx + 31) / 32, R);
+    lr_transpose_split_kernel<<<grid, dim3(32, 8), 0, st>>>(L.Y3, nkx, ny, (__nv_bfloat16*)L.a4_hi,
+                                                            (__nv_bfloat16*)L.a4_lo, L.k4, gate);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    Span sp(p, MRSTAT_K_XDFT_ADJ, st);
+    e = launch_tc_gemm(L.op_a4, p->tc[3], L.P, R * ny, 2 * nx, 2 * nkx, 2 * nx, 3, gate, p->dev_err, st);
+  }
+  if (e == cudaSuccess) {
+    Span sp(p, MRSTAT_K_JHW_DOT, st);
+    lr_final_kernel<<<(p->nv + 255) / 256, 256, 0, st>>>(L.P, L.coef, p->rho, p->maskf, nx, ny, p->nv, R, g, gate);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank adjoint DFT");
+}
+
+static int lr_prep(Plan* p, const float* v, const int* gate, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  Span sp(p, MRSTAT_K_YCONTRACT, st);
+  lr_prep_jvp_kernel<<<(p->nv + 255) / 256, 256, 0, st>>>(v, L.coef, p->rho, p->maskf, p->nx, p->ny, p->nv, L.R,
+                                                          (__nv_bfloat16*)L.a1_hi, (__nv_bfloat16*)L.a1_lo, L.k1,
+                                                          gate);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank prep");
+}
+
+int lowrank_jvp(Plan* p, const float* v, float2* jv, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  int s = lr_prep(p, v, p->gate, st);
+  if (s == MRSTAT_OK) s = lr_forward_dft(p, p->gate, st);
+  if (s != MRSTAT_OK) return s;
+  Span sp(p, MRSTAT_K_VECTOR, st);
+  dim3 grid((p->nkx + 127) / 128, p->ntr);
+  lr_expand_kernel<<<grid, 128, 0, st>>>(L.H, L.U, p->kyi, p->ntr, p->nkx, p->ny, L.R, jv);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank expand");
+}
+
+int lowrank_jhw(Plan* p, const float2* w, float* g, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  {
+    Span sp(p, MRSTAT_K_VECTOR, st);
+    lr_gather_kernel<<<p->ny, 128, 0, st>>>(w, L.U, L.kyptr, L.kytr, p->nkx, L.R, (__nv_bfloat16*)L.a23_hi,
+                                            (__nv_bfloat16*)L.a23_lo, L.k23);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "low-rank gather");
+  }
+  return lr_adjoint_dft_and_final(p, g, p->gate, st);
+}
+
+int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  int s = lr_prep(p, v, p->gate, st);
+  if (s == MRSTAT_OK) s = lr_forward_dft(p, p->gate, st);
+  if (s != MRSTAT_OK) return s;
+  {
+    Span sp(p, MRSTAT_K_VECTOR, st);
+    lr_gram_kernel<<<p->ny, 128, (size_t)L.R * L.R * sizeof(float), st>>>(
+        L.H, L.Mky, p->nkx, p->ny, L.R, (__nv_bfloat16*)L.a23_hi, (__nv_bfloat16*)L.a23_lo, L.k23, p->gate);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "low-rank Gram");
+  }
+  return lr_adjoint_dft_and_final(p, out, p->gate, st);
+}
+
+cudaError_t lowrank_train_matrix(const float4* D, int ns, int nq, int ntr, float2* Y, float2* Yt,
+                                 cudaStream_t st) {
+  const int64_t total = (int64_t)ntr * 3 * ns;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  lr_train_matrix_kernel<<<blocks, 256, 0, st>>>(D, ns, nq, ntr, Y, Yt);
+  return cudaGetLastError();
+}
+
+}  // namespace mrstat

@@ -1,0 +1,33 @@
+// Low-rank form work space (see lowrank.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tc_gemm.cuh"
+
+namespace mrstat {
+
+constexpr int kMaxRank = 32;
+
+struct LowRank {
+  int R = 0;
+  int k1 = 0, k23 = 0, k4 = 0;     // padded K of the operands (2 nx, 2 ny, 2 nkx)
+  float* U = nullptr;              // [ntr][R] time basis
+  float* Mky = nullptr;            // [ny][R][R] per-ky Gram of U rows
+  int* kyptr = nullptr;            // [ny + 1] TR lists per ky residue
+  int* kytr = nullptr;             // [ntr]
+  float* coef = nullptr;           // [3][R][nv]: c, dc/dlnT1, dc/dlnT2 (masked)
+  void *a1_hi = nullptr, *a1_lo = nullptr;    // [R ny][k1]   readout-DFT input rows
+  void *a23_hi = nullptr, *a23_lo = nullptr;  // [R nkx][k23] phase-encode DFT input rows
+  void *a4_hi = nullptr, *a4_lo = nullptr;    // [R ny][k4]   readout adjoint input rows
+  void *by_hi = nullptr, *by_lo = nullptr;    // [2 ny][k23] phase-encode DFT (K-major)
+  void *bya_hi = nullptr, *bya_lo = nullptr;  // [2 ny][k23] its adjoint
+  float* X1 = nullptr;             // [R ny][2 nkx]
+  float* H = nullptr;              // [R nkx][2 ny]
+  float* Y3 = nullptr;             // [R nkx][2 ny]
+  float* P = nullptr;              // [R ny][2 nx]
+  TcOperand op_a1, op_a23, op_a4, op_by, op_bya;
+  bool active = false;             // the plan's current linearisation is this low-rank one
+};
+
+}  // namespace mrstat

@@ -49,6 +49,7 @@ void free_plan(Plan* p) {
     if (q) cudaFree(q);
   for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
   delete[] p->tc;
+  lowrank_free(p->lr);
   delete p;
 }
 
@@ -76,6 +77,71 @@ cudaError_t ensure_timecourses(Plan* p) {
 cudaError_t ensure_forward_scratch(Plan* p) {
   if (p->dfwd != nullptr) return cudaSuccess;
   return dalloc(p, &p->dfwd, (size_t)p->nq * p->nv);
+}
+
+int build_split_tables(Plan* p) {
+  if (p->tc != nullptr) return MRSTAT_OK;
+  p->kf_pad = (2 * p->nx + 7) / 8 * 8;
+  p->ka_pad = (2 * p->nkx + 7) / 8 * 8;
+  const size_t nf = (size_t)2 * p->nkx * p->kf_pad, na = (size_t)2 * p->nx * p->ka_pad;
+  // real embeddings of the complex DFT matrices (K-major), split into bf16 hi + lo
+  std::vector<uint16_t> bfh_f(nf, 0), bfl_f(nf, 0), bfh_a(na, 0), bfl_a(na, 0);
+  auto put = [](std::vector<uint16_t>& hi, std::vector<uint16_t>& lo, size_t idx, double v) {
+    const uint16_t h = host_bf16((float)v);
+    hi[idx] = h;
+    lo[idx] = host_bf16((float)(v - (double)host_bf16_to_float(h)));
+  };
+  for (int k = 0; k < p->nkx; ++k)
+    for (int ix = 0; ix < p->nx; ++ix) {
+      const long long kx = k - p->nkx / 2;
+      long long r = (kx * ix) % p->nx;
+      if (r < 0) r += p->nx;
+      const double ang = -2.0 * M_PI * (double)r / (double)p->nx;
+      const double fr = std::cos(ang), fi = std::sin(ang);  // F = exp(-2 pi i kx ix / nx)
+      // forward: rows 2k (re), 2k+1 (im) of the output; columns 2ix (re A), 2ix+1 (im A)
+      put(bfh_f, bfl_f, (size_t)(2 * k) * p->kf_pad + 2 * ix, fr);
+      put(bfh_f, bfl_f, (size_t)(2 * k) * p->kf_pad + 2 * ix + 1, -fi);
+      put(bfh_f, bfl_f, (size_t)(2 * k + 1) * p->kf_pad + 2 * ix, fi);
+      put(bfh_f, bfl_f, (size_t)(2 * k + 1) * p->kf_pad + 2 * ix + 1, fr);
+      // adjoint with G = conj(F): rows 2ix, 2ix+1 of the output; columns 2k, 2k+1 of w
+      put(bfh_a, bfl_a, (size_t)(2 * ix) * p->ka_pad + 2 * k, fr);
+      put(bfh_a, bfl_a, (size_t)(2 * ix) * p->ka_pad + 2 * k + 1, fi);
+      put(bfh_a, bfl_a, (size_t)(2 * ix + 1) * p->ka_pad + 2 * k, -fi);
+      put(bfh_a, bfl_a, (size_t)(2 * ix + 1) * p->ka_pad + 2 * k + 1, fr);
+    }
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  chk(cudaMalloc(&p->bf_ft_hi, nf * 2));
+  chk(cudaMalloc(&p->bf_ft_lo, nf * 2));
+  chk(cudaMalloc(&p->bf_fh_hi, na * 2));
+  chk(cudaMalloc(&p->bf_fh_lo, na * 2));
+  chk(cudaMalloc(&p->bf_a_hi, (size_t)p->ntr * p->kf_pad * 2));
+  chk(cudaMalloc(&p->bf_a_lo, (size_t)p->ntr * p->kf_pad * 2));
+  chk(cudaMalloc(&p->bf_w_hi, (size_t)p->ntr * p->ka_pad * 2));
+  chk(cudaMalloc(&p->bf_w_lo, (size_t)p->ntr * p->ka_pad * 2));
+  if (e != cudaSuccess) return cuda_fail(e, "split-BF16 table allocation");
+  p->bytes += (int64_t)(2 * (nf + na) * 2 + 2 * (size_t)p->ntr * (p->kf_pad + p->ka_pad) * 2);
+  chk(cudaMemcpy(p->bf_ft_hi, bfh_f.data(), nf * 2, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(p->bf_ft_lo, bfl_f.data(), nf * 2, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(p->bf_fh_hi, bfh_a.data(), na * 2, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(p->bf_fh_lo, bfl_a.data(), na * 2, cudaMemcpyHostToDevice));
+  chk(cudaMemset(p->bf_a_hi, 0, (size_t)p->ntr * p->kf_pad * 2));
+  chk(cudaMemset(p->bf_a_lo, 0, (size_t)p->ntr * p->kf_pad * 2));
+  chk(cudaMemset(p->bf_w_hi, 0, (size_t)p->ntr * p->ka_pad * 2));
+  chk(cudaMemset(p->bf_w_lo, 0, (size_t)p->ntr * p->ka_pad * 2));
+  TcOperand* tc = new TcOperand[4];
+  chk(make_split_operand(&tc[0], p->bf_a_hi, p->bf_a_lo, p->ntr, 2 * p->nx, p->kf_pad, true));
+  chk(make_split_operand(&tc[1], p->bf_ft_hi, p->bf_ft_lo, 2 * p->nkx, 2 * p->nx, p->kf_pad, false));
+  chk(make_split_operand(&tc[2], p->bf_w_hi, p->bf_w_lo, p->ntr, 2 * p->nkx, p->ka_pad, true));
+  chk(make_split_operand(&tc[3], p->bf_fh_hi, p->bf_fh_lo, 2 * p->nx, 2 * p->nkx, p->ka_pad, false));
+  if (e != cudaSuccess) {
+    delete[] tc;
+    return cuda_fail(e, "split-BF16 tables");
+  }
+  p->tc = tc;
+  return MRSTAT_OK;
 }
 
 cudaEvent_t pool_event(Plan* p) {
@@ -182,6 +248,13 @@ int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* ma
   }
   if (e != cudaSuccess) return cuda_fail(e, "bloch launch");
   return MRSTAT_OK;
+}
+
+int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st) {
+  if (p->lr && p->lr->active) return lowrank_jhjv(p, v, out, st);
+  int s = do_jvp(p, v, p->cg_jv, st);
+  if (s == MRSTAT_OK) s = do_jhw(p, p->cg_jv, out, st);
+  return s;
 }
 
 cudaError_t do_dot(Plan* p, const float* a, const float* b, int64_t n, double* out, cudaStream_t st) {
@@ -350,50 +423,6 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(dalloc(p, &p->cg_jv, (size_t)p->ntr * p->nkx));
   chk(dalloc(p, &p->cg_frozen, 1));
   chk(dalloc(p, &p->dev_err, 1));
-  std::vector<uint16_t> bfh_f, bfl_f, bfh_a, bfl_a;
-  if (form == MRSTAT_FORM_SPLIT_BF16) {
-    p->kf_pad = (2 * p->nx + 7) / 8 * 8;
-    p->ka_pad = (2 * p->nkx + 7) / 8 * 8;
-    const size_t nf = (size_t)2 * p->nkx * p->kf_pad, na = (size_t)2 * p->nx * p->ka_pad;
-    chk(cudaMalloc(&p->bf_ft_hi, nf * 2));
-    chk(cudaMalloc(&p->bf_ft_lo, nf * 2));
-    chk(cudaMalloc(&p->bf_fh_hi, na * 2));
-    chk(cudaMalloc(&p->bf_fh_lo, na * 2));
-    chk(cudaMalloc(&p->bf_a_hi, (size_t)p->ntr * p->kf_pad * 2));
-    chk(cudaMalloc(&p->bf_a_lo, (size_t)p->ntr * p->kf_pad * 2));
-    chk(cudaMalloc(&p->bf_w_hi, (size_t)p->ntr * p->ka_pad * 2));
-    chk(cudaMalloc(&p->bf_w_lo, (size_t)p->ntr * p->ka_pad * 2));
-    p->bytes += (int64_t)(2 * (nf + na) * 2 + 2 * (size_t)p->ntr * (p->kf_pad + p->ka_pad) * 2);
-    // real embeddings of the complex DFT matrices (K-major), split into bf16 hi + lo
-    bfh_f.assign(nf, 0);
-    bfl_f.assign(nf, 0);
-    bfh_a.assign(na, 0);
-    bfl_a.assign(na, 0);
-    auto put = [](std::vector<uint16_t>& hi, std::vector<uint16_t>& lo, size_t idx, double v) {
-      const float f = (float)v;
-      const uint16_t h = host_bf16(f);
-      hi[idx] = h;
-      lo[idx] = host_bf16((float)(v - (double)host_bf16_to_float(h)));
-    };
-    for (int k = 0; k < p->nkx; ++k)
-      for (int ix = 0; ix < p->nx; ++ix) {
-        const long long kx = k - p->nkx / 2;
-        long long r = (kx * ix) % p->nx;
-        if (r < 0) r += p->nx;
-        const double ang = -2.0 * M_PI * (double)r / (double)p->nx;
-        const double fr = std::cos(ang), fi = std::sin(ang);  // F = exp(-2 pi i kx ix / nx)
-        // forward: rows 2k (re), 2k+1 (im) of the output; columns 2ix (re A), 2ix+1 (im A)
-        put(bfh_f, bfl_f, (size_t)(2 * k) * p->kf_pad + 2 * ix, fr);
-        put(bfh_f, bfl_f, (size_t)(2 * k) * p->kf_pad + 2 * ix + 1, -fi);
-        put(bfh_f, bfl_f, (size_t)(2 * k + 1) * p->kf_pad + 2 * ix, fi);
-        put(bfh_f, bfl_f, (size_t)(2 * k + 1) * p->kf_pad + 2 * ix + 1, fr);
-        // adjoint with G = conj(F): rows 2ix, 2ix+1 of the output; columns 2k, 2k+1 of w
-        put(bfh_a, bfl_a, (size_t)(2 * ix) * p->ka_pad + 2 * k, fr);
-        put(bfh_a, bfl_a, (size_t)(2 * ix) * p->ka_pad + 2 * k + 1, fi);
-        put(bfh_a, bfl_a, (size_t)(2 * ix + 1) * p->ka_pad + 2 * k, -fi);
-        put(bfh_a, bfl_a, (size_t)(2 * ix + 1) * p->ka_pad + 2 * k + 1, fr);
-      }
-  }
   if (e != cudaSuccess) {
     int st = cuda_fail(e, "plan allocation");
     free_plan(p);
@@ -408,20 +437,12 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(cudaMemset(p->wt, 0, (size_t)p->ntr_pad * p->nx * sizeof(float2)));
   chk(cudaMemset(p->ticket, 0, sizeof(unsigned)));
   chk(cudaMemset(p->dev_err, 0, sizeof(int)));
-  if (form == MRSTAT_FORM_SPLIT_BF16) {
-    chk(cudaMemcpy(p->bf_ft_hi, bfh_f.data(), bfh_f.size() * 2, cudaMemcpyHostToDevice));
-    chk(cudaMemcpy(p->bf_ft_lo, bfl_f.data(), bfl_f.size() * 2, cudaMemcpyHostToDevice));
-    chk(cudaMemcpy(p->bf_fh_hi, bfh_a.data(), bfh_a.size() * 2, cudaMemcpyHostToDevice));
-    chk(cudaMemcpy(p->bf_fh_lo, bfl_a.data(), bfl_a.size() * 2, cudaMemcpyHostToDevice));
-    chk(cudaMemset(p->bf_a_hi, 0, (size_t)p->ntr * p->kf_pad * 2));
-    chk(cudaMemset(p->bf_a_lo, 0, (size_t)p->ntr * p->kf_pad * 2));
-    chk(cudaMemset(p->bf_w_hi, 0, (size_t)p->ntr * p->ka_pad * 2));
-    chk(cudaMemset(p->bf_w_lo, 0, (size_t)p->ntr * p->ka_pad * 2));
-    p->tc = new TcOperand[4];
-    chk(make_split_operand(&p->tc[0], p->bf_a_hi, p->bf_a_lo, p->ntr, 2 * p->nx, p->kf_pad, true));
-    chk(make_split_operand(&p->tc[1], p->bf_ft_hi, p->bf_ft_lo, 2 * p->nkx, 2 * p->nx, p->kf_pad, false));
-    chk(make_split_operand(&p->tc[2], p->bf_w_hi, p->bf_w_lo, p->ntr, 2 * p->nkx, p->ka_pad, true));
-    chk(make_split_operand(&p->tc[3], p->bf_fh_hi, p->bf_fh_lo, 2 * p->nx, 2 * p->nkx, p->ka_pad, false));
+  if (e == cudaSuccess && form == MRSTAT_FORM_SPLIT_BF16) {
+    const int st = build_split_tables(p);
+    if (st != MRSTAT_OK) {
+      free_plan(p);
+      return st;
+    }
   }
   chk(cudaDeviceSynchronize());
   if (e != cudaSuccess) {
@@ -461,6 +482,7 @@ int mrstat_linearize(mrstat_plan* plan, const float* alpha, const float* b1, con
   DeviceGuard g(plan->device);
   cudaStream_t st = as_stream(stream);
   plan->linearized = false;
+  if (plan->lr) plan->lr->active = false;
   cudaError_t ea = ensure_timecourses(plan);
   if (ea != cudaSuccess) return cuda_fail(ea, "time-course allocation");
   const int status = do_linearize(plan, alpha, b1, mask, plan->D, plan->rho, st);
@@ -500,6 +522,7 @@ int mrstat_jvp(mrstat_plan* plan, const float* v, float* jv, void* stream) {
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, v or jv");
   if (!plan->linearized) return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_jvp before mrstat_linearize");
   DeviceGuard g(plan->device);
+  if (plan->lr && plan->lr->active) return lowrank_jvp(plan, v, reinterpret_cast<float2*>(jv), as_stream(stream));
   return do_jvp(plan, v, reinterpret_cast<float2*>(jv), as_stream(stream));
 }
 
@@ -508,6 +531,7 @@ int mrstat_jhw(mrstat_plan* plan, const float* w, float* gout, void* stream) {
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, w or g");
   if (!plan->linearized) return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_jhw before mrstat_linearize");
   DeviceGuard g(plan->device);
+  if (plan->lr && plan->lr->active) return lowrank_jhw(plan, reinterpret_cast<const float2*>(w), gout, as_stream(stream));
   return do_jhw(plan, reinterpret_cast<const float2*>(w), gout, as_stream(stream));
 }
 
@@ -515,7 +539,8 @@ int mrstat_timecourses(mrstat_plan* plan, int32_t channel, float* out, void* str
   if (plan == nullptr || out == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or out");
   if (channel < 0 || channel >= kChannels)
     return fail(MRSTAT_ERR_INVALID_ARG, "channel %d not in [0, %d)", channel, kChannels);
-  if (!plan->linearized) return fail(MRSTAT_ERR_NOT_LINEARIZED, "timecourses before mrstat_linearize");
+  if (!plan->linearized || plan->D == nullptr || (plan->lr && plan->lr->active))
+    return fail(MRSTAT_ERR_NOT_LINEARIZED, "timecourses need an exact mrstat_linearize");
   DeviceGuard g(plan->device);
   Span sp(plan, MRSTAT_K_VECTOR, as_stream(stream));
   cudaError_t e = launch_timecourse(*plan, channel, out, as_stream(stream));
@@ -601,6 +626,14 @@ int mrstat_jhw_ckpt(mrstat_plan* plan, const float* w, float* gout, void* stream
   return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "segment recompute launch");
 }
 
+int mrstat_jhjv(mrstat_plan* plan, const float* v, float* out, void* stream) {
+  if (plan == nullptr || v == nullptr || out == nullptr)
+    return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, v or out");
+  if (!plan->linearized) return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_jhjv before a linearisation");
+  DeviceGuard g(plan->device);
+  return do_jhjv(plan, v, out, as_stream(stream));
+}
+
 int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters, void* stream) {
   if (plan == nullptr || rhs == nullptr || x == nullptr || iters < 0)
     return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_cg_fixed");
@@ -633,9 +666,7 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
     double* rr = sc + 4 * it;
     double* pq = rr + 1;
     double* rr_next = sc + 4 * (it + 1);
-    int s = do_jvp(plan, plan->cg_p, plan->cg_jv, st);
-    if (s != MRSTAT_OK) return s;
-    s = do_jhw(plan, plan->cg_jv, plan->cg_q, st);
+    int s = do_jhjv(plan, plan->cg_p, plan->cg_q, st);
     if (s != MRSTAT_OK) return s;
     e = do_dot(plan, plan->cg_p, plan->cg_q, n, pq, st);
     if (e == cudaSuccess) {

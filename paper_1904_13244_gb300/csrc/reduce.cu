@@ -3,7 +3,11 @@
 //
 // Reductions are deterministic and single-pass: every block writes its partial sum,
 // and the last block to finish (a release fence plus an atomic ticket) adds the
-// partials in block order and resets the ticket for the next launch.  CG scalars
+// partials in block order and resets the ticket for the next launch.  A thread forms
+// the products of its few elements (grid-stride, a handful per thread) in float32;
+// everything from the warp level up is added in float64.  GB300 runs float64 at a small
+// fraction of the float32 rate, and converting every element to float64 kept the FP64
+// pipe busy for most of these kernels' time.  CG scalars
 // never leave the device: each update kernel reads the float64 inner products it
 // needs, forms alpha or beta once per block (GB300's float64 rate makes a per-thread
 // division visible) and the x/r update also produces the partial sums of r.r.
@@ -58,10 +62,10 @@ __global__ void __launch_bounds__(kT)
 dot_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n, double* part,
            unsigned* ticket, double* __restrict__ out) {
   __shared__ double ws[kT / 32];
-  double s = 0.0;
+  float sf = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
-    s = fma((double)a[i], (double)b[i], s);
-  s = block_sum<kT>(s, ws);
+    sf = fmaf(a[i], b[i], sf);
+  const double s = block_sum<kT>((double)sf, ws);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
   finish_reduction<kT>(part, ticket, out, ws);
 }
@@ -96,7 +100,7 @@ cg_update_xr_kernel(float* __restrict__ x, float* __restrict__ r, const float* _
   }
   __syncthreads();
   const float al = s_alpha;
-  double s = 0.0;
+  float sf = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
     float ri = r[i];
     if (s_apply) {
@@ -104,9 +108,9 @@ cg_update_xr_kernel(float* __restrict__ x, float* __restrict__ r, const float* _
       ri = fmaf(-al, q[i], ri);
       r[i] = ri;
     }
-    s = fma((double)ri, (double)ri, s);
+    sf = fmaf(ri, ri, sf);
   }
-  s = block_sum<kT>(s, ws);
+  const double s = block_sum<kT>((double)sf, ws);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
   finish_reduction<kT>(part, ticket, rr_new, ws);
 }

@@ -1,0 +1,126 @@
+"""Low-rank (compressed) form on the GPU against the oracle's projected model.
+
+The low-rank model replaces every time course by its projection onto a real time
+basis U (oracle.model.project_onto_basis); given the same U, the GPU products must
+equal the oracle's products of the projected model.  The DFTs run as split-BF16
+tcgen05 products, so the bar is the split form's 3e-5 normwise.  The basis itself is
+checked against numpy's SVD of the same simulated training time courses.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import bloch, encoding, model, metrics
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 3e-5
+
+
+@pytest.fixture(scope="module")
+def mr():
+    import paper_1904_13244_gb300 as mr
+    from paper_1904_13244_gb300 import build
+    build.build()
+    return mr
+
+
+def f32(x):
+    return np.asarray(x).astype(np.float32).astype(np.float64)
+
+
+def cuda(x, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def training_set(n, seed):
+    rng = np.random.default_rng(seed)
+    return f32(np.stack([rng.uniform(np.log(100), np.log(6000), n), rng.uniform(np.log(10), np.log(3000), n)]))
+
+
+def random_phantom(nx, ny, seed):
+    rng = np.random.default_rng(seed)
+    t1 = np.exp(rng.uniform(np.log(200), np.log(3000), (ny, nx)))
+    t2 = np.exp(rng.uniform(np.log(20), np.log(300), (ny, nx)))
+    rho = rng.uniform(0.5, 1.0, (ny, nx)) * np.exp(1j * rng.uniform(0, 2 * np.pi, (ny, nx)))
+    return f32(np.stack([np.log(t1.ravel()), np.log(t2.ravel()), rho.real.ravel(), rho.imag.ravel()]))
+
+
+def test_time_basis_matches_numpy_svd(mr):
+    seq = synth.make_sequence(40, 24, 5, 7.8, 3.9, seed=3, extra_trs=6)
+    train = training_set(600, 1)
+    U_ref, s_ref = model.time_basis(seq, np.exp(train[0]), np.exp(train[1]), 16)
+    with mr.Plan(seq) as plan:
+        U, sv = plan.lowrank_basis(cuda(train), 16)
+        U = U.cpu().numpy().astype(np.float64)
+    assert np.allclose(U.T @ U, np.eye(16), atol=1e-6)
+    assert np.allclose(sv, s_ref, rtol=1e-4)
+    # the well-separated leading directions span the same subspace, and the whole basis
+    # compresses the training time courses as well as the exact SVD basis does
+    assert np.linalg.norm(U[:, :8] @ U[:, :8].T - U_ref[:, :8] @ U_ref[:, :8].T, 2) < 1e-3
+    sim = bloch.simulate(seq, np.exp(train[0]), np.exp(train[1]))
+    Y = np.concatenate([sim["m"].imag, sim["dm_dlnT1"].imag, sim["dm_dlnT2"].imag], axis=1)
+    res_gpu = np.linalg.norm(Y - U @ (U.T @ Y))
+    res_ref = np.linalg.norm(Y - U_ref @ (U_ref.T @ Y))
+    assert res_gpu < 1.01 * res_ref
+
+
+@pytest.mark.parametrize("case", [(40, 24, 5, 6, 48, 16), (33, 17, 3, 3, 30, 8), (64, 64, 5, 0, 64, 32)])
+def test_lowrank_products_match_projected_oracle(mr, case):
+    nx, ny, fills, extra, nkx, R = case
+    seq = synth.make_sequence(nx, ny, fills, 7.8, 3.9, seed=5, nkx=nkx, extra_trs=extra)
+    alpha = random_phantom(nx, ny, 7)
+    train = training_set(400, 2)
+    U, _ = model.time_basis(seq, np.exp(train[0]), np.exp(train[1]), R)
+    U = f32(U)
+    lin = model.project_onto_basis(model.linearize(seq, alpha), U)
+    v = synth.random_params(seq.nv, 11)
+    w = synth.random_kspace(seq.ntr, seq.nkx, 12)
+    with mr.Plan(seq) as plan:
+        plan.lowrank_set_basis(cuda(U))
+        plan.lowrank_linearize(cuda(alpha))
+        coef = plan.lowrank_coefficients().cpu().numpy()
+        jv = plan.jvp(cuda(v)).cpu().numpy()
+        g = plan.jhw(cuda(w, torch.complex64)).cpu().numpy()
+        h = plan.jhjv(cuda(v)).cpu().numpy()
+        h2 = plan.jhw(plan.jvp(cuda(v))).cpu().numpy()
+        plan.check()
+    raw = model.linearize(seq, alpha)
+    assert metrics.relerr(coef[0], U.T @ raw.m.imag) < 1e-5
+    assert metrics.relerr(coef[1], U.T @ raw.dm1.imag) < 1e-5
+    assert metrics.relerr(coef[2], U.T @ raw.dm2.imag) < 1e-5
+    assert metrics.relerr(jv, model.jvp(lin, v)) < TOL
+    assert metrics.relerr(g, model.jhw(lin, w)) < TOL
+    ref_h = model.gauss_newton_product(lin, v)
+    assert metrics.relerr(h, ref_h) < TOL
+    assert metrics.relerr(h2, ref_h) < TOL
+
+
+def test_lowrank_full_size_sampled_jhw(mr):
+    seq, ph = synth.config("brain224")
+    alpha = f32(np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(),
+                          ph.rho.imag.ravel()]))
+    w = synth.random_kspace(seq.ntr, seq.nkx, 52)
+    vox = np.sort(np.random.default_rng(5).choice(seq.nv, 64, replace=False))
+    with mr.Plan(seq) as plan:
+        train = cuda(training_set(2048, 3))
+        U, sv = plan.lowrank_basis(train, 32)
+        plan.lowrank_set_basis(U)
+        plan.lowrank_linearize(cuda(alpha))
+        g = plan.jhw(cuda(w, torch.complex64)).cpu().numpy()[:, vox]
+        Uh = U.cpu().numpy().astype(np.float64)
+        plan.check()
+    sim = bloch.simulate(seq, np.exp(alpha[0, vox]), np.exp(alpha[1, vox]))
+    W = encoding.encode_adjoint(seq, w, vox)
+    rho = alpha[2, vox] + 1j * alpha[3, vox]
+    P = lambda x: 1j * (Uh @ (Uh.T @ x.imag))
+    m, d1, d2 = P(sim["m"]), P(sim["dm_dlnT1"]), P(sim["dm_dlnT2"])
+    ref = np.stack([np.real(np.sum(np.conj(rho[None] * d1) * W, 0)), np.real(np.sum(np.conj(rho[None] * d2) * W, 0)),
+                    np.real(np.sum(np.conj(m) * W, 0)), np.real(np.sum(np.conj(1j * m) * W, 0))])
+    assert metrics.relerr(g, ref) < TOL
+    # the rank-32 model is close to the exact one on these voxels (projection error ~1e-3)
+    exact = np.stack([np.real(np.sum(np.conj(rho[None] * sim["dm_dlnT1"]) * W, 0)),
+                      np.real(np.sum(np.conj(rho[None] * sim["dm_dlnT2"]) * W, 0)),
+                      np.real(np.sum(np.conj(sim["m"]) * W, 0)), np.real(np.sum(np.conj(1j * sim["m"]) * W, 0))])
+    assert metrics.relerr(g, exact) < 1e-2
