@@ -233,6 +233,62 @@ int mrstat_lowrank_coefficients(mrstat_plan* plan, float* coef, void* stream);
 int mrstat_lowrank_rank(const mrstat_plan* plan);
 
 /*
+ * Coefficients of the exact time courses of ns parameter samples in the plan's time
+ * basis (training targets of the learned surrogate): the Bloch recursion with its
+ * tangents projected onto U on the fly, as in mrstat_lowrank_linearize.
+ *   params: device float [2][ns] (ln T1, ln T2); b1: device float [ns] or NULL;
+ *   coef: device float [3][R][ns] (c, dc/dlnT1, dc/dlnT2).
+ * Errors: INVALID_ARG, NOT_LINEARIZED (no basis), CUDA.
+ */
+int mrstat_lowrank_project_samples(mrstat_plan* plan, const float* params, const float* b1, int32_t ns,
+                                   float* coef, void* stream);
+
+/*
+ * Learned surrogate of the compressed Bloch model.  The paper names surrogate models as
+ * a way to cut the cost of its partial-derivative computations (Discussion).  The MLP
+ * maps u = ((ln T1 - mu1)/s1, (ln T2 - mu2)/s2, (B1 - mu3)/s3) through three tanh
+ * layers of width `hidden` to R coefficients c = scale * (W4 a3 + b4) of the echo time
+ * course in the plan's time basis; dc/dln T1 and dc/dln T2 come from forward-mode
+ * tangents through the same layers, all three streams sharing one BF16 tcgen05 GEMM
+ * per layer (float32 accumulation).  Training minimises the Sobolev loss
+ *   L = 1/B sum_b sum_r [(c - c*)^2 + lam ((dc1 - dc1*)^2 + (dc2 - dc2*)^2)] / scale_r^2
+ * by Adam with hand-written forward, backward and update kernels; float32 master
+ * weights, BF16 copies for the GEMMs.  Parameters are flat float32 in the order
+ * W1 [hidden][3], b1, W2, b2, W3, b3, W4 [R][hidden], b4.
+ *
+ * All pointers are device memory unless marked host.  lnT: [2][n] (ln T1, ln T2 in
+ * ms); b1: [n] or NULL (B1 = 1); target/coef: [3][R][n] (c, dc/dlnT1, dc/dlnT2).
+ * mrstat_mlp_train_step: one Adam step on a batch (lr = 0: gradient only); *loss
+ *   (device double, may be NULL) receives the batch loss before the step.
+ * mrstat_mlp_loss_grad: loss (host double) and gradient (device float [num_params], may
+ *   be NULL) of a batch at the current weights; synchronises.
+ * mrstat_mlp_infer: coefficients and their ln T1 / ln T2 derivatives for n samples.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, TIMEOUT, CUDA.
+ */
+typedef struct mrstat_mlp mrstat_mlp;
+
+typedef struct mrstat_mlp_config {
+  int32_t hidden;          /* 64, 128 or 256                                           */
+  int32_t rank;            /* R, 1..32                                                 */
+  float norm[6];           /* mu1, s1, mu2, s2, mu3, s3 (s > 0)                         */
+  float sobolev_weight;    /* lam                                                      */
+  uint64_t seed;           /* Glorot-uniform initial weights, zero biases              */
+} mrstat_mlp_config;
+
+int mrstat_mlp_create(const mrstat_mlp_config* cfg, mrstat_mlp** out);
+int mrstat_mlp_destroy(mrstat_mlp* mlp);
+int64_t mrstat_mlp_num_params(const mrstat_mlp* mlp);
+int mrstat_mlp_set_output_scale(mrstat_mlp* mlp, const float* scale /* host [R] */);
+int mrstat_mlp_get_params(mrstat_mlp* mlp, float* params /* host [num_params] */);
+int mrstat_mlp_set_params(mrstat_mlp* mlp, const float* params /* host [num_params] */);
+int mrstat_mlp_train_step(mrstat_mlp* mlp, const float* lnT, const float* b1, const float* target,
+                          int32_t batch, float lr, double* loss, void* stream);
+int mrstat_mlp_loss_grad(mrstat_mlp* mlp, const float* lnT, const float* b1, const float* target,
+                         int32_t batch, double* loss /* host */, float* grad, void* stream);
+int mrstat_mlp_infer(mrstat_mlp* mlp, const float* lnT, const float* b1, int32_t n, float* coef,
+                     void* stream);
+
+/*
  * *out = sum_i a[i] * b[i] (the CG inner products of the inner Gauss-Newton loop,
  * Algorithm 6): each thread adds its few products (a grid-stride handful) in float32,
  * all partial sums are added in float64; the relative error is ~1e-7 of sum |a b|.  a, b: device float [n]; out: device double.

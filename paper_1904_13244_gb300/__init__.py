@@ -23,9 +23,12 @@ from ._binding import (MrstatError, MRSTAT_FORM_PLAIN_FP32, MRSTAT_FORM_SPLIT_BF
                        mrstat_profile_start, mrstat_profile_stop, mrstat_gn_default_opts,
                        mrstat_gn_solve, mrstat_plan_check, mrstat_forward_ckpt, mrstat_jhw_ckpt,
                        mrstat_jhjv, mrstat_lowrank_basis, mrstat_lowrank_set_basis, mrstat_lowrank_linearize,
-                       mrstat_lowrank_coefficients, mrstat_lowrank_rank)
+                       mrstat_lowrank_coefficients, mrstat_lowrank_rank, mrstat_lowrank_project_samples,
+                       mrstat_mlp_create, mrstat_mlp_destroy, mrstat_mlp_num_params, mrstat_mlp_set_output_scale,
+                       mrstat_mlp_get_params, mrstat_mlp_set_params, mrstat_mlp_train_step, mrstat_mlp_loss_grad,
+                       mrstat_mlp_infer)
 
-__all__ = ["Plan", "MrstatError", "load", "Signal", "signal"]
+__all__ = ["Plan", "Surrogate", "MrstatError", "load", "Signal", "signal"]
 
 
 def load():
@@ -125,6 +128,14 @@ class Plan:
         mrstat_lowrank_coefficients(self._h, out, stream)
         return out
 
+    def lowrank_project_samples(self, params, b1=None, out=None, stream=None):
+        """Exact coefficients [3, R, ns] of sample time courses (ln T1, ln T2 in params [2, ns])."""
+        R = mrstat_lowrank_rank(self._h)
+        if out is None:
+            out = torch.empty((3, R, int(params.shape[1])), dtype=torch.float32, device="cuda")
+        mrstat_lowrank_project_samples(self._h, params, b1, out, stream)
+        return out
+
     def jvp(self, v, out=None, stream=None):
         out = self._kspace(out)
         mrstat_jvp(self._h, v, out, stream)
@@ -160,6 +171,58 @@ class Plan:
     def cg_fixed(self, rhs, iters: int, out=None, stream=None):
         out = self._params(out)
         mrstat_cg_fixed(self._h, rhs, out, iters, stream)
+        return out
+
+
+
+class Surrogate:
+    """Learned surrogate (mrstat_mlp): (ln T1, ln T2, B1) -> time-basis coefficients and
+    their ln T1 / ln T2 derivatives, an MLP trained on device with a Sobolev loss."""
+
+    def __init__(self, hidden: int, rank: int, norm, sobolev_weight: float = 1.0, seed: int = 0):
+        self.hidden, self.rank = int(hidden), int(rank)
+        self._h = mrstat_mlp_create(hidden, rank, norm, sobolev_weight, seed)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value is not None:
+            mrstat_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def num_params(self) -> int:
+        return mrstat_mlp_num_params(self._h)
+
+    def set_output_scale(self, scale):
+        mrstat_mlp_set_output_scale(self._h, scale)
+
+    def get_params(self):
+        return mrstat_mlp_get_params(self._h)
+
+    def set_params(self, params):
+        mrstat_mlp_set_params(self._h, params)
+
+    def train_step(self, lnT, target, lr: float, b1=None, loss=None, stream=None):
+        mrstat_mlp_train_step(self._h, lnT, b1, target, lr, loss, stream)
+
+    def loss_grad(self, lnT, target, b1=None, grad=None, stream=None) -> float:
+        return mrstat_mlp_loss_grad(self._h, lnT, b1, target, grad, stream)
+
+    def infer(self, lnT, b1=None, out=None, stream=None):
+        if out is None:
+            out = torch.empty((3, self.rank, int(lnT.shape[1])), dtype=torch.float32, device="cuda")
+        mrstat_mlp_infer(self._h, lnT, b1, out, stream)
         return out
 
 

@@ -67,6 +67,11 @@ class mrstat_gn_report(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class mrstat_mlp_config(ctypes.Structure):
+    _fields_ = [("hidden", ctypes.c_int32), ("rank", ctypes.c_int32), ("norm", ctypes.c_float * 6),
+                ("sobolev_weight", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
 KERNEL_IDS = {"bloch": 0, "ycontract": 1, "xdft": 2, "xdft_adj": 3, "jhw_dot": 4, "vector": 5}
 
 _lib = None
@@ -93,6 +98,20 @@ _SIGS = {
                                  ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_lowrank_coefficients": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_lowrank_rank": [ctypes.c_void_p],
+    "mrstat_lowrank_project_samples": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_mlp_create": [ctypes.POINTER(mrstat_mlp_config), ctypes.POINTER(ctypes.c_void_p)],
+    "mrstat_mlp_destroy": [ctypes.c_void_p],
+    "mrstat_mlp_num_params": [ctypes.c_void_p],
+    "mrstat_mlp_set_output_scale": [ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_mlp_get_params": [ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_mlp_set_params": [ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_mlp_train_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                              ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_mlp_loss_grad": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                             ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p],
+    "mrstat_mlp_infer": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                         ctypes.c_void_p],
     "mrstat_dot": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                    ctypes.c_void_p],
     "mrstat_cg_fixed": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
@@ -120,6 +139,8 @@ def load(path: str = LIB_PATH):
                 f.restype = ctypes.c_char_p
             elif name == "mrstat_gn_default_opts":
                 f.restype = None
+            elif name == "mrstat_mlp_num_params":
+                f.restype = ctypes.c_int64
             else:
                 f.restype = ctypes.c_int
         _lib = lib
@@ -353,3 +374,77 @@ def mrstat_status_string(status: int) -> str:
 
 def mrstat_last_error() -> str:
     return load().mrstat_last_error().decode()
+
+
+# ---------------------------------------------------------------------------
+# learned surrogate
+# ---------------------------------------------------------------------------
+def mrstat_lowrank_project_samples(plan, params, b1, coef, stream=None):
+    ns = int(params.shape[1])
+    R = load().mrstat_lowrank_rank(plan)
+    _check(load().mrstat_lowrank_project_samples(plan, _ptr(params, torch.float32, (2, ns), "params"),
+                                                 _ptr(b1, torch.float32, (ns,), "b1"), ns,
+                                                 _ptr(coef, torch.float32, (3, R, ns), "coef"), _stream(stream)),
+           "mrstat_lowrank_project_samples")
+
+
+def mrstat_mlp_create(hidden, rank, norm, sobolev_weight=1.0, seed=0):
+    cfg = mrstat_mlp_config(int(hidden), int(rank), (ctypes.c_float * 6)(*[float(x) for x in norm]),
+                            float(sobolev_weight), int(seed))
+    h = ctypes.c_void_p()
+    _check(load().mrstat_mlp_create(ctypes.byref(cfg), ctypes.byref(h)), "mrstat_mlp_create")
+    return h
+
+
+def mrstat_mlp_destroy(mlp):
+    _check(load().mrstat_mlp_destroy(mlp), "mrstat_mlp_destroy")
+
+
+def mrstat_mlp_num_params(mlp) -> int:
+    return int(load().mrstat_mlp_num_params(mlp))
+
+
+def mrstat_mlp_set_output_scale(mlp, scale):
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(scale, np.float32))
+    _check(load().mrstat_mlp_set_output_scale(mlp, a.ctypes.data_as(ctypes.c_void_p)), "mrstat_mlp_set_output_scale")
+
+
+def mrstat_mlp_get_params(mlp):
+    import numpy as np
+    out = np.empty(mrstat_mlp_num_params(mlp), np.float32)
+    _check(load().mrstat_mlp_get_params(mlp, out.ctypes.data_as(ctypes.c_void_p)), "mrstat_mlp_get_params")
+    return out
+
+
+def mrstat_mlp_set_params(mlp, params):
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(params, np.float32))
+    if a.size != mrstat_mlp_num_params(mlp):
+        raise ValueError("parameter vector has the wrong length")
+    _check(load().mrstat_mlp_set_params(mlp, a.ctypes.data_as(ctypes.c_void_p)), "mrstat_mlp_set_params")
+
+
+def mrstat_mlp_train_step(mlp, lnT, b1, target, lr, loss=None, stream=None):
+    B = int(lnT.shape[1])
+    _check(load().mrstat_mlp_train_step(mlp, _ptr(lnT, torch.float32, (2, B), "lnT"),
+                                        _ptr(b1, torch.float32, (B,), "b1"),
+                                        _ptr(target, torch.float32, (3, target.shape[1], B), "target"), B, float(lr),
+                                        _ptr(loss, torch.float64, (), "loss"), _stream(stream)), "mrstat_mlp_train_step")
+
+
+def mrstat_mlp_loss_grad(mlp, lnT, b1, target, grad=None, stream=None) -> float:
+    B = int(lnT.shape[1])
+    L = ctypes.c_double()
+    _check(load().mrstat_mlp_loss_grad(mlp, _ptr(lnT, torch.float32, (2, B), "lnT"), _ptr(b1, torch.float32, (B,), "b1"),
+                                       _ptr(target, torch.float32, (3, target.shape[1], B), "target"), B,
+                                       ctypes.byref(L), _ptr(grad, torch.float32, None, "grad"), _stream(stream)),
+           "mrstat_mlp_loss_grad")
+    return L.value
+
+
+def mrstat_mlp_infer(mlp, lnT, b1, coef, stream=None):
+    n = int(lnT.shape[1])
+    _check(load().mrstat_mlp_infer(mlp, _ptr(lnT, torch.float32, (2, n), "lnT"), _ptr(b1, torch.float32, (n,), "b1"), n,
+                                   _ptr(coef, torch.float32, (3, coef.shape[1], n), "coef"), _stream(stream)),
+           "mrstat_mlp_infer")

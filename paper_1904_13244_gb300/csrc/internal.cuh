@@ -9,6 +9,7 @@
 #include "../../include/mrstat.h"
 #include "tc_gemm.cuh"
 #include "lowrank.cuh"
+#include "mlp.cuh"
 
 namespace mrstat {
 

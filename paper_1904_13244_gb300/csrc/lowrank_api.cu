@@ -119,6 +119,29 @@ int mrstat_lowrank_coefficients(mrstat_plan* plan_, float* coef, void* stream) {
   return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "coefficient copy");
 }
 
+int mrstat_lowrank_project_samples(mrstat_plan* plan_, const float* params, const float* b1, int32_t ns,
+                                   float* coef, void* stream) {
+  Plan* p = reinterpret_cast<Plan*>(plan_);
+  if (p == nullptr || params == nullptr || coef == nullptr || ns < 1)
+    return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_lowrank_project_samples");
+  if (p->lr == nullptr) return fail(MRSTAT_ERR_NOT_LINEARIZED, "no time basis: call mrstat_lowrank_set_basis");
+  DeviceGuard g(p->device);
+  Plan q;  // the plan's sequence tables with ns voxels
+  q.nv = ns;
+  q.ntr = p->ntr;
+  q.cs = p->cs;
+  q.phi = p->phi;
+  q.te_ms = p->te_ms;
+  q.tr_ms = p->tr_ms;
+  q.inversion = p->inversion;
+  cudaError_t e;
+  {
+    Span sp(p, MRSTAT_K_BLOCH, as_stream(stream));
+    e = lowrank_project(q, *p->lr, params, b1, nullptr, coef, as_stream(stream));
+  }
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "sample projection");
+}
+
 int mrstat_lowrank_rank(const mrstat_plan* plan_) {
   const Plan* p = reinterpret_cast<const Plan*>(plan_);
   return (p && p->lr) ? p->lr->R : 0;

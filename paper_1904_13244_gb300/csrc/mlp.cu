@@ -1,0 +1,549 @@
+// Learned surrogate of the compressed Bloch model (K8): an MLP 3 -> H -> H -> H -> R
+// from (ln T1, ln T2, B1) to the coefficients of the echo time course in the plan's
+// time basis, with its derivatives in ln T1 and ln T2 by forward-mode tangents.
+//
+// Network (tanh hidden layers, linear output, per-coefficient output scale):
+//     u = ((ln T1 - mu1)/s1, (ln T2 - mu2)/s2, (B1 - mu3)/s3)
+//     a_l = tanh(W_l a_{l-1} + b_l),   c = scale * (W_4 a_3 + b_4)
+// A tanh layer maps a tangent t to (1 - a^2) (W t); the tangents of u along ln T1 and
+// ln T2 are (1/s1, 0, 0) and (0, 1/s2, 0).  So a batch of B samples runs as M = 3B rows
+// (values, ln T1 tangents, ln T2 tangents) through every layer: one BF16 tcgen05 GEMM
+// per layer shared by the value and both tangent streams, float32 accumulation,
+// then one element-wise kernel for the activation and the tangent scaling.
+//
+// Training minimises the Sobolev loss
+//     L = 1/B sum_b sum_r [(c - c*)^2 + lam ((dc1 - dc1*)^2 + (dc2 - dc2*)^2)] / scale_r^2
+// with a hand-written backward pass: through s_k = (1 - a^2) z_k the value
+// pre-activation receives (g_a - 2 a sum_k g_sk z_k)(1 - a^2) and each tangent
+// pre-activation g_sk (1 - a^2); weight gradients are GEMMs of the gradient rows with
+// the layer inputs over all 3B rows, input gradients GEMMs with the transposed weights.
+// Adam keeps float32 master weights and refreshes the BF16 copies (row-major and
+// transposed) used by the GEMMs.
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "mlp.cuh"
+
+namespace mrstat {
+namespace {
+
+constexpr int kLayers = 4;
+
+inline int pad8(int k) { return (k + 7) / 8 * 8; }
+
+__global__ void mlp_input_kernel(const float* __restrict__ lnT, const float* __restrict__ b1, int B, float mu1,
+                                 float s1, float mu2, float s2, float mu3, float s3, __nv_bfloat16* __restrict__ X0,
+                                 __nv_bfloat16* __restrict__ X0T, int ldt) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const float bb = b1 != nullptr ? b1[b] : 1.f;
+  const float u[3] = {(lnT[b] - mu1) / s1, (lnT[B + b] - mu2) / s2, (bb - mu3) / s3};
+  const float t1[3] = {1.f / s1, 0.f, 0.f}, t2[3] = {0.f, 1.f / s2, 0.f};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float v0 = k < 3 ? u[k] : 0.f, v1 = k < 3 ? t1[k] : 0.f, v2 = k < 3 ? t2[k] : 0.f;
+    X0[(size_t)b * 8 + k] = __float2bfloat16_rn(v0);
+    X0[(size_t)(B + b) * 8 + k] = __float2bfloat16_rn(v1);
+    X0[(size_t)(2 * B + b) * 8 + k] = __float2bfloat16_rn(v2);
+    if (X0T != nullptr && k < 3) {
+      X0T[(size_t)k * ldt + b] = __float2bfloat16_rn(v0);
+      X0T[(size_t)k * ldt + B + b] = __float2bfloat16_rn(v1);
+      X0T[(size_t)k * ldt + 2 * B + b] = __float2bfloat16_rn(v2);
+    }
+  }
+}
+
+// hidden layer: value rows a = tanh(z + bias), tangent rows (1 - a^2) z_k
+__global__ void mlp_act_kernel(const float* __restrict__ Z, const float* __restrict__ bias, int B, int H,
+                               __nv_bfloat16* __restrict__ X, int ldx, __nv_bfloat16* __restrict__ XT, int ldt) {
+  const int64_t total = (int64_t)B * H;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / H), n = (int)(e - (int64_t)b * H);
+    const float a = tanhf(Z[(size_t)b * H + n] + bias[n]);
+    const float d = 1.f - a * a;
+    const float s1 = d * Z[(size_t)(B + b) * H + n];
+    const float s2 = d * Z[(size_t)(2 * B + b) * H + n];
+    X[(size_t)b * ldx + n] = __float2bfloat16_rn(a);
+    X[(size_t)(B + b) * ldx + n] = __float2bfloat16_rn(s1);
+    X[(size_t)(2 * B + b) * ldx + n] = __float2bfloat16_rn(s2);
+    if (XT != nullptr) {
+      XT[(size_t)n * ldt + b] = __float2bfloat16_rn(a);
+      XT[(size_t)n * ldt + B + b] = __float2bfloat16_rn(s1);
+      XT[(size_t)n * ldt + 2 * B + b] = __float2bfloat16_rn(s2);
+    }
+  }
+}
+
+// output layer: predictions (c, dc1, dc2) [3][R][B] and, with targets, the loss and its
+// gradient with respect to the output pre-activations
+__global__ void mlp_output_kernel(const float* __restrict__ Z, const float* __restrict__ bias,
+                                  const float* __restrict__ scale, int B, int R, float lam,
+                                  const float* __restrict__ target, float* __restrict__ pred,
+                                  __nv_bfloat16* __restrict__ GZ, int ldg, __nv_bfloat16* __restrict__ GZT, int ldt,
+                                  double* __restrict__ loss) {
+  const int64_t total = (int64_t)B * R;
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / R), r = (int)(e - (int64_t)b * R);
+    const float sc = scale[r];
+    const float y0 = Z[(size_t)b * R + r] + bias[r];
+    const float y1 = Z[(size_t)(B + b) * R + r];
+    const float y2 = Z[(size_t)(2 * B + b) * R + r];
+    if (pred != nullptr) {
+      pred[(size_t)r * B + b] = sc * y0;
+      pred[(size_t)(R + r) * B + b] = sc * y1;
+      pred[(size_t)(2 * R + r) * B + b] = sc * y2;
+    }
+    if (target != nullptr) {
+      const float r0 = y0 - target[(size_t)r * B + b] / sc;
+      const float r1 = y1 - target[(size_t)(R + r) * B + b] / sc;
+      const float r2 = y2 - target[(size_t)(2 * R + r) * B + b] / sc;
+      acc += (double)r0 * r0 + (double)lam * ((double)r1 * r1 + (double)r2 * r2);
+      const float inv = 2.f / (float)B;
+      const float g0 = inv * r0, g1 = inv * lam * r1, g2 = inv * lam * r2;
+      GZ[(size_t)b * ldg + r] = __float2bfloat16_rn(g0);
+      GZ[(size_t)(B + b) * ldg + r] = __float2bfloat16_rn(g1);
+      GZ[(size_t)(2 * B + b) * ldg + r] = __float2bfloat16_rn(g2);
+      GZT[(size_t)r * ldt + b] = __float2bfloat16_rn(g0);
+      GZT[(size_t)r * ldt + B + b] = __float2bfloat16_rn(g1);
+      GZT[(size_t)r * ldt + 2 * B + b] = __float2bfloat16_rn(g2);
+    }
+  }
+  if (target != nullptr) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(loss, acc / (double)B);
+  }
+}
+
+// backward through a tanh layer: GX [3B][H] = dL/d(layer output) -> GZ (and transposed), db
+__global__ void mlp_backact_kernel(const float* __restrict__ GX, const float* __restrict__ Z,
+                                   const float* __restrict__ bias, int B, int H, __nv_bfloat16* __restrict__ GZ,
+                                   int ldg, __nv_bfloat16* __restrict__ GZT, int ldt, float* __restrict__ db) {
+  const int64_t total = (int64_t)B * H;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / H), n = (int)(e - (int64_t)b * H);
+    const float a = tanhf(Z[(size_t)b * H + n] + bias[n]);
+    const float d = 1.f - a * a;
+    const float z1 = Z[(size_t)(B + b) * H + n], z2 = Z[(size_t)(2 * B + b) * H + n];
+    const float ga = GX[(size_t)b * H + n], g1 = GX[(size_t)(B + b) * H + n], g2 = GX[(size_t)(2 * B + b) * H + n];
+    const float gz1 = g1 * d, gz2 = g2 * d;
+    const float gz = (ga - 2.f * a * (g1 * z1 + g2 * z2)) * d;
+    GZ[(size_t)b * ldg + n] = __float2bfloat16_rn(gz);
+    GZ[(size_t)(B + b) * ldg + n] = __float2bfloat16_rn(gz1);
+    GZ[(size_t)(2 * B + b) * ldg + n] = __float2bfloat16_rn(gz2);
+    GZT[(size_t)n * ldt + b] = __float2bfloat16_rn(gz);
+    GZT[(size_t)n * ldt + B + b] = __float2bfloat16_rn(gz1);
+    GZT[(size_t)n * ldt + 2 * B + b] = __float2bfloat16_rn(gz2);
+    atomicAdd(db + n, gz);
+  }
+}
+
+// output-layer bias gradient: sum over the value rows of the output gradient
+__global__ void mlp_out_bias_grad_kernel(const float* __restrict__ Z, const float* __restrict__ bias,
+                                         const float* __restrict__ scale, const float* __restrict__ target, int B,
+                                         int R, float* __restrict__ db) {
+  const int r = blockIdx.x;
+  float acc = 0.f;
+  for (int b = threadIdx.x; b < B; b += blockDim.x)
+    acc += 2.f / (float)B * (Z[(size_t)b * R + r] + bias[r] - target[(size_t)r * B + b] / scale[r]);
+  __shared__ float ws[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+    db[r] = s;
+  }
+}
+
+// Adam on one layer (weights [out][in] then bias [out]) and refresh of its BF16 copies
+__global__ void mlp_adam_kernel(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                                const float* __restrict__ g, int out, int in, float lr, float b1, float b2, float eps,
+                                float c1, float c2, __nv_bfloat16* __restrict__ W, int ldw,
+                                __nv_bfloat16* __restrict__ WT, int ldwt) {
+  const int total = out * in + out;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const float gi = g[e];
+    const float mi = b1 * m[e] + (1.f - b1) * gi;
+    const float vi = b2 * v[e] + (1.f - b2) * gi * gi;
+    m[e] = mi;
+    v[e] = vi;
+    const float w = theta[e] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    theta[e] = w;
+    if (e < out * in) {
+      const int o = e / in, i = e - o * in;
+      W[(size_t)o * ldw + i] = __float2bfloat16_rn(w);
+      WT[(size_t)i * ldwt + o] = __float2bfloat16_rn(w);
+    }
+  }
+}
+
+// BF16 copies of one layer's weights from the float32 master (after set_params)
+__global__ void mlp_cast_kernel(const float* __restrict__ theta, int out, int in, __nv_bfloat16* __restrict__ W,
+                                int ldw, __nv_bfloat16* __restrict__ WT, int ldwt) {
+  const int total = out * in;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int o = e / in, i = e - o * in;
+    const __nv_bfloat16 w = __float2bfloat16_rn(theta[e]);
+    W[(size_t)o * ldw + i] = w;
+    WT[(size_t)i * ldwt + o] = w;
+  }
+}
+
+int blocks_for(int64_t n, int t = 256) {
+  int64_t b = (n + t - 1) / t;
+  return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+Mlp::~Mlp() {
+  release_batch();
+  free_weights();
+  if (dev_err) cudaFree(dev_err);
+}
+
+void Mlp::free_weights() {
+  void* ptrs[] = {theta, adam_m, adam_v, grad, scale_dev};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (int l = 0; l < 4; ++l) {
+    if (Wb[l]) cudaFree(Wb[l]);
+    if (WTb[l]) cudaFree(WTb[l]);
+    Wb[l] = WTb[l] = nullptr;
+  }
+  theta = adam_m = adam_v = grad = scale_dev = nullptr;
+}
+
+void Mlp::release_batch() {
+  for (int l = 0; l < 4; ++l) {
+    void* ptrs[] = {X[l], XT[l], Z[l], GZ[l], GZT[l]};
+    for (void* q : ptrs)
+      if (q) cudaFree(q);
+    X[l] = XT[l] = GZ[l] = GZT[l] = nullptr;
+    Z[l] = nullptr;
+  }
+  if (GX) cudaFree(GX);
+  if (loss_dev) cudaFree(loss_dev);
+  GX = nullptr;
+  loss_dev = nullptr;
+  cap = 0;
+  maps_b = -1;
+}
+
+int Mlp::setup(int h, int r, uint64_t seed) {
+  H = h;
+  R = r;
+  const int dims[5] = {3, H, H, H, R};
+  np = 0;
+  for (int l = 0; l < 4; ++l) {
+    in[l] = dims[l];
+    out[l] = dims[l + 1];
+    off[l] = np;
+    np += (int64_t)out[l] * in[l] + out[l];
+  }
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t q) {
+    if (e == cudaSuccess) e = q;
+  };
+  chk(cudaMalloc(&theta, np * sizeof(float)));
+  chk(cudaMalloc(&adam_m, np * sizeof(float)));
+  chk(cudaMalloc(&adam_v, np * sizeof(float)));
+  chk(cudaMalloc(&grad, np * sizeof(float)));
+  chk(cudaMalloc(&scale_dev, R * sizeof(float)));
+  chk(cudaMalloc(&dev_err, sizeof(int)));
+  if (e == cudaSuccess) chk(cudaMemset(dev_err, 0, sizeof(int)));
+  for (int l = 0; l < 4; ++l) {
+    chk(cudaMalloc(&Wb[l], (size_t)out[l] * pad8(in[l]) * 2));
+    chk(cudaMalloc(&WTb[l], (size_t)in[l] * pad8(out[l]) * 2));
+    if (e == cudaSuccess) {
+      chk(cudaMemset(Wb[l], 0, (size_t)out[l] * pad8(in[l]) * 2));
+      chk(cudaMemset(WTb[l], 0, (size_t)in[l] * pad8(out[l]) * 2));
+      chk(make_split_operand(&opW[l], Wb[l], Wb[l], out[l], in[l], pad8(in[l]), false));
+      chk(make_split_operand(&opWT[l], WTb[l], WTb[l], in[l], out[l], pad8(out[l]), false));
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "surrogate allocation");
+  // Glorot-uniform weights, zero biases, unit output scale
+  std::vector<float> th(np, 0.f), sc(R, 1.f);
+  std::mt19937_64 rng(seed);
+  for (int l = 0; l < 4; ++l) {
+    const float lim = std::sqrt(6.f / (float)(in[l] + out[l]));
+    std::uniform_real_distribution<float> U(-lim, lim);
+    for (int64_t k = 0; k < (int64_t)out[l] * in[l]; ++k) th[off[l] + k] = U(rng);
+  }
+  chk(cudaMemcpy(scale_dev, sc.data(), R * sizeof(float), cudaMemcpyHostToDevice));
+  scale_host = sc;
+  chk(cudaMemset(adam_m, 0, np * sizeof(float)));
+  chk(cudaMemset(adam_v, 0, np * sizeof(float)));
+  if (e != cudaSuccess) return cuda_fail(e, "surrogate init");
+  return set_params(th.data(), nullptr);
+}
+
+int Mlp::set_params(const float* host, cudaStream_t st) {
+  cudaError_t e = cudaMemcpy(theta, host, np * sizeof(float), cudaMemcpyHostToDevice);
+  for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+    mlp_cast_kernel<<<blocks_for((int64_t)out[l] * in[l]), 256, 0, st>>>(theta + off[l], out[l], in[l], Wb[l],
+                                                                        pad8(in[l]), WTb[l], pad8(out[l]));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  step = 0;
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "surrogate parameters");
+}
+
+// (re)allocates the activation buffers for up to B samples and encodes the tensor maps
+int Mlp::ensure_batch(int B, bool train) {
+  if (B > cap || (train && !have_train_buffers)) {
+    release_batch();
+    const int Mc = 3 * B, Mp = pad8(Mc);
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t q) {
+      if (e == cudaSuccess) e = q;
+    };
+    for (int l = 0; l < 4; ++l) {
+      chk(cudaMalloc(&X[l], (size_t)Mc * pad8(in[l]) * 2));
+      chk(cudaMalloc(&Z[l], (size_t)Mc * out[l] * sizeof(float)));
+      if (train) {
+        chk(cudaMalloc(&XT[l], (size_t)in[l] * Mp * 2));
+        chk(cudaMalloc(&GZ[l], (size_t)Mc * pad8(out[l]) * 2));
+        chk(cudaMalloc(&GZT[l], (size_t)out[l] * Mp * 2));
+      }
+    }
+    if (train) chk(cudaMalloc(&GX, (size_t)Mc * H * sizeof(float)));
+    chk(cudaMalloc(&loss_dev, sizeof(double)));
+    for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+      chk(cudaMemset(X[l], 0, (size_t)Mc * pad8(in[l]) * 2));
+      if (train) {
+        chk(cudaMemset(XT[l], 0, (size_t)in[l] * Mp * 2));
+        chk(cudaMemset(GZ[l], 0, (size_t)Mc * pad8(out[l]) * 2));
+        chk(cudaMemset(GZT[l], 0, (size_t)out[l] * Mp * 2));
+      }
+    }
+    if (e != cudaSuccess) {
+      release_batch();
+      return cuda_fail(e, "surrogate batch buffers");
+    }
+    cap = B;
+    have_train_buffers = train;
+  }
+  if (maps_b != B || maps_train != train) {
+    const int Mc = 3 * B, Mp = pad8(3 * cap);
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+      e = make_split_operand(&opX[l], X[l], X[l], Mc, in[l], pad8(in[l]), true);
+      if (e == cudaSuccess && train) e = make_split_operand(&opXT[l], XT[l], XT[l], in[l], Mc, Mp, false);
+      if (e == cudaSuccess && train) e = make_split_operand(&opGZ[l], GZ[l], GZ[l], Mc, out[l], pad8(out[l]), true);
+      if (e == cudaSuccess && train) e = make_split_operand(&opGZT[l], GZT[l], GZT[l], out[l], Mc, Mp, true);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "surrogate tensor maps");
+    maps_b = B;
+    maps_train = train;
+  }
+  return MRSTAT_OK;
+}
+
+int Mlp::forward(const float* lnT, const float* b1, int B, bool train, cudaStream_t st) {
+  const int Mc = 3 * B;
+  const int ldt = pad8(3 * cap);
+  mlp_input_kernel<<<blocks_for(B), 256, 0, st>>>(lnT, b1, B, norm[0], norm[1], norm[2], norm[3], norm[4], norm[5],
+                                                  X[0], train ? XT[0] : nullptr, ldt);
+  cudaError_t e = cudaGetLastError();
+  for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+    e = launch_tc_gemm(opX[l], opW[l], Z[l], Mc, out[l], in[l], out[l], 1, nullptr, dev_err, st);
+    if (e != cudaSuccess || l == 3) break;
+    mlp_act_kernel<<<blocks_for((int64_t)B * out[l]), 256, 0, st>>>(Z[l], theta + off[l] + (int64_t)out[l] * in[l],
+                                                                    B, out[l], X[l + 1], pad8(in[l + 1]),
+                                                                    train ? XT[l + 1] : nullptr, ldt);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "surrogate forward");
+}
+
+int Mlp::backward(const float* target, int B, cudaStream_t st) {
+  const int Mc = 3 * B;
+  const int ldt = pad8(3 * cap);
+  cudaError_t e = cudaMemsetAsync(grad, 0, np * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(loss_dev, 0, sizeof(double), st);
+  // output layer
+  const float* b4 = theta + off[3] + (int64_t)out[3] * in[3];
+  if (e == cudaSuccess) {
+    mlp_output_kernel<<<blocks_for((int64_t)B * R), 256, 0, st>>>(Z[3], b4, scale_dev, B, R, lam, target, nullptr,
+                                                                  GZ[3], pad8(out[3]), GZT[3], ldt, loss_dev);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    mlp_out_bias_grad_kernel<<<R, 256, 0, st>>>(Z[3], b4, scale_dev, target, B, R,
+                                                grad + off[3] + (int64_t)out[3] * in[3]);
+    e = cudaGetLastError();
+  }
+  for (int l = 3; l >= 0 && e == cudaSuccess; --l) {
+    // dW_l = GZ_l^T X_l over all 3B rows
+    e = launch_tc_gemm(opGZT[l], opXT[l], grad + off[l], out[l], in[l], Mc, in[l], 1, nullptr, dev_err, st);
+    if (e != cudaSuccess || l == 0) break;
+    // dL/dX_l = GZ_l W_l, then back through layer l-1's tanh
+    e = launch_tc_gemm(opGZ[l], opWT[l], GX, Mc, in[l], out[l], in[l], 1, nullptr, dev_err, st);
+    if (e != cudaSuccess) break;
+    const int lp = l - 1;
+    mlp_backact_kernel<<<blocks_for((int64_t)B * out[lp]), 256, 0, st>>>(
+        GX, Z[lp], theta + off[lp] + (int64_t)out[lp] * in[lp], B, out[lp], GZ[lp], pad8(out[lp]), GZT[lp], ldt,
+        grad + off[lp] + (int64_t)out[lp] * in[lp]);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "surrogate backward");
+}
+
+int Mlp::adam(float lr, cudaStream_t st) {
+  ++step;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.f - std::pow(b1, (float)step), c2 = 1.f - std::pow(b2, (float)step);
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+    mlp_adam_kernel<<<blocks_for((int64_t)out[l] * in[l] + out[l]), 256, 0, st>>>(
+        theta + off[l], adam_m + off[l], adam_v + off[l], grad + off[l], out[l], in[l], lr, b1, b2, eps, c1, c2, Wb[l],
+        pad8(in[l]), WTb[l], pad8(out[l]));
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "surrogate Adam step");
+}
+
+int Mlp::predict(int B, float* pred, cudaStream_t st) {
+  const float* b4 = theta + off[3] + (int64_t)out[3] * in[3];
+  mlp_output_kernel<<<blocks_for((int64_t)B * R), 256, 0, st>>>(Z[3], b4, scale_dev, B, R, lam, nullptr, pred,
+                                                                nullptr, 0, nullptr, 0, nullptr);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "surrogate output");
+}
+
+}  // namespace mrstat
+
+// ---------------------------------------------------------------------------
+// C entry points
+// ---------------------------------------------------------------------------
+using namespace mrstat;
+
+struct mrstat_mlp : public Mlp {};
+
+extern "C" {
+
+int mrstat_mlp_create(const mrstat_mlp_config* cfg, mrstat_mlp** out) {
+  if (out == nullptr || cfg == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL config or out");
+  *out = nullptr;
+  if ((cfg->hidden != 64 && cfg->hidden != 128 && cfg->hidden != 256) || cfg->rank < 1 || cfg->rank > kMaxRank)
+    return fail(MRSTAT_ERR_INVALID_ARG, "hidden %d (64, 128 or 256) or rank %d (1..32) not supported", cfg->hidden,
+                cfg->rank);
+  for (int k = 1; k < 6; k += 2)
+    if (!(cfg->norm[k] > 0)) return fail(MRSTAT_ERR_INVALID_ARG, "normalisation scales must be positive");
+  mrstat_mlp* m = new mrstat_mlp();
+  if (cudaGetDevice(&m->device) != cudaSuccess) {
+    delete m;
+    return fail(MRSTAT_ERR_CUDA, "no CUDA device");
+  }
+  for (int k = 0; k < 6; ++k) m->norm[k] = cfg->norm[k];
+  m->lam = cfg->sobolev_weight;
+  const int s = m->setup(cfg->hidden, cfg->rank, cfg->seed);
+  if (s != MRSTAT_OK) {
+    delete m;
+    return s;
+  }
+  *out = m;
+  return MRSTAT_OK;
+}
+
+int mrstat_mlp_destroy(mrstat_mlp* m) {
+  if (m == nullptr) return MRSTAT_OK;
+  DeviceGuard g(m->device);
+  cudaDeviceSynchronize();
+  delete m;
+  return MRSTAT_OK;
+}
+
+int64_t mrstat_mlp_num_params(const mrstat_mlp* m) { return m ? m->np : 0; }
+
+int mrstat_mlp_set_output_scale(mrstat_mlp* m, const float* scale) {
+  if (m == nullptr || scale == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL argument");
+  for (int r = 0; r < m->R; ++r)
+    if (!(scale[r] > 0)) return fail(MRSTAT_ERR_INVALID_ARG, "output scales must be positive");
+  DeviceGuard g(m->device);
+  m->scale_host.assign(scale, scale + m->R);
+  cudaError_t e = cudaMemcpy(m->scale_dev, scale, m->R * sizeof(float), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "output scale");
+}
+
+int mrstat_mlp_get_params(mrstat_mlp* m, float* host) {
+  if (m == nullptr || host == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(m->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(host, m->theta, m->np * sizeof(float), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "get parameters");
+}
+
+int mrstat_mlp_set_params(mrstat_mlp* m, const float* host) {
+  if (m == nullptr || host == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(m->device);
+  cudaDeviceSynchronize();
+  return m->set_params(host, nullptr);
+}
+
+int mrstat_mlp_infer(mrstat_mlp* m, const float* lnT, const float* b1, int32_t n, float* coef, void* stream) {
+  if (m == nullptr || lnT == nullptr || coef == nullptr || n < 1)
+    return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_mlp_infer");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int s = m->ensure_batch(n, false);
+  if (s == MRSTAT_OK) s = m->forward(lnT, b1, n, false, st);
+  if (s == MRSTAT_OK) s = m->predict(n, coef, st);
+  return s;
+}
+
+int mrstat_mlp_train_step(mrstat_mlp* m, const float* lnT, const float* b1, const float* target, int32_t B, float lr,
+                          double* loss_out, void* stream) {
+  if (m == nullptr || lnT == nullptr || target == nullptr || B < 1 || !(lr >= 0))
+    return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_mlp_train_step");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int s = m->ensure_batch(B, true);
+  if (s == MRSTAT_OK) s = m->forward(lnT, b1, B, true, st);
+  if (s == MRSTAT_OK) s = m->backward(target, B, st);
+  if (s == MRSTAT_OK && lr > 0) s = m->adam(lr, st);
+  if (s == MRSTAT_OK && loss_out != nullptr) {
+    cudaError_t e = cudaMemcpyAsync(loss_out, m->loss_dev, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) s = cuda_fail(e, "loss copy");
+  }
+  return s;
+}
+
+int mrstat_mlp_loss_grad(mrstat_mlp* m, const float* lnT, const float* b1, const float* target, int32_t B,
+                         double* loss_host, float* grad, void* stream) {
+  if (m == nullptr || lnT == nullptr || target == nullptr || B < 1)
+    return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_mlp_loss_grad");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int s = m->ensure_batch(B, true);
+  if (s == MRSTAT_OK) s = m->forward(lnT, b1, B, true, st);
+  if (s == MRSTAT_OK) s = m->backward(target, B, st);
+  if (s != MRSTAT_OK) return s;
+  cudaError_t e = cudaSuccess;
+  if (grad) e = cudaMemcpyAsync(grad, m->grad, m->np * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && loss_host) e = cudaMemcpyAsync(loss_host, m->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, m->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "surrogate gradient");
+  if (herr) {
+    cudaMemset(m->dev_err, 0, sizeof(int));
+    return fail(MRSTAT_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on its pipeline barriers");
+  }
+  return MRSTAT_OK;
+}
+
+}  // extern "C"
