@@ -299,6 +299,30 @@ int mrstat_dot(mrstat_plan* plan, const float* a, const float* b, int64_t n,
                double* out, void* stream);
 
 /*
+ * Allocation-free variant of mrstat_dot: *out = sum_i a[i] * b[i] with the same
+ * arithmetic (float32 per-thread partials over 16 elements, float64 from the warp level
+ * up, deterministic order), needing no plan.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc, such as code running while
+ * another framework owns the device allocator, inside a memory-pool budget that must not
+ * grow, or in a process that forbids allocation after start-up.  It allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library routine): its scratch is a file-scope
+ * device array of 4128 doubles (33 KB) holding one partial per block of 4096 elements
+ * and a ticket counter.
+ *   a, b: device float [n]; out: device double; stream: cudaStream_t or NULL.
+ *   n: 0 .. 16,777,216 (4096 blocks x 4096 elements); larger n is rejected with
+ *   INVALID_ARG (use mrstat_dot for those).
+ * The first call on each device looks up the array's address on that device
+ * (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture.  Every call on a device shares the one array, which keeps the last
+ * call's contents; each call clears the ticket before its kernel.  Calls that overlap on
+ * the GPU (concurrent streams, or several threads) race on the array and give wrong
+ * results: serialise them.
+ * Errors: INVALID_ARG (null pointer, n < 0, n above the limit), UNSUPPORTED (device index
+ * >= 64), CUDA.
+ */
+int mrstat_dot_static(const float* a, const float* b, int64_t n, double* out, void* stream);
+
+/*
  * Fixed-count conjugate gradients on Re(J_s^H J_s) x = rhs at the cached
  * linearisation (the inner CG of Algorithm 6 without trust-region exits): x_0 = 0,
  * then exactly `iters` iterations, each one J^H J v product (mrstat_jvp followed by

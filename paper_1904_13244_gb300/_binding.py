@@ -112,6 +112,7 @@ _SIGS = {
                              ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_mlp_infer": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                          ctypes.c_void_p],
+    "mrstat_dot_static": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_dot": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                    ctypes.c_void_p],
     "mrstat_cg_fixed": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
@@ -448,3 +449,11 @@ def mrstat_mlp_infer(mlp, lnT, b1, coef, stream=None):
     _check(load().mrstat_mlp_infer(mlp, _ptr(lnT, torch.float32, (2, n), "lnT"), _ptr(b1, torch.float32, (n,), "b1"), n,
                                    _ptr(coef, torch.float32, (3, coef.shape[1], n), "coef"), _stream(stream)),
            "mrstat_mlp_infer")
+
+
+def mrstat_dot_static(a, b, out, stream=None):
+    """Allocation-free inner product (no plan); out: cuda float64 scalar tensor."""
+    n = int(a.numel())
+    _check(load().mrstat_dot_static(_ptr(a, torch.float32, (n,), "a"), _ptr(b, torch.float32, (n,), "b"), n,
+                                    _ptr(out, torch.float64, None, "out"), _stream(stream)), "mrstat_dot_static")
+    return out
