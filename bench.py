@@ -7,9 +7,12 @@ number of CG iterations on Re(J^H J) x = b, each one J^H J v product plus the CG
 inner products.  value = CG products per second summed over ranks, for the form
 selected with --form:
 
-* lowrank (default): the compressed model in a rank-32 time basis; the linearisation
-  projects the exact Bloch recursion onto the basis, every J^H J v is the per-ky Gram
-  product of 4 split-BF16 tcgen05 DFT GEMMs;
+* surrogate (default): the compressed model in a rank-32 time basis whose coefficients
+  come from the learned surrogate (one MLP inference on the tensor cores per step);
+  every J^H J v is the per-ky Gram product between two split-BF16 tcgen05
+  phase-encode DFT GEMMs (the readout DFT pair cancels: nkx = nx);
+* lowrank: the same products, the linearisation projects the exact Bloch recursion
+  onto the basis;
 * plain: exact FP32 model; the linearisation caches m_y and its tangents
   (3 x 1120 x 50176 float32 = 674 MB, more than the 126 MB L2) and every J^H J v
   streams them twice (J.v, then Re(J^H w)) with an FP32 readout DFT between;
@@ -17,8 +20,10 @@ selected with --form:
 
 The run also times the plain form on the same inputs (key "plain") and runs the full
 reconstruction (15 Gauss-Newton x 30 CG from T1 = 1000 ms, T2 = 100 ms with the CGLS
-rho initialisation and mask, SNR 30 data) with the exact and the low-rank CG matrix
-(key "recon": seconds and T1/T2/rho NRMSE against the ground truth).
+rho initialisation and mask, SNR 30 data) with the exact CG matrix, the low-rank CG
+matrix, and 10 surrogate iterations followed by 5 exact ones (key "recon": seconds
+and T1/T2/rho NRMSE against the ground truth, and whether the fast runs reach the
+plain run's NRMSE: |NRMSE_fast - NRMSE_plain| <= max(0.1 NRMSE_plain, 1e-3)).
 Inputs are the seeded brain-like phantom and flip train of ``synth``.
 
 Multi-GPU: N independent replicas (one per rank), weak scaling, no collective on
@@ -64,7 +69,9 @@ def parse_args():
     ap.add_argument("--cg-iters", type=int, default=30)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="lowrank", choices=["lowrank", "plain", "split"])
+    ap.add_argument("--form", default="surrogate", choices=["surrogate", "lowrank", "plain", "split"])
+    ap.add_argument("--hidden", type=int, default=256)
+    ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--rank", type=int, default=32)
     ap.add_argument("--no-recon", action="store_true")
     return ap.parse_args()
@@ -100,6 +107,18 @@ def oracle_sample(workload: str, ntr_sample: int, products: int, seed: int = 0, 
         v = v / max(np.linalg.norm(v), 1e-30)
     t2 = time.perf_counter()
     return t1 - t0, (t2 - t1) / max(products, 1), scale
+
+
+def max_over_ranks(x: float, dist=None) -> float:
+    """Maximum of a per-rank float over the process group (the timing rule for N > 1);
+    the tensor lives on the current CUDA device under NCCL, on the CPU under gloo."""
+    if dist is None or not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def cpu_cores():
@@ -145,6 +164,40 @@ def run_reference(args, rank: int):
                              "sample": sample},
             "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# learned surrogate: trained on device on exact projections of the Bloch model
+# ---------------------------------------------------------------------------
+def train_surrogate(mr, torch, plan, rank, hidden, steps, n_train=262144, batch=4096, seed=0):
+    """MLP fitted to the plan's projected Bloch model: T1 log-U(100, 6000) ms, T2 log-U(10,
+    3000) ms, B1 = 1; targets from mrstat_lowrank_project_samples.  Returns the network and
+    a summary (training seconds, held-out relative errors of c, dc/dlnT1, dc/dlnT2)."""
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    rng = np.random.default_rng(seed + 77)
+
+    def draw(n):
+        return torch.tensor(np.stack([rng.uniform(np.log(100), np.log(6000), n),
+                                      rng.uniform(np.log(10), np.log(3000), n)]), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x = draw(n_train)
+    tgt = plan.lowrank_project_samples(x)
+    scale = tgt[0].abs().amax(dim=1).clamp_min(1e-6).cpu().numpy()
+    net = mr.Surrogate(hidden, rank, (np.log(1000.0), 1.0, np.log(100.0), 1.2, 1.0, 0.2), 0.5, seed=seed)
+    net.set_output_scale(scale)
+    for it in range(steps):
+        idx = torch.randint(0, n_train, (batch,), device="cuda", generator=gen)
+        lr = 2e-3 if it < steps * 0.6 else (6e-4 if it < steps * 0.85 else 2e-4)
+        net.train_step(x[:, idx].contiguous(), tgt[:, :, idx].contiguous(), lr)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    xt = draw(16384)
+    tt = plan.lowrank_project_samples(xt)
+    pred = net.infer(xt)
+    err = [float(torch.linalg.vector_norm(pred[k] - tt[k]) / torch.linalg.vector_norm(tt[k])) for k in range(3)]
+    return net, {"hidden": hidden, "train_seconds": secs, "train_samples": n_train, "steps": steps,
+                 "batch": batch, "holdout_relerr": {"c": err[0], "dc_dlnT1": err[1], "dc_dlnT2": err[2]}}
 
 
 # ---------------------------------------------------------------------------
@@ -247,17 +300,25 @@ def main():
     x_dev = torch.empty_like(rhs_dev)
     stream = torch.cuda.current_stream()
     basis = None
-    if args.form == "lowrank" or not args.no_recon:
+    net = None
+    surrogate_info = None
+    if args.form in ("lowrank", "surrogate") or not args.no_recon:
         rng = np.random.default_rng(1000)
         train = torch.tensor(np.stack([rng.uniform(np.log(100), np.log(6000), 4096),
                                        rng.uniform(np.log(10), np.log(3000), 4096)]), dtype=torch.float32,
                              device="cuda")
         basis, _ = plan.lowrank_basis(train, args.rank)
         plan.lowrank_set_basis(basis)
+    if args.form == "surrogate" or not args.no_recon:
+        net, surrogate_info = train_surrogate(mr, torch, plan, args.rank, args.hidden, args.train_steps)
+    coef_dev = torch.empty((3, args.rank, seq.nv), dtype=torch.float32, device="cuda")
 
     def make_step(pl, form):
         def step():
-            if form == "lowrank":
+            if form == "surrogate":
+                net.infer(a_dev[:2], out=coef_dev)
+                pl.lowrank_linearize(a_dev, coef=coef_dev)
+            elif form == "lowrank":
                 pl.lowrank_linearize(a_dev)
             else:
                 pl.linearize(a_dev)
@@ -283,11 +344,8 @@ def main():
         torch.cuda.synchronize()
         st = pl.profile_stop()
         clk = sampler.stop() if sampler else None
-        t = e0.elapsed_time(e1) / max(nsteps, 1)
+        t = max_over_ranks(e0.elapsed_time(e1) / max(nsteps, 1), dist if world > 1 else None)
         if world > 1:
-            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
             dist.barrier()
         return t, st, clk
 
@@ -323,11 +381,7 @@ def main():
             step()
             x_host.copy_(x_dev, non_blocking=True)
             torch.cuda.current_stream().synchronize()
-        dt = (time.perf_counter() - t0) / k
-        if world > 1:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks((time.perf_counter() - t0) / k, dist if world > 1 else None)
         e2e = {"value": world * iters / dt, "unit": "products/s",
                "h2d_bytes_per_step": int(a_host.numel() * 4 + rhs_host.numel() * 4),
                "d2h_bytes_per_step": int(x_host.numel() * 4)}
@@ -339,41 +393,73 @@ def main():
     d_bytes = 3 * ntr_pad * nv * 4
     per_step_ms = {k: stats[k]["ms"] / max(args.steps, 1) for k in all_kernels}
     per_launch = {k: stats[k]["ms"] / max(stats[k]["timed"], 1) for k in all_kernels}
-    if args.form == "lowrank":
-        # tensor kernels: 3 split products of the real-embedded DFT GEMMs; each class launches
-        # two GEMMs per product (readout stage and phase-encode stage): the mean per launch
+    lowrank_like = args.form in ("lowrank", "surrogate")
+    full_readout = nkx == nx
+    if lowrank_like and full_readout:
+        # per J^H J v: one phase-encode DFT GEMM in each of xdft / xdft_adj, three split
+        # BF16 products of the real-embedded [R nx x 2ny] x [2ny x 2ny] matrices
+        gemm_flops = 3 * 2 * (R * nx) * (2 * ny) * (2 * ny)
+        op_bytes = R * nx * 2 * ny * 2 * 2  # one BF16 hi + lo operand [R nx][2 ny]
+        work = {"xdft": (gemm_flops, "tensor"), "xdft_adj": (gemm_flops, "tensor"),
+                # prep: v, rho, mask and 3 R coefficient rows in, the split operand out
+                "ycontract": (nv * (16 + 8 + 4) + 3 * R * nv * 4 + op_bytes, "hbm"),
+                # final: the adjoint DFT output, coefficients, rho, mask in, g out
+                "jhw_dot": (R * nx * 2 * ny * 4 + 3 * R * nv * 4 + nv * (8 + 4) + nv * 16, "hbm")}
+    elif lowrank_like:
         gemm_flops = 3 * 2 * (R * ny * (2 * nkx) * (2 * nx) + R * nkx * (2 * ny) * (2 * ny))
-        work = {"xdft": (gemm_flops / 2, "tensor"), "xdft_adj": (gemm_flops / 2, "tensor"),
-                "bloch": (nv * 16 + 3 * R * nv * 4, "hbm")}
+        work = {"xdft": (gemm_flops / 2, "tensor"), "xdft_adj": (gemm_flops / 2, "tensor")}
     else:
         work = {"jhw_dot": (d_bytes + ntr_pad * nx * 8 + nv * (8 + 4 + 16) + ntr_pad * 4, "hbm"),
                 "ycontract": (d_bytes + nv * 24 + ntr * nx * 8 + ntr_pad * 4, "hbm"),
                 "bloch": (d_bytes + nv * 16, "hbm")}
-    cand = {k: per_step_ms[k] for k in work if stats[k]["timed"] > 0}
-    dom = max(cand, key=cand.get)
-    amount, bound = work[dom]
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    if bound == "hbm":
-        peak, peak_kind = measured_peak_hbm()
-        achieved = amount / (per_launch[dom] / 1e3) / 1e9
-        unit = "GB/s"
-    else:
-        # a kernel timed inside a long step: the sustained BF16 figure
-        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-        peak_kind = "measured sustained" if peaks else "fallback"
-        achieved = amount / (per_launch[dom] / 1e3) / 1e12
-        unit = "TFLOP/s"
+
+    def roof(k):
+        amount, bound = work[k]
+        if bound == "hbm":
+            peak, peak_kind = measured_peak_hbm()
+            achieved = amount / (per_launch[k] / 1e3) / 1e9
+            unit = "GB/s"
+        else:
+            # a kernel timed inside a long step: the sustained BF16 figure
+            peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+            peak_kind = "measured sustained" if peaks else "fallback"
+            achieved = amount / (per_launch[k] / 1e3) / 1e12
+            unit = "TFLOP/s"
+        return {"kernel": k, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "peak_source": peak_kind, "algorithmic_per_launch": amount,
+                "launch_ms": per_launch[k]}
+
+    cand = {k: per_step_ms[k] for k in work if stats[k]["timed"] > 0}
+    if args.form == "surrogate":
+        # the MLP inference is not one of the plan's kernel classes: time it on its own
+        for _ in range(3):
+            net.infer(a_dev[:2], out=coef_dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            net.infer(a_dev[:2], out=coef_dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        H = args.hidden
+        # value + two tangent rows per voxel through 3 -> H -> H -> H -> R
+        work["mlp_infer"] = (2 * 3 * nv * (3 * H + 2 * H * H + H * R), "tensor")
+        per_launch["mlp_infer"] = e0.elapsed_time(e1) / 20
+        per_step_ms["mlp_infer"] = per_launch["mlp_infer"]
+        cand["mlp_infer"] = per_step_ms["mlp_infer"]
+    dom = max(cand, key=cand.get)
     src = {"jhw_dot": "encode.cu", "ycontract": "encode.cu", "bloch": "bloch.cu", "xdft": "tc_gemm.cu",
-           "xdft_adj": "tc_gemm.cu"}
+           "xdft_adj": "tc_gemm.cu", "mlp_infer": "mlp.cu"}
+    if lowrank_like:
+        src.update({"jhw_dot": "lowrank.cu", "ycontract": "lowrank.cu"})
     h = source_hash(os.path.join(ROOT, "paper_1904_13244_gb300", "csrc", src[dom]))
-    traffic = NCU_TRAFFIC.get((dom, h))
-    roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                "algorithmic_per_launch": amount, "launch_ms": per_launch[dom]}
-    if args.form != "lowrank":
-        roofline["other_kernels"] = {k: {"launch_ms": per_launch[k], "GB/s": work[k][0] / (per_launch[k] / 1e3) / 1e9
-                                         if per_launch[k] > 0 else None} for k in work if k != dom}
+    roofline = roof(dom)
+    roofline["traffic"] = NCU_TRAFFIC.get((dom, h))
+    roofline["other_kernels"] = {k: {kk: vv for kk, vv in roof(k).items() if kk in ("achieved", "unit", "frac",
+                                                                                      "launch_ms")}
+                                 for k in cand if k != dom}
 
     # full reconstructions (Algorithm 6, 15 x 30) with the exact and the low-rank CG matrix
     recon = None
@@ -386,13 +472,16 @@ def main():
         noise = noise.to("cuda").to(torch.complex64)
         d = s_true + noise * (torch.linalg.vector_norm(s_true) / (30.0 * torch.linalg.vector_norm(noise)))
         sup = torch.tensor(ph.support.ravel(), device="cuda")
-        for name, hess in (("plain", 0), ("lowrank", 1)):
+        runs = [("plain", dict(hessian=0)), ("lowrank", dict(hessian=1))]
+        if net is not None:
+            runs.append(("surrogate", dict(hessian=1, surrogate_iters=10, surrogate=net)))
+        for name, kw in runs:
             a = torch.zeros((4, seq.nv), dtype=torch.float32, device="cuda")
             mask = torch.zeros(seq.nv, dtype=torch.uint8, device="cuda")
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             rep = plan.gn_solve(d, a, mask=mask, outer_iters=15, inner_iters=30, rho_init_iters=50,
-                                mask_threshold=0.1, hessian=hess)
+                                mask_threshold=0.1, **kw)
             torch.cuda.synchronize()
             secs = time.perf_counter() - t0
             m = (mask.bool() & sup)
@@ -404,7 +493,13 @@ def main():
                                               / torch.linalg.vector_norm(torch.complex(truth[2], truth[3])[m])),
                            "f_final": rep["f_final"], "accepted": sum(rep["accepted"]),
                            "cg_steps": sum(rep["cg_steps"]), "mask_voxels": rep["mask_voxels"]}
-        recon["settings"] = "15 GN x 30 CG, SNR 30, rho by 50 CGLS steps at T1 1000 ms / T2 100 ms, mask 0.1"
+        for name in ("lowrank", "surrogate"):
+            if name in recon:
+                recon[name]["equal_nrmse"] = all(
+                    abs(recon[name][k] - recon["plain"][k]) <= max(0.1 * recon["plain"][k], 1e-3)
+                    for k in ("nrmse_t1", "nrmse_t2"))
+        recon["settings"] = ("15 GN x 30 CG, SNR 30, rho by 50 CGLS steps at T1 1000 ms / T2 100 ms, mask 0.1; "
+                             "surrogate: 10 surrogate + 5 exact iterations, low-rank CG matrix")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -417,18 +512,23 @@ def main():
                          f"{iters} products; elementwise NumPy single-threaded, BLAS on all cores"}
 
     launches = int(sum(stats[k]["launches"] for k in stats))
+    if args.form == "surrogate":
+        # MLP inference per step: input, 4 GEMMs, 3 activations, output (outside the plan's counters)
+        launches += 9 * args.steps
     if rank == 0:
-        form_desc = {"lowrank": f"low-rank form (rank {R} time basis, split-BF16 tcgen05 DFTs, per-ky Gram J^H J v)",
+        form_desc = {"surrogate": f"learned surrogate + low-rank form (rank {R} time basis, MLP {args.hidden}x3 "
+                                  f"coefficients, split-BF16 tcgen05 DFTs, per-ky Gram J^H J v)",
+                     "lowrank": f"low-rank form (rank {R} time basis, split-BF16 tcgen05 DFTs, per-ky Gram J^H J v)",
                      "plain": "plain FP32 form (cached time courses, FP32 readout DFT)",
                      "split": "split-BF16 form (cached time courses, tcgen05 readout DFT)"}[args.form]
-        l2 = ("inputs larger than L2 (cached time courses %.0f MB)" % (d_bytes / 1e6) if args.form != "lowrank"
+        l2 = ("inputs larger than L2 (cached time courses %.0f MB)" % (d_bytes / 1e6) if not lowrank_like
               else "L2 not flushed: the low-rank operands (~%.0f MB) are L2-resident by design; the "
                    "linearisation streams the parameters and writes the coefficients each step"
               % ((R * ny * 2 * nx * 2 * 2 + R * nkx * 2 * ny * 4 * 3) / 1e6))
         line = {"metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16x3+f32" if args.form == "lowrank" else "f32",
+                "dtype": "bf16x3+f32" if lowrank_like else "f32",
                 "data": "synthetic",
                 "config": {"workload": f"{args.workload}: {seq.nx}x{seq.ny} grid, {seq.ntr} TRs, "
                                        f"{seq.nkx} readout samples, " + form_desc,
@@ -437,9 +537,11 @@ def main():
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu, "plain": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
-                "recon": recon,
+                "recon": recon, "surrogate": surrogate_info,
                 "kernel_ms_per_step": {k: v for k, v in per_step_ms.items()}}
         print(json.dumps(line), flush=True)
+    if net is not None:
+        net.close()
     plan.close()
     if world > 1:
         dist.destroy_process_group()

@@ -351,6 +351,14 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
  * T1 = t1_init_ms, T2 = t2_init_ms (Methods), and with mask_threshold > 0 the mask
  * |rho| > mask_threshold * max |rho| is drawn and written to `mask`.
  *
+ * With opts->surrogate_iters = k > 0 the first k outer iterations replace the Bloch
+ * simulation by the learned surrogate (mrstat_mlp_*), the remedy for the cost of the
+ * derivative computations the paper names (Discussion): the coefficients of every
+ * voxel's time course and tangents in the plan's basis come from one MLP inference, and
+ * objective, gradient and CG products are those of that low-rank model.  At iteration k
+ * the solver re-evaluates the objective with the exact model and continues with it, so
+ * the result is the exact model's minimiser; the report's f[] shows the switch.
+ *
  * With opts->hessian = 1 the CG uses the low-rank Gauss-Newton matrix of the plan's
  * time basis (the compressed model's Re(J^H J), recomputed at every accepted point by
  * projecting the exact recursion onto the basis), while gradient, objective and the
@@ -394,6 +402,12 @@ typedef struct mrstat_gn_opts {
   int32_t hessian;             /* 0: exact Re(J^H J); 1: low-rank per-ky Gram product of
                                   the plan's time basis (mrstat_lowrank_set_basis) for the
                                   CG, with the exact gradient and objective              */
+  int32_t surrogate_iters;     /* 0..outer_iters: the first surrogate_iters outer
+                                  iterations run on the learned surrogate's low-rank
+                                  model (objective, gradient, CG products and the
+                                  trust-region ratio); the rest on the exact model       */
+  const mrstat_mlp* surrogate; /* required when surrogate_iters > 0; its rank must equal
+                                  the plan's basis rank                                  */
 } mrstat_gn_opts;
 
 typedef struct mrstat_gn_report {

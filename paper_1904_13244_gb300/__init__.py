@@ -201,6 +201,10 @@ class Surrogate:
         self.close()
 
     @property
+    def handle(self):
+        return self._h
+
+    @property
     def num_params(self) -> int:
         return mrstat_mlp_num_params(self._h)
 

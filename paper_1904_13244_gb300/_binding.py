@@ -55,7 +55,8 @@ class mrstat_gn_opts(ctypes.Structure):
                 ("t2_min_ms", ctypes.c_double), ("t2_max_ms", ctypes.c_double),
                 ("rho_init_iters", ctypes.c_int32), ("t1_init_ms", ctypes.c_double),
                 ("t2_init_ms", ctypes.c_double), ("mask_threshold", ctypes.c_double),
-                ("hessian", ctypes.c_int32)]
+                ("hessian", ctypes.c_int32), ("surrogate_iters", ctypes.c_int32),
+                ("surrogate", ctypes.c_void_p)]
 
 
 class mrstat_gn_report(ctypes.Structure):
@@ -336,6 +337,10 @@ def mrstat_gn_default_opts(**overrides) -> mrstat_gn_opts:
     for k, v in overrides.items():
         if not hasattr(o, k):
             raise AttributeError(f"unknown Gauss-Newton option {k}")
+        if k == "surrogate" and v is not None and not isinstance(v, (int, ctypes.c_void_p)):
+            v = v.handle  # a Surrogate object
+        if isinstance(v, ctypes.c_void_p):
+            v = v.value
         setattr(o, k, v)
     return o
 

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256)
 jhw_dot_kernel(const float4* __restrict__ D, const float2* __restrict__ wt,
                const int* __restrict__ kyi, const float2* __restrict__ roots_g,
                const float2* __restrict__ rho, const float* __restrict__ maskf, int nx, int ny,
-               int nv, int nq, float inv_ny, float* __restrict__ g, const int* __restrict__ gate) {
+               int nv, int nq, float inv_ny, float scale, float* __restrict__ g, const int* __restrict__ gate) {
   if (gate != nullptr && *gate == 0) return;
   extern __shared__ float2 smem[];
   float2* roots = smem;                                  // [ny]
@@ -224,7 +224,7 @@ jhw_dot_kernel(const float4* __restrict__ D, const float2* __restrict__ wt,
       float a = 0.f;
 #pragma unroll
       for (int w = 0; w < 8; ++w) a += red[(w * 6 + c) * 32 + tx];
-      s[c] = a;
+      s[c] = a * scale;
     }
     const float2 r = rho[j];
     const float m = maskf[j];
@@ -296,15 +296,15 @@ cudaError_t launch_ycontract(const Plan& p, const float4* D, int nch, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_jhw_dot(const Plan& p, float* g, cudaStream_t st) {
+cudaError_t launch_jhw_dot(const Plan& p, float* g, cudaStream_t st, const float2* wt, float scale) {
   if (p.nv == 0) return cudaSuccess;
   dim3 block(32, 8);
   dim3 grid((p.nv + 31) / 32);
   size_t sm = sizeof(float2) * p.ny + sizeof(float) * 8 * 6 * 32;
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(jhw_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  jhw_dot_kernel<<<grid, block, sm, st>>>(p.D, p.wt, p.kyi, p.roots, p.rho, p.maskf, p.nx, p.ny,
-                                          p.nv, p.nq, 1.0f / (float)p.ny, g, p.gate);
+  jhw_dot_kernel<<<grid, block, sm, st>>>(p.D, wt != nullptr ? wt : p.wt, p.kyi, p.roots, p.rho, p.maskf, p.nx,
+                                          p.ny, p.nv, p.nq, 1.0f / (float)p.ny, scale, g, p.gate);
   return cudaGetLastError();
 }
 

@@ -417,6 +417,16 @@ __global__ void set_rho_rows_kernel(const float* __restrict__ x, int nv, float* 
   }
 }
 
+// v = (0, 0, Re rho, Im rho): J_s v is the signal itself (s is linear in rho)
+__global__ void rho_direction_kernel(const float* __restrict__ alpha, int nv, float* __restrict__ v) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+    v[j] = 0.f;
+    v[nv + j] = 0.f;
+    v[2 * (size_t)nv + j] = alpha[2 * (size_t)nv + j];
+    v[3 * (size_t)nv + j] = alpha[3 * (size_t)nv + j];
+  }
+}
+
 __global__ void count_mask_kernel(const uint8_t* __restrict__ mask, int nv, int* count) {
   int c = 0;
   GRID_STRIDE(j, nv) c += mask[j] != 0;
@@ -610,6 +620,18 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   if (o->hessian != 0 && o->hessian != 1) return fail(MRSTAT_ERR_INVALID_ARG, "hessian must be 0 or 1");
   if (o->hessian == 1 && p->lr == nullptr)
     return fail(MRSTAT_ERR_NOT_LINEARIZED, "the low-rank Hessian needs mrstat_lowrank_set_basis first");
+  if (o->surrogate_iters < 0 || o->surrogate_iters > o->outer_iters)
+    return fail(MRSTAT_ERR_INVALID_ARG, "surrogate_iters must lie in 0..outer_iters");
+  Mlp* net = nullptr;
+  if (o->surrogate_iters > 0) {
+    if (o->surrogate == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "surrogate_iters > 0 needs a surrogate");
+    if (p->lr == nullptr)
+      return fail(MRSTAT_ERR_NOT_LINEARIZED, "the surrogate phase needs mrstat_lowrank_set_basis first");
+    net = reinterpret_cast<Mlp*>(const_cast<mrstat_mlp*>(o->surrogate));
+    if (net->R != p->lr->R)
+      return fail(MRSTAT_ERR_INVALID_ARG, "surrogate rank %d differs from the basis rank %d", net->R, p->lr->R);
+    if (net->device != p->device) return fail(MRSTAT_ERR_INVALID_ARG, "surrogate and plan live on different devices");
+  }
   DeviceGuard guard(p->device);
   const auto t_start = std::chrono::steady_clock::now();
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -661,10 +683,37 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   }
   if (e != cudaSuccess) return cuda_fail(e, "mask");
 
+  // -- the surrogate's low-rank model: coefficients from one MLP inference --
+  auto sur_linearize = [&](const float* a, float2* rho_out, float* coef_out) -> int {
+    cudaError_t r;
+    {
+      Span sp(p, MRSTAT_K_VECTOR, st);
+      r = launch_prep_linearize(*p, a, p->gn_mask, rho_out, st);
+    }
+    if (r != cudaSuccess) return cuda_fail(r, "prep_linearize launch");
+    Span sp(p, MRSTAT_K_BLOCH, st);
+    return mlp_infer(net, a, b1, nv, coef_out, st);
+  };
+  auto sur_signal = [&](const float* a, float2* s_out) -> int {
+    cudaError_t r = S.vec([&] { rho_direction_kernel<<<g, kT, 0, st>>>(a, nv, p->gn_q); });
+    if (r != cudaSuccess) return cuda_fail(r, "rho direction");
+    return lowrank_jvp(p, p->gn_q, s_out, st);
+  };
+  auto exact_point = [&]() -> int {
+    int r = do_linearize(p, p->gn_alpha, b1, p->gn_mask, p->D, p->rho, st);
+    if (r == MRSTAT_OK) r = do_signal(p, p->D, p->rho, p->gn_s, st);
+    if (r == MRSTAT_OK) r = S.residual(p->gn_s, d, p->gn_r, p->gn_sc + S_F);
+    return r;
+  };
+
   // -- current point --
-  status = do_linearize(p, p->gn_alpha, b1, p->gn_mask, p->D, p->rho, st);
-  if (status == MRSTAT_OK) status = do_signal(p, p->D, p->rho, p->gn_s, st);
-  if (status == MRSTAT_OK) status = S.residual(p->gn_s, d, p->gn_r, p->gn_sc + S_F);
+  if (o->surrogate_iters > 0) {
+    status = sur_linearize(p->gn_alpha, p->rho, p->lr->coef);
+    if (status == MRSTAT_OK) status = sur_signal(p->gn_alpha, p->gn_s);
+    if (status == MRSTAT_OK) status = S.residual(p->gn_s, d, p->gn_r, p->gn_sc + S_F);
+  } else {
+    status = exact_point();
+  }
   if (status != MRSTAT_OK) return status;
   e = S.vec([&] {
     masked_norm_kernel<<<g, kT, 0, st>>>(p->gn_alpha, p->gn_mask, nv, p->red, p->ticket, p->gn_sc + S_ANORM2);
@@ -695,10 +744,27 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   const float lt2a = (float)std::log(o->t2_min_ms), lt2b = (float)std::log(o->t2_max_ms);
 
   for (int k = 0; k < o->outer_iters; ++k) {
+    const bool sur = k < o->surrogate_iters;
+    if (k > 0 && k == o->surrogate_iters) {
+      // leave the surrogate: exact objective at the current point from here on
+      p->lr->active = false;
+      status = exact_point();
+      if (status == MRSTAT_OK) status = fetch();
+      if (status != MRSTAT_OK) return status;
+      f = hs[S_F];
+      coef_stale = true;
+    }
     // gradient g = Re(J_s^H (s - d)) at the current point
-    status = do_jhw(p, p->gn_r, p->gn_g, st);
+    if (sur) {
+      p->lr->active = true;
+      status = lowrank_jhw(p, p->gn_r, p->gn_g, st);
+    } else {
+      status = do_jhw(p, p->gn_r, p->gn_g, st);
+    }
     if (status != MRSTAT_OK) return status;
-    if (o->hessian == 1) {
+    if (sur) {
+      p->lr->active = true;  // Steihaug's products: the surrogate's low-rank model
+    } else if (o->hessian == 1) {
       if (coef_stale) {
         Span sp(p, MRSTAT_K_BLOCH, st);
         e = lowrank_project(*p, *p->lr, p->gn_alpha, b1, p->gn_mask, p->lr->coef, st);
@@ -714,8 +780,18 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
       trial_kernel<<<g, kT, 0, st>>>(p->gn_alpha, p->gn_z, p->gn_mask, nv, lt1a, lt1b, lt2a, lt2b, p->gn_trial);
     });
     if (e != cudaSuccess) return cuda_fail(e, "trial point");
-    status = do_linearize(p, p->gn_trial, b1, p->gn_mask, p->D2, p->rho2, st);
-    if (status == MRSTAT_OK) status = do_signal(p, p->D2, p->rho2, p->gn_st, st);
+    if (sur) {
+      // the trial point's coefficients go to coef2, which the products read while the
+      // trial signal is formed; a rejected step swaps them back
+      status = sur_linearize(p->gn_trial, p->rho2, p->lr->coef2);
+      if (status == MRSTAT_OK) {
+        swap_ptr(p->lr->coef, p->lr->coef2);
+        status = sur_signal(p->gn_trial, p->gn_st);
+      }
+    } else {
+      status = do_linearize(p, p->gn_trial, b1, p->gn_mask, p->D2, p->rho2, st);
+      if (status == MRSTAT_OK) status = do_signal(p, p->D2, p->rho2, p->gn_st, st);
+    }
     if (status == MRSTAT_OK) status = S.residual(p->gn_st, d, p->gn_rt, p->gn_sc + S_F);
     if (status == MRSTAT_OK) status = fetch();
     if (status != MRSTAT_OK) return status;
@@ -734,8 +810,9 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
     const bool acc = ratio > o->eta;
     local.accepted[k] = acc;
     local.iterations = k + 1;
+    if (sur && !acc) swap_ptr(p->lr->coef, p->lr->coef2);
     if (acc) {
-      swap_ptr(p->D, p->D2);
+      if (!sur) swap_ptr(p->D, p->D2);
       swap_ptr(p->rho, p->rho2);
       swap_ptr(p->gn_alpha, p->gn_trial);
       swap_ptr(p->gn_s, p->gn_st);
@@ -745,7 +822,9 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
     }
   }
   local.f_final = f;
-  // the plan's cached linearisation is the one at the returned alpha (mask gn_mask)
+  // the plan's cached linearisation is the one at the returned alpha (mask gn_mask): the
+  // exact one, or the surrogate's low-rank one when every iteration used the surrogate
+  if (p->lr) p->lr->active = o->surrogate_iters > 0 && o->surrogate_iters == o->outer_iters;
   e = cudaMemcpyAsync(alpha, p->gn_alpha, 4 * (size_t)nv * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "Gauss-Newton result");

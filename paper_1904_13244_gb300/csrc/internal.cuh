@@ -45,7 +45,7 @@ struct Plan {
   // scratch
   float4* dfwd = nullptr;   // [nq][nv] m_y only, for mrstat_forward
   float2* cf = nullptr;     // [3][nv] per-voxel complex coefficients of the y-contraction
-  float2* A = nullptr;      // [ntr][nx] y-contracted image rows
+  float2* A = nullptr;      // [ntr_pad][nx] y-contracted image rows (padded rows zero)
   float2* wt = nullptr;     // [ntr_pad][nx] x-adjoint of a k-space vector (rows >= ntr zero)
   double* red = nullptr;    // [kRedBlocks] reduction partials
   unsigned* ticket = nullptr;  // last-block ticket of the reductions (0 between launches)
@@ -202,7 +202,8 @@ cudaError_t launch_prep_linearize(const Plan& p, const float* alpha, const uint8
                                   cudaStream_t st);
 cudaError_t launch_prep_jvp(const Plan& p, const float* v, cudaStream_t st);
 cudaError_t launch_ycontract(const Plan& p, const float4* D, int nch, cudaStream_t st);
-cudaError_t launch_jhw_dot(const Plan& p, float* g, cudaStream_t st);
+// g from W~ = p.wt, or from wt (then times scale) when given
+cudaError_t launch_jhw_dot(const Plan& p, float* g, cudaStream_t st, const float2* wt = nullptr, float scale = 1.f);
 cudaError_t launch_timecourse(const Plan& p, int channel, float* out, cudaStream_t st);
 // dft.cu
 cudaError_t launch_cgemm(const float2* A, const float2* B, float2* C, int M, int N, int K,

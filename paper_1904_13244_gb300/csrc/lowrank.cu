@@ -19,6 +19,7 @@
 // The coefficients c, dc1, dc2 come either from the exact Bloch recursion projected onto
 // U on the fly (lr_project_kernel: no time course is ever stored) or from a caller (the
 // learned surrogate).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -293,6 +294,182 @@ __global__ void lr_final_kernel(const float* __restrict__ P, const float* __rest
   g[3 * (size_t)nv + j] = a3 * m;
 }
 
+// ---------------------------------------------------------------------------
+// J^H J v with a fully sampled readout (nkx == nx).  The readout DFT and its adjoint
+// cancel (F^H F = nx I), so per image column ix only the phase-encode DFT, the per-ky
+// Gram and its adjoint remain:  P_r = nx F_y^H (M_ky (F_y h)).  Operands are stored
+// with rows (ix, r) = ix R + r and columns 2 iy (or 2 ky) + re/im, so every kernel below
+// reads and writes whole rows; the voxel-order inputs and outputs go through 32 x 32
+// shared-memory tiles.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void put_split_pair(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t idx, float2 v) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+  const float2 hf = __bfloat1622float2(h);
+  *reinterpret_cast<__nv_bfloat162*>(hi + idx) = h;
+  *reinterpret_cast<__nv_bfloat162*>(lo + idx) = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+}
+
+// h_r,j = i (rho_j (v0 dc1_r,j + v1 dc2_r,j) + (v2 + i v3) c_r,j) mask_j into rows (ix, r).
+// Block: a 32 x 32 voxel tile and 4 basis functions (blockIdx.z).
+__global__ void __launch_bounds__(256)
+lr_prep_t_kernel(const float* __restrict__ v, const float* __restrict__ coef, const float2* __restrict__ rho,
+                 const float* __restrict__ maskf, int nx, int ny, int nv, int R, __nv_bfloat16* __restrict__ hi,
+                 __nv_bfloat16* __restrict__ lo, int ldk, const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  __shared__ float2 S[4][32][33];  // [r - r0][ix - ix0][iy - iy0]
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int ix0 = blockIdx.x * 32, iy0 = blockIdx.y * 32;
+  const int ix = ix0 + tx;
+  float v0[4], v1[4], v2[4], v3[4];
+  float2 rh[4];
+  int jj[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int iy = iy0 + ty + 8 * k;
+    const bool ok = ix < nx && iy < ny;
+    const int j = ok ? iy * nx + ix : -1;
+    jj[k] = j;
+    const float m = ok ? maskf[j] : 0.f;
+    rh[k] = ok ? rho[j] : make_float2(0.f, 0.f);
+    v0[k] = ok ? v[j] : 0.f;
+    v1[k] = ok ? v[nv + j] : 0.f;
+    v2[k] = ok ? v[2 * (size_t)nv + j] * m : 0.f;
+    v3[k] = ok ? v[3 * (size_t)nv + j] * m : 0.f;
+  }
+  {
+    const int r0 = blockIdx.z * 4;  // this block's chunk of 4 basis functions
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = r0 + rr;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float2 h = make_float2(0.f, 0.f);
+        const int j = jj[k];
+        if (j >= 0 && r < R) {
+          const float c = coef[(size_t)r * nv + j];
+          const float t = fmaf(v0[k], coef[(size_t)(R + r) * nv + j], v1[k] * coef[(size_t)(2 * R + r) * nv + j]);
+          const float qr = rh[k].x * t + v2[k] * c, qi = rh[k].y * t + v3[k] * c;
+          h = make_float2(-qi, qr);
+        }
+        S[rr][tx][ty + 8 * k] = h;
+      }
+    }
+    __syncthreads();
+    const int iy = iy0 + tx;
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+      const int rl = ty + 8 * i, a = rl >> 2, rr = rl & 3;
+      const int ixa = ix0 + a, r = r0 + rr;
+      if (ixa < nx && r < R && iy < ny) put_split_pair(hi, lo, (size_t)(ixa * R + r) * ldk + 2 * iy, S[rr][a][tx]);
+    }
+  }
+}
+
+// G[(ix, r)][ky] = sum_{n : ky(n) = ky} U[n][r] sum_q U[n][q] H[(ix, q)][ky]: the per-ky
+// Gram applied through the TR axis (2 |S(ky)| R multiply-adds per value instead of R^2).
+// Block (32, 8): 32 consecutive ky (lanes) x 8 image columns; the rows of U of the TRs
+// of its 32 ky values (contiguous in Ug, U gathered in ky order) sit in shared memory,
+// rows padded to R + 1 floats.
+template <int R>
+__global__ void __launch_bounds__(256)
+lr_gram_t_kernel(const float* __restrict__ HT, int ldh, const float* __restrict__ Ug, const int* __restrict__ kyptr,
+                 int nx, int ny, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int ldk,
+                 const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  extern __shared__ float us[];  // [rows of this ky tile][R + 1]
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int ky0 = blockIdx.x * 32;
+  const int t0 = kyptr[ky0], t1 = kyptr[min(ky0 + 32, ny)];
+  for (int e = tid; e < (t1 - t0) * R; e += 256) {
+    const int t = e / R, r = e - t * R;
+    us[t * (R + 1) + r] = Ug[(size_t)t0 * R + e];
+  }
+  __syncthreads();
+  const int ky = ky0 + tx, ix = blockIdx.y * 8 + ty;
+  if (ky >= ny || ix >= nx) return;
+  const float2* H2 = reinterpret_cast<const float2*>(HT);
+  const int ld2 = ldh / 2;
+  float2 in[R], out[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    in[q] = H2[(size_t)(ix * R + q) * ld2 + ky];
+    out[q] = make_float2(0.f, 0.f);
+  }
+  const int ta = kyptr[ky], te = kyptr[ky + 1];
+  for (int t = ta; t < te; ++t) {
+    const float* un = us + (t - t0) * (R + 1);
+    float sr = 0.f, si = 0.f;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      sr = fmaf(un[q], in[q].x, sr);
+      si = fmaf(un[q], in[q].y, si);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      out[r].x = fmaf(un[r], sr, out[r].x);
+      out[r].y = fmaf(un[r], si, out[r].y);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) put_split_pair(hi, lo, (size_t)(ix * R + r) * ldk + 2 * ky, out[r]);
+}
+
+// g_k,j = scale Re sum_r conj(dh_r,j/dv_k) P[(ix, r)][iy] (P rows (ix, r), columns 2 iy +
+// re/im).  Block (16, 16): a 16 x 16 voxel tile, one voxel per thread; P arrives in
+// chunks of 8 basis functions through shared memory (reads of whole 128-byte row pieces).
+__global__ void __launch_bounds__(256)
+lr_final_t_kernel(const float* __restrict__ PT, int ldp, const float* __restrict__ coef,
+                  const float2* __restrict__ rho, const float* __restrict__ maskf, int nx, int ny, int nv, int R,
+                  float scale, float* __restrict__ g, const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  __shared__ float2 S[8][16][17];  // [r - r0][ix - ix0][iy - iy0]
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
+  const int ix0 = blockIdx.x * 16, iy0 = blockIdx.y * 16;
+  const int ix = ix0 + tx, iy = iy0 + ty;
+  const bool ok = ix < nx && iy < ny;
+  const int j = ok ? iy * nx + ix : 0;
+  const float2 rh = ok ? rho[j] : make_float2(0.f, 0.f);
+  const float2* P2 = reinterpret_cast<const float2*>(PT);
+  const int ld2 = ldp / 2;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  // load mapping: 16 lanes along iy, rows (ix, r) of the tile
+  const int ly = tid & 15, lrow = tid >> 4;  // 16 rows per pass
+  for (int r0 = 0; r0 < R; r0 += 8) {
+#pragma unroll
+    for (int pass = 0; pass < 8; ++pass) {
+      const int rl = lrow + 16 * pass, a = rl >> 3, rr = rl & 7;  // 128 rows = 16 ix x 8 r
+      const int ixa = ix0 + a, r = r0 + rr, iyl = iy0 + ly;
+      S[rr][a][ly] = (ixa < nx && r < R && iyl < ny) ? P2[(size_t)(ixa * R + r) * ld2 + iyl]
+                                                     : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (ok) {
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        const int r = r0 + rr;
+        if (r < R) {
+          const float2 pv = S[rr][tx][ty];
+          const float c = coef[(size_t)r * nv + j];
+          const float t1 = coef[(size_t)(R + r) * nv + j], t2 = coef[(size_t)(2 * R + r) * nv + j];
+          const float imcp = rh.x * pv.y - rh.y * pv.x;  // Im(conj(rho) P)
+          a0 = fmaf(t1, imcp, a0);
+          a1 = fmaf(t2, imcp, a1);
+          a2 = fmaf(c, pv.y, a2);
+          a3 = fmaf(-c, pv.x, a3);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (ok) {
+    const float m = maskf[j] * scale;
+    g[j] = a0 * m;
+    g[(size_t)nv + j] = a1 * m;
+    g[2 * (size_t)nv + j] = a2 * m;
+    g[3 * (size_t)nv + j] = a3 * m;
+  }
+}
+
 // training time courses [3][nq][ns] (quads) -> Y [ntr][3 ns] and Yt [3 ns][ntr] (complex
 // storage with zero imaginary part), columns c * ns + s
 __global__ void lr_train_matrix_kernel(const float4* __restrict__ D, int ns, int nq, int ntr,
@@ -337,7 +514,7 @@ cudaError_t lowrank_project(const Plan& p, const LowRank& L, const float* alpha,
 
 void lowrank_free(LowRank* L) {
   if (L == nullptr) return;
-  void* ptrs[] = {L->U, L->Mky, L->kyptr, L->kytr, L->coef, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
+  void* ptrs[] = {L->U, L->Ug, L->Mky, L->kyptr, L->kytr, L->coef, L->coef2, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
                   L->a4_hi, L->a4_lo, L->by_hi, L->by_lo, L->bya_hi, L->bya_lo, L->X1, L->H, L->Y3, L->P};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -360,6 +537,14 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   }
   LowRank* L = new LowRank();
   L->R = R;
+  {
+    int dev = 0, sms = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    L->sms = sms > 0 ? sms : 1;
+    L->smem_optin = optin;
+  }
   const int nx = p->nx, ny = p->ny, nkx = p->nkx, ntr = p->ntr;
   L->k1 = pad8(2 * nx);
   L->k23 = pad8(2 * ny);
@@ -381,6 +566,14 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
     std::vector<int> fill(ptr.begin(), ptr.end() - 1);
     for (int n = 0; n < ntr; ++n) trs[fill[kyi_h[n]]++] = n;
   }
+  // U gathered in ky order, and the largest number of TRs of any 32 consecutive ky values
+  std::vector<float> Ug((size_t)ntr * R);
+  for (int t = 0; t < ntr; ++t)
+    for (int r = 0; r < R; ++r) Ug[(size_t)t * R + r] = Uh[(size_t)trs[t] * R + r];
+  for (int k0 = 0; k0 < ny; k0 += 32) L->gram_rows_max = std::max(L->gram_rows_max, ptr[std::min(k0 + 32, ny)] - ptr[k0]);
+  // the cancelled readout DFT pair needs nkx == nx; the Gram kernel keeps a ky tile's rows of U
+  // in shared memory
+  L->full_readout = p->nkx == p->nx && (size_t)L->gram_rows_max * (R + 1) * sizeof(float) <= (size_t)L->smem_optin;
   std::vector<float> M((size_t)ny * R * R, 0.f);
   for (int k = 0; k < ny; ++k)
     for (int a = 0; a < R; ++a)
@@ -418,10 +611,12 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   };
   const size_t rny = (size_t)R * ny, rnk = (size_t)R * nkx;
   chk(cudaMalloc(&L->U, (size_t)ntr * R * sizeof(float)));
+  chk(cudaMalloc(&L->Ug, (size_t)ntr * R * sizeof(float)));
   chk(cudaMalloc(&L->Mky, M.size() * sizeof(float)));
   chk(cudaMalloc(&L->kyptr, ptr.size() * sizeof(int)));
   chk(cudaMalloc(&L->kytr, trs.size() * sizeof(int)));
   chk(cudaMalloc(&L->coef, (size_t)3 * R * p->nv * sizeof(float)));
+  chk(cudaMalloc(&L->coef2, (size_t)3 * R * p->nv * sizeof(float)));
   chk(cudaMalloc(&L->a1_hi, rny * L->k1 * 2));
   chk(cudaMalloc(&L->a1_lo, rny * L->k1 * 2));
   chk(cudaMalloc(&L->a23_hi, rnk * L->k23 * 2));
@@ -442,6 +637,7 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   }
   chk(cudaMemcpyAsync(L->U, U_dev, (size_t)ntr * R * sizeof(float), cudaMemcpyDeviceToDevice, st));
   chk(cudaMemcpy(L->Mky, M.data(), M.size() * sizeof(float), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(L->Ug, Ug.data(), Ug.size() * sizeof(float), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->kyptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->kytr, trs.data(), trs.size() * sizeof(int), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->by_hi, byh.data(), nby * 2, cudaMemcpyHostToDevice));
@@ -465,7 +661,7 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
     lowrank_free(L);
     return cuda_fail(e, "low-rank set-up");
   }
-  p->bytes += (int64_t)((size_t)ntr * R * 4 + M.size() * 4 + (size_t)3 * R * p->nv * 4 +
+  p->bytes += (int64_t)((size_t)2 * ntr * R * 4 + M.size() * 4 + (size_t)6 * R * p->nv * 4 +
                         2 * 2 * (rny * L->k1 + rnk * L->k23 + rny * L->k4) + 4 * nby * 2 +
                         (rny * 2 * nkx + 2 * rnk * 2 * ny + rny * 2 * nx) * 4);
   p->lr = L;
@@ -556,8 +752,63 @@ int lowrank_jhw(Plan* p, const float2* w, float* g, cudaStream_t st) {
   return lr_adjoint_dft_and_final(p, g, p->gate, st);
 }
 
+template <int R>
+static cudaError_t launch_gram_t(const Plan& p, const LowRank& L, const int* gate, cudaStream_t st) {
+  const size_t sm = (size_t)L.gram_rows_max * (R + 1) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(lr_gram_t_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((p.ny + 31) / 32, (p.nx + 7) / 8);
+  lr_gram_t_kernel<R><<<grid, dim3(32, 8), sm, st>>>(L.H, 2 * p.ny, L.Ug, L.kyptr, p.nx, p.ny,
+                                                      (__nv_bfloat16*)L.a23_hi, (__nv_bfloat16*)L.a23_lo, L.k23,
+                                                      gate);
+  return cudaGetLastError();
+}
+
+// J^H J v for a fully sampled readout: prep -> phase-encode DFT -> Gram through the TR axis
+// -> adjoint phase-encode DFT -> final, times nx for the cancelled readout DFT pair.
+static int lowrank_jhjv_full_readout(Plan* p, const float* v, float* out, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  const int R = L.R, nx = p->nx, ny = p->ny;
+  const int* gate = p->gate;
+  const dim3 tiles((nx + 31) / 32, (ny + 31) / 32), tb(32, 8);
+  cudaError_t e;
+  {
+    Span sp(p, MRSTAT_K_YCONTRACT, st);
+    const dim3 grid(tiles.x, tiles.y, (R + 3) / 4);
+    lr_prep_t_kernel<<<grid, tb, 0, st>>>(v, L.coef, p->rho, p->maskf, nx, ny, p->nv, R, (__nv_bfloat16*)L.a23_hi,
+                                          (__nv_bfloat16*)L.a23_lo, L.k23, gate);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    Span sp(p, MRSTAT_K_XDFT, st);
+    e = launch_tc_gemm(L.op_a23, L.op_by, L.H, R * nx, 2 * ny, 2 * ny, 2 * ny, 3, gate, p->dev_err, st);
+  }
+  if (e == cudaSuccess) {
+    Span sp(p, MRSTAT_K_VECTOR, st);
+    switch (R) {
+      case 8: e = launch_gram_t<8>(*p, L, gate, st); break;
+      case 16: e = launch_gram_t<16>(*p, L, gate, st); break;
+      case 24: e = launch_gram_t<24>(*p, L, gate, st); break;
+      default: e = launch_gram_t<32>(*p, L, gate, st); break;
+    }
+  }
+  if (e == cudaSuccess) {
+    Span sp(p, MRSTAT_K_XDFT_ADJ, st);
+    e = launch_tc_gemm(L.op_a23, L.op_bya, L.Y3, R * nx, 2 * ny, 2 * ny, 2 * ny, 3, gate, p->dev_err, st);
+  }
+  if (e == cudaSuccess) {
+    Span sp(p, MRSTAT_K_JHW_DOT, st);
+    const dim3 t16((nx + 15) / 16, (ny + 15) / 16);
+    lr_final_t_kernel<<<t16, dim3(16, 16), 0, st>>>(L.Y3, 2 * ny, L.coef, p->rho, p->maskf, nx, ny, p->nv, R,
+                                                     (float)nx, out, gate);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank J^H J v");
+}
+
 int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st) {
   LowRank& L = *p->lr;
+  if (L.full_readout) return lowrank_jhjv_full_readout(p, v, out, st);
   int s = lr_prep(p, v, p->gate, st);
   if (s == MRSTAT_OK) s = lr_forward_dft(p, p->gate, st);
   if (s != MRSTAT_OK) return s;

@@ -13,10 +13,14 @@ struct LowRank {
   int R = 0;
   int k1 = 0, k23 = 0, k4 = 0;     // padded K of the operands (2 nx, 2 ny, 2 nkx)
   float* U = nullptr;              // [ntr][R] time basis
+  float* Ug = nullptr;             // [ntr][R] rows of U in ky order (the order of kytr)
+  int gram_rows_max = 0;           // most TRs of any 32 consecutive ky values
+  int smem_optin = 0;              // opt-in shared memory per block
   float* Mky = nullptr;            // [ny][R][R] per-ky Gram of U rows
   int* kyptr = nullptr;            // [ny + 1] TR lists per ky residue
   int* kytr = nullptr;             // [ntr]
   float* coef = nullptr;           // [3][R][nv]: c, dc/dlnT1, dc/dlnT2 (masked)
+  float* coef2 = nullptr;          // [3][R][nv]: trial point of the surrogate Gauss-Newton phase
   void *a1_hi = nullptr, *a1_lo = nullptr;    // [R ny][k1]   readout-DFT input rows
   void *a23_hi = nullptr, *a23_lo = nullptr;  // [R nkx][k23] phase-encode DFT input rows
   void *a4_hi = nullptr, *a4_lo = nullptr;    // [R ny][k4]   readout adjoint input rows
@@ -28,6 +32,8 @@ struct LowRank {
   float* P = nullptr;              // [R ny][2 nx]
   TcOperand op_a1, op_a23, op_a4, op_by, op_bya;
   bool active = false;             // the plan's current linearisation is this low-rank one
+  bool full_readout = false;       // nkx == nx: J^H J v skips the readout DFT pair
+  int sms = 1;                     // SM count (grid of the Gram kernel)
 };
 
 }  // namespace mrstat

@@ -424,6 +424,13 @@ int Mlp::predict(int B, float* pred, cudaStream_t st) {
   return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "surrogate output");
 }
 
+int mlp_infer(Mlp* m, const float* lnT, const float* b1, int n, float* coef, cudaStream_t st) {
+  int s = m->ensure_batch(n, false);
+  if (s == MRSTAT_OK) s = m->forward(lnT, b1, n, false, st);
+  if (s == MRSTAT_OK) s = m->predict(n, coef, st);
+  return s;
+}
+
 }  // namespace mrstat
 
 // ---------------------------------------------------------------------------
@@ -498,11 +505,7 @@ int mrstat_mlp_infer(mrstat_mlp* m, const float* lnT, const float* b1, int32_t n
   if (m == nullptr || lnT == nullptr || coef == nullptr || n < 1)
     return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_mlp_infer");
   DeviceGuard g(m->device);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  int s = m->ensure_batch(n, false);
-  if (s == MRSTAT_OK) s = m->forward(lnT, b1, n, false, st);
-  if (s == MRSTAT_OK) s = m->predict(n, coef, st);
-  return s;
+  return mlp_infer(m, lnT, b1, n, coef, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int mrstat_mlp_train_step(mrstat_mlp* m, const float* lnT, const float* b1, const float* target, int32_t B, float lr,

@@ -49,4 +49,7 @@ struct Mlp {
   void free_weights();
 };
 
+// Coefficients [3][R][n] of n samples (lnT [2][n], b1 [n] or NULL) on stream st.
+int mlp_infer(Mlp* m, const float* lnT, const float* b1, int n, float* coef, cudaStream_t st);
+
 }  // namespace mrstat

@@ -250,8 +250,29 @@ int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* ma
   return MRSTAT_OK;
 }
 
+// J^H J v.  With a fully sampled readout (nkx == nx: kx runs over a whole period of the
+// x frequencies) the readout DFT and its adjoint cancel, F^H F = nx I, so
+// W~ = nx A and the two x-DFTs are skipped: exact, not an approximation.
 int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st) {
   if (p->lr && p->lr->active) return lowrank_jhjv(p, v, out, st);
+  if (p->nkx == p->nx) {
+    cudaError_t e;
+    {
+      Span sp(p, MRSTAT_K_VECTOR, st);
+      e = launch_prep_jvp(*p, v, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "prep_jvp launch");
+    {
+      Span sp(p, MRSTAT_K_YCONTRACT, st);
+      e = launch_ycontract(*p, p->D, kChannels, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
+    {
+      Span sp(p, MRSTAT_K_JHW_DOT, st);
+      e = launch_jhw_dot(*p, out, st, p->A, (float)p->nx);
+    }
+    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "jhw_dot launch");
+  }
   int s = do_jvp(p, v, p->cg_jv, st);
   if (s == MRSTAT_OK) s = do_jhw(p, p->cg_jv, out, st);
   return s;
@@ -413,7 +434,8 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(dalloc(p, &p->rho, nv));
   chk(dalloc(p, &p->maskf, nv));
   chk(dalloc(p, &p->cf, (size_t)kChannels * nv));
-  chk(dalloc(p, &p->A, (size_t)p->ntr * p->nx));
+  // A has the padded TR rows too (zero, never written): J^H J v reads it as W~ over TR quads
+  chk(dalloc(p, &p->A, (size_t)p->ntr_pad * p->nx));
   chk(dalloc(p, &p->wt, (size_t)p->ntr_pad * p->nx));
   chk(dalloc(p, &p->red, kRedBlocks));
   chk(dalloc(p, &p->ticket, 1));
@@ -435,6 +457,7 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(cudaMemcpy(p->ft, ft.data(), ft.size() * sizeof(float2), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(p->fh, fh.data(), fh.size() * sizeof(float2), cudaMemcpyHostToDevice));
   chk(cudaMemset(p->wt, 0, (size_t)p->ntr_pad * p->nx * sizeof(float2)));
+  chk(cudaMemset(p->A, 0, (size_t)p->ntr_pad * p->nx * sizeof(float2)));
   chk(cudaMemset(p->ticket, 0, sizeof(unsigned)));
   chk(cudaMemset(p->dev_err, 0, sizeof(int)));
   if (e == cudaSuccess && form == MRSTAT_FORM_SPLIT_BF16) {

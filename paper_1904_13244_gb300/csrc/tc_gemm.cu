@@ -152,10 +152,11 @@ struct TileShape {
   static constexpr uint32_t kStage = 2 * kA + 2 * kB;    // hi and lo of both
   static constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
   static constexpr size_t kSmem = (size_t)STAGES * kStage + 1024 /* align */ + 256 /* barriers */;
+  static_assert((size_t)STAGES * kStage >= (size_t)4 * 32 * (BN + 1) * 4, "epilogue staging fits the ring");
 };
 
 template <int BN, int STAGES>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
                float* __restrict__ C, int M, int N, int K, int ldc, int nprod, const int* __restrict__ gate,
@@ -242,19 +243,24 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant_
   __syncwarp();
   fence_after();
   if (ok) {
-    const int row = m0 + warp * 32 + lane;
-    float* crow = C + (size_t)row * ldc;
+    // Every MMA has completed, so the pipeline's shared memory is free: each warp stages
+    // its 32 accumulator rows there (row stride BN + 1 floats: conflict-free both ways)
+    // and then writes whole row segments, 32 consecutive columns per store.
+    float* stage = reinterpret_cast<float*>(smem) + warp * 32 * (BN + 1);
 #pragma unroll
     for (int cb = 0; cb < BN; cb += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
-      if (row < M) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + cb + j;
-          if (col < N) crow[col] = v[j];
-        }
-      }
+      for (int j = 0; j < 16; ++j) stage[lane * (BN + 1) + cb + j] = v[j];
+    }
+    __syncwarp();
+    const int rows = min(32, M - (m0 + warp * 32));
+    for (int r = 0; r < rows; ++r) {
+      float* crow = C + (size_t)(m0 + warp * 32 + r) * ldc;
+#pragma unroll
+      for (int c = lane; c < BN; c += 32)
+        if (n0 + c < N) crow[n0 + c] = stage[r * (BN + 1) + c];
     }
   } else if (threadIdx.x == 0) {
     atomicExch(err, 1);
@@ -304,7 +310,6 @@ EncodeFn encode_fn() {
   return fn;
 }
 
-constexpr int kBN = 64, kStages = 4;
 
 }  // namespace
 
@@ -324,32 +329,56 @@ cudaError_t make_bf16_tmap(CUtensorMap* map, const void* base, int rows, int k, 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+int tc_gemm_tile_n(int n) {
+  if (n >= 224 && n % 224 == 0) return 224;
+  if (n <= 64) return 64;
+  if (n <= 128) return 128;
+  return 256;
+}
+
 cudaError_t make_split_operand(TcOperand* op, const void* hi, const void* lo, int rows, int k, int ldk,
                                bool is_a) {
   op->rows = rows;
   op->k = k;
   op->ldk = ldk;
-  cudaError_t e = make_bf16_tmap(&op->hi, hi, rows, k, ldk, is_a ? BM : kBN);
-  if (e == cudaSuccess) e = make_bf16_tmap(&op->lo, lo, rows, k, ldk, is_a ? BM : kBN);
+  op->box = is_a ? BM : tc_gemm_tile_n(rows);
+  cudaError_t e = make_bf16_tmap(&op->hi, hi, rows, k, ldk, op->box);
+  if (e == cudaSuccess) e = make_bf16_tmap(&op->lo, lo, rows, k, ldk, op->box);
   return e;
 }
 
-size_t tc_gemm_smem_bytes() { return TileShape<kBN, kStages>::kSmem; }
+size_t tc_gemm_smem_bytes() { return TileShape<64, 4>::kSmem; }
 
+template <int BN, int STAGES>
+static cudaError_t launch_tile(const TcOperand& a, const TcOperand& b, float* C, int M, int N, int K, int ldc,
+                               int nprod, const int* gate, int* err, cudaStream_t st) {
+  const size_t sm = TileShape<BN, STAGES>::kSmem;
+  // the attribute is per device; setting it on every launch is cheap
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  tc_gemm_kernel<BN, STAGES><<<grid, 128, sm, st>>>(a.hi, a.lo, b.hi, b.lo, C, M, N, K, ldc, nprod, gate, err);
+  return cudaGetLastError();
+}
+
+// The N tile is the B operand's TMA box (chosen from its row count when it was made).
+// Rings: 64-wide tiles with short K loops (<= 8 chunks of 64) use 2 stages so that two
+// CTAs share an SM and one CTA's epilogue overlaps the other's loads, longer ones 4;
+// wider tiles fill about 190 KB of shared memory (one CTA per SM).
 cudaError_t launch_tc_gemm(const TcOperand& a, const TcOperand& b, float* C, int M, int N, int K, int ldc,
                            int nprod, const int* gate, int* err, cudaStream_t st) {
   if (M == 0 || N == 0) return cudaSuccess;
-  const size_t sm = TileShape<kBN, kStages>::kSmem;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kBN, kStages>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    attr = true;
+  if (a.box != BM) return cudaErrorInvalidValue;
+  switch (b.box) {
+    case 64:
+      if ((K + BK - 1) / BK <= 8) return launch_tile<64, 2>(a, b, C, M, N, K, ldc, nprod, gate, err, st);
+      return launch_tile<64, 4>(a, b, C, M, N, K, ldc, nprod, gate, err, st);
+    case 128: return launch_tile<128, 3>(a, b, C, M, N, K, ldc, nprod, gate, err, st);
+    case 224: return launch_tile<224, 2>(a, b, C, M, N, K, ldc, nprod, gate, err, st);
+    case 256: return launch_tile<256, 2>(a, b, C, M, N, K, ldc, nprod, gate, err, st);
+    default: return cudaErrorInvalidValue;
   }
-  dim3 grid((M + BM - 1) / BM, (N + kBN - 1) / kBN);
-  tc_gemm_kernel<kBN, kStages><<<grid, 128, sm, st>>>(a.hi, a.lo, b.hi, b.lo, C, M, N, K, ldc, nprod, gate, err);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_split_bf16(const float* x, int rows, int cols, int ld_src, void* hi, void* lo, int ldk,

@@ -12,7 +12,13 @@ struct TcOperand {
   CUtensorMap hi;
   CUtensorMap lo;
   int rows = 0, k = 0, ldk = 0;
+  int box = 0;  // rows per TMA box: 128 for an A operand, the GEMM's N tile for a B operand
 };
+
+// N tile for a GEMM with N columns (a B operand with N rows): 224 for multiples of 224
+// (exact tiles of the 2 x 224 real-embedded DFTs), else the smallest of 64 / 128 / 256
+// that covers N, 256 beyond.
+int tc_gemm_tile_n(int n);
 
 cudaError_t make_bf16_tmap(CUtensorMap* map, const void* base, int rows, int k, int ldk, int box_rows);
 cudaError_t make_split_operand(TcOperand* op, const void* hi, const void* lo, int rows, int k, int ldk,

@@ -175,3 +175,63 @@ def test_lowrank_hessian_noiseless_recovery(mr):
         a_gpu = a.cpu().numpy().astype(np.float64)
     assert metrics.nrmse(np.exp(a_gpu[0]), ph.t1_ms.ravel()) < 1e-3
     assert metrics.nrmse(np.exp(a_gpu[1]), ph.t2_ms.ravel()) < 1e-3
+
+
+def _trained_surrogate(mr, plan, rank, hidden=128, steps=2500, seed=0):
+    """A surrogate fitted to the plan's projected Bloch model (exact sample projections)."""
+    rng = np.random.default_rng(seed)
+    n = 32768
+    x = cuda(np.stack([rng.uniform(np.log(100), np.log(6000), n), rng.uniform(np.log(10), np.log(3000), n)]))
+    tgt = plan.lowrank_project_samples(x)
+    scale = tgt[0].abs().amax(dim=1).clamp_min(1e-6).cpu().numpy()
+    net = mr.Surrogate(hidden, rank, (np.log(1000.0), 1.0, np.log(100.0), 1.2, 1.0, 0.2), 0.5, seed=seed)
+    net.set_output_scale(scale)
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    for it in range(steps):
+        idx = torch.randint(0, n, (1024,), device="cuda", generator=gen)
+        net.train_step(x[:, idx].contiguous(), tgt[:, :, idx].contiguous(), 3e-3 if it < 1800 else 1e-3)
+    return net
+
+
+def test_surrogate_phase_then_exact_reaches_the_exact_minimiser(mr, noisy_quad):
+    """The first iterations on the learned surrogate's low-rank model, the rest exact: the
+    solve ends at the exact-model solution, and the surrogate phase lowers the exact
+    objective on its own."""
+    seq, ph, truth, d, a0 = noisy_quad
+    with mr.Plan(seq) as plan:
+        plan.lowrank_set_basis(_basis(plan, 16))
+        net = _trained_surrogate(mr, plan, 16)
+        a_ex = cuda(a0)
+        rep_ex = plan.gn_solve(cuda(d, torch.complex64), a_ex, outer_iters=12, inner_iters=20)
+        a_s = cuda(a0)
+        rep_s = plan.gn_solve(cuda(d, torch.complex64), a_s, outer_iters=12, inner_iters=20, surrogate_iters=6,
+                              surrogate=net)
+        # objective of the point the surrogate phase alone reaches, under the exact model
+        a_p = cuda(a0)
+        plan.gn_solve(cuda(d, torch.complex64), a_p, outer_iters=6, inner_iters=20, surrogate_iters=6, surrogate=net)
+        f_p = plan.gn_solve(cuda(d, torch.complex64), a_p.clone(), outer_iters=0)["f_final"]
+        plan.check()
+        net.close()
+    assert rep_s["iterations"] == 12
+    assert f_p < 0.5 * rep_ex["f"][0]
+    assert abs(rep_s["f_final"] - rep_ex["f_final"]) / rep_ex["f_final"] < 1e-3
+    assert metrics.relerr(a_s.cpu().numpy(), a_ex.cpu().numpy()) < 1e-2
+
+
+def test_surrogate_options_are_checked(mr, noisy_quad):
+    seq, ph, truth, d, a0 = noisy_quad
+    with mr.Plan(seq) as plan:
+        with pytest.raises(mr.MrstatError) as e:
+            plan.gn_solve(cuda(d, torch.complex64), cuda(a0), outer_iters=2, surrogate_iters=1)
+        assert e.value.status == 1
+        with pytest.raises(mr.MrstatError) as e:
+            plan.gn_solve(cuda(d, torch.complex64), cuda(a0), outer_iters=2, surrogate_iters=3)
+        assert e.value.status == 1
+        with mr.Surrogate(64, 8, (7.0, 1.0, 4.5, 1.2, 1.0, 0.2)) as net:
+            with pytest.raises(mr.MrstatError) as e:  # no basis yet
+                plan.gn_solve(cuda(d, torch.complex64), cuda(a0), outer_iters=2, surrogate_iters=1, surrogate=net)
+            assert e.value.status == 3
+            plan.lowrank_set_basis(_basis(plan, 16))
+            with pytest.raises(mr.MrstatError) as e:  # rank 8 net, rank 16 basis
+                plan.gn_solve(cuda(d, torch.complex64), cuda(a0), outer_iters=2, surrogate_iters=1, surrogate=net)
+            assert e.value.status == 1
