@@ -164,7 +164,9 @@ int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* ma
                  float2* rho, cudaStream_t st);
 cudaError_t do_dot(Plan* p, const float* a, const float* b, int64_t n, double* out, cudaStream_t st);
 // Re(J^H J) v with the plan's active linearisation (exact: J.v then J^H; low-rank: per-ky Gram)
-int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st);
+// Re(J^H J) v; with vdot also *vdot = <v, Re(J^H J) v> (fused into the last pass where the
+// path allows it, else one more inner-product launch)
+int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot = nullptr);
 // readout DFT of rows A [ntr][nx] (complex) into out [ntr][nkx], and its adjoint
 int do_xdft(Plan* p, const float2* A, float2* out, const int* gate, cudaStream_t st);
 int do_xdft_adj(Plan* p, const float2* w, float2* out, const int* gate, cudaStream_t st);
@@ -178,7 +180,8 @@ cudaError_t lowrank_project(const Plan& p, const LowRank& L, const float* alpha,
                             const uint8_t* mask, float* coef, cudaStream_t st);
 int lowrank_jvp(Plan* p, const float* v, float2* jv, cudaStream_t st);
 int lowrank_jhw(Plan* p, const float2* w, float* g, cudaStream_t st);
-int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st);
+// Re(J^H J) v; with vdot also *vdot = <v, Re(J^H J) v> (fused where the path allows)
+int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot = nullptr);
 cudaError_t lowrank_train_matrix(const float4* D, int ns, int nq, int ntr, float2* Y, float2* Yt,
                                  cudaStream_t st);
 cudaError_t ensure_forward_scratch(Plan* p);

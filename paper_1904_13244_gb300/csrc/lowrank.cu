@@ -28,6 +28,7 @@
 
 #include "internal.cuh"
 #include "lowrank.cuh"
+#include "reduce.cuh"
 
 namespace mrstat {
 namespace {
@@ -414,60 +415,80 @@ lr_gram_t_kernel(const float* __restrict__ HT, int ldh, const float* __restrict_
   for (int r = 0; r < R; ++r) put_split_pair(hi, lo, (size_t)(ix * R + r) * ldk + 2 * ky, out[r]);
 }
 
-// g_k,j = scale Re sum_r conj(dh_r,j/dv_k) P[(ix, r)][iy] (P rows (ix, r), columns 2 iy +
-// re/im).  Block (16, 16): a 16 x 16 voxel tile, one voxel per thread; P arrives in
-// chunks of 8 basis functions through shared memory (reads of whole 128-byte row pieces).
+// Partial sums over one chunk of 8 basis functions (blockIdx.z) of
+//   g_k,j = Re sum_r conj(dh_r,j/dv_k) P[(ix, r)][iy]   (P rows (ix, r), columns 2 iy + re/im)
+// into part[z][4][nv].  Block (16, 16): a 16 x 16 voxel tile, one voxel per thread; P
+// arrives through shared memory in whole 128-byte row pieces.
 __global__ void __launch_bounds__(256)
 lr_final_t_kernel(const float* __restrict__ PT, int ldp, const float* __restrict__ coef,
-                  const float2* __restrict__ rho, const float* __restrict__ maskf, int nx, int ny, int nv, int R,
-                  float scale, float* __restrict__ g, const int* __restrict__ gate) {
+                  const float2* __restrict__ rho, int nx, int ny, int nv, int R, float* __restrict__ part,
+                  const int* __restrict__ gate) {
   if (gate != nullptr && *gate == 0) return;
   __shared__ float2 S[8][16][17];  // [r - r0][ix - ix0][iy - iy0]
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
-  const int ix0 = blockIdx.x * 16, iy0 = blockIdx.y * 16;
-  const int ix = ix0 + tx, iy = iy0 + ty;
-  const bool ok = ix < nx && iy < ny;
-  const int j = ok ? iy * nx + ix : 0;
-  const float2 rh = ok ? rho[j] : make_float2(0.f, 0.f);
+  const int ix0 = blockIdx.x * 16, iy0 = blockIdx.y * 16, r0 = blockIdx.z * 8;
   const float2* P2 = reinterpret_cast<const float2*>(PT);
   const int ld2 = ldp / 2;
+  // load mapping: 16 lanes along iy, 128 rows (16 ix x 8 r) in 8 passes of 16
+  const int ly = tid & 15, lrow = tid >> 4;
+#pragma unroll
+  for (int pass = 0; pass < 8; ++pass) {
+    const int rl = lrow + 16 * pass, a = rl >> 3, rr = rl & 7;
+    const int ixa = ix0 + a, r = r0 + rr, iyl = iy0 + ly;
+    S[rr][a][ly] =
+        (ixa < nx && r < R && iyl < ny) ? P2[(size_t)(ixa * R + r) * ld2 + iyl] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int ix = ix0 + tx, iy = iy0 + ty;
+  if (ix >= nx || iy >= ny) return;
+  const int j = iy * nx + ix;
+  const float2 rh = rho[j];
   float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-  // load mapping: 16 lanes along iy, rows (ix, r) of the tile
-  const int ly = tid & 15, lrow = tid >> 4;  // 16 rows per pass
-  for (int r0 = 0; r0 < R; r0 += 8) {
 #pragma unroll
-    for (int pass = 0; pass < 8; ++pass) {
-      const int rl = lrow + 16 * pass, a = rl >> 3, rr = rl & 7;  // 128 rows = 16 ix x 8 r
-      const int ixa = ix0 + a, r = r0 + rr, iyl = iy0 + ly;
-      S[rr][a][ly] = (ixa < nx && r < R && iyl < ny) ? P2[(size_t)(ixa * R + r) * ld2 + iyl]
-                                                     : make_float2(0.f, 0.f);
+  for (int rr = 0; rr < 8; ++rr) {
+    const int r = r0 + rr;
+    if (r < R) {
+      const float2 pv = S[rr][tx][ty];
+      const float c = coef[(size_t)r * nv + j];
+      const float t1 = coef[(size_t)(R + r) * nv + j], t2 = coef[(size_t)(2 * R + r) * nv + j];
+      const float imcp = rh.x * pv.y - rh.y * pv.x;  // Im(conj(rho) P)
+      a0 = fmaf(t1, imcp, a0);
+      a1 = fmaf(t2, imcp, a1);
+      a2 = fmaf(c, pv.y, a2);
+      a3 = fmaf(-c, pv.x, a3);
     }
-    __syncthreads();
-    if (ok) {
-#pragma unroll
-      for (int rr = 0; rr < 8; ++rr) {
-        const int r = r0 + rr;
-        if (r < R) {
-          const float2 pv = S[rr][tx][ty];
-          const float c = coef[(size_t)r * nv + j];
-          const float t1 = coef[(size_t)(R + r) * nv + j], t2 = coef[(size_t)(2 * R + r) * nv + j];
-          const float imcp = rh.x * pv.y - rh.y * pv.x;  // Im(conj(rho) P)
-          a0 = fmaf(t1, imcp, a0);
-          a1 = fmaf(t2, imcp, a1);
-          a2 = fmaf(c, pv.y, a2);
-          a3 = fmaf(-c, pv.x, a3);
-        }
-      }
-    }
-    __syncthreads();
   }
-  if (ok) {
-    const float m = maskf[j] * scale;
-    g[j] = a0 * m;
-    g[(size_t)nv + j] = a1 * m;
-    g[2 * (size_t)nv + j] = a2 * m;
-    g[3 * (size_t)nv + j] = a3 * m;
+  float* pz = part + (size_t)blockIdx.z * 4 * nv;
+  pz[j] = a0;
+  pz[(size_t)nv + j] = a1;
+  pz[2 * (size_t)nv + j] = a2;
+  pz[3 * (size_t)nv + j] = a3;
+}
+
+// g = scale * mask * (sum of the chunk partials, in chunk order); with vdot, also
+// *vdot = sum_e v[e] g[e] (the CG inner product <p, Re(J^H J) p>: float32 per thread,
+// float64 from the warp level up, last-block finish over red / ticket)
+constexpr int kSumThreads = 256;
+__global__ void __launch_bounds__(kSumThreads)
+lr_final_sum_kernel(const float* __restrict__ part, int nchunk, const float* __restrict__ maskf, int nv, float scale,
+                    float* __restrict__ g, const int* __restrict__ gate, const float* __restrict__ v,
+                    double* red_part, unsigned* ticket, double* __restrict__ vdot) {
+  if (gate != nullptr && *gate == 0) return;
+  const int64_t n4 = 4 * (int64_t)nv;
+  float sf = 0.f;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < nchunk; ++z) s += part[(size_t)z * n4 + e];
+    const int j = (int)(e % nv);
+    const float val = s * maskf[j] * scale;
+    g[e] = val;
+    if (vdot != nullptr) sf = fmaf(v[e], val, sf);
   }
+  if (vdot == nullptr) return;
+  __shared__ double ws[kSumThreads / 32];
+  const double t = red::block_sum<kSumThreads>((double)sf, ws);
+  if (threadIdx.x == 0) red_part[blockIdx.x] = t;
+  red::finish_reduction<kSumThreads>(red_part, ticket, vdot, ws);
 }
 
 // training time courses [3][nq][ns] (quads) -> Y [ntr][3 ns] and Yt [3 ns][ntr] (complex
@@ -514,7 +535,7 @@ cudaError_t lowrank_project(const Plan& p, const LowRank& L, const float* alpha,
 
 void lowrank_free(LowRank* L) {
   if (L == nullptr) return;
-  void* ptrs[] = {L->U, L->Ug, L->Mky, L->kyptr, L->kytr, L->coef, L->coef2, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
+  void* ptrs[] = {L->U, L->Ug, L->Mky, L->kyptr, L->kytr, L->coef, L->coef2, L->gpart, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
                   L->a4_hi, L->a4_lo, L->by_hi, L->by_lo, L->bya_hi, L->bya_lo, L->X1, L->H, L->Y3, L->P};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -617,6 +638,7 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   chk(cudaMalloc(&L->kytr, trs.size() * sizeof(int)));
   chk(cudaMalloc(&L->coef, (size_t)3 * R * p->nv * sizeof(float)));
   chk(cudaMalloc(&L->coef2, (size_t)3 * R * p->nv * sizeof(float)));
+  chk(cudaMalloc(&L->gpart, (size_t)((R + 7) / 8) * 4 * p->nv * sizeof(float)));
   chk(cudaMalloc(&L->a1_hi, rny * L->k1 * 2));
   chk(cudaMalloc(&L->a1_lo, rny * L->k1 * 2));
   chk(cudaMalloc(&L->a23_hi, rnk * L->k23 * 2));
@@ -766,7 +788,7 @@ static cudaError_t launch_gram_t(const Plan& p, const LowRank& L, const int* gat
 
 // J^H J v for a fully sampled readout: prep -> phase-encode DFT -> Gram through the TR axis
 // -> adjoint phase-encode DFT -> final, times nx for the cancelled readout DFT pair.
-static int lowrank_jhjv_full_readout(Plan* p, const float* v, float* out, cudaStream_t st) {
+static int lowrank_jhjv_full_readout(Plan* p, const float* v, float* out, double* vdot, cudaStream_t st) {
   LowRank& L = *p->lr;
   const int R = L.R, nx = p->nx, ny = p->ny;
   const int* gate = p->gate;
@@ -798,17 +820,31 @@ static int lowrank_jhjv_full_readout(Plan* p, const float* v, float* out, cudaSt
   }
   if (e == cudaSuccess) {
     Span sp(p, MRSTAT_K_JHW_DOT, st);
-    const dim3 t16((nx + 15) / 16, (ny + 15) / 16);
-    lr_final_t_kernel<<<t16, dim3(16, 16), 0, st>>>(L.Y3, 2 * ny, L.coef, p->rho, p->maskf, nx, ny, p->nv, R,
-                                                     (float)nx, out, gate);
+    const int nchunk = (R + 7) / 8;
+    const dim3 t16((nx + 15) / 16, (ny + 15) / 16, nchunk);
+    lr_final_t_kernel<<<t16, dim3(16, 16), 0, st>>>(L.Y3, 2 * ny, L.coef, p->rho, nx, ny, p->nv, R, L.gpart, gate);
     e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      const int64_t n4 = 4 * (int64_t)p->nv;
+      // one float64 partial per block in the plan's reduction scratch
+      const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n4 + kSumThreads - 1) / kSumThreads, kRedBlocks));
+      lr_final_sum_kernel<<<blocks, kSumThreads, 0, st>>>(L.gpart, nchunk, p->maskf, p->nv, (float)nx, out, gate, v,
+                                                          p->red, p->ticket, vdot);
+      e = cudaGetLastError();
+    }
   }
   return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank J^H J v");
 }
 
-int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st) {
+int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot) {
   LowRank& L = *p->lr;
-  if (L.full_readout) return lowrank_jhjv_full_readout(p, v, out, st);
+  if (L.full_readout) return lowrank_jhjv_full_readout(p, v, out, vdot, st);
+  if (vdot != nullptr) {
+    const int s = lowrank_jhjv(p, v, out, st, nullptr);
+    if (s != MRSTAT_OK) return s;
+    const cudaError_t e = do_dot(p, v, out, 4 * (int64_t)p->nv, vdot, st);
+    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "dot launch");
+  }
   int s = lr_prep(p, v, p->gate, st);
   if (s == MRSTAT_OK) s = lr_forward_dft(p, p->gate, st);
   if (s != MRSTAT_OK) return s;

@@ -21,6 +21,7 @@ struct LowRank {
   int* kytr = nullptr;             // [ntr]
   float* coef = nullptr;           // [3][R][nv]: c, dc/dlnT1, dc/dlnT2 (masked)
   float* coef2 = nullptr;          // [3][R][nv]: trial point of the surrogate Gauss-Newton phase
+  float* gpart = nullptr;          // [ceil(R/8)][4][nv]: per-chunk partial sums of J^H J v
   void *a1_hi = nullptr, *a1_lo = nullptr;    // [R ny][k1]   readout-DFT input rows
   void *a23_hi = nullptr, *a23_lo = nullptr;  // [R nkx][k23] phase-encode DFT input rows
   void *a4_hi = nullptr, *a4_lo = nullptr;    // [R ny][k4]   readout adjoint input rows

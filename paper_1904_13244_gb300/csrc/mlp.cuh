@@ -29,7 +29,7 @@ struct Mlp {
   bool maps_train = false, have_train_buffers = false;
   __nv_bfloat16* X[4] = {nullptr, nullptr, nullptr, nullptr};    // bf16 [M][pad8(in)] layer inputs
   __nv_bfloat16* XT[4] = {nullptr, nullptr, nullptr, nullptr};   // bf16 [in][pad8(3 cap)]
-  float* Z[4] = {nullptr, nullptr, nullptr, nullptr};   // [M][out] pre-activations (no bias)
+  float* Z[4] = {nullptr, nullptr, nullptr, nullptr};   // [M][out] pre-activations (no bias; training)
   __nv_bfloat16* GZ[4] = {nullptr, nullptr, nullptr, nullptr};   // bf16 [M][pad8(out)]
   __nv_bfloat16* GZT[4] = {nullptr, nullptr, nullptr, nullptr};  // bf16 [out][pad8(3 cap)]
   float* GX = nullptr;                                  // [M][H]
@@ -44,7 +44,7 @@ struct Mlp {
   int forward(const float* lnT, const float* b1, int B, bool train, cudaStream_t st);
   int backward(const float* target, int B, cudaStream_t st);
   int adam(float lr, cudaStream_t st);
-  int predict(int B, float* pred, cudaStream_t st);
+  int infer_fused(const float* lnT, const float* b1, int B, float* pred, cudaStream_t st);
   void release_batch();
   void free_weights();
 };

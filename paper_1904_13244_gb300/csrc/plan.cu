@@ -253,8 +253,14 @@ int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* ma
 // J^H J v.  With a fully sampled readout (nkx == nx: kx runs over a whole period of the
 // x frequencies) the readout DFT and its adjoint cancel, F^H F = nx I, so
 // W~ = nx A and the two x-DFTs are skipped: exact, not an approximation.
-int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st) {
-  if (p->lr && p->lr->active) return lowrank_jhjv(p, v, out, st);
+int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot) {
+  if (p->lr && p->lr->active) return lowrank_jhjv(p, v, out, st, vdot);
+  if (vdot != nullptr) {
+    const int s = do_jhjv(p, v, out, st, nullptr);
+    if (s != MRSTAT_OK) return s;
+    const cudaError_t e = do_dot(p, v, out, 4 * (int64_t)p->nv, vdot, st);
+    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "dot launch");
+  }
   if (p->nkx == p->nx) {
     cudaError_t e;
     {
@@ -689,10 +695,10 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
     double* rr = sc + 4 * it;
     double* pq = rr + 1;
     double* rr_next = sc + 4 * (it + 1);
-    int s = do_jhjv(plan, plan->cg_p, plan->cg_q, st);
+    // q = Re(J^H J) p and pq = <p, q>
+    int s = do_jhjv(plan, plan->cg_p, plan->cg_q, st, pq);
     if (s != MRSTAT_OK) return s;
-    e = do_dot(plan, plan->cg_p, plan->cg_q, n, pq, st);
-    if (e == cudaSuccess) {
+    {
       Span sp(plan, MRSTAT_K_VECTOR, st);
       e = launch_cg_update_xr(x, plan->cg_r, plan->cg_p, plan->cg_q, n, rr, pq, plan->cg_frozen, plan->red,
                               plan->ticket, rr_next, st);

@@ -1,0 +1,52 @@
+// Deterministic single-pass reductions shared by the vector kernels: float64 warp and
+// block sums, and the last-block finish (release fence plus an atomic ticket; the last
+// block adds the per-block partials in block order and resets the ticket).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mrstat {
+namespace red {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; the result is valid in thread 0.  Uses `ws` (>= THREADS/32 doubles).
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v, double* ws) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < THREADS / 32) ? ws[threadIdx.x] : 0.0;
+  if (w == 0) v = warp_sum(v);
+  __syncthreads();
+  return v;
+}
+
+// Called by every thread after thread 0 of each block stored its partial in part[blockIdx.x].
+// The last block sums all partials in order into *out.
+template <int THREADS>
+__device__ __forceinline__ void finish_reduction(double* part, unsigned* ticket, double* out, double* ws) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += THREADS) s += ((volatile double*)part)[i];
+  s = block_sum<THREADS>(s, ws);
+  if (threadIdx.x == 0) {
+    *out = s;
+    *ticket = 0u;
+  }
+}
+
+}  // namespace red
+}  // namespace mrstat

@@ -14,136 +14,19 @@
 //   warps 0..3      epilogue: tcgen05.ld 32 lanes x 16 columns per warp, float32 stores.
 // Every mbarrier wait is bounded; on timeout the CTA records an error code, skips the
 // rest of its work, releases its tensor memory and returns.
+#include <algorithm>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cstring>
 
 #include "internal.cuh"
 #include "tc_gemm.cuh"
+#include "tc_prims.cuh"
 
 namespace mrstat {
 namespace {
 
-constexpr int BM = 128, BK = 64;
-constexpr uint32_t kSpinLimit = 1u << 26;
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait on an mbarrier phase: false after kWaitNs of wall time (or kSpinLimit
-// polls), or as soon as another thread of the CTA has given up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  const uint64_t t0 = global_ns();
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255u) == 255u) {
-      if (*abort_flag) return false;
-      if (global_ns() - t0 > kWaitNs) break;
-    }
-  }
-  *abort_flag = 1;
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of 64 BF16
-// (128 B), 8-row swizzle atoms 1024 B apart (stride byte offset), SM100 version 1.
-__device__ __forceinline__ uint64_t sdesc_sw128(const void* tile) {
-  const uint64_t a = smem_u32(tile);
-  uint64_t d = (a >> 4) & 0x3FFFull;   // start address
-  d |= 1ull << 16;                      // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
-  d |= 1ull << 46;                      // descriptor version
-  d |= 2ull << 61;                      // SWIZZLE_128B
-  return d;
-}
-
-// Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t make_idesc(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
+using namespace tc;
 
 template <int BN, int STAGES>
 struct TileShape {
@@ -162,7 +45,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant_
                float* __restrict__ C, int M, int N, int K, int ldc, int nprod, const int* __restrict__ gate,
                int* __restrict__ err) {
   using TS = TileShape<BN, STAGES>;
-  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
+  static_assert(BN == 64 || BN == 128, "N tiles of 64 or 128 columns");
   if (gate != nullptr && *gate == 0) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -239,6 +122,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant_
   }
 
   // ---------------- epilogue ----------------
+  // the other lanes of the producer and MMA warps wait here, not in the spin below, so
+  // that they do not compete with their role lane for the warp's issue slots
+  __syncwarp();
   const bool ok = mbar_wait(done, 0, abort_flag) && *abort_flag == 0;
   __syncwarp();
   fence_after();
@@ -274,6 +160,186 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant_
   fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, TS::kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form (one CTA per SM walks tiles blockIdx.x, + gridDim.x, ...; N tiles of an
+// M tile are consecutive, so CTAs running together share the A rows in L2):
+//   warp 0 lane 0  TMA producer, one ring of STAGES chunks across all of its tiles (the
+//                  ring never drains between tiles);
+//   warp 1 lane 0  MMA issuer into one of two TMEM accumulators (tile i uses i mod 2);
+//   warps 2..5     epilogue: wait for an accumulator, read it with tcgen05.ld (warp w
+//                  reads TMEM lanes 32 (w mod 4) ..), hand it back to the MMA warp, and
+//                  write the tile through a per-warp 32 x 33 float staging block, one
+//                  128-byte row piece per store.
+// The epilogue of tile i overlaps the loads and MMAs of tile i + 1.
+// ---------------------------------------------------------------------------
+template <int BN, int STAGES>
+struct PersistentShape {
+  static constexpr uint32_t kA = BM * BK * 2;
+  static constexpr uint32_t kB = BN * BK * 2;
+  static constexpr uint32_t kStage = 2 * kA + 2 * kB;
+  static constexpr uint32_t kTmemCols = 2 * BN;  // two accumulators (128 or 256: powers of 2)
+  static constexpr uint32_t kOut = 4 * 32 * 33 * 4;
+  static constexpr size_t kSmem = (size_t)STAGES * kStage + kOut + 1024 + 256;
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
+                          const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
+                          float* __restrict__ C, int M, int N, int K, int ldc, int nprod,
+                          const int* __restrict__ gate, int* __restrict__ err) {
+  using PS = PersistentShape<BN, STAGES>;
+  static_assert(BN == 64 || BN == 128, "N tiles of 64 or 128 columns");
+  if (gate != nullptr && *gate == 0) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float* outst = reinterpret_cast<float*>(smem + STAGES * PS::kStage);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * PS::kStage + PS::kOut);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;
+  uint64_t* acce = accf + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tiles = (N + BN - 1) / BN;
+  const int tiles = ((M + BM - 1) / BM) * n_tiles;
+  const int nk = (K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accf[a], 1);
+      mbar_init(&acce[a], 4);  // one arrival per epilogue warp
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, PS::kTmemCols);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      int g = 0;
+      bool go = true;
+      for (int t = blockIdx.x; t < tiles && go; t += gridDim.x) {
+        const int m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+        for (int c = 0; c < nk; ++c, ++g) {
+          const int s = g % STAGES;
+          const uint32_t use = (uint32_t)(g / STAGES);
+          if (g >= STAGES && !mbar_wait(&empty[s], (use - 1) & 1u, abort_flag)) {
+            go = false;
+            break;
+          }
+          uint8_t* a_hi = smem + s * PS::kStage;
+          uint8_t* a_lo = a_hi + PS::kA;
+          uint8_t* b_hi = a_lo + PS::kA;
+          uint8_t* b_lo = b_hi + PS::kB;
+          mbar_expect_tx(&full[s], nprod == 3 ? PS::kStage : PS::kA + PS::kB);
+          tma_load_2d(&ta_hi, &full[s], a_hi, c * BK, m0);
+          tma_load_2d(&tb_hi, &full[s], b_hi, c * BK, n0);
+          if (nprod == 3) {
+            tma_load_2d(&ta_lo, &full[s], a_lo, c * BK, m0);
+            tma_load_2d(&tb_lo, &full[s], b_lo, c * BK, n0);
+          }
+          issued = g + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(BM, BN);
+      int g = 0, i = 0;
+      bool go = true;
+      for (int t = blockIdx.x; t < tiles && go; t += gridDim.x, ++i) {
+        const int acc = i & 1;
+        if (i >= 2 && !mbar_wait(&acce[acc], (uint32_t)((i >> 1) - 1) & 1u, abort_flag)) break;
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        for (int c = 0; c < nk; ++c, ++g) {
+          const int s = g % STAGES;
+          if (!mbar_wait(&full[s], (uint32_t)(g / STAGES) & 1u, abort_flag)) {
+            go = false;
+            break;
+          }
+          fence_after();
+          const uint8_t* a_hi = smem + s * PS::kStage;
+          const uint8_t* a_lo = a_hi + PS::kA;
+          const uint8_t* b_hi = a_lo + PS::kA;
+          const uint8_t* b_lo = b_hi + PS::kB;
+          const uint64_t dah = sdesc_sw128(a_hi), dal = sdesc_sw128(a_lo);
+          const uint64_t dbh = sdesc_sw128(b_hi), dbl = sdesc_sw128(b_lo);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t off = 2ull * k;
+            mma_bf16(d, dah + off, dbh + off, idesc, (c > 0 || k > 0) ? 1u : 0u);
+            if (nprod == 3) {
+              mma_bf16(d, dah + off, dbl + off, idesc, 1u);
+              mma_bf16(d, dal + off, dbh + off, idesc, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        if (go) mma_commit(&accf[acc]);
+      }
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quarter of this warp
+    float* stg = outst + (warp - 2) * 32 * 33;
+    int i = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+      const int acc = i & 1;
+      if (!mbar_wait(&accf[acc], (uint32_t)(i >> 1) & 1u, abort_flag)) break;
+      __syncwarp();
+      fence_after();
+      const int m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+      for (int cb = 0; cb < BN; cb += 32) {
+        float v[32];
+        tmem_ld16(taddr + (uint32_t)cb, *reinterpret_cast<float(*)[16]>(v));
+        tmem_ld16(taddr + (uint32_t)(cb + 16), *reinterpret_cast<float(*)[16]>(v + 16));
+        if (cb + 32 >= BN) {
+          // the whole accumulator is in registers: hand it back to the MMA warp
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acce[acc]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
+        __syncwarp();
+        const int col = n0 + cb + lane;
+        for (int r = 0; r < 32; ++r) {
+          const int row = m0 + q * 32 + r;
+          if (row < M && col < N) C[(size_t)row * ldc + col] = stg[r * 33 + lane];
+        }
+        __syncwarp();
+      }
+    }
+  }
+
+  __syncwarp();
+  if (threadIdx.x == 0 && *abort_flag) {
+    atomicExch(err, 1);
+    // let the copies this thread issued land before the CTA's shared memory goes away
+    for (int g = issued > STAGES ? issued - STAGES : 0; g < issued; ++g) {
+      int spins = 0;
+      while (!mbar_try_wait(&full[g % STAGES], (uint32_t)(g / STAGES) & 1u) && ++spins < (1 << 16)) {
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, PS::kTmemCols);
 }
 
 // x (float, rows x cols, row stride ld_src) -> hi, lo (bf16, rows x ldk, zero padded)
@@ -329,12 +395,7 @@ cudaError_t make_bf16_tmap(CUtensorMap* map, const void* base, int rows, int k, 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-int tc_gemm_tile_n(int n) {
-  if (n >= 224 && n % 224 == 0) return 224;
-  if (n <= 64) return 64;
-  if (n <= 128) return 128;
-  return 256;
-}
+int tc_gemm_tile_n(int n) { return n <= 64 ? 64 : 128; }
 
 cudaError_t make_split_operand(TcOperand* op, const void* hi, const void* lo, int rows, int k, int ldk,
                                bool is_a) {
@@ -348,6 +409,10 @@ cudaError_t make_split_operand(TcOperand* op, const void* hi, const void* lo, in
 }
 
 size_t tc_gemm_smem_bytes() { return TileShape<64, 4>::kSmem; }
+
+// Which of the two schedules launch_tc_gemm uses (persistent by default).
+static bool g_tc_persistent = true;
+void tc_gemm_set_persistent(bool on) { g_tc_persistent = on; }
 
 template <int BN, int STAGES>
 static cudaError_t launch_tile(const TcOperand& a, const TcOperand& b, float* C, int M, int N, int K, int ldc,
@@ -365,18 +430,38 @@ static cudaError_t launch_tile(const TcOperand& a, const TcOperand& b, float* C,
 // The N tile is the B operand's TMA box (chosen from its row count when it was made).
 // Rings: 64-wide tiles with short K loops (<= 8 chunks of 64) use 2 stages so that two
 // CTAs share an SM and one CTA's epilogue overlaps the other's loads, longer ones 4;
-// wider tiles fill about 190 KB of shared memory (one CTA per SM).
+// 128-wide tiles use 3 stages (about 190 KB of shared memory, one CTA per SM).
+template <int BN, int STAGES>
+static cudaError_t launch_persistent(const TcOperand& a, const TcOperand& b, float* C, int M, int N, int K,
+                                     int ldc, int nprod, const int* gate, int* err, cudaStream_t st) {
+  const size_t sm = PersistentShape<BN, STAGES>::kSmem;
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_persistent_kernel<BN, STAGES>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int grid = std::max(1, std::min(tiles, sms));
+  tc_gemm_persistent_kernel<BN, STAGES><<<grid, 192, sm, st>>>(a.hi, a.lo, b.hi, b.lo, C, M, N, K, ldc, nprod,
+                                                               gate, err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tc_gemm(const TcOperand& a, const TcOperand& b, float* C, int M, int N, int K, int ldc,
                            int nprod, const int* gate, int* err, cudaStream_t st) {
   if (M == 0 || N == 0) return cudaSuccess;
   if (a.box != BM) return cudaErrorInvalidValue;
+  if (g_tc_persistent) {
+    if (b.box == 128) return launch_persistent<128, 3>(a, b, C, M, N, K, ldc, nprod, gate, err, st);
+    if (b.box == 64) return launch_persistent<64, 4>(a, b, C, M, N, K, ldc, nprod, gate, err, st);
+    return cudaErrorInvalidValue;
+  }
   switch (b.box) {
     case 64:
       if ((K + BK - 1) / BK <= 8) return launch_tile<64, 2>(a, b, C, M, N, K, ldc, nprod, gate, err, st);
       return launch_tile<64, 4>(a, b, C, M, N, K, ldc, nprod, gate, err, st);
     case 128: return launch_tile<128, 3>(a, b, C, M, N, K, ldc, nprod, gate, err, st);
-    case 224: return launch_tile<224, 2>(a, b, C, M, N, K, ldc, nprod, gate, err, st);
-    case 256: return launch_tile<256, 2>(a, b, C, M, N, K, ldc, nprod, gate, err, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -15,9 +15,7 @@ struct TcOperand {
   int box = 0;  // rows per TMA box: 128 for an A operand, the GEMM's N tile for a B operand
 };
 
-// N tile for a GEMM with N columns (a B operand with N rows): 224 for multiples of 224
-// (exact tiles of the 2 x 224 real-embedded DFTs), else the smallest of 64 / 128 / 256
-// that covers N, 256 beyond.
+// N tile for a GEMM with N columns (a B operand with N rows): 64 up to 64 columns, else 128.
 int tc_gemm_tile_n(int n);
 
 cudaError_t make_bf16_tmap(CUtensorMap* map, const void* base, int rows, int k, int ldk, int box_rows);
@@ -30,6 +28,8 @@ cudaError_t launch_tc_gemm(const TcOperand& a, const TcOperand& b, float* C, int
 cudaError_t launch_split_bf16(const float* x, int rows, int cols, int ld_src, void* hi, void* lo, int ldk,
                               const int* gate, cudaStream_t st);
 size_t tc_gemm_smem_bytes();
+// Persistent schedule (default) or one CTA per output tile.
+void tc_gemm_set_persistent(bool on);
 uint16_t host_bf16(float f);
 float host_bf16_to_float(uint16_t b);
 
