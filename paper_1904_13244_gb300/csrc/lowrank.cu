@@ -415,6 +415,68 @@ lr_gram_t_kernel(const float* __restrict__ HT, int ldh, const float* __restrict_
   for (int r = 0; r < R; ++r) put_split_pair(hi, lo, (size_t)(ix * R + r) * ldk + 2 * ky, out[r]);
 }
 
+// The same Gram product when no ky value has more than kGramShort TRs (one TR per fill
+// for up to 8 fills, the usual sequence): the TR-axis sums s_t stay in registers and each
+// output G[(ix, r)][ky] is written as soon as it is formed, so no R-long output array is
+// held (about half the registers of the general kernel, twice the resident warps).
+constexpr int kGramShort = 8;
+
+template <int R>
+__global__ void __launch_bounds__(256)
+lr_gram_short_kernel(const float* __restrict__ HT, int ldh, const float* __restrict__ Ug,
+                     const int* __restrict__ kyptr, int nx, int ny, __nv_bfloat16* __restrict__ hi,
+                     __nv_bfloat16* __restrict__ lo, int ldk, const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  extern __shared__ float us[];  // [rows of this ky tile][R + 1]
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int ky0 = blockIdx.x * 32;
+  const int t0 = kyptr[ky0], t1 = kyptr[min(ky0 + 32, ny)];
+  for (int e = tid; e < (t1 - t0) * R; e += 256) {
+    const int t = e / R, r = e - t * R;
+    us[t * (R + 1) + r] = Ug[(size_t)t0 * R + e];
+  }
+  __syncthreads();
+  const int ky = ky0 + tx, ix = blockIdx.y * 8 + ty;
+  if (ky >= ny || ix >= nx) return;
+  const float2* H2 = reinterpret_cast<const float2*>(HT);
+  const int ld2 = ldh / 2;
+  const int ta = kyptr[ky], ns = kyptr[ky + 1] - ta;  // ns <= kGramShort
+  float2 sv[kGramShort];
+#pragma unroll
+  for (int k = 0; k < kGramShort; ++k) sv[k] = make_float2(0.f, 0.f);
+  {
+    float2 in[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) in[q] = H2[(size_t)(ix * R + q) * ld2 + ky];
+#pragma unroll
+    for (int k = 0; k < kGramShort; ++k) {
+      if (k < ns) {
+        const float* un = us + (ta + k - t0) * (R + 1);
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          sr = fmaf(un[q], in[q].x, sr);
+          si = fmaf(un[q], in[q].y, si);
+        }
+        sv[k] = make_float2(sr, si);
+      }
+    }
+  }
+#pragma unroll 4
+  for (int r = 0; r < R; ++r) {
+    float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kGramShort; ++k) {
+      if (k < ns) {
+        const float u = us[(ta + k - t0) * (R + 1) + r];
+        o.x = fmaf(u, sv[k].x, o.x);
+        o.y = fmaf(u, sv[k].y, o.y);
+      }
+    }
+    put_split_pair(hi, lo, (size_t)(ix * R + r) * ldk + 2 * ky, o);
+  }
+}
+
 // Partial sums over one chunk of 8 basis functions (blockIdx.z) of
 //   g_k,j = Re sum_r conj(dh_r,j/dv_k) P[(ix, r)][iy]   (P rows (ix, r), columns 2 iy + re/im)
 // into part[z][4][nv].  Block (16, 16): a 16 x 16 voxel tile, one voxel per thread; P
@@ -592,6 +654,7 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   for (int t = 0; t < ntr; ++t)
     for (int r = 0; r < R; ++r) Ug[(size_t)t * R + r] = Uh[(size_t)trs[t] * R + r];
   for (int k0 = 0; k0 < ny; k0 += 32) L->gram_rows_max = std::max(L->gram_rows_max, ptr[std::min(k0 + 32, ny)] - ptr[k0]);
+  for (int k = 0; k < ny; ++k) L->ky_count_max = std::max(L->ky_count_max, ptr[k + 1] - ptr[k]);
   // the cancelled readout DFT pair needs nkx == nx; the Gram kernel keeps a ky tile's rows of U
   // in shared memory
   L->full_readout = p->nkx == p->nx && (size_t)L->gram_rows_max * (R + 1) * sizeof(float) <= (size_t)L->smem_optin;
@@ -777,12 +840,20 @@ int lowrank_jhw(Plan* p, const float2* w, float* g, cudaStream_t st) {
 template <int R>
 static cudaError_t launch_gram_t(const Plan& p, const LowRank& L, const int* gate, cudaStream_t st) {
   const size_t sm = (size_t)L.gram_rows_max * (R + 1) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(lr_gram_t_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
   const dim3 grid((p.ny + 31) / 32, (p.nx + 7) / 8);
-  lr_gram_t_kernel<R><<<grid, dim3(32, 8), sm, st>>>(L.H, 2 * p.ny, L.Ug, L.kyptr, p.nx, p.ny,
-                                                      (__nv_bfloat16*)L.a23_hi, (__nv_bfloat16*)L.a23_lo, L.k23,
-                                                      gate);
+  __nv_bfloat16* hi = (__nv_bfloat16*)L.a23_hi;
+  __nv_bfloat16* lo = (__nv_bfloat16*)L.a23_lo;
+  if (L.ky_count_max <= kGramShort) {
+    cudaError_t e =
+        cudaFuncSetAttribute(lr_gram_short_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    lr_gram_short_kernel<R><<<grid, dim3(32, 8), sm, st>>>(L.H, 2 * p.ny, L.Ug, L.kyptr, p.nx, p.ny, hi, lo, L.k23,
+                                                            gate);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(lr_gram_t_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    lr_gram_t_kernel<R><<<grid, dim3(32, 8), sm, st>>>(L.H, 2 * p.ny, L.Ug, L.kyptr, p.nx, p.ny, hi, lo, L.k23, gate);
+  }
   return cudaGetLastError();
 }
 

@@ -15,6 +15,7 @@ struct LowRank {
   float* U = nullptr;              // [ntr][R] time basis
   float* Ug = nullptr;             // [ntr][R] rows of U in ky order (the order of kytr)
   int gram_rows_max = 0;           // most TRs of any 32 consecutive ky values
+  int ky_count_max = 0;            // most TRs of any single ky value
   int smem_optin = 0;              // opt-in shared memory per block
   float* Mky = nullptr;            // [ny][R][R] per-ky Gram of U rows
   int* kyptr = nullptr;            // [ny + 1] TR lists per ky residue
