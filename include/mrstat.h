@@ -11,9 +11,10 @@
  * ---------------------------------------
  *  - Image grid nx (readout, x) by ny (phase encode, y); nv = nx * ny voxels; voxel
  *    j = iy * nx + ix (ix fastest).
- *  - Parameter maps alpha are float32 [4][nv] in DEVICE memory, parameter-major
+ *  - Parameter maps alpha are float32 [npar][nv] in DEVICE memory, parameter-major
  *    (Theory: index j + k Nv): k = 0 ln(T1/ms), 1 ln(T2/ms), 2 Re rho, 3 Im rho
- *    (log scaling of T1 and T2: Methods, "Reconstructions").
+ *    (log scaling of T1 and T2: Methods, "Reconstructions"), and k = 4 B1 for plans
+ *    created with MRSTAT_ESTIMATE_B1 (npar = 5; otherwise npar = 4).
  *  - k-space vectors (s, d, J.v, w) are interleaved complex float32 [ntr][nkx][2]
  *    in DEVICE memory; TR n samples the phase-encode line ky[n] and readout points
  *    kx = k - nkx/2, k = 0..nkx-1; the encoding phase is exp(-2 pi i (kx ix/nx +
@@ -92,15 +93,29 @@ typedef struct mrstat_plan_info_t {
   int32_t ntr_padded;          /* ntr rounded up to a multiple of 4 (TR quads)      */
   int64_t device_bytes;        /* device memory owned by the plan                   */
   int64_t timecourse_bytes;    /* of which the cached time courses D                */
+  int32_t npar;                /* unknowns per voxel: 4, or 5 with B1 estimated     */
 } mrstat_plan_info_t;
+
+/*
+ * OR this flag into the form of mrstat_plan_create to make B1 the fifth unknown per
+ * voxel (the paper estimates B1 along with T1, T2 and rho: Methods, "Reconstructions";
+ * the derivative of the Bloch recursion with respect to B1 is the S2 forward-mode
+ * derivative through the rotation angle).  Such a plan works on npar = 5 rows
+ * alpha = (ln T1, ln T2, Re rho, Im rho, B1): every [4][nv] below becomes [5][nv], the
+ * time courses carry a fourth channel dm_y/dB1, the b1 arguments must be NULL (B1 is
+ * alpha row 4), and the low-rank and checkpointed entry points return UNSUPPORTED.
+ */
+#define MRSTAT_ESTIMATE_B1 0x100
 
 /*
  * Create a plan: validates the sequence, builds the per-TR rotation and phase
  * tables and allocates the small work buffers (x-DFT matrices, reduction scratch,
  * CG vectors).  The large buffers are allocated by the first call that needs them:
- * the cached time courses D (3 x ntr_padded x nv float32) by mrstat_linearize, the
+ * the cached time courses D (3 x ntr_padded x nv float32, 4 x with B1 estimated) by
+ * mrstat_linearize, the
  * m_y scratch (ntr_padded x nv float32) by mrstat_forward / mrstat_forward_ckpt.  Synchronises the current device once.  On failure *out is
- * set to NULL.  Errors: INVALID_ARG (null seq/out/arrays, bad form, non-finite or
+ * set to NULL.  form: a mrstat_form, optionally | MRSTAT_ESTIMATE_B1.
+ * Errors: INVALID_ARG (null seq/out/arrays, bad form, non-finite or
  * negative flips, te/tr), SHAPE (sizes outside the ranges above, ky out of range),
  * OUT_OF_MEMORY, CUDA.
  */
@@ -124,12 +139,14 @@ int mrstat_plan_check(mrstat_plan* plan);
  * forward-mode derivatives of Supporting Information S2): runs the Bloch recursion
  * of every voxel and caches m_y and dm_y/dln T1, dm_y/dln T2 at every echo, plus
  * rho and the mask, for later mrstat_jvp / mrstat_jhw / mrstat_timecourses calls.
- *   alpha: device float [4][nv] (see top).
- *   b1:    device float [nv] relative transmit field, or NULL for B1 = 1.
+ *   alpha: device float [npar][nv] (see top; row 4 = B1 when B1 is estimated, and then
+ *          a fourth channel dm_y/dB1 is cached).
+ *   b1:    device float [nv] relative transmit field, or NULL for B1 = 1 (must be NULL
+ *          when B1 is estimated).
  *   mask:  device uint8 [nv], nonzero = voxel takes part, or NULL for all voxels
  *          (Methods: voxels without significant proton density are excluded; a
  *          masked-out voxel contributes nothing to s and gets zero gradient).
- * Errors: INVALID_ARG (null plan/alpha), CUDA.
+ * Errors: INVALID_ARG (null plan/alpha, b1 given with B1 estimated), CUDA.
  */
 int mrstat_linearize(mrstat_plan* plan, const float* alpha, const float* b1,
                      const uint8_t* mask, void* stream);
@@ -144,8 +161,8 @@ int mrstat_forward(mrstat_plan* plan, const float* alpha, const float* b1,
 
 /*
  * jv = J_s v at the cached linearisation ("Similar techniques ... J v", text before
- * Eq. 4): jv = encode(rho (v0 dm/dlnT1 + v1 dm/dlnT2) + (v2 + i v3) m).
- *   v: device float [4][nv];  jv: device float [ntr][nkx][2].
+ * Eq. 4): jv = encode(rho (v0 dm/dlnT1 + v1 dm/dlnT2 [+ v4 dm/dB1]) + (v2 + i v3) m).
+ *   v: device float [npar][nv];  jv: device float [ntr][nkx][2].
  * Errors: INVALID_ARG, NOT_LINEARIZED, CUDA.
  */
 int mrstat_jvp(mrstat_plan* plan, const float* v, float* jv, void* stream);
@@ -153,14 +170,14 @@ int mrstat_jvp(mrstat_plan* plan, const float* v, float* jv, void* stream);
 /*
  * g = Re(J_s^H w) at the cached linearisation (Algorithm 4 with J_s = -J):
  * g[k][j] = Re sum_{n,kx} conj(d(rho_j m_j[n])/dalpha_k exp(-i k.r_j)) w[n][kx].
- *   w: device float [ntr][nkx][2];  g: device float [4][nv] (zero outside the mask).
+ *   w: device float [ntr][nkx][2];  g: device float [npar][nv] (zero outside the mask).
  * Errors: INVALID_ARG, NOT_LINEARIZED, CUDA.
  */
 int mrstat_jhw(mrstat_plan* plan, const float* w, float* g, void* stream);
 
 /*
  * Copy one cached time course channel out of the plan: channel 0 = m_y, 1 =
- * dm_y/dln T1, 2 = dm_y/dln T2 at every echo (the echo signal is i * m_y because
+ * dm_y/dln T1, 2 = dm_y/dln T2 (3 = dm_y/dB1 when B1 is estimated) at every echo (the echo signal is i * m_y because
  * the RF phases 0/180 keep m_x = 0; Supporting Information S2).
  *   out: device float [ntr][nv].  Masked-out voxels read as 0.
  * Errors: INVALID_ARG (bad channel), NOT_LINEARIZED, CUDA.
@@ -190,7 +207,7 @@ int mrstat_jhw_ckpt(mrstat_plan* plan, const float* w, float* g, void* stream);
  * (Eq. 4: first y = J v, then Re(J^H y)), with the plan's current linearisation:
  * mrstat_jvp then mrstat_jhw after mrstat_linearize, or the per-ky Gram product of the
  * low-rank form after mrstat_lowrank_linearize.
- *   v, out: device float [4][nv].
+ *   v, out: device float [npar][nv].
  * Errors: INVALID_ARG, NOT_LINEARIZED, CUDA.
  */
 int mrstat_jhjv(mrstat_plan* plan, const float* v, float* out, void* stream);
@@ -329,7 +346,7 @@ int mrstat_dot_static(const float* a, const float* b, int64_t n, double* out, vo
  * mrstat_jhw) plus float64 inner products; every scalar stays on the device.  An
  * iteration whose curvature p.Hp is not positive, or whose residual is exactly
  * zero, freezes x for the remaining iterations.
- *   rhs, x: device float [4][nv].  iters >= 0.
+ *   rhs, x: device float [npar][nv].  iters >= 0.
  * Errors: INVALID_ARG, NOT_LINEARIZED, CUDA.
  */
 int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters,
@@ -359,6 +376,9 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
  * the solver re-evaluates the objective with the exact model and continues with it, so
  * the result is the exact model's minimiser; the report's f[] shows the switch.
  *
+ * With B1 estimated (MRSTAT_ESTIMATE_B1) every vector has npar = 5 rows; hessian = 1 and
+ * surrogate_iters > 0 are then UNSUPPORTED.
+ *
  * With opts->hessian = 1 the CG uses the low-rank Gauss-Newton matrix of the plan's
  * time basis (the compressed model's Re(J^H J), recomputed at every accepted point by
  * projecting the exact recursion onto the basis), while gradient, objective and the
@@ -369,7 +389,8 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
  * outer iteration to evaluate the trust-region ratio.  On return the plan holds the
  * linearisation at the returned alpha.
  *   d:      device float [ntr][nkx][2] measured k-space data.
- *   alpha:  device float [4][nv], initial guess in, estimate out.
+ *   alpha:  device float [npar][nv], initial guess in, estimate out (B1 in row 4 when
+ *           estimated; reflected into [b1_min, b1_max] like T1 and T2).
  *   b1:     device float [nv] or NULL (B1 = 1); a known map, not estimated.
  *   mask:   device uint8 [nv]: in, the voxels to fit (NULL = all), unless a mask is
  *           drawn, in which case it is written (must then be non-NULL).
@@ -408,6 +429,7 @@ typedef struct mrstat_gn_opts {
                                   trust-region ratio); the rest on the exact model       */
   const mrstat_mlp* surrogate; /* required when surrogate_iters > 0; its rank must equal
                                   the plan's basis rank                                  */
+  double b1_min, b1_max;       /* B1 box when B1 is estimated                           */
 } mrstat_gn_opts;
 
 typedef struct mrstat_gn_report {
@@ -426,7 +448,8 @@ typedef struct mrstat_gn_report {
 
 /* Fill opts with the defaults: 10 x 20 iterations, delta0 from alpha_0, eta = 1e-4,
    no CG tolerance, T1 in [50, 6000] ms, T2 in [5, 3000] ms, no rho initialisation
-   (t1_init 1000 ms, t2_init 100 ms, 50 CGLS steps and threshold 0.1 when enabled). */
+   (t1_init 1000 ms, t2_init 100 ms, 50 CGLS steps and threshold 0.1 when enabled),
+   B1 in [0.5, 1.5] (start B1 = 1 with the rho initialisation). */
 void mrstat_gn_default_opts(mrstat_gn_opts* opts);
 
 int mrstat_gn_solve(mrstat_plan* plan, const float* d, float* alpha, const float* b1,

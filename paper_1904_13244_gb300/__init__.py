@@ -16,7 +16,7 @@ from __future__ import annotations
 import torch
 
 from . import _binding as _b
-from ._binding import (MrstatError, MRSTAT_FORM_PLAIN_FP32, MRSTAT_FORM_SPLIT_BF16,  # noqa: F401
+from ._binding import (MrstatError, MRSTAT_FORM_PLAIN_FP32, MRSTAT_FORM_SPLIT_BF16, MRSTAT_ESTIMATE_B1,  # noqa: F401
                        mrstat_plan_create, mrstat_plan_destroy, mrstat_plan_info, mrstat_linearize,
                        mrstat_forward, mrstat_jvp, mrstat_jhw, mrstat_timecourses, mrstat_dot,
                        mrstat_cg_fixed, mrstat_status_string, mrstat_last_error,
@@ -39,11 +39,13 @@ def load():
 class Plan:
     """Owns one mrstat_plan (device tables and the cached linearisation)."""
 
-    def __init__(self, seq, form: int = MRSTAT_FORM_PLAIN_FP32):
+    def __init__(self, seq, form: int = MRSTAT_FORM_PLAIN_FP32, estimate_b1: bool = False):
+        """estimate_b1: B1 is the fifth unknown (alpha, v, g and the GN vectors get 5 rows)."""
         self.nx, self.ny, self.nkx = int(seq.nx), int(seq.ny), int(seq.nkx)
         self.ntr = int(len(seq.flip_rad))
         self.nv = self.nx * self.ny
-        self._h = mrstat_plan_create(seq, form)
+        self.npar = 5 if estimate_b1 else 4
+        self._h = mrstat_plan_create(seq, form | (MRSTAT_ESTIMATE_B1 if estimate_b1 else 0))
 
     # -- life cycle --
     def close(self):
@@ -82,7 +84,7 @@ class Plan:
 
     def _params(self, out):
         if out is None:
-            out = torch.empty((4, self.nv), dtype=torch.float32, device="cuda")
+            out = torch.empty((self.npar, self.nv), dtype=torch.float32, device="cuda")
         return out
 
     def linearize(self, alpha, b1=None, mask=None, stream=None):

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmrstat.so")
 MRSTAT_OK = 0
 MRSTAT_FORM_PLAIN_FP32 = 0
 MRSTAT_FORM_SPLIT_BF16 = 1
+MRSTAT_ESTIMATE_B1 = 0x100
 
 
 class MrstatError(RuntimeError):
@@ -37,7 +38,7 @@ class mrstat_plan_info_t(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nkx", ctypes.c_int32),
                 ("ntr", ctypes.c_int32), ("nv", ctypes.c_int32), ("form", ctypes.c_int32),
                 ("ntr_padded", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("timecourse_bytes", ctypes.c_int64)]
+                ("timecourse_bytes", ctypes.c_int64), ("npar", ctypes.c_int32)]
 
 
 class mrstat_kernel_stats(ctypes.Structure):
@@ -56,7 +57,7 @@ class mrstat_gn_opts(ctypes.Structure):
                 ("rho_init_iters", ctypes.c_int32), ("t1_init_ms", ctypes.c_double),
                 ("t2_init_ms", ctypes.c_double), ("mask_threshold", ctypes.c_double),
                 ("hessian", ctypes.c_int32), ("surrogate_iters", ctypes.c_int32),
-                ("surrogate", ctypes.c_void_p)]
+                ("surrogate", ctypes.c_void_p), ("b1_min", ctypes.c_double), ("b1_max", ctypes.c_double)]
 
 
 class mrstat_gn_report(ctypes.Structure):
@@ -171,6 +172,14 @@ def _stream(stream):
 _dims_cache = {}
 
 
+def _npar(plan) -> int:
+    """Unknowns per voxel of a plan (4, or 5 with B1 estimated)."""
+    key = ("npar", plan.value if isinstance(plan, ctypes.c_void_p) else plan)
+    if key not in _dims_cache:
+        _dims_cache[key] = mrstat_plan_info(plan)["npar"]
+    return _dims_cache[key]
+
+
 def _dims(plan):
     """(nv, ntr, nkx) of a plan, from mrstat_plan_info (cached per handle)."""
     key = plan.value if isinstance(plan, ctypes.c_void_p) else plan
@@ -212,7 +221,9 @@ def mrstat_plan_create(seq, form: int = MRSTAT_FORM_PLAIN_FP32) -> ctypes.c_void
 
 
 def mrstat_plan_destroy(plan):
-    _dims_cache.pop(plan.value if isinstance(plan, ctypes.c_void_p) else plan, None)
+    key = plan.value if isinstance(plan, ctypes.c_void_p) else plan
+    _dims_cache.pop(key, None)
+    _dims_cache.pop(("npar", key), None)
     _check(load().mrstat_plan_destroy(plan), "mrstat_plan_destroy")
 
 
@@ -228,7 +239,8 @@ def mrstat_plan_check(plan):
 
 def mrstat_linearize(plan, alpha, b1=None, mask=None, stream=None):
     nv, _, _ = _dims(plan)
-    _check(load().mrstat_linearize(plan, _ptr(alpha, torch.float32, (4, nv), "alpha"),
+    npar = _npar(plan)
+    _check(load().mrstat_linearize(plan, _ptr(alpha, torch.float32, (npar, nv), "alpha"),
                                    _ptr(b1, torch.float32, (nv,), "b1"),
                                    _ptr(mask, torch.uint8, (nv,), "mask"), _stream(stream)),
            "mrstat_linearize")
@@ -236,21 +248,24 @@ def mrstat_linearize(plan, alpha, b1=None, mask=None, stream=None):
 
 def mrstat_forward(plan, alpha, b1, mask, s, stream=None):
     nv, ntr, nkx = _dims(plan)
-    _check(load().mrstat_forward(plan, _ptr(alpha, torch.float32, (4, nv), "alpha"),
+    npar = _npar(plan)
+    _check(load().mrstat_forward(plan, _ptr(alpha, torch.float32, (npar, nv), "alpha"),
                                  _ptr(b1, torch.float32, (nv,), "b1"), _ptr(mask, torch.uint8, (nv,), "mask"),
                                  _ptr(s, torch.complex64, (ntr, nkx), "s"), _stream(stream)), "mrstat_forward")
 
 
 def mrstat_jvp(plan, v, jv, stream=None):
     nv, ntr, nkx = _dims(plan)
-    _check(load().mrstat_jvp(plan, _ptr(v, torch.float32, (4, nv), "v"),
+    npar = _npar(plan)
+    _check(load().mrstat_jvp(plan, _ptr(v, torch.float32, (npar, nv), "v"),
                              _ptr(jv, torch.complex64, (ntr, nkx), "jv"), _stream(stream)), "mrstat_jvp")
 
 
 def mrstat_jhw(plan, w, g, stream=None):
     nv, ntr, nkx = _dims(plan)
+    npar = _npar(plan)
     _check(load().mrstat_jhw(plan, _ptr(w, torch.complex64, (ntr, nkx), "w"),
-                             _ptr(g, torch.float32, (4, nv), "g"), _stream(stream)), "mrstat_jhw")
+                             _ptr(g, torch.float32, (npar, nv), "g"), _stream(stream)), "mrstat_jhw")
 
 
 def mrstat_forward_ckpt(plan, alpha, b1, mask, interval, s, stream=None):
@@ -269,7 +284,8 @@ def mrstat_jhw_ckpt(plan, w, g, stream=None):
 
 def mrstat_jhjv(plan, v, out, stream=None):
     nv, _, _ = _dims(plan)
-    _check(load().mrstat_jhjv(plan, _ptr(v, torch.float32, (4, nv), "v"), _ptr(out, torch.float32, (4, nv), "out"),
+    npar = _npar(plan)
+    _check(load().mrstat_jhjv(plan, _ptr(v, torch.float32, (npar, nv), "v"), _ptr(out, torch.float32, (npar, nv), "out"),
                               _stream(stream)), "mrstat_jhjv")
 
 
@@ -326,8 +342,9 @@ def mrstat_dot(plan, a, b, n, out, stream=None):
 
 def mrstat_cg_fixed(plan, rhs, x, iters, stream=None):
     nv, _, _ = _dims(plan)
-    _check(load().mrstat_cg_fixed(plan, _ptr(rhs, torch.float32, (4, nv), "rhs"),
-                                  _ptr(x, torch.float32, (4, nv), "x"), int(iters), _stream(stream)),
+    npar = _npar(plan)
+    _check(load().mrstat_cg_fixed(plan, _ptr(rhs, torch.float32, (npar, nv), "rhs"),
+                                  _ptr(x, torch.float32, (npar, nv), "x"), int(iters), _stream(stream)),
            "mrstat_cg_fixed")
 
 
@@ -347,10 +364,11 @@ def mrstat_gn_default_opts(**overrides) -> mrstat_gn_opts:
 
 def mrstat_gn_solve(plan, d, alpha, b1=None, mask=None, opts=None, stream=None) -> dict:
     nv, ntr, nkx = _dims(plan)
+    npar = _npar(plan)
     opts = opts if opts is not None else mrstat_gn_default_opts()
     rep = mrstat_gn_report()
     _check(load().mrstat_gn_solve(plan, _ptr(d, torch.complex64, (ntr, nkx), "d"),
-                                  _ptr(alpha, torch.float32, (4, nv), "alpha"), _ptr(b1, torch.float32, (nv,), "b1"),
+                                  _ptr(alpha, torch.float32, (npar, nv), "alpha"), _ptr(b1, torch.float32, (nv,), "b1"),
                                   _ptr(mask, torch.uint8, (nv,), "mask"), ctypes.byref(opts), ctypes.byref(rep),
                                   _stream(stream)), "mrstat_gn_solve")
     k = rep.iterations

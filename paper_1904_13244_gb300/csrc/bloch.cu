@@ -14,6 +14,10 @@
 // Tangents with respect to ln T1 and ln T2 (T1 and T2 times the S2 d/dT form):
 //     the rotation acts on them unchanged (k and theta do not depend on T1, T2);
 //     decay adds (dt/T1) E1 (m_z - 1) to dm_z/dlnT1 and (dt/T2) E2 m_y to dm_y/dlnT2.
+// With B1 as an unknown (NCH = 4) a fourth channel carries dm/dB1: the rotation angle is
+// phi_n B1, so the rotation maps the B1 tangent t to R t + phi_n (m_z', -m_y') with m'
+// the rotated magnetisation (the derivative of R(theta) m with respect to theta), and
+// the decay scales it like m without a source term.
 // Four consecutive TRs are written as one float4 per channel: D[c][n/4][j] holds
 // TRs 4(n/4)..4(n/4)+3 of voxel j, so a warp stores 512 contiguous bytes.
 #include "internal.cuh"
@@ -55,15 +59,17 @@ bloch_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
   float my = 0.f, mz = m0z;   // magnetisation
   float ay = 0.f, az = 0.f;   // d m / d ln T1
   float by = 0.f, bz = 0.f;   // d m / d ln T2
+  float cy = 0.f, cz = 0.f;   // d m / d B1 (NCH = 4)
 
   for (int q = 0; q < nq; ++q) {
-    float o0[4], o1[4], o2[4];
+    float o0[4], o1[4], o2[4], o3[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int n = 4 * q + k;
       float c, s;
+      const float phn = (B1MAP || NCH > 3) ? __ldg(phi + n) : 0.f;
       if (B1MAP) {
-        sincosf(__ldg(phi + n) * bj, &s, &c);
+        sincosf(phn * bj, &s, &c);
       } else {
         const float2 t = __ldg(cs + n);
         c = t.x;
@@ -81,6 +87,12 @@ bloch_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
         bz = c * bz - s * by;
         by = ty;
       }
+      if (NCH > 3) {
+        ty = c * cy + s * cz;
+        cz = c * cz - s * cy;
+        cy = fmaf(phn, mz, ty);
+        cz = fmaf(-phn, my, cz);
+      }
       // decay and regrowth over TE: m += (E - 1) o (m - m_eq), tangents gain their source terms
       float zm1 = mz - 1.f;
       if (NCH > 1) {
@@ -89,6 +101,10 @@ bloch_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
         by = fmaf(x2a, by, fmaf(d2a, my, by));
         bz = fmaf(x1a, bz, bz);
       }
+      if (NCH > 3) {
+        cy = fmaf(x2a, cy, cy);
+        cz = fmaf(x1a, cz, cz);
+      }
       my = fmaf(x2a, my, my);
       mz = fmaf(x1a, zm1, mz);
       o0[k] = my;
@@ -96,6 +112,7 @@ bloch_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
         o1[k] = ay;
         o2[k] = by;
       }
+      if (NCH > 3) o3[k] = cy;
       // decay and regrowth over TR - TE
       zm1 = mz - 1.f;
       if (NCH > 1) {
@@ -103,6 +120,10 @@ bloch_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
         az = fmaf(x1b, az, fmaf(d1b, zm1, az));
         by = fmaf(x2b, by, fmaf(d2b, my, by));
         bz = fmaf(x1b, bz, bz);
+      }
+      if (NCH > 3) {
+        cy = fmaf(x2b, cy, cy);
+        cz = fmaf(x1b, cz, cz);
       }
       my = fmaf(x2b, my, my);
       mz = fmaf(x1b, zm1, mz);
@@ -112,6 +133,7 @@ bloch_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
       __stcs(out + cstride + (size_t)q * nv, make_float4(o1[0], o1[1], o1[2], o1[3]));
       __stcs(out + 2 * cstride + (size_t)q * nv, make_float4(o2[0], o2[1], o2[2], o2[3]));
     }
+    if (NCH > 3) __stcs(out + 3 * cstride + (size_t)q * nv, make_float4(o3[0], o3[1], o3[2], o3[3]));
   }
 }
 
@@ -136,6 +158,9 @@ cudaError_t launch_t(const Plan& p, const float* alpha, const float* b1, const u
 cudaError_t launch_bloch(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,
                          float4* D, int nch, cudaStream_t st) {
   if (p.nv == 0) return cudaSuccess;
+  // with B1 estimated, B1 is alpha row 4
+  if (p.npar == 5) b1 = alpha + 4 * (size_t)p.nv;
+  if (nch == 4) return launch_t<4>(p, alpha, b1, mask, D, st);
   return nch == 1 ? launch_t<1>(p, alpha, b1, mask, D, st)
                   : launch_t<kChannels>(p, alpha, b1, mask, D, st);
 }

@@ -47,7 +47,7 @@ __global__ void prep_rho_kernel(const float2* __restrict__ rho, int nv, float2* 
 }
 
 __global__ void prep_jvp_kernel(const float* __restrict__ v, const float2* __restrict__ rho,
-                                const float* __restrict__ maskf, int nv, float2* __restrict__ cf,
+                                const float* __restrict__ maskf, int nv, int nch, float2* __restrict__ cf,
                                 const int* __restrict__ gate) {
   if (gate != nullptr && *gate == 0) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -58,6 +58,10 @@ __global__ void prep_jvp_kernel(const float* __restrict__ v, const float2* __res
   cf[j] = make_float2(v[2 * nv + j] * m, v[3 * nv + j] * m);
   cf[nv + j] = make_float2(r.x * v0, r.y * v0);
   cf[2 * nv + j] = make_float2(r.x * v1, r.y * v1);
+  if (nch > 3) {
+    const float v4 = v[4 * (size_t)nv + j];
+    cf[3 * (size_t)nv + j] = make_float2(r.x * v4, r.y * v4);
+  }
 }
 
 __device__ __forceinline__ int mod_small(int a, int n, float inv_n) {
@@ -111,21 +115,23 @@ ycontract_kernel(const float4* __restrict__ D, const float2* __restrict__ cf,
     for (int iy = ty; iy < ny; iy += 8) {
       const int j = iy * nx + ix;
       const float2 c0 = __ldg(cf + j);
-      float2 c1 = make_float2(0.f, 0.f), c2 = c1;
+      float2 c1 = make_float2(0.f, 0.f), c2 = c1, c3 = c1;
       if (NCH > 1) {
         c1 = __ldg(cf + nv + j);
         c2 = __ldg(cf + 2 * nv + j);
       }
+      if (NCH > 3) c3 = __ldg(cf + 3 * (size_t)nv + j);
 #pragma unroll
       for (int qb = 0; qb < QB; ++qb) {
         const int q = q0 + qb;
         if (q >= nq) break;
         const float4 y0 = __ldg(D + (size_t)q * nv + j);
-        float4 y1 = make_float4(0.f, 0.f, 0.f, 0.f), y2 = y1;
+        float4 y1 = make_float4(0.f, 0.f, 0.f, 0.f), y2 = y1, y3 = y1;
         if (NCH > 1) {
           y1 = __ldg(D + cstride + (size_t)q * nv + j);
           y2 = __ldg(D + 2 * cstride + (size_t)q * nv + j);
         }
+        if (NCH > 3) y3 = __ldg(D + 3 * cstride + (size_t)q * nv + j);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const float a0 = f4get(y0, k);
@@ -134,6 +140,11 @@ ycontract_kernel(const float4* __restrict__ D, const float2* __restrict__ cf,
             const float a1 = f4get(y1, k), a2 = f4get(y2, k);
             pr = fmaf(c1.x, a1, fmaf(c2.x, a2, pr));
             pi = fmaf(c1.y, a1, fmaf(c2.y, a2, pi));
+          }
+          if (NCH > 3) {
+            const float a3 = f4get(y3, k);
+            pr = fmaf(c3.x, a3, pr);
+            pi = fmaf(c3.y, a3, pi);
           }
           // Q = i P = (-pi, pr); acc += E * Q
           const float2 e = ey[(qb * 4 + k) * ny + iy];
@@ -169,29 +180,33 @@ ycontract_kernel(const float4* __restrict__ D, const float2* __restrict__ cf,
 // K4: g = Re(J^H w) from Wt.  block (32, 8): lanes over 32 consecutive voxels, warps
 // over 8 segments of the TR quads; partial sums reduced through shared memory.
 // ---------------------------------------------------------------------------
+template <int NCH>
 __global__ void __launch_bounds__(256)
 jhw_dot_kernel(const float4* __restrict__ D, const float2* __restrict__ wt,
                const int* __restrict__ kyi, const float2* __restrict__ roots_g,
                const float2* __restrict__ rho, const float* __restrict__ maskf, int nx, int ny,
                int nv, int nq, float inv_ny, float scale, float* __restrict__ g, const int* __restrict__ gate) {
+  constexpr int NZ = 2 * NCH;  // real and imaginary part per channel
   if (gate != nullptr && *gate == 0) return;
   extern __shared__ float2 smem[];
   float2* roots = smem;                                  // [ny]
-  float* red = reinterpret_cast<float*>(smem + ny);      // [8][6][32]
+  float* red = reinterpret_cast<float*>(smem + ny);      // [8][NZ][32]
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   for (int e = tid; e < ny; e += 256) roots[e] = roots_g[e];
   __syncthreads();
 
   const int j = blockIdx.x * 32 + tx;
-  float z0r = 0.f, z0i = 0.f, z1r = 0.f, z1i = 0.f, z2r = 0.f, z2i = 0.f;
+  float z[NZ];
+#pragma unroll
+  for (int c = 0; c < NZ; ++c) z[c] = 0.f;
   if (j < nv) {
     const int iy = j / nx, ix = j - iy * nx;
     const int qa = (int)(((long long)nq * ty) / 8), qe = (int)(((long long)nq * (ty + 1)) / 8);
     const size_t cstride = (size_t)nq * nv;
     for (int q = qa; q < qe; ++q) {
-      const float4 y0 = __ldg(D + (size_t)q * nv + j);
-      const float4 y1 = __ldg(D + cstride + (size_t)q * nv + j);
-      const float4 y2 = __ldg(D + 2 * cstride + (size_t)q * nv + j);
+      float4 y[NCH];
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) y[c] = __ldg(D + c * cstride + (size_t)q * nv + j);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int n = 4 * q + k;
@@ -200,30 +215,25 @@ jhw_dot_kernel(const float4* __restrict__ D, const float2* __restrict__ wt,
         // u = conj(Ey) * Wt
         const float ur = fmaf(e.x, w.x, e.y * w.y);
         const float ui = fmaf(e.x, w.y, -e.y * w.x);
-        const float a0 = f4get(y0, k), a1 = f4get(y1, k), a2 = f4get(y2, k);
-        z0r = fmaf(a0, ur, z0r);
-        z0i = fmaf(a0, ui, z0i);
-        z1r = fmaf(a1, ur, z1r);
-        z1i = fmaf(a1, ui, z1i);
-        z2r = fmaf(a2, ur, z2r);
-        z2i = fmaf(a2, ui, z2i);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          const float a = f4get(y[c], k);
+          z[2 * c] = fmaf(a, ur, z[2 * c]);
+          z[2 * c + 1] = fmaf(a, ui, z[2 * c + 1]);
+        }
       }
     }
   }
-  red[(ty * 6 + 0) * 32 + tx] = z0r;
-  red[(ty * 6 + 1) * 32 + tx] = z0i;
-  red[(ty * 6 + 2) * 32 + tx] = z1r;
-  red[(ty * 6 + 3) * 32 + tx] = z1i;
-  red[(ty * 6 + 4) * 32 + tx] = z2r;
-  red[(ty * 6 + 5) * 32 + tx] = z2i;
+#pragma unroll
+  for (int c = 0; c < NZ; ++c) red[(ty * NZ + c) * 32 + tx] = z[c];
   __syncthreads();
   if (ty == 0 && j < nv) {
-    float s[6];
+    float s[NZ];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
+    for (int c = 0; c < NZ; ++c) {
       float a = 0.f;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) a += red[(w * 6 + c) * 32 + tx];
+      for (int w = 0; w < 8; ++w) a += red[(w * NZ + c) * 32 + tx];
       s[c] = a * scale;
     }
     const float2 r = rho[j];
@@ -232,6 +242,7 @@ jhw_dot_kernel(const float4* __restrict__ D, const float2* __restrict__ wt,
     g[nv + j] = (r.x * s[5] - r.y * s[4]) * m;      // Im(conj(rho) Z2)
     g[2 * nv + j] = s[1] * m;                       // Im(Z0)
     g[3 * nv + j] = -s[0] * m;                      // -Re(Z0)
+    if (NCH > 3) g[4 * (size_t)nv + j] = (r.x * s[7] - r.y * s[6]) * m;  // Im(conj(rho) Z3): B1
   }
 }
 
@@ -271,7 +282,7 @@ cudaError_t launch_prep_rho(const Plan& p, const float2* rho, cudaStream_t st) {
 
 cudaError_t launch_prep_jvp(const Plan& p, const float* v, cudaStream_t st) {
   if (p.nv == 0) return cudaSuccess;
-  prep_jvp_kernel<<<(p.nv + 255) / 256, 256, 0, st>>>(v, p.rho, p.maskf, p.nv, p.cf, p.gate);
+  prep_jvp_kernel<<<(p.nv + 255) / 256, 256, 0, st>>>(v, p.rho, p.maskf, p.nv, p.nch, p.cf, p.gate);
   return cudaGetLastError();
 }
 
@@ -286,6 +297,11 @@ cudaError_t launch_ycontract(const Plan& p, const float4* D, int nch, cudaStream
       cudaFuncSetAttribute(ycontract_kernel<1, kQB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     ycontract_kernel<1, kQB><<<grid, block, sm, st>>>(D, p.cf, p.kyi, p.roots, p.nx, p.ny, p.nv,
                                                       p.nq, p.ntr, inv_ny, p.A, p.gate);
+  } else if (nch == 4) {
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(ycontract_kernel<4, kQB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    ycontract_kernel<4, kQB><<<grid, block, sm, st>>>(D, p.cf, p.kyi, p.roots, p.nx, p.ny, p.nv, p.nq, p.ntr,
+                                                      inv_ny, p.A, p.gate);
   } else {
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(ycontract_kernel<kChannels, kQB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -296,16 +312,21 @@ cudaError_t launch_ycontract(const Plan& p, const float4* D, int nch, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_jhw_dot(const Plan& p, float* g, cudaStream_t st, const float2* wt, float scale) {
-  if (p.nv == 0) return cudaSuccess;
+template <int NCH>
+static cudaError_t launch_jhw_dot_t(const Plan& p, float* g, cudaStream_t st, const float2* wt, float scale) {
   dim3 block(32, 8);
   dim3 grid((p.nv + 31) / 32);
-  size_t sm = sizeof(float2) * p.ny + sizeof(float) * 8 * 6 * 32;
+  size_t sm = sizeof(float2) * p.ny + sizeof(float) * 8 * 2 * NCH * 32;
   if (sm > 48 * 1024)
-    cudaFuncSetAttribute(jhw_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  jhw_dot_kernel<<<grid, block, sm, st>>>(p.D, wt != nullptr ? wt : p.wt, p.kyi, p.roots, p.rho, p.maskf, p.nx,
-                                          p.ny, p.nv, p.nq, 1.0f / (float)p.ny, scale, g, p.gate);
+    cudaFuncSetAttribute(jhw_dot_kernel<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  jhw_dot_kernel<NCH><<<grid, block, sm, st>>>(p.D, wt != nullptr ? wt : p.wt, p.kyi, p.roots, p.rho, p.maskf,
+                                               p.nx, p.ny, p.nv, p.nq, 1.0f / (float)p.ny, scale, g, p.gate);
   return cudaGetLastError();
+}
+
+cudaError_t launch_jhw_dot(const Plan& p, float* g, cudaStream_t st, const float2* wt, float scale) {
+  if (p.nv == 0) return cudaSuccess;
+  return p.nch == 4 ? launch_jhw_dot_t<4>(p, g, st, wt, scale) : launch_jhw_dot_t<kChannels>(p, g, st, wt, scale);
 }
 
 cudaError_t launch_timecourse(const Plan& p, int channel, float* out, cudaStream_t st) {

@@ -112,16 +112,15 @@ residual_kernel(const float* __restrict__ s, const float* __restrict__ d, float*
   finish_n<1>(part, ticket, f, ws);
 }
 
-// ||alpha * mask||^2 over all four parameter rows
+// ||alpha * mask||^2 over all npar parameter rows
 __global__ void __launch_bounds__(kT)
-masked_norm_kernel(const float* __restrict__ alpha, const uint8_t* __restrict__ mask, int nv,
+masked_norm_kernel(const float* __restrict__ alpha, const uint8_t* __restrict__ mask, int nv, int npar,
                    double* part, unsigned* ticket, double* out) {
   __shared__ double ws[8];
   double acc[1] = {0.0};
   GRID_STRIDE(j, nv) {
     if (mask[j]) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < npar; ++k) {
         const double a = alpha[k * (int64_t)nv + j];
         acc[0] = fma(a, a, acc[0]);
       }
@@ -283,20 +282,20 @@ __device__ __forceinline__ float reflect(float x, float lo, float hi) {
   return fminf(fmaxf(x, lo), hi);
 }
 
-// trial = alpha + z inside the mask, with ln T1 and ln T2 reflected into their box
+// trial = alpha + z inside the mask, with ln T1, ln T2 (and B1) reflected into their box
 __global__ void trial_kernel(const float* __restrict__ alpha, const float* __restrict__ z,
-                             const uint8_t* __restrict__ mask, int nv, float lt1a, float lt1b,
-                             float lt2a, float lt2b, float* __restrict__ trial) {
+                             const uint8_t* __restrict__ mask, int nv, int npar, float lt1a, float lt1b,
+                             float lt2a, float lt2b, float b1a, float b1b, float* __restrict__ trial) {
   GRID_STRIDE(j, nv) {
     const bool on = mask[j] != 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < npar; ++k) {
       const int64_t i = k * (int64_t)nv + j;
       float v = alpha[i];
       if (on) {
         v += z[i];
         if (k == 0) v = reflect(v, lt1a, lt1b);
         if (k == 1) v = reflect(v, lt2a, lt2b);
+        if (k == 4) v = reflect(v, b1a, b1b);
       }
       trial[i] = v;
     }
@@ -314,12 +313,13 @@ __global__ void z_norm_kernel(const float* __restrict__ z, int64_t n, double* pa
 }
 
 // ---- rho initialisation (CGLS on the rho block) ----
-__global__ void fill_rows_kernel(float* __restrict__ alpha, int nv, float lt1, float lt2) {
+__global__ void fill_rows_kernel(float* __restrict__ alpha, int nv, int npar, float lt1, float lt2) {
   GRID_STRIDE(j, nv) {
     alpha[j] = lt1;
     alpha[nv + j] = lt2;
     alpha[2 * (int64_t)nv + j] = 0.f;
     alpha[3 * (int64_t)nv + j] = 0.f;
+    if (npar > 4) alpha[4 * (int64_t)nv + j] = 1.f;  // B1 = 1 (Methods, "Reconstructions")
   }
 }
 
@@ -448,15 +448,16 @@ cudaError_t ensure_workspace(Plan* p) {
   auto chk = [&](cudaError_t r) {
     if (e == cudaSuccess) e = r;
   };
-  chk(dalloc(p, &p->D2, (size_t)kChannels * p->nq * nv));
+  const size_t npv = (size_t)p->npar * nv;
+  chk(dalloc(p, &p->D2, (size_t)p->nch * p->nq * nv));
   chk(dalloc(p, &p->rho2, nv));
-  chk(dalloc(p, &p->gn_g, 4 * nv));
-  chk(dalloc(p, &p->gn_z, 4 * nv));
-  chk(dalloc(p, &p->gn_res, 4 * nv));
-  chk(dalloc(p, &p->gn_dir, 4 * nv));
-  chk(dalloc(p, &p->gn_q, 4 * nv));
-  chk(dalloc(p, &p->gn_alpha, 4 * nv));
-  chk(dalloc(p, &p->gn_trial, 4 * nv));
+  chk(dalloc(p, &p->gn_g, npv));
+  chk(dalloc(p, &p->gn_z, npv));
+  chk(dalloc(p, &p->gn_res, npv));
+  chk(dalloc(p, &p->gn_dir, npv));
+  chk(dalloc(p, &p->gn_q, npv));
+  chk(dalloc(p, &p->gn_alpha, npv));
+  chk(dalloc(p, &p->gn_trial, npv));
   chk(dalloc(p, &p->gn_s, nk));
   chk(dalloc(p, &p->gn_r, nk));
   chk(dalloc(p, &p->gn_st, nk));
@@ -537,8 +538,8 @@ struct Solver {
     float* s = p->gn_g;             // A^H r
     float2* r = p->gn_r;            // k-space residual d - A x
     float2* q = p->gn_jv;
-    cudaError_t e = cudaMemsetAsync(p->gn_z, 0, 4 * p->nv * sizeof(float), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(pr, 0, 4 * p->nv * sizeof(float), st);
+    cudaError_t e = cudaMemsetAsync(p->gn_z, 0, (size_t)p->npar * p->nv * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pr, 0, (size_t)p->npar * p->nv * sizeof(float), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(r, d, nkf * sizeof(float), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(si + I_FROZEN, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(e, "CGLS init");
@@ -602,6 +603,8 @@ void mrstat_gn_default_opts(mrstat_gn_opts* o) {
   o->t1_init_ms = 1000.0;
   o->t2_init_ms = 100.0;
   o->mask_threshold = 0.0;
+  o->b1_min = 0.5;
+  o->b1_max = 1.5;
 }
 
 int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const float* b1, uint8_t* mask,
@@ -618,6 +621,12 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   if (o->rho_init_iters > 0 && o->mask_threshold > 0 && mask == nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "drawing a mask needs a mask buffer");
   if (o->hessian != 0 && o->hessian != 1) return fail(MRSTAT_ERR_INVALID_ARG, "hessian must be 0 or 1");
+  if (p->npar == 5) {
+    if (b1 != nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "B1 is estimated (alpha row 4): pass b1 = NULL");
+    if (!(o->b1_min > 0) || !(o->b1_max > o->b1_min)) return fail(MRSTAT_ERR_INVALID_ARG, "need 0 < b1_min < b1_max");
+    if (o->hessian != 0 || o->surrogate_iters != 0)
+      return fail(MRSTAT_ERR_UNSUPPORTED, "the low-rank and surrogate models do not estimate B1");
+  }
   if (o->hessian == 1 && p->lr == nullptr)
     return fail(MRSTAT_ERR_NOT_LINEARIZED, "the low-rank Hessian needs mrstat_lowrank_set_basis first");
   if (o->surrogate_iters < 0 || o->surrogate_iters > o->outer_iters)
@@ -638,7 +647,7 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   cudaError_t e = ensure_workspace(p);
   if (e != cudaSuccess) return cuda_fail(e, "Gauss-Newton work space");
 
-  Solver S{p, st, 4 * (int64_t)p->nv, 2 * (int64_t)p->ntr * p->nkx, p->gn_sc, p->gn_si};
+  Solver S{p, st, (int64_t)p->npar * p->nv, 2 * (int64_t)p->ntr * p->nkx, p->gn_sc, p->gn_si};
   if (p->lr) p->lr->active = false;
   bool coef_stale = true;  // low-rank coefficients of the current point
   const int nv = p->nv;
@@ -647,14 +656,14 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   std::memset(&local, 0, sizeof(local));
   int status = MRSTAT_OK;
 
-  e = cudaMemcpyAsync(p->gn_alpha, alpha, 4 * (size_t)nv * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  e = cudaMemcpyAsync(p->gn_alpha, alpha, (size_t)p->npar * nv * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->gn_si, 0, I_COUNT * sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "Gauss-Newton setup");
 
   // -- rho initialisation and mask (Methods, "Reconstructions") --
   if (o->rho_init_iters > 0) {
     e = S.vec([&] {
-      fill_rows_kernel<<<g, kT, 0, st>>>(p->gn_alpha, nv, (float)std::log(o->t1_init_ms),
+      fill_rows_kernel<<<g, kT, 0, st>>>(p->gn_alpha, nv, p->npar, (float)std::log(o->t1_init_ms),
                                          (float)std::log(o->t2_init_ms));
     });
     if (e != cudaSuccess) return cuda_fail(e, "rho init fill");
@@ -716,7 +725,8 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   }
   if (status != MRSTAT_OK) return status;
   e = S.vec([&] {
-    masked_norm_kernel<<<g, kT, 0, st>>>(p->gn_alpha, p->gn_mask, nv, p->red, p->ticket, p->gn_sc + S_ANORM2);
+    masked_norm_kernel<<<g, kT, 0, st>>>(p->gn_alpha, p->gn_mask, nv, p->npar, p->red, p->ticket,
+                                         p->gn_sc + S_ANORM2);
   });
   if (e != cudaSuccess) return cuda_fail(e, "alpha norm");
   double hs[S_COUNT];
@@ -777,7 +787,8 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
     if (p->lr) p->lr->active = false;
     if (status != MRSTAT_OK) return status;
     e = S.vec([&] {
-      trial_kernel<<<g, kT, 0, st>>>(p->gn_alpha, p->gn_z, p->gn_mask, nv, lt1a, lt1b, lt2a, lt2b, p->gn_trial);
+      trial_kernel<<<g, kT, 0, st>>>(p->gn_alpha, p->gn_z, p->gn_mask, nv, p->npar, lt1a, lt1b, lt2a, lt2b,
+                                     (float)o->b1_min, (float)o->b1_max, p->gn_trial);
     });
     if (e != cudaSuccess) return cuda_fail(e, "trial point");
     if (sur) {
@@ -825,7 +836,7 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   // the plan's cached linearisation is the one at the returned alpha (mask gn_mask): the
   // exact one, or the surrogate's low-rank one when every iteration used the surrogate
   if (p->lr) p->lr->active = o->surrogate_iters > 0 && o->surrogate_iters == o->outer_iters;
-  e = cudaMemcpyAsync(alpha, p->gn_alpha, 4 * (size_t)nv * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  e = cudaMemcpyAsync(alpha, p->gn_alpha, (size_t)p->npar * nv * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "Gauss-Newton result");
   p->linearized = true;

@@ -13,8 +13,10 @@
 
 namespace mrstat {
 
-// Number of channels of the cached time courses: m_y, dm_y/dlnT1, dm_y/dlnT2.
+// Number of channels of the cached time courses: m_y, dm_y/dlnT1, dm_y/dlnT2 (a plan
+// that estimates B1 adds dm_y/dB1: Plan::nch = 4).
 constexpr int kChannels = 3;
+constexpr int kMaxChannels = 4;
 // Maximum number of blocks of a float64 reduction (partials buffer size).
 constexpr int kRedBlocks = 608;
 
@@ -24,6 +26,8 @@ struct Plan {
   int nq = 0;        // ntr_pad / 4 TR quads
   int nv = 0;
   int form = 0;
+  int npar = 4;      // unknowns per voxel (5 with B1 estimated)
+  int nch = 3;       // cached time-course channels (4 with B1 estimated)
   int device = 0;
   double tr_ms = 0, te_ms = 0;
   int inversion = 0, alternate = 0;
@@ -37,21 +41,21 @@ struct Plan {
   float2* fh = nullptr;     // [nkx][nx] exp(+2 pi i kx ix / nx)
 
   // cached linearisation
-  float4* D = nullptr;      // [3][nq][nv] four consecutive TRs per float4
+  float4* D = nullptr;      // [nch][nq][nv] four consecutive TRs per float4
   float2* rho = nullptr;    // [nv] rho * mask
   float* maskf = nullptr;   // [nv] 1 inside the mask, 0 outside
   bool linearized = false;
 
   // scratch
   float4* dfwd = nullptr;   // [nq][nv] m_y only, for mrstat_forward
-  float2* cf = nullptr;     // [3][nv] per-voxel complex coefficients of the y-contraction
+  float2* cf = nullptr;     // [4][nv] per-voxel complex coefficients of the y-contraction
   float2* A = nullptr;      // [ntr_pad][nx] y-contracted image rows (padded rows zero)
   float2* wt = nullptr;     // [ntr_pad][nx] x-adjoint of a k-space vector (rows >= ntr zero)
   double* red = nullptr;    // [kRedBlocks] reduction partials
   unsigned* ticket = nullptr;  // last-block ticket of the reductions (0 between launches)
-  float* cg_r = nullptr;    // [4][nv]
-  float* cg_p = nullptr;    // [4][nv]
-  float* cg_q = nullptr;    // [4][nv]
+  float* cg_r = nullptr;    // [npar][nv]
+  float* cg_p = nullptr;    // [npar][nv]
+  float* cg_q = nullptr;    // [npar][nv]
   float2* cg_jv = nullptr;  // [ntr][nkx]
   double* cg_s = nullptr;   // CG scalars, 4 per iteration
   int* cg_frozen = nullptr; // CG stop flag

@@ -76,6 +76,7 @@ extern "C" {
 int mrstat_lowrank_set_basis(mrstat_plan* plan_, const float* U, int32_t rank, void* stream) {
   Plan* p = reinterpret_cast<Plan*>(plan_);
   if (p == nullptr || U == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or basis");
+  if (p->npar != 4) return fail(MRSTAT_ERR_UNSUPPORTED, "the low-rank form does not estimate B1");
   DeviceGuard g(p->device);
   return lowrank_setup(p, U, rank, as_stream(stream));
 }

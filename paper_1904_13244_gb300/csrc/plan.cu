@@ -69,7 +69,7 @@ inline void unit_root(long long a, long long n, float2* out, bool conj) {
 cudaError_t ensure_timecourses(Plan* p) {
   if (p->D != nullptr) return cudaSuccess;
   const int64_t before = p->bytes;
-  cudaError_t e = dalloc(p, &p->D, (size_t)kChannels * p->nq * p->nv);
+  cudaError_t e = dalloc(p, &p->D, (size_t)p->nch * p->nq * p->nv);
   p->d_bytes = p->bytes - before;
   return e;
 }
@@ -162,7 +162,7 @@ int do_jvp(Plan* p, const float* v, float2* jv, cudaStream_t st) {
   if (e != cudaSuccess) return cuda_fail(e, "prep_jvp launch");
   {
     Span sp(p, MRSTAT_K_YCONTRACT, st);
-    e = launch_ycontract(*p, p->D, kChannels, st);
+    e = launch_ycontract(*p, p->D, p->nch, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
   return do_xdft(p, p->A, jv, p->gate, st);
@@ -244,7 +244,7 @@ int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* ma
   if (e != cudaSuccess) return cuda_fail(e, "prep_linearize launch");
   {
     Span sp(p, MRSTAT_K_BLOCH, st);
-    e = launch_bloch(*p, alpha, b1, mask, D, kChannels, st);
+    e = launch_bloch(*p, alpha, b1, mask, D, p->nch, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "bloch launch");
   return MRSTAT_OK;
@@ -258,7 +258,7 @@ int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot) 
   if (vdot != nullptr) {
     const int s = do_jhjv(p, v, out, st, nullptr);
     if (s != MRSTAT_OK) return s;
-    const cudaError_t e = do_dot(p, v, out, 4 * (int64_t)p->nv, vdot, st);
+    const cudaError_t e = do_dot(p, v, out, (int64_t)p->npar * p->nv, vdot, st);
     return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "dot launch");
   }
   if (p->nkx == p->nx) {
@@ -270,7 +270,7 @@ int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot) 
     if (e != cudaSuccess) return cuda_fail(e, "prep_jvp launch");
     {
       Span sp(p, MRSTAT_K_YCONTRACT, st);
-      e = launch_ycontract(*p, p->D, kChannels, st);
+      e = launch_ycontract(*p, p->D, p->nch, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "ycontract launch");
     {
@@ -365,6 +365,8 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   if (out == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (seq == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "seq is NULL");
+  const bool estimate_b1 = (form & MRSTAT_ESTIMATE_B1) != 0;
+  form &= ~MRSTAT_ESTIMATE_B1;
   if (form != MRSTAT_FORM_PLAIN_FP32 && form != MRSTAT_FORM_SPLIT_BF16)
     return fail(MRSTAT_ERR_INVALID_ARG, "form %d not available", form);
   if (seq->nx < 1 || seq->nx > 2048 || seq->ny < 1 || seq->ny > 2048 || seq->nkx < 1 ||
@@ -398,6 +400,8 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   p->nq = p->ntr_pad / 4;
   p->nv = seq->nx * seq->ny;
   p->form = form;
+  p->npar = estimate_b1 ? 5 : 4;
+  p->nch = estimate_b1 ? 4 : kChannels;
   p->tr_ms = seq->tr_ms;
   p->te_ms = seq->te_ms;
   p->inversion = seq->inversion != 0;
@@ -439,15 +443,15 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(dalloc(p, &p->fh, fh.size()));
   chk(dalloc(p, &p->rho, nv));
   chk(dalloc(p, &p->maskf, nv));
-  chk(dalloc(p, &p->cf, (size_t)kChannels * nv));
+  chk(dalloc(p, &p->cf, (size_t)kMaxChannels * nv));
   // A has the padded TR rows too (zero, never written): J^H J v reads it as W~ over TR quads
   chk(dalloc(p, &p->A, (size_t)p->ntr_pad * p->nx));
   chk(dalloc(p, &p->wt, (size_t)p->ntr_pad * p->nx));
   chk(dalloc(p, &p->red, kRedBlocks));
   chk(dalloc(p, &p->ticket, 1));
-  chk(dalloc(p, &p->cg_r, 4 * nv));
-  chk(dalloc(p, &p->cg_p, 4 * nv));
-  chk(dalloc(p, &p->cg_q, 4 * nv));
+  chk(dalloc(p, &p->cg_r, (size_t)p->npar * nv));
+  chk(dalloc(p, &p->cg_p, (size_t)p->npar * nv));
+  chk(dalloc(p, &p->cg_q, (size_t)p->npar * nv));
   chk(dalloc(p, &p->cg_jv, (size_t)p->ntr * p->nkx));
   chk(dalloc(p, &p->cg_frozen, 1));
   chk(dalloc(p, &p->dev_err, 1));
@@ -502,12 +506,15 @@ int mrstat_plan_info(const mrstat_plan* plan, mrstat_plan_info_t* info) {
   info->ntr_padded = plan->ntr_pad;
   info->device_bytes = plan->bytes;
   info->timecourse_bytes = plan->d_bytes;
+  info->npar = plan->npar;
   return MRSTAT_OK;
 }
 
 int mrstat_linearize(mrstat_plan* plan, const float* alpha, const float* b1, const uint8_t* mask,
                      void* stream) {
   if (plan == nullptr || alpha == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or alpha");
+  if (plan->npar == 5 && b1 != nullptr)
+    return fail(MRSTAT_ERR_INVALID_ARG, "B1 is estimated (alpha row 4): pass b1 = NULL");
   DeviceGuard g(plan->device);
   cudaStream_t st = as_stream(stream);
   plan->linearized = false;
@@ -524,6 +531,8 @@ int mrstat_forward(mrstat_plan* plan, const float* alpha, const float* b1, const
                    float* s, void* stream) {
   if (plan == nullptr || alpha == nullptr || s == nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, alpha or s");
+  if (plan->npar == 5 && b1 != nullptr)
+    return fail(MRSTAT_ERR_INVALID_ARG, "B1 is estimated (alpha row 4): pass b1 = NULL");
   DeviceGuard g(plan->device);
   cudaStream_t st = as_stream(stream);
   cudaError_t e = ensure_forward_scratch(plan);
@@ -566,8 +575,8 @@ int mrstat_jhw(mrstat_plan* plan, const float* w, float* gout, void* stream) {
 
 int mrstat_timecourses(mrstat_plan* plan, int32_t channel, float* out, void* stream) {
   if (plan == nullptr || out == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or out");
-  if (channel < 0 || channel >= kChannels)
-    return fail(MRSTAT_ERR_INVALID_ARG, "channel %d not in [0, %d)", channel, kChannels);
+  if (channel < 0 || channel >= plan->nch)
+    return fail(MRSTAT_ERR_INVALID_ARG, "channel %d not in [0, %d)", channel, plan->nch);
   if (!plan->linearized || plan->D == nullptr || (plan->lr && plan->lr->active))
     return fail(MRSTAT_ERR_NOT_LINEARIZED, "timecourses need an exact mrstat_linearize");
   DeviceGuard g(plan->device);
@@ -591,6 +600,7 @@ int mrstat_forward_ckpt(mrstat_plan* plan, const float* alpha, const float* b1, 
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, alpha or s");
   if (interval < 4 || interval % 4 != 0)
     return fail(MRSTAT_ERR_INVALID_ARG, "checkpoint interval %d is not a positive multiple of 4", interval);
+  if (plan->npar != 4) return fail(MRSTAT_ERR_UNSUPPORTED, "the checkpointed form does not estimate B1");
   DeviceGuard g(plan->device);
   cudaStream_t st = as_stream(stream);
   cudaError_t e = ensure_forward_scratch(plan);
@@ -682,7 +692,7 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
     if (e != cudaSuccess) return cuda_fail(e, "CG scalar allocation");
     plan->cg_s_cap = cap;
   }
-  const int64_t n = 4 * (int64_t)plan->nv;
+  const int64_t n = (int64_t)plan->npar * plan->nv;
   double* sc = plan->cg_s;
   cudaError_t e = cudaMemsetAsync(plan->cg_frozen, 0, sizeof(int), st);
   if (e == cudaSuccess) {

@@ -92,3 +92,25 @@ def test_noisy_fit_reaches_the_noise_floor():
     # the fit absorbs about N of the 2 Nt real noise components: f_final ~ floor * (1 - N / (2 Nt))
     expected = floor * (1 - truth.size / (2 * d.size))
     assert 0.8 * expected < rep.f_final < 1.05 * floor
+
+
+@pytest.mark.slow
+def test_noiseless_recovery_with_b1_estimated():
+    """B1 as the fifth unknown (Methods, "Reconstructions"): from T1 = 1000 ms, T2 = 100 ms,
+    B1 = 1 and the CGLS rho, the fit recovers a smooth B1 field in [0.8, 1.2] with the
+    tissue maps on the 16x16 phantom scanned with 24 fills."""
+    seq = synth.make_sequence(16, 16, 24, 7.8, 3.9, seed=0)
+    ph = synth.quadrant_phantom(16, 0)
+    b1 = synth.smooth_b1(16, 16, 3).ravel()
+    truth = np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(), ph.rho.imag.ravel(),
+                      b1])
+    d = model.forward(seq, truth)
+    a0, mask = solver.initial_alpha(seq, d, seq.nv, estimate_b1=True)
+    assert a0.shape[0] == 5 and np.all(a0[4] == 1.0)
+    # B1 and T1 are partly confounded, so the Gauss-Newton systems are worse conditioned
+    # than with B1 known: 60 CG steps per outer iteration instead of 20
+    a, rep = solver.gauss_newton(seq, d, a0, mask=mask, opts=solver.GNOptions(outer_iters=15, inner_iters=60))
+    assert rep.f_final < 1e-10 * rep.f[0]
+    assert metrics.nrmse(np.exp(a[0]), ph.t1_ms.ravel()) < 1e-5
+    assert metrics.nrmse(np.exp(a[1]), ph.t2_ms.ravel()) < 1e-5
+    assert metrics.nrmse(a[4], b1) < 1e-5
