@@ -9,8 +9,9 @@ selected with --form:
 
 * surrogate (default): the compressed model in a rank-32 time basis whose coefficients
   come from the learned surrogate (one MLP inference on the tensor cores per step);
-  every J^H J v is the per-ky Gram product between two split-BF16 tcgen05
-  phase-encode DFT GEMMs (the readout DFT pair cancels: nkx = nx);
+  every J^H J v is the per-ky Gram product between the phase-encode DFT and its
+  adjoint (factorised 224 = 7 x 32 on the CUDA cores, fused into the first and last
+  pass; the readout DFT pair cancels: nkx = nx);
 * lowrank: the same products, the linearisation projects the exact Bloch recursion
   onto the basis;
 * plain: exact FP32 model; the linearisation caches m_y and its tangents
@@ -401,7 +402,12 @@ def main():
     per_launch = {k: stats[k]["ms"] / max(stats[k]["timed"], 1) for k in all_kernels}
     lowrank_like = args.form in ("lowrank", "surrogate")
     full_readout = nkx == nx
-    if lowrank_like and full_readout:
+    fft_y = full_readout and ny % 32 == 0 and ny // 32 <= 8
+    if lowrank_like and fft_y:
+        # factorised phase-encode DFT on the CUDA cores, fused into the first and last pass
+        work = {"ycontract": (nv * (16 + 8 + 4) + 3 * R * nv * 4 + R * nv * 8, "hbm"),   # v, rho, mask, c -> H
+                "jhw_dot": (R * nv * 8 + 3 * R * nv * 4 + nv * (8 + 4) + nv * 16 + nv * 16, "hbm")}  # G, c, v -> g
+    elif lowrank_like and full_readout:
         # per J^H J v: one phase-encode DFT GEMM in each of xdft / xdft_adj, three split
         # BF16 products of the real-embedded [R nx x 2ny] x [2ny x 2ny] matrices
         gemm_flops = 3 * 2 * (R * nx) * (2 * ny) * (2 * ny)
@@ -460,6 +466,8 @@ def main():
            "xdft_adj": "tc_gemm.cu", "mlp_infer": "mlp.cu"}
     if lowrank_like:
         src.update({"jhw_dot": "lowrank.cu", "ycontract": "lowrank.cu"})
+    if dom == "mlp_infer":
+        src["mlp_infer"] = "mlp.cu"
     h = source_hash(os.path.join(ROOT, "paper_1904_13244_gb300", "csrc", src[dom]))
     roofline = roof(dom)
     roofline["traffic"] = NCU_TRAFFIC.get((dom, h))
@@ -551,9 +559,10 @@ def main():
         # MLP inference per step: input, 4 GEMMs, 3 activations, output (outside the plan's counters)
         launches += 9 * args.steps
     if rank == 0:
+        dft = ("factorised FP32 phase-encode DFT" if fft_y else "split-BF16 tcgen05 DFTs")
         form_desc = {"surrogate": f"learned surrogate + low-rank form (rank {R} time basis, MLP {args.hidden}x3 "
-                                  f"coefficients, split-BF16 tcgen05 DFTs, per-ky Gram J^H J v)",
-                     "lowrank": f"low-rank form (rank {R} time basis, split-BF16 tcgen05 DFTs, per-ky Gram J^H J v)",
+                                  f"tcgen05 coefficients, {dft}, per-ky Gram J^H J v)",
+                     "lowrank": f"low-rank form (rank {R} time basis, {dft}, per-ky Gram J^H J v)",
                      "plain": "plain FP32 form (cached time courses, FP32 readout DFT)",
                      "split": "split-BF16 form (cached time courses, tcgen05 readout DFT)"}[args.form]
         l2 = ("inputs larger than L2 (cached time courses %.0f MB)" % (d_bytes / 1e6) if not lowrank_like
@@ -563,7 +572,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16x3+f32" if lowrank_like else "f32",
+                "dtype": ("f32 (MLP bf16)" if args.form == "surrogate" else "f32") if (not lowrank_like or fft_y)
+                else "bf16x3+f32",
                 "data": "synthetic",
                 "config": {"workload": f"{args.workload}: {seq.nx}x{seq.ny} grid, {seq.ntr} TRs, "
                                        f"{seq.nkx} readout samples, " + form_desc,

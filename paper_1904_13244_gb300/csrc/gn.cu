@@ -718,6 +718,7 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   // -- current point --
   if (o->surrogate_iters > 0) {
     status = sur_linearize(p->gn_alpha, p->rho, p->lr->coef);
+    p->lr->coefT_dirty = true;
     if (status == MRSTAT_OK) status = sur_signal(p->gn_alpha, p->gn_s);
     if (status == MRSTAT_OK) status = S.residual(p->gn_s, d, p->gn_r, p->gn_sc + S_F);
   } else {
@@ -778,6 +779,7 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
       if (coef_stale) {
         Span sp(p, MRSTAT_K_BLOCH, st);
         e = lowrank_project(*p, *p->lr, p->gn_alpha, b1, p->gn_mask, p->lr->coef, st);
+        p->lr->coefT_dirty = true;
         if (e != cudaSuccess) return cuda_fail(e, "low-rank projection");
         coef_stale = false;
       }

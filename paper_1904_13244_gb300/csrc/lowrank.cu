@@ -371,11 +371,11 @@ lr_prep_t_kernel(const float* __restrict__ v, const float* __restrict__ coef, co
 // Block (32, 8): 32 consecutive ky (lanes) x 8 image columns; the rows of U of the TRs
 // of its 32 ky values (contiguous in Ug, U gathered in ky order) sit in shared memory,
 // rows padded to R + 1 floats.
-template <int R>
+template <int R, bool SPLIT>
 __global__ void __launch_bounds__(256)
 lr_gram_t_kernel(const float* __restrict__ HT, int ldh, const float* __restrict__ Ug, const int* __restrict__ kyptr,
                  int nx, int ny, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int ldk,
-                 const int* __restrict__ gate) {
+                 float2* __restrict__ gout, const int* __restrict__ gate) {
   if (gate != nullptr && *gate == 0) return;
   extern __shared__ float us[];  // [rows of this ky tile][R + 1]
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
@@ -412,7 +412,10 @@ lr_gram_t_kernel(const float* __restrict__ HT, int ldh, const float* __restrict_
     }
   }
 #pragma unroll
-  for (int r = 0; r < R; ++r) put_split_pair(hi, lo, (size_t)(ix * R + r) * ldk + 2 * ky, out[r]);
+  for (int r = 0; r < R; ++r) {
+    if (SPLIT) put_split_pair(hi, lo, (size_t)(ix * R + r) * ldk + 2 * ky, out[r]);
+    else gout[(size_t)(ix * R + r) * ny + ky] = out[r];
+  }
 }
 
 // The same Gram product when no ky value has more than kGramShort TRs (one TR per fill
@@ -421,11 +424,12 @@ lr_gram_t_kernel(const float* __restrict__ HT, int ldh, const float* __restrict_
 // held (about half the registers of the general kernel, twice the resident warps).
 constexpr int kGramShort = 8;
 
-template <int R>
+template <int R, bool SPLIT>
 __global__ void __launch_bounds__(256)
 lr_gram_short_kernel(const float* __restrict__ HT, int ldh, const float* __restrict__ Ug,
                      const int* __restrict__ kyptr, int nx, int ny, __nv_bfloat16* __restrict__ hi,
-                     __nv_bfloat16* __restrict__ lo, int ldk, const int* __restrict__ gate) {
+                     __nv_bfloat16* __restrict__ lo, int ldk, float2* __restrict__ gout,
+                     const int* __restrict__ gate) {
   if (gate != nullptr && *gate == 0) return;
   extern __shared__ float us[];  // [rows of this ky tile][R + 1]
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
@@ -473,8 +477,221 @@ lr_gram_short_kernel(const float* __restrict__ HT, int ldh, const float* __restr
         o.y = fmaf(u, sv[k].y, o.y);
       }
     }
-    put_split_pair(hi, lo, (size_t)(ix * R + r) * ldk + 2 * ky, o);
+    if (SPLIT) put_split_pair(hi, lo, (size_t)(ix * R + r) * ldk + 2 * ky, o);
+    else gout[(size_t)(ix * R + r) * ny + ky] = o;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Phase-encode DFT by factorisation, for ny = 32 N1 (N1 <= 8): with iy = 32 i1 + i2 and
+// ky = k1 + N1 k2 the exponent ky iy (mod ny) splits into N1-point, twiddle and 32-point
+// parts,
+//     X[k1 + N1 k2] = sum_i2 w32^(k2 i2) w^(k1 i2) sum_i1 wN1^(k1 i1) x[32 i1 + i2],
+// with w = exp(-2 pi i / ny), wN1 = w^32 and w32 = w^N1, all read from the exact root
+// table.  A warp holds one column (lane = i2): a dense N1-point DFT per lane, the twiddle,
+// then a 32-point FFT across the lanes (radix-2 decimation in frequency by shuffles; lane
+// L ends with output index bitrev(L)).  The adjoint is the same with conjugate roots in
+// the reverse order.  Everything stays in float32 (no split-BF16 rounding).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+
+// in-warp 32-point DFT of v (lane = input index); the result at lane L is output bitrev(L).
+// CONJ: exp(+2 pi i / 32) roots (the adjoint).  rt[k] = w^k with w32 = w^N1.
+template <bool CONJ>
+__device__ __forceinline__ float2 fft32_warp(float2 v, const float2* rt, int n1, int lane) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const float px = __shfl_xor_sync(0xffffffffu, v.x, h);
+    const float py = __shfl_xor_sync(0xffffffffu, v.y, h);
+    const int pos = lane & (2 * h - 1);
+    if (pos < h) {
+      v = make_float2(v.x + px, v.y + py);
+    } else {
+      const float2 d = make_float2(px - v.x, py - v.y);
+      const float2 w = rt[(pos - h) * (16 / h) * n1];  // w_(2h)^(pos - h)
+      v = CONJ ? cmulc(d, w) : cmul(d, w);
+    }
+  }
+  return v;
+}
+
+// coefT[(k R + r)][ix][iy] = coef[(k R + r)][iy nx + ix]: the coefficients in image-column
+// order, so that a block working on one column ix reads them contiguously (32 x 32 tiles)
+__global__ void lr_coef_transpose_kernel(const float* __restrict__ coef, int nx, int ny, float* __restrict__ coefT) {
+  __shared__ float tile[32][33];
+  const int plane = blockIdx.z;
+  const int ix0 = blockIdx.x * 32, iy0 = blockIdx.y * 32;
+  const size_t nv = (size_t)nx * ny;
+  const float* src = coef + plane * nv;
+  float* dst = coefT + plane * nv;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int iy = iy0 + k, ix = ix0 + threadIdx.x;
+    tile[k][threadIdx.x] = (iy < ny && ix < nx) ? src[(size_t)iy * nx + ix] : 0.f;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int ix = ix0 + k, iy = iy0 + threadIdx.x;
+    if (ix < nx && iy < ny) dst[(size_t)ix * ny + iy] = tile[threadIdx.x][k];
+  }
+}
+
+// One block per image column ix: h_r(iy) = i (rho (v0 dc1_r + v1 dc2_r) + (v2 + i v3) c_r)
+// mask for every iy and r, then the phase-encode DFT of every r column, written as
+// H[(ix, r)][ky] (float2 rows).  Threads over iy for the first part, warps over r for the
+// DFTs.
+template <int N1>
+__global__ void __launch_bounds__(256)
+lr_prep_fft_kernel(const float* __restrict__ v, const float* __restrict__ coefT, const float2* __restrict__ rho,
+                   const float* __restrict__ maskf, const float2* __restrict__ roots, int nx, int ny, int nv, int R,
+                   float2* __restrict__ H, const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  const int ld = ny + 1;
+  extern __shared__ float2 fsm[];
+  float2* rt = fsm;              // [ny] w^k
+  float2* hs = rt + ny;          // [R][ny + 1]
+  float2* stg = hs + R * ld;     // [8 warps][ny] output staging
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int brev = (int)(__brev((unsigned)lane) >> 27);
+  const size_t plane = (size_t)nx * ny;
+  for (int e = tid; e < ny; e += 256) rt[e] = roots[e];
+  for (int ix = blockIdx.x; ix < nx; ix += gridDim.x) {
+    for (int iy = tid; iy < ny; iy += 256) {
+      const int j = iy * nx + ix;
+      const float m = maskf[j];
+      const float2 rh = rho[j];
+      const float v0 = v[j], v1 = v[nv + j], v2 = v[2 * (size_t)nv + j] * m, v3 = v[3 * (size_t)nv + j] * m;
+      const float* c0 = coefT + (size_t)ix * ny + iy;
+#pragma unroll 8
+      for (int r = 0; r < R; ++r) {
+        const float c = c0[(size_t)r * plane];
+        const float t = fmaf(v0, c0[(size_t)(R + r) * plane], v1 * c0[(size_t)(2 * R + r) * plane]);
+        const float qr = rh.x * t + v2 * c, qi = rh.y * t + v3 * c;
+        hs[r * ld + iy] = make_float2(-qi, qr);
+      }
+    }
+    __syncthreads();
+    float2* sw = stg + warp * ny;
+    for (int r = warp; r < R; r += 8) {
+      const float2* x = hs + r * ld;
+      float2 xin[N1];
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1) xin[i1] = x[32 * i1 + lane];
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i1 = 0; i1 < N1; ++i1) {
+          const float2 w = rt[32 * ((k1 * i1) % N1)];
+          acc = make_float2(fmaf(w.x, xin[i1].x, fmaf(-w.y, xin[i1].y, acc.x)),
+                            fmaf(w.x, xin[i1].y, fmaf(w.y, xin[i1].x, acc.y)));
+        }
+        acc = cmul(acc, rt[(k1 * lane) % ny]);
+        acc = fft32_warp<false>(acc, rt, N1, lane);
+        sw[k1 + N1 * brev] = acc;
+      }
+      __syncwarp();
+      float2* dst = H + (size_t)(ix * R + r) * ny;
+      for (int k = lane; k < ny; k += 32) dst[k] = sw[k];
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+// One block per image column ix: adjoint phase-encode DFT of G[(ix, r)][ky] for every r,
+// then g_k,j = scale mask_j Re sum_r conj(dh_r,j/dv_k) P_r,j for the column's voxels and,
+// with vdot, the block's part of <v, g> (last-block finish over red / ticket).
+template <int N1>
+__global__ void __launch_bounds__(256)
+lr_final_fft_kernel(const float2* __restrict__ G, const float* __restrict__ coefT, const float2* __restrict__ rho,
+                    const float* __restrict__ maskf, const float2* __restrict__ roots, int nx, int ny, int nv, int R,
+                    float scale, float* __restrict__ g, const float* __restrict__ v, double* red_part,
+                    unsigned* ticket, double* __restrict__ vdot, const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  const int ld = ny + 1;
+  extern __shared__ float2 fsm[];
+  float2* rt = fsm;        // [ny]
+  float2* gs = rt + ny;    // [R][ny + 1]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i2 = (int)(__brev((unsigned)lane) >> 27);
+  const size_t plane = (size_t)nx * ny;
+  for (int e = tid; e < ny; e += 256) rt[e] = roots[e];
+  float sf = 0.f;
+  for (int ix = blockIdx.x; ix < nx; ix += gridDim.x) {
+    for (int e = tid; e < R * ny; e += 256) {
+      const int r = e / ny, k = e - r * ny;
+      gs[r * ld + k] = G[(size_t)(ix * R + r) * ny + k];
+    }
+    __syncthreads();
+    for (int r = warp; r < R; r += 8) {
+      float2* x = gs + r * ld;
+      float2 z[N1];
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) z[k1] = x[k1 + N1 * lane];  // k2 = lane
+      __syncwarp();
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const float2 t = fft32_warp<true>(z[k1], rt, N1, lane);  // at i2 = bitrev(lane)
+        z[k1] = cmulc(t, rt[(k1 * i2) % ny]);
+      }
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+          const float2 w = rt[32 * ((k1 * i1) % N1)];
+          acc = make_float2(fmaf(w.x, z[k1].x, fmaf(w.y, z[k1].y, acc.x)),
+                            fmaf(w.x, z[k1].y, fmaf(-w.y, z[k1].x, acc.y)));
+        }
+        x[32 * i1 + i2] = acc;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int iy = tid; iy < ny; iy += 256) {
+      const int j = iy * nx + ix;
+      const float2 rh = rho[j];
+      const float* c0 = coefT + (size_t)ix * ny + iy;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 8
+      for (int r = 0; r < R; ++r) {
+        const float2 pv = gs[r * ld + iy];
+        const float c = c0[(size_t)r * plane];
+        const float t1 = c0[(size_t)(R + r) * plane], t2 = c0[(size_t)(2 * R + r) * plane];
+        const float imcp = rh.x * pv.y - rh.y * pv.x;  // Im(conj(rho) P)
+        a0 = fmaf(t1, imcp, a0);
+        a1 = fmaf(t2, imcp, a1);
+        a2 = fmaf(c, pv.y, a2);
+        a3 = fmaf(-c, pv.x, a3);
+      }
+      const float m = maskf[j] * scale;
+      a0 *= m;
+      a1 *= m;
+      a2 *= m;
+      a3 *= m;
+      g[j] = a0;
+      g[(size_t)nv + j] = a1;
+      g[2 * (size_t)nv + j] = a2;
+      g[3 * (size_t)nv + j] = a3;
+      if (vdot != nullptr) {
+        sf = fmaf(v[j], a0, sf);
+        sf = fmaf(v[(size_t)nv + j], a1, sf);
+        sf = fmaf(v[2 * (size_t)nv + j], a2, sf);
+        sf = fmaf(v[3 * (size_t)nv + j], a3, sf);
+      }
+    }
+    __syncthreads();
+  }
+  if (vdot == nullptr) return;
+  __shared__ double ws[8];
+  const double t = red::block_sum<256>((double)sf, ws);
+  if (threadIdx.x == 0) red_part[blockIdx.x] = t;
+  red::finish_reduction<256>(red_part, ticket, vdot, ws);
 }
 
 // Partial sums over one chunk of 8 basis functions (blockIdx.z) of
@@ -597,7 +814,7 @@ cudaError_t lowrank_project(const Plan& p, const LowRank& L, const float* alpha,
 
 void lowrank_free(LowRank* L) {
   if (L == nullptr) return;
-  void* ptrs[] = {L->U, L->Ug, L->Mky, L->kyptr, L->kytr, L->coef, L->coef2, L->gpart, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
+  void* ptrs[] = {L->U, L->Ug, L->Mky, L->kyptr, L->kytr, L->coef, L->coef2, L->gpart, L->coefT, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
                   L->a4_hi, L->a4_lo, L->by_hi, L->by_lo, L->bya_hi, L->bya_lo, L->X1, L->H, L->Y3, L->P};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -658,6 +875,8 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   // the cancelled readout DFT pair needs nkx == nx; the Gram kernel keeps a ky tile's rows of U
   // in shared memory
   L->full_readout = p->nkx == p->nx && (size_t)L->gram_rows_max * (R + 1) * sizeof(float) <= (size_t)L->smem_optin;
+  // factorised phase-encode DFT: ny = 32 N1 with N1 <= 8
+  L->fft_y = L->full_readout && ny % 32 == 0 && ny / 32 <= 8;
   std::vector<float> M((size_t)ny * R * R, 0.f);
   for (int k = 0; k < ny; ++k)
     for (int a = 0; a < R; ++a)
@@ -702,6 +921,7 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   chk(cudaMalloc(&L->coef, (size_t)3 * R * p->nv * sizeof(float)));
   chk(cudaMalloc(&L->coef2, (size_t)3 * R * p->nv * sizeof(float)));
   chk(cudaMalloc(&L->gpart, (size_t)((R + 7) / 8) * 4 * p->nv * sizeof(float)));
+  if (L->fft_y) chk(cudaMalloc(&L->coefT, (size_t)3 * R * p->nv * sizeof(float)));
   chk(cudaMalloc(&L->a1_hi, rny * L->k1 * 2));
   chk(cudaMalloc(&L->a1_lo, rny * L->k1 * 2));
   chk(cudaMalloc(&L->a23_hi, rnk * L->k23 * 2));
@@ -837,24 +1057,38 @@ int lowrank_jhw(Plan* p, const float2* w, float* g, cudaStream_t st) {
   return lr_adjoint_dft_and_final(p, g, p->gate, st);
 }
 
-template <int R>
-static cudaError_t launch_gram_t(const Plan& p, const LowRank& L, const int* gate, cudaStream_t st) {
+// SPLIT: write G as the split-BF16 operand of the adjoint phase-encode GEMM; else as
+// float2 rows [(ix, r)][ky] into gout (the FFT path)
+template <int R, bool SPLIT>
+static cudaError_t launch_gram_t(const Plan& p, const LowRank& L, float2* gout, const int* gate, cudaStream_t st) {
   const size_t sm = (size_t)L.gram_rows_max * (R + 1) * sizeof(float);
   const dim3 grid((p.ny + 31) / 32, (p.nx + 7) / 8);
   __nv_bfloat16* hi = (__nv_bfloat16*)L.a23_hi;
   __nv_bfloat16* lo = (__nv_bfloat16*)L.a23_lo;
   if (L.ky_count_max <= kGramShort) {
-    cudaError_t e =
-        cudaFuncSetAttribute(lr_gram_short_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(lr_gram_short_kernel<R, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
     if (e != cudaSuccess) return e;
-    lr_gram_short_kernel<R><<<grid, dim3(32, 8), sm, st>>>(L.H, 2 * p.ny, L.Ug, L.kyptr, p.nx, p.ny, hi, lo, L.k23,
-                                                            gate);
+    lr_gram_short_kernel<R, SPLIT><<<grid, dim3(32, 8), sm, st>>>(L.H, 2 * p.ny, L.Ug, L.kyptr, p.nx, p.ny, hi, lo,
+                                                                   L.k23, gout, gate);
   } else {
-    cudaError_t e = cudaFuncSetAttribute(lr_gram_t_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e =
+        cudaFuncSetAttribute(lr_gram_t_kernel<R, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    lr_gram_t_kernel<R><<<grid, dim3(32, 8), sm, st>>>(L.H, 2 * p.ny, L.Ug, L.kyptr, p.nx, p.ny, hi, lo, L.k23, gate);
+    lr_gram_t_kernel<R, SPLIT><<<grid, dim3(32, 8), sm, st>>>(L.H, 2 * p.ny, L.Ug, L.kyptr, p.nx, p.ny, hi, lo, L.k23,
+                                                               gout, gate);
   }
   return cudaGetLastError();
+}
+
+template <bool SPLIT>
+static cudaError_t launch_gram(const Plan& p, const LowRank& L, float2* gout, const int* gate, cudaStream_t st) {
+  switch (L.R) {
+    case 8: return launch_gram_t<8, SPLIT>(p, L, gout, gate, st);
+    case 16: return launch_gram_t<16, SPLIT>(p, L, gout, gate, st);
+    case 24: return launch_gram_t<24, SPLIT>(p, L, gout, gate, st);
+    default: return launch_gram_t<32, SPLIT>(p, L, gout, gate, st);
+  }
 }
 
 // J^H J v for a fully sampled readout: prep -> phase-encode DFT -> Gram through the TR axis
@@ -878,12 +1112,7 @@ static int lowrank_jhjv_full_readout(Plan* p, const float* v, float* out, double
   }
   if (e == cudaSuccess) {
     Span sp(p, MRSTAT_K_VECTOR, st);
-    switch (R) {
-      case 8: e = launch_gram_t<8>(*p, L, gate, st); break;
-      case 16: e = launch_gram_t<16>(*p, L, gate, st); break;
-      case 24: e = launch_gram_t<24>(*p, L, gate, st); break;
-      default: e = launch_gram_t<32>(*p, L, gate, st); break;
-    }
+    e = launch_gram<true>(*p, L, nullptr, gate, st);
   }
   if (e == cudaSuccess) {
     Span sp(p, MRSTAT_K_XDFT_ADJ, st);
@@ -907,8 +1136,82 @@ static int lowrank_jhjv_full_readout(Plan* p, const float* v, float* out, double
   return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank J^H J v");
 }
 
+template <int N1>
+static cudaError_t launch_fft_pair(Plan* p, const float* v, bool prep, double* vdot, float* out, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  const int nx = p->nx, ny = p->ny, R = L.R;
+  // one block per image column (grid capped at the reduction scratch for the fused dot)
+  const int grid = std::min(nx, kRedBlocks);
+  if (prep) {
+    const size_t sm = sizeof(float2) * ((size_t)ny + (size_t)R * (ny + 1) + 8 * (size_t)ny);
+    cudaError_t e = cudaFuncSetAttribute(lr_prep_fft_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    lr_prep_fft_kernel<N1><<<grid, 256, sm, st>>>(v, L.coefT, p->rho, p->maskf, p->roots, nx, ny, p->nv, R,
+                                                  reinterpret_cast<float2*>(L.H), p->gate);
+  } else {
+    const size_t sm = sizeof(float2) * ((size_t)ny + (size_t)R * (ny + 1));
+    cudaError_t e =
+        cudaFuncSetAttribute(lr_final_fft_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    lr_final_fft_kernel<N1><<<grid, 256, sm, st>>>(reinterpret_cast<const float2*>(L.Y3), L.coefT, p->rho, p->maskf,
+                                                   p->roots, nx, ny, p->nv, R, (float)nx, out, v, p->red, p->ticket,
+                                                   vdot, p->gate);
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_fft_stage(Plan* p, const float* v, bool prep, double* vdot, float* out, cudaStream_t st) {
+  switch (p->ny / 32) {
+    case 1: return launch_fft_pair<1>(p, v, prep, vdot, out, st);
+    case 2: return launch_fft_pair<2>(p, v, prep, vdot, out, st);
+    case 3: return launch_fft_pair<3>(p, v, prep, vdot, out, st);
+    case 4: return launch_fft_pair<4>(p, v, prep, vdot, out, st);
+    case 5: return launch_fft_pair<5>(p, v, prep, vdot, out, st);
+    case 6: return launch_fft_pair<6>(p, v, prep, vdot, out, st);
+    case 7: return launch_fft_pair<7>(p, v, prep, vdot, out, st);
+    default: return launch_fft_pair<8>(p, v, prep, vdot, out, st);
+  }
+}
+
+// The image-column copy of the coefficients, refreshed when they changed.
+static cudaError_t ensure_coef_columns(Plan* p, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  if (!L.coefT_dirty && L.coefT_src == L.coef) return cudaSuccess;
+  const dim3 grid((p->nx + 31) / 32, (p->ny + 31) / 32, 3 * L.R);
+  lr_coef_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(L.coef, p->nx, p->ny, L.coefT);
+  L.coefT_src = L.coef;
+  L.coefT_dirty = false;
+  return cudaGetLastError();
+}
+
+// J^H J v for a fully sampled readout and ny = 32 N1: prep with the factorised
+// phase-encode DFT -> Gram through the TR axis -> factorised adjoint DFT fused with the
+// contraction (and <v, J^H J v>), times nx for the cancelled readout DFT pair.
+static int lowrank_jhjv_fft(Plan* p, const float* v, float* out, double* vdot, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  cudaError_t e;
+  {
+    Span sp(p, MRSTAT_K_VECTOR, st);
+    e = ensure_coef_columns(p, st);
+  }
+  if (e == cudaSuccess) {
+    Span sp(p, MRSTAT_K_YCONTRACT, st);
+    e = launch_fft_stage(p, v, true, nullptr, nullptr, st);
+  }
+  if (e == cudaSuccess) {
+    Span sp(p, MRSTAT_K_VECTOR, st);
+    e = launch_gram<false>(*p, L, reinterpret_cast<float2*>(L.Y3), p->gate, st);
+  }
+  if (e == cudaSuccess) {
+    Span sp(p, MRSTAT_K_JHW_DOT, st);
+    e = launch_fft_stage(p, v, false, vdot, out, st);
+  }
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank J^H J v (factorised DFT)");
+}
+
 int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot) {
   LowRank& L = *p->lr;
+  if (L.fft_y) return lowrank_jhjv_fft(p, v, out, vdot, st);
   if (L.full_readout) return lowrank_jhjv_full_readout(p, v, out, vdot, st);
   if (vdot != nullptr) {
     const int s = lowrank_jhjv(p, v, out, st, nullptr);

@@ -23,6 +23,9 @@ struct LowRank {
   float* coef = nullptr;           // [3][R][nv]: c, dc/dlnT1, dc/dlnT2 (masked)
   float* coef2 = nullptr;          // [3][R][nv]: trial point of the surrogate Gauss-Newton phase
   float* gpart = nullptr;          // [ceil(R/8)][4][nv]: per-chunk partial sums of J^H J v
+  float* coefT = nullptr;          // [3 R][nx][ny]: coef in image-column order (factorised-DFT path)
+  const float* coefT_src = nullptr;  // the coef buffer coefT was made from
+  bool coefT_dirty = true;         // coef changed in place since
   void *a1_hi = nullptr, *a1_lo = nullptr;    // [R ny][k1]   readout-DFT input rows
   void *a23_hi = nullptr, *a23_lo = nullptr;  // [R nkx][k23] phase-encode DFT input rows
   void *a4_hi = nullptr, *a4_lo = nullptr;    // [R ny][k4]   readout adjoint input rows
@@ -35,6 +38,7 @@ struct LowRank {
   TcOperand op_a1, op_a23, op_a4, op_by, op_bya;
   bool active = false;             // the plan's current linearisation is this low-rank one
   bool full_readout = false;       // nkx == nx: J^H J v skips the readout DFT pair
+  bool fft_y = false;              // ... and ny = 32 N1 (N1 <= 8): factorised phase-encode DFT
   int sms = 1;                     // SM count (grid of the Gram kernel)
 };
 

@@ -104,6 +104,7 @@ int mrstat_lowrank_linearize(mrstat_plan* plan_, const float* alpha, const float
     e = cudaMemcpyAsync(L.coef, coef, (size_t)3 * L.R * p->nv * sizeof(float), cudaMemcpyDeviceToDevice, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "low-rank coefficients");
+  L.coefT_dirty = true;
   L.active = true;
   p->linearized = true;
   return MRSTAT_OK;

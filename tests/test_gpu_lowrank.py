@@ -66,9 +66,11 @@ def test_time_basis_matches_numpy_svd(mr):
     assert res_gpu < 1.01 * res_ref
 
 
-# the last three have nkx == nx: J^H J v takes the path without the readout DFT pair
+# nkx == nx from the third case on: J^H J v takes the path without the readout DFT pair;
+# ny = 32 N1 (64, 96, 224, 256) takes the factorised phase-encode DFT on top
 @pytest.mark.parametrize("case", [(40, 24, 5, 6, 48, 16), (33, 17, 3, 3, 30, 8), (64, 64, 5, 0, 64, 32),
-                                  (36, 20, 3, 2, 36, 24), (1, 12, 2, 1, 1, 8)])
+                                  (36, 20, 3, 2, 36, 24), (1, 12, 2, 1, 1, 8), (24, 96, 2, 3, 24, 16),
+                                  (8, 224, 1, 0, 8, 8), (13, 256, 1, 1, 13, 24)])
 def test_lowrank_products_match_projected_oracle(mr, case):
     nx, ny, fills, extra, nkx, R = case
     seq = synth.make_sequence(nx, ny, fills, 7.8, 3.9, seed=5, nkx=nkx, extra_trs=extra)
