@@ -402,8 +402,20 @@ def main():
     per_launch = {k: stats[k]["ms"] / max(stats[k]["timed"], 1) for k in all_kernels}
     lowrank_like = args.form in ("lowrank", "surrogate")
     full_readout = nkx == nx
+    column_bytes = None
+    max_trs_per_ky = int(np.bincount(np.mod(np.asarray(seq.ky), ny), minlength=ny).max())
     fft_y = full_readout and ny % 32 == 0 and ny // 32 <= 8
-    if lowrank_like and fft_y:
+    if lowrank_like and fft_y and max_trs_per_ky <= 8:
+        # the whole product in one kernel per image column (FP32 CUDA cores): count its
+        # arithmetic (h, forward and adjoint factorised DFT, Gram through the TR axis,
+        # contraction) against the FP32-pipe peak; its algorithmic bytes are the
+        # coefficients, v, rho, mask in and g out
+        n1 = ny // 32
+        col_flops = nx * (R * ny * 20 + 2 * R * (256 * n1 * n1 + 992 * n1) + 8 * ntr * R)
+        col_bytes = nv * (12 * R + 16 + 8 + 4 + 16)
+        work = {"jhw_dot": (col_flops, "alu")}
+        column_bytes = col_bytes
+    elif lowrank_like and fft_y:
         # factorised phase-encode DFT on the CUDA cores, fused into the first and last pass
         work = {"ycontract": (nv * (16 + 8 + 4) + 3 * R * nv * 4 + R * nv * 8, "hbm"),   # v, rho, mask, c -> H
                 "jhw_dot": (R * nv * 8 + 3 * R * nv * 4 + nv * (8 + 4) + nv * 16 + nv * 16, "hbm")}  # G, c, v -> g
@@ -433,6 +445,14 @@ def main():
             peak, peak_kind = measured_peak_hbm()
             achieved = amount / (per_launch[k] / 1e3) / 1e9
             unit = "GB/s"
+        elif bound == "alu":
+            # FP32 FMA pipes: SMs x 128 lanes x 2 flops x the maximum SM clock
+            props = torch.cuda.get_device_properties(torch.cuda.current_device())
+            mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+            peak = props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
+            peak_kind = f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz"
+            achieved = amount / (per_launch[k] / 1e3) / 1e12
+            unit = "TFLOP/s"
         else:
             # a kernel timed inside a long step: the sustained BF16 figure
             peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
@@ -471,6 +491,10 @@ def main():
     h = source_hash(os.path.join(ROOT, "paper_1904_13244_gb300", "csrc", src[dom]))
     roofline = roof(dom)
     roofline["traffic"] = NCU_TRAFFIC.get((dom, h))
+    if column_bytes is not None and dom == "jhw_dot":
+        hbm_peak, _ = measured_peak_hbm()
+        gbs = column_bytes / (per_launch[dom] / 1e3) / 1e9
+        roofline["hbm"] = {"algorithmic_bytes": column_bytes, "achieved_GBs": gbs, "frac": gbs / hbm_peak}
     roofline["other_kernels"] = {k: {kk: vv for kk, vv in roof(k).items() if kk in ("achieved", "unit", "frac",
                                                                                       "launch_ms")}
                                  for k in cand if k != dom}

@@ -94,7 +94,7 @@ int grid_for(int64_t n) {
 }
 
 #define GRID_STRIDE(i, n) \
-  for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kT)
+  _Pragma("unroll 4") for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kT)
 
 // r = s - d (complex as float pairs, n floats) and f = 1/2 ||r||^2
 __global__ void __launch_bounds__(kT)

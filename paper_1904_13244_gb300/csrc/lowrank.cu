@@ -694,6 +694,186 @@ lr_final_fft_kernel(const float2* __restrict__ G, const float* __restrict__ coef
   red::finish_reduction<256>(red_part, ticket, vdot, ws);
 }
 
+// ---------------------------------------------------------------------------
+// The whole low-rank J^H J v for one image column ix in one block (ny = 32 N1, at most
+// kGramShort TRs per ky): the R columns h_r(iy) never leave shared memory.
+//   1. warp r forms h_r(iy) for iy = 32 i1 + lane in registers and applies the factorised
+//      phase-encode DFT -> H_r(ky) in shared memory;
+//   2. a warp per ky applies the per-ky Gram through the TR axis (lanes over the basis
+//      index: coalesced rows of U, shuffle reductions), in place;
+//   3. warp r applies the adjoint DFT -> P_r(iy);
+//   4. threads over (iy, half of r) contract with the tangents, the two partial sums are
+//      added in order, and g (masked, times nx) and the block's part of <v, g> are
+//      written; the last block adds the parts.
+// 512 threads (two blocks per SM): warp w owns basis functions r = w and w + 16.
+// ---------------------------------------------------------------------------
+constexpr int kColThreads = 512, kColWarps = kColThreads / 32;
+
+
+
+template <int N1>
+__global__ void __launch_bounds__(kColThreads, 2)
+lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restrict__ v,
+                      const float* __restrict__ coefT, const float2* __restrict__ rho,
+                      const float* __restrict__ maskf, const float2* __restrict__ roots, const float* __restrict__ Ug,
+                      const int* __restrict__ kyptr, int nx, int ny, int nv, int R, float scale,
+                      float* __restrict__ g, double* red_part, unsigned* ticket, double* __restrict__ vdot,
+                      const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  const int ld = ny + 1;
+  extern __shared__ float2 fsm[];
+  float2* rt = fsm;                                        // [ny] w^k
+  float2* hs = rt + ny;                                    // [R][ny + 1]
+  float* vox = reinterpret_cast<float*>(hs + R * ld);      // [6][ny]: v0, v1, m v2, m v3, Re rho, Im rho
+  float* red2 = vox + 6 * ny;                              // [2 halves of r][4][ny]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int brev = (int)(__brev((unsigned)lane) >> 27);
+  const size_t plane = (size_t)nx * ny;
+  for (int e = tid; e < ny; e += kColThreads) rt[e] = roots[e];
+  float sf = 0.f;
+  for (int ix = blockIdx.x; ix < nx; ix += gridDim.x) {
+    for (int iy = tid; iy < ny; iy += kColThreads) {
+      const int j = iy * nx + ix;
+      const float m = maskf[j];
+      const float2 rh = rho[j];
+      vox[iy] = v[j];
+      vox[ny + iy] = v[nv + j];
+      vox[2 * ny + iy] = v[2 * (size_t)nv + j] * m;
+      vox[3 * ny + iy] = v[3 * (size_t)nv + j] * m;
+      vox[4 * ny + iy] = rh.x;
+      vox[5 * ny + iy] = rh.y;
+    }
+    __syncthreads();
+    // 1. h_r and its phase-encode DFT (warp w: r = w, w + 16)
+    for (int r = warp; r < R; r += kColWarps) {
+      const float* cr = coefT + (size_t)r * plane + (size_t)ix * ny;
+      float2 xin[N1];
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1) {
+        const int iy = 32 * i1 + lane;
+        const float c = cr[iy];
+        const float t = fmaf(vox[iy], cr[(size_t)R * plane + iy], vox[ny + iy] * cr[(size_t)2 * R * plane + iy]);
+        const float qr = vox[4 * ny + iy] * t + vox[2 * ny + iy] * c;
+        const float qi = vox[5 * ny + iy] * t + vox[3 * ny + iy] * c;
+        xin[i1] = make_float2(-qi, qr);
+      }
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i1 = 0; i1 < N1; ++i1) {
+          const float2 w = W.w[k1][i1];
+          acc = make_float2(fmaf(w.x, xin[i1].x, fmaf(-w.y, xin[i1].y, acc.x)),
+                            fmaf(w.x, xin[i1].y, fmaf(w.y, xin[i1].x, acc.y)));
+        }
+        acc = cmul(acc, rt[k1 * lane]);  // k1 lane <= 31 (N1 - 1) < ny
+        acc = fft32_warp<false>(acc, rt, N1, lane);
+        hs[r * ld + k1 + N1 * brev] = acc;
+      }
+    }
+    __syncthreads();
+    // 2. per-ky Gram through the TR axis: a warp per ky, lanes over the basis index, so
+    //    each row of U is one 128-byte load and sum_q is a shuffle reduction; the warp
+    //    reads H[.][ky] before it writes G[.][ky] (no other warp touches column ky)
+    for (int ky = warp; ky < ny; ky += kColWarps) {
+      const int ta = kyptr[ky], ns = kyptr[ky + 1] - ta;  // ns <= kGramShort
+      const float2 h = lane < R ? hs[lane * ld + ky] : make_float2(0.f, 0.f);
+      float u[kGramShort];
+      float2 sv[kGramShort];
+#pragma unroll
+      for (int k = 0; k < kGramShort; ++k) {
+        u[k] = 0.f;
+        sv[k] = make_float2(0.f, 0.f);
+        if (k < ns) {
+          u[k] = lane < R ? __ldg(Ug + (size_t)(ta + k) * R + lane) : 0.f;
+          float sr = u[k] * h.x, si = u[k] * h.y;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
+          }
+          sv[k] = make_float2(sr, si);
+        }
+      }
+      float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < kGramShort; ++k) {
+        o.x = fmaf(u[k], sv[k].x, o.x);
+        o.y = fmaf(u[k], sv[k].y, o.y);
+      }
+      if (lane < R) hs[lane * ld + ky] = o;
+    }
+    __syncthreads();
+    // 3. adjoint phase-encode DFT (warp w: r = w, w + 16)
+    for (int r = warp; r < R; r += kColWarps) {
+      float2* x = hs + r * ld;
+      const int i2 = brev;
+      float2 z[N1];
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) z[k1] = x[k1 + N1 * lane];  // k2 = lane
+      __syncwarp();
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const float2 t = fft32_warp<true>(z[k1], rt, N1, lane);  // at i2 = bitrev(lane)
+        z[k1] = cmulc(t, rt[k1 * i2]);
+      }
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+          const float2 w = W.w[k1][i1];
+          acc = make_float2(fmaf(w.x, z[k1].x, fmaf(w.y, z[k1].y, acc.x)),
+                            fmaf(w.x, z[k1].y, fmaf(-w.y, z[k1].x, acc.y)));
+        }
+        x[32 * i1 + i2] = acc;
+      }
+    }
+    __syncthreads();
+    // 4. contraction with the tangents: thread (half of r, iy)
+    {
+      const int iy = tid & 255, half = tid >> 8;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      if (iy < ny) {
+        const float rhx = vox[4 * ny + iy], rhy = vox[5 * ny + iy];
+        const int rq = (R + 1) / 2, ra = half * rq, re = min(R, ra + rq);
+        const float* cc = coefT + (size_t)ix * ny + iy;
+        for (int r = ra; r < re; ++r) {
+          const float2 pv = hs[r * ld + iy];
+          const float c = cc[(size_t)r * plane];
+          const float t1 = cc[(size_t)(R + r) * plane], t2 = cc[(size_t)(2 * R + r) * plane];
+          const float imcp = rhx * pv.y - rhy * pv.x;  // Im(conj(rho) P)
+          a0 = fmaf(t1, imcp, a0);
+          a1 = fmaf(t2, imcp, a1);
+          a2 = fmaf(c, pv.y, a2);
+          a3 = fmaf(-c, pv.x, a3);
+        }
+        red2[(half * 4 + 0) * ny + iy] = a0;
+        red2[(half * 4 + 1) * ny + iy] = a1;
+        red2[(half * 4 + 2) * ny + iy] = a2;
+        red2[(half * 4 + 3) * ny + iy] = a3;
+      }
+      __syncthreads();
+      if (tid < ny) {
+        const int j = tid * nx + ix;
+        const float m = maskf[j] * scale;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float val = (red2[k * ny + tid] + red2[(4 + k) * ny + tid]) * m;
+          g[(size_t)k * nv + j] = val;
+          if (vdot != nullptr) sf = fmaf(v[(size_t)k * nv + j], val, sf);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (vdot == nullptr) return;
+  __shared__ double ws[kColWarps];
+  const double t = red::block_sum<kColThreads>((double)sf, ws);
+  if (threadIdx.x == 0) red_part[blockIdx.x] = t;
+  red::finish_reduction<kColThreads>(red_part, ticket, vdot, ws);
+}
+
 // Partial sums over one chunk of 8 basis functions (blockIdx.z) of
 //   g_k,j = Re sum_r conj(dh_r,j/dv_k) P[(ix, r)][iy]   (P rows (ix, r), columns 2 iy + re/im)
 // into part[z][4][nv].  Block (16, 16): a 16 x 16 voxel tile, one voxel per thread; P
@@ -877,6 +1057,15 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   L->full_readout = p->nkx == p->nx && (size_t)L->gram_rows_max * (R + 1) * sizeof(float) <= (size_t)L->smem_optin;
   // factorised phase-encode DFT: ny = 32 N1 with N1 <= 8
   L->fft_y = L->full_readout && ny % 32 == 0 && ny / 32 <= 8;
+  if (L->fft_y) {
+    const int n1 = ny / 32;
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b) {
+        const double ang = -2.0 * M_PI * (double)((a * b) % n1) / (double)n1;
+        L->dft_small.w[a][b] = (a < n1 && b < n1) ? make_float2((float)std::cos(ang), (float)std::sin(ang))
+                                                  : make_float2(0.f, 0.f);
+      }
+  }
   std::vector<float> M((size_t)ny * R * R, 0.f);
   for (int k = 0; k < ny; ++k)
     for (int a = 0; a < R; ++a)
@@ -1184,6 +1373,34 @@ static cudaError_t ensure_coef_columns(Plan* p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int N1>
+static cudaError_t launch_column_t(Plan* p, const float* v, double* vdot, float* out, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  const int nx = p->nx, ny = p->ny, R = L.R;
+  const size_t sm = sizeof(float2) * ((size_t)ny + (size_t)R * (ny + 1)) + sizeof(float) * 14 * (size_t)ny;
+  cudaError_t e =
+      cudaFuncSetAttribute(lr_jhjv_column_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(nx, kRedBlocks);
+  lr_jhjv_column_kernel<N1><<<grid, kColThreads, sm, st>>>(L.dft_small, v, L.coefT, p->rho, p->maskf, p->roots,
+                                                           L.Ug, L.kyptr, nx, ny, p->nv, R, (float)nx, out, p->red,
+                                                           p->ticket, vdot, p->gate);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_column(Plan* p, const float* v, double* vdot, float* out, cudaStream_t st) {
+  switch (p->ny / 32) {
+    case 1: return launch_column_t<1>(p, v, vdot, out, st);
+    case 2: return launch_column_t<2>(p, v, vdot, out, st);
+    case 3: return launch_column_t<3>(p, v, vdot, out, st);
+    case 4: return launch_column_t<4>(p, v, vdot, out, st);
+    case 5: return launch_column_t<5>(p, v, vdot, out, st);
+    case 6: return launch_column_t<6>(p, v, vdot, out, st);
+    case 7: return launch_column_t<7>(p, v, vdot, out, st);
+    default: return launch_column_t<8>(p, v, vdot, out, st);
+  }
+}
+
 // J^H J v for a fully sampled readout and ny = 32 N1: prep with the factorised
 // phase-encode DFT -> Gram through the TR axis -> factorised adjoint DFT fused with the
 // contraction (and <v, J^H J v>), times nx for the cancelled readout DFT pair.
@@ -1193,6 +1410,12 @@ static int lowrank_jhjv_fft(Plan* p, const float* v, float* out, double* vdot, c
   {
     Span sp(p, MRSTAT_K_VECTOR, st);
     e = ensure_coef_columns(p, st);
+  }
+  if (e == cudaSuccess && L.ky_count_max <= kGramShort) {
+    // the whole product in one kernel, one block per image column
+    Span sp(p, MRSTAT_K_JHW_DOT, st);
+    e = launch_column(p, v, vdot, out, st);
+    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank J^H J v (column kernel)");
   }
   if (e == cudaSuccess) {
     Span sp(p, MRSTAT_K_YCONTRACT, st);

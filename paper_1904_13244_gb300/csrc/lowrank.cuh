@@ -9,6 +9,13 @@ namespace mrstat {
 
 constexpr int kMaxRank = 32;
 
+// The N1-point DFT matrix wN1^(k1 i1) = w^(32 k1 i1) (N1 <= 8) of the factorised
+// phase-encode DFT, passed to the kernel by value so that its entries are constant-bank
+// operands of the multiply-adds.
+struct DftSmall {
+  float2 w[8][8];
+};
+
 struct LowRank {
   int R = 0;
   int k1 = 0, k23 = 0, k4 = 0;     // padded K of the operands (2 nx, 2 ny, 2 nkx)
@@ -39,6 +46,7 @@ struct LowRank {
   bool active = false;             // the plan's current linearisation is this low-rank one
   bool full_readout = false;       // nkx == nx: J^H J v skips the readout DFT pair
   bool fft_y = false;              // ... and ny = 32 N1 (N1 <= 8): factorised phase-encode DFT
+  DftSmall dft_small;              // the N1-point DFT matrix of the factorised path
   int sms = 1;                     // SM count (grid of the Gram kernel)
 };
 

@@ -26,6 +26,7 @@ dot_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n, 
            unsigned* ticket, double* __restrict__ out) {
   __shared__ double ws[kT / 32];
   float sf = 0.f;
+#pragma unroll 4
   for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
     sf = fmaf(a[i], b[i], sf);
   const double s = block_sum<kT>((double)sf, ws);
@@ -64,6 +65,7 @@ cg_update_xr_kernel(float* __restrict__ x, float* __restrict__ r, const float* _
   __syncthreads();
   const float al = s_alpha;
   float sf = 0.f;
+#pragma unroll 4
   for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
     float ri = r[i];
     if (s_apply) {
@@ -91,12 +93,15 @@ cg_update_p_kernel(float* __restrict__ p, const float* __restrict__ r, int64_t n
   __syncthreads();
   if (!s_apply) return;
   const float beta = s_beta;
+#pragma unroll 4
   for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
     p[i] = fmaf(beta, p[i], r[i]);
 }
 
+// About four elements per thread: fewer blocks to schedule and fewer partials for the
+// last block to add than one element per thread, with the loads unrolled by four.
 int grid_for(int64_t n) {
-  int64_t b = (n + kT - 1) / kT;
+  int64_t b = (n + 4 * kT - 1) / (4 * kT);
   if (b > kRedBlocks) b = kRedBlocks;
   return (int)(b > 0 ? b : 1);
 }

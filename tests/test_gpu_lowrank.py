@@ -67,10 +67,12 @@ def test_time_basis_matches_numpy_svd(mr):
 
 
 # nkx == nx from the third case on: J^H J v takes the path without the readout DFT pair;
-# ny = 32 N1 (64, 96, 224, 256) takes the factorised phase-encode DFT on top
+# ny = 32 N1 (64, 96, 224, 256, 32) takes the factorised phase-encode DFT on top, in one
+# kernel per image column when no ky has more than 8 TRs (the last case has 10: three
+# kernels)
 @pytest.mark.parametrize("case", [(40, 24, 5, 6, 48, 16), (33, 17, 3, 3, 30, 8), (64, 64, 5, 0, 64, 32),
                                   (36, 20, 3, 2, 36, 24), (1, 12, 2, 1, 1, 8), (24, 96, 2, 3, 24, 16),
-                                  (8, 224, 1, 0, 8, 8), (13, 256, 1, 1, 13, 24)])
+                                  (8, 224, 1, 0, 8, 8), (13, 256, 1, 1, 13, 24), (16, 32, 10, 0, 16, 8)])
 def test_lowrank_products_match_projected_oracle(mr, case):
     nx, ny, fills, extra, nkx, R = case
     seq = synth.make_sequence(nx, ny, fills, 7.8, 3.9, seed=5, nkx=nkx, extra_trs=extra)
