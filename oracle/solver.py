@@ -7,6 +7,9 @@ Pieces, in the order the paper uses them (Methods, "Reconstructions"):
   algebraically equivalent normal-equations form).  T1 = 1000 ms, T2 = 100 ms,
   B1 = 1 for alpha_0.  The unknowns are (Re rho, Im rho) and the operator is the
   rho-block of J_s, which is exactly linear in rho.
+* ``ls_rho``: the same least-squares solution computed exactly (minimum norm) from the
+  dense matrix M(alpha_0) by an SVD-based solver -- the plain definition of what the
+  Krylov solver approximates.
 * ``draw_mask``: voxels whose initial |rho| exceeds a fraction of the maximum.
 * ``steihaug_cg``: truncated CG on the Gauss-Newton model
   m(p) = f + g.p + 1/2 p.B p with B = Re(J^H J) (Eq. 4) inside ||p|| <= Delta,
@@ -31,7 +34,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import model
+from . import encoding, model
 
 
 # ----------------------------------------------------------------------------
@@ -74,6 +77,22 @@ def cgls_rho(lin: model.Linearization, d, iters: int = 50):
         p = s + (gamma_new / gamma) * p
         gamma = gamma_new
     return x[0] + 1j * x[1]
+
+
+def ls_rho(lin: model.Linearization, d):
+    """Minimum-norm least-squares rho for fixed (T1, T2, B1): argmin ||d - M rho||, with
+    M[(n, kx), j] = m_j[n] E_{ky(n)}[kx, j] built densely (small cases only) and solved
+    by numpy's SVD-based lstsq.  Returns complex rho [nv]."""
+    seq = lin.seq
+    nv = lin.m.shape[1]
+    M = np.zeros((seq.ntr, seq.nkx, nv), np.complex128)
+    ky = np.asarray(seq.ky)
+    for u in np.unique(ky):
+        sel = np.nonzero(ky == u)[0]
+        e = encoding.phase_matrix(seq, int(u))
+        M[sel] = lin.m[sel][:, None, :] * e[None, :, :]
+    rho, *_ = np.linalg.lstsq(M.reshape(seq.ntr * seq.nkx, nv), np.asarray(d).reshape(-1), rcond=None)
+    return rho
 
 
 def draw_mask(rho, threshold: float = 0.1):
@@ -226,8 +245,9 @@ def gauss_newton(seq, d, alpha0, b1=None, mask=None, opts: GNOptions | None = No
 
 
 def initial_alpha(seq, d, nv, rho_iters=50, t1_ms=1000.0, t2_ms=100.0, b1=None,
-                  mask_threshold=0.1, estimate_b1=False):
-    """alpha_0 of the paper (T1 = 1000 ms, T2 = 100 ms, B1 = 1, rho from CGLS) and its mask."""
+                  mask_threshold=0.1, estimate_b1=False, exact=False):
+    """alpha_0 of the paper (T1 = 1000 ms, T2 = 100 ms, B1 = 1, rho the least-squares
+    solution: rho_iters CGLS steps, or with exact=True the exact solution) and its mask."""
     npar = 5 if estimate_b1 else 4
     a0 = np.zeros((npar, nv))
     a0[0] = np.log(t1_ms)
@@ -235,7 +255,7 @@ def initial_alpha(seq, d, nv, rho_iters=50, t1_ms=1000.0, t2_ms=100.0, b1=None,
     if estimate_b1:
         a0[4] = 1.0
     lin = model.linearize(seq, a0, b1)
-    rho = cgls_rho(lin, d, rho_iters)
+    rho = ls_rho(lin, d) if exact else cgls_rho(lin, d, rho_iters)
     mask = draw_mask(rho, mask_threshold)
     a0[2] = np.where(mask, rho.real, 0.0)
     a0[3] = np.where(mask, rho.imag, 0.0)

@@ -2,9 +2,10 @@
 // the CGLS proton-density initialisation and the mask (Methods, "Reconstructions").
 //
 // The truncated CG runs entirely on the device: its float64 scalars live in a small
-// device block, tiny single-thread kernels take the Steihaug decisions (negative
-// curvature, trust boundary, tolerance, iteration count), and once CG has stopped
-// the product kernels return at once through the plan's gate flag.  The host waits
+// device block, the last block of each reduction takes the Steihaug decisions (negative
+// curvature, trust boundary, tolerance, iteration count) from the sums it has just
+// formed, and once CG has stopped the product kernels return at once through the plan's
+// gate flag.  The host waits
 // once per outer iteration, to evaluate the trust-region ratio in float64.
 #include <chrono>
 #include <cmath>
@@ -61,16 +62,17 @@ __device__ __forceinline__ void block_sum_n(double (&v)[NV], double* ws /* [NV][
 }
 
 // After thread 0 of every block stored its NV partials in part[k * gridDim.x + block], the
-// last block sums them in block order into out[0..NV) and resets the ticket.
+// last block sums them in block order into out[0..NV) and resets the ticket; returns true
+// in the last block (where thread 0 may then act on the sums).
 template <int NV>
-__device__ __forceinline__ void finish_n(double* part, unsigned* ticket, double* out, double* ws) {
+__device__ __forceinline__ bool finish_n(double* part, unsigned* ticket, double* out, double* ws) {
   __shared__ bool last;
   if (threadIdx.x == 0) {
     __threadfence();
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
   double v[NV];
 #pragma unroll
@@ -85,11 +87,15 @@ __device__ __forceinline__ void finish_n(double* part, unsigned* ticket, double*
     for (int k = 0; k < NV; ++k) out[k] = v[k];
     *ticket = 0u;
   }
+  return true;
 }
 
+// About four elements per thread (float32 partial sums over those, float64 from the warp
+// level up), at most kRedBlocks blocks: the plan's reduction scratch holds five partial
+// vectors of that length.
 int grid_for(int64_t n) {
-  int64_t b = (n + kT - 1) / kT;
-  if (b > kRedBlocks / 5) b = kRedBlocks / 5;  // room for five partial vectors
+  int64_t b = (n + 4 * kT - 1) / (4 * kT);
+  if (b > kRedBlocks) b = kRedBlocks;
   return (int)(b > 0 ? b : 1);
 }
 
@@ -101,12 +107,13 @@ __global__ void __launch_bounds__(kT)
 residual_kernel(const float* __restrict__ s, const float* __restrict__ d, float* __restrict__ r,
                 int64_t n, double* part, unsigned* ticket, double* f) {
   __shared__ double ws[8];
-  double acc[1] = {0.0};
+  float a = 0.f;
   GRID_STRIDE(i, n) {
     const float v = s[i] - d[i];
     r[i] = v;
-    acc[0] = fma((double)v, (double)v, acc[0]);
+    a = fmaf(v, v, a);
   }
+  double acc[1] = {(double)a};
   block_sum_n<1>(acc, ws);
   if (threadIdx.x == 0) part[blockIdx.x] = 0.5 * acc[0];
   finish_n<1>(part, ticket, f, ws);
@@ -136,14 +143,15 @@ __global__ void __launch_bounds__(kT)
 st_init_kernel(const float* __restrict__ g, float* __restrict__ z, float* __restrict__ res,
                float* __restrict__ dir, int64_t n, double* part, unsigned* ticket, double* rr) {
   __shared__ double ws[8];
-  double acc[1] = {0.0};
+  float a = 0.f;
   GRID_STRIDE(i, n) {
     const float v = g[i];
     z[i] = 0.f;
     res[i] = v;
     dir[i] = -v;
-    acc[0] = fma((double)v, (double)v, acc[0]);
+    a = fmaf(v, v, a);
   }
+  double acc[1] = {(double)a};
   block_sum_n<1>(acc, ws);
   if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
   finish_n<1>(part, ticket, rr, ws);
@@ -161,42 +169,13 @@ __global__ void st_start_kernel(double* sc, int* si) {
   si[I_EXIT] = rr > 0.0 ? MRSTAT_CG_MAX_ITER : MRSTAT_CG_ZERO_GRADIENT;
 }
 
-// dir.q, res.dir, dir.dir, z.dir, z.z in one pass
-__global__ void __launch_bounds__(kT)
-multidot_kernel(const float* __restrict__ dir, const float* __restrict__ q, const float* __restrict__ res,
-                const float* __restrict__ z, int64_t n, const int* __restrict__ si, double* part,
-                unsigned* ticket, double* out) {
-  if (si[I_ACTIVE] == 0) return;
-  __shared__ double ws[5 * 8];
-  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  GRID_STRIDE(i, n) {
-    const double d = dir[i], qq = q[i], r = res[i], zz = z[i];
-    acc[0] = fma(d, qq, acc[0]);
-    acc[1] = fma(r, d, acc[1]);
-    acc[2] = fma(d, d, acc[2]);
-    acc[3] = fma(zz, d, acc[3]);
-    acc[4] = fma(zz, zz, acc[4]);
-  }
-  block_sum_n<5>(acc, ws);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) part[k * gridDim.x + blockIdx.x] = acc[k];
-  }
-  finish_n<5>(part, ticket, out, ws);
-}
-
 __device__ double to_boundary(double zz, double zd, double dd, double delta) {
   const double disc = fmax(zd * zd + dd * (delta * delta - zz), 0.0);
   return (-zd + sqrt(disc)) / dd;
 }
 
 // One Steihaug decision (Nocedal & Wright Alg. 7.2): choose the step along dir.
-__global__ void st_step_kernel(double* sc, int* si, double delta) {
-  if (si[I_ACTIVE] == 0) {
-    sc[S_COEF] = 0.0;
-    si[I_CONT] = 0;
-    return;
-  }
+__device__ void st_step(double* sc, int* si, double delta) {
   const double dBd = sc[S_DBD], rd = sc[S_RD], dd = sc[S_DD], zd = sc[S_ZD], zz = sc[S_ZZ];
   si[I_STEPS] += 1;
   if (!(dBd > 0.0)) {
@@ -224,33 +203,41 @@ __global__ void st_step_kernel(double* sc, int* si, double delta) {
   si[I_CONT] = 1;
 }
 
-// z += coef dir; while continuing also res += coef q and rr_new = res.res
+// dir.q, res.dir, dir.dir, z.dir, z.z in one pass
 __global__ void __launch_bounds__(kT)
-st_update_kernel(float* __restrict__ z, float* __restrict__ res, const float* __restrict__ dir,
-                 const float* __restrict__ q, int64_t n, const double* __restrict__ sc,
-                 const int* __restrict__ si, double* part, unsigned* ticket, double* rr_new) {
-  const double coef = sc[S_COEF];
-  const int cont = si[I_CONT];
-  if (coef == 0.0 && !cont) return;
-  __shared__ double ws[8];
-  const float c = (float)coef;
-  double acc[1] = {0.0};
-  GRID_STRIDE(i, n) {
-    z[i] = fmaf(c, dir[i], z[i]);
-    if (cont) {
-      const float r = fmaf(c, q[i], res[i]);
-      res[i] = r;
-      acc[0] = fma((double)r, (double)r, acc[0]);
+multidot_kernel(const float* __restrict__ dir, const float* __restrict__ q, const float* __restrict__ res,
+                const float* __restrict__ z, int64_t n, double* sc, int* si, double delta, double* part,
+                unsigned* ticket) {
+  // every block reads I_ACTIVE before its ticket; the step decision below runs in the last
+  // block only, after all the others have taken theirs
+  if (si[I_ACTIVE] == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // no step once CG has stopped
+      sc[S_COEF] = 0.0;
+      si[I_CONT] = 0;
     }
+    return;
   }
-  if (!cont) return;
-  block_sum_n<1>(acc, ws);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
-  finish_n<1>(part, ticket, rr_new, ws);
+  __shared__ double ws[5 * 8];
+  float a[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  GRID_STRIDE(i, n) {
+    const float d = dir[i], qq = q[i], r = res[i], zz = z[i];
+    a[0] = fmaf(d, qq, a[0]);
+    a[1] = fmaf(r, d, a[1]);
+    a[2] = fmaf(d, d, a[2]);
+    a[3] = fmaf(zz, d, a[3]);
+    a[4] = fmaf(zz, zz, a[4]);
+  }
+  double acc[5] = {(double)a[0], (double)a[1], (double)a[2], (double)a[3], (double)a[4]};
+  block_sum_n<5>(acc, ws);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) part[k * gridDim.x + blockIdx.x] = acc[k];
+  }
+  if (finish_n<5>(part, ticket, sc + S_DBD, ws) && threadIdx.x == 0) st_step(sc, si, delta);
 }
 
-__global__ void st_beta_kernel(double* sc, int* si, double rel_tol, int max_steps) {
-  if (si[I_CONT] == 0) return;
+// tolerance and iteration-count test after a continuing step; beta for the next direction
+__device__ void st_beta(double* sc, int* si, double rel_tol, int max_steps) {
   const double rr_new = sc[S_RR_NEW];
   if (sqrt(rr_new) <= rel_tol * sc[S_GNORM]) {
     si[I_ACTIVE] = 0;
@@ -265,6 +252,33 @@ __global__ void st_beta_kernel(double* sc, int* si, double rel_tol, int max_step
     si[I_CONT] = 0;
     si[I_EXIT] = MRSTAT_CG_MAX_ITER;
   }
+}
+
+// z += coef dir; while continuing also res += coef q and rr_new = res.res, then (last
+// block) the tolerance and iteration-count test
+__global__ void __launch_bounds__(kT)
+st_update_kernel(float* __restrict__ z, float* __restrict__ res, const float* __restrict__ dir,
+                 const float* __restrict__ q, int64_t n, double* sc, int* si, double rel_tol, int max_steps,
+                 double* part, unsigned* ticket) {
+  const double coef = sc[S_COEF];
+  const int cont = si[I_CONT];
+  if (coef == 0.0 && !cont) return;
+  __shared__ double ws[8];
+  const float c = (float)coef;
+  float a = 0.f;
+  GRID_STRIDE(i, n) {
+    z[i] = fmaf(c, dir[i], z[i]);
+    if (cont) {
+      const float r = fmaf(c, q[i], res[i]);
+      res[i] = r;
+      a = fmaf(r, r, a);
+    }
+  }
+  if (!cont) return;
+  double acc[1] = {(double)a};
+  block_sum_n<1>(acc, ws);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+  if (finish_n<1>(part, ticket, sc + S_RR_NEW, ws) && threadIdx.x == 0) st_beta(sc, si, rel_tol, max_steps);
 }
 
 // dir = -res + beta dir
@@ -305,8 +319,9 @@ __global__ void trial_kernel(const float* __restrict__ alpha, const float* __res
 __global__ void z_norm_kernel(const float* __restrict__ z, int64_t n, double* part, unsigned* ticket,
                               double* out) {
   __shared__ double ws[8];
-  double acc[1] = {0.0};
-  GRID_STRIDE(i, n) acc[0] = fma((double)z[i], (double)z[i], acc[0]);
+  float a = 0.f;
+  GRID_STRIDE(i, n) a = fmaf(z[i], z[i], a);
+  double acc[1] = {(double)a};
   block_sum_n<1>(acc, ws);
   if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
   finish_n<1>(part, ticket, out, ws);
@@ -506,21 +521,32 @@ struct Solver {
     if (e != cudaSuccess) return cuda_fail(e, "Steihaug init");
     p->gate = si + I_ACTIVE;
     int status = MRSTAT_OK;
+    // the low-rank column kernel takes each direction update dir <- -res + beta dir into its
+    // first pass (the update of iteration it - 1 at the start of the product of iteration it)
+    const bool fuse_dir = lowrank_fuses_pupdate(p);
     for (int it = 0; it < inner && status == MRSTAT_OK; ++it) {
-      status = do_jhjv(p, p->gn_dir, p->gn_q, st);
+      if (fuse_dir && it > 0) {
+        PUpdate pu;
+        pu.r = p->gn_res;
+        pu.r_sign = -1.f;
+        pu.beta_num = sc + S_BETA;
+        pu.on_a = si + I_CONT;
+        pu.on_b = si + I_ACTIVE;
+        status = lowrank_jhjv(p, p->gn_dir, p->gn_q, st, nullptr, &pu);
+      } else {
+        status = do_jhjv(p, p->gn_dir, p->gn_q, st);
+      }
       if (status != MRSTAT_OK) break;
       e = vec([&] {
-        multidot_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_dir, p->gn_q, p->gn_res, p->gn_z, n4, si, p->red,
-                                                     p->ticket, sc + S_DBD);
+        multidot_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_dir, p->gn_q, p->gn_res, p->gn_z, n4, sc, si, delta,
+                                                     p->red, p->ticket);
       });
-      if (e == cudaSuccess) e = vec([&] { st_step_kernel<<<1, 1, 0, st>>>(sc, si, delta); });
       if (e == cudaSuccess)
         e = vec([&] {
           st_update_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_z, p->gn_res, p->gn_dir, p->gn_q, n4, sc, si,
-                                                        p->red, p->ticket, sc + S_RR_NEW);
+                                                        rel_tol, inner, p->red, p->ticket);
         });
-      if (e == cudaSuccess) e = vec([&] { st_beta_kernel<<<1, 1, 0, st>>>(sc, si, rel_tol, inner); });
-      if (e == cudaSuccess)
+      if (e == cudaSuccess && !fuse_dir)
         e = vec([&] { st_dir_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_dir, p->gn_res, n4, sc, si); });
       if (e != cudaSuccess) status = cuda_fail(e, "Steihaug iteration");
     }

@@ -24,6 +24,7 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -540,213 +541,103 @@ __global__ void lr_coef_transpose_kernel(const float* __restrict__ coef, int nx,
   }
 }
 
-// One block per image column ix: h_r(iy) = i (rho (v0 dc1_r + v1 dc2_r) + (v2 + i v3) c_r)
-// mask for every iy and r, then the phase-encode DFT of every r column, written as
-// H[(ix, r)][ky] (float2 rows).  Threads over iy for the first part, warps over r for the
-// DFTs.
-template <int N1>
-__global__ void __launch_bounds__(256)
-lr_prep_fft_kernel(const float* __restrict__ v, const float* __restrict__ coefT, const float2* __restrict__ rho,
-                   const float* __restrict__ maskf, const float2* __restrict__ roots, int nx, int ny, int nv, int R,
-                   float2* __restrict__ H, const int* __restrict__ gate) {
-  if (gate != nullptr && *gate == 0) return;
-  const int ld = ny + 1;
-  extern __shared__ float2 fsm[];
-  float2* rt = fsm;              // [ny] w^k
-  float2* hs = rt + ny;          // [R][ny + 1]
-  float2* stg = hs + R * ld;     // [8 warps][ny] output staging
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int brev = (int)(__brev((unsigned)lane) >> 27);
-  const size_t plane = (size_t)nx * ny;
-  for (int e = tid; e < ny; e += 256) rt[e] = roots[e];
-  for (int ix = blockIdx.x; ix < nx; ix += gridDim.x) {
-    for (int iy = tid; iy < ny; iy += 256) {
-      const int j = iy * nx + ix;
-      const float m = maskf[j];
-      const float2 rh = rho[j];
-      const float v0 = v[j], v1 = v[nv + j], v2 = v[2 * (size_t)nv + j] * m, v3 = v[3 * (size_t)nv + j] * m;
-      const float* c0 = coefT + (size_t)ix * ny + iy;
-#pragma unroll 8
-      for (int r = 0; r < R; ++r) {
-        const float c = c0[(size_t)r * plane];
-        const float t = fmaf(v0, c0[(size_t)(R + r) * plane], v1 * c0[(size_t)(2 * R + r) * plane]);
-        const float qr = rh.x * t + v2 * c, qi = rh.y * t + v3 * c;
-        hs[r * ld + iy] = make_float2(-qi, qr);
-      }
-    }
-    __syncthreads();
-    float2* sw = stg + warp * ny;
-    for (int r = warp; r < R; r += 8) {
-      const float2* x = hs + r * ld;
-      float2 xin[N1];
-#pragma unroll
-      for (int i1 = 0; i1 < N1; ++i1) xin[i1] = x[32 * i1 + lane];
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int i1 = 0; i1 < N1; ++i1) {
-          const float2 w = rt[32 * ((k1 * i1) % N1)];
-          acc = make_float2(fmaf(w.x, xin[i1].x, fmaf(-w.y, xin[i1].y, acc.x)),
-                            fmaf(w.x, xin[i1].y, fmaf(w.y, xin[i1].x, acc.y)));
-        }
-        acc = cmul(acc, rt[(k1 * lane) % ny]);
-        acc = fft32_warp<false>(acc, rt, N1, lane);
-        sw[k1 + N1 * brev] = acc;
-      }
-      __syncwarp();
-      float2* dst = H + (size_t)(ix * R + r) * ny;
-      for (int k = lane; k < ny; k += 32) dst[k] = sw[k];
-      __syncwarp();
-    }
-    __syncthreads();
-  }
+// ---------------------------------------------------------------------------
+// The whole low-rank J^H J v for one image column ix in one cluster of two blocks
+// (ny = 32 N1); block c of the pair owns the basis functions r in [c RC, (c + 1) RC),
+// RC = ceil(R / 2), and the R columns h_r(iy) never leave shared memory.
+//   0. each block forms half of the column's voxel data (v, after the fused direction
+//      update when asked, and rho) and stores it into both blocks' shared memory;
+//   1. warp w forms h_r(iy) for iy = 32 i1 + lane in registers for its r and applies the
+//      factorised phase-encode DFT -> H_r(ky);
+//   2. the per-ky Gram through the TR axis: one thread per TR forms the block's part of
+//      s_t = sum_q U[t][q] H_q(ky(t)), the two parts are added (the same sum in both
+//      blocks), then one thread per (r, ky) sums U[t][r] s_t over the TRs of ky;
+//   3. warp w applies the adjoint DFT -> P_r(iy);
+//   4. one thread per iy contracts with the tangents over the block's r, and each block
+//      adds the two partial sums for its half of the column, writes g (masked, times nx)
+//      and its part of <v, g>; the last block adds the parts.
+// Two blocks per column (448 for 224 columns, three per SM) balance the SMs better than
+// one block of twice the size (224 blocks on 152 SMs).
+// ---------------------------------------------------------------------------
+constexpr int kColThreads = 256, kColWarps = kColThreads / 32;
+
+size_t column_smem_bytes(int ny, int R, int ntr) {
+  const size_t rc = (size_t)(R + 1) / 2;
+  return sizeof(float2) * ((size_t)ny + rc * (ny + 1) + 2 * (size_t)ntr) + sizeof(float) * 10 * (size_t)ny;
 }
 
-// One block per image column ix: adjoint phase-encode DFT of G[(ix, r)][ky] for every r,
-// then g_k,j = scale mask_j Re sum_r conj(dh_r,j/dv_k) P_r,j for the column's voxels and,
-// with vdot, the block's part of <v, g> (last-block finish over red / ticket).
 template <int N1>
-__global__ void __launch_bounds__(256)
-lr_final_fft_kernel(const float2* __restrict__ G, const float* __restrict__ coefT, const float2* __restrict__ rho,
-                    const float* __restrict__ maskf, const float2* __restrict__ roots, int nx, int ny, int nv, int R,
-                    float scale, float* __restrict__ g, const float* __restrict__ v, double* red_part,
-                    unsigned* ticket, double* __restrict__ vdot, const int* __restrict__ gate) {
-  if (gate != nullptr && *gate == 0) return;
-  const int ld = ny + 1;
-  extern __shared__ float2 fsm[];
-  float2* rt = fsm;        // [ny]
-  float2* gs = rt + ny;    // [R][ny + 1]
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int i2 = (int)(__brev((unsigned)lane) >> 27);
-  const size_t plane = (size_t)nx * ny;
-  for (int e = tid; e < ny; e += 256) rt[e] = roots[e];
-  float sf = 0.f;
-  for (int ix = blockIdx.x; ix < nx; ix += gridDim.x) {
-    for (int e = tid; e < R * ny; e += 256) {
-      const int r = e / ny, k = e - r * ny;
-      gs[r * ld + k] = G[(size_t)(ix * R + r) * ny + k];
-    }
-    __syncthreads();
-    for (int r = warp; r < R; r += 8) {
-      float2* x = gs + r * ld;
-      float2 z[N1];
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) z[k1] = x[k1 + N1 * lane];  // k2 = lane
-      __syncwarp();
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        const float2 t = fft32_warp<true>(z[k1], rt, N1, lane);  // at i2 = bitrev(lane)
-        z[k1] = cmulc(t, rt[(k1 * i2) % ny]);
-      }
-#pragma unroll
-      for (int i1 = 0; i1 < N1; ++i1) {
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          const float2 w = rt[32 * ((k1 * i1) % N1)];
-          acc = make_float2(fmaf(w.x, z[k1].x, fmaf(w.y, z[k1].y, acc.x)),
-                            fmaf(w.x, z[k1].y, fmaf(-w.y, z[k1].x, acc.y)));
-        }
-        x[32 * i1 + i2] = acc;
-      }
-      __syncwarp();
-    }
-    __syncthreads();
-    for (int iy = tid; iy < ny; iy += 256) {
-      const int j = iy * nx + ix;
-      const float2 rh = rho[j];
-      const float* c0 = coefT + (size_t)ix * ny + iy;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll 8
-      for (int r = 0; r < R; ++r) {
-        const float2 pv = gs[r * ld + iy];
-        const float c = c0[(size_t)r * plane];
-        const float t1 = c0[(size_t)(R + r) * plane], t2 = c0[(size_t)(2 * R + r) * plane];
-        const float imcp = rh.x * pv.y - rh.y * pv.x;  // Im(conj(rho) P)
-        a0 = fmaf(t1, imcp, a0);
-        a1 = fmaf(t2, imcp, a1);
-        a2 = fmaf(c, pv.y, a2);
-        a3 = fmaf(-c, pv.x, a3);
-      }
-      const float m = maskf[j] * scale;
-      a0 *= m;
-      a1 *= m;
-      a2 *= m;
-      a3 *= m;
-      g[j] = a0;
-      g[(size_t)nv + j] = a1;
-      g[2 * (size_t)nv + j] = a2;
-      g[3 * (size_t)nv + j] = a3;
-      if (vdot != nullptr) {
-        sf = fmaf(v[j], a0, sf);
-        sf = fmaf(v[(size_t)nv + j], a1, sf);
-        sf = fmaf(v[2 * (size_t)nv + j], a2, sf);
-        sf = fmaf(v[3 * (size_t)nv + j], a3, sf);
-      }
-    }
-    __syncthreads();
-  }
-  if (vdot == nullptr) return;
-  __shared__ double ws[8];
-  const double t = red::block_sum<256>((double)sf, ws);
-  if (threadIdx.x == 0) red_part[blockIdx.x] = t;
-  red::finish_reduction<256>(red_part, ticket, vdot, ws);
-}
-
-// ---------------------------------------------------------------------------
-// The whole low-rank J^H J v for one image column ix in one block (ny = 32 N1, at most
-// kGramShort TRs per ky): the R columns h_r(iy) never leave shared memory.
-//   1. warp r forms h_r(iy) for iy = 32 i1 + lane in registers and applies the factorised
-//      phase-encode DFT -> H_r(ky) in shared memory;
-//   2. a warp per ky applies the per-ky Gram through the TR axis (lanes over the basis
-//      index: coalesced rows of U, shuffle reductions), in place;
-//   3. warp r applies the adjoint DFT -> P_r(iy);
-//   4. threads over (iy, half of r) contract with the tangents, the two partial sums are
-//      added in order, and g (masked, times nx) and the block's part of <v, g> are
-//      written; the last block adds the parts.
-// 512 threads (two blocks per SM): warp w owns basis functions r = w and w + 16.
-// ---------------------------------------------------------------------------
-constexpr int kColThreads = 512, kColWarps = kColThreads / 32;
-
-
-
-template <int N1>
-__global__ void __launch_bounds__(kColThreads, 2)
-lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restrict__ v,
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kColThreads, 3)
+lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, float* __restrict__ v, const __grid_constant__ PUpdate pu,
                       const float* __restrict__ coefT, const float2* __restrict__ rho,
-                      const float* __restrict__ maskf, const float2* __restrict__ roots, const float* __restrict__ Ug,
-                      const int* __restrict__ kyptr, int nx, int ny, int nv, int R, float scale,
+                      const float* __restrict__ maskf, const float2* __restrict__ roots, const float* __restrict__ UgT,
+                      const int* __restrict__ kyptr, const int* __restrict__ kyof, int ntr, int nx, int ny, int nv,
+                      int R, float scale,
                       float* __restrict__ g, double* red_part, unsigned* ticket, double* __restrict__ vdot,
                       const int* __restrict__ gate) {
+  // the gate and the update flags are written by earlier launches only: both blocks of a
+  // cluster take the same branch, so every cluster barrier below is reached by both
   if (gate != nullptr && *gate == 0) return;
+  namespace cgp = cooperative_groups;
+  cgp::cluster_group cl = cgp::this_cluster();
+  const int crank = (int)cl.block_rank(), peer = crank ^ 1;
+  // with pu.r: first v <- r_sign r + beta v on this cluster's columns (the CG direction
+  // update; beta formed once per block, as the separate update kernel forms it)
+  __shared__ float s_beta;
+  __shared__ int s_upd;
+  if (threadIdx.x == 0) {
+    int u = pu.r != nullptr;
+    if (u && pu.off != nullptr) u = *pu.off == 0;
+    if (u && pu.on_a != nullptr) u = *pu.on_a != 0;
+    if (u && pu.on_b != nullptr) u = *pu.on_b != 0;
+    s_upd = u;
+    s_beta = u ? (float)(pu.beta_den != nullptr ? *pu.beta_num / *pu.beta_den : *pu.beta_num) : 0.f;
+  }
   const int ld = ny + 1;
+  const int RC = (R + 1) / 2, r0 = crank * RC, nr = min(R, r0 + RC) - r0;
   extern __shared__ float2 fsm[];
-  float2* rt = fsm;                                        // [ny] w^k
-  float2* hs = rt + ny;                                    // [R][ny + 1]
-  float* vox = reinterpret_cast<float*>(hs + R * ld);      // [6][ny]: v0, v1, m v2, m v3, Re rho, Im rho
-  float* red2 = vox + 6 * ny;                              // [2 halves of r][4][ny]
+  float2* rt = fsm;                                      // [ny] w^k
+  float2* hs = rt + ny;                                  // [RC][ny + 1]: H, then G, then P
+  float2* sbuf = hs + RC * ld;                           // [ntr] this block's part of s_t
+  float2* sfull = sbuf + ntr;                            // [ntr] s_t
+  float* vox = reinterpret_cast<float*>(sfull + ntr);    // [6][ny]: v0, v1, m v2, m v3, Re rho, Im rho
+  float* red4 = vox + 6 * ny;                            // [4][ny] contraction over this block's r
+  float* vox_peer = cl.map_shared_rank(vox, peer);
+  const float* red4_peer = cl.map_shared_rank(red4, peer);
+  const float2* sbuf_peer = cl.map_shared_rank(sbuf, peer);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int brev = (int)(__brev((unsigned)lane) >> 27);
   const size_t plane = (size_t)nx * ny;
+  const int hy = (ny + 1) / 2, ya = crank * hy, ye = min(ny, ya + hy);  // this block's half of iy
   for (int e = tid; e < ny; e += kColThreads) rt[e] = roots[e];
+  __syncthreads();
   float sf = 0.f;
-  for (int ix = blockIdx.x; ix < nx; ix += gridDim.x) {
-    for (int iy = tid; iy < ny; iy += kColThreads) {
+  for (int ix = blockIdx.x >> 1; ix < nx; ix += gridDim.x >> 1) {
+    // 0. voxel data of this block's half, into both blocks
+    for (int iy = ya + tid; iy < ye; iy += kColThreads) {
       const int j = iy * nx + ix;
       const float m = maskf[j];
       const float2 rh = rho[j];
-      vox[iy] = v[j];
-      vox[ny + iy] = v[nv + j];
-      vox[2 * ny + iy] = v[2 * (size_t)nv + j] * m;
-      vox[3 * ny + iy] = v[3 * (size_t)nv + j] * m;
-      vox[4 * ny + iy] = rh.x;
-      vox[5 * ny + iy] = rh.y;
+      float vk[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        vk[k] = v[(size_t)k * nv + j];
+        if (s_upd) {
+          vk[k] = fmaf(s_beta, vk[k], pu.r_sign * pu.r[(size_t)k * nv + j]);
+          v[(size_t)k * nv + j] = vk[k];
+        }
+      }
+      const float val[6] = {vk[0], vk[1], vk[2] * m, vk[3] * m, rh.x, rh.y};
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        vox[c * ny + iy] = val[c];
+        vox_peer[c * ny + iy] = val[c];
+      }
     }
-    __syncthreads();
-    // 1. h_r and its phase-encode DFT (warp w: r = w, w + 16)
-    for (int r = warp; r < R; r += kColWarps) {
-      const float* cr = coefT + (size_t)r * plane + (size_t)ix * ny;
+    cl.sync();
+    // 1. h_r and its phase-encode DFT (warp w: local r = w, w + 8)
+    for (int rl = warp; rl < nr; rl += kColWarps) {
+      const float* cr = coefT + (size_t)(r0 + rl) * plane + (size_t)ix * ny;
       float2 xin[N1];
 #pragma unroll
       for (int i1 = 0; i1 < N1; ++i1) {
@@ -768,45 +659,46 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
         }
         acc = cmul(acc, rt[k1 * lane]);  // k1 lane <= 31 (N1 - 1) < ny
         acc = fft32_warp<false>(acc, rt, N1, lane);
-        hs[r * ld + k1 + N1 * brev] = acc;
+        hs[rl * ld + k1 + N1 * brev] = acc;
       }
     }
     __syncthreads();
-    // 2. per-ky Gram through the TR axis: a warp per ky, lanes over the basis index, so
-    //    each row of U is one 128-byte load and sum_q is a shuffle reduction; the warp
-    //    reads H[.][ky] before it writes G[.][ky] (no other warp touches column ky)
-    for (int ky = warp; ky < ny; ky += kColWarps) {
-      const int ta = kyptr[ky], ns = kyptr[ky + 1] - ta;  // ns <= kGramShort
-      const float2 h = lane < R ? hs[lane * ld + ky] : make_float2(0.f, 0.f);
-      float u[kGramShort];
-      float2 sv[kGramShort];
-#pragma unroll
-      for (int k = 0; k < kGramShort; ++k) {
-        u[k] = 0.f;
-        sv[k] = make_float2(0.f, 0.f);
-        if (k < ns) {
-          u[k] = lane < R ? __ldg(Ug + (size_t)(ta + k) * R + lane) : 0.f;
-          float sr = u[k] * h.x, si = u[k] * h.y;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            sr += __shfl_xor_sync(0xffffffffu, sr, o);
-            si += __shfl_xor_sync(0xffffffffu, si, o);
-          }
-          sv[k] = make_float2(sr, si);
-        }
+    // 2. per-ky Gram through the TR axis (U transposed: coalesced over t)
+    for (int t = tid; t < ntr; t += kColThreads) {
+      const int ky = kyof[t];
+      float sr = 0.f, si = 0.f;
+#pragma unroll 8
+      for (int q = 0; q < nr; ++q) {
+        const float u = __ldg(UgT + (size_t)(r0 + q) * ntr + t);
+        const float2 h = hs[q * ld + ky];
+        sr = fmaf(u, h.x, sr);
+        si = fmaf(u, h.y, si);
       }
+      sbuf[t] = make_float2(sr, si);
+    }
+    cl.sync();
+    for (int t = tid; t < ntr; t += kColThreads) {
+      const float2 a = sbuf[t], b = sbuf_peer[t];
+      sfull[t] = make_float2(a.x + b.x, a.y + b.y);  // commutative: the same s_t in both blocks
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * ny; e += kColThreads) {
+      const int rl = e / ny, ky = e - rl * ny;
+      const int ta = __ldg(kyptr + ky), te = __ldg(kyptr + ky + 1);
+      const float* ur = UgT + (size_t)(r0 + rl) * ntr;
       float2 o = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k < kGramShort; ++k) {
-        o.x = fmaf(u[k], sv[k].x, o.x);
-        o.y = fmaf(u[k], sv[k].y, o.y);
+      for (int t = ta; t < te; ++t) {
+        const float u = __ldg(ur + t);
+        const float2 sv = sfull[t];
+        o.x = fmaf(u, sv.x, o.x);
+        o.y = fmaf(u, sv.y, o.y);
       }
-      if (lane < R) hs[lane * ld + ky] = o;
+      hs[rl * ld + ky] = o;
     }
     __syncthreads();
-    // 3. adjoint phase-encode DFT (warp w: r = w, w + 16)
-    for (int r = warp; r < R; r += kColWarps) {
-      float2* x = hs + r * ld;
+    // 3. adjoint phase-encode DFT
+    for (int rl = warp; rl < nr; rl += kColWarps) {
+      float2* x = hs + rl * ld;
       const int i2 = brev;
       float2 z[N1];
 #pragma unroll
@@ -830,42 +722,40 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
       }
     }
     __syncthreads();
-    // 4. contraction with the tangents: thread (half of r, iy)
-    {
-      const int iy = tid & 255, half = tid >> 8;
+    // 4. contraction with the tangents over this block's r, one thread per iy
+    for (int iy = tid; iy < ny; iy += kColThreads) {
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      if (iy < ny) {
-        const float rhx = vox[4 * ny + iy], rhy = vox[5 * ny + iy];
-        const int rq = (R + 1) / 2, ra = half * rq, re = min(R, ra + rq);
-        const float* cc = coefT + (size_t)ix * ny + iy;
-        for (int r = ra; r < re; ++r) {
-          const float2 pv = hs[r * ld + iy];
-          const float c = cc[(size_t)r * plane];
-          const float t1 = cc[(size_t)(R + r) * plane], t2 = cc[(size_t)(2 * R + r) * plane];
-          const float imcp = rhx * pv.y - rhy * pv.x;  // Im(conj(rho) P)
-          a0 = fmaf(t1, imcp, a0);
-          a1 = fmaf(t2, imcp, a1);
-          a2 = fmaf(c, pv.y, a2);
-          a3 = fmaf(-c, pv.x, a3);
-        }
-        red2[(half * 4 + 0) * ny + iy] = a0;
-        red2[(half * 4 + 1) * ny + iy] = a1;
-        red2[(half * 4 + 2) * ny + iy] = a2;
-        red2[(half * 4 + 3) * ny + iy] = a3;
+      const float rhx = vox[4 * ny + iy], rhy = vox[5 * ny + iy];
+      const float* cc = coefT + (size_t)ix * ny + iy;
+      for (int rl = 0; rl < nr; ++rl) {
+        const int r = r0 + rl;
+        const float2 pv = hs[rl * ld + iy];
+        const float c = cc[(size_t)r * plane];
+        const float t1 = cc[(size_t)(R + r) * plane], t2 = cc[(size_t)(2 * R + r) * plane];
+        const float imcp = rhx * pv.y - rhy * pv.x;  // Im(conj(rho) P)
+        a0 = fmaf(t1, imcp, a0);
+        a1 = fmaf(t2, imcp, a1);
+        a2 = fmaf(c, pv.y, a2);
+        a3 = fmaf(-c, pv.x, a3);
       }
-      __syncthreads();
-      if (tid < ny) {
-        const int j = tid * nx + ix;
-        const float m = maskf[j] * scale;
+      red4[iy] = a0;
+      red4[ny + iy] = a1;
+      red4[2 * ny + iy] = a2;
+      red4[3 * ny + iy] = a3;
+    }
+    cl.sync();
+    for (int iy = ya + tid; iy < ye; iy += kColThreads) {
+      const int j = iy * nx + ix;
+      const float m = maskf[j] * scale;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float val = (red2[k * ny + tid] + red2[(4 + k) * ny + tid]) * m;
-          g[(size_t)k * nv + j] = val;
-          if (vdot != nullptr) sf = fmaf(v[(size_t)k * nv + j], val, sf);
-        }
+      for (int k = 0; k < 4; ++k) {
+        const float val = (red4[k * ny + iy] + red4_peer[k * ny + iy]) * m;
+        g[(size_t)k * nv + j] = val;
+        if (vdot != nullptr) sf = fmaf(v[(size_t)k * nv + j], val, sf);  // written by this thread in 0.
       }
     }
-    __syncthreads();
+    // the peer reads this block's vox, sbuf and red4 until here
+    cl.sync();
   }
   if (vdot == nullptr) return;
   __shared__ double ws[kColWarps];
@@ -994,7 +884,7 @@ cudaError_t lowrank_project(const Plan& p, const LowRank& L, const float* alpha,
 
 void lowrank_free(LowRank* L) {
   if (L == nullptr) return;
-  void* ptrs[] = {L->U, L->Ug, L->Mky, L->kyptr, L->kytr, L->coef, L->coef2, L->gpart, L->coefT, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
+  void* ptrs[] = {L->U, L->Ug, L->UgT, L->kyof, L->Mky, L->kyptr, L->kytr, L->coef, L->coef2, L->gpart, L->coefT, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
                   L->a4_hi, L->a4_lo, L->by_hi, L->by_lo, L->bya_hi, L->bya_lo, L->X1, L->H, L->Y3, L->P};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -1046,10 +936,17 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
     std::vector<int> fill(ptr.begin(), ptr.end() - 1);
     for (int n = 0; n < ntr; ++n) trs[fill[kyi_h[n]]++] = n;
   }
-  // U gathered in ky order, and the largest number of TRs of any 32 consecutive ky values
-  std::vector<float> Ug((size_t)ntr * R);
+  // U gathered in ky order (and transposed), the ky of each gathered TR, and the largest
+  // number of TRs of any 32 consecutive ky values
+  std::vector<float> Ug((size_t)ntr * R), UgT((size_t)ntr * R);
+  std::vector<int> kyof(ntr);
   for (int t = 0; t < ntr; ++t)
-    for (int r = 0; r < R; ++r) Ug[(size_t)t * R + r] = Uh[(size_t)trs[t] * R + r];
+    for (int r = 0; r < R; ++r) {
+      Ug[(size_t)t * R + r] = Uh[(size_t)trs[t] * R + r];
+      UgT[(size_t)r * ntr + t] = Uh[(size_t)trs[t] * R + r];
+    }
+  for (int k = 0; k < ny; ++k)
+    for (int t = ptr[k]; t < ptr[k + 1]; ++t) kyof[t] = k;
   for (int k0 = 0; k0 < ny; k0 += 32) L->gram_rows_max = std::max(L->gram_rows_max, ptr[std::min(k0 + 32, ny)] - ptr[k0]);
   for (int k = 0; k < ny; ++k) L->ky_count_max = std::max(L->ky_count_max, ptr[k + 1] - ptr[k]);
   // the cancelled readout DFT pair needs nkx == nx; the Gram kernel keeps a ky tile's rows of U
@@ -1057,6 +954,9 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   L->full_readout = p->nkx == p->nx && (size_t)L->gram_rows_max * (R + 1) * sizeof(float) <= (size_t)L->smem_optin;
   // factorised phase-encode DFT: ny = 32 N1 with N1 <= 8
   L->fft_y = L->full_readout && ny % 32 == 0 && ny / 32 <= 8;
+  // one pair of blocks per image column: ceil(R / 2) x ny values and two copies of the ntr
+  // TR-axis sums in each block's shared memory
+  L->column_path = L->fft_y && column_smem_bytes(ny, R, ntr) <= (size_t)L->smem_optin;
   if (L->fft_y) {
     const int n1 = ny / 32;
     for (int a = 0; a < 8; ++a)
@@ -1104,6 +1004,8 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   const size_t rny = (size_t)R * ny, rnk = (size_t)R * nkx;
   chk(cudaMalloc(&L->U, (size_t)ntr * R * sizeof(float)));
   chk(cudaMalloc(&L->Ug, (size_t)ntr * R * sizeof(float)));
+  chk(cudaMalloc(&L->UgT, (size_t)ntr * R * sizeof(float)));
+  chk(cudaMalloc(&L->kyof, (size_t)ntr * sizeof(int)));
   chk(cudaMalloc(&L->Mky, M.size() * sizeof(float)));
   chk(cudaMalloc(&L->kyptr, ptr.size() * sizeof(int)));
   chk(cudaMalloc(&L->kytr, trs.size() * sizeof(int)));
@@ -1132,6 +1034,8 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   chk(cudaMemcpyAsync(L->U, U_dev, (size_t)ntr * R * sizeof(float), cudaMemcpyDeviceToDevice, st));
   chk(cudaMemcpy(L->Mky, M.data(), M.size() * sizeof(float), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->Ug, Ug.data(), Ug.size() * sizeof(float), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(L->UgT, UgT.data(), UgT.size() * sizeof(float), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(L->kyof, kyof.data(), kyof.size() * sizeof(int), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->kyptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->kytr, trs.data(), trs.size() * sizeof(int), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->by_hi, byh.data(), nby * 2, cudaMemcpyHostToDevice));
@@ -1325,43 +1229,6 @@ static int lowrank_jhjv_full_readout(Plan* p, const float* v, float* out, double
   return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank J^H J v");
 }
 
-template <int N1>
-static cudaError_t launch_fft_pair(Plan* p, const float* v, bool prep, double* vdot, float* out, cudaStream_t st) {
-  LowRank& L = *p->lr;
-  const int nx = p->nx, ny = p->ny, R = L.R;
-  // one block per image column (grid capped at the reduction scratch for the fused dot)
-  const int grid = std::min(nx, kRedBlocks);
-  if (prep) {
-    const size_t sm = sizeof(float2) * ((size_t)ny + (size_t)R * (ny + 1) + 8 * (size_t)ny);
-    cudaError_t e = cudaFuncSetAttribute(lr_prep_fft_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    lr_prep_fft_kernel<N1><<<grid, 256, sm, st>>>(v, L.coefT, p->rho, p->maskf, p->roots, nx, ny, p->nv, R,
-                                                  reinterpret_cast<float2*>(L.H), p->gate);
-  } else {
-    const size_t sm = sizeof(float2) * ((size_t)ny + (size_t)R * (ny + 1));
-    cudaError_t e =
-        cudaFuncSetAttribute(lr_final_fft_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    lr_final_fft_kernel<N1><<<grid, 256, sm, st>>>(reinterpret_cast<const float2*>(L.Y3), L.coefT, p->rho, p->maskf,
-                                                   p->roots, nx, ny, p->nv, R, (float)nx, out, v, p->red, p->ticket,
-                                                   vdot, p->gate);
-  }
-  return cudaGetLastError();
-}
-
-static cudaError_t launch_fft_stage(Plan* p, const float* v, bool prep, double* vdot, float* out, cudaStream_t st) {
-  switch (p->ny / 32) {
-    case 1: return launch_fft_pair<1>(p, v, prep, vdot, out, st);
-    case 2: return launch_fft_pair<2>(p, v, prep, vdot, out, st);
-    case 3: return launch_fft_pair<3>(p, v, prep, vdot, out, st);
-    case 4: return launch_fft_pair<4>(p, v, prep, vdot, out, st);
-    case 5: return launch_fft_pair<5>(p, v, prep, vdot, out, st);
-    case 6: return launch_fft_pair<6>(p, v, prep, vdot, out, st);
-    case 7: return launch_fft_pair<7>(p, v, prep, vdot, out, st);
-    default: return launch_fft_pair<8>(p, v, prep, vdot, out, st);
-  }
-}
-
 // The image-column copy of the coefficients, refreshed when they changed.
 static cudaError_t ensure_coef_columns(Plan* p, cudaStream_t st) {
   LowRank& L = *p->lr;
@@ -1374,67 +1241,56 @@ static cudaError_t ensure_coef_columns(Plan* p, cudaStream_t st) {
 }
 
 template <int N1>
-static cudaError_t launch_column_t(Plan* p, const float* v, double* vdot, float* out, cudaStream_t st) {
+static cudaError_t launch_column_t(Plan* p, float* v, const PUpdate& pu, double* vdot, float* out, cudaStream_t st) {
   LowRank& L = *p->lr;
   const int nx = p->nx, ny = p->ny, R = L.R;
-  const size_t sm = sizeof(float2) * ((size_t)ny + (size_t)R * (ny + 1)) + sizeof(float) * 14 * (size_t)ny;
+  const size_t sm = column_smem_bytes(ny, R, p->ntr);
   cudaError_t e =
       cudaFuncSetAttribute(lr_jhjv_column_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  const int grid = std::min(nx, kRedBlocks);
-  lr_jhjv_column_kernel<N1><<<grid, kColThreads, sm, st>>>(L.dft_small, v, L.coefT, p->rho, p->maskf, p->roots,
-                                                           L.Ug, L.kyptr, nx, ny, p->nv, R, (float)nx, out, p->red,
-                                                           p->ticket, vdot, p->gate);
+  // two blocks per column (cluster pairs), one float64 partial per block
+  const int grid = 2 * std::min(nx, kRedBlocks / 2);
+  lr_jhjv_column_kernel<N1><<<grid, kColThreads, sm, st>>>(L.dft_small, v, pu, L.coefT, p->rho, p->maskf, p->roots,
+                                                           L.UgT, L.kyptr, L.kyof, p->ntr, nx, ny, p->nv, R,
+                                                           (float)nx, out, p->red, p->ticket, vdot, p->gate);
   return cudaGetLastError();
 }
 
-static cudaError_t launch_column(Plan* p, const float* v, double* vdot, float* out, cudaStream_t st) {
+static cudaError_t launch_column(Plan* p, float* v, const PUpdate& pu, double* vdot, float* out, cudaStream_t st) {
   switch (p->ny / 32) {
-    case 1: return launch_column_t<1>(p, v, vdot, out, st);
-    case 2: return launch_column_t<2>(p, v, vdot, out, st);
-    case 3: return launch_column_t<3>(p, v, vdot, out, st);
-    case 4: return launch_column_t<4>(p, v, vdot, out, st);
-    case 5: return launch_column_t<5>(p, v, vdot, out, st);
-    case 6: return launch_column_t<6>(p, v, vdot, out, st);
-    case 7: return launch_column_t<7>(p, v, vdot, out, st);
-    default: return launch_column_t<8>(p, v, vdot, out, st);
+    case 1: return launch_column_t<1>(p, v, pu, vdot, out, st);
+    case 2: return launch_column_t<2>(p, v, pu, vdot, out, st);
+    case 3: return launch_column_t<3>(p, v, pu, vdot, out, st);
+    case 4: return launch_column_t<4>(p, v, pu, vdot, out, st);
+    case 5: return launch_column_t<5>(p, v, pu, vdot, out, st);
+    case 6: return launch_column_t<6>(p, v, pu, vdot, out, st);
+    case 7: return launch_column_t<7>(p, v, pu, vdot, out, st);
+    default: return launch_column_t<8>(p, v, pu, vdot, out, st);
   }
 }
 
-// J^H J v for a fully sampled readout and ny = 32 N1: prep with the factorised
-// phase-encode DFT -> Gram through the TR axis -> factorised adjoint DFT fused with the
-// contraction (and <v, J^H J v>), times nx for the cancelled readout DFT pair.
-static int lowrank_jhjv_fft(Plan* p, const float* v, float* out, double* vdot, cudaStream_t st) {
-  LowRank& L = *p->lr;
+// J^H J v for a fully sampled readout and ny = 32 N1: the column kernel (factorised
+// phase-encode DFT, Gram through the TR axis, adjoint, contraction and <v, J^H J v>), times
+// nx for the cancelled readout DFT pair.
+static int lowrank_jhjv_columns(Plan* p, const float* v, float* out, double* vdot, const PUpdate* pu,
+                                cudaStream_t st) {
   cudaError_t e;
   {
     Span sp(p, MRSTAT_K_VECTOR, st);
     e = ensure_coef_columns(p, st);
   }
-  if (e == cudaSuccess && L.ky_count_max <= kGramShort) {
-    // the whole product in one kernel, one block per image column
-    Span sp(p, MRSTAT_K_JHW_DOT, st);
-    e = launch_column(p, v, vdot, out, st);
-    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank J^H J v (column kernel)");
-  }
-  if (e == cudaSuccess) {
-    Span sp(p, MRSTAT_K_YCONTRACT, st);
-    e = launch_fft_stage(p, v, true, nullptr, nullptr, st);
-  }
-  if (e == cudaSuccess) {
-    Span sp(p, MRSTAT_K_VECTOR, st);
-    e = launch_gram<false>(*p, L, reinterpret_cast<float2*>(L.Y3), p->gate, st);
-  }
   if (e == cudaSuccess) {
     Span sp(p, MRSTAT_K_JHW_DOT, st);
-    e = launch_fft_stage(p, v, false, vdot, out, st);
+    // v is only written when pu asks for the direction update (then v is the caller's p)
+    e = launch_column(p, const_cast<float*>(v), pu ? *pu : PUpdate{}, vdot, out, st);
   }
-  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank J^H J v (factorised DFT)");
+  return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank J^H J v (column kernel)");
 }
 
-int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot) {
+int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot, const PUpdate* pu) {
   LowRank& L = *p->lr;
-  if (L.fft_y) return lowrank_jhjv_fft(p, v, out, vdot, st);
+  if (L.column_path) return lowrank_jhjv_columns(p, v, out, vdot, pu, st);
+  if (pu != nullptr) return fail(MRSTAT_ERR_UNSUPPORTED, "direction update fused only into the column kernel");
   if (L.full_readout) return lowrank_jhjv_full_readout(p, v, out, vdot, st);
   if (vdot != nullptr) {
     const int s = lowrank_jhjv(p, v, out, st, nullptr);

@@ -21,6 +21,8 @@ struct LowRank {
   int k1 = 0, k23 = 0, k4 = 0;     // padded K of the operands (2 nx, 2 ny, 2 nkx)
   float* U = nullptr;              // [ntr][R] time basis
   float* Ug = nullptr;             // [ntr][R] rows of U in ky order (the order of kytr)
+  float* UgT = nullptr;            // [R][ntr] the same, transposed
+  int* kyof = nullptr;             // [ntr] ky of each TR in that order
   int gram_rows_max = 0;           // most TRs of any 32 consecutive ky values
   int ky_count_max = 0;            // most TRs of any single ky value
   int smem_optin = 0;              // opt-in shared memory per block
@@ -30,7 +32,7 @@ struct LowRank {
   float* coef = nullptr;           // [3][R][nv]: c, dc/dlnT1, dc/dlnT2 (masked)
   float* coef2 = nullptr;          // [3][R][nv]: trial point of the surrogate Gauss-Newton phase
   float* gpart = nullptr;          // [ceil(R/8)][4][nv]: per-chunk partial sums of J^H J v
-  float* coefT = nullptr;          // [3 R][nx][ny]: coef in image-column order (factorised-DFT path)
+  float* coefT = nullptr;          // [3 R][nx][ny]: coef in image-column order (column kernel)
   const float* coefT_src = nullptr;  // the coef buffer coefT was made from
   bool coefT_dirty = true;         // coef changed in place since
   void *a1_hi = nullptr, *a1_lo = nullptr;    // [R ny][k1]   readout-DFT input rows
@@ -45,8 +47,9 @@ struct LowRank {
   TcOperand op_a1, op_a23, op_a4, op_by, op_bya;
   bool active = false;             // the plan's current linearisation is this low-rank one
   bool full_readout = false;       // nkx == nx: J^H J v skips the readout DFT pair
-  bool fft_y = false;              // ... and ny = 32 N1 (N1 <= 8): factorised phase-encode DFT
+  bool fft_y = false;              // ... and ny = 32 N1 (N1 <= 8): the factorised phase-encode DFT applies
   DftSmall dft_small;              // the N1-point DFT matrix of the factorised path
+  bool column_path = false;        // fft_y and the column kernel's shared memory fits
   int sms = 1;                     // SM count (grid of the Gram kernel)
 };
 

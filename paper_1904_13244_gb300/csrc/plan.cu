@@ -447,7 +447,7 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   // A has the padded TR rows too (zero, never written): J^H J v reads it as W~ over TR quads
   chk(dalloc(p, &p->A, (size_t)p->ntr_pad * p->nx));
   chk(dalloc(p, &p->wt, (size_t)p->ntr_pad * p->nx));
-  chk(dalloc(p, &p->red, kRedBlocks));
+  chk(dalloc(p, &p->red, 5 * (size_t)kRedBlocks));  // up to five partial vectors
   chk(dalloc(p, &p->ticket, 1));
   chk(dalloc(p, &p->cg_r, (size_t)p->npar * nv));
   chk(dalloc(p, &p->cg_p, (size_t)p->npar * nv));
@@ -701,19 +701,32 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
   }
   if (e == cudaSuccess) e = do_dot(plan, plan->cg_r, plan->cg_r, n, sc + 0, st);
   if (e != cudaSuccess) return cuda_fail(e, "CG init");
+  // the low-rank column kernel takes each direction update p <- r + beta p into its first
+  // pass (the update of iteration it - 1 runs at the start of the product of iteration it)
+  const bool fuse_p = lowrank_fuses_pupdate(plan);
   for (int it = 0; it < iters; ++it) {
     double* rr = sc + 4 * it;
     double* pq = rr + 1;
     double* rr_next = sc + 4 * (it + 1);
     // q = Re(J^H J) p and pq = <p, q>
-    int s = do_jhjv(plan, plan->cg_p, plan->cg_q, st, pq);
+    int s;
+    if (fuse_p && it > 0) {
+      PUpdate pu;
+      pu.r = plan->cg_r;
+      pu.beta_num = rr;
+      pu.beta_den = sc + 4 * (it - 1);
+      pu.off = plan->cg_frozen;
+      s = lowrank_jhjv(plan, plan->cg_p, plan->cg_q, st, pq, &pu);
+    } else {
+      s = do_jhjv(plan, plan->cg_p, plan->cg_q, st, pq);
+    }
     if (s != MRSTAT_OK) return s;
     {
       Span sp(plan, MRSTAT_K_VECTOR, st);
       e = launch_cg_update_xr(x, plan->cg_r, plan->cg_p, plan->cg_q, n, rr, pq, plan->cg_frozen, plan->red,
                               plan->ticket, rr_next, st);
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !fuse_p) {
       Span sp(plan, MRSTAT_K_VECTOR, st);
       e = launch_cg_update_p(plan->cg_p, plan->cg_r, n, rr, rr_next, plan->cg_frozen, st);
     }

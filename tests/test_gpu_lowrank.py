@@ -67,9 +67,8 @@ def test_time_basis_matches_numpy_svd(mr):
 
 
 # nkx == nx from the third case on: J^H J v takes the path without the readout DFT pair;
-# ny = 32 N1 (64, 96, 224, 256, 32) takes the factorised phase-encode DFT on top, in one
-# kernel per image column when no ky has more than 8 TRs (the last case has 10: three
-# kernels)
+# ny = 32 N1 (64, 96, 224, 256, 32) takes the factorised phase-encode DFT on top, the
+# whole product in one kernel per image column (the last case has 10 TRs per ky)
 @pytest.mark.parametrize("case", [(40, 24, 5, 6, 48, 16), (33, 17, 3, 3, 30, 8), (64, 64, 5, 0, 64, 32),
                                   (36, 20, 3, 2, 36, 24), (1, 12, 2, 1, 1, 8), (24, 96, 2, 3, 24, 16),
                                   (8, 224, 1, 0, 8, 8), (13, 256, 1, 1, 13, 24), (16, 32, 10, 0, 16, 8)])
@@ -101,6 +100,38 @@ def test_lowrank_products_match_projected_oracle(mr, case):
     ref_h = model.gauss_newton_product(lin, v)
     assert metrics.relerr(h, ref_h) < TOL
     assert metrics.relerr(h2, ref_h) < TOL
+
+
+@pytest.mark.parametrize("iters", [1, 4])
+def test_lowrank_cg_fixed_matches_oracle_cg(mr, iters):
+    """Fixed-count CG on the low-rank Re(J^H J) through the column kernel, which also takes
+    each direction update p <- r + beta p into its first pass from the second iteration
+    on.  Against textbook CG in float64 on the projected oracle model; the bar after
+    several iterations is 1e-4, as for the exact form."""
+    seq = synth.make_sequence(64, 64, 5, 7.8, 3.9, seed=5)
+    alpha = random_phantom(64, 64, 7)
+    train = training_set(400, 2)
+    U = f32(model.time_basis(seq, np.exp(train[0]), np.exp(train[1]), 16)[0])
+    lin = model.project_onto_basis(model.linearize(seq, alpha), U)
+    b = model.jhw(lin, synth.random_kspace(seq.ntr, seq.nkx, 40))
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = float(np.sum(r * r))
+    for _ in range(iters):
+        q = model.gauss_newton_product(lin, p)
+        a = rr / float(np.sum(p * q))
+        x = x + a * p
+        r = r - a * q
+        rr_new = float(np.sum(r * r))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    with mr.Plan(seq) as plan:
+        plan.lowrank_set_basis(cuda(U))
+        plan.lowrank_linearize(cuda(alpha))
+        xg = plan.cg_fixed(cuda(b), iters).cpu().numpy()
+        plan.check()
+    assert metrics.relerr(xg, x) < (1e-5 if iters == 1 else 1e-4)
 
 
 def test_lowrank_full_size_sampled_jhw(mr):

@@ -52,6 +52,54 @@ def test_cgls_recovers_rho_at_the_true_relaxation_times():
     assert metrics.nrmse(rho, ph.rho.ravel()) < 1e-8
 
 
+def test_ls_rho_recovers_rho_at_the_true_relaxation_times():
+    seq, ph = synth.config("quad16")
+    alpha = np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(), ph.rho.imag.ravel()])
+    lin = model.linearize(seq, alpha)
+    rho = solver.ls_rho(lin, model.signal(lin))
+    assert metrics.nrmse(rho, ph.rho.ravel()) < 1e-10
+
+
+def _initial_lin(seq):
+    a0 = np.zeros((4, seq.nv))
+    a0[0], a0[1] = np.log(1000.0), np.log(100.0)
+    return model.linearize(seq, a0)
+
+
+def test_ls_rho_solves_the_normal_equations_and_matches_converged_cgls():
+    """At the paper's initial guess (uniform T1 = 1000 ms, T2 = 100 ms) and arbitrary
+    data on a ragged grid (Ny = 12, extra TRs): the residual is orthogonal to the range
+    of M, checked through the oracle's adjoint (encode_adjoint, not the dense M), and
+    CGLS reaches the same rho.  With uniform relaxation times M^H M has one eigenvalue
+    per sampled ky, so CGLS converges in at most Ny steps; 20 steps, not many more
+    (past convergence the tiny residual only feeds rounding)."""
+    seq = synth.make_sequence(16, 12, 3, 7.8, 3.9, seed=1, extra_trs=5)
+    lin = _initial_lin(seq)
+    d = synth.random_kspace(seq.ntr, seq.nkx, 3)
+    rho = solver.ls_rho(lin, d)
+    v = np.zeros((4, seq.nv))
+    v[2], v[3] = rho.real, rho.imag
+    g = model.jhw(lin, d - model.jvp(lin, v))[2:4]
+    assert np.linalg.norm(g) < 1e-9 * np.linalg.norm(model.jhw(lin, d)[2:4])
+    assert metrics.relerr(solver.cgls_rho(lin, d, iters=20), rho) < 1e-8
+
+
+def test_ls_rho_is_minimum_norm_when_a_phase_encode_line_is_never_sampled():
+    """With ky = 2 dropped from the sequence that component of rho is unobservable; the
+    least-squares solution of minimum norm has none of it (E_2 rho = 0)."""
+    full = synth.make_sequence(8, 8, 2, 7.8, 3.9, seed=2)
+    keep = np.asarray(full.ky) != 2
+    seq = synth.Sequence(nx=8, ny=8, nkx=8, tr_ms=full.tr_ms, te_ms=full.te_ms,
+                         flip_rad=np.asarray(full.flip_rad)[keep], ky=np.asarray(full.ky)[keep],
+                         inversion=full.inversion, alternate_phase=full.alternate_phase)
+    lin = _initial_lin(seq)
+    d = synth.random_kspace(seq.ntr, seq.nkx, 4)
+    rho = solver.ls_rho(lin, d)
+    from oracle import encoding
+    assert np.linalg.norm(encoding.phase_matrix(seq, 2) @ rho) < 1e-9 * np.linalg.norm(rho)
+    assert np.linalg.norm(encoding.phase_matrix(seq, 1) @ rho) > 1e-3 * np.linalg.norm(rho)
+
+
 def test_gauss_newton_converges_quadratically_near_the_solution():
     seq, ph = synth.config("quad16")
     truth = np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(), ph.rho.imag.ravel()])
