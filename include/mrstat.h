@@ -366,7 +366,12 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
  * on the boundary.  With rho_init_iters > 0 the complex proton density is first
  * initialised as the least-squares solution of M(alpha_0) rho = d by CGLS at
  * T1 = t1_init_ms, T2 = t2_init_ms (Methods), and with mask_threshold > 0 the mask
- * |rho| > mask_threshold * max |rho| is drawn and written to `mask`.
+ * |rho| > mask_threshold * max |rho| is drawn and written to `mask`.  With
+ * rho_init_exact != 0 that least-squares solution is computed exactly instead (the
+ * minimum-norm one, which the paper's LSQR from zero approaches): every voxel shares the
+ * time course m_n at alpha_0, so M^H M is diagonal in k-space and rho = F^H P / (nx ny)
+ * with P(kx, ky) = sum_{n: ky(n) = ky} conj(m_n) d_n(kx) / sum |m_n|^2 (P = 0 on a ky no TR
+ * samples); this needs nkx == nx, b1 == NULL and ntr >= ny (else UNSUPPORTED).
  *
  * With opts->surrogate_iters = k > 0 the first k outer iterations replace the Bloch
  * simulation by the learned surrogate (mrstat_mlp_*), the remedy for the cost of the
@@ -395,8 +400,9 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
  *   mask:   device uint8 [nv]: in, the voxels to fit (NULL = all), unless a mask is
  *           drawn, in which case it is written (must then be non-NULL).
  *   report: host struct filled with the per-iteration history (may be NULL).
- * Errors: INVALID_ARG (bad pointers or options), OUT_OF_MEMORY (the solver's work
- * space: a second set of time courses plus a few vectors), CUDA.
+ * Errors: INVALID_ARG (bad pointers or options), UNSUPPORTED (see above),
+ * OUT_OF_MEMORY (the solver's work space: a second set of time courses plus a few
+ * vectors), CUDA.
  */
 #define MRSTAT_GN_MAX_OUTER 64
 
@@ -430,6 +436,9 @@ typedef struct mrstat_gn_opts {
   const mrstat_mlp* surrogate; /* required when surrogate_iters > 0; its rank must equal
                                   the plan's basis rank                                  */
   double b1_min, b1_max;       /* B1 box when B1 is estimated                           */
+  int32_t rho_init_exact;      /* != 0: the rho initialisation is the exact least-squares
+                                  solution instead of rho_init_iters CGLS steps (needs
+                                  nkx == nx, b1 == NULL and ntr >= ny)                   */
 } mrstat_gn_opts;
 
 typedef struct mrstat_gn_report {

@@ -57,7 +57,8 @@ class mrstat_gn_opts(ctypes.Structure):
                 ("rho_init_iters", ctypes.c_int32), ("t1_init_ms", ctypes.c_double),
                 ("t2_init_ms", ctypes.c_double), ("mask_threshold", ctypes.c_double),
                 ("hessian", ctypes.c_int32), ("surrogate_iters", ctypes.c_int32),
-                ("surrogate", ctypes.c_void_p), ("b1_min", ctypes.c_double), ("b1_max", ctypes.c_double)]
+                ("surrogate", ctypes.c_void_p), ("b1_min", ctypes.c_double), ("b1_max", ctypes.c_double),
+                ("rho_init_exact", ctypes.c_int32)]
 
 
 class mrstat_gn_report(ctypes.Structure):

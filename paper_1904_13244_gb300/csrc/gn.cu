@@ -379,6 +379,60 @@ xpby_kernel(float* __restrict__ p, const float* __restrict__ s, int64_t n, const
 
 __global__ void copy_scalar_kernel(double* dst, const double* src) { *dst = *src; }
 
+// The exact minimum-norm least-squares rho at a uniform linearisation (one time course
+// m_n shared by every voxel, as at alpha_0 of the Methods) with a fully sampled Cartesian
+// readout (nkx = nx): M = diag(m) (F_y x F_x) row by row, so M^H M = F^H W F with W(ky) =
+// sum over the TRs of ky of |m_n|^2, diagonal in k-space.  First the per-k-space solution
+//   P[ky][kx] = sum_{n: ky(n) = ky} conj(m_n) d[n][kx] / W(ky)   (0 where W(ky) = 0),
+// block per ky, thread per kx; m_n = i m_y,n is voxel 0's channel-0 time course.
+__global__ void rho_ls_kspace_kernel(const float* __restrict__ D, int nv, const float2* __restrict__ d, int nkx,
+                                     const int* __restrict__ ky_ptr, const int* __restrict__ ky_tr,
+                                     float2* __restrict__ P) {
+  const int ky = blockIdx.x;
+  const int ta = ky_ptr[ky], te = ky_ptr[ky + 1];
+  float w = 0.f;
+  for (int i = ta; i < te; ++i) {
+    const int n = ky_tr[i];
+    const float m = D[(size_t)(n >> 2) * nv * 4 + (n & 3)];
+    w = fmaf(m, m, w);
+  }
+  const float inv = w > 0.f ? 1.f / w : 0.f;
+  for (int kx = threadIdx.x; kx < nkx; kx += blockDim.x) {
+    float re = 0.f, im = 0.f;
+    for (int i = ta; i < te; ++i) {
+      const int n = ky_tr[i];
+      const float m = D[(size_t)(n >> 2) * nv * 4 + (n & 3)];
+      const float2 dv = d[(size_t)n * nkx + kx];
+      re = fmaf(m, dv.y, re);  // conj(i m) d = m Im d - i m Re d
+      im = fmaf(-m, dv.x, im);
+    }
+    P[(size_t)ky * nkx + kx] = make_float2(re * inv, im * inv);
+  }
+}
+
+// Then rho = F^H P / (nx ny): Q = P F_x^H (readout adjoint, a complex GEMM) and here the
+// phase-encode adjoint, rho[iy][ix] = sum_ky conj(w^(ky iy)) Q[ky][ix] / (nx ny), written
+// as the (Re, Im) rows x[0..nv) and x[nv..2 nv).
+__global__ void rho_ls_y_kernel(const float2* __restrict__ Q, const float2* __restrict__ roots, int nx, int ny,
+                                float scale, float* __restrict__ x) {
+  const int nv = nx * ny;
+  GRID_STRIDE(j, nv) {
+    const int iy = (int)(j / nx), ix = (int)(j - (int64_t)iy * nx);
+    float re = 0.f, im = 0.f;
+    int e = 0;  // (ky iy) mod ny
+    for (int ky = 0; ky < ny; ++ky) {
+      const float2 w = roots[e];
+      const float2 q = Q[(size_t)ky * nx + ix];
+      re = fmaf(w.x, q.x, fmaf(w.y, q.y, re));  // conj(w) q
+      im = fmaf(w.x, q.y, fmaf(-w.y, q.x, im));
+      e += iy;
+      if (e >= ny) e -= ny;
+    }
+    x[j] = re * scale;
+    x[nv + j] = im * scale;
+  }
+}
+
 __global__ void rho_max_kernel(const float* __restrict__ x, int nv, double* part, unsigned* ticket,
                                double* out) {
   // max |rho|^2 via the same deterministic two-level pattern (max instead of sum)
@@ -556,6 +610,29 @@ struct Solver {
     return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "step norm");
   }
 
+  // The exact least-squares rho at the current (uniform) linearisation, nkx = nx and
+  // ny <= ntr (the k-space work arrays hold ny rows); solution rows 2..3 of gn_z
+  int ls_rho(const float* d) {
+    const int nx = p->nx, ny = p->ny, nkx = p->nkx;
+    cudaError_t e = cudaMemsetAsync(p->gn_z, 0, (size_t)p->npar * p->nv * sizeof(float), st);
+    if (e == cudaSuccess)
+      e = vec([&] {
+        rho_ls_kspace_kernel<<<ny, 256, 0, st>>>(reinterpret_cast<const float*>(p->D), p->nv,
+                                                 reinterpret_cast<const float2*>(d), nkx, p->ky_ptr, p->ky_tr,
+                                                 p->gn_jv);
+      });
+    if (e == cudaSuccess) {
+      Span sp(p, MRSTAT_K_XDFT_ADJ, st);
+      e = launch_cgemm(p->gn_jv, p->fh, p->gn_r, ny, nx, nkx, nullptr, st);
+    }
+    if (e == cudaSuccess)
+      e = vec([&] {
+        rho_ls_y_kernel<<<grid_for(p->nv), kT, 0, st>>>(p->gn_r, p->roots, nx, ny, (float)(1.0 / ((double)nx * ny)),
+                                                        p->gn_z + 2 * (int64_t)p->nv);
+      });
+    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "exact rho initialisation");
+  }
+
   // CGLS for rho at the current linearisation (rho rows only); solution rows 2..3 of gn_z
   int cgls_rho(const float* d, int iters) {
     const int64_t n2 = 2 * (int64_t)p->nv;
@@ -642,10 +719,14 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
       o->rho_init_iters < 0 || !(o->t1_min_ms > 0) || !(o->t1_max_ms > o->t1_min_ms) ||
       !(o->t2_min_ms > 0) || !(o->t2_max_ms > o->t2_min_ms) || !std::isfinite(o->eta))
     return fail(MRSTAT_ERR_INVALID_ARG, "invalid Gauss-Newton options");
-  if (o->rho_init_iters > 0 && (!(o->t1_init_ms > 0) || !(o->t2_init_ms > 0)))
+  const bool rho_init = o->rho_init_iters > 0 || o->rho_init_exact != 0;
+  if (rho_init && (!(o->t1_init_ms > 0) || !(o->t2_init_ms > 0)))
     return fail(MRSTAT_ERR_INVALID_ARG, "invalid rho initialisation point");
-  if (o->rho_init_iters > 0 && o->mask_threshold > 0 && mask == nullptr)
+  if (rho_init && o->mask_threshold > 0 && mask == nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "drawing a mask needs a mask buffer");
+  if (o->rho_init_exact != 0 && (p->nkx != p->nx || b1 != nullptr || p->ny > p->ntr))
+    return fail(MRSTAT_ERR_UNSUPPORTED,
+                "the exact rho initialisation needs nkx == nx, no B1 map and at least ny TRs");
   if (o->hessian != 0 && o->hessian != 1) return fail(MRSTAT_ERR_INVALID_ARG, "hessian must be 0 or 1");
   if (p->npar == 5) {
     if (b1 != nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "B1 is estimated (alpha row 4): pass b1 = NULL");
@@ -687,14 +768,14 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   if (e != cudaSuccess) return cuda_fail(e, "Gauss-Newton setup");
 
   // -- rho initialisation and mask (Methods, "Reconstructions") --
-  if (o->rho_init_iters > 0) {
+  if (rho_init) {
     e = S.vec([&] {
       fill_rows_kernel<<<g, kT, 0, st>>>(p->gn_alpha, nv, p->npar, (float)std::log(o->t1_init_ms),
                                          (float)std::log(o->t2_init_ms));
     });
     if (e != cudaSuccess) return cuda_fail(e, "rho init fill");
     status = do_linearize(p, p->gn_alpha, b1, nullptr, p->D, p->rho, st);
-    if (status == MRSTAT_OK) status = S.cgls_rho(d, o->rho_init_iters);
+    if (status == MRSTAT_OK) status = o->rho_init_exact ? S.ls_rho(d) : S.cgls_rho(d, o->rho_init_iters);
     if (status != MRSTAT_OK) return status;
     const float* x = p->gn_z + 2 * (int64_t)nv;
     if (o->mask_threshold > 0) {

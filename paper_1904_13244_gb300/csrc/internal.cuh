@@ -36,6 +36,8 @@ struct Plan {
   float2* cs = nullptr;     // [ntr_pad] (cos phi_n, sin phi_n), phi_n the signed flip
   float* phi = nullptr;     // [ntr_pad] signed flip (radians)
   int* kyi = nullptr;       // [ntr_pad] ky mod ny in [0, ny)
+  int* ky_ptr = nullptr;    // [ny + 1] TRs of each ky (CSR over ky_tr)
+  int* ky_tr = nullptr;     // [ntr] TR indices grouped by ky, ascending within a ky
   float2* roots = nullptr;  // [ny] exp(-2 pi i k / ny)
   float2* ft = nullptr;     // [nx][nkx] exp(-2 pi i kx ix / nx)
   float2* fh = nullptr;     // [nkx][nx] exp(+2 pi i kx ix / nx)

@@ -39,7 +39,7 @@ namespace {
 
 void free_plan(Plan* p) {
   if (p == nullptr) return;
-  void* ptrs[] = {p->cs, p->phi, p->kyi, p->roots, p->ft, p->fh, p->D, p->rho, p->maskf,
+  void* ptrs[] = {p->cs, p->phi, p->kyi, p->ky_ptr, p->ky_tr, p->roots, p->ft, p->fh, p->D, p->rho, p->maskf,
                   p->dfwd, p->cf, p->A, p->wt, p->red, p->ticket, p->cg_r, p->cg_p, p->cg_q,
                   p->cg_jv, p->cg_s, p->cg_frozen, p->D2, p->rho2, p->gn_g, p->gn_z, p->gn_res,
                   p->gn_dir, p->gn_q, p->gn_alpha, p->gn_trial, p->gn_s, p->gn_r, p->gn_st,
@@ -421,6 +421,13 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
     phi[n] = (float)ph;
     cs[n] = make_float2((float)std::cos(ph), (float)std::sin(ph));
   }
+  std::vector<int> ky_ptr(p->ny + 1, 0), ky_tr(std::max(p->ntr, 1), 0);
+  for (int n = 0; n < p->ntr; ++n) ky_ptr[kyi[n] + 1]++;
+  for (int k = 0; k < p->ny; ++k) ky_ptr[k + 1] += ky_ptr[k];
+  {
+    std::vector<int> fill(ky_ptr.begin(), ky_ptr.end() - 1);
+    for (int n = 0; n < p->ntr; ++n) ky_tr[fill[kyi[n]]++] = n;
+  }
   std::vector<float2> roots(p->ny), ft((size_t)p->nx * p->nkx), fh((size_t)p->nkx * p->nx);
   for (int k = 0; k < p->ny; ++k) unit_root(k, p->ny, &roots[k], false);
   for (int ix = 0; ix < p->nx; ++ix)
@@ -439,6 +446,8 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(dalloc(p, &p->phi, p->ntr_pad));
   chk(dalloc(p, &p->kyi, p->ntr_pad));
   chk(dalloc(p, &p->roots, p->ny));
+  chk(dalloc(p, &p->ky_ptr, ky_ptr.size()));
+  chk(dalloc(p, &p->ky_tr, ky_tr.size()));
   chk(dalloc(p, &p->ft, ft.size()));
   chk(dalloc(p, &p->fh, fh.size()));
   chk(dalloc(p, &p->rho, nv));
@@ -464,6 +473,8 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(cudaMemcpy(p->phi, phi.data(), phi.size() * sizeof(float), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(p->kyi, kyi.data(), kyi.size() * sizeof(int), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(p->roots, roots.data(), roots.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(p->ky_ptr, ky_ptr.data(), ky_ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(p->ky_tr, ky_tr.data(), ky_tr.size() * sizeof(int), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(p->ft, ft.data(), ft.size() * sizeof(float2), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(p->fh, fh.data(), fh.size() * sizeof(float2), cudaMemcpyHostToDevice));
   chk(cudaMemset(p->wt, 0, (size_t)p->ntr_pad * p->nx * sizeof(float2)));

@@ -100,6 +100,108 @@ def test_rho_initialisation_and_mask_match_oracle(mr):
     assert np.allclose(a_gpu[0], np.log(1000.0)) and np.allclose(a_gpu[1], np.log(100.0))
 
 
+def _dropped_ky_sequence():
+    full = synth.make_sequence(8, 8, 2, 7.8, 3.9, seed=2)
+    keep = np.asarray(full.ky) != 2
+    return synth.Sequence(nx=8, ny=8, nkx=8, tr_ms=full.tr_ms, te_ms=full.te_ms,
+                          flip_rad=np.asarray(full.flip_rad)[keep], ky=np.asarray(full.ky)[keep],
+                          inversion=full.inversion, alternate_phase=full.alternate_phase)
+
+
+EXACT_RHO_CASES = {
+    "quad16": lambda: synth.config("quad16")[0],
+    "ragged_24x20": lambda: synth.make_sequence(24, 20, 2, 7.8, 3.9, seed=3, extra_trs=5),
+    "one_ky_never_sampled": _dropped_ky_sequence,
+    "ny_equals_ntr": lambda: synth.make_sequence(12, 12, 1, 7.8, 3.9, seed=4),
+}
+
+
+@pytest.mark.parametrize("name", list(EXACT_RHO_CASES))
+def test_exact_rho_initialisation_matches_oracle_lstsq(mr, name):
+    """rho_init_exact against the oracle's dense minimum-norm least squares at the paper's
+    alpha_0 (T1 = 1000 ms, T2 = 100 ms), arbitrary data, no mask drawn."""
+    seq = EXACT_RHO_CASES[name]()
+    a0 = np.zeros((4, seq.nv))
+    a0[0], a0[1] = np.log(1000.0), np.log(100.0)
+    d = synth.random_kspace(seq.ntr, seq.nkx, 5).astype(np.complex64).astype(np.complex128)
+    ref = solver.ls_rho(model.linearize(seq, a0), d)
+    with mr.Plan(seq) as plan:
+        a = cuda(np.zeros((4, seq.nv)))
+        rep = plan.gn_solve(cuda(d, torch.complex64), a, outer_iters=0, rho_init_exact=1, mask_threshold=0.0)
+        a_gpu = a.cpu().numpy().astype(np.float64)
+    assert rep["mask_voxels"] == seq.nv
+    assert metrics.relerr(a_gpu[2] + 1j * a_gpu[3], ref) < 1e-5
+    assert np.allclose(a_gpu[0], np.log(1000.0)) and np.allclose(a_gpu[1], np.log(100.0))
+
+
+def test_exact_rho_initialisation_and_mask_match_oracle(mr):
+    seq, ph = synth.config("ellipse64")
+    d = model.forward(seq, truth_of(ph)).astype(np.complex64).astype(np.complex128)
+    a0 = np.zeros((4, seq.nv))
+    a0[0], a0[1] = np.log(1000.0), np.log(100.0)
+    lin0 = model.linearize(seq, a0)
+    # the oracle's dense M is too large at 64 x 64: converged CGLS (one eigenvalue of M^H M
+    # per sampled ky, so Ny steps reach the solution) stands in for lstsq here
+    rho_ref = solver.cgls_rho(lin0, d, iters=seq.ny + 8)
+    mask_ref = solver.draw_mask(rho_ref, 0.1)
+    with mr.Plan(seq) as plan:
+        a = cuda(np.zeros((4, seq.nv)))
+        mask = torch.zeros(seq.nv, dtype=torch.uint8, device="cuda")
+        rep = plan.gn_solve(cuda(d, torch.complex64), a, mask=mask, outer_iters=0, rho_init_exact=1,
+                            mask_threshold=0.1)
+        a_gpu = a.cpu().numpy()
+        m_gpu = mask.cpu().numpy().astype(bool)
+    diff = m_gpu != mask_ref
+    thr = 0.1 * np.abs(rho_ref).max()
+    assert np.all(np.abs(np.abs(rho_ref[diff]) - thr) < 1e-4 * thr)
+    assert rep["mask_voxels"] == int(m_gpu.sum())
+    both = m_gpu & mask_ref
+    assert metrics.relerr((a_gpu[2] + 1j * a_gpu[3])[both], rho_ref[both]) < 1e-5
+
+
+def test_exact_rho_initialisation_rejects_what_it_does_not_cover(mr):
+    cases = [synth.make_sequence(16, 16, 2, 7.8, 3.9, seed=0, nkx=20),   # oversampled readout
+             synth.make_sequence(16, 16, 0, 7.8, 3.9, seed=0, extra_trs=9)]  # fewer TRs than ky lines
+    for seq in cases:
+        with mr.Plan(seq) as plan:
+            d = cuda(np.zeros((seq.ntr, seq.nkx)), torch.complex64)
+            with pytest.raises(mr.MrstatError) as e:
+                plan.gn_solve(d, cuda(np.zeros((4, seq.nv))), outer_iters=0, rho_init_exact=1, mask_threshold=0.0)
+            assert e.value.status == 7
+    seq = synth.make_sequence(16, 16, 2, 7.8, 3.9, seed=0)
+    with mr.Plan(seq) as plan:
+        d = cuda(np.zeros((seq.ntr, seq.nkx)), torch.complex64)
+        with pytest.raises(mr.MrstatError) as e:
+            plan.gn_solve(d, cuda(np.zeros((4, seq.nv))), b1=cuda(np.ones(seq.nv)), outer_iters=0,
+                          rho_init_exact=1, mask_threshold=0.0)
+        assert e.value.status == 7
+
+
+def test_exact_rho_initialisation_full_size_normal_equations(mr):
+    """224 x 224, 1120 TRs: the exact rho satisfies the normal equations of the rho block
+    (checked with the plan's own J^H, itself pinned to the oracle) and the 50-step CGLS
+    of the same problem lands close to it."""
+    seq, ph = synth.config("brain224")
+    truth = truth_of(ph)
+    a0 = np.zeros((4, seq.nv), np.float32)
+    a0[0], a0[1] = np.log(1000.0), np.log(100.0)
+    with mr.Plan(seq) as plan:
+        d = plan.forward(cuda(truth))
+        d = d + 0.01 * torch.linalg.vector_norm(d) / np.sqrt(d.numel()) * torch.randn_like(d)
+        a = cuda(np.zeros((4, seq.nv)))
+        plan.gn_solve(d, a, outer_iters=0, rho_init_exact=1, mask_threshold=0.0)
+        a_cg = cuda(np.zeros((4, seq.nv)))
+        plan.gn_solve(d, a_cg, outer_iters=0, rho_init_iters=50, mask_threshold=0.0)
+        plan.linearize(a)
+        r = d - plan.forward(a)
+        g = plan.jhw(r)[2:4]
+        g0 = plan.jhw(d)[2:4]
+        rel = float(torch.linalg.vector_norm(g) / torch.linalg.vector_norm(g0))
+        drift = float(torch.linalg.vector_norm(a_cg[2:4] - a[2:4]) / torch.linalg.vector_norm(a[2:4]))
+    assert rel < 1e-4
+    assert drift < 1e-2
+
+
 @pytest.mark.parametrize("seed", [0, 2])
 def test_noiseless_recovery_from_the_papers_initial_guess(mr, seed):
     seq = synth.make_sequence(16, 16, 24, 7.8, 3.9, seed=seed)
