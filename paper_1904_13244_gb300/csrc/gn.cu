@@ -25,7 +25,7 @@ enum {
   S_MVAL,        // CG model value m(z) - f
   S_COEF,        // step applied to z (alpha_j or tau)
   S_BETA,
-  S_DBD, S_RD, S_DD, S_ZD, S_ZZ,  // multidot outputs (contiguous)
+  S_DBD, S_RD, S_DD, S_ZD, S_ZZ,  // sums of the step decision (contiguous)
   S_ANORM2,      // ||alpha * mask||^2
   S_GAMMA, S_GAMMA_NEW, S_QQ,     // CGLS
   S_RHOMAX,      // max |rho| (as float bits in a double slot is not needed: stored as double)
@@ -159,6 +159,11 @@ st_init_kernel(const float* __restrict__ g, float* __restrict__ z, float* __rest
 
 __global__ void st_start_kernel(double* sc, int* si) {
   const double rr = sc[S_RR];
+  // the sums the first step decision needs besides dir.B dir: res = g, dir = -g, z = 0
+  sc[S_RD] = -rr;
+  sc[S_DD] = rr;
+  sc[S_ZD] = 0.0;
+  sc[S_ZZ] = 0.0;
   sc[S_GNORM] = sqrt(rr);
   sc[S_MVAL] = 0.0;
   sc[S_COEF] = 0.0;
@@ -203,39 +208,6 @@ __device__ void st_step(double* sc, int* si, double delta) {
   si[I_CONT] = 1;
 }
 
-// dir.q, res.dir, dir.dir, z.dir, z.z in one pass
-__global__ void __launch_bounds__(kT)
-multidot_kernel(const float* __restrict__ dir, const float* __restrict__ q, const float* __restrict__ res,
-                const float* __restrict__ z, int64_t n, double* sc, int* si, double delta, double* part,
-                unsigned* ticket) {
-  // every block reads I_ACTIVE before its ticket; the step decision below runs in the last
-  // block only, after all the others have taken theirs
-  if (si[I_ACTIVE] == 0) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {  // no step once CG has stopped
-      sc[S_COEF] = 0.0;
-      si[I_CONT] = 0;
-    }
-    return;
-  }
-  __shared__ double ws[5 * 8];
-  float a[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  GRID_STRIDE(i, n) {
-    const float d = dir[i], qq = q[i], r = res[i], zz = z[i];
-    a[0] = fmaf(d, qq, a[0]);
-    a[1] = fmaf(r, d, a[1]);
-    a[2] = fmaf(d, d, a[2]);
-    a[3] = fmaf(zz, d, a[3]);
-    a[4] = fmaf(zz, zz, a[4]);
-  }
-  double acc[5] = {(double)a[0], (double)a[1], (double)a[2], (double)a[3], (double)a[4]};
-  block_sum_n<5>(acc, ws);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) part[k * gridDim.x + blockIdx.x] = acc[k];
-  }
-  if (finish_n<5>(part, ticket, sc + S_DBD, ws) && threadIdx.x == 0) st_step(sc, si, delta);
-}
-
 // tolerance and iteration-count test after a continuing step; beta for the next direction
 __device__ void st_beta(double* sc, int* si, double rel_tol, int max_steps) {
   const double rr_new = sc[S_RR_NEW];
@@ -254,40 +226,135 @@ __device__ void st_beta(double* sc, int* si, double rel_tol, int max_steps) {
   }
 }
 
-// z += coef dir; while continuing also res += coef q and rr_new = res.res, then (last
-// block) the tolerance and iteration-count test
+__device__ __forceinline__ float4 ld4(const float* p, int64_t i) { return reinterpret_cast<const float4*>(p)[i]; }
+__device__ __forceinline__ void st4(float* p, int64_t i, float4 v) { reinterpret_cast<float4*>(p)[i] = v; }
+__device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y) {  // a x + y
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float dot4(float4 a, float4 b, float s) {
+  return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, s))));
+}
+
+// One Steihaug iteration after the product q = B dir (which also left dir.q in S_DBD):
+// the step decision from S_DBD..S_ZZ, then z += coef dir and, while continuing,
+// res += coef q and rr_new = res.res.  Every block takes the same decision from the same
+// sums (read before its ticket); the last block commits it, adds rr_new and takes the
+// tolerance and iteration-count test.  Vectors as float4 over [0, 4 n4), then element by
+// element; a block's first loads are issued before its thread 0 reads the scalars.
 __global__ void __launch_bounds__(kT)
 st_update_kernel(float* __restrict__ z, float* __restrict__ res, const float* __restrict__ dir,
-                 const float* __restrict__ q, int64_t n, double* sc, int* si, double rel_tol, int max_steps,
-                 double* part, unsigned* ticket) {
-  const double coef = sc[S_COEF];
-  const int cont = si[I_CONT];
-  if (coef == 0.0 && !cont) return;
-  __shared__ double ws[8];
-  const float c = (float)coef;
-  float a = 0.f;
-  GRID_STRIDE(i, n) {
+                 const float* __restrict__ q, int64_t n, int64_t n4, double* sc, int* si, double delta,
+                 double rel_tol, int max_steps, double* part, unsigned* ticket) {
+  const int64_t t0 = blockIdx.x * (int64_t)kT + threadIdx.x, stride = (int64_t)gridDim.x * kT;
+  float4 zv, rv, dv, qv;
+  if (t0 < n4) {
+    zv = ld4(z, t0);
+    rv = ld4(res, t0);
+    dv = ld4(dir, t0);
+    qv = ld4(q, t0);
+  }
+  __shared__ double lsc[S_COUNT];
+  __shared__ int lsi[I_COUNT];
+  __shared__ int s_go;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < S_COUNT; ++k) lsc[k] = sc[k];
+    for (int k = 0; k < I_COUNT; ++k) lsi[k] = si[k];
+    s_go = lsi[I_ACTIVE] != 0;  // CG stopped before this step: nothing to do, nothing to commit
+    if (s_go) st_step(lsc, lsi, delta);
+  }
+  __syncthreads();
+  if (!s_go) return;
+  const float c = (float)lsc[S_COEF];
+  const int cont = lsi[I_CONT];
+  float sf = 0.f;
+  for (int64_t i = t0; i < n4; i += stride) {
+    if (i != t0) {
+      zv = ld4(z, i);
+      rv = ld4(res, i);
+      dv = ld4(dir, i);
+      qv = ld4(q, i);
+    }
+    st4(z, i, axpy4(c, dv, zv));
+    if (cont) {
+      rv = axpy4(c, qv, rv);
+      st4(res, i, rv);
+      sf = dot4(rv, rv, sf);
+    }
+  }
+  for (int64_t i = 4 * n4 + t0; i < n; i += stride) {
     z[i] = fmaf(c, dir[i], z[i]);
     if (cont) {
       const float r = fmaf(c, q[i], res[i]);
       res[i] = r;
-      a = fmaf(r, r, a);
+      sf = fmaf(r, r, sf);
     }
   }
-  if (!cont) return;
-  double acc[1] = {(double)a};
+  __shared__ double ws[8];
+  double acc[1] = {(double)sf};
   block_sum_n<1>(acc, ws);
   if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
-  if (finish_n<1>(part, ticket, sc + S_RR_NEW, ws) && threadIdx.x == 0) st_beta(sc, si, rel_tol, max_steps);
+  if (finish_n<1>(part, ticket, sc + S_RR_NEW, ws) && threadIdx.x == 0) {
+    sc[S_MVAL] = lsc[S_MVAL];
+    sc[S_COEF] = lsc[S_COEF];
+    si[I_STEPS] = lsi[I_STEPS];
+    si[I_CONT] = lsi[I_CONT];
+    si[I_ACTIVE] = lsi[I_ACTIVE];
+    si[I_EXIT] = lsi[I_EXIT];
+    if (cont) st_beta(sc, si, rel_tol, max_steps);
+  }
 }
 
-// dir = -res + beta dir
+// dir = -res + beta dir while CG continues, and the sums of the next step decision:
+// res.dir, dir.dir, z.dir, z.z into S_RD..S_ZZ (dir.B dir comes with the next product)
 __global__ void __launch_bounds__(kT)
-st_dir_kernel(float* __restrict__ dir, const float* __restrict__ res, int64_t n,
-              const double* __restrict__ sc, const int* __restrict__ si) {
-  if (si[I_CONT] == 0 || si[I_ACTIVE] == 0) return;
-  const float beta = (float)sc[S_BETA];
-  GRID_STRIDE(i, n) dir[i] = fmaf(beta, dir[i], -res[i]);
+st_dir_kernel(float* __restrict__ dir, const float* __restrict__ res, const float* __restrict__ z, int64_t n,
+              int64_t n4, double* sc, const int* __restrict__ si, double* part, unsigned* ticket) {
+  const int64_t t0 = blockIdx.x * (int64_t)kT + threadIdx.x, stride = (int64_t)gridDim.x * kT;
+  float4 dv, rv, zv;
+  if (t0 < n4) {
+    dv = ld4(dir, t0);
+    rv = ld4(res, t0);
+    zv = ld4(z, t0);
+  }
+  __shared__ float s_beta;
+  __shared__ int s_go;
+  if (threadIdx.x == 0) {
+    s_go = si[I_CONT] != 0 && si[I_ACTIVE] != 0;
+    s_beta = (float)sc[S_BETA];
+  }
+  __syncthreads();
+  if (!s_go) return;
+  const float beta = s_beta;
+  float a[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int64_t i = t0; i < n4; i += stride) {
+    if (i != t0) {
+      dv = ld4(dir, i);
+      rv = ld4(res, i);
+      zv = ld4(z, i);
+    }
+    dv = axpy4(beta, dv, make_float4(-rv.x, -rv.y, -rv.z, -rv.w));
+    st4(dir, i, dv);
+    a[0] = dot4(rv, dv, a[0]);
+    a[1] = dot4(dv, dv, a[1]);
+    a[2] = dot4(zv, dv, a[2]);
+    a[3] = dot4(zv, zv, a[3]);
+  }
+  for (int64_t i = 4 * n4 + t0; i < n; i += stride) {
+    const float d = fmaf(beta, dir[i], -res[i]), r = res[i], zz = z[i];
+    dir[i] = d;
+    a[0] = fmaf(r, d, a[0]);
+    a[1] = fmaf(d, d, a[1]);
+    a[2] = fmaf(zz, d, a[2]);
+    a[3] = fmaf(zz, zz, a[3]);
+  }
+  __shared__ double ws[4 * 8];
+  double acc[4] = {(double)a[0], (double)a[1], (double)a[2], (double)a[3]};
+  block_sum_n<4>(acc, ws);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) part[k * gridDim.x + blockIdx.x] = acc[k];
+  }
+  finish_n<4>(part, ticket, sc + S_RD, ws);
 }
 
 __device__ __forceinline__ float reflect(float x, float lo, float hi) {
@@ -542,7 +609,7 @@ cudaError_t ensure_workspace(Plan* p) {
 struct Solver {
   Plan* p;
   cudaStream_t st;
-  int64_t n4;    // 4 nv
+  int64_t n4;    // npar nv (the GN vector length)
   int64_t nkf;   // k-space floats 2 ntr nkx
   double* sc;
   int* si;
@@ -574,34 +641,22 @@ struct Solver {
     if (e == cudaSuccess) e = vec([&] { st_start_kernel<<<1, 1, 0, st>>>(sc, si); });
     if (e != cudaSuccess) return cuda_fail(e, "Steihaug init");
     p->gate = si + I_ACTIVE;
+    // the GN vectors are whole allocations (16-byte aligned): float4 over all of them
+    const int64_t v4 = n4 / 4;
     int status = MRSTAT_OK;
-    // the low-rank column kernel takes each direction update dir <- -res + beta dir into its
-    // first pass (the update of iteration it - 1 at the start of the product of iteration it)
-    const bool fuse_dir = lowrank_fuses_pupdate(p);
     for (int it = 0; it < inner && status == MRSTAT_OK; ++it) {
-      if (fuse_dir && it > 0) {
-        PUpdate pu;
-        pu.r = p->gn_res;
-        pu.r_sign = -1.f;
-        pu.beta_num = sc + S_BETA;
-        pu.on_a = si + I_CONT;
-        pu.on_b = si + I_ACTIVE;
-        status = lowrank_jhjv(p, p->gn_dir, p->gn_q, st, nullptr, &pu);
-      } else {
-        status = do_jhjv(p, p->gn_dir, p->gn_q, st);
-      }
+      // q = B dir and dir.B dir (gated like the product once CG has stopped)
+      status = do_jhjv(p, p->gn_dir, p->gn_q, st, sc + S_DBD);
       if (status != MRSTAT_OK) break;
       e = vec([&] {
-        multidot_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_dir, p->gn_q, p->gn_res, p->gn_z, n4, sc, si, delta,
-                                                     p->red, p->ticket);
+        st_update_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_z, p->gn_res, p->gn_dir, p->gn_q, n4, v4, sc, si,
+                                                      delta, rel_tol, inner, p->red, p->ticket);
       });
       if (e == cudaSuccess)
         e = vec([&] {
-          st_update_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_z, p->gn_res, p->gn_dir, p->gn_q, n4, sc, si,
-                                                        rel_tol, inner, p->red, p->ticket);
+          st_dir_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_dir, p->gn_res, p->gn_z, n4, v4, sc, si, p->red,
+                                                     p->ticket);
         });
-      if (e == cudaSuccess && !fuse_dir)
-        e = vec([&] { st_dir_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_dir, p->gn_res, n4, sc, si); });
       if (e != cudaSuccess) status = cuda_fail(e, "Steihaug iteration");
     }
     p->gate = nullptr;

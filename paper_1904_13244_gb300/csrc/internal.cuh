@@ -186,23 +186,8 @@ cudaError_t lowrank_project(const Plan& p, const LowRank& L, const float* alpha,
                             const uint8_t* mask, float* coef, cudaStream_t st);
 int lowrank_jvp(Plan* p, const float* v, float2* jv, cudaStream_t st);
 int lowrank_jhw(Plan* p, const float2* w, float* g, cudaStream_t st);
-// A CG direction update v <- r_sign r + beta v, beta = *beta_num (/ *beta_den when given),
-// fused into the first pass of a product that can take it (PUpdate{} = none).  It applies
-// when *off == 0 and *on_a, *on_b != 0 (each test only where its pointer is set).
-struct PUpdate {
-  const float* r = nullptr;
-  float r_sign = 1.f;
-  const double* beta_num = nullptr;
-  const double* beta_den = nullptr;
-  const int* off = nullptr;
-  const int* on_a = nullptr;
-  const int* on_b = nullptr;
-};
-// Re(J^H J) v; with vdot also *vdot = <v, Re(J^H J) v> (fused where the path allows); with
-// pu, v is first replaced by the updated direction (only where lowrank_fuses_pupdate)
-int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot = nullptr,
-                 const PUpdate* pu = nullptr);
-inline bool lowrank_fuses_pupdate(const Plan* p) { return p->lr != nullptr && p->lr->active && p->lr->column_path; }
+// Re(J^H J) v; with vdot also *vdot = <v, Re(J^H J) v> (fused where the path allows)
+int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot = nullptr);
 cudaError_t lowrank_train_matrix(const float4* D, int ns, int nq, int ntr, float2* Y, float2* Yt,
                                  cudaStream_t st);
 cudaError_t ensure_forward_scratch(Plan* p);
@@ -234,7 +219,7 @@ cudaError_t launch_cgemm(const float2* A, const float2* B, float2* C, int M, int
                          const int* gate, cudaStream_t st);
 // reduce.cu
 cudaError_t launch_dot(const float* a, const float* b, int64_t n, double* partials, unsigned* ticket,
-                       double* out, cudaStream_t st);
+                       double* out, cudaStream_t st, const int* gate = nullptr);
 cudaError_t launch_cg_init(const float* rhs, float* x, float* r, float* p, int64_t n, cudaStream_t st);
 cudaError_t launch_cg_update_xr(float* x, float* r, const float* p, const float* q, int64_t n,
                                 const double* rr, const double* pq, int* frozen, double* partials,

@@ -501,24 +501,80 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
   return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
 }
 
-// in-warp 32-point DFT of v (lane = input index); the result at lane L is output bitrev(L).
-// CONJ: exp(+2 pi i / 32) roots (the adjoint).  rt[k] = w^k with w32 = w^N1.
+// In-warp 32-point DFT (lane = input index; the result at lane L is output bitrev(L)),
+// radix-2 decimation in frequency by shuffles, branch-free: at the stage of span h a lane
+// whose bit h is clear keeps v + p, the other p - v times w_(2h)^(pos - h) (pos = lane mod
+// 2h).  The per-lane stage factors are the same for every column a warp transforms, so
+// they are formed once: sign[s] = -1 / +1 and tw[s] for the spans h = 16, 8, 4, 2 (1 for
+// the lanes that keep the sum; span 1 needs none).  CONJ: conjugate roots (the adjoint).
+// rt[k] = w^k with w32 = w^N1.
+struct Fft32Lane {
+  float sg[5];
+  float2 tw[4];
+};
+
 template <bool CONJ>
-__device__ __forceinline__ float2 fft32_warp(float2 v, const float2* rt, int n1, int lane) {
+__device__ __forceinline__ Fft32Lane fft32_lane(const float2* rt, int n1, int lane) {
+  Fft32Lane f;
 #pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
-    const float px = __shfl_xor_sync(0xffffffffu, v.x, h);
-    const float py = __shfl_xor_sync(0xffffffffu, v.y, h);
+  for (int s = 0; s < 5; ++s) {
+    const int h = 16 >> s;
     const int pos = lane & (2 * h - 1);
-    if (pos < h) {
-      v = make_float2(v.x + px, v.y + py);
-    } else {
-      const float2 d = make_float2(px - v.x, py - v.y);
-      const float2 w = rt[(pos - h) * (16 / h) * n1];  // w_(2h)^(pos - h)
-      v = CONJ ? cmulc(d, w) : cmul(d, w);
+    f.sg[s] = pos < h ? 1.f : -1.f;
+    if (s < 4) {
+      float2 w = pos < h ? make_float2(1.f, 0.f) : rt[(pos - h) * (16 / h) * n1];  // w_(2h)^(pos - h)
+      if (CONJ) w.y = -w.y;
+      f.tw[s] = w;
     }
   }
+  return f;
+}
+
+__device__ __forceinline__ float2 fft32_warp(float2 v, const Fft32Lane& f) {
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int h = 16 >> s;
+    const float px = __shfl_xor_sync(0xffffffffu, v.x, h);
+    const float py = __shfl_xor_sync(0xffffffffu, v.y, h);
+    v = make_float2(fmaf(f.sg[s], v.x, px), fmaf(f.sg[s], v.y, py));
+    if (s < 4) v = cmul(v, f.tw[s]);
+  }
   return v;
+}
+
+// Dense N1-point DFT of x by the conjugate symmetry of its matrix (W[N1 - k][i] =
+// conj(W[k][i])): with A_k = sum_i Re W[k][i] x_i and B_k = sum_i Im W[k][i] x_i,
+// X_k = A_k + i B_k and X_(N1 - k) = A_k - i B_k; X_0 is the plain sum, and for even N1
+// X_(N1/2) is the alternating sum.  CONJ: the conjugate matrix (W is symmetric, so this
+// is also its adjoint).
+template <int N1, bool CONJ>
+__device__ __forceinline__ void dft_small(const DftSmall& W, const float2 (&x)[N1], float2 (&X)[N1]) {
+  float2 s0 = x[0];
+#pragma unroll
+  for (int i = 1; i < N1; ++i) s0 = make_float2(s0.x + x[i].x, s0.y + x[i].y);
+  X[0] = s0;
+#pragma unroll
+  for (int k = 1; 2 * k < N1; ++k) {
+    float ax = x[0].x, ay = x[0].y, bx = 0.f, by = 0.f;
+#pragma unroll
+    for (int i = 1; i < N1; ++i) {
+      const float2 w = W.w[k][i];
+      ax = fmaf(w.x, x[i].x, ax);
+      ay = fmaf(w.x, x[i].y, ay);
+      bx = fmaf(w.y, x[i].x, bx);
+      by = fmaf(w.y, x[i].y, by);
+    }
+    // A + i B = (ax - by, ay + bx); A - i B = (ax + by, ay - bx)
+    const float2 plus = make_float2(ax - by, ay + bx), minus = make_float2(ax + by, ay - bx);
+    X[k] = CONJ ? minus : plus;
+    X[N1 - k] = CONJ ? plus : minus;
+  }
+  if (N1 % 2 == 0) {
+    float2 a = x[0];
+#pragma unroll
+    for (int i = 1; i < N1; ++i) a = (i & 1) ? make_float2(a.x - x[i].x, a.y - x[i].y) : make_float2(a.x + x[i].x, a.y + x[i].y);
+    X[N1 / 2] = a;
+  }
 }
 
 // coefT[(k R + r)][ix][iy] = coef[(k R + r)][iy nx + ix]: the coefficients in image-column
@@ -545,8 +601,8 @@ __global__ void lr_coef_transpose_kernel(const float* __restrict__ coef, int nx,
 // The whole low-rank J^H J v for one image column ix in one cluster of two blocks
 // (ny = 32 N1); block c of the pair owns the basis functions r in [c RC, (c + 1) RC),
 // RC = ceil(R / 2), and the R columns h_r(iy) never leave shared memory.
-//   0. each block forms half of the column's voxel data (v, after the fused direction
-//      update when asked, and rho) and stores it into both blocks' shared memory;
+//   0. each block forms half of the column's voxel data (v and rho) and stores it into
+//      both blocks' shared memory;
 //   1. warp w forms h_r(iy) for iy = 32 i1 + lane in registers for its r and applies the
 //      factorised phase-encode DFT -> H_r(ky);
 //   2. the per-ky Gram through the TR axis: one thread per TR forms the block's part of
@@ -568,31 +624,19 @@ size_t column_smem_bytes(int ny, int R, int ntr) {
 
 template <int N1>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kColThreads, 3)
-lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, float* __restrict__ v, const __grid_constant__ PUpdate pu,
+lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restrict__ v,
                       const float* __restrict__ coefT, const float2* __restrict__ rho,
                       const float* __restrict__ maskf, const float2* __restrict__ roots, const float* __restrict__ UgT,
                       const int* __restrict__ kyptr, const int* __restrict__ kyof, int ntr, int nx, int ny, int nv,
                       int R, float scale,
                       float* __restrict__ g, double* red_part, unsigned* ticket, double* __restrict__ vdot,
                       const int* __restrict__ gate) {
-  // the gate and the update flags are written by earlier launches only: both blocks of a
-  // cluster take the same branch, so every cluster barrier below is reached by both
+  // the gate is written by earlier launches only: both blocks of a cluster take the same
+  // branch, so every cluster barrier below is reached by both
   if (gate != nullptr && *gate == 0) return;
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
   const int crank = (int)cl.block_rank(), peer = crank ^ 1;
-  // with pu.r: first v <- r_sign r + beta v on this cluster's columns (the CG direction
-  // update; beta formed once per block, as the separate update kernel forms it)
-  __shared__ float s_beta;
-  __shared__ int s_upd;
-  if (threadIdx.x == 0) {
-    int u = pu.r != nullptr;
-    if (u && pu.off != nullptr) u = *pu.off == 0;
-    if (u && pu.on_a != nullptr) u = *pu.on_a != 0;
-    if (u && pu.on_b != nullptr) u = *pu.on_b != 0;
-    s_upd = u;
-    s_beta = u ? (float)(pu.beta_den != nullptr ? *pu.beta_num / *pu.beta_den : *pu.beta_num) : 0.f;
-  }
   const int ld = ny + 1;
   const int RC = (R + 1) / 2, r0 = crank * RC, nr = min(R, r0 + RC) - r0;
   extern __shared__ float2 fsm[];
@@ -611,6 +655,7 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, float* __restrict__ v,
   const int hy = (ny + 1) / 2, ya = crank * hy, ye = min(ny, ya + hy);  // this block's half of iy
   for (int e = tid; e < ny; e += kColThreads) rt[e] = roots[e];
   __syncthreads();
+  const Fft32Lane ffw = fft32_lane<false>(rt, N1, lane), ffa = fft32_lane<true>(rt, N1, lane);
   float sf = 0.f;
   for (int ix = blockIdx.x >> 1; ix < nx; ix += gridDim.x >> 1) {
     // 0. voxel data of this block's half, into both blocks
@@ -620,13 +665,7 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, float* __restrict__ v,
       const float2 rh = rho[j];
       float vk[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        vk[k] = v[(size_t)k * nv + j];
-        if (s_upd) {
-          vk[k] = fmaf(s_beta, vk[k], pu.r_sign * pu.r[(size_t)k * nv + j]);
-          v[(size_t)k * nv + j] = vk[k];
-        }
-      }
+      for (int k = 0; k < 4; ++k) vk[k] = v[(size_t)k * nv + j];
       const float val[6] = {vk[0], vk[1], vk[2] * m, vk[3] * m, rh.x, rh.y};
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
@@ -648,17 +687,12 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, float* __restrict__ v,
         const float qi = vox[5 * ny + iy] * t + vox[3 * ny + iy] * c;
         xin[i1] = make_float2(-qi, qr);
       }
+      float2 X[N1];
+      dft_small<N1, false>(W, xin, X);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) {
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int i1 = 0; i1 < N1; ++i1) {
-          const float2 w = W.w[k1][i1];
-          acc = make_float2(fmaf(w.x, xin[i1].x, fmaf(-w.y, xin[i1].y, acc.x)),
-                            fmaf(w.x, xin[i1].y, fmaf(w.y, xin[i1].x, acc.y)));
-        }
-        acc = cmul(acc, rt[k1 * lane]);  // k1 lane <= 31 (N1 - 1) < ny
-        acc = fft32_warp<false>(acc, rt, N1, lane);
+        float2 acc = cmul(X[k1], rt[k1 * lane]);  // k1 lane <= 31 (N1 - 1) < ny
+        acc = fft32_warp(acc, ffw);
         hs[rl * ld + k1 + N1 * brev] = acc;
       }
     }
@@ -706,20 +740,13 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, float* __restrict__ v,
       __syncwarp();
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) {
-        const float2 t = fft32_warp<true>(z[k1], rt, N1, lane);  // at i2 = bitrev(lane)
+        const float2 t = fft32_warp(z[k1], ffa);  // at i2 = bitrev(lane)
         z[k1] = cmulc(t, rt[k1 * i2]);
       }
+      float2 out[N1];
+      dft_small<N1, true>(W, z, out);
 #pragma unroll
-      for (int i1 = 0; i1 < N1; ++i1) {
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          const float2 w = W.w[k1][i1];
-          acc = make_float2(fmaf(w.x, z[k1].x, fmaf(w.y, z[k1].y, acc.x)),
-                            fmaf(w.x, z[k1].y, fmaf(-w.y, z[k1].x, acc.y)));
-        }
-        x[32 * i1 + i2] = acc;
-      }
+      for (int i1 = 0; i1 < N1; ++i1) x[32 * i1 + i2] = out[i1];
     }
     __syncthreads();
     // 4. contraction with the tangents over this block's r, one thread per iy
@@ -751,7 +778,7 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, float* __restrict__ v,
       for (int k = 0; k < 4; ++k) {
         const float val = (red4[k * ny + iy] + red4_peer[k * ny + iy]) * m;
         g[(size_t)k * nv + j] = val;
-        if (vdot != nullptr) sf = fmaf(v[(size_t)k * nv + j], val, sf);  // written by this thread in 0.
+        if (vdot != nullptr) sf = fmaf(v[(size_t)k * nv + j], val, sf);
       }
     }
     // the peer reads this block's vox, sbuf and red4 until here
@@ -1241,7 +1268,7 @@ static cudaError_t ensure_coef_columns(Plan* p, cudaStream_t st) {
 }
 
 template <int N1>
-static cudaError_t launch_column_t(Plan* p, float* v, const PUpdate& pu, double* vdot, float* out, cudaStream_t st) {
+static cudaError_t launch_column_t(Plan* p, const float* v, double* vdot, float* out, cudaStream_t st) {
   LowRank& L = *p->lr;
   const int nx = p->nx, ny = p->ny, R = L.R;
   const size_t sm = column_smem_bytes(ny, R, p->ntr);
@@ -1250,30 +1277,29 @@ static cudaError_t launch_column_t(Plan* p, float* v, const PUpdate& pu, double*
   if (e != cudaSuccess) return e;
   // two blocks per column (cluster pairs), one float64 partial per block
   const int grid = 2 * std::min(nx, kRedBlocks / 2);
-  lr_jhjv_column_kernel<N1><<<grid, kColThreads, sm, st>>>(L.dft_small, v, pu, L.coefT, p->rho, p->maskf, p->roots,
+  lr_jhjv_column_kernel<N1><<<grid, kColThreads, sm, st>>>(L.dft_small, v, L.coefT, p->rho, p->maskf, p->roots,
                                                            L.UgT, L.kyptr, L.kyof, p->ntr, nx, ny, p->nv, R,
                                                            (float)nx, out, p->red, p->ticket, vdot, p->gate);
   return cudaGetLastError();
 }
 
-static cudaError_t launch_column(Plan* p, float* v, const PUpdate& pu, double* vdot, float* out, cudaStream_t st) {
+static cudaError_t launch_column(Plan* p, const float* v, double* vdot, float* out, cudaStream_t st) {
   switch (p->ny / 32) {
-    case 1: return launch_column_t<1>(p, v, pu, vdot, out, st);
-    case 2: return launch_column_t<2>(p, v, pu, vdot, out, st);
-    case 3: return launch_column_t<3>(p, v, pu, vdot, out, st);
-    case 4: return launch_column_t<4>(p, v, pu, vdot, out, st);
-    case 5: return launch_column_t<5>(p, v, pu, vdot, out, st);
-    case 6: return launch_column_t<6>(p, v, pu, vdot, out, st);
-    case 7: return launch_column_t<7>(p, v, pu, vdot, out, st);
-    default: return launch_column_t<8>(p, v, pu, vdot, out, st);
+    case 1: return launch_column_t<1>(p, v, vdot, out, st);
+    case 2: return launch_column_t<2>(p, v, vdot, out, st);
+    case 3: return launch_column_t<3>(p, v, vdot, out, st);
+    case 4: return launch_column_t<4>(p, v, vdot, out, st);
+    case 5: return launch_column_t<5>(p, v, vdot, out, st);
+    case 6: return launch_column_t<6>(p, v, vdot, out, st);
+    case 7: return launch_column_t<7>(p, v, vdot, out, st);
+    default: return launch_column_t<8>(p, v, vdot, out, st);
   }
 }
 
 // J^H J v for a fully sampled readout and ny = 32 N1: the column kernel (factorised
 // phase-encode DFT, Gram through the TR axis, adjoint, contraction and <v, J^H J v>), times
 // nx for the cancelled readout DFT pair.
-static int lowrank_jhjv_columns(Plan* p, const float* v, float* out, double* vdot, const PUpdate* pu,
-                                cudaStream_t st) {
+static int lowrank_jhjv_columns(Plan* p, const float* v, float* out, double* vdot, cudaStream_t st) {
   cudaError_t e;
   {
     Span sp(p, MRSTAT_K_VECTOR, st);
@@ -1281,16 +1307,14 @@ static int lowrank_jhjv_columns(Plan* p, const float* v, float* out, double* vdo
   }
   if (e == cudaSuccess) {
     Span sp(p, MRSTAT_K_JHW_DOT, st);
-    // v is only written when pu asks for the direction update (then v is the caller's p)
-    e = launch_column(p, const_cast<float*>(v), pu ? *pu : PUpdate{}, vdot, out, st);
+    e = launch_column(p, v, vdot, out, st);
   }
   return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank J^H J v (column kernel)");
 }
 
-int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot, const PUpdate* pu) {
+int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot) {
   LowRank& L = *p->lr;
-  if (L.column_path) return lowrank_jhjv_columns(p, v, out, vdot, pu, st);
-  if (pu != nullptr) return fail(MRSTAT_ERR_UNSUPPORTED, "direction update fused only into the column kernel");
+  if (L.column_path) return lowrank_jhjv_columns(p, v, out, vdot, st);
   if (L.full_readout) return lowrank_jhjv_full_readout(p, v, out, vdot, st);
   if (vdot != nullptr) {
     const int s = lowrank_jhjv(p, v, out, st, nullptr);

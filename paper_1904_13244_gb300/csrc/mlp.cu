@@ -200,126 +200,164 @@ __global__ void mlp_cast_kernel(const float* __restrict__ theta, int out, int in
 }
 
 // ---------------------------------------------------------------------------
-// Fused inference layer.  One CTA owns 128 samples and BN output features: per K chunk
-// TMA brings the three 128-row tiles of the layer input (value rows b, ln T1 tangent
-// rows B + b, ln T2 tangent rows 2B + b) and one weight tile; one thread issues three
-// tcgen05.mma per K step into three TMEM accumulators (columns 0, BN, 2 BN), so the
-// epilogue sees z, z1, z2 of the same (sample, feature) and applies the layer there:
-//   hidden: a = tanh(z + bias), s_k = (1 - a^2) z_k, written as the next layer's BF16
-//           input through shared memory (whole row pieces);
+// Fused inference layer.  Per K chunk TMA brings the three 128-row tiles of the layer
+// input (value rows b, ln T1 tangent rows B + b, ln T2 tangent rows 2B + b) and one weight
+// tile; one thread issues three tcgen05.mma per K step into three TMEM accumulators, so
+// the epilogue sees z, z1, z2 of the same (sample, feature) and applies the layer there:
+//   hidden: a = tanh(z + bias), s_k = (1 - a^2) z_k, written as the next layer's BF16 input;
 //   output: pred[k][r][b] = scale_r (z_k + [k = 0] bias_r), coalesced along the samples.
-// The pre-activations never reach global memory.  Eight warps share the epilogue: warp w
-// reads TMEM lanes 32 (w mod 4) .. +31 and column half w / 4.  The hidden-layer tanh is
-// the hardware tanh.approx.f32 (relative error about 2^-11, below the BF16 rounding of the
-// values it produces).  The grid's x dimension runs over the N tiles, so the CTAs that
-// read the same 128 input rows run together and the rows come from DRAM once.
-// ---------------------------------------------------------------------------
+// The pre-activations never reach global memory.  The hidden-layer tanh is the hardware
+// tanh.approx.f32 (relative error about 2^-11, below the BF16 rounding of the values it
+// produces).
+//
 __device__ __forceinline__ float tanh_fast(float x) {
   float y;
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
-constexpr int kFusedStages = 3;
-
-template <int BN>
-struct FusedShape {
-  static constexpr uint32_t kA = tc::BM * tc::BK * 2;         // one 128-row input tile
-  static constexpr uint32_t kB = BN * tc::BK * 2;             // one weight tile
+// Persistent kernel: one CTA per SM walks the (128-row tile, 64-column tile) pairs, n
+// fastest, so the CTAs working on one row tile at a time share its three input tiles
+// through L2.  Warp 0 issues the TMA loads (three input
+// tiles and the weight tile per 64-wide K chunk) into a ring of stages, warp 1 issues the
+// three MMAs per K step into one of two TMEM accumulator sets (3 x 64 columns each), and
+// warps 2..5 (one TMEM lane quarter each) run the epilogue of tile i while the MMAs of
+// tile i + 1 proceed: bias and tanh, the tangent scaling 1 - a^2, BF16, 32-byte stores
+// straight to the next layer's input rows (or, for the last layer, the scaled outputs).
+// Every wait is bounded; a CTA that gives up sets err and drains its copies in flight.
+// ---------------------------------------------------------------------------
+constexpr int kPerStages = 3;
+struct PerShape {
+  static constexpr int BN = 64;
+  static constexpr uint32_t kA = tc::BM * tc::BK * 2;  // one 128-row input tile
+  static constexpr uint32_t kB = BN * tc::BK * 2;      // one 64-row weight tile
   static constexpr uint32_t kStage = 3 * kA + kB;
-  static constexpr uint32_t kTmemCols = 3 * BN <= 128 ? 128 : (3 * BN <= 256 ? 256 : 512);
-  static constexpr int kLd = BN + 8;                          // staging row stride (bf16)
-  static constexpr size_t kSmem = (size_t)kFusedStages * kStage + 1024 + 256;
-  static_assert((size_t)kFusedStages * kStage >= (size_t)3 * 128 * kLd * 2, "staging fits the ring");
+  static constexpr uint32_t kTmemCols = 512;           // 2 sets x 3 streams x 64 columns
+  static constexpr size_t kSmem = (size_t)kPerStages * kStage + 1024 + 256;
 };
 
-template <int BN, bool LAST>
-__global__ void __launch_bounds__(256, 1)
-mlp_fused_layer_kernel(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tw, int B,
-                       int N, int K, const float* __restrict__ bias, __nv_bfloat16* __restrict__ xn, int ldn,
-                       const float* __restrict__ scale, float* __restrict__ pred, int* __restrict__ err) {
+template <bool LAST>
+__global__ void __launch_bounds__(192, 1)
+mlp_layer_persistent_kernel(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tw, int B,
+                            int N, int K, const float* __restrict__ bias, __nv_bfloat16* __restrict__ xn, int ldn,
+                            const float* __restrict__ scale, float* __restrict__ pred, int* __restrict__ err) {
   using namespace tc;
-  using FS = FusedShape<BN>;
+  using PS = PerShape;
+  constexpr int BN = PS::BN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kFusedStages * FS::kStage);
-  uint64_t* empty = full + kFusedStages;
-  uint64_t* done = empty + kFusedStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kPerStages * PS::kStage);
+  uint64_t* empty = full + kPerStages;
+  uint64_t* accf = empty + kPerStages;
+  uint64_t* acce = accf + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int n_tiles = (N + BN - 1) / BN;
+  const int tiles = ((B + BM - 1) / BM) * n_tiles;
   const int nk = (K + BK - 1) / BK;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kFusedStages; ++s) {
+    for (int s = 0; s < kPerStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accf[a], 1);
+      mbar_init(&acce[a], 4);  // one arrival per epilogue warp
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(tmem_slot, FS::kTmemCols);
+  if (warp == 0) tmem_alloc(tmem_slot, PS::kTmemCols);
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
   int issued = 0;
-  if (warp == 0 && lane == 0) {
-    for (int c = 0; c < nk; ++c) {
-      const int s = c % kFusedStages;
-      const uint32_t use = (uint32_t)(c / kFusedStages);
-      if (c >= kFusedStages && !mbar_wait(&empty[s], (use - 1) & 1u, abort_flag)) break;
-      uint8_t* st = smem + s * FS::kStage;
-      mbar_expect_tx(&full[s], FS::kStage);
-      tma_load_2d(&tx, &full[s], st, c * BK, b0);
-      tma_load_2d(&tx, &full[s], st + FS::kA, c * BK, B + b0);
-      tma_load_2d(&tx, &full[s], st + 2 * FS::kA, c * BK, 2 * B + b0);
-      tma_load_2d(&tw, &full[s], st + 3 * FS::kA, c * BK, n0);
-      issued = c + 1;
-    }
-  } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc = make_idesc(BM, BN);
-    for (int c = 0; c < nk; ++c) {
-      const int s = c % kFusedStages;
-      if (!mbar_wait(&full[s], (uint32_t)(c / kFusedStages) & 1u, abort_flag)) break;
-      fence_after();
-      const uint8_t* st = smem + s * FS::kStage;
-      const uint64_t d0 = sdesc_sw128(st), d1 = sdesc_sw128(st + FS::kA), d2 = sdesc_sw128(st + 2 * FS::kA);
-      const uint64_t dw = sdesc_sw128(st + 3 * FS::kA);
-#pragma unroll
-      for (int k = 0; k < BK / 16; ++k) {
-        const uint64_t off = 2ull * k;
-        const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
-        mma_bf16(tmem, d0 + off, dw + off, idesc, acc);
-        mma_bf16(tmem + BN, d1 + off, dw + off, idesc, acc);
-        mma_bf16(tmem + 2 * BN, d2 + off, dw + off, idesc, acc);
+  if (warp == 0) {
+    if (lane == 0) {
+      int g = 0;
+      bool go = true;
+      for (int t = blockIdx.x; t < tiles && go; t += gridDim.x) {
+        const int b0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+        for (int c = 0; c < nk; ++c, ++g) {
+          const int s = g % kPerStages;
+          const uint32_t use = (uint32_t)(g / kPerStages);
+          if (g >= kPerStages && !mbar_wait(&empty[s], (use - 1) & 1u, abort_flag)) {
+            go = false;
+            break;
+          }
+          uint8_t* st = smem + s * PS::kStage;
+          mbar_expect_tx(&full[s], PS::kStage);
+          tma_load_2d(&tx, &full[s], st, c * BK, b0);
+          tma_load_2d(&tx, &full[s], st + PS::kA, c * BK, B + b0);
+          tma_load_2d(&tx, &full[s], st + 2 * PS::kA, c * BK, 2 * B + b0);
+          tma_load_2d(&tw, &full[s], st + 3 * PS::kA, c * BK, n0);
+          issued = g + 1;
+        }
       }
-      mma_commit(&empty[s]);
     }
-    mma_commit(done);
-  }
-
-  __syncwarp();
-  const bool ok = mbar_wait(done, 0, abort_flag) && *abort_flag == 0;
-  __syncwarp();
-  fence_after();
-  if (ok) {
-    const int q = warp & 3, half = warp >> 2;  // TMEM lane quarter, column half
-    constexpr int HB = BN / 2;
-    const int m = q * 32 + lane;  // tile row = sample b0 + m
-    const int b = b0 + m;
-    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-    if (LAST) {
-      // N <= BN: features r = n0 + col < N
-      for (int cb = half * HB; cb < (half + 1) * HB && n0 + cb < N; cb += 16) {
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(BM, BN);
+      int g = 0, i = 0;
+      bool go = true;
+      for (int t = blockIdx.x; t < tiles && go; t += gridDim.x, ++i) {
+        const int acc = i & 1;
+        if (i >= 2 && !mbar_wait(&acce[acc], (uint32_t)((i >> 1) - 1) & 1u, abort_flag)) break;
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * 3 * BN);
+        for (int c = 0; c < nk; ++c, ++g) {
+          const int s = g % kPerStages;
+          if (!mbar_wait(&full[s], (uint32_t)(g / kPerStages) & 1u, abort_flag)) {
+            go = false;
+            break;
+          }
+          fence_after();
+          const uint8_t* st = smem + s * PS::kStage;
+          const uint64_t d0 = sdesc_sw128(st), d1 = sdesc_sw128(st + PS::kA), d2 = sdesc_sw128(st + 2 * PS::kA);
+          const uint64_t dw = sdesc_sw128(st + 3 * PS::kA);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t off = 2ull * k;
+            const uint32_t accum = (c > 0 || k > 0) ? 1u : 0u;
+            mma_bf16(d, d0 + off, dw + off, idesc, accum);
+            mma_bf16(d + BN, d1 + off, dw + off, idesc, accum);
+            mma_bf16(d + 2 * BN, d2 + off, dw + off, idesc, accum);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (go) mma_commit(&accf[acc]);
+      }
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quarter of this warp
+    int i = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+      const int acc = i & 1;
+      if (!mbar_wait(&accf[acc], (uint32_t)(i >> 1) & 1u, abort_flag)) break;
+      __syncwarp();
+      fence_after();
+      const int b0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+      const int b = b0 + q * 32 + lane;  // this lane's row (sample)
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 3 * BN);
+#pragma unroll 1
+      for (int cb = 0; cb < BN; cb += 16) {
+        __syncwarp();  // tcgen05.ld is warp-collective
         float v0[16], v1[16], v2[16];
         tmem_ld16(trow + (uint32_t)cb, v0);
         tmem_ld16(trow + (uint32_t)(BN + cb), v1);
         tmem_ld16(trow + (uint32_t)(2 * BN + cb), v2);
-        if (b < B) {
+        if (cb + 16 >= BN) {
+          // the whole accumulator set is in registers: hand it back to the MMA warp
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acce[acc]);
+        }
+        if (b >= B) continue;
+        if (LAST) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int r = n0 + cb + j;
@@ -330,60 +368,46 @@ mlp_fused_layer_kernel(const __grid_constant__ CUtensorMap tx, const __grid_cons
               pred[(size_t)(2 * N + r) * B + b] = sc * v2[j];
             }
           }
-        }
-      }
-    } else {
-      __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(smem);  // [3][128][kLd]
-#pragma unroll 1
-      for (int cb = half * HB; cb < (half + 1) * HB; cb += 16) {
-        float v0[16], v1[16], v2[16];
-        tmem_ld16(trow + (uint32_t)cb, v0);
-        tmem_ld16(trow + (uint32_t)(BN + cb), v1);
-        tmem_ld16(trow + (uint32_t)(2 * BN + cb), v2);
-        __align__(16) __nv_bfloat16 o0[16], o1[16], o2[16];
+        } else {
+          __align__(16) __nv_bfloat16 o[3][16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = n0 + cb + j;
-          const float a = tanh_fast(v0[j] + (n < N ? bias[n] : 0.f));
-          const float d = 1.f - a * a;
-          o0[j] = __float2bfloat16_rn(a);
-          o1[j] = __float2bfloat16_rn(d * v1[j]);
-          o2[j] = __float2bfloat16_rn(d * v2[j]);
-        }
-        uint4* r0 = reinterpret_cast<uint4*>(stage + (size_t)m * FS::kLd + cb);
-        uint4* r1 = reinterpret_cast<uint4*>(stage + (size_t)(128 + m) * FS::kLd + cb);
-        uint4* r2 = reinterpret_cast<uint4*>(stage + (size_t)(256 + m) * FS::kLd + cb);
-        r0[0] = reinterpret_cast<const uint4*>(o0)[0];
-        r0[1] = reinterpret_cast<const uint4*>(o0)[1];
-        r1[0] = reinterpret_cast<const uint4*>(o1)[0];
-        r1[1] = reinterpret_cast<const uint4*>(o1)[1];
-        r2[0] = reinterpret_cast<const uint4*>(o2)[0];
-        r2[1] = reinterpret_cast<const uint4*>(o2)[1];
-      }
-      __syncwarp();
-      // this warp's 32 rows and column half of each stream, two bf16 per lane per store
-      const int c_end = min((half + 1) * HB, N - n0);
-      for (int k = 0; k < 3; ++k) {
-        for (int r = 0; r < 32; ++r) {
-          const int mm = q * 32 + r, bb = b0 + mm;
-          if (bb >= B) break;
-          const uint32_t* srow = reinterpret_cast<const uint32_t*>(stage + (size_t)(k * 128 + mm) * FS::kLd);
-          uint32_t* drow = reinterpret_cast<uint32_t*>(xn + ((size_t)k * B + bb) * ldn + n0);
-          for (int c2 = half * HB / 2 + lane; 2 * c2 < c_end; c2 += 32) drow[c2] = srow[c2];
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + cb + j;
+            const float a = tanh_fast(v0[j] + (n < N ? bias[n] : 0.f));
+            const float dd = 1.f - a * a;
+            o[0][j] = __float2bfloat16_rn(a);
+            o[1][j] = __float2bfloat16_rn(dd * v1[j]);
+            o[2][j] = __float2bfloat16_rn(dd * v2[j]);
+          }
+          const int col = n0 + cb;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            __nv_bfloat16* dst = xn + ((size_t)k * B + b) * ldn + col;
+            if (col + 16 <= ldn) {  // 32 bytes (ldn and col are multiples of 8 elements)
+              reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(o[k])[0];
+              reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(o[k])[1];
+            } else {
+              for (int j = 0; col + j < ldn; ++j) dst[j] = o[k][j];
+            }
+          }
         }
       }
     }
-  } else if (threadIdx.x == 0) {
+  }
+
+  __syncwarp();
+  if (threadIdx.x == 0 && *abort_flag) {
     atomicExch(err, 1);
-    for (int c = issued > kFusedStages ? issued - kFusedStages : 0; c < issued; ++c) {
+    // let the copies this thread issued land before the CTA's shared memory goes away
+    for (int g = issued > kPerStages ? issued - kPerStages : 0; g < issued; ++g) {
       int spins = 0;
-      while (!mbar_try_wait(&full[c % kFusedStages], (uint32_t)(c / kFusedStages) & 1u) && ++spins < (1 << 16)) {
+      while (!mbar_try_wait(&full[g % kPerStages], (uint32_t)(g / kPerStages) & 1u) && ++spins < (1 << 16)) {
       }
     }
   }
   fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, FS::kTmemCols);
+  if (warp == 0) tmem_dealloc(tmem, PS::kTmemCols);
 }
 
 int blocks_for(int64_t n, int t = 256) {
@@ -457,6 +481,7 @@ int Mlp::setup(int h, int r, uint64_t seed) {
       chk(cudaMemset(Wb[l], 0, (size_t)out[l] * pad8(in[l]) * 2));
       chk(cudaMemset(WTb[l], 0, (size_t)in[l] * pad8(out[l]) * 2));
       chk(make_split_operand(&opW[l], Wb[l], Wb[l], out[l], in[l], pad8(in[l]), false));
+      chk(make_bf16_tmap(&wmap64[l], Wb[l], out[l], in[l], pad8(in[l]), PerShape::BN));
       chk(make_split_operand(&opWT[l], WTb[l], WTb[l], in[l], out[l], pad8(out[l]), false));
     }
   }
@@ -605,20 +630,26 @@ int Mlp::adam(float lr, cudaStream_t st) {
 }
 
 
-template <int BN, bool LAST>
-static cudaError_t launch_fused(const TcOperand& x, const TcOperand& w, int B, int N, int K, const float* bias,
-                                __nv_bfloat16* xn, int ldn, const float* scale, float* pred, int* err,
-                                cudaStream_t st) {
-  const size_t sm = FusedShape<BN>::kSmem;
-  cudaError_t e = cudaFuncSetAttribute(mlp_fused_layer_kernel<BN, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+template <bool LAST>
+static cudaError_t launch_persistent(const TcOperand& x, const CUtensorMap& w64, int B, int N, int K,
+                                     const float* bias, __nv_bfloat16* xn, int ldn, const float* scale, float* pred,
+                                     int* err, cudaStream_t st) {
+  const size_t sm = PerShape::kSmem;
+  cudaError_t e = cudaFuncSetAttribute(mlp_layer_persistent_kernel<LAST>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  const dim3 grid((N + BN - 1) / BN, (B + tc::BM - 1) / tc::BM);
-  mlp_fused_layer_kernel<BN, LAST><<<grid, 256, sm, st>>>(x.hi, w.hi, B, N, K, bias, xn, ldn, scale, pred, err);
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int tiles = ((B + tc::BM - 1) / tc::BM) * ((N + PerShape::BN - 1) / PerShape::BN);
+  const int grid = std::max(1, std::min(tiles, sms));
+  mlp_layer_persistent_kernel<LAST><<<grid, 192, sm, st>>>(x.hi, w64, B, N, K, bias, xn, ldn, scale, pred, err);
   return cudaGetLastError();
 }
 
-// Inference: the input kernel, then one fused kernel per layer (no pre-activation buffers).
+// Inference: the input kernel, then one persistent fused kernel per layer (no
+// pre-activation buffers).
 int Mlp::infer_fused(const float* lnT, const float* b1, int B, float* pred, cudaStream_t st) {
   mlp_input_kernel<<<blocks_for(B), 256, 0, st>>>(lnT, b1, B, norm[0], norm[1], norm[2], norm[3], norm[4], norm[5],
                                                   X[0], nullptr, 0);
@@ -628,15 +659,9 @@ int Mlp::infer_fused(const float* lnT, const float* b1, int B, float* pred, cuda
     const bool last = l == 3;
     __nv_bfloat16* xn = last ? nullptr : X[l + 1];
     const int ldn = last ? 0 : pad8(in[l + 1]);
-    if (opW[l].box == 128) {
-      e = last ? launch_fused<128, true>(opX[l], opW[l], B, out[l], in[l], bias, xn, ldn, scale_dev, pred, dev_err, st)
-               : launch_fused<128, false>(opX[l], opW[l], B, out[l], in[l], bias, xn, ldn, scale_dev, pred, dev_err,
-                                          st);
-    } else {
-      e = last ? launch_fused<64, true>(opX[l], opW[l], B, out[l], in[l], bias, xn, ldn, scale_dev, pred, dev_err, st)
-               : launch_fused<64, false>(opX[l], opW[l], B, out[l], in[l], bias, xn, ldn, scale_dev, pred, dev_err,
-                                         st);
-    }
+    e = last ? launch_persistent<true>(opX[l], wmap64[l], B, out[l], in[l], bias, xn, ldn, scale_dev, pred, dev_err, st)
+             : launch_persistent<false>(opX[l], wmap64[l], B, out[l], in[l], bias, xn, ldn, scale_dev, pred, dev_err,
+                                        st);
   }
   return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "surrogate inference");
 }

@@ -24,6 +24,7 @@ struct Mlp {
   __nv_bfloat16* Wb[4] = {nullptr, nullptr, nullptr, nullptr};   // bf16 [out][pad8(in)]
   __nv_bfloat16* WTb[4] = {nullptr, nullptr, nullptr, nullptr};  // bf16 [in][pad8(out)]
   TcOperand opW[4], opWT[4];
+  CUtensorMap wmap64[4];  // the weights with 64-row boxes (the persistent inference layers)
   // batch buffers (M = 3 B rows: values, ln T1 tangents, ln T2 tangents)
   int cap = 0, maps_b = -1;
   bool maps_train = false, have_train_buffers = false;

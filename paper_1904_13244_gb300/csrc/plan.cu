@@ -286,7 +286,7 @@ int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot) 
 
 cudaError_t do_dot(Plan* p, const float* a, const float* b, int64_t n, double* out, cudaStream_t st) {
   Span sp(p, MRSTAT_K_VECTOR, st);
-  return launch_dot(a, b, n, p->red, p->ticket, out, st);
+  return launch_dot(a, b, n, p->red, p->ticket, out, st, p->gate);
 }
 
 }  // namespace mrstat
@@ -712,32 +712,19 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
   }
   if (e == cudaSuccess) e = do_dot(plan, plan->cg_r, plan->cg_r, n, sc + 0, st);
   if (e != cudaSuccess) return cuda_fail(e, "CG init");
-  // the low-rank column kernel takes each direction update p <- r + beta p into its first
-  // pass (the update of iteration it - 1 runs at the start of the product of iteration it)
-  const bool fuse_p = lowrank_fuses_pupdate(plan);
   for (int it = 0; it < iters; ++it) {
     double* rr = sc + 4 * it;
     double* pq = rr + 1;
     double* rr_next = sc + 4 * (it + 1);
     // q = Re(J^H J) p and pq = <p, q>
-    int s;
-    if (fuse_p && it > 0) {
-      PUpdate pu;
-      pu.r = plan->cg_r;
-      pu.beta_num = rr;
-      pu.beta_den = sc + 4 * (it - 1);
-      pu.off = plan->cg_frozen;
-      s = lowrank_jhjv(plan, plan->cg_p, plan->cg_q, st, pq, &pu);
-    } else {
-      s = do_jhjv(plan, plan->cg_p, plan->cg_q, st, pq);
-    }
+    const int s = do_jhjv(plan, plan->cg_p, plan->cg_q, st, pq);
     if (s != MRSTAT_OK) return s;
     {
       Span sp(plan, MRSTAT_K_VECTOR, st);
       e = launch_cg_update_xr(x, plan->cg_r, plan->cg_p, plan->cg_q, n, rr, pq, plan->cg_frozen, plan->red,
                               plan->ticket, rr_next, st);
     }
-    if (e == cudaSuccess && !fuse_p) {
+    if (e == cudaSuccess) {
       Span sp(plan, MRSTAT_K_VECTOR, st);
       e = launch_cg_update_p(plan->cg_p, plan->cg_r, n, rr, rr_next, plan->cg_frozen, st);
     }
