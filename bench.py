@@ -580,8 +580,9 @@ def main():
 
     launches = int(sum(stats[k]["launches"] for k in stats))
     if args.form == "surrogate":
-        # MLP inference per step: input, 4 GEMMs, 3 activations, output (outside the plan's counters)
-        launches += 9 * args.steps
+        # MLP inference per step: the input kernel and four fused layer kernels (outside the
+        # plan's counters)
+        launches += 5 * args.steps
     if rank == 0:
         dft = ("factorised FP32 phase-encode DFT" if fft_y else "split-BF16 tcgen05 DFTs")
         form_desc = {"surrogate": f"learned surrogate + low-rank form (rank {R} time basis, MLP {args.hidden}x3 "

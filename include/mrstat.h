@@ -342,10 +342,12 @@ int mrstat_dot_static(const float* a, const float* b, int64_t n, double* out, vo
 /*
  * Fixed-count conjugate gradients on Re(J_s^H J_s) x = rhs at the cached
  * linearisation (the inner CG of Algorithm 6 without trust-region exits): x_0 = 0,
- * then exactly `iters` iterations, each one J^H J v product (mrstat_jvp followed by
- * mrstat_jhw) plus float64 inner products; every scalar stays on the device.  An
- * iteration whose curvature p.Hp is not positive, or whose residual is exactly
- * zero, freezes x for the remaining iterations.
+ * then exactly `iters` iterations, each one J^H J v product plus float64 inner products;
+ * every scalar stays on the device.  The iteration is written in the Chronopoulos-Gear
+ * form (the product is applied to the residual r, and <r, Hr>, <r, r> come with it;
+ * p.Hp follows from them), which has textbook CG's iterates in exact arithmetic and one
+ * vector update per iteration.  An iteration whose curvature p.Hp is not positive, or
+ * whose residual is exactly zero, freezes x for the remaining iterations.
  *   rhs, x: device float [npar][nv].  iters >= 0.
  * Errors: INVALID_ARG, NOT_LINEARIZED, CUDA.
  */

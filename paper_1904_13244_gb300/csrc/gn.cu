@@ -682,8 +682,10 @@ struct Solver {
     }
     if (e == cudaSuccess)
       e = vec([&] {
-        rho_ls_y_kernel<<<grid_for(p->nv), kT, 0, st>>>(p->gn_r, p->roots, nx, ny, (float)(1.0 / ((double)nx * ny)),
-                                                        p->gn_z + 2 * (int64_t)p->nv);
+        // one voxel per thread: each runs a whole ny-term sum
+        rho_ls_y_kernel<<<(int)((p->nv + kT - 1) / kT), kT, 0, st>>>(p->gn_r, p->roots, nx, ny,
+                                                                     (float)(1.0 / ((double)nx * ny)),
+                                                                     p->gn_z + 2 * (int64_t)p->nv);
       });
     return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "exact rho initialisation");
   }

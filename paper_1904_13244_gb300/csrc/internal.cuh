@@ -58,6 +58,7 @@ struct Plan {
   float* cg_r = nullptr;    // [npar][nv]
   float* cg_p = nullptr;    // [npar][nv]
   float* cg_q = nullptr;    // [npar][nv]
+  float* cg_w = nullptr;    // [npar][nv] Re(J^H J) r
   float2* cg_jv = nullptr;  // [ntr][nkx]
   double* cg_s = nullptr;   // CG scalars, 4 per iteration
   int* cg_frozen = nullptr; // CG stop flag
@@ -169,10 +170,10 @@ int do_signal(Plan* p, const float4* D, const float2* rho_masked, float2* s, cud
 int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* mask, float4* D,
                  float2* rho, cudaStream_t st);
 cudaError_t do_dot(Plan* p, const float* a, const float* b, int64_t n, double* out, cudaStream_t st);
-// Re(J^H J) v with the plan's active linearisation (exact: J.v then J^H; low-rank: per-ky Gram)
-// Re(J^H J) v; with vdot also *vdot = <v, Re(J^H J) v> (fused into the last pass where the
-// path allows it, else one more inner-product launch)
-int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot = nullptr);
+// Re(J^H J) v with the plan's active linearisation (exact: J.v then J^H; low-rank: per-ky
+// Gram); with vdot also *vdot = <v, Re(J^H J) v> and with vv also *vv = <v, v> (fused into
+// the last pass where the path allows it, else one more inner-product launch each)
+int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot = nullptr, double* vv = nullptr);
 // readout DFT of rows A [ntr][nx] (complex) into out [ntr][nkx], and its adjoint
 int do_xdft(Plan* p, const float2* A, float2* out, const int* gate, cudaStream_t st);
 int do_xdft_adj(Plan* p, const float2* w, float2* out, const int* gate, cudaStream_t st);
@@ -186,8 +187,10 @@ cudaError_t lowrank_project(const Plan& p, const LowRank& L, const float* alpha,
                             const uint8_t* mask, float* coef, cudaStream_t st);
 int lowrank_jvp(Plan* p, const float* v, float2* jv, cudaStream_t st);
 int lowrank_jhw(Plan* p, const float2* w, float* g, cudaStream_t st);
-// Re(J^H J) v; with vdot also *vdot = <v, Re(J^H J) v> (fused where the path allows)
-int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot = nullptr);
+// Re(J^H J) v; with vdot also *vdot = <v, Re(J^H J) v>, with vv also *vv = <v, v> (fused
+// where the path allows)
+int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot = nullptr,
+                 double* vv = nullptr);
 cudaError_t lowrank_train_matrix(const float4* D, int ns, int nq, int ntr, float2* Y, float2* Yt,
                                  cudaStream_t st);
 cudaError_t ensure_forward_scratch(Plan* p);
@@ -220,11 +223,10 @@ cudaError_t launch_cgemm(const float2* A, const float2* B, float2* C, int M, int
 // reduce.cu
 cudaError_t launch_dot(const float* a, const float* b, int64_t n, double* partials, unsigned* ticket,
                        double* out, cudaStream_t st, const int* gate = nullptr);
-cudaError_t launch_cg_init(const float* rhs, float* x, float* r, float* p, int64_t n, cudaStream_t st);
-cudaError_t launch_cg_update_xr(float* x, float* r, const float* p, const float* q, int64_t n,
-                                const double* rr, const double* pq, int* frozen, double* partials,
-                                unsigned* ticket, double* rr_new, cudaStream_t st);
-cudaError_t launch_cg_update_p(float* p, const float* r, int64_t n, const double* rr_old,
-                               const double* rr_new, const int* frozen, cudaStream_t st);
+cudaError_t launch_cg_init(const float* rhs, float* x, float* r, float* p, float* q, int64_t n, cudaStream_t st);
+// one Chronopoulos-Gear CG step (see reduce.cu); sk = {delta_k, gamma_k, alpha_k, -} of
+// this iteration, sp the previous iteration's (NULL in the first)
+cudaError_t launch_cg_cg_step(float* x, float* r, float* p, float* q, const float* w, int64_t n, double* sk,
+                              const double* sp, int* frozen, cudaStream_t st);
 
 }  // namespace mrstat

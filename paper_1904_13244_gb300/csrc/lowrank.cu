@@ -601,17 +601,18 @@ __global__ void lr_coef_transpose_kernel(const float* __restrict__ coef, int nx,
 // The whole low-rank J^H J v for one image column ix in one cluster of two blocks
 // (ny = 32 N1); block c of the pair owns the basis functions r in [c RC, (c + 1) RC),
 // RC = ceil(R / 2), and the R columns h_r(iy) never leave shared memory.
-//   0. each block forms half of the column's voxel data (v and rho) and stores it into
-//      both blocks' shared memory;
+//   0. each block loads the column's voxel data (v and rho);
 //   1. warp w forms h_r(iy) for iy = 32 i1 + lane in registers for its r and applies the
 //      factorised phase-encode DFT -> H_r(ky);
 //   2. the per-ky Gram through the TR axis: one thread per TR forms the block's part of
-//      s_t = sum_q U[t][q] H_q(ky(t)), the two parts are added (the same sum in both
-//      blocks), then one thread per (r, ky) sums U[t][r] s_t over the TRs of ky;
+//      s_t = sum_q U[t][q] H_q(ky(t)) and also stores it into the peer; after a cluster
+//      barrier each block adds the two parts (the same sum in both), then one lane per ky
+//      (a warp per r) sums U[t][r] s_t over the TRs of ky;
 //   3. warp w applies the adjoint DFT -> P_r(iy);
-//   4. one thread per iy contracts with the tangents over the block's r, and each block
-//      adds the two partial sums for its half of the column, writes g (masked, times nx)
-//      and its part of <v, g>; the last block adds the parts.
+//   4. one thread per iy contracts with the tangents over the block's r, keeping the part
+//      for its own half of the column and storing the rest into the peer; after a second
+//      cluster barrier each block adds the two parts for its half, writes g (masked,
+//      times nx) and its part of <v, g>; the last block adds the parts.
 // Two blocks per column (448 for 224 columns, three per SM) balance the SMs better than
 // one block of twice the size (224 blocks on 152 SMs).
 // ---------------------------------------------------------------------------
@@ -619,7 +620,8 @@ constexpr int kColThreads = 256, kColWarps = kColThreads / 32;
 
 size_t column_smem_bytes(int ny, int R, int ntr) {
   const size_t rc = (size_t)(R + 1) / 2;
-  return sizeof(float2) * ((size_t)ny + rc * (ny + 1) + 2 * (size_t)ntr) + sizeof(float) * 10 * (size_t)ny;
+  return sizeof(float2) * ((size_t)ny + rc * (ny + 1) + 2 * (size_t)ntr) + sizeof(float) * 14 * (size_t)ny +
+         sizeof(int) * ((size_t)ny + 1);
 }
 
 template <int N1>
@@ -630,7 +632,7 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
                       const int* __restrict__ kyptr, const int* __restrict__ kyof, int ntr, int nx, int ny, int nv,
                       int R, float scale,
                       float* __restrict__ g, double* red_part, unsigned* ticket, double* __restrict__ vdot,
-                      const int* __restrict__ gate) {
+                      double* __restrict__ vv, const int* __restrict__ gate) {
   // the gate is written by earlier launches only: both blocks of a cluster take the same
   // branch, so every cluster barrier below is reached by both
   if (gate != nullptr && *gate == 0) return;
@@ -642,24 +644,26 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
   extern __shared__ float2 fsm[];
   float2* rt = fsm;                                      // [ny] w^k
   float2* hs = rt + ny;                                  // [RC][ny + 1]: H, then G, then P
-  float2* sbuf = hs + RC * ld;                           // [ntr] this block's part of s_t
-  float2* sfull = sbuf + ntr;                            // [ntr] s_t
-  float* vox = reinterpret_cast<float*>(sfull + ntr);    // [6][ny]: v0, v1, m v2, m v3, Re rho, Im rho
+  float2* sbuf = hs + RC * ld;                           // [ntr] this block's part of s_t, then s_t
+  float2* sin = sbuf + ntr;                              // [ntr] the peer's part of s_t (written by it)
+  float* vox = reinterpret_cast<float*>(sin + ntr);      // [6][ny]: v0, v1, m v2, m v3, Re rho, Im rho
   float* red4 = vox + 6 * ny;                            // [4][ny] contraction over this block's r
-  float* vox_peer = cl.map_shared_rank(vox, peer);
-  const float* red4_peer = cl.map_shared_rank(red4, peer);
-  const float2* sbuf_peer = cl.map_shared_rank(sbuf, peer);
+  float* rin = red4 + 4 * ny;                            // [4][ny] the peer's contraction (written by it)
+  int* kyp = reinterpret_cast<int*>(rin + 4 * ny);       // [ny + 1] TR range of each ky
+  float2* sin_peer = cl.map_shared_rank(sin, peer);
+  float* red4_peer_in = cl.map_shared_rank(rin, peer);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int brev = (int)(__brev((unsigned)lane) >> 27);
   const size_t plane = (size_t)nx * ny;
   const int hy = (ny + 1) / 2, ya = crank * hy, ye = min(ny, ya + hy);  // this block's half of iy
   for (int e = tid; e < ny; e += kColThreads) rt[e] = roots[e];
-  __syncthreads();
+  for (int e = tid; e <= ny; e += kColThreads) kyp[e] = kyptr[e];
+  cl.sync();  // both blocks are running before either stores into the other's shared memory
   const Fft32Lane ffw = fft32_lane<false>(rt, N1, lane), ffa = fft32_lane<true>(rt, N1, lane);
-  float sf = 0.f;
+  float sf = 0.f, sv = 0.f;
   for (int ix = blockIdx.x >> 1; ix < nx; ix += gridDim.x >> 1) {
-    // 0. voxel data of this block's half, into both blocks
-    for (int iy = ya + tid; iy < ye; iy += kColThreads) {
+    // 0. the column's voxel data (each block loads all of it)
+    for (int iy = tid; iy < ny; iy += kColThreads) {
       const int j = iy * nx + ix;
       const float m = maskf[j];
       const float2 rh = rho[j];
@@ -668,12 +672,9 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
       for (int k = 0; k < 4; ++k) vk[k] = v[(size_t)k * nv + j];
       const float val[6] = {vk[0], vk[1], vk[2] * m, vk[3] * m, rh.x, rh.y};
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        vox[c * ny + iy] = val[c];
-        vox_peer[c * ny + iy] = val[c];
-      }
+      for (int c = 0; c < 6; ++c) vox[c * ny + iy] = val[c];
     }
-    cl.sync();
+    __syncthreads();
     // 1. h_r and its phase-encode DFT (warp w: local r = w, w + 8)
     for (int rl = warp; rl < nr; rl += kColWarps) {
       const float* cr = coefT + (size_t)(r0 + rl) * plane + (size_t)ix * ny;
@@ -708,26 +709,29 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
         sr = fmaf(u, h.x, sr);
         si = fmaf(u, h.y, si);
       }
-      sbuf[t] = make_float2(sr, si);
+      const float2 part = make_float2(sr, si);
+      sbuf[t] = part;
+      sin_peer[t] = part;  // the peer's copy of this block's part
     }
-    cl.sync();
+    cl.sync();  // both parts of every s_t are in both blocks
     for (int t = tid; t < ntr; t += kColThreads) {
-      const float2 a = sbuf[t], b = sbuf_peer[t];
-      sfull[t] = make_float2(a.x + b.x, a.y + b.y);  // commutative: the same s_t in both blocks
+      const float2 a = sbuf[t], b = sin[t];
+      sbuf[t] = make_float2(a.x + b.x, a.y + b.y);  // commutative: the same s_t in both blocks
     }
     __syncthreads();
-    for (int e = tid; e < nr * ny; e += kColThreads) {
-      const int rl = e / ny, ky = e - rl * ny;
-      const int ta = __ldg(kyptr + ky), te = __ldg(kyptr + ky + 1);
+    for (int rl = warp; rl < nr; rl += kColWarps) {  // warp per r, lanes over ky
       const float* ur = UgT + (size_t)(r0 + rl) * ntr;
-      float2 o = make_float2(0.f, 0.f);
-      for (int t = ta; t < te; ++t) {
-        const float u = __ldg(ur + t);
-        const float2 sv = sfull[t];
-        o.x = fmaf(u, sv.x, o.x);
-        o.y = fmaf(u, sv.y, o.y);
+      for (int ky = lane; ky < ny; ky += 32) {
+        const int ta = kyp[ky], te = kyp[ky + 1];
+        float2 o = make_float2(0.f, 0.f);
+        for (int t = ta; t < te; ++t) {
+          const float u = __ldg(ur + t);
+          const float2 sv = sbuf[t];
+          o.x = fmaf(u, sv.x, o.x);
+          o.y = fmaf(u, sv.y, o.y);
+        }
+        hs[rl * ld + ky] = o;
       }
-      hs[rl * ld + ky] = o;
     }
     __syncthreads();
     // 3. adjoint phase-encode DFT
@@ -765,30 +769,49 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
         a2 = fmaf(c, pv.y, a2);
         a3 = fmaf(-c, pv.x, a3);
       }
-      red4[iy] = a0;
-      red4[ny + iy] = a1;
-      red4[2 * ny + iy] = a2;
-      red4[3 * ny + iy] = a3;
+      // the part for this block's half of the column stays here, the rest goes to the peer
+      float* dst = (iy >= ya && iy < ye) ? red4 : red4_peer_in;
+      dst[iy] = a0;
+      dst[ny + iy] = a1;
+      dst[2 * ny + iy] = a2;
+      dst[3 * ny + iy] = a3;
     }
-    cl.sync();
+    cl.sync();  // the peer's part of this block's half has arrived
     for (int iy = ya + tid; iy < ye; iy += kColThreads) {
       const int j = iy * nx + ix;
       const float m = maskf[j] * scale;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const float val = (red4[k * ny + iy] + red4_peer[k * ny + iy]) * m;
+        const float val = (red4[k * ny + iy] + rin[k * ny + iy]) * m;
         g[(size_t)k * nv + j] = val;
-        if (vdot != nullptr) sf = fmaf(v[(size_t)k * nv + j], val, sf);
+        if (vdot != nullptr) {
+          const float vk = v[(size_t)k * nv + j];
+          sf = fmaf(vk, val, sf);
+          sv = fmaf(vk, vk, sv);
+        }
       }
     }
-    // the peer reads this block's vox, sbuf and red4 until here
-    cl.sync();
+    // No block reads the other's shared memory: every exchange is a store into the peer
+    // followed by a cluster barrier.  The next column's store into the peer's sin comes
+    // after this column's second barrier, and its store into the peer's rin after the
+    // next column's first barrier; the peer reaches those barriers only after it has read
+    // sin and rin for this column.
+    __syncthreads();
   }
   if (vdot == nullptr) return;
   __shared__ double ws[kColWarps];
   const double t = red::block_sum<kColThreads>((double)sf, ws);
-  if (threadIdx.x == 0) red_part[blockIdx.x] = t;
-  red::finish_reduction<kColThreads>(red_part, ticket, vdot, ws);
+  if (vv == nullptr) {
+    if (threadIdx.x == 0) red_part[blockIdx.x] = t;
+    red::finish_reduction<kColThreads>(red_part, ticket, vdot, ws);
+    return;
+  }
+  const double t2 = red::block_sum<kColThreads>((double)sv, ws);
+  if (threadIdx.x == 0) {
+    red_part[blockIdx.x] = t;
+    red_part[gridDim.x + blockIdx.x] = t2;
+  }
+  red::finish_reduction2<kColThreads>(red_part, ticket, vdot, vv, ws);
 }
 
 // Partial sums over one chunk of 8 basis functions (blockIdx.z) of
@@ -1268,7 +1291,7 @@ static cudaError_t ensure_coef_columns(Plan* p, cudaStream_t st) {
 }
 
 template <int N1>
-static cudaError_t launch_column_t(Plan* p, const float* v, double* vdot, float* out, cudaStream_t st) {
+static cudaError_t launch_column_t(Plan* p, const float* v, double* vdot, double* vv, float* out, cudaStream_t st) {
   LowRank& L = *p->lr;
   const int nx = p->nx, ny = p->ny, R = L.R;
   const size_t sm = column_smem_bytes(ny, R, p->ntr);
@@ -1279,27 +1302,27 @@ static cudaError_t launch_column_t(Plan* p, const float* v, double* vdot, float*
   const int grid = 2 * std::min(nx, kRedBlocks / 2);
   lr_jhjv_column_kernel<N1><<<grid, kColThreads, sm, st>>>(L.dft_small, v, L.coefT, p->rho, p->maskf, p->roots,
                                                            L.UgT, L.kyptr, L.kyof, p->ntr, nx, ny, p->nv, R,
-                                                           (float)nx, out, p->red, p->ticket, vdot, p->gate);
+                                                           (float)nx, out, p->red, p->ticket, vdot, vv, p->gate);
   return cudaGetLastError();
 }
 
-static cudaError_t launch_column(Plan* p, const float* v, double* vdot, float* out, cudaStream_t st) {
+static cudaError_t launch_column(Plan* p, const float* v, double* vdot, double* vv, float* out, cudaStream_t st) {
   switch (p->ny / 32) {
-    case 1: return launch_column_t<1>(p, v, vdot, out, st);
-    case 2: return launch_column_t<2>(p, v, vdot, out, st);
-    case 3: return launch_column_t<3>(p, v, vdot, out, st);
-    case 4: return launch_column_t<4>(p, v, vdot, out, st);
-    case 5: return launch_column_t<5>(p, v, vdot, out, st);
-    case 6: return launch_column_t<6>(p, v, vdot, out, st);
-    case 7: return launch_column_t<7>(p, v, vdot, out, st);
-    default: return launch_column_t<8>(p, v, vdot, out, st);
+    case 1: return launch_column_t<1>(p, v, vdot, vv, out, st);
+    case 2: return launch_column_t<2>(p, v, vdot, vv, out, st);
+    case 3: return launch_column_t<3>(p, v, vdot, vv, out, st);
+    case 4: return launch_column_t<4>(p, v, vdot, vv, out, st);
+    case 5: return launch_column_t<5>(p, v, vdot, vv, out, st);
+    case 6: return launch_column_t<6>(p, v, vdot, vv, out, st);
+    case 7: return launch_column_t<7>(p, v, vdot, vv, out, st);
+    default: return launch_column_t<8>(p, v, vdot, vv, out, st);
   }
 }
 
 // J^H J v for a fully sampled readout and ny = 32 N1: the column kernel (factorised
 // phase-encode DFT, Gram through the TR axis, adjoint, contraction and <v, J^H J v>), times
 // nx for the cancelled readout DFT pair.
-static int lowrank_jhjv_columns(Plan* p, const float* v, float* out, double* vdot, cudaStream_t st) {
+static int lowrank_jhjv_columns(Plan* p, const float* v, float* out, double* vdot, double* vv, cudaStream_t st) {
   cudaError_t e;
   {
     Span sp(p, MRSTAT_K_VECTOR, st);
@@ -1307,14 +1330,26 @@ static int lowrank_jhjv_columns(Plan* p, const float* v, float* out, double* vdo
   }
   if (e == cudaSuccess) {
     Span sp(p, MRSTAT_K_JHW_DOT, st);
-    e = launch_column(p, v, vdot, out, st);
+    e = launch_column(p, v, vdot, vv, out, st);
   }
   return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "low-rank J^H J v (column kernel)");
 }
 
-int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot) {
+int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot, double* vv) {
   LowRank& L = *p->lr;
-  if (L.column_path) return lowrank_jhjv_columns(p, v, out, vdot, st);
+  if (vv != nullptr && vdot == nullptr) {
+    const int s = lowrank_jhjv(p, v, out, st);
+    if (s != MRSTAT_OK) return s;
+    const cudaError_t e = do_dot(p, v, v, 4 * (int64_t)p->nv, vv, st);
+    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "dot launch");
+  }
+  if (L.column_path) return lowrank_jhjv_columns(p, v, out, vdot, vv, st);
+  if (vv != nullptr) {
+    const int s = lowrank_jhjv(p, v, out, st, vdot);
+    if (s != MRSTAT_OK) return s;
+    const cudaError_t e = do_dot(p, v, v, 4 * (int64_t)p->nv, vv, st);
+    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "dot launch");
+  }
   if (L.full_readout) return lowrank_jhjv_full_readout(p, v, out, vdot, st);
   if (vdot != nullptr) {
     const int s = lowrank_jhjv(p, v, out, st, nullptr);

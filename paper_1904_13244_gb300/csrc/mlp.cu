@@ -221,8 +221,9 @@ __device__ __forceinline__ float tanh_fast(float x) {
 // through L2.  Warp 0 issues the TMA loads (three input
 // tiles and the weight tile per 64-wide K chunk) into a ring of stages, warp 1 issues the
 // three MMAs per K step into one of two TMEM accumulator sets (3 x 64 columns each), and
-// warps 2..5 (one TMEM lane quarter each) run the epilogue of tile i while the MMAs of
-// tile i + 1 proceed: bias and tanh, the tangent scaling 1 - a^2, BF16, 32-byte stores
+// sixteen epilogue warps (four per TMEM lane quarter, one 16-column chunk each: enough
+// warps to hide the latency of the per-element work) run the epilogue of tile i while the
+// MMAs of tile i + 1 proceed: bias and tanh, the tangent scaling 1 - a^2, BF16, 32-byte stores
 // straight to the next layer's input rows (or, for the last layer, the scaled outputs).
 // Every wait is bounded; a CTA that gives up sets err and drains its copies in flight.
 // ---------------------------------------------------------------------------
@@ -236,8 +237,11 @@ struct PerShape {
   static constexpr size_t kSmem = (size_t)kPerStages * kStage + 1024 + 256;
 };
 
+constexpr int kPerEpiWarps = 16;  // four per TMEM lane quarter, one 16-column chunk each
+constexpr int kPerThreads = 64 + 32 * kPerEpiWarps;
+
 template <bool LAST>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kPerThreads, 1)
 mlp_layer_persistent_kernel(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tw, int B,
                             int N, int K, const float* __restrict__ bias, __nv_bfloat16* __restrict__ xn, int ldn,
                             const float* __restrict__ scale, float* __restrict__ pred, int* __restrict__ err) {
@@ -264,7 +268,7 @@ mlp_layer_persistent_kernel(const __grid_constant__ CUtensorMap tx, const __grid
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&accf[a], 1);
-      mbar_init(&acce[a], 4);  // one arrival per epilogue warp
+      mbar_init(&acce[a], kPerEpiWarps);  // one arrival per epilogue warp
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -333,7 +337,8 @@ mlp_layer_persistent_kernel(const __grid_constant__ CUtensorMap tx, const __grid
       }
     }
   } else {
-    const int q = warp & 3;  // TMEM lane quarter of this warp
+    const int q = warp & 3;              // TMEM lane quarter of this warp
+    const int cb = ((warp - 2) >> 2) * 16;  // its 16-column chunk of the tile
     int i = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
       const int acc = i & 1;
@@ -343,53 +348,51 @@ mlp_layer_persistent_kernel(const __grid_constant__ CUtensorMap tx, const __grid
       const int b0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
       const int b = b0 + q * 32 + lane;  // this lane's row (sample)
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 3 * BN);
-#pragma unroll 1
-      for (int cb = 0; cb < BN; cb += 16) {
-        __syncwarp();  // tcgen05.ld is warp-collective
-        float v0[16], v1[16], v2[16];
-        tmem_ld16(trow + (uint32_t)cb, v0);
-        tmem_ld16(trow + (uint32_t)(BN + cb), v1);
-        tmem_ld16(trow + (uint32_t)(2 * BN + cb), v2);
-        if (cb + 16 >= BN) {
-          // the whole accumulator set is in registers: hand it back to the MMA warp
-          fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&acce[acc]);
+      float v0[16], v1[16], v2[16];
+      tmem_ld16(trow + (uint32_t)cb, v0);
+      tmem_ld16(trow + (uint32_t)(BN + cb), v1);
+      tmem_ld16(trow + (uint32_t)(2 * BN + cb), v2);
+      // this warp's part of the accumulator set is in registers: hand it back
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[acc]);
+      if (b >= B) continue;
+      if (LAST) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int r = n0 + cb + j;
+          if (r < N) {
+            const float sc = scale[r];
+            pred[(size_t)r * B + b] = sc * (v0[j] + bias[r]);
+            pred[(size_t)(N + r) * B + b] = sc * v1[j];
+            pred[(size_t)(2 * N + r) * B + b] = sc * v2[j];
+          }
         }
-        if (b >= B) continue;
-        if (LAST) {
+      } else {
+        __align__(16) __nv_bfloat16 o[3][16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int r = n0 + cb + j;
-            if (r < N) {
-              const float sc = scale[r];
-              pred[(size_t)r * B + b] = sc * (v0[j] + bias[r]);
-              pred[(size_t)(N + r) * B + b] = sc * v1[j];
-              pred[(size_t)(2 * N + r) * B + b] = sc * v2[j];
-            }
-          }
-        } else {
-          __align__(16) __nv_bfloat16 o[3][16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = n0 + cb + j;
-            const float a = tanh_fast(v0[j] + (n < N ? bias[n] : 0.f));
-            const float dd = 1.f - a * a;
-            o[0][j] = __float2bfloat16_rn(a);
-            o[1][j] = __float2bfloat16_rn(dd * v1[j]);
-            o[2][j] = __float2bfloat16_rn(dd * v2[j]);
-          }
-          const int col = n0 + cb;
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + cb + j;
+          const float a = tanh_fast(v0[j] + (n < N ? bias[n] : 0.f));
+          const float dd = 1.f - a * a;
+          o[0][j] = __float2bfloat16_rn(a);
+          o[1][j] = __float2bfloat16_rn(dd * v1[j]);
+          o[2][j] = __float2bfloat16_rn(dd * v2[j]);
+        }
+        const int col = n0 + cb;
+        if (col + 16 <= ldn) {  // 32 bytes per stream (ldn and col are multiples of 8 elements)
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            __nv_bfloat16* dst = xn + ((size_t)k * B + b) * ldn + col;
-            if (col + 16 <= ldn) {  // 32 bytes (ldn and col are multiples of 8 elements)
-              reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(o[k])[0];
-              reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(o[k])[1];
-            } else {
-              for (int j = 0; col + j < ldn; ++j) dst[j] = o[k][j];
-            }
+            uint4* dst = reinterpret_cast<uint4*>(xn + ((size_t)k * B + b) * ldn + col);
+            dst[0] = reinterpret_cast<const uint4*>(o[k])[0];
+            dst[1] = reinterpret_cast<const uint4*>(o[k])[1];
           }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (col + j < ldn) xn[((size_t)k * B + b) * ldn + col + j] = o[k][j];
         }
       }
     }
@@ -644,7 +647,7 @@ static cudaError_t launch_persistent(const TcOperand& x, const CUtensorMap& w64,
   if (e != cudaSuccess) return e;
   const int tiles = ((B + tc::BM - 1) / tc::BM) * ((N + PerShape::BN - 1) / PerShape::BN);
   const int grid = std::max(1, std::min(tiles, sms));
-  mlp_layer_persistent_kernel<LAST><<<grid, 192, sm, st>>>(x.hi, w64, B, N, K, bias, xn, ldn, scale, pred, err);
+  mlp_layer_persistent_kernel<LAST><<<grid, kPerThreads, sm, st>>>(x.hi, w64, B, N, K, bias, xn, ldn, scale, pred, err);
   return cudaGetLastError();
 }
 

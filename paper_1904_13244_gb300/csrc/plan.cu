@@ -40,7 +40,7 @@ namespace {
 void free_plan(Plan* p) {
   if (p == nullptr) return;
   void* ptrs[] = {p->cs, p->phi, p->kyi, p->ky_ptr, p->ky_tr, p->roots, p->ft, p->fh, p->D, p->rho, p->maskf,
-                  p->dfwd, p->cf, p->A, p->wt, p->red, p->ticket, p->cg_r, p->cg_p, p->cg_q,
+                  p->dfwd, p->cf, p->A, p->wt, p->red, p->ticket, p->cg_r, p->cg_p, p->cg_q, p->cg_w,
                   p->cg_jv, p->cg_s, p->cg_frozen, p->D2, p->rho2, p->gn_g, p->gn_z, p->gn_res,
                   p->gn_dir, p->gn_q, p->gn_alpha, p->gn_trial, p->gn_s, p->gn_r, p->gn_st,
                   p->gn_rt, p->gn_jv, p->gn_mask, p->gn_sc, p->gn_si, p->bf_ft_hi, p->bf_ft_lo,
@@ -253,8 +253,14 @@ int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* ma
 // J^H J v.  With a fully sampled readout (nkx == nx: kx runs over a whole period of the
 // x frequencies) the readout DFT and its adjoint cancel, F^H F = nx I, so
 // W~ = nx A and the two x-DFTs are skipped: exact, not an approximation.
-int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot) {
-  if (p->lr && p->lr->active) return lowrank_jhjv(p, v, out, st, vdot);
+int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot, double* vv) {
+  if (p->lr && p->lr->active) return lowrank_jhjv(p, v, out, st, vdot, vv);
+  if (vv != nullptr) {
+    const int s = do_jhjv(p, v, out, st, vdot);
+    if (s != MRSTAT_OK) return s;
+    const cudaError_t e = do_dot(p, v, v, (int64_t)p->npar * p->nv, vv, st);
+    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "dot launch");
+  }
   if (vdot != nullptr) {
     const int s = do_jhjv(p, v, out, st, nullptr);
     if (s != MRSTAT_OK) return s;
@@ -461,6 +467,7 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(dalloc(p, &p->cg_r, (size_t)p->npar * nv));
   chk(dalloc(p, &p->cg_p, (size_t)p->npar * nv));
   chk(dalloc(p, &p->cg_q, (size_t)p->npar * nv));
+  chk(dalloc(p, &p->cg_w, (size_t)p->npar * nv));
   chk(dalloc(p, &p->cg_jv, (size_t)p->ntr * p->nkx));
   chk(dalloc(p, &p->cg_frozen, 1));
   chk(dalloc(p, &p->dev_err, 1));
@@ -705,28 +712,23 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
   }
   const int64_t n = (int64_t)plan->npar * plan->nv;
   double* sc = plan->cg_s;
+  // Chronopoulos-Gear form: the product is applied to the residual, w = B r, with
+  // delta = <r, w> and gamma = <r, r> formed in the same pass; one vector kernel then
+  // updates p, q = B p, x and r.  Per iteration k the scalars sit at sc[4k..4k+2].
   cudaError_t e = cudaMemsetAsync(plan->cg_frozen, 0, sizeof(int), st);
   if (e == cudaSuccess) {
     Span sp(plan, MRSTAT_K_VECTOR, st);
-    e = launch_cg_init(rhs, x, plan->cg_r, plan->cg_p, n, st);
+    e = launch_cg_init(rhs, x, plan->cg_r, plan->cg_p, plan->cg_q, n, st);
   }
-  if (e == cudaSuccess) e = do_dot(plan, plan->cg_r, plan->cg_r, n, sc + 0, st);
   if (e != cudaSuccess) return cuda_fail(e, "CG init");
   for (int it = 0; it < iters; ++it) {
-    double* rr = sc + 4 * it;
-    double* pq = rr + 1;
-    double* rr_next = sc + 4 * (it + 1);
-    // q = Re(J^H J) p and pq = <p, q>
-    const int s = do_jhjv(plan, plan->cg_p, plan->cg_q, st, pq);
+    double* sk = sc + 4 * it;
+    const int s = do_jhjv(plan, plan->cg_r, plan->cg_w, st, sk, sk + 1);
     if (s != MRSTAT_OK) return s;
     {
       Span sp(plan, MRSTAT_K_VECTOR, st);
-      e = launch_cg_update_xr(x, plan->cg_r, plan->cg_p, plan->cg_q, n, rr, pq, plan->cg_frozen, plan->red,
-                              plan->ticket, rr_next, st);
-    }
-    if (e == cudaSuccess) {
-      Span sp(plan, MRSTAT_K_VECTOR, st);
-      e = launch_cg_update_p(plan->cg_p, plan->cg_r, n, rr, rr_next, plan->cg_frozen, st);
+      e = launch_cg_cg_step(x, plan->cg_r, plan->cg_p, plan->cg_q, plan->cg_w, n, sk, it > 0 ? sk - 4 : nullptr,
+                            plan->cg_frozen, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "CG iteration");
   }

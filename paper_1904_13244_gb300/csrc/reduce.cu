@@ -1,5 +1,5 @@
-// K5: float64-accumulated inner products and the vector updates of the inner CG
-// solve (Algorithm 6; Eq. 4 solved by CG).
+// K5: float64-accumulated inner products and the vector update of the inner CG solve
+// (Algorithm 6; Eq. 4 solved by CG).
 //
 // Reductions are deterministic and single-pass: every block writes its partial sum,
 // and the last block to finish (a release fence plus an atomic ticket) adds the
@@ -8,9 +8,8 @@
 // everything from the warp level up is added in float64.  GB300 runs float64 at a small
 // fraction of the float32 rate, and converting every element to float64 kept the FP64
 // pipe busy for most of these kernels' time.  CG scalars
-// never leave the device: each update kernel reads the float64 inner products it
-// needs, forms alpha or beta once per block (GB300's float64 rate makes a per-thread
-// division visible) and the x/r update also produces the partial sums of r.r.
+// never leave the device: the update kernel reads the float64 inner products it needs and
+// forms alpha and beta once per warp.
 #include "internal.cuh"
 #include "reduce.cuh"
 
@@ -48,103 +47,87 @@ dot_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n, 
   finish_reduction<kT>(part, ticket, out, ws);
 }
 
-__global__ void cg_init_kernel(const float* __restrict__ rhs, float* __restrict__ x,
-                               float* __restrict__ r, float* __restrict__ p, int64_t n) {
+__global__ void cg_init_kernel(const float* __restrict__ rhs, float* __restrict__ x, float* __restrict__ r,
+                               float* __restrict__ p, float* __restrict__ q, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const float b = rhs[i];
     x[i] = 0.f;
-    r[i] = b;
-    p[i] = b;
+    r[i] = rhs[i];
+    p[i] = 0.f;
+    q[i] = 0.f;
   }
 }
 
-// x += alpha p, r -= alpha q with alpha = rr / pq (0 once frozen: pq <= 0 or rr == 0),
-// then rr_new = r.r.  When alpha is 0 the vectors are left alone and rr_new = rr.  Lane 0
-// of each warp forms alpha in float64 (once per warp: GB300's float64 rate makes a
-// per-thread division visible).  Block 0 marks the solve frozen; a block that reads the
-// flag after that reaches the same decision, since the flag is only set when it holds.
+// One CG iteration in the Chronopoulos-Gear form on B x = b, after the product w = B r
+// that also left delta = <r, w> and gamma = <r, r> in sk[0] and sk[1]:
+//   beta = gamma / gamma_prev (0 in the first iteration),
+//   pq = delta - beta gamma / alpha_prev (= <p, B p> of the new p; delta at first),
+//   alpha = gamma / pq,
+//   p = r + beta p,  q = w + beta q (= B p),  x += alpha p,  r -= alpha q.
+// In exact arithmetic these are the iterates of textbook CG; the product is applied to r,
+// so the inner products come with it and one vector pass remains.  An iteration with
+// pq <= 0 or gamma == 0 freezes x, r, p and q for the rest (block 0 marks the solve
+// frozen; a block that reads the flag after that reaches the same decision).  Lane 0 of
+// each warp forms the scalars in float64 (GB300's float64 rate makes a per-thread
+// division visible); block 0 keeps alpha for the next iteration in sk[2].
 __global__ void __launch_bounds__(kT)
-cg_update_xr_kernel(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p,
-                    const float* __restrict__ q, int64_t n, int64_t n4, const double* __restrict__ rr,
-                    const double* __restrict__ pq, int* __restrict__ frozen, double* part,
-                    unsigned* ticket, double* __restrict__ rr_new) {
-  __shared__ double ws[kT / 32];
+cg_cg_step_kernel(float* __restrict__ x, float* __restrict__ r, float* __restrict__ p, float* __restrict__ q,
+                  const float* __restrict__ w, int64_t n, int64_t n4, double* __restrict__ sk,
+                  const double* __restrict__ sp, int* __restrict__ frozen) {
   const int64_t t0 = blockIdx.x * (int64_t)kT + threadIdx.x, stride = (int64_t)gridDim.x * kT;
-  float4 xv, rv, pv, qv;
+  float4 xv, rv, pv, qv, wv;
   if (t0 < n4) {
     xv = ld4(x, t0);
     rv = ld4(r, t0);
     pv = ld4(p, t0);
     qv = ld4(q, t0);
+    wv = ld4(w, t0);
   }
-  float al = 0.f;
+  float al = 0.f, be = 0.f;
   int apply = 0;
   if ((threadIdx.x & 31) == 0) {
-    const double rrv = *rr, pqv = *pq;
-    apply = !*frozen && pqv > 0.0 && rrv > 0.0;
-    al = apply ? (float)(rrv / pqv) : 0.f;
-    if (!apply && blockIdx.x == 0 && threadIdx.x == 0) *frozen = 1;
+    const double delta = sk[0], gamma = sk[1];
+    double beta = 0.0, pq = delta;
+    if (sp != nullptr) {
+      beta = gamma / sp[1];
+      pq = delta - beta * gamma / sp[2];
+    }
+    apply = !*frozen && pq > 0.0 && gamma > 0.0;
+    if (apply) {
+      al = (float)(gamma / pq);
+      be = (float)beta;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (apply) sk[2] = gamma / pq;
+      else *frozen = 1;
+    }
   }
   al = __shfl_sync(0xffffffffu, al, 0);
+  be = __shfl_sync(0xffffffffu, be, 0);
   apply = __shfl_sync(0xffffffffu, apply, 0);
-  float sf = 0.f;
+  if (!apply) return;
   for (int64_t i = t0; i < n4; i += stride) {
     if (i != t0) {
       xv = ld4(x, i);
       rv = ld4(r, i);
       pv = ld4(p, i);
       qv = ld4(q, i);
+      wv = ld4(w, i);
     }
-    if (apply) {
-      st4(x, i, axpy4(al, pv, xv));
-      rv = axpy4(-al, qv, rv);
-      st4(r, i, rv);
-    }
-    sf = dot4(rv, rv, sf);
+    pv = axpy4(be, pv, rv);
+    qv = axpy4(be, qv, wv);
+    st4(p, i, pv);
+    st4(q, i, qv);
+    st4(x, i, axpy4(al, pv, xv));
+    st4(r, i, axpy4(-al, qv, rv));
   }
   for (int64_t i = 4 * n4 + t0; i < n; i += stride) {
-    float ri = r[i];
-    if (apply) {
-      x[i] = fmaf(al, p[i], x[i]);
-      ri = fmaf(-al, q[i], ri);
-      r[i] = ri;
-    }
-    sf = fmaf(ri, ri, sf);
+    const float pi = fmaf(be, p[i], r[i]), qi = fmaf(be, q[i], w[i]);
+    p[i] = pi;
+    q[i] = qi;
+    x[i] = fmaf(al, pi, x[i]);
+    r[i] = fmaf(-al, qi, r[i]);
   }
-  const double s = block_sum<kT>((double)sf, ws);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-  finish_reduction<kT>(part, ticket, rr_new, ws);
-}
-
-// p = r + beta p with beta = rr_new / rr_old (left alone once frozen)
-__global__ void __launch_bounds__(kT)
-cg_update_p_kernel(float* __restrict__ p, const float* __restrict__ r, int64_t n, int64_t n4,
-                   const double* __restrict__ rr_old, const double* __restrict__ rr_new,
-                   const int* __restrict__ frozen) {
-  const int64_t t0 = blockIdx.x * (int64_t)kT + threadIdx.x, stride = (int64_t)gridDim.x * kT;
-  float4 pv, rv;
-  if (t0 < n4) {
-    pv = ld4(p, t0);
-    rv = ld4(r, t0);
-  }
-  float beta = 0.f;
-  int apply = 0;
-  if ((threadIdx.x & 31) == 0) {
-    apply = !*frozen;
-    beta = apply ? (float)(*rr_new / *rr_old) : 0.f;
-  }
-  beta = __shfl_sync(0xffffffffu, beta, 0);
-  apply = __shfl_sync(0xffffffffu, apply, 0);
-  if (!apply) return;
-  for (int64_t i = t0; i < n4; i += stride) {
-    if (i != t0) {
-      pv = ld4(p, i);
-      rv = ld4(r, i);
-    }
-    st4(p, i, axpy4(beta, pv, rv));
-  }
-  for (int64_t i = 4 * n4 + t0; i < n; i += stride) p[i] = fmaf(beta, p[i], r[i]);
 }
 
 // About one float4 per thread, at most kRedBlocks blocks (one float64 partial each).
@@ -165,23 +148,15 @@ cudaError_t launch_dot(const float* a, const float* b, int64_t n, double* partia
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_init(const float* rhs, float* x, float* r, float* p, int64_t n, cudaStream_t st) {
-  cg_init_kernel<<<grid_for(n), kT, 0, st>>>(rhs, x, r, p, n);
+cudaError_t launch_cg_init(const float* rhs, float* x, float* r, float* p, float* q, int64_t n, cudaStream_t st) {
+  cg_init_kernel<<<grid_for(n), kT, 0, st>>>(rhs, x, r, p, q, n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_update_xr(float* x, float* r, const float* p, const float* q, int64_t n,
-                                const double* rr, const double* pq, int* frozen, double* partials,
-                                unsigned* ticket, double* rr_new, cudaStream_t st) {
-  const int64_t n4 = aligned16(x) && aligned16(r) && aligned16(p) && aligned16(q) ? n / 4 : 0;
-  cg_update_xr_kernel<<<grid_for(n), kT, 0, st>>>(x, r, p, q, n, n4, rr, pq, frozen, partials, ticket, rr_new);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cg_update_p(float* p, const float* r, int64_t n, const double* rr_old,
-                               const double* rr_new, const int* frozen, cudaStream_t st) {
-  const int64_t n4 = aligned16(p) && aligned16(r) ? n / 4 : 0;
-  cg_update_p_kernel<<<grid_for(n), kT, 0, st>>>(p, r, n, n4, rr_old, rr_new, frozen);
+cudaError_t launch_cg_cg_step(float* x, float* r, float* p, float* q, const float* w, int64_t n, double* sk,
+                              const double* sp, int* frozen, cudaStream_t st) {
+  const int64_t n4 = aligned16(x) && aligned16(r) && aligned16(p) && aligned16(q) && aligned16(w) ? n / 4 : 0;
+  cg_cg_step_kernel<<<grid_for(n), kT, 0, st>>>(x, r, p, q, w, n, n4, sk, sp, frozen);
   return cudaGetLastError();
 }
 

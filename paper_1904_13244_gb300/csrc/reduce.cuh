@@ -48,5 +48,33 @@ __device__ __forceinline__ void finish_reduction(double* part, unsigned* ticket,
   }
 }
 
+// Two sums at once: after thread 0 of each block stored its partials in part[blockIdx.x]
+// and part[gridDim.x + blockIdx.x], the last block adds each in block order into out0,
+// out1.  Uses `ws` (>= THREADS/32 doubles).
+template <int THREADS>
+__device__ __forceinline__ void finish_reduction2(double* part, unsigned* ticket, double* out0, double* out1,
+                                                  double* ws) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s0 = 0.0, s1 = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += THREADS) {
+    s0 += ((volatile double*)part)[i];
+    s1 += ((volatile double*)part)[gridDim.x + i];
+  }
+  s0 = block_sum<THREADS>(s0, ws);
+  s1 = block_sum<THREADS>(s1, ws);
+  if (threadIdx.x == 0) {
+    *out0 = s0;
+    *out1 = s1;
+    *ticket = 0u;
+  }
+}
+
 }  // namespace red
 }  // namespace mrstat
