@@ -26,7 +26,9 @@ matrix, and 10 surrogate iterations followed by 5 exact ones (key "recon": secon
 and T1/T2/rho NRMSE against the ground truth, and whether the fast runs reach the
 plain run's NRMSE: |NRMSE_fast - NRMSE_plain| <= max(0.1 NRMSE_plain, 1e-3)), plus one
 reconstruction with B1 as a fifth unknown on the phantom with a smooth B1 field
-(key "recon.b1_estimated").
+(key "recon.b1_estimated"), and the same step in the low-rank form on the paper's other
+sequence shapes: 224 x 224 with 1792 TRs and the sine-squared train, and the 112 x 88,
+16-fill constant-flip scan (key "shapes": products/s).
 Inputs are the seeded brain-like phantom and flip train of ``synth``.
 
 Multi-GPU: N independent replicas (one per rank), weak scaling, no collective on
@@ -81,6 +83,7 @@ def parse_args():
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--rank", type=int, default=32)
     ap.add_argument("--no-recon", action="store_true")
+    ap.add_argument("--no-shapes", action="store_true")
     return ap.parse_args()
 
 
@@ -371,6 +374,34 @@ def main():
         plain = {"value": world * iters / (pms / 1e3), "ms_per_step": pms,
                  "kernel_ms_per_step": {k: pstats[k]["ms"] / max(1, args.steps // 4) for k in all_kernels}}
 
+    # the paper's other sequence shapes (Supporting Information S1 / S3): the same step in
+    # the low-rank form (coefficients by exact projection), products/s
+    shapes = None
+    if not args.no_shapes and world == 1:
+        shapes = {}
+        rng_s = np.random.default_rng(1000)
+        train_s = torch.tensor(np.stack([rng_s.uniform(np.log(100), np.log(6000), 4096),
+                                         rng_s.uniform(np.log(10), np.log(3000), 4096)]), dtype=torch.float32,
+                               device="cuda")
+        for name in ("brain224_1792", "const112x88"):
+            sseq, sph = synth.config(name, seed=rank)
+            splan = mr.Plan(sseq)
+            sa = torch.tensor(alpha_of(sph), device="cuda")
+            srhs = torch.tensor(synth.random_params(sseq.nv, 100 + rank).astype(np.float32), device="cuda")
+            sx = torch.empty_like(srhs)
+            sU, _ = splan.lowrank_basis(train_s, args.rank)
+            splan.lowrank_set_basis(sU)
+
+            def sstep(splan=splan, sa=sa, srhs=srhs, sx=sx):
+                splan.lowrank_linearize(sa)
+                splan.cg_fixed(srhs, iters, out=sx)
+            sms, _, _ = timed(splan, sstep, max(3, args.steps // 6), ())
+            shapes[name] = {"products_per_s": iters / (sms / 1e3), "ms_per_step": sms,
+                            "grid": [sseq.nx, sseq.ny], "ntr": sseq.ntr,
+                            "train": synth.CONFIGS[name].get("train", "smooth"),
+                            "column_kernel": bool(sseq.ny % 32 == 0 and sseq.ny // 32 <= 8)}
+            splan.close()
+
     # end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -580,9 +611,9 @@ def main():
 
     launches = int(sum(stats[k]["launches"] for k in stats))
     if args.form == "surrogate":
-        # MLP inference per step: the input kernel and four fused layer kernels (outside the
-        # plan's counters)
-        launches += 5 * args.steps
+        # MLP inference per step: the first layer on the CUDA cores and three fused
+        # tensor-core layers (outside the plan's counters)
+        launches += 4 * args.steps
     if rank == 0:
         dft = ("factorised FP32 phase-encode DFT" if fft_y else "split-BF16 tcgen05 DFTs")
         form_desc = {"surrogate": f"learned surrogate + low-rank form (rank {R} time basis, MLP {args.hidden}x3 "
@@ -607,7 +638,7 @@ def main():
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu, "plain": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
-                "recon": recon, "surrogate": surrogate_info,
+                "recon": recon, "surrogate": surrogate_info, "shapes": shapes,
                 "kernel_ms_per_step": {k: v for k, v in per_step_ms.items()}}
         print(json.dumps(line), flush=True)
     if net is not None:

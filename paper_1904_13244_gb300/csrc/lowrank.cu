@@ -40,14 +40,6 @@ __device__ __forceinline__ void put_split(__nv_bfloat16* hi, __nv_bfloat16* lo, 
   lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-__device__ __forceinline__ int mod_small_l(int a, int n, float inv_n) {
-  int q = __float2int_rz(__int2float_rn(a) * inv_n);
-  int r = a - q * n;
-  r += (r < 0) ? n : 0;
-  r -= (r >= n) ? n : 0;
-  return r;
-}
-
 // ---------------------------------------------------------------------------
 // exact linearisation projected onto U: Bloch recursion with tangents (as bloch.cu),
 // accumulating c_r += U[n][r] m_y, dc1_r += U[n][r] dm_y/dlnT1, dc2_r += U[n][r] dm_y/dlnT2
@@ -617,20 +609,19 @@ __global__ void lr_coef_transpose_kernel(const float* __restrict__ coef, int nx,
 // one block of twice the size (224 blocks on 152 SMs).
 // ---------------------------------------------------------------------------
 constexpr int kColThreads = 256, kColWarps = kColThreads / 32;
+constexpr int kColMaxRc = 16;  // basis functions per block: R <= 32
 
-size_t column_smem_bytes(int ny, int R, int ntr) {
+size_t column_smem_bytes(int ny, int R, int kmax) {
   const size_t rc = (size_t)(R + 1) / 2;
-  return sizeof(float2) * ((size_t)ny + rc * (ny + 1) + 2 * (size_t)ntr) + sizeof(float) * 14 * (size_t)ny +
-         sizeof(int) * ((size_t)ny + 1);
+  return sizeof(float2) * ((size_t)ny + rc * (ny + 1) + 2 * (size_t)kmax * ny) + sizeof(float) * 14 * (size_t)ny;
 }
 
 template <int N1>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kColThreads, 3)
 lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restrict__ v,
                       const float* __restrict__ coefT, const float2* __restrict__ rho,
-                      const float* __restrict__ maskf, const float2* __restrict__ roots, const float* __restrict__ UgT,
-                      const int* __restrict__ kyptr, const int* __restrict__ kyof, int ntr, int nx, int ny, int nv,
-                      int R, float scale,
+                      const float* __restrict__ maskf, const float2* __restrict__ roots, const float* __restrict__ UgS,
+                      int kmax, int nx, int ny, int nv, int R, float scale,
                       float* __restrict__ g, double* red_part, unsigned* ticket, double* __restrict__ vdot,
                       double* __restrict__ vv, const int* __restrict__ gate) {
   // the gate is written by earlier launches only: both blocks of a cluster take the same
@@ -639,31 +630,29 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
   const int crank = (int)cl.block_rank(), peer = crank ^ 1;
-  const int ld = ny + 1;
+  constexpr int NY = 32 * N1, LD = NY + 1;  // the launch passes ny == NY
   const int RC = (R + 1) / 2, r0 = crank * RC, nr = min(R, r0 + RC) - r0;
   extern __shared__ float2 fsm[];
-  float2* rt = fsm;                                      // [ny] w^k
-  float2* hs = rt + ny;                                  // [RC][ny + 1]: H, then G, then P
-  float2* sbuf = hs + RC * ld;                           // [ntr] this block's part of s_t, then s_t
-  float2* sin = sbuf + ntr;                              // [ntr] the peer's part of s_t (written by it)
-  float* vox = reinterpret_cast<float*>(sin + ntr);      // [6][ny]: v0, v1, m v2, m v3, Re rho, Im rho
-  float* red4 = vox + 6 * ny;                            // [4][ny] contraction over this block's r
-  float* rin = red4 + 4 * ny;                            // [4][ny] the peer's contraction (written by it)
-  int* kyp = reinterpret_cast<int*>(rin + 4 * ny);       // [ny + 1] TR range of each ky
+  float2* rt = fsm;                                      // [NY] w^k
+  float2* hs = rt + NY;                                  // [RC][NY + 1]: H, then G, then P
+  float2* sbuf = hs + RC * LD;                           // [kmax][NY] this block's part of s, then s
+  float2* sin = sbuf + kmax * NY;                        // [kmax][NY] the peer's part (written by it)
+  float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // [6][NY]: v0, v1, m v2, m v3, Re rho, Im rho
+  float* red4 = vox + 6 * NY;                            // [4][NY] contraction over this block's r
+  float* rin = red4 + 4 * NY;                            // [4][NY] the peer's contraction (written by it)
   float2* sin_peer = cl.map_shared_rank(sin, peer);
   float* red4_peer_in = cl.map_shared_rank(rin, peer);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int brev = (int)(__brev((unsigned)lane) >> 27);
-  const size_t plane = (size_t)nx * ny;
-  const int hy = (ny + 1) / 2, ya = crank * hy, ye = min(ny, ya + hy);  // this block's half of iy
-  for (int e = tid; e < ny; e += kColThreads) rt[e] = roots[e];
-  for (int e = tid; e <= ny; e += kColThreads) kyp[e] = kyptr[e];
+  const size_t plane = (size_t)nx * NY;
+  const int hy = (NY + 1) / 2, ya = crank * hy, ye = min(NY, ya + hy);  // this block's half of iy
+  for (int e = tid; e < NY; e += kColThreads) rt[e] = roots[e];
   cl.sync();  // both blocks are running before either stores into the other's shared memory
   const Fft32Lane ffw = fft32_lane<false>(rt, N1, lane), ffa = fft32_lane<true>(rt, N1, lane);
   float sf = 0.f, sv = 0.f;
   for (int ix = blockIdx.x >> 1; ix < nx; ix += gridDim.x >> 1) {
     // 0. the column's voxel data (each block loads all of it)
-    for (int iy = tid; iy < ny; iy += kColThreads) {
+    for (int iy = tid; iy < NY; iy += kColThreads) {
       const int j = iy * nx + ix;
       const float m = maskf[j];
       const float2 rh = rho[j];
@@ -672,71 +661,95 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
       for (int k = 0; k < 4; ++k) vk[k] = v[(size_t)k * nv + j];
       const float val[6] = {vk[0], vk[1], vk[2] * m, vk[3] * m, rh.x, rh.y};
 #pragma unroll
-      for (int c = 0; c < 6; ++c) vox[c * ny + iy] = val[c];
+      for (int c = 0; c < 6; ++c) vox[c * NY + iy] = val[c];
     }
     __syncthreads();
-    // 1. h_r and its phase-encode DFT (warp w: local r = w, w + 8)
-    for (int rl = warp; rl < nr; rl += kColWarps) {
-      const float* cr = coefT + (size_t)(r0 + rl) * plane + (size_t)ix * ny;
-      float2 xin[N1];
+    // 1. h_r and its phase-encode DFT; warp w takes the pair of local r = w, w + 8: the
+    //    coefficient loads of both issue together and the voxel data is read once; the
+    //    second column waits in its own row of hs (in iy order) while the first is
+    //    transformed
+    for (int ra = warp; ra < nr; ra += 2 * kColWarps) {
+      const int rb = ra + kColWarps;
+      const bool two = rb < nr;
+      const float* ca = coefT + (size_t)(r0 + ra) * plane + (size_t)ix * NY;
+      const float* cbp = two ? coefT + (size_t)(r0 + rb) * plane + (size_t)ix * NY : ca;
+      float2 xa[N1];
 #pragma unroll
       for (int i1 = 0; i1 < N1; ++i1) {
         const int iy = 32 * i1 + lane;
-        const float c = cr[iy];
-        const float t = fmaf(vox[iy], cr[(size_t)R * plane + iy], vox[ny + iy] * cr[(size_t)2 * R * plane + iy]);
-        const float qr = vox[4 * ny + iy] * t + vox[2 * ny + iy] * c;
-        const float qi = vox[5 * ny + iy] * t + vox[3 * ny + iy] * c;
-        xin[i1] = make_float2(-qi, qr);
+        const float v0 = vox[iy], v1 = vox[NY + iy], v2 = vox[2 * NY + iy], v3 = vox[3 * NY + iy];
+        const float rr = vox[4 * NY + iy], ri = vox[5 * NY + iy];
+        const float c = ca[iy], t = fmaf(v0, ca[(size_t)R * plane + iy], v1 * ca[(size_t)2 * R * plane + iy]);
+        const float d = cbp[iy], u = fmaf(v0, cbp[(size_t)R * plane + iy], v1 * cbp[(size_t)2 * R * plane + iy]);
+        xa[i1] = make_float2(-(ri * t + v3 * c), rr * t + v2 * c);
+        if (two) hs[rb * LD + iy] = make_float2(-(ri * u + v3 * d), rr * u + v2 * d);
       }
-      float2 X[N1];
-      dft_small<N1, false>(W, xin, X);
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1) {
+          if (!two) break;
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        float2 acc = cmul(X[k1], rt[k1 * lane]);  // k1 lane <= 31 (N1 - 1) < ny
-        acc = fft32_warp(acc, ffw);
-        hs[rl * ld + k1 + N1 * brev] = acc;
+          for (int i1 = 0; i1 < N1; ++i1) xa[i1] = hs[rb * LD + 32 * i1 + lane];  // this lane's own stores
+          __syncwarp();  // every lane has its inputs before any output lands in the row
+        }
+        float2 X[N1];
+        dft_small<N1, false>(W, xa, X);
+        const int rl = h == 0 ? ra : rb;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+          float2 acc = cmul(X[k1], rt[k1 * lane]);  // k1 lane <= 31 (N1 - 1) < NY
+          acc = fft32_warp(acc, ffw);
+          hs[rl * LD + k1 + N1 * brev] = acc;
+        }
       }
     }
     __syncthreads();
-    // 2. per-ky Gram through the TR axis (U transposed: coalesced over t)
-    for (int t = tid; t < ntr; t += kColThreads) {
-      const int ky = kyof[t];
+    // 2. per-ky Gram through the TR axis, with the TRs of each ky in slots i < kmax
+    //    (U as UgS[r][i][ky], zero past a ky's TRs; s as [i][ky]): consecutive lanes take
+    //    consecutive ky, so U is read coalesced and s without bank conflicts.
+    //    2a. thread per (i, ky): this block's part of s[i][ky] = sum_q U[i-th TR of ky][q] H_q(ky)
+    for (int e = tid; e < kmax * NY; e += kColThreads) {
+      const int i = e / NY, ky = e - i * NY;
       float sr = 0.f, si = 0.f;
-#pragma unroll 8
-      for (int q = 0; q < nr; ++q) {
-        const float u = __ldg(UgT + (size_t)(r0 + q) * ntr + t);
-        const float2 h = hs[q * ld + ky];
-        sr = fmaf(u, h.x, sr);
-        si = fmaf(u, h.y, si);
+#pragma unroll
+      for (int q = 0; q < kColMaxRc; ++q) {  // unrolled: the loads of U issue together
+        if (q < nr) {
+          const float u = __ldg(UgS + ((size_t)(r0 + q) * kmax + i) * NY + ky);
+          const float2 h = hs[q * LD + ky];
+          sr = fmaf(u, h.x, sr);
+          si = fmaf(u, h.y, si);
+        }
       }
       const float2 part = make_float2(sr, si);
-      sbuf[t] = part;
-      sin_peer[t] = part;  // the peer's copy of this block's part
+      sbuf[e] = part;
+      sin_peer[e] = part;  // the peer's copy of this block's part
     }
-    cl.sync();  // both parts of every s_t are in both blocks
-    for (int t = tid; t < ntr; t += kColThreads) {
-      const float2 a = sbuf[t], b = sin[t];
-      sbuf[t] = make_float2(a.x + b.x, a.y + b.y);  // commutative: the same s_t in both blocks
+    cl.sync();  // both parts of every s are in both blocks
+    for (int e = tid; e < kmax * NY; e += kColThreads) {
+      const float2 a = sbuf[e], b = sin[e];
+      sbuf[e] = make_float2(a.x + b.x, a.y + b.y);  // commutative: the same s in both blocks
     }
     __syncthreads();
-    for (int rl = warp; rl < nr; rl += kColWarps) {  // warp per r, lanes over ky
-      const float* ur = UgT + (size_t)(r0 + rl) * ntr;
-      for (int ky = lane; ky < ny; ky += 32) {
-        const int ta = kyp[ky], te = kyp[ky + 1];
+    //    2b. warp per r, lane per ky: G_r(ky) = sum_i U[i-th TR of ky][r] s[i][ky]
+    for (int rl = warp; rl < nr; rl += kColWarps) {
+      const float* ur = UgS + (size_t)(r0 + rl) * kmax * NY;
+#pragma unroll
+      for (int ky = lane; ky < NY; ky += 32) {
         float2 o = make_float2(0.f, 0.f);
-        for (int t = ta; t < te; ++t) {
-          const float u = __ldg(ur + t);
-          const float2 sv = sbuf[t];
+#pragma unroll 4
+        for (int i = 0; i < kmax; ++i) {
+          const float u = __ldg(ur + (size_t)i * NY + ky);
+          const float2 sv = sbuf[i * NY + ky];
           o.x = fmaf(u, sv.x, o.x);
           o.y = fmaf(u, sv.y, o.y);
         }
-        hs[rl * ld + ky] = o;
+        hs[rl * LD + ky] = o;
       }
     }
     __syncthreads();
     // 3. adjoint phase-encode DFT
     for (int rl = warp; rl < nr; rl += kColWarps) {
-      float2* x = hs + rl * ld;
+      float2* x = hs + rl * LD;
       const int i2 = brev;
       float2 z[N1];
 #pragma unroll
@@ -754,27 +767,30 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
     }
     __syncthreads();
     // 4. contraction with the tangents over this block's r, one thread per iy
-    for (int iy = tid; iy < ny; iy += kColThreads) {
+    for (int iy = tid; iy < NY; iy += kColThreads) {
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      const float rhx = vox[4 * ny + iy], rhy = vox[5 * ny + iy];
-      const float* cc = coefT + (size_t)ix * ny + iy;
-      for (int rl = 0; rl < nr; ++rl) {
-        const int r = r0 + rl;
-        const float2 pv = hs[rl * ld + iy];
-        const float c = cc[(size_t)r * plane];
-        const float t1 = cc[(size_t)(R + r) * plane], t2 = cc[(size_t)(2 * R + r) * plane];
-        const float imcp = rhx * pv.y - rhy * pv.x;  // Im(conj(rho) P)
-        a0 = fmaf(t1, imcp, a0);
-        a1 = fmaf(t2, imcp, a1);
-        a2 = fmaf(c, pv.y, a2);
-        a3 = fmaf(-c, pv.x, a3);
+      const float rhx = vox[4 * NY + iy], rhy = vox[5 * NY + iy];
+      const float* cc = coefT + (size_t)ix * NY + iy;
+#pragma unroll
+      for (int rl = 0; rl < kColMaxRc; ++rl) {
+        if (rl < nr) {
+          const int r = r0 + rl;
+          const float2 pv = hs[rl * LD + iy];
+          const float c = cc[(size_t)r * plane];
+          const float t1 = cc[(size_t)(R + r) * plane], t2 = cc[(size_t)(2 * R + r) * plane];
+          const float imcp = rhx * pv.y - rhy * pv.x;  // Im(conj(rho) P)
+          a0 = fmaf(t1, imcp, a0);
+          a1 = fmaf(t2, imcp, a1);
+          a2 = fmaf(c, pv.y, a2);
+          a3 = fmaf(-c, pv.x, a3);
+        }
       }
       // the part for this block's half of the column stays here, the rest goes to the peer
       float* dst = (iy >= ya && iy < ye) ? red4 : red4_peer_in;
       dst[iy] = a0;
-      dst[ny + iy] = a1;
-      dst[2 * ny + iy] = a2;
-      dst[3 * ny + iy] = a3;
+      dst[NY + iy] = a1;
+      dst[2 * NY + iy] = a2;
+      dst[3 * NY + iy] = a3;
     }
     cl.sync();  // the peer's part of this block's half has arrived
     for (int iy = ya + tid; iy < ye; iy += kColThreads) {
@@ -782,7 +798,7 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
       const float m = maskf[j] * scale;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const float val = (red4[k * ny + iy] + rin[k * ny + iy]) * m;
+        const float val = (red4[k * NY + iy] + rin[k * NY + iy]) * m;
         g[(size_t)k * nv + j] = val;
         if (vdot != nullptr) {
           const float vk = v[(size_t)k * nv + j];
@@ -934,7 +950,7 @@ cudaError_t lowrank_project(const Plan& p, const LowRank& L, const float* alpha,
 
 void lowrank_free(LowRank* L) {
   if (L == nullptr) return;
-  void* ptrs[] = {L->U, L->Ug, L->UgT, L->kyof, L->Mky, L->kyptr, L->kytr, L->coef, L->coef2, L->gpart, L->coefT, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
+  void* ptrs[] = {L->U, L->Ug, L->UgT, L->UgS, L->kyof, L->Mky, L->kyptr, L->kytr, L->coef, L->coef2, L->gpart, L->coefT, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
                   L->a4_hi, L->a4_lo, L->by_hi, L->by_lo, L->bya_hi, L->bya_lo, L->X1, L->H, L->Y3, L->P};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -999,6 +1015,12 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
     for (int t = ptr[k]; t < ptr[k + 1]; ++t) kyof[t] = k;
   for (int k0 = 0; k0 < ny; k0 += 32) L->gram_rows_max = std::max(L->gram_rows_max, ptr[std::min(k0 + 32, ny)] - ptr[k0]);
   for (int k = 0; k < ny; ++k) L->ky_count_max = std::max(L->ky_count_max, ptr[k + 1] - ptr[k]);
+  // U by (r, slot, ky): the i-th TR of ky at [r][i][ky], zero past the ky's TRs
+  const int kmax = L->ky_count_max;
+  std::vector<float> UgS((size_t)R * kmax * ny, 0.f);
+  for (int k = 0; k < ny; ++k)
+    for (int t = ptr[k]; t < ptr[k + 1]; ++t)
+      for (int r = 0; r < R; ++r) UgS[((size_t)r * kmax + (t - ptr[k])) * ny + k] = Uh[(size_t)trs[t] * R + r];
   // the cancelled readout DFT pair needs nkx == nx; the Gram kernel keeps a ky tile's rows of U
   // in shared memory
   L->full_readout = p->nkx == p->nx && (size_t)L->gram_rows_max * (R + 1) * sizeof(float) <= (size_t)L->smem_optin;
@@ -1006,7 +1028,8 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   L->fft_y = L->full_readout && ny % 32 == 0 && ny / 32 <= 8;
   // one pair of blocks per image column: ceil(R / 2) x ny values and two copies of the ntr
   // TR-axis sums in each block's shared memory
-  L->column_path = L->fft_y && column_smem_bytes(ny, R, ntr) <= (size_t)L->smem_optin;
+  L->column_path =
+      L->fft_y && R <= 2 * kColMaxRc && column_smem_bytes(ny, R, L->ky_count_max) <= (size_t)L->smem_optin;
   if (L->fft_y) {
     const int n1 = ny / 32;
     for (int a = 0; a < 8; ++a)
@@ -1055,6 +1078,7 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   chk(cudaMalloc(&L->U, (size_t)ntr * R * sizeof(float)));
   chk(cudaMalloc(&L->Ug, (size_t)ntr * R * sizeof(float)));
   chk(cudaMalloc(&L->UgT, (size_t)ntr * R * sizeof(float)));
+  chk(cudaMalloc(&L->UgS, std::max<size_t>(UgS.size(), 1) * sizeof(float)));
   chk(cudaMalloc(&L->kyof, (size_t)ntr * sizeof(int)));
   chk(cudaMalloc(&L->Mky, M.size() * sizeof(float)));
   chk(cudaMalloc(&L->kyptr, ptr.size() * sizeof(int)));
@@ -1085,6 +1109,7 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   chk(cudaMemcpy(L->Mky, M.data(), M.size() * sizeof(float), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->Ug, Ug.data(), Ug.size() * sizeof(float), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->UgT, UgT.data(), UgT.size() * sizeof(float), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(L->UgS, UgS.data(), UgS.size() * sizeof(float), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->kyof, kyof.data(), kyof.size() * sizeof(int), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->kyptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->kytr, trs.data(), trs.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -1294,14 +1319,14 @@ template <int N1>
 static cudaError_t launch_column_t(Plan* p, const float* v, double* vdot, double* vv, float* out, cudaStream_t st) {
   LowRank& L = *p->lr;
   const int nx = p->nx, ny = p->ny, R = L.R;
-  const size_t sm = column_smem_bytes(ny, R, p->ntr);
+  const size_t sm = column_smem_bytes(ny, R, L.ky_count_max);
   cudaError_t e =
       cudaFuncSetAttribute(lr_jhjv_column_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   // two blocks per column (cluster pairs), one float64 partial per block
   const int grid = 2 * std::min(nx, kRedBlocks / 2);
   lr_jhjv_column_kernel<N1><<<grid, kColThreads, sm, st>>>(L.dft_small, v, L.coefT, p->rho, p->maskf, p->roots,
-                                                           L.UgT, L.kyptr, L.kyof, p->ntr, nx, ny, p->nv, R,
+                                                           L.UgS, L.ky_count_max, nx, ny, p->nv, R,
                                                            (float)nx, out, p->red, p->ticket, vdot, vv, p->gate);
   return cudaGetLastError();
 }

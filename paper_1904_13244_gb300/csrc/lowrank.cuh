@@ -22,6 +22,7 @@ struct LowRank {
   float* U = nullptr;              // [ntr][R] time basis
   float* Ug = nullptr;             // [ntr][R] rows of U in ky order (the order of kytr)
   float* UgT = nullptr;            // [R][ntr] the same, transposed
+  float* UgS = nullptr;            // [R][ky_count_max][ny]: the i-th TR of ky at [r][i][ky], else 0
   int* kyof = nullptr;             // [ntr] ky of each TR in that order
   int gram_rows_max = 0;           // most TRs of any 32 consecutive ky values
   int ky_count_max = 0;            // most TRs of any single ky value

@@ -227,6 +227,56 @@ __device__ __forceinline__ float tanh_fast(float x) {
 // straight to the next layer's input rows (or, for the last layer, the scaled outputs).
 // Every wait is bounded; a CTA that gives up sets err and drains its copies in flight.
 // ---------------------------------------------------------------------------
+// Layer 0 (three inputs: ln T1, ln T2, B1) on the CUDA cores, straight from the
+// parameters: the same BF16-rounded inputs and weights and float32 sums as a tensor-core
+// layer, then the hidden-layer epilogue, written as layer 1's BF16 input rows (value,
+// ln T1 tangent, ln T2 tangent).  Thread per (sample, 8 features): consecutive threads
+// take consecutive feature groups of one sample, so the 16-byte stores of a warp fill
+// whole rows; the block's copy of the weights and biases sits in shared memory as
+// [input][feature within group][group], which the lanes of a warp read without bank
+// conflicts.  N <= 256 features (groups <= 32), N a multiple of 8.
+constexpr int kFirstMaxGroups = 32;
+__global__ void __launch_bounds__(256)
+mlp_first_layer_kernel(const float* __restrict__ lnT, const float* __restrict__ b1, int B, float mu1, float s1,
+                       float mu2, float s2, float mu3, float s3, const __nv_bfloat16* __restrict__ W0, int ldw,
+                       const float* __restrict__ bias, int N, __nv_bfloat16* __restrict__ xn, int ldn) {
+  __shared__ float ws[4][8][kFirstMaxGroups];
+  const int groups = N / 8;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    const int g = n >> 3, j = n & 7;
+    ws[0][j][g] = __bfloat162float(W0[(size_t)n * ldw]);
+    ws[1][j][g] = __bfloat162float(W0[(size_t)n * ldw + 1]);
+    ws[2][j][g] = __bfloat162float(W0[(size_t)n * ldw + 2]);
+    ws[3][j][g] = bias[n];
+  }
+  __syncthreads();
+  const float d1 = __bfloat162float(__float2bfloat16_rn(1.f / s1));
+  const float d2 = __bfloat162float(__float2bfloat16_rn(1.f / s2));
+  const int total = B * groups;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int b = e / groups, g = e - b * groups;
+    const float bb = b1 != nullptr ? b1[b] : 1.f;
+    const float u0 = __bfloat162float(__float2bfloat16_rn((lnT[b] - mu1) / s1));
+    const float u1 = __bfloat162float(__float2bfloat16_rn((lnT[B + b] - mu2) / s2));
+    const float u2 = __bfloat162float(__float2bfloat16_rn((bb - mu3) / s3));
+    __align__(16) __nv_bfloat16 o0[8], o1[8], o2[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float w0 = ws[0][j][g], w1 = ws[1][j][g], w2 = ws[2][j][g];
+      const float z = fmaf(w2, u2, fmaf(w1, u1, w0 * u0));
+      const float a = tanh_fast(z + ws[3][j][g]);
+      const float dd = 1.f - a * a;
+      o0[j] = __float2bfloat16_rn(a);
+      o1[j] = __float2bfloat16_rn(dd * (w0 * d1));
+      o2[j] = __float2bfloat16_rn(dd * (w1 * d2));
+    }
+    const size_t row = (size_t)b * ldn + 8 * g, plane = (size_t)B * ldn;
+    *reinterpret_cast<uint4*>(xn + row) = *reinterpret_cast<const uint4*>(o0);
+    *reinterpret_cast<uint4*>(xn + plane + row) = *reinterpret_cast<const uint4*>(o1);
+    *reinterpret_cast<uint4*>(xn + 2 * plane + row) = *reinterpret_cast<const uint4*>(o2);
+  }
+}
+
 constexpr int kPerStages = 3;
 struct PerShape {
   static constexpr int BN = 64;
@@ -651,13 +701,17 @@ static cudaError_t launch_persistent(const TcOperand& x, const CUtensorMap& w64,
   return cudaGetLastError();
 }
 
-// Inference: the input kernel, then one persistent fused kernel per layer (no
-// pre-activation buffers).
+// Inference: layer 0 on the CUDA cores, then one persistent fused tensor-core kernel per
+// layer (no pre-activation buffers).
 int Mlp::infer_fused(const float* lnT, const float* b1, int B, float* pred, cudaStream_t st) {
-  mlp_input_kernel<<<blocks_for(B), 256, 0, st>>>(lnT, b1, B, norm[0], norm[1], norm[2], norm[3], norm[4], norm[5],
-                                                  X[0], nullptr, 0);
+  {
+    const int groups = out[0] / 8;  // hidden width 64, 128 or 256
+    mlp_first_layer_kernel<<<blocks_for((int64_t)B * groups), 256, 0, st>>>(
+        lnT, b1, B, norm[0], norm[1], norm[2], norm[3], norm[4], norm[5], Wb[0], pad8(in[0]),
+        theta + off[0] + (int64_t)out[0] * in[0], out[0], X[1], pad8(in[1]));
+  }
   cudaError_t e = cudaGetLastError();
-  for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+  for (int l = 1; l < 4 && e == cudaSuccess; ++l) {
     const float* bias = theta + off[l] + (int64_t)out[l] * in[l];
     const bool last = l == 3;
     __nv_bfloat16* xn = last ? nullptr : X[l + 1];

@@ -27,7 +27,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "Sequence", "Phantom", "flip_train", "cartesian_ky", "make_sequence",
+    "Sequence", "Phantom", "flip_train", "constant_flip_train", "sine_squared_train", "cartesian_ky",
+    "make_sequence",
     "quadrant_phantom", "ellipse_phantom", "brain_phantom", "smooth_field",
     "smooth_b1", "random_params", "random_kspace", "complex_noise", "add_noise",
     "CONFIGS", "config",
@@ -86,6 +87,32 @@ def flip_train(ntr: int, fills: float, seed: int = 0, max_deg: float = 60.0) -> 
     return np.deg2rad(max_deg) * (raw - lo) / (hi - lo)
 
 
+def constant_flip_train(ntr: int, ny: int, seed: int = 0, lo_deg: float = 10.0,
+                        hi_deg: float = 60.0) -> np.ndarray:
+    """One flip angle per k-space fill (TRs f*ny .. f*ny + ny - 1), different between fills
+    (the sequence of Supporting Information S3): alpha_f ~ U(lo_deg, hi_deg) degrees,
+    seeded; radians."""
+    if ntr <= 0:
+        return np.zeros(0)
+    nf = (ntr + ny - 1) // ny
+    a = np.random.default_rng(seed).uniform(lo_deg, hi_deg, nf)
+    return np.deg2rad(a[np.arange(ntr) // ny])
+
+
+def sine_squared_train(ntr: int, ny: int, seed: int = 0, max_deg: float = 60.0,
+                       lo_frac: float = 0.3) -> np.ndarray:
+    """Connected sine-squared waves, one per k-space fill, starting at zero, each peaking
+    where the fill samples the central line ky = 0 (Supporting Information S1):
+    alpha_n = A_f sin^2(pi (n mod ny) / ny) with peak A_f ~ U(lo_frac, 1) * max_deg, seeded;
+    radians."""
+    if ntr <= 0:
+        return np.zeros(0)
+    nf = (ntr + ny - 1) // ny
+    peak = np.random.default_rng(seed).uniform(lo_frac, 1.0, nf) * max_deg
+    n = np.arange(ntr)
+    return np.deg2rad(peak[n // ny] * np.sin(np.pi * (n % ny) / ny) ** 2)
+
+
 def cartesian_ky(ntr: int, ny: int) -> np.ndarray:
     """Linear Cartesian order: TR n samples ky = (n mod ny) - ny//2."""
     return (np.arange(ntr) % ny - ny // 2).astype(np.int32)
@@ -93,10 +120,20 @@ def cartesian_ky(ntr: int, ny: int) -> np.ndarray:
 
 def make_sequence(nx: int, ny: int, fills: int, tr_ms: float, te_ms: float, seed: int = 0,
                   nkx: int | None = None, extra_trs: int = 0, inversion: bool = True,
-                  alternate_phase: bool = True, max_deg: float = 60.0) -> Sequence:
+                  alternate_phase: bool = True, max_deg: float = 60.0, train: str = "smooth") -> Sequence:
+    """train: "smooth" (flip_train), "constant" (constant_flip_train) or "sine2"
+    (sine_squared_train)."""
     ntr = fills * ny + extra_trs
+    if train == "smooth":
+        flips = flip_train(ntr, fills + extra_trs / max(ny, 1), seed, max_deg)
+    elif train == "constant":
+        flips = constant_flip_train(ntr, ny, seed, hi_deg=max_deg)
+    elif train == "sine2":
+        flips = sine_squared_train(ntr, ny, seed, max_deg)
+    else:
+        raise ValueError(f"unknown flip train {train!r}")
     # flips are rounded to float32 so that a float32 consumer sees exactly these values
-    flips = flip_train(ntr, fills + extra_trs / max(ny, 1), seed, max_deg).astype(np.float32)
+    flips = flips.astype(np.float32)
     return Sequence(nx=nx, ny=ny, nkx=nx if nkx is None else nkx, tr_ms=tr_ms, te_ms=te_ms,
                     flip_rad=flips.astype(np.float64),
                     ky=cartesian_ky(ntr, ny), inversion=inversion,
@@ -213,7 +250,7 @@ BRAIN_T2 = np.array([70.0, 90.0, 2000.0, 80.0])
 BRAIN_PD = np.array([0.65, 0.80, 1.00, 0.90])
 
 
-def _brain_labels(n: int) -> np.ndarray:
+def _brain_labels(n: int, ny: int | None = None) -> np.ndarray:
     ell = [
         (0.0, 0.0, 0.760, 0.840, 0.0, 3),   # fat (scalp) ring: outer boundary
         (0.0, 0.0, 0.700, 0.780, 0.0, 1),   # cortex (GM)
@@ -230,28 +267,30 @@ def _brain_labels(n: int) -> np.ndarray:
         r = 0.64
         ell.append((r * np.cos(t) * 0.76 / 0.76, r * np.sin(t) * 0.84 / 0.76 * 0.9,
                     0.085, 0.018, np.rad2deg(t), 2))
-    return _paint(n, n, ell)
+    return _paint(n, n if ny is None else ny, ell)
 
 
-def brain_phantom(n: int = 224, seed: int = 0, b1_map: bool = False) -> Phantom:
+def brain_phantom(n: int = 224, seed: int = 0, b1_map: bool = False, ny: int | None = None) -> Phantom:
     """Brain-like phantom: fat ring, GM cortex, WM core, deep GM, CSF ventricles/sulci.
 
     T1 = 800/1300/4000/350 ms and T2 = 70/90/2000/80 ms for WM/GM/CSF/fat, each
     multiplied by (1 + 0.1 g) with g a smooth unit-std Gaussian field (independent
     for T1 and T2); |rho| = 0.65/0.8/1.0/0.9 with a smooth polynomial phase; about
     half of the FOV lies inside the head.  With ``b1_map`` the relative transmit
-    field is 1 + 0.2 * smooth field, clipped to [0.8, 1.2]; else B1 = 1.
+    field is 1 + 0.2 * smooth field, clipped to [0.8, 1.2]; else B1 = 1.  With ``ny`` the
+    grid is n (x) by ny (y) and the head an ellipse filling that field of view.
     """
     rng = np.random.default_rng(seed)
-    lab = _brain_labels(n)
+    nx, ny = n, (n if ny is None else ny)
+    lab = _brain_labels(nx, ny)
     inside = lab >= 0
     li = np.where(inside, lab, 0)
-    g1 = smooth_field(n, n, seed + 101, n / 32)
-    g2 = smooth_field(n, n, seed + 202, n / 32)
+    g1 = smooth_field(nx, ny, seed + 101, nx / 32)
+    g2 = smooth_field(nx, ny, seed + 202, nx / 32)
     t1 = np.where(inside, BRAIN_T1[li] * (1 + 0.1 * g1), 1000.0)
     t2 = np.where(inside, BRAIN_T2[li] * (1 + 0.1 * g2), 100.0)
-    rho = np.where(inside, BRAIN_PD[li], 0.0) * np.exp(1j * _poly_phase(n, n, rng))
-    b1 = smooth_b1(n, n, seed + 303) if b1_map else np.ones((n, n))
+    rho = np.where(inside, BRAIN_PD[li], 0.0) * np.exp(1j * _poly_phase(nx, ny, rng))
+    b1 = smooth_b1(nx, ny, seed + 303) if b1_map else np.ones((ny, nx))
     return Phantom(t1_ms=t1, t2_ms=t2, rho=rho, b1=b1, support=inside, labels=lab)
 
 
@@ -293,6 +332,11 @@ CONFIGS = {
     "ellipse64": dict(n=64, fills=5, tr=7.8, te=3.9, phantom="ellipse"),
     "brain224": dict(n=224, fills=5, tr=7.6, te=3.8, phantom="brain"),
     "brain256": dict(n=256, fills=5, tr=7.6, te=3.8, phantom="brain"),
+    # the in-vivo shape: 224 x 224 with 8 fills (1792 TRs), sine-squared train (S1)
+    "brain224_1792": dict(n=224, fills=8, tr=7.6, te=3.8, phantom="brain", train="sine2"),
+    # Supporting Information S3: 1.8 mm over 201.5 x 158 mm (112 x 88), TR 5.6 ms, TE 2.8 ms,
+    # 16 k-spaces with a constant flip angle each (1408 TRs, 7.9 s)
+    "const112x88": dict(n=112, ny=88, fills=16, tr=5.6, te=2.8, phantom="brain", train="constant"),
 }
 
 
@@ -300,11 +344,12 @@ def config(name: str, seed: int = 0, b1_map: bool = False):
     """Return (Sequence, Phantom) of a named workload."""
     c = CONFIGS[name]
     n = c["n"]
-    seq = make_sequence(n, n, c["fills"], c["tr"], c["te"], seed=seed)
+    ny = c.get("ny", n)
+    seq = make_sequence(n, ny, c["fills"], c["tr"], c["te"], seed=seed, train=c.get("train", "smooth"))
     if c["phantom"] == "quadrant":
         ph = quadrant_phantom(n, seed)
     elif c["phantom"] == "ellipse":
         ph = ellipse_phantom(n, seed)
     else:
-        ph = brain_phantom(n, seed, b1_map=b1_map)
+        ph = brain_phantom(n, seed, b1_map=b1_map, ny=ny)
     return seq, ph

@@ -57,6 +57,10 @@ CASES = {
     "single_voxel_single_tr": (1, 1, 1, 0, 1, {}),
     "no_inversion_const_phase": (24, 16, 3, 1, 24, {"inversion": False, "alternate_phase": False}),
     "ellipse64": (64, 64, 5, 0, 64, {}),
+    # the flip trains of the supporting information: constant per k-space fill (S3) and
+    # connected sine-squared waves peaking at the central line (S1)
+    "constant_flip_12x16": (12, 16, 4, 0, 12, {"train": "constant"}),
+    "sine2_ragged_20x12": (20, 12, 3, 5, 24, {"train": "sine2"}),
 }
 
 
