@@ -29,7 +29,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import bloch, encoding
+from . import bloch, encoding, slice_profile
 
 
 @dataclass
@@ -52,8 +52,9 @@ class Linearization:
         return self.alpha.shape[0]
 
 
-def linearize(seq, alpha, b1=None, mask=None) -> Linearization:
-    """Simulate m and its tangents at alpha (Algorithm 2 step 1 plus S2 derivatives)."""
+def linearize(seq, alpha, b1=None, mask=None, profile=None) -> Linearization:
+    """Simulate m and its tangents at alpha (Algorithm 2 step 1 plus S2 derivatives);
+    with a slice profile (oracle.slice_profile.SliceProfile) the slice-averaged model."""
     alpha = np.asarray(alpha, np.float64)
     nv = alpha.shape[1]
     estimate_b1 = alpha.shape[0] == 5
@@ -62,8 +63,13 @@ def linearize(seq, alpha, b1=None, mask=None) -> Linearization:
     elif b1 is None:
         b1 = np.ones(nv)
     mask = np.ones(nv, bool) if mask is None else np.asarray(mask, bool)
-    sim = bloch.simulate(seq, np.exp(alpha[0]), np.exp(alpha[1]), b1, tangents=True,
-                         b1_tangent=estimate_b1)
+    if profile is not None:
+        if estimate_b1:
+            raise ValueError("the slice-profile model has no B1 tangent")
+        sim = slice_profile.simulate(seq, np.exp(alpha[0]), np.exp(alpha[1]), profile, b1)
+    else:
+        sim = bloch.simulate(seq, np.exp(alpha[0]), np.exp(alpha[1]), b1, tangents=True,
+                             b1_tangent=estimate_b1)
     return Linearization(seq, alpha, np.asarray(b1, np.float64), mask, sim["m"],
                          sim["dm_dlnT1"], sim["dm_dlnT2"], sim.get("dm_dB1"))
 
@@ -74,8 +80,8 @@ def signal(lin: Linearization) -> np.ndarray:
     return encoding.encode(lin.seq, q)
 
 
-def forward(seq, alpha, b1=None, mask=None) -> np.ndarray:
-    return signal(linearize(seq, alpha, b1, mask))
+def forward(seq, alpha, b1=None, mask=None, profile=None) -> np.ndarray:
+    return signal(linearize(seq, alpha, b1, mask, profile))
 
 
 def objective(d, s) -> float:
