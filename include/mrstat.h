@@ -340,6 +340,34 @@ int mrstat_dot(mrstat_plan* plan, const float* a, const float* b, int64_t n,
 int mrstat_dot_static(const float* a, const float* b, int64_t n, double* out, void* stream);
 
 /*
+ * Slice profile (Methods, "Pulse Sequence": every RF pulse has a Gaussian envelope;
+ * "Reconstructions": the Bloch solver takes the slice profile into account).  With a
+ * profile set, mrstat_linearize / mrstat_forward (and the Gauss-Newton solver) simulate
+ * every voxel as n_iso isochromats across the slice, at u_k = extent ((k + 1/2)/n_iso
+ * - 1/2) slice thicknesses; each RF pulse is n_sub hard sub-pulses with Gaussian weights
+ * exp(-((s + 1/2)/n_sub - 1/2)^2 / (2 sigma^2)) (normalised to sum 1, so the slice centre
+ * turns by the nominal flip), sub-step s followed by a slice-select precession of
+ * 2 pi tbw u_k / n_sub, with a pre-winder and a rewinder of half the pulse's gradient
+ * area each (a balanced sequence); relaxation as in the hard-pulse model; the echo is
+ * the mean over the isochromats.  The paper gives no pulse parameters: these are the
+ * build's readings.  profile = NULL restores hard pulses.  Either way the cached
+ * linearisation is dropped.
+ *   n_iso: a power of two in 1..32; n_sub: 1..64; sigma > 0; extent > 0.
+ * The slice-profile model takes B1 = 1: a b1 map, B1 estimation, the low-rank and
+ * surrogate forms and the checkpointed form are UNSUPPORTED with it.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA.
+ */
+typedef struct mrstat_slice_profile {
+  int32_t n_iso;   /* isochromats across the slice */
+  int32_t n_sub;   /* RF sub-steps */
+  double sigma;    /* Gaussian width, fraction of the pulse */
+  double tbw;      /* time-bandwidth product */
+  double extent;   /* the isochromats span this many slice thicknesses */
+} mrstat_slice_profile;
+
+int mrstat_set_slice_profile(mrstat_plan* plan, const mrstat_slice_profile* profile);
+
+/*
  * Fixed-count conjugate gradients on Re(J_s^H J_s) x = rhs at the cached
  * linearisation (the inner CG of Algorithm 6 without trust-region exits): x_0 = 0,
  * then exactly `iters` iterations, each one J^H J v product plus float64 inner products;

@@ -196,17 +196,18 @@ def apply_bounds(alpha, opts: GNOptions):
     return a
 
 
-def gauss_newton(seq, d, alpha0, b1=None, mask=None, opts: GNOptions | None = None):
+def gauss_newton(seq, d, alpha0, b1=None, mask=None, opts: GNOptions | None = None, profile=None):
     """Algorithm 6: outer GN iterations, each with one truncated-CG inner solve.
 
-    Returns (alpha, report).  Parameters outside the mask stay at alpha0.
+    Returns (alpha, report).  Parameters outside the mask stay at alpha0.  With a slice
+    profile (oracle.slice_profile.SliceProfile) the model is the slice-averaged one.
     """
     opts = opts or GNOptions()
     alpha = np.array(alpha0, np.float64)
     nv = alpha.shape[1]
     mask = np.ones(nv, bool) if mask is None else np.asarray(mask, bool)
     mflt = mask[None, :].astype(np.float64)
-    lin = model.linearize(seq, alpha, b1, mask)
+    lin = model.linearize(seq, alpha, b1, mask, profile)
     s = model.signal(lin)
     f = model.objective(d, s)
     delta = opts.delta0 if opts.delta0 > 0 else 0.1 * np.linalg.norm(alpha * mflt)
@@ -225,7 +226,7 @@ def gauss_newton(seq, d, alpha0, b1=None, mask=None, opts: GNOptions | None = No
         rep.exit.append(why)
         trial = apply_bounds(alpha + p, opts)
         trial = np.where(mask[None, :], trial, alpha)
-        lin_t = model.linearize(seq, trial, b1, mask)
+        lin_t = model.linearize(seq, trial, b1, mask, profile)
         s_t = model.signal(lin_t)
         f_t = model.objective(d, s_t)
         pred = -mchange

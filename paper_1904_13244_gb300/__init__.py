@@ -26,7 +26,7 @@ from ._binding import (MrstatError, MRSTAT_FORM_PLAIN_FP32, MRSTAT_FORM_SPLIT_BF
                        mrstat_lowrank_coefficients, mrstat_lowrank_rank, mrstat_lowrank_project_samples,
                        mrstat_mlp_create, mrstat_mlp_destroy, mrstat_mlp_num_params, mrstat_mlp_set_output_scale,
                        mrstat_mlp_get_params, mrstat_mlp_set_params, mrstat_mlp_train_step, mrstat_mlp_loss_grad,
-                       mrstat_mlp_infer)
+                       mrstat_mlp_infer, mrstat_set_slice_profile)
 
 __all__ = ["Plan", "Surrogate", "MrstatError", "load", "Signal", "signal"]
 
@@ -169,6 +169,11 @@ class Plan:
 
     def profile_stop(self) -> dict:
         return mrstat_profile_stop(self._h)
+
+    def set_slice_profile(self, n_iso=None, n_sub=16, sigma=0.2, tbw=4.0, extent=2.0):
+        """Slice-profile Bloch model (n_iso isochromats, n_sub Gaussian RF sub-steps);
+        n_iso=None restores hard pulses.  Drops the cached linearisation."""
+        mrstat_set_slice_profile(self._h, n_iso, n_sub, sigma, tbw, extent)
 
     def cg_fixed(self, rhs, iters: int, out=None, stream=None):
         out = self._params(out)

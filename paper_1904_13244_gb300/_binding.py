@@ -61,6 +61,11 @@ class mrstat_gn_opts(ctypes.Structure):
                 ("rho_init_exact", ctypes.c_int32)]
 
 
+class mrstat_slice_profile(ctypes.Structure):
+    _fields_ = [("n_iso", ctypes.c_int32), ("n_sub", ctypes.c_int32), ("sigma", ctypes.c_double),
+                ("tbw", ctypes.c_double), ("extent", ctypes.c_double)]
+
+
 class mrstat_gn_report(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("mask_voxels", ctypes.c_int32),
                 ("cg_steps", ctypes.c_int32 * GN_MAX_OUTER), ("cg_exit", ctypes.c_int32 * GN_MAX_OUTER),
@@ -84,6 +89,7 @@ _SIGS = {
     "mrstat_plan_destroy": [ctypes.c_void_p],
     "mrstat_plan_info": [ctypes.c_void_p, ctypes.POINTER(mrstat_plan_info_t)],
     "mrstat_plan_check": [ctypes.c_void_p],
+    "mrstat_set_slice_profile": [ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_linearize": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_forward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                        ctypes.c_void_p],
@@ -347,6 +353,15 @@ def mrstat_cg_fixed(plan, rhs, x, iters, stream=None):
     _check(load().mrstat_cg_fixed(plan, _ptr(rhs, torch.float32, (npar, nv), "rhs"),
                                   _ptr(x, torch.float32, (npar, nv), "x"), int(iters), _stream(stream)),
            "mrstat_cg_fixed")
+
+
+def mrstat_set_slice_profile(plan, n_iso=None, n_sub=16, sigma=0.2, tbw=4.0, extent=2.0):
+    """n_iso = None: hard pulses; else the slice-profile model with these pulse readings."""
+    if n_iso is None:
+        _check(load().mrstat_set_slice_profile(plan, None), "mrstat_set_slice_profile")
+        return
+    prof = mrstat_slice_profile(int(n_iso), int(n_sub), float(sigma), float(tbw), float(extent))
+    _check(load().mrstat_set_slice_profile(plan, ctypes.byref(prof)), "mrstat_set_slice_profile")
 
 
 def mrstat_gn_default_opts(**overrides) -> mrstat_gn_opts:

@@ -35,6 +35,10 @@ struct Plan {
   // per-TR tables (device)
   float2* cs = nullptr;     // [ntr_pad] (cos phi_n, sin phi_n), phi_n the signed flip
   float* phi = nullptr;     // [ntr_pad] signed flip (radians)
+  // slice profile (mrstat_set_slice_profile): 0 isochromats = hard pulses
+  int slice_iso = 0, slice_sub = 0;
+  float* slice_w = nullptr;      // [64] sub-pulse weights
+  float2* slice_prec = nullptr;  // [64] (cos, sin) of beta_k at [k] and of -n_sub/2 beta_k at [32 + k]
   int* kyi = nullptr;       // [ntr_pad] ky mod ny in [0, ny)
   int* ky_ptr = nullptr;    // [ny + 1] TRs of each ky (CSR over ky_tr)
   int* ky_tr = nullptr;     // [ntr] TR indices grouped by ky, ascending within a ky
@@ -199,6 +203,8 @@ cudaError_t ensure_forward_scratch(Plan* p);
 // bloch.cu
 cudaError_t launch_bloch(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,
                          float4* D, int nch, cudaStream_t st);
+// slice.cu: the slice-profile recursion (three channels, B1 = 1)
+cudaError_t launch_bloch_slice(const Plan& p, const float* alpha, const uint8_t* mask, float4* D, cudaStream_t st);
 // the same recursion for nv_override voxels laid out [2][nv_override] (ln T1, ln T2)
 cudaError_t launch_bloch_n(const Plan& p, const float* alpha, const float* b1, float4* D, int nv_override,
                            cudaStream_t st);

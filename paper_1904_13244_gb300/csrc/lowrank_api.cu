@@ -77,6 +77,7 @@ int mrstat_lowrank_set_basis(mrstat_plan* plan_, const float* U, int32_t rank, v
   Plan* p = reinterpret_cast<Plan*>(plan_);
   if (p == nullptr || U == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or basis");
   if (p->npar != 4) return fail(MRSTAT_ERR_UNSUPPORTED, "the low-rank form does not estimate B1");
+  if (p->slice_iso > 0) return fail(MRSTAT_ERR_UNSUPPORTED, "the low-rank forms use the hard-pulse model");
   DeviceGuard g(p->device);
   return lowrank_setup(p, U, rank, as_stream(stream));
 }
@@ -85,6 +86,7 @@ int mrstat_lowrank_linearize(mrstat_plan* plan_, const float* alpha, const float
                              const float* coef, void* stream) {
   Plan* p = reinterpret_cast<Plan*>(plan_);
   if (p == nullptr || alpha == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or alpha");
+  if (p->slice_iso > 0) return fail(MRSTAT_ERR_UNSUPPORTED, "the low-rank forms use the hard-pulse model");
   if (p->lr == nullptr) return fail(MRSTAT_ERR_NOT_LINEARIZED, "no time basis: call mrstat_lowrank_set_basis");
   DeviceGuard g(p->device);
   cudaStream_t st = as_stream(stream);
@@ -126,6 +128,7 @@ int mrstat_lowrank_project_samples(mrstat_plan* plan_, const float* params, cons
   Plan* p = reinterpret_cast<Plan*>(plan_);
   if (p == nullptr || params == nullptr || coef == nullptr || ns < 1)
     return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_lowrank_project_samples");
+  if (p->slice_iso > 0) return fail(MRSTAT_ERR_UNSUPPORTED, "the low-rank forms use the hard-pulse model");
   if (p->lr == nullptr) return fail(MRSTAT_ERR_NOT_LINEARIZED, "no time basis: call mrstat_lowrank_set_basis");
   DeviceGuard g(p->device);
   Plan q;  // the plan's sequence tables with ns voxels
@@ -156,6 +159,8 @@ int mrstat_lowrank_basis(mrstat_plan* plan_, const float* train, const float* tr
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, training set or output");
   if (ns < 1 || rank < 1 || rank > kMaxRank || rank > p->ntr)
     return fail(MRSTAT_ERR_INVALID_ARG, "bad training size %d or rank %d", ns, rank);
+  if (p->slice_iso > 0) return fail(MRSTAT_ERR_UNSUPPORTED, "the low-rank forms use the hard-pulse model");
+
   DeviceGuard g(p->device);
   cudaStream_t st = as_stream(stream);
   const int ntr = p->ntr, nq = p->nq;

@@ -39,7 +39,7 @@ namespace {
 
 void free_plan(Plan* p) {
   if (p == nullptr) return;
-  void* ptrs[] = {p->cs, p->phi, p->kyi, p->ky_ptr, p->ky_tr, p->roots, p->ft, p->fh, p->D, p->rho, p->maskf,
+  void* ptrs[] = {p->slice_w, p->slice_prec, p->cs, p->phi, p->kyi, p->ky_ptr, p->ky_tr, p->roots, p->ft, p->fh, p->D, p->rho, p->maskf,
                   p->dfwd, p->cf, p->A, p->wt, p->red, p->ticket, p->cg_r, p->cg_p, p->cg_q, p->cg_w,
                   p->cg_jv, p->cg_s, p->cg_frozen, p->D2, p->rho2, p->gn_g, p->gn_z, p->gn_res,
                   p->gn_dir, p->gn_q, p->gn_alpha, p->gn_trial, p->gn_s, p->gn_r, p->gn_st,
@@ -242,9 +242,11 @@ int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* ma
     e = launch_prep_linearize(*p, alpha, mask, rho, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "prep_linearize launch");
+  if (p->slice_iso > 0 && b1 != nullptr)
+    return fail(MRSTAT_ERR_UNSUPPORTED, "the slice-profile model takes B1 = 1 (no map)");
   {
     Span sp(p, MRSTAT_K_BLOCH, st);
-    e = launch_bloch(*p, alpha, b1, mask, D, p->nch, st);
+    e = p->slice_iso > 0 ? launch_bloch_slice(*p, alpha, mask, D, st) : launch_bloch(*p, alpha, b1, mask, D, p->nch, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "bloch launch");
   return MRSTAT_OK;
@@ -619,6 +621,7 @@ int mrstat_forward_ckpt(mrstat_plan* plan, const float* alpha, const float* b1, 
   if (interval < 4 || interval % 4 != 0)
     return fail(MRSTAT_ERR_INVALID_ARG, "checkpoint interval %d is not a positive multiple of 4", interval);
   if (plan->npar != 4) return fail(MRSTAT_ERR_UNSUPPORTED, "the checkpointed form does not estimate B1");
+  if (plan->slice_iso > 0) return fail(MRSTAT_ERR_UNSUPPORTED, "the checkpointed form uses the hard-pulse model");
   DeviceGuard g(plan->device);
   cudaStream_t st = as_stream(stream);
   cudaError_t e = ensure_forward_scratch(plan);
