@@ -62,9 +62,12 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM traffic per launch from one ncu capture, keyed by the SHA-256 prefix of the
 # kernel's source file at capture time; reported only while the source is unchanged.
 NCU_TRAFFIC = {
-    # profiles/tc_gemm_persistent_brain224.md (dram__bytes_read.sum + dram__bytes_write.sum)
+    # (kernel class, source hash): dram__bytes_read.sum + dram__bytes_write.sum per launch
+    # profiles/tc_gemm_persistent_brain224.md
     ("xdft", "0728f575d9d96a3d"): 13670656.0,
     ("xdft_adj", "0728f575d9d96a3d"): 13668608.0,
+    # profiles/lr_jhjv_column_kernel_brain224.md (warm L2, as in the CG loop)
+    ("jhw_dot", "f1f10e7119e1e2c3"): 4608.0,
 }
 
 

@@ -203,8 +203,9 @@ cudaError_t ensure_forward_scratch(Plan* p);
 // bloch.cu
 cudaError_t launch_bloch(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,
                          float4* D, int nch, cudaStream_t st);
-// slice.cu: the slice-profile recursion (three channels, B1 = 1)
-cudaError_t launch_bloch_slice(const Plan& p, const float* alpha, const uint8_t* mask, float4* D, cudaStream_t st);
+// slice.cu: the slice-profile recursion (B1 = 1; nch 1: m only, 3: m and the two tangents)
+cudaError_t launch_bloch_slice(const Plan& p, const float* alpha, const uint8_t* mask, float4* D, int nch,
+                               cudaStream_t st);
 // the same recursion for nv_override voxels laid out [2][nv_override] (ln T1, ln T2)
 cudaError_t launch_bloch_n(const Plan& p, const float* alpha, const float* b1, float4* D, int nv_override,
                            cudaStream_t st);

@@ -725,12 +725,8 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
       sin_peer[e] = part;  // the peer's copy of this block's part
     }
     cl.sync();  // both parts of every s are in both blocks
-    for (int e = tid; e < kmax * NY; e += kColThreads) {
-      const float2 a = sbuf[e], b = sin[e];
-      sbuf[e] = make_float2(a.x + b.x, a.y + b.y);  // commutative: the same s in both blocks
-    }
-    __syncthreads();
-    //    2b. warp per r, lane per ky: G_r(ky) = sum_i U[i-th TR of ky][r] s[i][ky]
+    //    2b. warp per r, lane per ky: G_r(ky) = sum_i U[i-th TR of ky][r] s[i][ky], with s the
+    //        sum of the two parts (commutative: the same s in both blocks)
     for (int rl = warp; rl < nr; rl += kColWarps) {
       const float* ur = UgS + (size_t)(r0 + rl) * kmax * NY;
 #pragma unroll
@@ -739,14 +735,15 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
 #pragma unroll 4
         for (int i = 0; i < kmax; ++i) {
           const float u = __ldg(ur + (size_t)i * NY + ky);
-          const float2 sv = sbuf[i * NY + ky];
+          const float2 sa = sbuf[i * NY + ky], sb = sin[i * NY + ky];
+          const float2 sv = make_float2(sa.x + sb.x, sa.y + sb.y);
           o.x = fmaf(u, sv.x, o.x);
           o.y = fmaf(u, sv.y, o.y);
         }
         hs[rl * LD + ky] = o;
       }
     }
-    __syncthreads();
+    __syncwarp();  // the adjoint below reads only the rows this warp has just written
     // 3. adjoint phase-encode DFT
     for (int rl = warp; rl < nr; rl += kColWarps) {
       float2* x = hs + rl * LD;

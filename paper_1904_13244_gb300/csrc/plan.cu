@@ -246,7 +246,8 @@ int do_linearize(Plan* p, const float* alpha, const float* b1, const uint8_t* ma
     return fail(MRSTAT_ERR_UNSUPPORTED, "the slice-profile model takes B1 = 1 (no map)");
   {
     Span sp(p, MRSTAT_K_BLOCH, st);
-    e = p->slice_iso > 0 ? launch_bloch_slice(*p, alpha, mask, D, st) : launch_bloch(*p, alpha, b1, mask, D, p->nch, st);
+    e = p->slice_iso > 0 ? launch_bloch_slice(*p, alpha, mask, D, 3, st)
+                         : launch_bloch(*p, alpha, b1, mask, D, p->nch, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "bloch launch");
   return MRSTAT_OK;
@@ -553,13 +554,16 @@ int mrstat_forward(mrstat_plan* plan, const float* alpha, const float* b1, const
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, alpha or s");
   if (plan->npar == 5 && b1 != nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "B1 is estimated (alpha row 4): pass b1 = NULL");
+  if (plan->slice_iso > 0 && b1 != nullptr)
+    return fail(MRSTAT_ERR_UNSUPPORTED, "the slice-profile model takes B1 = 1 (no map)");
   DeviceGuard g(plan->device);
   cudaStream_t st = as_stream(stream);
   cudaError_t e = ensure_forward_scratch(plan);
   if (e != cudaSuccess) return cuda_fail(e, "forward scratch allocation");
   {
     Span sp(plan, MRSTAT_K_BLOCH, st);
-    e = launch_bloch(*plan, alpha, b1, mask, plan->dfwd, 1, st);
+    e = plan->slice_iso > 0 ? launch_bloch_slice(*plan, alpha, mask, plan->dfwd, 1, st)
+                            : launch_bloch(*plan, alpha, b1, mask, plan->dfwd, 1, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "bloch launch");
   {

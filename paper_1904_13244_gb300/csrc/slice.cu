@@ -29,7 +29,7 @@ constexpr int kSliceMaxSub = 64;
 __global__ void __launch_bounds__(kSliceThreads)
 bloch_slice_kernel(const float* __restrict__ alpha, const uint8_t* __restrict__ mask,
                    const float* __restrict__ phi, const float* __restrict__ wsub, const float2* __restrict__ prec,
-                   int n_iso, int log2_iso, int n_sub, int nv, int nq, float te, float tb, float m0z,
+                   int n_iso, int log2_iso, int n_sub, int nv, int nq, float te, float tb, float m0z, int nch,
                    float4* __restrict__ D) {
   __shared__ float rot[kSliceChunk * 32 * 9];        // [TR in chunk][isochromat][3 x 3, column-major]
   __shared__ float2 cs[kSliceChunk * kSliceMaxSub];  // cos / sin of each sub-step's angle
@@ -153,8 +153,10 @@ bloch_slice_kernel(const float* __restrict__ alpha, const uint8_t* __restrict__ 
         const size_t q = (size_t)((n0 + nq4) >> 2) * nv + j;
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         __stcs(D + q, on ? make_float4(o0[0], o0[1], o0[2], o0[3]) : z4);
-        __stcs(D + cstride + q, on ? make_float4(o1[0], o1[1], o1[2], o1[3]) : z4);
-        __stcs(D + 2 * cstride + q, on ? make_float4(o2[0], o2[1], o2[2], o2[3]) : z4);
+        if (nch > 1) {  // the tangent channels (absent from the forward-only buffer)
+          __stcs(D + cstride + q, on ? make_float4(o1[0], o1[1], o1[2], o1[3]) : z4);
+          __stcs(D + 2 * cstride + q, on ? make_float4(o2[0], o2[1], o2[2], o2[3]) : z4);
+        }
       }
     }
   }
@@ -162,7 +164,7 @@ bloch_slice_kernel(const float* __restrict__ alpha, const uint8_t* __restrict__ 
 
 }  // namespace
 
-cudaError_t launch_bloch_slice(const Plan& p, const float* alpha, const uint8_t* mask, float4* D,
+cudaError_t launch_bloch_slice(const Plan& p, const float* alpha, const uint8_t* mask, float4* D, int nch,
                                cudaStream_t st) {
   if (p.nv == 0) return cudaSuccess;
   const int vpb = (kSliceThreads / 32) * (32 / p.slice_iso);  // voxels per block
@@ -172,7 +174,7 @@ cudaError_t launch_bloch_slice(const Plan& p, const float* alpha, const uint8_t*
   while ((1 << log2_iso) < p.slice_iso) ++log2_iso;
   bloch_slice_kernel<<<blocks, kSliceThreads, 0, st>>>(alpha, mask, p.phi, p.slice_w, p.slice_prec, p.slice_iso,
                                                       log2_iso, p.slice_sub, p.nv, p.nq, te, tb,
-                                                      p.inversion ? -1.f : 1.f, D);
+                                                      p.inversion ? -1.f : 1.f, nch, D);
   return cudaGetLastError();
 }
 
