@@ -624,9 +624,7 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
                       int kmax, int nx, int ny, int nv, int R, float scale,
                       float* __restrict__ g, double* red_part, unsigned* ticket, double* __restrict__ vdot,
                       double* __restrict__ vv, const int* __restrict__ gate) {
-  // the gate is written by earlier launches only: both blocks of a cluster take the same
-  // branch, so every cluster barrier below is reached by both
-  if (gate != nullptr && *gate == 0) return;
+  red::pdl_trigger();  // the successor may stage its own set-up meanwhile
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
   const int crank = (int)cl.block_rank(), peer = crank ^ 1;
@@ -646,9 +644,13 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
   const int brev = (int)(__brev((unsigned)lane) >> 27);
   const size_t plane = (size_t)nx * NY;
   const int hy = (NY + 1) / 2, ya = crank * hy, ye = min(NY, ya + hy);  // this block's half of iy
-  for (int e = tid; e < NY; e += kColThreads) rt[e] = roots[e];
+  for (int e = tid; e < NY; e += kColThreads) rt[e] = roots[e];  // plan constants: before the wait
   cl.sync();  // both blocks are running before either stores into the other's shared memory
   const Fft32Lane ffw = fft32_lane<false>(rt, N1, lane), ffa = fft32_lane<true>(rt, N1, lane);
+  red::pdl_wait();  // v, rho, the coefficients and the gate come from earlier launches
+  // the gate is written by earlier launches only: both blocks of a cluster take the same
+  // branch, so every cluster barrier below is reached by both
+  if (gate != nullptr && *gate == 0) return;
   float sf = 0.f, sv = 0.f;
   for (int ix = blockIdx.x >> 1; ix < nx; ix += gridDim.x >> 1) {
     // 0. the column's voxel data (each block loads all of it)
@@ -1322,10 +1324,22 @@ static cudaError_t launch_column_t(Plan* p, const float* v, double* vdot, double
   if (e != cudaSuccess) return e;
   // two blocks per column (cluster pairs), one float64 partial per block
   const int grid = 2 * std::min(nx, kRedBlocks / 2);
-  lr_jhjv_column_kernel<N1><<<grid, kColThreads, sm, st>>>(L.dft_small, v, L.coefT, p->rho, p->maskf, p->roots,
-                                                           L.UgS, L.ky_count_max, nx, ny, p->nv, R,
-                                                           (float)nx, out, p->red, p->ticket, vdot, vv, p->gate);
-  return cudaGetLastError();
+  // programmatic dependent launch: the set-up above the kernel's pdl_wait overlaps the
+  // tail of the previous launch in the stream
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kColThreads);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, lr_jhjv_column_kernel<N1>, L.dft_small, v, (const float*)L.coefT,
+                            (const float2*)p->rho, (const float*)p->maskf, (const float2*)p->roots,
+                            (const float*)L.UgS, L.ky_count_max, nx, ny, p->nv, R, (float)nx, out, p->red,
+                            p->ticket, vdot, vv, (const int*)p->gate);
 }
 
 static cudaError_t launch_column(Plan* p, const float* v, double* vdot, double* vv, float* out, cudaStream_t st) {

@@ -74,6 +74,8 @@ __global__ void __launch_bounds__(kT)
 cg_cg_step_kernel(float* __restrict__ x, float* __restrict__ r, float* __restrict__ p, float* __restrict__ q,
                   const float* __restrict__ w, int64_t n, int64_t n4, double* __restrict__ sk,
                   const double* __restrict__ sp, int* __restrict__ frozen) {
+  pdl_trigger();
+  pdl_wait();  // w and the inner products come from the product launch
   const int64_t t0 = blockIdx.x * (int64_t)kT + threadIdx.x, stride = (int64_t)gridDim.x * kT;
   float4 xv, rv, pv, qv, wv;
   if (t0 < n4) {
@@ -156,8 +158,16 @@ cudaError_t launch_cg_init(const float* rhs, float* x, float* r, float* p, float
 cudaError_t launch_cg_cg_step(float* x, float* r, float* p, float* q, const float* w, int64_t n, double* sk,
                               const double* sp, int* frozen, cudaStream_t st) {
   const int64_t n4 = aligned16(x) && aligned16(r) && aligned16(p) && aligned16(q) && aligned16(w) ? n / 4 : 0;
-  cg_cg_step_kernel<<<grid_for(n), kT, 0, st>>>(x, r, p, q, w, n, n4, sk, sp, frozen);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid_for(n));
+  cfg.blockDim = dim3(kT);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, cg_cg_step_kernel, x, r, p, q, w, n, n4, sk, sp, frozen);
 }
 
 }  // namespace mrstat

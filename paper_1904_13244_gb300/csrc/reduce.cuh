@@ -8,6 +8,14 @@
 namespace mrstat {
 namespace red {
 
+// Programmatic dependent launch (sm_90+): a kernel launched with the programmatic
+// stream-serialization attribute may start while its predecessor runs; pdl_wait() returns
+// once the predecessor has completed and its memory is visible (at once when there was
+// no early start), and pdl_trigger() lets this kernel's own successor start early.
+// Everything a kernel reads from earlier launches must come after its pdl_wait().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
