@@ -87,6 +87,9 @@ def parse_args():
     ap.add_argument("--rank", type=int, default=32)
     ap.add_argument("--no-recon", action="store_true")
     ap.add_argument("--no-shapes", action="store_true")
+    ap.add_argument("--profile-recon", default=None, choices=["plain", "lowrank", "surrogate"],
+                    help="run that reconstruction once more first and bracket the timed one with "
+                         "cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -558,12 +561,19 @@ def main():
         for name, kw in runs:
             a = torch.zeros((4, seq.nv), dtype=torch.float32, device="cuda")
             mask = torch.zeros(seq.nv, dtype=torch.uint8, device="cuda")
+            if args.profile_recon == name:
+                plan.gn_solve(d, a.clone(), mask=mask.clone(), outer_iters=15, inner_iters=30, rho_init_exact=1,
+                              mask_threshold=0.1, **kw)
+                torch.cuda.synchronize()
+                torch.cuda.profiler.start()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             rep = plan.gn_solve(d, a, mask=mask, outer_iters=15, inner_iters=30, rho_init_exact=1,
                                 mask_threshold=0.1, **kw)
             torch.cuda.synchronize()
             secs = time.perf_counter() - t0
+            if args.profile_recon == name:
+                torch.cuda.profiler.stop()
             m = (mask.bool() & sup)
             def nrmse(x, y):
                 return float(torch.linalg.vector_norm((x - y)[m]) / torch.linalg.vector_norm(y[m]))

@@ -55,6 +55,12 @@ lr_project_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = j < nv;
   const bool on = valid && (mask == nullptr || mask[j] != 0);
+  // a block whose voxels all lie outside the mask has only zeros to write
+  if (!__syncthreads_or(on)) {
+    if (valid)
+      for (int r = 0; r < 3 * R; ++r) coef[(size_t)r * nv + j] = 0.f;
+    return;
+  }
   float t1 = 1000.f, t2 = 100.f, bj = 1.f;
   if (valid) {
     t1 = expf(alpha[j]);
@@ -654,6 +660,7 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
   float sf = 0.f, sv = 0.f;
   for (int ix = blockIdx.x >> 1; ix < nx; ix += gridDim.x >> 1) {
     // 0. the column's voxel data (each block loads all of it)
+    int inside = 0;
     for (int iy = tid; iy < NY; iy += kColThreads) {
       const int j = iy * nx + ix;
       const float m = maskf[j];
@@ -664,8 +671,24 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
       const float val[6] = {vk[0], vk[1], vk[2] * m, vk[3] * m, rh.x, rh.y};
 #pragma unroll
       for (int c = 0; c < 6; ++c) vox[c * NY + iy] = val[c];
+      inside |= m != 0.f;
     }
-    __syncthreads();
+    if (!__syncthreads_or(inside)) {
+      // no voxel of the column lies inside the mask, so g is zero on it (the product is
+      // column by column); both blocks of the cluster see the same column and skip it
+      for (int iy = ya + tid; iy < ye; iy += kColThreads) {
+        const int j = iy * nx + ix;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          g[(size_t)k * nv + j] = 0.f;
+          if (vdot != nullptr) {
+            const float vk = v[(size_t)k * nv + j];
+            sv = fmaf(vk, vk, sv);
+          }
+        }
+      }
+      continue;
+    }
     // 1. h_r and its phase-encode DFT; warp w takes the pair of local r = w, w + 8: the
     //    coefficient loads of both issue together and the voxel data is read once; the
     //    second column waits in its own row of hs (in iy order) while the first is

@@ -102,6 +102,31 @@ def test_lowrank_products_match_projected_oracle(mr, case):
     assert metrics.relerr(h2, ref_h) < TOL
 
 
+def test_lowrank_masked_columns_match_projected_oracle(mr):
+    """A mask that leaves whole image columns empty (the column kernel skips them) and
+    random holes elsewhere: the low-rank products against the projected oracle model."""
+    seq = synth.make_sequence(64, 64, 5, 7.8, 3.9, seed=6)
+    alpha = random_phantom(64, 64, 8)
+    train = training_set(400, 2)
+    U = f32(model.time_basis(seq, np.exp(train[0]), np.exp(train[1]), 16)[0])
+    mask = np.random.default_rng(9).random((64, 64)) > 0.3
+    mask[:, :10] = False
+    mask[:, 40:44] = False
+    mask = mask.ravel()
+    lin = model.project_onto_basis(model.linearize(seq, alpha, mask=mask), U)
+    v = synth.random_params(seq.nv, 13)
+    with mr.Plan(seq) as plan:
+        plan.lowrank_set_basis(cuda(U))
+        plan.lowrank_linearize(cuda(alpha), mask=cuda(mask.astype(np.uint8), torch.uint8))
+        h = plan.jhjv(cuda(v)).cpu().numpy()
+        h2 = plan.jhw(plan.jvp(cuda(v))).cpu().numpy()
+        plan.check()
+    ref = model.gauss_newton_product(lin, v)
+    assert metrics.relerr(h, ref) < TOL
+    assert metrics.relerr(h2, ref) < TOL
+    assert np.all(h[:, ~mask] == 0)
+
+
 @pytest.mark.parametrize("iters", [1, 4])
 def test_lowrank_cg_fixed_matches_oracle_cg(mr, iters):
     """Fixed-count CG on the low-rank Re(J^H J) through the column kernel, which also takes
