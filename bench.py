@@ -67,7 +67,7 @@ NCU_TRAFFIC = {
     ("xdft", "0728f575d9d96a3d"): 13670656.0,
     ("xdft_adj", "0728f575d9d96a3d"): 13668608.0,
     # profiles/lr_jhjv_column_kernel_brain224.md (warm L2, as in the CG loop)
-    ("jhw_dot", "f1f10e7119e1e2c3"): 4608.0,
+    ("jhw_dot", "5ef12bc0a000a478"): 512.0,
 }
 
 

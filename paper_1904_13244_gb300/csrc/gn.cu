@@ -11,7 +11,10 @@
 #include <cmath>
 #include <cstring>
 
+#include <type_traits>
+
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace mrstat {
 namespace {
@@ -245,6 +248,8 @@ __global__ void __launch_bounds__(kT)
 st_update_kernel(float* __restrict__ z, float* __restrict__ res, const float* __restrict__ dir,
                  const float* __restrict__ q, int64_t n, int64_t n4, double* sc, int* si, double delta,
                  double rel_tol, int max_steps, double* part, unsigned* ticket) {
+  red::pdl_trigger();
+  red::pdl_wait();  // q, the sums and the flags come from the previous launches
   const int64_t t0 = blockIdx.x * (int64_t)kT + threadIdx.x, stride = (int64_t)gridDim.x * kT;
   float4 zv, rv, dv, qv;
   if (t0 < n4) {
@@ -309,6 +314,8 @@ st_update_kernel(float* __restrict__ z, float* __restrict__ res, const float* __
 __global__ void __launch_bounds__(kT)
 st_dir_kernel(float* __restrict__ dir, const float* __restrict__ res, const float* __restrict__ z, int64_t n,
               int64_t n4, double* sc, const int* __restrict__ si, double* part, unsigned* ticket) {
+  red::pdl_trigger();
+  red::pdl_wait();  // res, z and the flags come from the update launch
   const int64_t t0 = blockIdx.x * (int64_t)kT + threadIdx.x, stride = (int64_t)gridDim.x * kT;
   float4 dv, rv, zv;
   if (t0 < n4) {
@@ -620,7 +627,12 @@ struct Solver {
   template <typename F>
   cudaError_t vec(F&& launch, int nlaunch = 1) {
     Span sp(p, MRSTAT_K_VECTOR, st, nlaunch);
-    launch();
+    if constexpr (std::is_same_v<decltype(launch()), cudaError_t>) {
+      const cudaError_t e = launch();
+      if (e != cudaSuccess) return e;
+    } else {
+      launch();
+    }
     return cudaGetLastError();
   }
 
@@ -648,14 +660,15 @@ struct Solver {
       // q = B dir and dir.B dir (gated like the product once CG has stopped)
       status = do_jhjv(p, p->gn_dir, p->gn_q, st, sc + S_DBD);
       if (status != MRSTAT_OK) break;
+      // programmatic dependent launches: each kernel's launch overlaps the previous one's tail
       e = vec([&] {
-        st_update_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_z, p->gn_res, p->gn_dir, p->gn_q, n4, v4, sc, si,
-                                                      delta, rel_tol, inner, p->red, p->ticket);
+        return launch_pdl(st_update_kernel, dim3(grid_for(n4)), dim3(kT), 0, st, p->gn_z, p->gn_res, p->gn_dir,
+                          p->gn_q, n4, v4, sc, si, delta, rel_tol, inner, p->red, p->ticket);
       });
       if (e == cudaSuccess)
         e = vec([&] {
-          st_dir_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_dir, p->gn_res, p->gn_z, n4, v4, sc, si, p->red,
-                                                     p->ticket);
+          return launch_pdl(st_dir_kernel, dim3(grid_for(n4)), dim3(kT), 0, st, p->gn_dir, p->gn_res, p->gn_z, n4,
+                            v4, sc, si, p->red, p->ticket);
         });
       if (e != cudaSuccess) status = cuda_fail(e, "Steihaug iteration");
     }

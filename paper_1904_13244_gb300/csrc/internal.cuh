@@ -199,6 +199,25 @@ cudaError_t lowrank_train_matrix(const float4* D, int ns, int nq, int ntr, float
                                  cudaStream_t st);
 cudaError_t ensure_forward_scratch(Plan* p);
 
+// Launch with programmatic stream serialization: the kernel may start while the previous
+// launch in the stream runs (if that one allows it), so it must call red::pdl_wait()
+// before it reads anything an earlier launch wrote.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---- launchers (each returns the launch's cudaError_t) ----
 // bloch.cu
 cudaError_t launch_bloch(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,

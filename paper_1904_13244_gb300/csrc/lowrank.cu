@@ -1349,20 +1349,9 @@ static cudaError_t launch_column_t(Plan* p, const float* v, double* vdot, double
   const int grid = 2 * std::min(nx, kRedBlocks / 2);
   // programmatic dependent launch: the set-up above the kernel's pdl_wait overlaps the
   // tail of the previous launch in the stream
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kColThreads);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, lr_jhjv_column_kernel<N1>, L.dft_small, v, (const float*)L.coefT,
-                            (const float2*)p->rho, (const float*)p->maskf, (const float2*)p->roots,
-                            (const float*)L.UgS, L.ky_count_max, nx, ny, p->nv, R, (float)nx, out, p->red,
-                            p->ticket, vdot, vv, (const int*)p->gate);
+  return launch_pdl(lr_jhjv_column_kernel<N1>, dim3(grid), dim3(kColThreads), sm, st, L.dft_small, v, L.coefT,
+                    p->rho, p->maskf, p->roots, L.UgS, L.ky_count_max, nx, ny, p->nv, R, (float)nx, out, p->red,
+                    p->ticket, vdot, vv, p->gate);
 }
 
 static cudaError_t launch_column(Plan* p, const float* v, double* vdot, double* vv, float* out, cudaStream_t st) {

@@ -158,16 +158,7 @@ cudaError_t launch_cg_init(const float* rhs, float* x, float* r, float* p, float
 cudaError_t launch_cg_cg_step(float* x, float* r, float* p, float* q, const float* w, int64_t n, double* sk,
                               const double* sp, int* frozen, cudaStream_t st) {
   const int64_t n4 = aligned16(x) && aligned16(r) && aligned16(p) && aligned16(q) && aligned16(w) ? n / 4 : 0;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid_for(n));
-  cfg.blockDim = dim3(kT);
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, cg_cg_step_kernel, x, r, p, q, w, n, n4, sk, sp, frozen);
+  return launch_pdl(cg_cg_step_kernel, dim3(grid_for(n)), dim3(kT), 0, st, x, r, p, q, w, n, n4, sk, sp, frozen);
 }
 
 }  // namespace mrstat
