@@ -28,7 +28,9 @@ plain run's NRMSE: |NRMSE_fast - NRMSE_plain| <= max(0.1 NRMSE_plain, 1e-3)), pl
 reconstruction with B1 as a fifth unknown on the phantom with a smooth B1 field
 (key "recon.b1_estimated"), and the same step in the low-rank form on the paper's other
 sequence shapes: 224 x 224 with 1792 TRs and the sine-squared train, and the 112 x 88,
-16-fill constant-flip scan (key "shapes": products/s).
+16-fill constant-flip scan (key "shapes": products/s), and the slice-profile Bloch model
+(32 isochromats, 16 Gaussian RF sub-steps): one linearisation and the plain-form step with
+it (key "slice_profile").
 Inputs are the seeded brain-like phantom and flip train of ``synth``.
 
 Multi-GPU: N independent replicas (one per rank), weak scaling, no collective on
@@ -416,6 +418,34 @@ def main():
                             "column_kernel": bool(sseq.ny % 32 == 0 and sseq.ny // 32 <= 8)}
             splan.close()
 
+    # the slice-profile Bloch model (32 isochromats, 16 Gaussian RF sub-steps): one
+    # linearisation of the same phantom, and the exact-form step with it
+    slice_prof = None
+    if not args.no_shapes and world == 1:
+        sp_plan = mr.Plan(seq)
+        sp_plan.set_slice_profile(32, 16)
+        for _ in range(2):
+            sp_plan.linearize(a_dev)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        reps = 5
+        for _ in range(reps):
+            sp_plan.linearize(a_dev)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        lin_ms = ev0.elapsed_time(ev1) / reps
+        # per voxel, TR and isochromat: the pulse applied to m and both tangents (3 x 15
+        # flops) and two relaxations with the tangents' source terms (2 x 25 flops)
+        flops = seq.nv * seq.ntr * 32 * 95.0
+        fp32_peak = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * 2.07e9
+        sms, _, _ = timed(sp_plan, make_step(sp_plan, "plain"), max(3, args.steps // 6), ())
+        slice_prof = {"linearize_ms": lin_ms, "isochromats": 32, "rf_substeps": 16,
+                      "achieved_tflops": flops / (lin_ms / 1e3) / 1e12,
+                      "fp32_peak_tflops": fp32_peak / 1e12, "frac": flops / (lin_ms / 1e3) / fp32_peak,
+                      "plain_step_products_per_s": iters / (sms / 1e3), "plain_step_ms": sms}
+        sp_plan.close()
+
     # end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -659,7 +689,7 @@ def main():
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu, "plain": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
-                "recon": recon, "surrogate": surrogate_info, "shapes": shapes,
+                "recon": recon, "surrogate": surrogate_info, "shapes": shapes, "slice_profile": slice_prof,
                 "kernel_ms_per_step": {k: v for k, v in per_step_ms.items()}}
         print(json.dumps(line), flush=True)
     if net is not None:
