@@ -63,6 +63,7 @@ struct Plan {
   float* cg_p = nullptr;    // [npar][nv]
   float* cg_q = nullptr;    // [npar][nv]
   float* cg_w = nullptr;    // [npar][nv] Re(J^H J) r
+  unsigned* cg_bar = nullptr;  // [2] grid barrier of the persistent CG (arrivals, generation)
   float2* cg_jv = nullptr;  // [ntr][nkx]
   double* cg_s = nullptr;   // CG scalars, 4 per iteration
   int* cg_frozen = nullptr; // CG stop flag
@@ -111,6 +112,7 @@ struct Plan {
   struct Mark {
     int kid;
     cudaEvent_t a, b;
+    int n;  // launches (or, for a persistent kernel, products) the events bracket
   };
   std::vector<Mark> marks;
   std::vector<cudaEvent_t> event_pool;
@@ -150,8 +152,9 @@ struct Span {
   Plan* p;
   int kid;
   cudaStream_t st;
+  int n;
   cudaEvent_t a = nullptr, b = nullptr;
-  Span(Plan* plan, int k, cudaStream_t s, int nlaunch = 1) : p(plan), kid(k), st(s) {
+  Span(Plan* plan, int k, cudaStream_t s, int nlaunch = 1) : p(plan), kid(k), st(s), n(nlaunch) {
     p->launches[kid] += nlaunch;
     if (p->prof_on && ((p->prof_mask >> kid) & 1u)) {
       a = pool_event(p);
@@ -162,7 +165,7 @@ struct Span {
   ~Span() {
     if (a && b) {
       cudaEventRecord(b, st);
-      p->marks.push_back({kid, a, b});
+      p->marks.push_back({kid, a, b, n});
     }
   }
 };
@@ -195,6 +198,9 @@ int lowrank_jhw(Plan* p, const float2* w, float* g, cudaStream_t st);
 // where the path allows)
 int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot = nullptr,
                  double* vv = nullptr);
+// mrstat_cg_fixed in one persistent launch when the low-rank column path applies (false:
+// not launched); *err: the launch's error
+bool lowrank_cg_fixed_persistent(Plan* p, const float* rhs, float* x, int iters, cudaStream_t st, cudaError_t* err);
 cudaError_t lowrank_train_matrix(const float4* D, int ns, int nq, int ntr, float2* Y, float2* Yt,
                                  cudaStream_t st);
 cudaError_t ensure_forward_scratch(Plan* p);

@@ -622,6 +622,168 @@ size_t column_smem_bytes(int ny, int R, int kmax) {
   return sizeof(float2) * ((size_t)ny + rc * (ny + 1) + 2 * (size_t)kmax * ny) + sizeof(float) * 14 * (size_t)ny;
 }
 
+// Shared-memory layout of the column kernels and the peer's exchange buffers.
+struct ColShared {
+  float2* rt;      // [NY] w^k
+  float2* hs;      // [RC][NY + 1]: H, then G, then P
+  float2* sbuf;    // [kmax][NY] this block's part of s, then s
+  float2* sin;     // [kmax][NY] the peer's part (written by it)
+  float* vox;      // [6][NY]: v0, v1, m v2, m v3, Re rho, Im rho
+  float* red4;     // [4][NY] contraction over this block's r
+  float* rin;      // [4][NY] the peer's contraction (written by it)
+  float2* sin_peer;
+  float* rin_peer;
+};
+
+// Steps 1-4 of the column product for image column ix (the voxel data in S.vox): on return
+// red4 (this block's half of iy) and rin hold the two parts of the contraction.
+template <int N1>
+__device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& S, const Fft32Lane& ffw,
+                                            const Fft32Lane& ffa, const float* __restrict__ coefT,
+                                            const float* __restrict__ UgS, int kmax, int ix, int nx, int R, int r0,
+                                            int nr, int ya, int ye) {
+  namespace cgp = cooperative_groups;
+  cgp::cluster_group cl = cgp::this_cluster();
+  constexpr int NY = 32 * N1, LD = NY + 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int brev = (int)(__brev((unsigned)lane) >> 27);
+  const size_t plane = (size_t)nx * NY;
+  const float2* rt = S.rt;
+  float2* hs = S.hs;
+  float2* sbuf = S.sbuf;
+  const float2* sin = S.sin;
+  const float* vox = S.vox;
+  float* red4 = S.red4;
+  float2* sin_peer = S.sin_peer;
+  float* red4_peer_in = S.rin_peer;
+  // 1. h_r and its phase-encode DFT; warp w takes the pair of local r = w, w + 8: the
+  //    coefficient loads of both issue together and the voxel data is read once; the
+  //    second column waits in its own row of hs (in iy order) while the first is
+  //    transformed
+  for (int ra = warp; ra < nr; ra += 2 * kColWarps) {
+    const int rb = ra + kColWarps;
+    const bool two = rb < nr;
+    const float* ca = coefT + (size_t)(r0 + ra) * plane + (size_t)ix * NY;
+    const float* cbp = two ? coefT + (size_t)(r0 + rb) * plane + (size_t)ix * NY : ca;
+    float2 xa[N1];
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) {
+      const int iy = 32 * i1 + lane;
+      const float v0 = vox[iy], v1 = vox[NY + iy], v2 = vox[2 * NY + iy], v3 = vox[3 * NY + iy];
+      const float rr = vox[4 * NY + iy], ri = vox[5 * NY + iy];
+      const float c = ca[iy], t = fmaf(v0, ca[(size_t)R * plane + iy], v1 * ca[(size_t)2 * R * plane + iy]);
+      const float d = cbp[iy], u = fmaf(v0, cbp[(size_t)R * plane + iy], v1 * cbp[(size_t)2 * R * plane + iy]);
+      xa[i1] = make_float2(-(ri * t + v3 * c), rr * t + v2 * c);
+      if (two) hs[rb * LD + iy] = make_float2(-(ri * u + v3 * d), rr * u + v2 * d);
+    }
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1) {
+        if (!two) break;
+#pragma unroll
+        for (int i1 = 0; i1 < N1; ++i1) xa[i1] = hs[rb * LD + 32 * i1 + lane];  // this lane's own stores
+        __syncwarp();  // every lane has its inputs before any output lands in the row
+      }
+      float2 X[N1];
+      dft_small<N1, false>(W, xa, X);
+      const int rl = h == 0 ? ra : rb;
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        float2 acc = cmul(X[k1], rt[k1 * lane]);  // k1 lane <= 31 (N1 - 1) < NY
+        acc = fft32_warp(acc, ffw);
+        hs[rl * LD + k1 + N1 * brev] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  // 2. per-ky Gram through the TR axis, with the TRs of each ky in slots i < kmax
+  //    (U as UgS[r][i][ky], zero past a ky's TRs; s as [i][ky]): consecutive lanes take
+  //    consecutive ky, so U is read coalesced and s without bank conflicts.
+  //    2a. thread per (i, ky): this block's part of s[i][ky] = sum_q U[i-th TR of ky][q] H_q(ky)
+  for (int e = tid; e < kmax * NY; e += kColThreads) {
+    const int i = e / NY, ky = e - i * NY;
+    float sr = 0.f, si = 0.f;
+#pragma unroll
+    for (int q = 0; q < kColMaxRc; ++q) {  // unrolled: the loads of U issue together
+      if (q < nr) {
+        const float u = __ldg(UgS + ((size_t)(r0 + q) * kmax + i) * NY + ky);
+        const float2 h = hs[q * LD + ky];
+        sr = fmaf(u, h.x, sr);
+        si = fmaf(u, h.y, si);
+      }
+    }
+    const float2 part = make_float2(sr, si);
+    sbuf[e] = part;
+    sin_peer[e] = part;  // the peer's copy of this block's part
+  }
+  cl.sync();  // both parts of every s are in both blocks
+  //    2b. warp per r, lane per ky: G_r(ky) = sum_i U[i-th TR of ky][r] s[i][ky], with s the
+  //        sum of the two parts (commutative: the same s in both blocks)
+  for (int rl = warp; rl < nr; rl += kColWarps) {
+    const float* ur = UgS + (size_t)(r0 + rl) * kmax * NY;
+#pragma unroll
+    for (int ky = lane; ky < NY; ky += 32) {
+      float2 o = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int i = 0; i < kmax; ++i) {
+        const float u = __ldg(ur + (size_t)i * NY + ky);
+        const float2 sa = sbuf[i * NY + ky], sb = sin[i * NY + ky];
+        const float2 sv = make_float2(sa.x + sb.x, sa.y + sb.y);
+        o.x = fmaf(u, sv.x, o.x);
+        o.y = fmaf(u, sv.y, o.y);
+      }
+      hs[rl * LD + ky] = o;
+    }
+  }
+  __syncwarp();  // the adjoint below reads only the rows this warp has just written
+  // 3. adjoint phase-encode DFT
+  for (int rl = warp; rl < nr; rl += kColWarps) {
+    float2* x = hs + rl * LD;
+    const int i2 = brev;
+    float2 z[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) z[k1] = x[k1 + N1 * lane];  // k2 = lane
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const float2 t = fft32_warp(z[k1], ffa);  // at i2 = bitrev(lane)
+      z[k1] = cmulc(t, rt[k1 * i2]);
+    }
+    float2 out[N1];
+    dft_small<N1, true>(W, z, out);
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) x[32 * i1 + i2] = out[i1];
+  }
+  __syncthreads();
+  // 4. contraction with the tangents over this block's r, one thread per iy
+  for (int iy = tid; iy < NY; iy += kColThreads) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const float rhx = vox[4 * NY + iy], rhy = vox[5 * NY + iy];
+    const float* cc = coefT + (size_t)ix * NY + iy;
+#pragma unroll
+    for (int rl = 0; rl < kColMaxRc; ++rl) {
+      if (rl < nr) {
+        const int r = r0 + rl;
+        const float2 pv = hs[rl * LD + iy];
+        const float c = cc[(size_t)r * plane];
+        const float t1 = cc[(size_t)(R + r) * plane], t2 = cc[(size_t)(2 * R + r) * plane];
+        const float imcp = rhx * pv.y - rhy * pv.x;  // Im(conj(rho) P)
+        a0 = fmaf(t1, imcp, a0);
+        a1 = fmaf(t2, imcp, a1);
+        a2 = fmaf(c, pv.y, a2);
+        a3 = fmaf(-c, pv.x, a3);
+      }
+    }
+    // the part for this block's half of the column stays here, the rest goes to the peer
+    float* dst = (iy >= ya && iy < ye) ? red4 : red4_peer_in;
+    dst[iy] = a0;
+    dst[NY + iy] = a1;
+    dst[2 * NY + iy] = a2;
+    dst[3 * NY + iy] = a3;
+  }
+  cl.sync();  // the peer's part of this block's half has arrived
+}
+
 template <int N1>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kColThreads, 3)
 lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restrict__ v,
@@ -644,11 +806,8 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
   float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // [6][NY]: v0, v1, m v2, m v3, Re rho, Im rho
   float* red4 = vox + 6 * NY;                            // [4][NY] contraction over this block's r
   float* rin = red4 + 4 * NY;                            // [4][NY] the peer's contraction (written by it)
-  float2* sin_peer = cl.map_shared_rank(sin, peer);
-  float* red4_peer_in = cl.map_shared_rank(rin, peer);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int brev = (int)(__brev((unsigned)lane) >> 27);
-  const size_t plane = (size_t)nx * NY;
+  const ColShared S = {rt, hs, sbuf, sin, vox, red4, rin, cl.map_shared_rank(sin, peer), cl.map_shared_rank(rin, peer)};
+  const int tid = threadIdx.x, lane = tid & 31;
   const int hy = (NY + 1) / 2, ya = crank * hy, ye = min(NY, ya + hy);  // this block's half of iy
   for (int e = tid; e < NY; e += kColThreads) rt[e] = roots[e];  // plan constants: before the wait
   cl.sync();  // both blocks are running before either stores into the other's shared memory
@@ -689,132 +848,7 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
       }
       continue;
     }
-    // 1. h_r and its phase-encode DFT; warp w takes the pair of local r = w, w + 8: the
-    //    coefficient loads of both issue together and the voxel data is read once; the
-    //    second column waits in its own row of hs (in iy order) while the first is
-    //    transformed
-    for (int ra = warp; ra < nr; ra += 2 * kColWarps) {
-      const int rb = ra + kColWarps;
-      const bool two = rb < nr;
-      const float* ca = coefT + (size_t)(r0 + ra) * plane + (size_t)ix * NY;
-      const float* cbp = two ? coefT + (size_t)(r0 + rb) * plane + (size_t)ix * NY : ca;
-      float2 xa[N1];
-#pragma unroll
-      for (int i1 = 0; i1 < N1; ++i1) {
-        const int iy = 32 * i1 + lane;
-        const float v0 = vox[iy], v1 = vox[NY + iy], v2 = vox[2 * NY + iy], v3 = vox[3 * NY + iy];
-        const float rr = vox[4 * NY + iy], ri = vox[5 * NY + iy];
-        const float c = ca[iy], t = fmaf(v0, ca[(size_t)R * plane + iy], v1 * ca[(size_t)2 * R * plane + iy]);
-        const float d = cbp[iy], u = fmaf(v0, cbp[(size_t)R * plane + iy], v1 * cbp[(size_t)2 * R * plane + iy]);
-        xa[i1] = make_float2(-(ri * t + v3 * c), rr * t + v2 * c);
-        if (two) hs[rb * LD + iy] = make_float2(-(ri * u + v3 * d), rr * u + v2 * d);
-      }
-#pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        if (h == 1) {
-          if (!two) break;
-#pragma unroll
-          for (int i1 = 0; i1 < N1; ++i1) xa[i1] = hs[rb * LD + 32 * i1 + lane];  // this lane's own stores
-          __syncwarp();  // every lane has its inputs before any output lands in the row
-        }
-        float2 X[N1];
-        dft_small<N1, false>(W, xa, X);
-        const int rl = h == 0 ? ra : rb;
-#pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          float2 acc = cmul(X[k1], rt[k1 * lane]);  // k1 lane <= 31 (N1 - 1) < NY
-          acc = fft32_warp(acc, ffw);
-          hs[rl * LD + k1 + N1 * brev] = acc;
-        }
-      }
-    }
-    __syncthreads();
-    // 2. per-ky Gram through the TR axis, with the TRs of each ky in slots i < kmax
-    //    (U as UgS[r][i][ky], zero past a ky's TRs; s as [i][ky]): consecutive lanes take
-    //    consecutive ky, so U is read coalesced and s without bank conflicts.
-    //    2a. thread per (i, ky): this block's part of s[i][ky] = sum_q U[i-th TR of ky][q] H_q(ky)
-    for (int e = tid; e < kmax * NY; e += kColThreads) {
-      const int i = e / NY, ky = e - i * NY;
-      float sr = 0.f, si = 0.f;
-#pragma unroll
-      for (int q = 0; q < kColMaxRc; ++q) {  // unrolled: the loads of U issue together
-        if (q < nr) {
-          const float u = __ldg(UgS + ((size_t)(r0 + q) * kmax + i) * NY + ky);
-          const float2 h = hs[q * LD + ky];
-          sr = fmaf(u, h.x, sr);
-          si = fmaf(u, h.y, si);
-        }
-      }
-      const float2 part = make_float2(sr, si);
-      sbuf[e] = part;
-      sin_peer[e] = part;  // the peer's copy of this block's part
-    }
-    cl.sync();  // both parts of every s are in both blocks
-    //    2b. warp per r, lane per ky: G_r(ky) = sum_i U[i-th TR of ky][r] s[i][ky], with s the
-    //        sum of the two parts (commutative: the same s in both blocks)
-    for (int rl = warp; rl < nr; rl += kColWarps) {
-      const float* ur = UgS + (size_t)(r0 + rl) * kmax * NY;
-#pragma unroll
-      for (int ky = lane; ky < NY; ky += 32) {
-        float2 o = make_float2(0.f, 0.f);
-#pragma unroll 4
-        for (int i = 0; i < kmax; ++i) {
-          const float u = __ldg(ur + (size_t)i * NY + ky);
-          const float2 sa = sbuf[i * NY + ky], sb = sin[i * NY + ky];
-          const float2 sv = make_float2(sa.x + sb.x, sa.y + sb.y);
-          o.x = fmaf(u, sv.x, o.x);
-          o.y = fmaf(u, sv.y, o.y);
-        }
-        hs[rl * LD + ky] = o;
-      }
-    }
-    __syncwarp();  // the adjoint below reads only the rows this warp has just written
-    // 3. adjoint phase-encode DFT
-    for (int rl = warp; rl < nr; rl += kColWarps) {
-      float2* x = hs + rl * LD;
-      const int i2 = brev;
-      float2 z[N1];
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) z[k1] = x[k1 + N1 * lane];  // k2 = lane
-      __syncwarp();
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        const float2 t = fft32_warp(z[k1], ffa);  // at i2 = bitrev(lane)
-        z[k1] = cmulc(t, rt[k1 * i2]);
-      }
-      float2 out[N1];
-      dft_small<N1, true>(W, z, out);
-#pragma unroll
-      for (int i1 = 0; i1 < N1; ++i1) x[32 * i1 + i2] = out[i1];
-    }
-    __syncthreads();
-    // 4. contraction with the tangents over this block's r, one thread per iy
-    for (int iy = tid; iy < NY; iy += kColThreads) {
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      const float rhx = vox[4 * NY + iy], rhy = vox[5 * NY + iy];
-      const float* cc = coefT + (size_t)ix * NY + iy;
-#pragma unroll
-      for (int rl = 0; rl < kColMaxRc; ++rl) {
-        if (rl < nr) {
-          const int r = r0 + rl;
-          const float2 pv = hs[rl * LD + iy];
-          const float c = cc[(size_t)r * plane];
-          const float t1 = cc[(size_t)(R + r) * plane], t2 = cc[(size_t)(2 * R + r) * plane];
-          const float imcp = rhx * pv.y - rhy * pv.x;  // Im(conj(rho) P)
-          a0 = fmaf(t1, imcp, a0);
-          a1 = fmaf(t2, imcp, a1);
-          a2 = fmaf(c, pv.y, a2);
-          a3 = fmaf(-c, pv.x, a3);
-        }
-      }
-      // the part for this block's half of the column stays here, the rest goes to the peer
-      float* dst = (iy >= ya && iy < ye) ? red4 : red4_peer_in;
-      dst[iy] = a0;
-      dst[NY + iy] = a1;
-      dst[2 * NY + iy] = a2;
-      dst[3 * NY + iy] = a3;
-    }
-    cl.sync();  // the peer's part of this block's half has arrived
+    column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ye);
     for (int iy = ya + tid; iy < ye; iy += kColThreads) {
       const int j = iy * nx + ix;
       const float m = maskf[j] * scale;
@@ -850,6 +884,233 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
     red_part[gridDim.x + blockIdx.x] = t2;
   }
   red::finish_reduction2<kColThreads>(red_part, ticket, vdot, vv, ws);
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-count CG on the low-rank B = Re(J^H J) in one persistent launch (Chronopoulos-Gear
+// form, as mrstat_cg_fixed takes it elsewhere): one cluster of two blocks per image
+// column for the whole solve, every cluster resident (cooperative launch).  J^H J is
+// block diagonal in the image columns when the readout DFT pair cancels, so each cluster
+// multiplies its own column and the CG vectors of its column never leave shared memory
+// (each block keeps its half of iy).  Per iteration k:
+//   w = B r on the column (steps 1-4 of the column product), the block's parts of
+//   delta = <r, w> and gamma = <r, r>; a grid barrier whose last block adds the parts
+//   (block order); beta = gamma / gamma_prev, pq = delta - beta gamma / alpha_prev,
+//   alpha = gamma / pq (an iteration with pq <= 0 or gamma = 0 freezes the rest);
+//   p = r + beta p, q = w + beta q, x += alpha p, r -= alpha q on the block's half; the
+//   new r of each half goes into both blocks' voxel data (a store into the peer and a
+//   cluster barrier).
+// The grid barrier's wait is bounded (2 s): a block that gives up sets the error flag, and
+// both blocks of a cluster leave together at the next cluster barrier.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kGridWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint64_t col_global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier over all blocks (bar[0] arrivals, bar[1] generation) whose last arriving
+// block adds the partials part[0..G) and part[G..2G) in block order into out[0..1].
+// Returns false in a block whose wait ran out.
+__device__ bool grid_barrier_sum2(double* part, unsigned* bar, double* out, int* err, double* ws) {
+  __shared__ int s_last, s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    s_last = atomicAdd(bar, 1u) == gridDim.x - 1;
+    s_ok = 1;
+    if (!s_last) {
+      const uint64_t t0 = col_global_ns();
+      uint32_t spins = 0;
+      while (*vgen == gen) {
+        if ((++spins & 1023u) == 0 && col_global_ns() - t0 > kGridWaitNs) {
+          atomicExch(err, 1);
+          s_ok = 0;
+          break;
+        }
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kColThreads) {
+      a += ((volatile double*)part)[i];
+      b += ((volatile double*)part)[gridDim.x + i];
+    }
+    a = red::block_sum<kColThreads>(a, ws);
+    b = red::block_sum<kColThreads>(b, ws);
+    if (threadIdx.x == 0) {
+      out[0] = a;
+      out[1] = b;
+      bar[0] = 0u;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);  // release
+    }
+    __syncthreads();
+  }
+  return s_ok != 0;
+}
+
+size_t cg_column_smem_bytes(int ny, int R, int kmax) {
+  const int hy = (ny + 1) / 2;
+  return column_smem_bytes(ny, R, kmax) + sizeof(float) * ((size_t)ny + 16 * (size_t)hy);
+}
+
+template <int N1>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kColThreads, 3)
+lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict__ rhs, float* __restrict__ xout,
+                     const float* __restrict__ coefT, const float2* __restrict__ rho,
+                     const float* __restrict__ maskf, const float2* __restrict__ roots,
+                     const float* __restrict__ UgS, int kmax, int nx, int nv, int R, float scale, int iters,
+                     double* part, unsigned* bar, double* sums, int* err) {
+  namespace cgp = cooperative_groups;
+  cgp::cluster_group cl = cgp::this_cluster();
+  const int crank = (int)cl.block_rank(), peer = crank ^ 1;
+  constexpr int NY = 32 * N1, LD = NY + 1, HY = (NY + 1) / 2;
+  const int RC = (R + 1) / 2, r0 = crank * RC, nr = min(R, r0 + RC) - r0;
+  extern __shared__ float2 fsm[];
+  float2* rt = fsm;
+  float2* hs = rt + NY;
+  float2* sbuf = hs + RC * LD;
+  float2* sin = sbuf + kmax * NY;
+  float* vox = reinterpret_cast<float*>(sin + kmax * NY);
+  float* red4 = vox + 6 * NY;
+  float* rin = red4 + 4 * NY;
+  float* mk = rin + 4 * NY;      // [NY] mask of the column
+  float* cgv = mk + NY;          // [4 vectors r, p, q, x][4 rows][HY] this block's half
+  const ColShared S = {rt, hs, sbuf, sin, vox, red4, rin, cl.map_shared_rank(sin, peer), cl.map_shared_rank(rin, peer)};
+  float* vox_peer = cl.map_shared_rank(vox, peer);
+  __shared__ int s_ok_peer;  // written by the peer
+  int* ok_peer_remote = cl.map_shared_rank(&s_ok_peer, peer);
+  __shared__ double ws[kColWarps];
+  __shared__ float s_al, s_be;
+  __shared__ int s_apply;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ix = blockIdx.x >> 1;  // one column per cluster
+  const int ya = crank * HY, nh = min(NY, ya + HY) - ya;  // this block's half of iy: ya .. ya + nh
+  float* const cr = cgv;
+  float* const cp = cgv + 4 * HY;
+  float* const cq = cgv + 8 * HY;
+  float* const cx = cgv + 12 * HY;
+  for (int e = tid; e < NY; e += kColThreads) rt[e] = roots[e];
+  cl.sync();
+  const Fft32Lane ffw = fft32_lane<false>(rt, N1, lane), ffa = fft32_lane<true>(rt, N1, lane);
+
+  // rho and the mask of the whole column; r = rhs and p = q = x = 0 on this block's half
+  int inside = 0;
+  for (int iy = tid; iy < NY; iy += kColThreads) {
+    const int j = iy * nx + ix;
+    const float2 rh = rho[j];
+    const float m = maskf[j];
+    vox[4 * NY + iy] = rh.x;
+    vox[5 * NY + iy] = rh.y;
+    mk[iy] = m;
+    inside |= m != 0.f;
+  }
+  inside = __syncthreads_or(inside);  // the same column in both blocks: the same answer
+  if (tid < nh) {
+    const int iy = ya + tid, j = iy * nx + ix;
+    const float m = mk[iy];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float r = rhs[(size_t)k * nv + j];
+      cr[k * HY + tid] = r;
+      cp[k * HY + tid] = 0.f;
+      cq[k * HY + tid] = 0.f;
+      cx[k * HY + tid] = 0.f;
+      const float vv = k >= 2 ? r * m : r;
+      vox[k * NY + iy] = vv;
+      vox_peer[k * NY + iy] = vv;
+    }
+  }
+  cl.sync();
+
+  double gam_prev = 0.0, alpha_prev = 0.0;
+  bool frozen = false;
+  for (int it = 0; it < iters; ++it) {
+    if (inside) column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+    // w on this block's half, and the block's parts of <r, w> and <r, r>
+    float w[4] = {0.f, 0.f, 0.f, 0.f};
+    float sd = 0.f, sg = 0.f;
+    if (tid < nh) {
+      const int iy = ya + tid;
+      const float m = mk[iy] * scale;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (inside) w[k] = (red4[k * NY + iy] + rin[k * NY + iy]) * m;
+        const float r = cr[k * HY + tid];
+        sd = fmaf(r, w[k], sd);
+        sg = fmaf(r, r, sg);
+      }
+    }
+    const double bd = red::block_sum<kColThreads>((double)sd, ws);
+    const double bg = red::block_sum<kColThreads>((double)sg, ws);
+    if (tid == 0) {
+      part[blockIdx.x] = bd;
+      part[gridDim.x + blockIdx.x] = bg;
+    }
+    const bool ok = grid_barrier_sum2(part, bar, sums + 2 * it, err, ws);
+    if (tid == 0) {
+      int apply = 0;
+      float al = 0.f, be = 0.f;
+      if (ok) {
+        const double delta = ((volatile double*)sums)[2 * it], gamma = ((volatile double*)sums)[2 * it + 1];
+        double beta = 0.0, pq = delta;
+        if (it > 0) {
+          beta = gamma / gam_prev;
+          pq = delta - beta * gamma / alpha_prev;
+        }
+        apply = !frozen && pq > 0.0 && gamma > 0.0;
+        if (apply) {
+          const double alpha = gamma / pq;
+          al = (float)alpha;
+          be = (float)beta;
+          gam_prev = gamma;
+          alpha_prev = alpha;
+        } else {
+          frozen = true;
+        }
+      }
+      s_apply = apply;
+      s_al = al;
+      s_be = be;
+      *ok_peer_remote = ok;
+    }
+    __syncthreads();
+    if (s_apply && tid < nh) {
+      const int iy = ya + tid;
+      const float m = mk[iy];
+      const float al = s_al, be = s_be;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int e = k * HY + tid;
+        const float pv = fmaf(be, cp[e], cr[e]);
+        const float qv = fmaf(be, cq[e], w[k]);
+        cp[e] = pv;
+        cq[e] = qv;
+        cx[e] = fmaf(al, pv, cx[e]);
+        const float rv = fmaf(-al, qv, cr[e]);
+        cr[e] = rv;
+        const float vv = k >= 2 ? rv * m : rv;
+        vox[k * NY + iy] = vv;
+        vox_peer[k * NY + iy] = vv;
+      }
+    }
+    cl.sync();  // the new r of both halves is in both blocks; the peer's flag has arrived
+    if (!ok || !s_ok_peer) break;  // both blocks of the cluster leave together
+  }
+  if (tid < nh) {
+    const int j = (ya + tid) * nx + ix;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xout[(size_t)k * nv + j] = cx[k * HY + tid];
+  }
 }
 
 // Partial sums over one chunk of 8 basis functions (blockIdx.z) of
@@ -1365,6 +1626,83 @@ static cudaError_t launch_column(Plan* p, const float* v, double* vdot, double* 
     case 7: return launch_column_t<7>(p, v, vdot, vv, out, st);
     default: return launch_column_t<8>(p, v, vdot, vv, out, st);
   }
+}
+
+template <int N1>
+static cudaError_t launch_cg_columns_t(Plan* p, const float* rhs, float* x, int iters, bool launch, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  const int nx = p->nx, ny = p->ny, R = L.R;
+  const size_t sm = cg_column_smem_bytes(ny, R, L.ky_count_max);
+  cudaError_t e =
+      cudaFuncSetAttribute(lr_cg_columns_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * nx);
+  cfg.blockDim = dim3(kColThreads);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  if (!launch) {
+    // every cluster must be resident at once (the grid barrier waits for all of them)
+    int max_clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&max_clusters, lr_cg_columns_kernel<N1>, &cfg);
+    if (e != cudaSuccess) return e;
+    return max_clusters >= nx ? cudaSuccess : cudaErrorCooperativeLaunchTooLarge;
+  }
+  e = cudaMemsetAsync(p->cg_bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, lr_cg_columns_kernel<N1>, L.dft_small, rhs, x, (const float*)L.coefT,
+                            (const float2*)p->rho, (const float*)p->maskf, (const float2*)p->roots,
+                            (const float*)L.UgS, L.ky_count_max, nx, p->nv, R, (float)nx, iters, p->red, p->cg_bar,
+                            p->cg_s, p->dev_err);
+}
+
+static cudaError_t launch_cg_columns(Plan* p, const float* rhs, float* x, int iters, bool launch, cudaStream_t st) {
+  switch (p->ny / 32) {
+    case 1: return launch_cg_columns_t<1>(p, rhs, x, iters, launch, st);
+    case 2: return launch_cg_columns_t<2>(p, rhs, x, iters, launch, st);
+    case 3: return launch_cg_columns_t<3>(p, rhs, x, iters, launch, st);
+    case 4: return launch_cg_columns_t<4>(p, rhs, x, iters, launch, st);
+    case 5: return launch_cg_columns_t<5>(p, rhs, x, iters, launch, st);
+    case 6: return launch_cg_columns_t<6>(p, rhs, x, iters, launch, st);
+    case 7: return launch_cg_columns_t<7>(p, rhs, x, iters, launch, st);
+    default: return launch_cg_columns_t<8>(p, rhs, x, iters, launch, st);
+  }
+}
+
+// Fixed-count CG on the low-rank Gauss-Newton matrix in one persistent launch where the
+// column kernel applies and every cluster fits on the device at once; returns false (and
+// nothing was launched) otherwise.
+bool lowrank_cg_fixed_persistent(Plan* p, const float* rhs, float* x, int iters, cudaStream_t st, cudaError_t* err) {
+  *err = cudaSuccess;
+  if (p->lr == nullptr || !p->lr->active || !p->lr->column_path || iters < 1 || p->cg_bar == nullptr) return false;
+  cudaError_t e = launch_cg_columns(p, rhs, x, iters, false, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // does not fit (or cannot be asked): the caller iterates launch by launch
+    return false;
+  }
+  {
+    Span sp(p, MRSTAT_K_VECTOR, st);
+    e = ensure_coef_columns(p, st);
+  }
+  if (e != cudaSuccess) {
+    *err = e;
+    return true;
+  }
+  {
+    Span sp(p, MRSTAT_K_JHW_DOT, st, iters);  // one span, counted as `iters` products
+    e = launch_cg_columns(p, rhs, x, iters, true, st);
+  }
+  if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorInvalidConfiguration || e == cudaErrorNotSupported) {
+    cudaGetLastError();  // refused at launch (nothing ran): iterate launch by launch
+    return false;
+  }
+  *err = e;
+  return true;
 }
 
 // J^H J v for a fully sampled readout and ny = 32 N1: the column kernel (factorised

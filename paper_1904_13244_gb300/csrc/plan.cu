@@ -40,7 +40,7 @@ namespace {
 void free_plan(Plan* p) {
   if (p == nullptr) return;
   void* ptrs[] = {p->slice_w, p->slice_prec, p->cs, p->phi, p->kyi, p->ky_ptr, p->ky_tr, p->roots, p->ft, p->fh, p->D, p->rho, p->maskf,
-                  p->dfwd, p->cf, p->A, p->wt, p->red, p->ticket, p->cg_r, p->cg_p, p->cg_q, p->cg_w,
+                  p->dfwd, p->cf, p->A, p->wt, p->red, p->ticket, p->cg_r, p->cg_p, p->cg_q, p->cg_w, p->cg_bar,
                   p->cg_jv, p->cg_s, p->cg_frozen, p->D2, p->rho2, p->gn_g, p->gn_z, p->gn_res,
                   p->gn_dir, p->gn_q, p->gn_alpha, p->gn_trial, p->gn_s, p->gn_r, p->gn_st,
                   p->gn_rt, p->gn_jv, p->gn_mask, p->gn_sc, p->gn_si, p->bf_ft_hi, p->bf_ft_lo,
@@ -361,7 +361,7 @@ int mrstat_profile_stop(mrstat_plan* plan, mrstat_kernel_stats* out) {
       return cuda_fail(e, "profile events");
     }
     out->ms[m.kid] += ms;
-    out->timed[m.kid] += 1;
+    out->timed[m.kid] += m.n;
   }
   plan->marks.clear();
   plan->pool_used = 0;
@@ -471,6 +471,7 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   chk(dalloc(p, &p->cg_p, (size_t)p->npar * nv));
   chk(dalloc(p, &p->cg_q, (size_t)p->npar * nv));
   chk(dalloc(p, &p->cg_w, (size_t)p->npar * nv));
+  chk(dalloc(p, &p->cg_bar, 2));
   chk(dalloc(p, &p->cg_jv, (size_t)p->ntr * p->nkx));
   chk(dalloc(p, &p->cg_frozen, 1));
   chk(dalloc(p, &p->dev_err, 1));
@@ -719,6 +720,12 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
   }
   const int64_t n = (int64_t)plan->npar * plan->nv;
   double* sc = plan->cg_s;
+  {
+    // the low-rank column path runs the whole solve in one persistent launch
+    cudaError_t pe;
+    if (lowrank_cg_fixed_persistent(plan, rhs, x, iters, st, &pe))
+      return pe == cudaSuccess ? MRSTAT_OK : cuda_fail(pe, "persistent CG launch");
+  }
   // Chronopoulos-Gear form: the product is applied to the residual, w = B r, with
   // delta = <r, w> and gamma = <r, r> formed in the same pass; one vector kernel then
   // updates p, q = B p, x and r.  Per iteration k the scalars sit at sc[4k..4k+2].
