@@ -374,8 +374,13 @@ int mrstat_set_slice_profile(mrstat_plan* plan, const mrstat_slice_profile* prof
  * every scalar stays on the device.  The iteration is written in the Chronopoulos-Gear
  * form (the product is applied to the residual r, and <r, Hr>, <r, r> come with it;
  * p.Hp follows from them), which has textbook CG's iterates in exact arithmetic and one
- * vector update per iteration.  An iteration whose curvature p.Hp is not positive, or
- * whose residual is exactly zero, freezes x for the remaining iterations.
+ * vector update per iteration.  Where the low-rank model's column form applies and all
+ * of its image columns fit on the device at once, the whole solve is one persistent
+ * launch in the pipelined form of the same recurrences (Ghysels and Vanroose 2014: Hr is
+ * carried by recurrence, so the grid-wide inner products overlap the next product);
+ * also textbook CG's iterates in exact arithmetic, with `iters` products in all.  An
+ * iteration whose curvature p.Hp is not positive, or whose residual is exactly zero,
+ * freezes x for the remaining iterations.
  *   rhs, x: device float [npar][nv].  iters >= 0.
  * Errors: INVALID_ARG, NOT_LINEARIZED, CUDA.
  */

@@ -15,28 +15,11 @@
 
 #include "internal.cuh"
 #include "reduce.cuh"
+#include "steihaug.cuh"
 
 namespace mrstat {
 namespace {
 
-// float64 scalar slots (gn_sc)
-enum {
-  S_F = 0,       // objective at the trial point / current point
-  S_RR,          // res . res
-  S_RR_NEW,
-  S_GNORM,
-  S_MVAL,        // CG model value m(z) - f
-  S_COEF,        // step applied to z (alpha_j or tau)
-  S_BETA,
-  S_DBD, S_RD, S_DD, S_ZD, S_ZZ,  // sums of the step decision (contiguous)
-  S_ANORM2,      // ||alpha * mask||^2
-  S_GAMMA, S_GAMMA_NEW, S_QQ,     // CGLS
-  S_RHOMAX,      // max |rho| (as float bits in a double slot is not needed: stored as double)
-  S_PNORM2,      // z . z after CG
-  S_COUNT
-};
-// integer slots (gn_si)
-enum { I_ACTIVE = 0, I_CONT, I_EXIT, I_STEPS, I_FROZEN, I_MASKCOUNT, I_COUNT };
 
 constexpr int kT = 256;
 
@@ -175,58 +158,6 @@ __global__ void st_start_kernel(double* sc, int* si) {
   si[I_CONT] = 0;
   si[I_ACTIVE] = rr > 0.0 ? 1 : 0;
   si[I_EXIT] = rr > 0.0 ? MRSTAT_CG_MAX_ITER : MRSTAT_CG_ZERO_GRADIENT;
-}
-
-__device__ double to_boundary(double zz, double zd, double dd, double delta) {
-  const double disc = fmax(zd * zd + dd * (delta * delta - zz), 0.0);
-  return (-zd + sqrt(disc)) / dd;
-}
-
-// One Steihaug decision (Nocedal & Wright Alg. 7.2): choose the step along dir.
-__device__ void st_step(double* sc, int* si, double delta) {
-  const double dBd = sc[S_DBD], rd = sc[S_RD], dd = sc[S_DD], zd = sc[S_ZD], zz = sc[S_ZZ];
-  si[I_STEPS] += 1;
-  if (!(dBd > 0.0)) {
-    const double tau = to_boundary(zz, zd, dd, delta);
-    sc[S_MVAL] += tau * rd + 0.5 * tau * tau * dBd;
-    sc[S_COEF] = tau;
-    si[I_CONT] = 0;
-    si[I_ACTIVE] = 0;
-    si[I_EXIT] = MRSTAT_CG_NEGATIVE_CURVATURE;
-    return;
-  }
-  const double a = sc[S_RR] / dBd;
-  const double zn2 = zz + 2.0 * a * zd + a * a * dd;
-  if (sqrt(fmax(zn2, 0.0)) >= delta) {
-    const double tau = to_boundary(zz, zd, dd, delta);
-    sc[S_MVAL] += tau * rd + 0.5 * tau * tau * dBd;
-    sc[S_COEF] = tau;
-    si[I_CONT] = 0;
-    si[I_ACTIVE] = 0;
-    si[I_EXIT] = MRSTAT_CG_BOUNDARY;
-    return;
-  }
-  sc[S_MVAL] += a * rd + 0.5 * a * a * dBd;
-  sc[S_COEF] = a;
-  si[I_CONT] = 1;
-}
-
-// tolerance and iteration-count test after a continuing step; beta for the next direction
-__device__ void st_beta(double* sc, int* si, double rel_tol, int max_steps) {
-  const double rr_new = sc[S_RR_NEW];
-  if (sqrt(rr_new) <= rel_tol * sc[S_GNORM]) {
-    si[I_ACTIVE] = 0;
-    si[I_CONT] = 0;
-    si[I_EXIT] = MRSTAT_CG_CONVERGED;
-    return;
-  }
-  sc[S_BETA] = rr_new / sc[S_RR];
-  sc[S_RR] = rr_new;
-  if (si[I_STEPS] >= max_steps) {
-    si[I_ACTIVE] = 0;
-    si[I_CONT] = 0;
-    si[I_EXIT] = MRSTAT_CG_MAX_ITER;
-  }
 }
 
 __device__ __forceinline__ float4 ld4(const float* p, int64_t i) { return reinterpret_cast<const float4*>(p)[i]; }
@@ -621,8 +552,6 @@ struct Solver {
   double* sc;
   int* si;
 
-  cudaError_t last() { return cudaGetLastError(); }
-
   // vector kernel launch bookkeeping
   template <typename F>
   cudaError_t vec(F&& launch, int nlaunch = 1) {
@@ -646,7 +575,17 @@ struct Solver {
 
   // Steihaug truncated CG on B = Re(J^H J) with gradient p->gn_g; result in p->gn_z
   int steihaug(double delta, int inner, double rel_tol) {
-    cudaError_t e = vec([&] {
+    cudaError_t e;
+    {
+      // the low-rank column path: the whole solve in one persistent launch
+      cudaError_t pe;
+      if (lowrank_steihaug_persistent(p, p->gn_g, p->gn_z, delta, inner, rel_tol, sc, si, st, &pe)) {
+        if (pe != cudaSuccess) return cuda_fail(pe, "persistent Steihaug launch");
+        e = vec([&] { z_norm_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_z, n4, p->red, p->ticket, sc + S_PNORM2); });
+        return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "step norm");
+      }
+    }
+    e = vec([&] {
       st_init_kernel<<<grid_for(n4), kT, 0, st>>>(p->gn_g, p->gn_z, p->gn_res, p->gn_dir, n4, p->red,
                                                   p->ticket, sc + S_RR);
     });
@@ -920,7 +859,7 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
     if (r != cudaSuccess) return cuda_fail(r, "Gauss-Newton scalars");
     if (herr) {
       cudaMemsetAsync(p->dev_err, 0, sizeof(int), st);
-      return fail(MRSTAT_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on its pipeline barriers");
+      return fail(MRSTAT_ERR_TIMEOUT, "a kernel's bounded wait ran out (tensor-core pipeline or grid barrier)");
     }
     return MRSTAT_OK;
   };

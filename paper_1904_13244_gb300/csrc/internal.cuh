@@ -19,6 +19,9 @@ constexpr int kChannels = 3;
 constexpr int kMaxChannels = 4;
 // Maximum number of blocks of a float64 reduction (partials buffer size).
 constexpr int kRedBlocks = 608;
+// doubles in Plan::red: five partials per block of the vector kernels, or two parity
+// buffers of five partials per block of the persistent column kernels
+constexpr int kRedSlots = 10 * kRedBlocks;
 
 struct Plan {
   int nx = 0, ny = 0, nkx = 0, ntr = 0;
@@ -57,7 +60,7 @@ struct Plan {
   float2* cf = nullptr;     // [4][nv] per-voxel complex coefficients of the y-contraction
   float2* A = nullptr;      // [ntr_pad][nx] y-contracted image rows (padded rows zero)
   float2* wt = nullptr;     // [ntr_pad][nx] x-adjoint of a k-space vector (rows >= ntr zero)
-  double* red = nullptr;    // [kRedBlocks] reduction partials
+  double* red = nullptr;    // [kRedSlots] reduction partials
   unsigned* ticket = nullptr;  // last-block ticket of the reductions (0 between launches)
   float* cg_r = nullptr;    // [npar][nv]
   float* cg_p = nullptr;    // [npar][nv]
@@ -201,6 +204,11 @@ int lowrank_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* v
 // mrstat_cg_fixed in one persistent launch when the low-rank column path applies (false:
 // not launched); *err: the launch's error
 bool lowrank_cg_fixed_persistent(Plan* p, const float* rhs, float* x, int iters, cudaStream_t st, cudaError_t* err);
+// Steihaug's truncated CG from the gradient g in one persistent launch when the low-rank
+// column path applies (false: not launched): the step into z, the solver's scalars into
+// sc / si; *err: the launch's error
+bool lowrank_steihaug_persistent(Plan* p, const float* g, float* z, double delta, int max_steps, double rel_tol,
+                                 double* sc, int* si, cudaStream_t st, cudaError_t* err);
 cudaError_t lowrank_train_matrix(const float4* D, int ns, int nq, int ntr, float2* Y, float2* Yt,
                                  cudaStream_t st);
 cudaError_t ensure_forward_scratch(Plan* p);

@@ -30,6 +30,7 @@
 #include "internal.cuh"
 #include "lowrank.cuh"
 #include "reduce.cuh"
+#include "steihaug.cuh"
 
 namespace mrstat {
 namespace {
@@ -887,21 +888,27 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Fixed-count CG on the low-rank B = Re(J^H J) in one persistent launch (Chronopoulos-Gear
-// form, as mrstat_cg_fixed takes it elsewhere): one cluster of two blocks per image
-// column for the whole solve, every cluster resident (cooperative launch).  J^H J is
-// block diagonal in the image columns when the readout DFT pair cancels, so each cluster
-// multiplies its own column and the CG vectors of its column never leave shared memory
-// (each block keeps its half of iy).  Per iteration k:
-//   w = B r on the column (steps 1-4 of the column product), the block's parts of
-//   delta = <r, w> and gamma = <r, r>; a grid barrier whose last block adds the parts
-//   (block order); beta = gamma / gamma_prev, pq = delta - beta gamma / alpha_prev,
-//   alpha = gamma / pq (an iteration with pq <= 0 or gamma = 0 freezes the rest);
-//   p = r + beta p, q = w + beta q, x += alpha p, r -= alpha q on the block's half; the
-//   new r of each half goes into both blocks' voxel data (a store into the peer and a
-//   cluster barrier).
-// The grid barrier's wait is bounded (2 s): a block that gives up sets the error flag, and
-// both blocks of a cluster leave together at the next cluster barrier.
+// Fixed-count CG on the low-rank B = Re(J^H J) in one persistent launch: one cluster of
+// two blocks per image column for the whole solve, every cluster resident (cooperative
+// launch).  J^H J is block diagonal in the image columns when the readout DFT pair
+// cancels, so each cluster multiplies its own column and the CG vectors of its column
+// never leave shared memory (each block keeps its half of iy).
+// The iteration is the pipelined form of CG (Ghysels and Vanroose, Parallel Computing
+// 40, 2014): with w = B r carried by recurrence, the two inner products of iteration k
+// depend only on r_k and w_k, so their grid-wide sum runs while the cluster applies B to
+// w_k.  Before the loop w_0 = B r_0; per iteration k:
+//   the block's parts of gamma = <r, r> and delta = <w, r> go to part[k mod 2] and the
+//   block arrives at the grid counter (no wait); q = B w (not in the last iteration);
+//   the block waits until every block has arrived k + 1 times and adds the parts itself
+//   in block order (the same sums in every block); beta = gamma / gamma_prev,
+//   pq = delta - beta gamma / alpha_prev, alpha = gamma / pq (an iteration with pq <= 0
+//   or gamma = 0 freezes the rest); z = q + beta z, s = w + beta s, p = r + beta p,
+//   x += alpha p, r -= alpha s, w -= alpha z on the block's half; the new w of each half
+//   goes into both blocks' voxel data (a store into the peer and a cluster barrier).
+// Two parity buffers of partials suffice: a block writes part[k mod 2] again only after
+// passing the wait of iteration k + 1, when every block has finished reading it.
+// The wait is bounded (2 s): a block that gives up sets the error flag, and both blocks of
+// a cluster leave together at the next cluster barrier.
 // ---------------------------------------------------------------------------
 constexpr uint64_t kGridWaitNs = 2000000000ull;
 
@@ -911,56 +918,75 @@ __device__ __forceinline__ uint64_t col_global_ns() {
   return t;
 }
 
-// Grid barrier over all blocks (bar[0] arrivals, bar[1] generation) whose last arriving
-// block adds the partials part[0..G) and part[G..2G) in block order into out[0..1].
-// Returns false in a block whose wait ran out.
-__device__ bool grid_barrier_sum2(double* part, unsigned* bar, double* out, int* err, double* ws) {
-  __shared__ int s_last, s_ok;
+// Sums of NV values over the block, valid in thread 0 (two block barriers); ws holds
+// NV kColWarps doubles.
+template <int NV>
+__device__ __forceinline__ void block_sums(double (&v)[NV], double* ws) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    v[k] = red::warp_sum(v[k]);
+    if (lane == 0) ws[k * kColWarps + w] = v[k];
+  }
   __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = red::warp_sum(lane < kColWarps ? ws[k * kColWarps + lane] : 0.0);
+  }
+  __syncthreads();
+}
+
+// Thread 0 stores the block's NV partials (block sums in thread 0) into part[k G + block]
+// and arrives at the grid counter; it does not wait.
+template <int NV>
+__device__ __forceinline__ void grid_arrive(double* part, unsigned* bar, const double (&v)[NV]) {
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) part[(size_t)k * gridDim.x + blockIdx.x] = v[k];
     __threadfence();
-    s_last = atomicAdd(bar, 1u) == gridDim.x - 1;
-    s_ok = 1;
-    if (!s_last) {
+    atomicAdd(bar, 1u);
+  }
+}
+
+// Thread 0 waits until the grid counter reaches `target` (bounded), then the block adds
+// part[k G .. (k + 1) G) in block order for each k < NV; the sums are valid in thread 0
+// and the same in every block.  Returns false in a block whose wait ran out.
+template <int NV>
+__device__ bool grid_wait_sums(const double* part, const unsigned* bar, unsigned target, int* err, double* ws,
+                               double (&out)[NV]) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    const volatile unsigned* vb = bar;
+    int ok = 1;
+    if (*vb < target) {
       const uint64_t t0 = col_global_ns();
       uint32_t spins = 0;
-      while (*vgen == gen) {
+      while (*vb < target) {
         if ((++spins & 1023u) == 0 && col_global_ns() - t0 > kGridWaitNs) {
           atomicExch(err, 1);
-          s_ok = 0;
+          ok = 0;
           break;
         }
       }
-      __threadfence();
     }
+    __threadfence();
+    s_ok = ok;
   }
   __syncthreads();
-  if (s_last) {
-    __threadfence();
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += kColThreads) {
-      a += ((volatile double*)part)[i];
-      b += ((volatile double*)part)[gridDim.x + i];
-    }
-    a = red::block_sum<kColThreads>(a, ws);
-    b = red::block_sum<kColThreads>(b, ws);
-    if (threadIdx.x == 0) {
-      out[0] = a;
-      out[1] = b;
-      bar[0] = 0u;
-      __threadfence();
-      atomicAdd(bar + 1, 1u);  // release
-    }
-    __syncthreads();
+  const int G = gridDim.x;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = 0.0;
+  for (int i = threadIdx.x; i < G; i += kColThreads) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] += ((const volatile double*)part)[(size_t)k * G + i];
   }
+  block_sums<NV>(out, ws);
   return s_ok != 0;
 }
 
 size_t cg_column_smem_bytes(int ny, int R, int kmax) {
   const int hy = (ny + 1) / 2;
-  return column_smem_bytes(ny, R, kmax) + sizeof(float) * ((size_t)ny + 16 * (size_t)hy);
+  return column_smem_bytes(ny, R, kmax) + sizeof(float) * ((size_t)ny + 20 * (size_t)hy);
 }
 
 template <int N1>
@@ -980,30 +1006,33 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   float2* hs = rt + NY;
   float2* sbuf = hs + RC * LD;
   float2* sin = sbuf + kmax * NY;
-  float* vox = reinterpret_cast<float*>(sin + kmax * NY);
+  float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // rows 0..3: the product's input
   float* red4 = vox + 6 * NY;
   float* rin = red4 + 4 * NY;
   float* mk = rin + 4 * NY;      // [NY] mask of the column
-  float* cgv = mk + NY;          // [4 vectors r, p, q, x][4 rows][HY] this block's half
+  float* cgv = mk + NY;          // [5 vectors r, p, s, z, x][4 rows][HY] this block's half
   const ColShared S = {rt, hs, sbuf, sin, vox, red4, rin, cl.map_shared_rank(sin, peer), cl.map_shared_rank(rin, peer)};
   float* vox_peer = cl.map_shared_rank(vox, peer);
-  __shared__ int s_ok_peer;  // written by the peer
-  int* ok_peer_remote = cl.map_shared_rank(&s_ok_peer, peer);
-  __shared__ double ws[kColWarps];
+  __shared__ int s_ok_peer[2];  // written by the peer, slot it mod 2 in iteration it
+  int* ok_peer_remote = cl.map_shared_rank(s_ok_peer, peer);
+  __shared__ double ws[2 * kColWarps];
   __shared__ float s_al, s_be;
   __shared__ int s_apply;
   const int tid = threadIdx.x, lane = tid & 31;
   const int ix = blockIdx.x >> 1;  // one column per cluster
+  const int G = gridDim.x;
   const int ya = crank * HY, nh = min(NY, ya + HY) - ya;  // this block's half of iy: ya .. ya + nh
   float* const cr = cgv;
   float* const cp = cgv + 4 * HY;
-  float* const cq = cgv + 8 * HY;
-  float* const cx = cgv + 12 * HY;
+  float* const cs = cgv + 8 * HY;
+  float* const cz = cgv + 12 * HY;
+  float* const cx = cgv + 16 * HY;
   for (int e = tid; e < NY; e += kColThreads) rt[e] = roots[e];
   cl.sync();
   const Fft32Lane ffw = fft32_lane<false>(rt, N1, lane), ffa = fft32_lane<true>(rt, N1, lane);
 
-  // rho and the mask of the whole column; r = rhs and p = q = x = 0 on this block's half
+  // rho and the mask of the whole column; r = rhs and p = s = z = x = 0 on this block's
+  // half; the product's input is r (rows 2, 3 masked)
   int inside = 0;
   for (int iy = tid; iy < NY; iy += kColThreads) {
     const int j = iy * nx + ix;
@@ -1023,7 +1052,8 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
       const float r = rhs[(size_t)k * nv + j];
       cr[k * HY + tid] = r;
       cp[k * HY + tid] = 0.f;
-      cq[k * HY + tid] = 0.f;
+      cs[k * HY + tid] = 0.f;
+      cz[k * HY + tid] = 0.f;
       cx[k * HY + tid] = 0.f;
       const float vv = k >= 2 ? r * m : r;
       vox[k * NY + iy] = vv;
@@ -1032,36 +1062,53 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   }
   cl.sync();
 
+  // w_0 = B r_0 (masked, like every product) becomes the product's input
+  if (inside) column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+  if (tid < nh) {
+    const int iy = ya + tid;
+    const float m = mk[iy] * scale;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float wv = inside ? (red4[k * NY + iy] + rin[k * NY + iy]) * m : 0.f;
+      vox[k * NY + iy] = wv;
+      vox_peer[k * NY + iy] = wv;
+    }
+  }
+  cl.sync();
+
   double gam_prev = 0.0, alpha_prev = 0.0;
   bool frozen = false;
   for (int it = 0; it < iters; ++it) {
-    if (inside) column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
-    // w on this block's half, and the block's parts of <r, w> and <r, r>
-    float w[4] = {0.f, 0.f, 0.f, 0.f};
-    float sd = 0.f, sg = 0.f;
-    if (tid < nh) {
-      const int iy = ya + tid;
-      const float m = mk[iy] * scale;
+    double* pk = part + (size_t)(it & 1) * 2 * G;
+    {
+      // the block's parts of gamma = <r, r> and delta = <w, r>, then arrive (no wait)
+      float sd = 0.f, sg = 0.f;
+      if (tid < nh) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (inside) w[k] = (red4[k * NY + iy] + rin[k * NY + iy]) * m;
-        const float r = cr[k * HY + tid];
-        sd = fmaf(r, w[k], sd);
-        sg = fmaf(r, r, sg);
+        for (int k = 0; k < 4; ++k) {
+          const float r = cr[k * HY + tid];
+          sd = fmaf(r, vox[k * NY + ya + tid], sd);
+          sg = fmaf(r, r, sg);
+        }
       }
+      double v[2] = {sd, sg};
+      block_sums<2>(v, ws);
+      grid_arrive<2>(pk, bar, v);
     }
-    const double bd = red::block_sum<kColThreads>((double)sd, ws);
-    const double bg = red::block_sum<kColThreads>((double)sg, ws);
-    if (tid == 0) {
-      part[blockIdx.x] = bd;
-      part[gridDim.x + blockIdx.x] = bg;
-    }
-    const bool ok = grid_barrier_sum2(part, bar, sums + 2 * it, err, ws);
+    // q = B w while the other blocks arrive (not needed in the last iteration)
+    const bool prod = inside && it + 1 < iters;
+    if (prod) column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+    double sums2[2];
+    const bool ok = grid_wait_sums<2>(pk, bar, (unsigned)G * (unsigned)(it + 1), err, ws, sums2);
+    const double delta = sums2[0], gamma = sums2[1];
     if (tid == 0) {
       int apply = 0;
       float al = 0.f, be = 0.f;
       if (ok) {
-        const double delta = ((volatile double*)sums)[2 * it], gamma = ((volatile double*)sums)[2 * it + 1];
+        if (blockIdx.x == 0) {
+          sums[2 * it] = delta;
+          sums[2 * it + 1] = gamma;
+        }
         double beta = 0.0, pq = delta;
         if (it > 0) {
           beta = gamma / gam_prev;
@@ -1081,35 +1128,272 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
       s_apply = apply;
       s_al = al;
       s_be = be;
-      *ok_peer_remote = ok;
+      ok_peer_remote[it & 1] = ok;
     }
     __syncthreads();
     if (s_apply && tid < nh) {
       const int iy = ya + tid;
-      const float m = mk[iy];
-      const float al = s_al, be = s_be;
+      const float al = s_al, be = s_be, m = prod ? mk[iy] * scale : 0.f;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int e = k * HY + tid;
+        const float wv = vox[k * NY + iy];
+        const float qv = prod ? (red4[k * NY + iy] + rin[k * NY + iy]) * m : 0.f;  // q = B w
+        const float zv = fmaf(be, cz[e], qv);
+        const float sv = fmaf(be, cs[e], wv);
         const float pv = fmaf(be, cp[e], cr[e]);
-        const float qv = fmaf(be, cq[e], w[k]);
+        cz[e] = zv;
+        cs[e] = sv;
         cp[e] = pv;
-        cq[e] = qv;
         cx[e] = fmaf(al, pv, cx[e]);
-        const float rv = fmaf(-al, qv, cr[e]);
-        cr[e] = rv;
-        const float vv = k >= 2 ? rv * m : rv;
-        vox[k * NY + iy] = vv;
-        vox_peer[k * NY + iy] = vv;
+        cr[e] = fmaf(-al, sv, cr[e]);
+        const float wn = fmaf(-al, zv, wv);
+        vox[k * NY + iy] = wn;
+        vox_peer[k * NY + iy] = wn;
       }
     }
-    cl.sync();  // the new r of both halves is in both blocks; the peer's flag has arrived
-    if (!ok || !s_ok_peer) break;  // both blocks of the cluster leave together
+    cl.sync();  // the new w of both halves is in both blocks; the peer's flag has arrived
+    // both blocks of the cluster leave together; the slot is written again only after the
+    // peer has passed the next cluster barrier, i.e. after this read
+    if (!ok || !s_ok_peer[it & 1]) break;
   }
   if (tid < nh) {
     const int j = (ya + tid) * nx + ix;
 #pragma unroll
     for (int k = 0; k < 4; ++k) xout[(size_t)k * nv + j] = cx[k * HY + tid];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Steihaug's truncated CG (Nocedal & Wright Alg. 7.2, the inner solve of Algorithm 6) on
+// the low-rank B = Re(J^H J) in one persistent launch, laid out like the fixed-count CG
+// above: one cluster per image column, the column's res, dir and z in shared memory
+// (each block its half of iy), every block taking the same decisions from the same
+// grid-wide sums.  Per step:
+//   q = B dir on the column; dir.q over the grid (wait 1); the step decision (negative
+//   curvature or the trust boundary end CG with z on the boundary); z += c dir, and
+//   while CG continues res += c q with the block's parts of res.res, res.dir, z.res,
+//   z.dir, z.z; their grid sums (wait 2) give the tolerance and step-count test and beta;
+//   dir = -res + beta dir, and the sums of the next decision follow from the new
+//   direction's definition: res.dir' = -res.res + beta res.dir,
+//   dir'.dir' = res.res - 2 beta res.dir + beta^2 dir.dir, z.dir' = -z.res + beta z.dir.
+// Each grid wait is followed by an exchange of the two blocks' wait flags, so both blocks
+// of a cluster leave together when one wait ran out (2 s: the error flag is set).
+// ---------------------------------------------------------------------------
+size_t st_column_smem_bytes(int ny, int R, int kmax) {
+  const int hy = (ny + 1) / 2;
+  return column_smem_bytes(ny, R, kmax) + sizeof(float) * ((size_t)ny + 12 * (size_t)hy);
+}
+
+template <int N1>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kColThreads, 3)
+lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict__ grad,
+                           float* __restrict__ zout, const float* __restrict__ coefT,
+                           const float2* __restrict__ rho, const float* __restrict__ maskf,
+                           const float2* __restrict__ roots, const float* __restrict__ UgS, int kmax, int nx, int nv,
+                           int R, float scale, double delta, double rel_tol, int max_steps, double* sc, int* si,
+                           double* part, unsigned* bar, int* err) {
+  namespace cgp = cooperative_groups;
+  cgp::cluster_group cl = cgp::this_cluster();
+  const int crank = (int)cl.block_rank(), peer = crank ^ 1;
+  constexpr int NY = 32 * N1, LD = NY + 1, HY = (NY + 1) / 2;
+  constexpr int NP = 5;  // partials per block and grid wait, at most
+  const int RC = (R + 1) / 2, r0 = crank * RC, nr = min(R, r0 + RC) - r0;
+  extern __shared__ float2 fsm[];
+  float2* rt = fsm;
+  float2* hs = rt + NY;
+  float2* sbuf = hs + RC * LD;
+  float2* sin = sbuf + kmax * NY;
+  float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // rows 0..3: dir (rows 2, 3 masked)
+  float* red4 = vox + 6 * NY;
+  float* rin = red4 + 4 * NY;
+  float* mk = rin + 4 * NY;  // [NY] mask of the column
+  float* const cr = mk + NY;  // [3 vectors res, dir, z][4 rows][HY] this block's half
+  float* const cd = cr + 4 * HY;
+  float* const cz = cr + 8 * HY;
+  const ColShared S = {rt, hs, sbuf, sin, vox, red4, rin, cl.map_shared_rank(sin, peer), cl.map_shared_rank(rin, peer)};
+  float* vox_peer = cl.map_shared_rank(vox, peer);
+  // the wait flags of the two blocks, exchanged after every grid wait: slot n mod 2 in
+  // exchange n, written again only after the peer has passed the next cluster barrier
+  __shared__ int s_ok_peer[2];  // written by the peer
+  int* ok_peer_remote = cl.map_shared_rank(s_ok_peer, peer);
+  unsigned xch = 0;
+  __shared__ double ws[NP * kColWarps];
+  __shared__ double lsc[S_COUNT];
+  __shared__ int lsi[I_COUNT];
+  __shared__ int s_ok, s_go, s_cont;
+  __shared__ float s_c, s_beta;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ix = blockIdx.x >> 1;  // one column per cluster
+  const int G = gridDim.x;
+  const int ya = crank * HY, nh = min(NY, ya + HY) - ya;  // this block's half of iy: ya .. ya + nh
+  unsigned waits = 0;  // grid waits passed; wait n uses part[(n mod 2) NP G ..]
+  for (int e = tid; e < NY; e += kColThreads) rt[e] = roots[e];
+  cl.sync();  // both blocks run (before any store into the peer) and hold the roots
+  const Fft32Lane ffw = fft32_lane<false>(rt, N1, lane), ffa = fft32_lane<true>(rt, N1, lane);
+
+  // rho and the mask of the whole column; res = g, dir = -g, z = 0 on this block's half
+  int inside = 0;
+  for (int iy = tid; iy < NY; iy += kColThreads) {
+    const int j = iy * nx + ix;
+    const float2 rh = rho[j];
+    const float m = maskf[j];
+    vox[4 * NY + iy] = rh.x;
+    vox[5 * NY + iy] = rh.y;
+    mk[iy] = m;
+    inside |= m != 0.f;
+  }
+  inside = __syncthreads_or(inside);  // the same column in both blocks: the same answer
+  float sg = 0.f;
+  if (tid < nh) {
+    const int iy = ya + tid, j = iy * nx + ix;
+    const float m = mk[iy];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float gv = grad[(size_t)k * nv + j];
+      cr[k * HY + tid] = gv;
+      cd[k * HY + tid] = -gv;
+      cz[k * HY + tid] = 0.f;
+      const float dv = k >= 2 ? -gv * m : -gv;
+      vox[k * NY + iy] = dv;
+      vox_peer[k * NY + iy] = dv;
+      sg = fmaf(gv, gv, sg);
+    }
+  }
+  // rr = g.g and the start of the decisions (the sums of the first step besides dir.B dir)
+  {
+    double v[1] = {sg}, t[1];
+    block_sums<1>(v, ws);
+    double* pk = part + (size_t)(waits & 1) * NP * G;
+    grid_arrive<1>(pk, bar, v);
+    const bool ok = grid_wait_sums<1>(pk, bar, (unsigned)G * ++waits, err, ws, t);
+    if (tid == 0) {
+      const double rr = t[0];
+      for (int k = 0; k < S_COUNT; ++k) lsc[k] = 0.0;
+      for (int k = 0; k < I_COUNT; ++k) lsi[k] = 0;
+      lsc[S_RR] = rr;
+      lsc[S_RD] = -rr;
+      lsc[S_DD] = rr;
+      lsc[S_GNORM] = sqrt(rr);
+      lsi[I_ACTIVE] = rr > 0.0 ? 1 : 0;
+      lsi[I_EXIT] = rr > 0.0 ? MRSTAT_CG_MAX_ITER : MRSTAT_CG_ZERO_GRADIENT;
+      s_ok = ok;
+      s_go = lsi[I_ACTIVE];
+      ok_peer_remote[xch & 1] = ok;
+    }
+  }
+  cl.sync();  // dir of both halves is in both blocks; the peer's flag has arrived
+  bool failed = !s_ok || !s_ok_peer[xch++ & 1];
+  for (int step = 0; step < max_steps && s_go && !failed; ++step) {
+    // q = B dir
+    if (inside) column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+    const float mq = mk[ya + min(tid, nh - 1)] * scale;
+    {
+      float sd = 0.f;
+      if (inside && tid < nh) {
+        const int iy = ya + tid;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sd = fmaf(cd[k * HY + tid], (red4[k * NY + iy] + rin[k * NY + iy]) * mq, sd);
+      }
+      double v[1] = {sd}, t[1];
+      block_sums<1>(v, ws);
+      double* pk = part + (size_t)(waits & 1) * NP * G;
+      grid_arrive<1>(pk, bar, v);
+      const bool ok = grid_wait_sums<1>(pk, bar, (unsigned)G * ++waits, err, ws, t);
+      if (tid == 0) {
+        lsc[S_DBD] = t[0];
+        if (ok) st_step(lsc, lsi, delta);
+        s_ok = ok;
+        s_cont = lsi[I_CONT];
+        s_c = (float)lsc[S_COEF];
+        ok_peer_remote[xch & 1] = ok;
+      }
+      cl.sync();  // the peer's flag has arrived
+      if (!s_ok || !s_ok_peer[xch++ & 1]) {
+        failed = true;
+        break;
+      }
+    }
+    // z += c dir; while continuing res += c q and the parts of the next sums
+    const float c = s_c;
+    const int cont = s_cont;
+    float a[NP] = {0.f, 0.f, 0.f, 0.f, 0.f};  // res.res, res.dir, z.res, z.dir, z.z
+    if (tid < nh) {
+      const int iy = ya + tid;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int e = k * HY + tid;
+        const float dv = cd[e];
+        const float zv = fmaf(c, dv, cz[e]);
+        cz[e] = zv;
+        if (cont) {
+          const float qv = inside ? (red4[k * NY + iy] + rin[k * NY + iy]) * mq : 0.f;
+          const float rv = fmaf(c, qv, cr[e]);
+          cr[e] = rv;
+          a[0] = fmaf(rv, rv, a[0]);
+          a[1] = fmaf(rv, dv, a[1]);
+          a[2] = fmaf(zv, rv, a[2]);
+          a[3] = fmaf(zv, dv, a[3]);
+          a[4] = fmaf(zv, zv, a[4]);
+        }
+      }
+    }
+    if (!cont) break;  // negative curvature or the trust boundary: the same in every block
+    {
+      double v[NP] = {a[0], a[1], a[2], a[3], a[4]}, t[NP];
+      block_sums<NP>(v, ws);
+      double* pk = part + (size_t)(waits & 1) * NP * G;
+      grid_arrive<NP>(pk, bar, v);
+      const bool ok = grid_wait_sums<NP>(pk, bar, (unsigned)G * ++waits, err, ws, t);
+      if (tid == 0) {
+        float be = 0.f;
+        if (ok) {
+          lsc[S_RR_NEW] = t[0];
+          st_beta(lsc, lsi, rel_tol, max_steps);
+          if (lsi[I_ACTIVE]) {
+            const double beta = lsc[S_BETA], rr = t[0], rd = t[1], dd = lsc[S_DD];
+            lsc[S_RD] = -rr + beta * rd;
+            lsc[S_DD] = rr - 2.0 * beta * rd + beta * beta * dd;
+            lsc[S_ZD] = -t[2] + beta * t[3];
+            lsc[S_ZZ] = t[4];
+            be = (float)beta;
+          }
+        }
+        s_ok = ok;
+        s_go = ok && lsi[I_ACTIVE];
+        s_beta = be;
+        ok_peer_remote[xch & 1] = ok;
+      }
+      __syncthreads();
+    }
+    // dir = -res + beta dir, into both blocks' voxel data
+    if (s_go && tid < nh) {
+      const int iy = ya + tid;
+      const float be = s_beta, m = mk[iy];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int e = k * HY + tid;
+        const float dv = fmaf(be, cd[e], -cr[e]);
+        cd[e] = dv;
+        const float vv = k >= 2 ? dv * m : dv;
+        vox[k * NY + iy] = vv;
+        vox_peer[k * NY + iy] = vv;
+      }
+    }
+    cl.sync();  // the new dir of both halves is in both blocks; the peer's flag has arrived
+    if (!s_ok || !s_ok_peer[xch++ & 1]) failed = true;
+  }
+  if (tid < nh) {
+    const int j = (ya + tid) * nx + ix;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) zout[(size_t)k * nv + j] = cz[k * HY + tid];
+  }
+  if (blockIdx.x == 0 && tid == 0 && !failed) {
+    for (int k = S_RR; k <= S_ZZ; ++k) sc[k] = lsc[k];
+    si[I_ACTIVE] = 0;
+    si[I_CONT] = 0;
+    si[I_EXIT] = lsi[I_EXIT];
+    si[I_STEPS] = lsi[I_STEPS];
   }
 }
 
@@ -1628,25 +1912,24 @@ static cudaError_t launch_column(Plan* p, const float* v, double* vdot, double* 
   }
 }
 
-template <int N1>
-static cudaError_t launch_cg_columns_t(Plan* p, const float* rhs, float* x, int iters, bool launch, cudaStream_t st) {
-  LowRank& L = *p->lr;
-  const int nx = p->nx, ny = p->ny, R = L.R;
-  const size_t sm = cg_column_smem_bytes(ny, R, L.ky_count_max);
-  cudaError_t e =
-      cudaFuncSetAttribute(lr_cg_columns_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+// A persistent column kernel: one cluster of two blocks per image column, all resident at
+// once (cooperative launch).  With launch = false only checks that every cluster fits.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_persistent_columns(Plan* p, void (*kernel)(KArgs...), size_t sm, bool launch,
+                                             cudaStream_t st, Args... args) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * nx);
+  cfg.gridDim = dim3(2 * p->nx);
   cfg.blockDim = dim3(kColThreads);
   cfg.dynamicSmemBytes = sm;
   cfg.stream = st;
   if (!launch) {
-    // every cluster must be resident at once (the grid barrier waits for all of them)
+    // every cluster must be resident at once (the grid waits wait for all of them)
     int max_clusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&max_clusters, lr_cg_columns_kernel<N1>, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&max_clusters, kernel, &cfg);
     if (e != cudaSuccess) return e;
-    return max_clusters >= nx ? cudaSuccess : cudaErrorCooperativeLaunchTooLarge;
+    return max_clusters >= p->nx ? cudaSuccess : cudaErrorCooperativeLaunchTooLarge;
   }
   e = cudaMemsetAsync(p->cg_bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
@@ -1655,10 +1938,17 @@ static cudaError_t launch_cg_columns_t(Plan* p, const float* rhs, float* x, int 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, lr_cg_columns_kernel<N1>, L.dft_small, rhs, x, (const float*)L.coefT,
-                            (const float2*)p->rho, (const float*)p->maskf, (const float2*)p->roots,
-                            (const float*)L.UgS, L.ky_count_max, nx, p->nv, R, (float)nx, iters, p->red, p->cg_bar,
-                            p->cg_s, p->dev_err);
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <int N1>
+static cudaError_t launch_cg_columns_t(Plan* p, const float* rhs, float* x, int iters, bool launch, cudaStream_t st) {
+  LowRank& L = *p->lr;
+  const size_t sm = cg_column_smem_bytes(p->ny, L.R, L.ky_count_max);
+  return launch_persistent_columns(p, lr_cg_columns_kernel<N1>, sm, launch, st, L.dft_small, rhs, x,
+                                   (const float*)L.coefT, (const float2*)p->rho, (const float*)p->maskf,
+                                   (const float2*)p->roots, (const float*)L.UgS, L.ky_count_max, p->nx, p->nv, L.R,
+                                   (float)p->nx, iters, p->red, p->cg_bar, p->cg_s, p->dev_err);
 }
 
 static cudaError_t launch_cg_columns(Plan* p, const float* rhs, float* x, int iters, bool launch, cudaStream_t st) {
@@ -1674,12 +1964,88 @@ static cudaError_t launch_cg_columns(Plan* p, const float* rhs, float* x, int it
   }
 }
 
+struct SteihaugArgs {
+  double delta, rel_tol;
+  int max_steps;
+  double* sc;
+  int* si;
+};
+
+template <int N1>
+static cudaError_t launch_st_columns_t(Plan* p, const float* g, float* z, const SteihaugArgs& a, bool launch,
+                                       cudaStream_t st) {
+  LowRank& L = *p->lr;
+  const size_t sm = st_column_smem_bytes(p->ny, L.R, L.ky_count_max);
+  return launch_persistent_columns(p, lr_steihaug_columns_kernel<N1>, sm, launch, st, L.dft_small, g, z,
+                                   (const float*)L.coefT, (const float2*)p->rho, (const float*)p->maskf,
+                                   (const float2*)p->roots, (const float*)L.UgS, L.ky_count_max, p->nx, p->nv, L.R,
+                                   (float)p->nx, a.delta, a.rel_tol, a.max_steps, a.sc, a.si, p->red, p->cg_bar,
+                                   p->dev_err);
+}
+
+static cudaError_t launch_st_columns(Plan* p, const float* g, float* z, const SteihaugArgs& a, bool launch,
+                                     cudaStream_t st) {
+  switch (p->ny / 32) {
+    case 1: return launch_st_columns_t<1>(p, g, z, a, launch, st);
+    case 2: return launch_st_columns_t<2>(p, g, z, a, launch, st);
+    case 3: return launch_st_columns_t<3>(p, g, z, a, launch, st);
+    case 4: return launch_st_columns_t<4>(p, g, z, a, launch, st);
+    case 5: return launch_st_columns_t<5>(p, g, z, a, launch, st);
+    case 6: return launch_st_columns_t<6>(p, g, z, a, launch, st);
+    case 7: return launch_st_columns_t<7>(p, g, z, a, launch, st);
+    default: return launch_st_columns_t<8>(p, g, z, a, launch, st);
+  }
+}
+
+// Steihaug's truncated CG on the low-rank Gauss-Newton matrix in one persistent launch
+// where the column kernel applies and every cluster fits on the device at once; returns
+// false (and nothing was launched) otherwise.  On return z holds the step and sc / si the
+// solver's scalars (S_RR .. S_ZZ, I_EXIT, I_STEPS; I_ACTIVE = I_CONT = 0).
+bool lowrank_steihaug_persistent(Plan* p, const float* g, float* z, double delta, int max_steps, double rel_tol,
+                                 double* sc, int* si, cudaStream_t st, cudaError_t* err) {
+  *err = cudaSuccess;
+  if (p->lr == nullptr || !p->lr->active || !p->lr->column_path || p->cg_bar == nullptr || max_steps < 0)
+    return false;
+  // two parity buffers of five partials per block in p->red; a grid counter that reaches
+  // 2 nx (2 max_steps + 1)
+  const int64_t G = 2 * (int64_t)p->nx;
+  if (10 * G > kRedSlots || G * (2 * (int64_t)max_steps + 1) >= (int64_t)1 << 31) return false;
+  const SteihaugArgs a = {delta, rel_tol, max_steps, sc, si};
+  cudaError_t e = launch_st_columns(p, g, z, a, false, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // does not fit (or cannot be asked): the caller iterates launch by launch
+    return false;
+  }
+  {
+    Span sp(p, MRSTAT_K_VECTOR, st);
+    e = ensure_coef_columns(p, st);
+  }
+  if (e != cudaSuccess) {
+    *err = e;
+    return true;
+  }
+  {
+    Span sp(p, MRSTAT_K_JHW_DOT, st);
+    e = launch_st_columns(p, g, z, a, true, st);
+  }
+  if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorInvalidConfiguration || e == cudaErrorNotSupported) {
+    cudaGetLastError();  // refused at launch (nothing ran): iterate launch by launch
+    return false;
+  }
+  *err = e;
+  return true;
+}
+
 // Fixed-count CG on the low-rank Gauss-Newton matrix in one persistent launch where the
 // column kernel applies and every cluster fits on the device at once; returns false (and
 // nothing was launched) otherwise.
 bool lowrank_cg_fixed_persistent(Plan* p, const float* rhs, float* x, int iters, cudaStream_t st, cudaError_t* err) {
   *err = cudaSuccess;
   if (p->lr == nullptr || !p->lr->active || !p->lr->column_path || iters < 1 || p->cg_bar == nullptr) return false;
+  // two parity buffers of two partials per block in p->red, and a grid counter that
+  // reaches 2 nx iters
+  const int64_t G = 2 * (int64_t)p->nx;
+  if (4 * G > kRedSlots || G * iters >= (int64_t)1 << 31) return false;
   cudaError_t e = launch_cg_columns(p, rhs, x, iters, false, st);
   if (e != cudaSuccess) {
     cudaGetLastError();  // does not fit (or cannot be asked): the caller iterates launch by launch

@@ -465,7 +465,7 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
   // A has the padded TR rows too (zero, never written): J^H J v reads it as W~ over TR quads
   chk(dalloc(p, &p->A, (size_t)p->ntr_pad * p->nx));
   chk(dalloc(p, &p->wt, (size_t)p->ntr_pad * p->nx));
-  chk(dalloc(p, &p->red, 5 * (size_t)kRedBlocks));  // up to five partial vectors
+  chk(dalloc(p, &p->red, (size_t)kRedSlots));
   chk(dalloc(p, &p->ticket, 1));
   chk(dalloc(p, &p->cg_r, (size_t)p->npar * nv));
   chk(dalloc(p, &p->cg_p, (size_t)p->npar * nv));

@@ -337,3 +337,39 @@ def test_surrogate_options_are_checked(mr, noisy_quad):
             with pytest.raises(mr.MrstatError) as e:  # rank 8 net, rank 16 basis
                 plan.gn_solve(cuda(d, torch.complex64), cuda(a0), outer_iters=2, surrogate_iters=1, surrogate=net)
             assert e.value.status == 1
+
+
+@pytest.mark.parametrize("inner,delta_scale", [(8, 1.0), (40, 0.02)])
+def test_lowrank_hessian_steihaug_on_the_column_path_matches_oracle(mr, inner, delta_scale):
+    """64 x 64 with a fully sampled readout: the low-rank Gauss-Newton matrix takes the
+    column form, and Steihaug's CG runs in one persistent launch.  Its first outer
+    iteration against the oracle's Steihaug CG with the projected model's B and the exact
+    gradient: the same exit and step count, and the same step.  The small trust region of
+    the second case ends CG on the boundary."""
+    seq = synth.make_sequence(64, 64, 5, 7.8, 3.9, seed=2)
+    ph = synth.ellipse_phantom(64, 1)
+    truth = truth_of(ph)
+    d = synth.add_noise(model.forward(seq, truth), 50.0, 5).astype(np.complex64).astype(np.complex128)
+    a0 = f32(truth + 0.05 * synth.random_params(seq.nv, 6))
+    delta = delta_scale * 0.1 * float(np.linalg.norm(a0))
+    with mr.Plan(seq) as plan:
+        U = _basis(plan, 32)
+        plan.lowrank_set_basis(U)
+        plan.profile_start(kernels=("jhw_dot",))
+        a = cuda(a0)
+        rep = plan.gn_solve(cuda(d, torch.complex64), a, outer_iters=1, inner_iters=inner, hessian=1,
+                            delta0=delta)
+        prof = plan.profile_stop()
+        plan.check()
+        a_gpu = a.cpu().numpy()
+        Uh = U.cpu().numpy().astype(np.float64)
+    # one persistent launch for the whole inner solve (plus the gradient's product)
+    assert prof["jhw_dot"]["launches"] <= 2
+    lin = model.linearize(seq, a0)
+    g = -model.jhw(lin, d - model.signal(lin))
+    lin_p = model.project_onto_basis(lin, Uh)
+    z, mchange, steps, why = solver.steihaug_cg(lambda v: model.gauss_newton_product(lin_p, v), g, delta, inner)
+    assert rep["cg_exit"][0] == why
+    assert rep["cg_steps"][0] == steps
+    assert rep["accepted"][0]
+    assert metrics.relerr(a_gpu - a0, solver.apply_bounds(a0 + z, solver.GNOptions()) - a0) < 1e-3
