@@ -20,8 +20,8 @@ constexpr int kMaxChannels = 4;
 // Maximum number of blocks of a float64 reduction (partials buffer size).
 constexpr int kRedBlocks = 608;
 // doubles in Plan::red: five partials per block of the vector kernels, or two parity
-// buffers of five partials per block of the persistent column kernels
-constexpr int kRedSlots = 10 * kRedBlocks;
+// buffers of up to eight partials per block of the persistent column kernels
+constexpr int kRedSlots = 16 * kRedBlocks;
 
 struct Plan {
   int nx = 0, ny = 0, nkx = 0, ntr = 0;

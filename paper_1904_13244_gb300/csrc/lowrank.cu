@@ -918,20 +918,49 @@ __device__ __forceinline__ uint64_t col_global_ns() {
   return t;
 }
 
+// The persistent kernels' inner products are summed in float-float arithmetic (an
+// unevaluated sum hi + lo of two floats, about 44 significant bits): GB300 issues float64
+// at a small fraction of the float32 rate, and the float64 block and grid sums of an
+// earlier version cost 15 us per Steihaug step.  Addition of two float-float values:
+// Knuth's TwoSum of the high parts, the low parts added to the error, then a Fast2Sum
+// renormalisation (Dekker 1971; Shewchuk 1997).  No multiplications: nothing for the
+// compiler to contract.
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
 // Sums of NV values over the block, valid in thread 0 (two block barriers); ws holds
-// NV kColWarps doubles.
+// NV kColWarps values.
 template <int NV>
-__device__ __forceinline__ void block_sums(double (&v)[NV], double* ws) {
+__device__ __forceinline__ void block_sums(FF (&v)[NV], FF* ws) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    v[k] = red::warp_sum(v[k]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = ff_add(v[k], ff_shfl_xor(v[k], o));
     if (lane == 0) ws[k * kColWarps + w] = v[k];
   }
   __syncthreads();
   if (w == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = red::warp_sum(lane < kColWarps ? ws[k * kColWarps + lane] : 0.0);
+    for (int k = 0; k < NV; ++k) {
+      v[k] = lane < kColWarps ? ws[k * kColWarps + lane] : FF{0.f, 0.f};
+#pragma unroll
+      for (int o = kColWarps / 2; o > 0; o >>= 1) v[k] = ff_add(v[k], ff_shfl_xor(v[k], o));
+    }
   }
   __syncthreads();
 }
@@ -939,7 +968,7 @@ __device__ __forceinline__ void block_sums(double (&v)[NV], double* ws) {
 // Thread 0 stores the block's NV partials (block sums in thread 0) into part[k G + block]
 // and arrives at the grid counter; it does not wait.
 template <int NV>
-__device__ __forceinline__ void grid_arrive(double* part, unsigned* bar, const double (&v)[NV]) {
+__device__ __forceinline__ void grid_arrive(FF* part, unsigned* bar, const FF (&v)[NV]) {
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) part[(size_t)k * gridDim.x + blockIdx.x] = v[k];
@@ -952,17 +981,22 @@ __device__ __forceinline__ void grid_arrive(double* part, unsigned* bar, const d
 // part[k G .. (k + 1) G) in block order for each k < NV; the sums are valid in thread 0
 // and the same in every block.  Returns false in a block whose wait ran out.
 template <int NV>
-__device__ bool grid_wait_sums(const double* part, const unsigned* bar, unsigned target, int* err, double* ws,
+__device__ bool grid_wait_sums(const FF* part, const unsigned* bar, unsigned target, int* err, FF* ws,
                                double (&out)[NV]) {
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     const volatile unsigned* vb = bar;
     int ok = 1;
     if (*vb < target) {
+      // polls back off (32 ns doubling to 512 ns): blocks that arrive early, e.g. those
+      // of image columns outside the mask, neither take issue slots from the SM's other
+      // blocks nor flood the counter's L2 slice while the rest compute
       const uint64_t t0 = col_global_ns();
-      uint32_t spins = 0;
+      uint32_t spins = 0, ns = 32;
       while (*vb < target) {
-        if ((++spins & 1023u) == 0 && col_global_ns() - t0 > kGridWaitNs) {
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
+        if ((++spins & 63u) == 0 && col_global_ns() - t0 > kGridWaitNs) {
           atomicExch(err, 1);
           ok = 0;
           break;
@@ -974,13 +1008,21 @@ __device__ bool grid_wait_sums(const double* part, const unsigned* bar, unsigned
   }
   __syncthreads();
   const int G = gridDim.x;
+  FF acc[NV];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = 0.0;
+  for (int k = 0; k < NV; ++k) acc[k] = FF{0.f, 0.f};
+  // other blocks wrote the partials: read them from L2 (ld.global.cg), not from L1
+  const float2* vp = reinterpret_cast<const float2*>(part);
   for (int i = threadIdx.x; i < G; i += kColThreads) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) out[k] += ((const volatile double*)part)[(size_t)k * G + i];
+    for (int k = 0; k < NV; ++k) {
+      const float2 t = __ldcg(vp + (size_t)k * G + i);
+      acc[k] = ff_add(acc[k], FF{t.x, t.y});
+    }
   }
-  block_sums<NV>(out, ws);
+  block_sums<NV>(acc, ws);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = (double)acc[k].hi + (double)acc[k].lo;
   return s_ok != 0;
 }
 
@@ -1015,7 +1057,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   float* vox_peer = cl.map_shared_rank(vox, peer);
   __shared__ int s_ok_peer[2];  // written by the peer, slot it mod 2 in iteration it
   int* ok_peer_remote = cl.map_shared_rank(s_ok_peer, peer);
-  __shared__ double ws[2 * kColWarps];
+  __shared__ FF ws[2 * kColWarps];
   __shared__ float s_al, s_be;
   __shared__ int s_apply;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -1079,7 +1121,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   double gam_prev = 0.0, alpha_prev = 0.0;
   bool frozen = false;
   for (int it = 0; it < iters; ++it) {
-    double* pk = part + (size_t)(it & 1) * 2 * G;
+    FF* pk = reinterpret_cast<FF*>(part) + (size_t)(it & 1) * 2 * G;
     {
       // the block's parts of gamma = <r, r> and delta = <w, r>, then arrive (no wait)
       float sd = 0.f, sg = 0.f;
@@ -1091,7 +1133,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
           sg = fmaf(r, r, sg);
         }
       }
-      double v[2] = {sd, sg};
+      FF v[2] = {{sd, 0.f}, {sg, 0.f}};
       block_sums<2>(v, ws);
       grid_arrive<2>(pk, bar, v);
     }
@@ -1167,22 +1209,26 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
 // ---------------------------------------------------------------------------
 // Steihaug's truncated CG (Nocedal & Wright Alg. 7.2, the inner solve of Algorithm 6) on
 // the low-rank B = Re(J^H J) in one persistent launch, laid out like the fixed-count CG
-// above: one cluster per image column, the column's res, dir and z in shared memory
-// (each block its half of iy), every block taking the same decisions from the same
-// grid-wide sums.  Per step:
-//   q = B dir on the column; dir.q over the grid (wait 1); the step decision (negative
-//   curvature or the trust boundary end CG with z on the boundary); z += c dir, and
-//   while CG continues res += c q with the block's parts of res.res, res.dir, z.res,
-//   z.dir, z.z; their grid sums (wait 2) give the tolerance and step-count test and beta;
-//   dir = -res + beta dir, and the sums of the next decision follow from the new
-//   direction's definition: res.dir' = -res.res + beta res.dir,
-//   dir'.dir' = res.res - 2 beta res.dir + beta^2 dir.dir, z.dir' = -z.res + beta z.dir.
+// above: one cluster per image column, the column's res, dir, z and q = B dir in shared
+// memory (each block its half of iy), every block taking the same decisions from the
+// same grid-wide sums.  The product is applied to the residual, u = B res, so that one
+// grid wait per step carries every sum (the direction's product follows by recurrence,
+// B dir' = -u + beta q, as in the pipelined CG above).  Before the loop q = B dir_0 and
+// one wait gives g.g and dir.q.  Per step:
+//   the step decision from dir.q (negative curvature or the trust boundary end CG with z
+//   on the boundary); z += c dir, and while CG continues res += c q; u = B res (not after
+//   the last step); the parts of res.res, res.dir, z.res, z.dir, z.z, res.u, dir.u,
+//   res.q go to one grid wait; the tolerance and step-count test and beta; then
+//   dir' = -res + beta dir, q' = -u + beta q, and the next decision's sums follow from
+//   the definitions: res.dir' = -res.res + beta res.dir,
+//   dir'.dir' = res.res - 2 beta res.dir + beta^2 dir.dir, z.dir' = -z.res + beta z.dir,
+//   dir'.q' = res.u - beta (dir.u + res.q) + beta^2 dir.q.
 // Each grid wait is followed by an exchange of the two blocks' wait flags, so both blocks
 // of a cluster leave together when one wait ran out (2 s: the error flag is set).
 // ---------------------------------------------------------------------------
 size_t st_column_smem_bytes(int ny, int R, int kmax) {
   const int hy = (ny + 1) / 2;
-  return column_smem_bytes(ny, R, kmax) + sizeof(float) * ((size_t)ny + 12 * (size_t)hy);
+  return column_smem_bytes(ny, R, kmax) + sizeof(float) * ((size_t)ny + 16 * (size_t)hy);
 }
 
 template <int N1>
@@ -1197,20 +1243,21 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
   cgp::cluster_group cl = cgp::this_cluster();
   const int crank = (int)cl.block_rank(), peer = crank ^ 1;
   constexpr int NY = 32 * N1, LD = NY + 1, HY = (NY + 1) / 2;
-  constexpr int NP = 5;  // partials per block and grid wait, at most
+  constexpr int NP = 8;  // partials per block and grid wait, at most
   const int RC = (R + 1) / 2, r0 = crank * RC, nr = min(R, r0 + RC) - r0;
   extern __shared__ float2 fsm[];
   float2* rt = fsm;
   float2* hs = rt + NY;
   float2* sbuf = hs + RC * LD;
   float2* sin = sbuf + kmax * NY;
-  float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // rows 0..3: dir (rows 2, 3 masked)
+  float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // rows 0..3: the product's input
   float* red4 = vox + 6 * NY;
   float* rin = red4 + 4 * NY;
   float* mk = rin + 4 * NY;  // [NY] mask of the column
-  float* const cr = mk + NY;  // [3 vectors res, dir, z][4 rows][HY] this block's half
+  float* const cr = mk + NY;  // [4 vectors res, dir, z, q][4 rows][HY] this block's half
   float* const cd = cr + 4 * HY;
   float* const cz = cr + 8 * HY;
+  float* const cq = cr + 12 * HY;
   const ColShared S = {rt, hs, sbuf, sin, vox, red4, rin, cl.map_shared_rank(sin, peer), cl.map_shared_rank(rin, peer)};
   float* vox_peer = cl.map_shared_rank(vox, peer);
   // the wait flags of the two blocks, exchanged after every grid wait: slot n mod 2 in
@@ -1218,55 +1265,70 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
   __shared__ int s_ok_peer[2];  // written by the peer
   int* ok_peer_remote = cl.map_shared_rank(s_ok_peer, peer);
   unsigned xch = 0;
-  __shared__ double ws[NP * kColWarps];
+  __shared__ FF ws[NP * kColWarps];
   __shared__ double lsc[S_COUNT];
   __shared__ int lsi[I_COUNT];
-  __shared__ int s_ok, s_go, s_cont;
+  __shared__ int s_ok, s_go, s_cont, s_prod;
   __shared__ float s_c, s_beta;
   const int tid = threadIdx.x, lane = tid & 31;
   const int ix = blockIdx.x >> 1;  // one column per cluster
   const int G = gridDim.x;
   const int ya = crank * HY, nh = min(NY, ya + HY) - ya;  // this block's half of iy: ya .. ya + nh
+  const int own = tid < nh;
+  const int iy = ya + min(tid, nh - 1);
   unsigned waits = 0;  // grid waits passed; wait n uses part[(n mod 2) NP G ..]
   for (int e = tid; e < NY; e += kColThreads) rt[e] = roots[e];
   cl.sync();  // both blocks run (before any store into the peer) and hold the roots
   const Fft32Lane ffw = fft32_lane<false>(rt, N1, lane), ffa = fft32_lane<true>(rt, N1, lane);
 
-  // rho and the mask of the whole column; res = g, dir = -g, z = 0 on this block's half
+  // rho and the mask of the whole column; res = g, dir = -g, z = 0 on this block's half;
+  // the product's input is dir (rows 2, 3 masked)
   int inside = 0;
-  for (int iy = tid; iy < NY; iy += kColThreads) {
-    const int j = iy * nx + ix;
+  for (int y = tid; y < NY; y += kColThreads) {
+    const int j = y * nx + ix;
     const float2 rh = rho[j];
     const float m = maskf[j];
-    vox[4 * NY + iy] = rh.x;
-    vox[5 * NY + iy] = rh.y;
-    mk[iy] = m;
+    vox[4 * NY + y] = rh.x;
+    vox[5 * NY + y] = rh.y;
+    mk[y] = m;
     inside |= m != 0.f;
   }
   inside = __syncthreads_or(inside);  // the same column in both blocks: the same answer
-  float sg = 0.f;
-  if (tid < nh) {
-    const int iy = ya + tid, j = iy * nx + ix;
-    const float m = mk[iy];
+  const float mq = mk[iy] * scale;
+  if (own) {
+    const int j = iy * nx + ix;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const float gv = grad[(size_t)k * nv + j];
       cr[k * HY + tid] = gv;
       cd[k * HY + tid] = -gv;
       cz[k * HY + tid] = 0.f;
-      const float dv = k >= 2 ? -gv * m : -gv;
+      const float dv = k >= 2 ? -gv * mk[iy] : -gv;
       vox[k * NY + iy] = dv;
       vox_peer[k * NY + iy] = dv;
-      sg = fmaf(gv, gv, sg);
     }
   }
-  // rr = g.g and the start of the decisions (the sums of the first step besides dir.B dir)
+  cl.sync();  // dir of both halves is in both blocks
+  // q = B dir_0, then g.g and dir.q
+  if (inside) column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
   {
-    double v[1] = {sg}, t[1];
-    block_sums<1>(v, ws);
-    double* pk = part + (size_t)(waits & 1) * NP * G;
-    grid_arrive<1>(pk, bar, v);
-    const bool ok = grid_wait_sums<1>(pk, bar, (unsigned)G * ++waits, err, ws, t);
+    float sg = 0.f, sq = 0.f;
+    if (own) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float qv = inside ? (red4[k * NY + iy] + rin[k * NY + iy]) * mq : 0.f;
+        const float gv = cr[k * HY + tid];
+        cq[k * HY + tid] = qv;
+        sg = fmaf(gv, gv, sg);
+        sq = fmaf(cd[k * HY + tid], qv, sq);
+      }
+    }
+    FF v[2] = {{sg, 0.f}, {sq, 0.f}};
+    double t[2];
+    block_sums<2>(v, ws);
+    FF* pk = reinterpret_cast<FF*>(part) + (size_t)(waits & 1) * NP * G;
+    grid_arrive<2>(pk, bar, v);
+    const bool ok = grid_wait_sums<2>(pk, bar, (unsigned)G * ++waits, err, ws, t);
     if (tid == 0) {
       const double rr = t[0];
       for (int k = 0; k < S_COUNT; ++k) lsc[k] = 0.0;
@@ -1274,6 +1336,7 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
       lsc[S_RR] = rr;
       lsc[S_RD] = -rr;
       lsc[S_DD] = rr;
+      lsc[S_DBD] = t[1];
       lsc[S_GNORM] = sqrt(rr);
       lsi[I_ACTIVE] = rr > 0.0 ? 1 : 0;
       lsi[I_EXIT] = rr > 0.0 ? MRSTAT_CG_MAX_ITER : MRSTAT_CG_ZERO_GRADIENT;
@@ -1282,44 +1345,22 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
       ok_peer_remote[xch & 1] = ok;
     }
   }
-  cl.sync();  // dir of both halves is in both blocks; the peer's flag has arrived
+  cl.sync();  // the peer's flag has arrived
   bool failed = !s_ok || !s_ok_peer[xch++ & 1];
   for (int step = 0; step < max_steps && s_go && !failed; ++step) {
-    // q = B dir
-    if (inside) column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
-    const float mq = mk[ya + min(tid, nh - 1)] * scale;
-    {
-      float sd = 0.f;
-      if (inside && tid < nh) {
-        const int iy = ya + tid;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sd = fmaf(cd[k * HY + tid], (red4[k * NY + iy] + rin[k * NY + iy]) * mq, sd);
-      }
-      double v[1] = {sd}, t[1];
-      block_sums<1>(v, ws);
-      double* pk = part + (size_t)(waits & 1) * NP * G;
-      grid_arrive<1>(pk, bar, v);
-      const bool ok = grid_wait_sums<1>(pk, bar, (unsigned)G * ++waits, err, ws, t);
-      if (tid == 0) {
-        lsc[S_DBD] = t[0];
-        if (ok) st_step(lsc, lsi, delta);
-        s_ok = ok;
-        s_cont = lsi[I_CONT];
-        s_c = (float)lsc[S_COEF];
-        ok_peer_remote[xch & 1] = ok;
-      }
-      cl.sync();  // the peer's flag has arrived
-      if (!s_ok || !s_ok_peer[xch++ & 1]) {
-        failed = true;
-        break;
-      }
+    // the step decision from dir.q (the same sums in every block)
+    if (tid == 0) {
+      st_step(lsc, lsi, delta);
+      s_cont = lsi[I_CONT];
+      s_c = (float)lsc[S_COEF];
+      s_prod = lsi[I_STEPS] < max_steps;  // a next step can follow: its product is needed
     }
-    // z += c dir; while continuing res += c q and the parts of the next sums
+    __syncthreads();
     const float c = s_c;
     const int cont = s_cont;
-    float a[NP] = {0.f, 0.f, 0.f, 0.f, 0.f};  // res.res, res.dir, z.res, z.dir, z.z
-    if (tid < nh) {
-      const int iy = ya + tid;
+    // z += c dir; while continuing res += c q, which is the next product's input
+    float a[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (own) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int e = k * HY + tid;
@@ -1327,9 +1368,11 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
         const float zv = fmaf(c, dv, cz[e]);
         cz[e] = zv;
         if (cont) {
-          const float qv = inside ? (red4[k * NY + iy] + rin[k * NY + iy]) * mq : 0.f;
-          const float rv = fmaf(c, qv, cr[e]);
+          const float rv = fmaf(c, cq[e], cr[e]);
           cr[e] = rv;
+          const float vv = k >= 2 ? rv * mk[iy] : rv;
+          vox[k * NY + iy] = vv;
+          vox_peer[k * NY + iy] = vv;
           a[0] = fmaf(rv, rv, a[0]);
           a[1] = fmaf(rv, dv, a[1]);
           a[2] = fmaf(zv, rv, a[2]);
@@ -1339,11 +1382,39 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
       }
     }
     if (!cont) break;  // negative curvature or the trust boundary: the same in every block
+    FF* pk = reinterpret_cast<FF*>(part) + (size_t)(waits & 1) * NP * G;
     {
-      double v[NP] = {a[0], a[1], a[2], a[3], a[4]}, t[NP];
-      block_sums<NP>(v, ws);
-      double* pk = part + (size_t)(waits & 1) * NP * G;
-      grid_arrive<NP>(pk, bar, v);
+      // the block's first five parts go out now (thread 0 stores them; the arrival after
+      // the product publishes them), so that nothing is held across the product
+      FF v[5] = {{a[0], 0.f}, {a[1], 0.f}, {a[2], 0.f}, {a[3], 0.f}, {a[4], 0.f}};
+      block_sums<5>(v, ws);
+      if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) pk[(size_t)k * G + blockIdx.x] = v[k];
+      }
+    }
+    cl.sync();  // res of both halves is in both blocks
+    // u = B res, and its parts res.u, dir.u, res.q
+    const bool prod = inside && s_prod;
+    float b[3] = {0.f, 0.f, 0.f};
+    if (prod) {
+      column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+      if (own) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int e = k * HY + tid;
+          const float uv = (red4[k * NY + iy] + rin[k * NY + iy]) * mq, rv = cr[e];
+          b[0] = fmaf(rv, uv, b[0]);
+          b[1] = fmaf(cd[e], uv, b[1]);
+          b[2] = fmaf(rv, cq[e], b[2]);
+        }
+      }
+    }
+    {
+      FF v[3] = {{b[0], 0.f}, {b[1], 0.f}, {b[2], 0.f}};
+      double t[NP];
+      block_sums<3>(v, ws);
+      grid_arrive<3>(pk + (size_t)5 * G, bar, v);
       const bool ok = grid_wait_sums<NP>(pk, bar, (unsigned)G * ++waits, err, ws, t);
       if (tid == 0) {
         float be = 0.f;
@@ -1351,11 +1422,12 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
           lsc[S_RR_NEW] = t[0];
           st_beta(lsc, lsi, rel_tol, max_steps);
           if (lsi[I_ACTIVE]) {
-            const double beta = lsc[S_BETA], rr = t[0], rd = t[1], dd = lsc[S_DD];
+            const double beta = lsc[S_BETA], rr = t[0], rd = t[1], dd = lsc[S_DD], dq = lsc[S_DBD];
             lsc[S_RD] = -rr + beta * rd;
             lsc[S_DD] = rr - 2.0 * beta * rd + beta * beta * dd;
             lsc[S_ZD] = -t[2] + beta * t[3];
             lsc[S_ZZ] = t[4];
+            lsc[S_DBD] = t[5] - beta * (t[6] + t[7]) + beta * beta * dq;
             be = (float)beta;
           }
         }
@@ -1364,27 +1436,27 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
         s_beta = be;
         ok_peer_remote[xch & 1] = ok;
       }
-      __syncthreads();
+      cl.sync();  // the peer's flag has arrived
+      if (!s_ok || !s_ok_peer[xch++ & 1]) {
+        failed = true;
+        break;
+      }
     }
-    // dir = -res + beta dir, into both blocks' voxel data
-    if (s_go && tid < nh) {
-      const int iy = ya + tid;
-      const float be = s_beta, m = mk[iy];
+    // dir' = -res + beta dir, q' = -u + beta q
+    if (s_go && own) {
+      const float be = s_beta;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int e = k * HY + tid;
-        const float dv = fmaf(be, cd[e], -cr[e]);
-        cd[e] = dv;
-        const float vv = k >= 2 ? dv * m : dv;
-        vox[k * NY + iy] = vv;
-        vox_peer[k * NY + iy] = vv;
+        const float uv = prod ? (red4[k * NY + iy] + rin[k * NY + iy]) * mq : 0.f;
+        cd[e] = fmaf(be, cd[e], -cr[e]);
+        cq[e] = fmaf(be, cq[e], -uv);
       }
     }
-    cl.sync();  // the new dir of both halves is in both blocks; the peer's flag has arrived
-    if (!s_ok || !s_ok_peer[xch++ & 1]) failed = true;
+    __syncthreads();
   }
-  if (tid < nh) {
-    const int j = (ya + tid) * nx + ix;
+  if (own) {
+    const int j = iy * nx + ix;
 #pragma unroll
     for (int k = 0; k < 4; ++k) zout[(size_t)k * nv + j] = cz[k * HY + tid];
   }
@@ -2006,10 +2078,10 @@ bool lowrank_steihaug_persistent(Plan* p, const float* g, float* z, double delta
   *err = cudaSuccess;
   if (p->lr == nullptr || !p->lr->active || !p->lr->column_path || p->cg_bar == nullptr || max_steps < 0)
     return false;
-  // two parity buffers of five partials per block in p->red; a grid counter that reaches
-  // 2 nx (2 max_steps + 1)
+  // two parity buffers of eight partials per block in p->red; a grid counter that
+  // reaches 2 nx (max_steps + 1)
   const int64_t G = 2 * (int64_t)p->nx;
-  if (10 * G > kRedSlots || G * (2 * (int64_t)max_steps + 1) >= (int64_t)1 << 31) return false;
+  if (16 * G > kRedSlots || G * ((int64_t)max_steps + 1) >= (int64_t)1 << 31) return false;
   const SteihaugArgs a = {delta, rel_tol, max_steps, sc, si};
   cudaError_t e = launch_st_columns(p, g, z, a, false, st);
   if (e != cudaSuccess) {
