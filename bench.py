@@ -68,8 +68,9 @@ NCU_TRAFFIC = {
     # profiles/tc_gemm_persistent_brain224.md
     ("xdft", "0728f575d9d96a3d"): 13670656.0,
     ("xdft_adj", "0728f575d9d96a3d"): 13668608.0,
-    # profiles/lr_jhjv_column_kernel_brain224.md (warm L2, as in the CG loop)
-    ("jhw_dot", "5ef12bc0a000a478"): 512.0,
+    # profiles/lr_cg_columns_kernel_brain224.md: one persistent CG launch of 30 products
+    # read 20 997 120 B and wrote 17 152 B (caches flushed before it), per product
+    ("jhw_dot", "22bc61d2bc0fbdf9"): (20997120.0 + 17152.0) / 30,
 }
 
 
