@@ -129,7 +129,8 @@ int mrstat_plan_info(const mrstat_plan* plan, mrstat_plan_info_t* info);
 /*
  * Wait for the plan's device work and report device-side failures: returns
  * MRSTAT_ERR_TIMEOUT (and clears the flag) when a tensor-core kernel stopped because a
- * bounded wait on its pipeline barriers ran out; its outputs are then undefined.
+ * bounded wait on its pipeline barriers ran out, or a persistent CG launch because its
+ * bounded grid wait ran out (2 s); its outputs are then undefined.
  * Synchronises the plan's device.
  */
 int mrstat_plan_check(mrstat_plan* plan);
@@ -380,7 +381,8 @@ int mrstat_set_slice_profile(mrstat_plan* plan, const mrstat_slice_profile* prof
  * carried by recurrence, so the grid-wide inner products overlap the next product);
  * also textbook CG's iterates in exact arithmetic, with `iters` products in all.  An
  * iteration whose curvature p.Hp is not positive, or whose residual is exactly zero,
- * freezes x for the remaining iterations.
+ * freezes x for the remaining iterations.  A persistent launch whose grid wait ran out
+ * sets the flag mrstat_plan_check reports.
  *   rhs, x: device float [npar][nv].  iters >= 0.
  * Errors: INVALID_ARG, NOT_LINEARIZED, CUDA.
  */
@@ -426,8 +428,13 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
  * solution.
  *
  * Every CG scalar lives on the device in float64; the host synchronises once per
- * outer iteration to evaluate the trust-region ratio.  On return the plan holds the
- * linearisation at the returned alpha.
+ * outer iteration to evaluate the trust-region ratio.  Where the CG matrix is the
+ * low-rank one (hessian = 1 or the surrogate phase) on a fully sampled readout with
+ * ny = 32 N1 (N1 <= 8) and every image column's pair of blocks fits on the device at
+ * once, each Steihaug solve is one persistent launch (the residual's product carries the
+ * direction's by recurrence; the same decisions in exact arithmetic); if its grid waits
+ * run out (2 s) the call returns TIMEOUT.  On return the plan holds the linearisation
+ * at the returned alpha.
  *   d:      device float [ntr][nkx][2] measured k-space data.
  *   alpha:  device float [npar][nv], initial guess in, estimate out (B1 in row 4 when
  *           estimated; reflected into [b1_min, b1_max] like T1 and T2).
@@ -437,7 +444,7 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
  *   report: host struct filled with the per-iteration history (may be NULL).
  * Errors: INVALID_ARG (bad pointers or options), UNSUPPORTED (see above),
  * OUT_OF_MEMORY (the solver's work space: a second set of time courses plus a few
- * vectors), CUDA.
+ * vectors), TIMEOUT (a bounded device wait ran out), CUDA.
  */
 #define MRSTAT_GN_MAX_OUTER 64
 

@@ -972,9 +972,16 @@ __device__ __forceinline__ void grid_arrive(FF* part, unsigned* bar, const FF (&
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) part[(size_t)k * gridDim.x + blockIdx.x] = v[k];
-    __threadfence();
-    atomicAdd(bar, 1u);
+    // a release reduction: the partials (and the earlier stores of this thread) are
+    // visible to whoever acquires a count that includes this arrival
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
   }
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
 // Thread 0 waits until the grid counter reaches `target` (bounded), then the block adds
@@ -985,15 +992,14 @@ __device__ bool grid_wait_sums(const FF* part, const unsigned* bar, unsigned tar
                                double (&out)[NV]) {
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
-    const volatile unsigned* vb = bar;
     int ok = 1;
-    if (*vb < target) {
+    if (ld_acquire(bar) < target) {
       // polls back off (32 ns doubling to 512 ns): blocks that arrive early, e.g. those
       // of image columns outside the mask, neither take issue slots from the SM's other
       // blocks nor flood the counter's L2 slice while the rest compute
       const uint64_t t0 = col_global_ns();
       uint32_t spins = 0, ns = 32;
-      while (*vb < target) {
+      while (ld_acquire(bar) < target) {
         __nanosleep(ns);
         if (ns < 512) ns <<= 1;
         if ((++spins & 63u) == 0 && col_global_ns() - t0 > kGridWaitNs) {
@@ -1003,23 +1009,23 @@ __device__ bool grid_wait_sums(const FF* part, const unsigned* bar, unsigned tar
         }
       }
     }
-    __threadfence();
     s_ok = ok;
   }
-  __syncthreads();
-  const int G = gridDim.x;
+  __syncthreads();  // the acquire in thread 0 orders the other threads' reads after it
+  const int G = gridDim.x;  // at most 2 kColThreads (checked at launch)
   FF acc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = FF{0.f, 0.f};
-  // other blocks wrote the partials: read them from L2 (ld.global.cg), not from L1
+  // other blocks wrote the partials: read them from L2 (ld.global.cg), not from L1; both
+  // blocks of a thread are loaded before any is added
   const float2* vp = reinterpret_cast<const float2*>(part);
-  for (int i = threadIdx.x; i < G; i += kColThreads) {
+  const int i0 = threadIdx.x, i1 = threadIdx.x + kColThreads;
+  float2 t0v[NV], t1v[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      const float2 t = __ldcg(vp + (size_t)k * G + i);
-      acc[k] = ff_add(acc[k], FF{t.x, t.y});
-    }
+  for (int k = 0; k < NV; ++k) {
+    t0v[k] = i0 < G ? __ldcg(vp + (size_t)k * G + i0) : make_float2(0.f, 0.f);
+    t1v[k] = i1 < G ? __ldcg(vp + (size_t)k * G + i1) : make_float2(0.f, 0.f);
   }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = ff_add(FF{t0v[k].x, t0v[k].y}, FF{t1v[k].x, t1v[k].y});
   block_sums<NV>(acc, ws);
 #pragma unroll
   for (int k = 0; k < NV; ++k) out[k] = (double)acc[k].hi + (double)acc[k].lo;
@@ -1118,21 +1124,23 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   }
   cl.sync();
 
-  double gam_prev = 0.0, alpha_prev = 0.0;
+  // the thread's parts of delta = <w, r> and gamma = <r, r> (formed with every update)
+  float sd = 0.f, sg = 0.f;
+  if (tid < nh) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float r = cr[k * HY + tid];
+      sd = fmaf(r, vox[k * NY + ya + tid], sd);
+      sg = fmaf(r, r, sg);
+    }
+  }
+  // pq_prev = p.Bp of the previous iteration: beta gamma / alpha_prev = beta^2 pq_prev
+  double gam_prev = 0.0, pq_prev = 0.0;
   bool frozen = false;
   for (int it = 0; it < iters; ++it) {
     FF* pk = reinterpret_cast<FF*>(part) + (size_t)(it & 1) * 2 * G;
     {
-      // the block's parts of gamma = <r, r> and delta = <w, r>, then arrive (no wait)
-      float sd = 0.f, sg = 0.f;
-      if (tid < nh) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float r = cr[k * HY + tid];
-          sd = fmaf(r, vox[k * NY + ya + tid], sd);
-          sg = fmaf(r, r, sg);
-        }
-      }
+      // the block's parts of delta and gamma, then arrive (no wait)
       FF v[2] = {{sd, 0.f}, {sg, 0.f}};
       block_sums<2>(v, ws);
       grid_arrive<2>(pk, bar, v);
@@ -1154,15 +1162,14 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
         double beta = 0.0, pq = delta;
         if (it > 0) {
           beta = gamma / gam_prev;
-          pq = delta - beta * gamma / alpha_prev;
+          pq = delta - beta * beta * pq_prev;
         }
         apply = !frozen && pq > 0.0 && gamma > 0.0;
         if (apply) {
-          const double alpha = gamma / pq;
-          al = (float)alpha;
+          al = (float)(gamma / pq);
           be = (float)beta;
           gam_prev = gamma;
-          alpha_prev = alpha;
+          pq_prev = pq;
         } else {
           frozen = true;
         }
@@ -1192,6 +1199,17 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
         const float wn = fmaf(-al, zv, wv);
         vox[k * NY + iy] = wn;
         vox_peer[k * NY + iy] = wn;
+      }
+    }
+    // the next iteration's parts from r and w as they now stand
+    sd = 0.f;
+    sg = 0.f;
+    if (tid < nh) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float r = cr[k * HY + tid];
+        sd = fmaf(r, vox[k * NY + ya + tid], sd);
+        sg = fmaf(r, r, sg);
       }
     }
     cl.sync();  // the new w of both halves is in both blocks; the peer's flag has arrived
@@ -2081,7 +2099,8 @@ bool lowrank_steihaug_persistent(Plan* p, const float* g, float* z, double delta
   // two parity buffers of eight partials per block in p->red; a grid counter that
   // reaches 2 nx (max_steps + 1)
   const int64_t G = 2 * (int64_t)p->nx;
-  if (16 * G > kRedSlots || G * ((int64_t)max_steps + 1) >= (int64_t)1 << 31) return false;
+  if (16 * G > kRedSlots || G > 2 * kColThreads || G * ((int64_t)max_steps + 1) >= (int64_t)1 << 31)
+    return false;
   const SteihaugArgs a = {delta, rel_tol, max_steps, sc, si};
   cudaError_t e = launch_st_columns(p, g, z, a, false, st);
   if (e != cudaSuccess) {
@@ -2117,7 +2136,7 @@ bool lowrank_cg_fixed_persistent(Plan* p, const float* rhs, float* x, int iters,
   // two parity buffers of two partials per block in p->red, and a grid counter that
   // reaches 2 nx iters
   const int64_t G = 2 * (int64_t)p->nx;
-  if (4 * G > kRedSlots || G * iters >= (int64_t)1 << 31) return false;
+  if (4 * G > kRedSlots || G > 2 * kColThreads || G * iters >= (int64_t)1 << 31) return false;
   cudaError_t e = launch_cg_columns(p, rhs, x, iters, false, st);
   if (e != cudaSuccess) {
     cudaGetLastError();  // does not fit (or cannot be asked): the caller iterates launch by launch

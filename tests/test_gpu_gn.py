@@ -373,3 +373,45 @@ def test_lowrank_hessian_steihaug_on_the_column_path_matches_oracle(mr, inner, d
     assert rep["cg_steps"][0] == steps
     assert rep["accepted"][0]
     assert metrics.relerr(a_gpu - a0, solver.apply_bounds(a0 + z, solver.GNOptions()) - a0) < 1e-3
+
+
+def test_lowrank_hessian_steihaug_column_path_converges_under_a_mask(mr):
+    """The persistent Steihaug launch on a 48 x 64 grid with rank 24, whole image
+    columns outside the mask, and a relative tolerance that ends CG early (exit
+    'converged'): against the oracle's Steihaug CG on the projected model."""
+    seq = synth.make_sequence(48, 64, 5, 7.8, 3.9, seed=4)
+    rng = np.random.default_rng(14)
+    t1 = np.exp(rng.uniform(np.log(300), np.log(2500), (64, 48)))
+    t2 = np.exp(rng.uniform(np.log(30), np.log(250), (64, 48)))
+    rho = rng.uniform(0.6, 1.0, (64, 48)) * np.exp(1j * rng.uniform(0, 0.5, (64, 48)))
+    truth = f32(np.stack([np.log(t1.ravel()), np.log(t2.ravel()), rho.real.ravel(), rho.imag.ravel()]))
+    mask = rng.random((64, 48)) > 0.1
+    mask[:, :6] = False
+    mask[:, 30:33] = False
+    mask = mask.ravel()
+    d = synth.add_noise(model.forward(seq, truth), 50.0, 8).astype(np.complex64).astype(np.complex128)
+    a0 = f32(truth + 0.03 * synth.random_params(seq.nv, 9))
+    delta = 0.1 * float(np.linalg.norm(a0 * mask[None]))
+    with mr.Plan(seq) as plan:
+        U = _basis(plan, 24)
+        plan.lowrank_set_basis(U)
+        plan.profile_start(kernels=("jhw_dot",))
+        a = cuda(a0)
+        rep = plan.gn_solve(cuda(d, torch.complex64), a, mask=cuda(mask.astype(np.uint8), torch.uint8),
+                            outer_iters=1, inner_iters=40, hessian=1, cg_rel_tol=0.1)
+        prof = plan.profile_stop()
+        plan.check()
+        a_gpu = a.cpu().numpy()
+        Uh = U.cpu().numpy().astype(np.float64)
+    assert prof["jhw_dot"]["launches"] <= 2
+    lin = model.linearize(seq, a0, mask=mask)
+    g = -model.jhw(lin, d - model.signal(lin))
+    lin_p = model.project_onto_basis(lin, Uh)
+    z, mchange, steps, why = solver.steihaug_cg(lambda v: model.gauss_newton_product(lin_p, v), g, delta, 40, 0.1)
+    assert why == "converged"
+    assert rep["cg_exit"][0] == why
+    assert rep["cg_steps"][0] == steps
+    assert rep["accepted"][0]
+    trial = np.where(mask[None], solver.apply_bounds(a0 + z, solver.GNOptions()), a0)
+    assert metrics.relerr(a_gpu - a0, trial - a0) < 1e-3
+    assert np.array_equal(a_gpu[:, ~mask], a0[:, ~mask].astype(np.float32))

@@ -186,3 +186,48 @@ def test_lowrank_full_size_sampled_jhw(mr):
                       np.real(np.sum(np.conj(rho[None] * sim["dm_dlnT2"]) * W, 0)),
                       np.real(np.sum(np.conj(sim["m"]) * W, 0)), np.real(np.sum(np.conj(1j * sim["m"]) * W, 0))])
     assert metrics.relerr(g, exact) < 1e-2
+
+
+@pytest.mark.parametrize("nx,ny,rank,holes", [(40, 96, 24, True), (33, 32, 8, False)])
+def test_persistent_cg_shapes_match_oracle_cg(mr, nx, ny, rank, holes):
+    """The persistent CG launch on other column shapes: 96 = 3 x 32 rows with rank 24
+    (twelve basis functions per block of a cluster), whole image columns and
+    random voxels outside the mask; and 32 rows (one 32-point FFT, half-columns of 16)
+    with an odd number of columns.  Six iterations against textbook CG in float64 on the
+    projected oracle model; one launch carries all products."""
+    seq = synth.make_sequence(nx, ny, 4, 7.8, 3.9, seed=11)
+    alpha = random_phantom(nx, ny, 12)
+    train = training_set(400, 3)
+    U = f32(model.time_basis(seq, np.exp(train[0]), np.exp(train[1]), rank)[0])
+    mask = np.ones((ny, nx), bool)
+    if holes:
+        mask = np.random.default_rng(13).random((ny, nx)) > 0.2
+        mask[:, :5] = False
+        mask[:, 20:23] = False
+    mask = mask.ravel()
+    lin = model.project_onto_basis(model.linearize(seq, alpha, mask=mask), U)
+    b = model.jhw(lin, synth.random_kspace(seq.ntr, seq.nkx, 41))
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = float(np.sum(r * r))
+    for _ in range(6):
+        q = model.gauss_newton_product(lin, p)
+        a = rr / float(np.sum(p * q))
+        x = x + a * p
+        r = r - a * q
+        rr_new = float(np.sum(r * r))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    with mr.Plan(seq) as plan:
+        plan.lowrank_set_basis(cuda(U))
+        plan.lowrank_linearize(cuda(alpha), mask=cuda(mask.astype(np.uint8), torch.uint8))
+        plan.profile_start(kernels=("jhw_dot", "vector"))
+        xg = plan.cg_fixed(cuda(b), 6).cpu().numpy()
+        prof = plan.profile_stop()
+        plan.check()
+    # one persistent launch (counted as six products) and no per-iteration vector launches
+    assert prof["jhw_dot"]["launches"] == 6
+    assert prof["vector"]["launches"] <= 1
+    assert metrics.relerr(xg, x) < 1e-4
+    assert np.all(xg[:, ~mask] == 0)
