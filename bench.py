@@ -176,9 +176,13 @@ def run_reference(args, rank: int):
               f"and the first {rows} of {seq.ny} image rows of {args.workload}, extrapolated linearly in TRs "
               f"and rows to linearise + {args.cg_iters} products")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "products/s",
-            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "cg_iters": args.cg_iters},
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {seq.nx}x{seq.ny} grid, {seq.ntr} TRs, {seq.nkx} readout "
+                                   "samples, exact Bloch model (the oracle)",
+                       "form": "oracle", "step": f"linearize + {args.cg_iters} CG iterations (one J^H J v each)",
+                       "cg_iters": args.cg_iters, "parallelism": "rank 0 on the host cores"},
             "cpu_baseline": {"value": value, "unit": "products/s", "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
