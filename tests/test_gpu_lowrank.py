@@ -188,14 +188,17 @@ def test_lowrank_full_size_sampled_jhw(mr):
     assert metrics.relerr(g, exact) < 1e-2
 
 
-@pytest.mark.parametrize("nx,ny,rank,holes", [(40, 96, 24, True), (33, 32, 8, False)])
-def test_persistent_cg_shapes_match_oracle_cg(mr, nx, ny, rank, holes):
+@pytest.mark.parametrize("nx,ny,rank,holes,fills", [(40, 96, 24, True, 4), (33, 32, 8, False, 4),
+                                                     (24, 224, 32, True, 8)])
+def test_persistent_cg_shapes_match_oracle_cg(mr, nx, ny, rank, holes, fills):
     """The persistent CG launch on other column shapes: 96 = 3 x 32 rows with rank 24
     (twelve basis functions per block of a cluster), whole image columns and
     random voxels outside the mask; and 32 rows (one 32-point FFT, half-columns of 16)
-    with an odd number of columns.  Six iterations against textbook CG in float64 on the
-    projected oracle model; one launch carries all products."""
-    seq = synth.make_sequence(nx, ny, 4, 7.8, 3.9, seed=11)
+    with an odd number of columns; and 224 rows with eight TRs per phase-encode line (the
+    largest shared-memory layout: two blocks per SM, enough for these 24 columns).  Six
+    iterations against textbook CG in float64 on the projected oracle model; one launch
+    carries all products."""
+    seq = synth.make_sequence(nx, ny, fills, 7.8, 3.9, seed=11)
     alpha = random_phantom(nx, ny, 12)
     train = training_set(400, 3)
     U = f32(model.time_basis(seq, np.exp(train[0]), np.exp(train[1]), rank)[0])
