@@ -136,6 +136,16 @@ int mrstat_plan_info(const mrstat_plan* plan, mrstat_plan_info_t* info);
 int mrstat_plan_check(mrstat_plan* plan);
 
 /*
+ * Test hook for the failure path of the persistent CG and Steihaug launches: with
+ * block >= 0, block `block` of the next persistent launches withholds its first arrival
+ * at the grid counter, so every block's bounded grid wait (2 s) runs out; the launch
+ * ends early, x (or the Steihaug step) is undefined, and mrstat_plan_check /
+ * mrstat_gn_solve report MRSTAT_ERR_TIMEOUT.  block < 0 turns it off (the default).
+ * Nothing faults or hangs.  Errors: INVALID_ARG (NULL plan).
+ */
+int mrstat_plan_inject_grid_stall(mrstat_plan* plan, int32_t block);
+
+/*
  * Linearise the model at alpha (Algorithm 2 step 1 for every voxel, with the
  * forward-mode derivatives of Supporting Information S2): runs the Bloch recursion
  * of every voxel and caches m_y and dm_y/dln T1, dm_y/dln T2 at every echo, plus

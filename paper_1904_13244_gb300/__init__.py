@@ -18,6 +18,7 @@ import torch
 from . import _binding as _b
 from ._binding import (MrstatError, MRSTAT_FORM_PLAIN_FP32, MRSTAT_FORM_SPLIT_BF16, MRSTAT_ESTIMATE_B1,  # noqa: F401
                        mrstat_plan_create, mrstat_plan_destroy, mrstat_plan_info, mrstat_linearize,
+                       mrstat_plan_inject_grid_stall,
                        mrstat_forward, mrstat_jvp, mrstat_jhw, mrstat_timecourses, mrstat_dot,
                        mrstat_cg_fixed, mrstat_status_string, mrstat_last_error,
                        mrstat_profile_start, mrstat_profile_stop, mrstat_gn_default_opts,
@@ -75,6 +76,11 @@ class Plan:
     def check(self):
         """Synchronise and raise if a device-side bounded wait gave up."""
         mrstat_plan_check(self._h)
+
+    def inject_grid_stall(self, block=-1):
+        """Test hook: block `block` of the persistent CG / Steihaug launches withholds its
+        first grid arrival, so their bounded waits run out (TIMEOUT); -1 turns it off."""
+        mrstat_plan_inject_grid_stall(self._h, block)
 
     # -- products --
     def _kspace(self, out):

@@ -89,6 +89,7 @@ _SIGS = {
     "mrstat_plan_destroy": [ctypes.c_void_p],
     "mrstat_plan_info": [ctypes.c_void_p, ctypes.POINTER(mrstat_plan_info_t)],
     "mrstat_plan_check": [ctypes.c_void_p],
+    "mrstat_plan_inject_grid_stall": [ctypes.c_void_p, ctypes.c_int32],
     "mrstat_set_slice_profile": [ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_linearize": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "mrstat_forward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -242,6 +243,10 @@ def mrstat_plan_info(plan) -> dict:
 
 def mrstat_plan_check(plan):
     _check(load().mrstat_plan_check(plan), "mrstat_plan_check")
+
+
+def mrstat_plan_inject_grid_stall(plan, block):
+    _check(load().mrstat_plan_inject_grid_stall(plan, int(block)), "mrstat_plan_inject_grid_stall")
 
 
 def mrstat_linearize(plan, alpha, b1=None, mask=None, stream=None):

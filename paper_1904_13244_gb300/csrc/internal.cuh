@@ -66,7 +66,8 @@ struct Plan {
   float* cg_p = nullptr;    // [npar][nv]
   float* cg_q = nullptr;    // [npar][nv]
   float* cg_w = nullptr;    // [npar][nv] Re(J^H J) r
-  unsigned* cg_bar = nullptr;  // [2] grid barrier of the persistent CG (arrivals, generation)
+  unsigned* cg_bar = nullptr;  // [2] grid counter of the persistent column launches
+  int grid_stall_block = -1;   // test hook: this block of those launches withholds an arrival
   float2* cg_jv = nullptr;  // [ntr][nkx]
   double* cg_s = nullptr;   // CG scalars, 4 per iteration
   int* cg_frozen = nullptr; // CG stop flag

@@ -1043,7 +1043,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
                      const float* __restrict__ coefT, const float2* __restrict__ rho,
                      const float* __restrict__ maskf, const float2* __restrict__ roots,
                      const float* __restrict__ UgS, int kmax, int nx, int nv, int R, float scale, int iters,
-                     double* part, unsigned* bar, double* sums, int* err) {
+                     int stall_block, double* part, unsigned* bar, double* sums, int* err) {
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
   const int crank = (int)cl.block_rank(), peer = crank ^ 1;
@@ -1140,10 +1140,11 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   for (int it = 0; it < iters; ++it) {
     FF* pk = reinterpret_cast<FF*>(part) + (size_t)(it & 1) * 2 * G;
     {
-      // the block's parts of delta and gamma, then arrive (no wait)
+      // the block's parts of delta and gamma, then arrive (no wait); a block named by the
+      // test hook withholds its first arrival, and every wait runs out
       FF v[2] = {{sd, 0.f}, {sg, 0.f}};
       block_sums<2>(v, ws);
-      grid_arrive<2>(pk, bar, v);
+      if (it > 0 || (int)blockIdx.x != stall_block) grid_arrive<2>(pk, bar, v);
     }
     // q = B w while the other blocks arrive (not needed in the last iteration)
     const bool prod = inside && it + 1 < iters;
@@ -1256,7 +1257,7 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
                            const float2* __restrict__ rho, const float* __restrict__ maskf,
                            const float2* __restrict__ roots, const float* __restrict__ UgS, int kmax, int nx, int nv,
                            int R, float scale, double delta, double rel_tol, int max_steps, double* sc, int* si,
-                           double* part, unsigned* bar, int* err) {
+                           int stall_block, double* part, unsigned* bar, int* err) {
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
   const int crank = (int)cl.block_rank(), peer = crank ^ 1;
@@ -1345,7 +1346,7 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
     double t[2];
     block_sums<2>(v, ws);
     FF* pk = reinterpret_cast<FF*>(part) + (size_t)(waits & 1) * NP * G;
-    grid_arrive<2>(pk, bar, v);
+    if ((int)blockIdx.x != stall_block) grid_arrive<2>(pk, bar, v);  // the test hook withholds it
     const bool ok = grid_wait_sums<2>(pk, bar, (unsigned)G * ++waits, err, ws, t);
     if (tid == 0) {
       const double rr = t[0];
@@ -2038,7 +2039,8 @@ static cudaError_t launch_cg_columns_t(Plan* p, const float* rhs, float* x, int 
   return launch_persistent_columns(p, lr_cg_columns_kernel<N1>, sm, launch, st, L.dft_small, rhs, x,
                                    (const float*)L.coefT, (const float2*)p->rho, (const float*)p->maskf,
                                    (const float2*)p->roots, (const float*)L.UgS, L.ky_count_max, p->nx, p->nv, L.R,
-                                   (float)p->nx, iters, p->red, p->cg_bar, p->cg_s, p->dev_err);
+                                   (float)p->nx, iters, p->grid_stall_block, p->red, p->cg_bar, p->cg_s,
+                                   p->dev_err);
 }
 
 static cudaError_t launch_cg_columns(Plan* p, const float* rhs, float* x, int iters, bool launch, cudaStream_t st) {
@@ -2069,8 +2071,8 @@ static cudaError_t launch_st_columns_t(Plan* p, const float* g, float* z, const 
   return launch_persistent_columns(p, lr_steihaug_columns_kernel<N1>, sm, launch, st, L.dft_small, g, z,
                                    (const float*)L.coefT, (const float2*)p->rho, (const float*)p->maskf,
                                    (const float2*)p->roots, (const float*)L.UgS, L.ky_count_max, p->nx, p->nv, L.R,
-                                   (float)p->nx, a.delta, a.rel_tol, a.max_steps, a.sc, a.si, p->red, p->cg_bar,
-                                   p->dev_err);
+                                   (float)p->nx, a.delta, a.rel_tol, a.max_steps, a.sc, a.si, p->grid_stall_block,
+                                   p->red, p->cg_bar, p->dev_err);
 }
 
 static cudaError_t launch_st_columns(Plan* p, const float* g, float* z, const SteihaugArgs& a, bool launch,

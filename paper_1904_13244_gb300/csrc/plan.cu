@@ -323,6 +323,12 @@ const char* mrstat_status_string(int status) {
 
 const char* mrstat_last_error(void) { return g_last_error.c_str(); }
 
+int mrstat_plan_inject_grid_stall(mrstat_plan* plan, int32_t block) {
+  if (plan == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan");
+  plan->grid_stall_block = block < 0 ? -1 : block;
+  return MRSTAT_OK;
+}
+
 int mrstat_plan_check(mrstat_plan* plan) {
   if (plan == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan");
   DeviceGuard g(plan->device);
@@ -332,7 +338,7 @@ int mrstat_plan_check(mrstat_plan* plan) {
   if (e != cudaSuccess) return cuda_fail(e, "plan check");
   if (flag) {
     cudaMemset(plan->dev_err, 0, sizeof(int));
-    return fail(MRSTAT_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on its pipeline barriers");
+    return fail(MRSTAT_ERR_TIMEOUT, "a kernel's bounded wait ran out (tensor-core pipeline or grid counter)");
   }
   return MRSTAT_OK;
 }

@@ -234,3 +234,40 @@ def test_persistent_cg_shapes_match_oracle_cg(mr, nx, ny, rank, holes, fills):
     assert prof["vector"]["launches"] <= 1
     assert metrics.relerr(xg, x) < 1e-4
     assert np.all(xg[:, ~mask] == 0)
+
+
+def test_persistent_launch_wait_runs_out_and_the_plan_recovers(mr):
+    """Failure path of the persistent launches, without a fault: with the test hook one
+    block withholds its first arrival at the grid counter, every block's bounded wait runs
+    out (2 s), the CG launch ends and mrstat_plan_check reports TIMEOUT (and clears the
+    flag); the Gauss-Newton solve reports TIMEOUT from its Steihaug launch.  With the hook
+    off the same plan then solves correctly."""
+    import time
+    seq = synth.make_sequence(64, 64, 5, 7.8, 3.9, seed=5)
+    alpha = random_phantom(64, 64, 7)
+    train = training_set(400, 2)
+    U = f32(model.time_basis(seq, np.exp(train[0]), np.exp(train[1]), 16)[0])
+    lin = model.project_onto_basis(model.linearize(seq, alpha), U)
+    b = model.jhw(lin, synth.random_kspace(seq.ntr, seq.nkx, 40))
+    q = model.gauss_newton_product(lin, b)
+    x1 = (float(np.sum(b * b)) / float(np.sum(b * q))) * b  # one CG iteration from zero
+    with mr.Plan(seq) as plan:
+        plan.lowrank_set_basis(cuda(U))
+        plan.lowrank_linearize(cuda(alpha))
+        plan.inject_grid_stall(5)
+        t0 = time.perf_counter()
+        plan.cg_fixed(cuda(b), 3)
+        with pytest.raises(mr.MrstatError) as e:
+            plan.check()
+        assert e.value.status == 6  # MRSTAT_ERR_TIMEOUT
+        assert time.perf_counter() - t0 > 1.5
+        d = synth.add_noise(model.forward(seq, alpha), 50.0, 3).astype(np.complex64)
+        with pytest.raises(mr.MrstatError) as e:
+            plan.gn_solve(cuda(d, torch.complex64), cuda(alpha), outer_iters=1, inner_iters=5, hessian=1)
+        assert e.value.status == 6
+        plan.inject_grid_stall(-1)
+        plan.check()
+        plan.lowrank_linearize(cuda(alpha))
+        xg = plan.cg_fixed(cuda(b), 1).cpu().numpy()
+        plan.check()
+    assert metrics.relerr(xg, x1) < 1e-5
