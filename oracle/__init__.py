@@ -28,6 +28,10 @@ itself: the Freeman-Hill bSSFP steady state, pure inversion recovery, free
 induction decay, complex-step and central finite-difference derivatives,
 numpy.fft on piecewise-constant time courses, exact linearity in rho, the
 adjoint identity, brute-force double sums on tiny grids and noiseless recovery
-of ground-truth maps.
+of ground-truth maps.  The low-rank model (model.project_onto_basis,
+model.time_basis) is pinned to the identity at full rank, numpy's least-squares
+solver, the algebra of orthogonal projectors, Eckart-Young optimality and the
+Freeman-Hill steady-state pattern; the bound reflections (solver.reflect_into_bounds,
+solver.apply_bounds) to hand-computed values (tests/test_oracle_lowrank.py).
 """
 from . import bloch, encoding, model, solver, metrics  # noqa: F401
