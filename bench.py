@@ -90,6 +90,9 @@ def parse_args():
     ap.add_argument("--rank", type=int, default=32)
     ap.add_argument("--no-recon", action="store_true")
     ap.add_argument("--no-shapes", action="store_true")
+    ap.add_argument("--clock-log", default=os.environ.get("MRSTAT_CLOCK_LOG"),
+                    help="CSV file for the nvidia-smi clock samples of the timed region "
+                         "(default: a file in the system temp directory)")
     ap.add_argument("--profile-recon", default=None, choices=["plain", "lowrank", "surrogate"],
                     help="run that reconstruction once more first and bracket the timed one with "
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off)")
@@ -224,6 +227,37 @@ def train_surrogate(mr, torch, plan, rank, hidden, steps, n_train=262144, batch=
 
 
 # ---------------------------------------------------------------------------
+# the timed solve's result, checked after the timed region
+# ---------------------------------------------------------------------------
+def check_cg(torch, plan, rhs, x, iters):
+    """After the timed steps: no device wait ran out (mrstat_plan_check raises), every CG
+    iteration was applied, and x of the last step against CG run product by product
+    through mrstat_jhjv at the same linearisation with float64 vectors and scalars."""
+    plan.check()
+    applied = plan.cg_applied()
+    xr = torch.zeros_like(rhs, dtype=torch.float64)
+    r = rhs.double().clone()
+    p = r.clone()
+    rr = float(torch.sum(r * r))
+    rr0 = rr
+    for _ in range(iters):
+        q = plan.jhjv(p.float()).double()
+        a = rr / float(torch.sum(p * q))
+        xr += a * p
+        r -= a * q
+        rr_new = float(torch.sum(r * r))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    err = float(torch.linalg.vector_norm(x.double() - xr) / torch.linalg.vector_norm(xr))
+    res = plan.jhjv(x).double() - rhs.double()
+    return {"iterations_applied": applied, "iterations": iters,
+            "relerr_vs_product_by_product_cg_f64": err,
+            "true_residual_rel": float(torch.linalg.vector_norm(res)) / np.sqrt(rr0),
+            "f64_cg_recursive_residual_rel": float(np.sqrt(rr / rr0)),
+            "plan_check": "ok"}
+
+
+# ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
@@ -231,10 +265,13 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, path: str | None = None):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        if path is None:
+            import tempfile
+            path = os.path.join(tempfile.gettempdir(), f"mrstat_clocks_{os.getpid()}.csv")
+        self.path = path
 
     def start(self):
         try:
@@ -382,8 +419,9 @@ def main():
 
     all_kernels = ("bloch", "ycontract", "xdft", "xdft_adj", "jhw_dot")
     step = make_step(plan, args.form)
-    ms, stats, clk = timed(plan, step, args.steps, all_kernels, ClockSampler(local))
+    ms, stats, clk = timed(plan, step, args.steps, all_kernels, ClockSampler(local, args.clock_log))
     value = world * iters / (ms / 1e3)
+    cg_check = check_cg(torch, plan, rhs_dev, x_dev, iters)
 
     # the plain FP32 form on the same inputs, for the comparison the metric asks for
     plain = None
@@ -735,7 +773,7 @@ def main():
                            "form": args.form, "step": f"linearize + {iters} CG iterations (one J^H J v each)",
                            "cg_iters": iters, "l2": l2, "parallelism": f"replicas{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-                "cpu_baseline": cpu, "plain": plain,
+                "cpu_baseline": cpu, "cg_check": cg_check, "plain": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
                 "recon": recon, "surrogate": surrogate_info, "shapes": shapes, "slice_profile": slice_prof,
                 "kernel_ms_per_step": {k: v for k, v in per_step_ms.items()}}

@@ -141,7 +141,8 @@ int mrstat_plan_check(mrstat_plan* plan);
  * at the grid counter, so every block's bounded grid wait (2 s) runs out; the launch
  * ends early, x (or the Steihaug step) is undefined, and mrstat_plan_check /
  * mrstat_gn_solve report MRSTAT_ERR_TIMEOUT.  block < 0 turns it off (the default).
- * Nothing faults or hangs.  Errors: INVALID_ARG (NULL plan).
+ * Nothing faults or hangs.  Errors: INVALID_ARG (NULL plan, or block >= 2 nx: the
+ * persistent launches have two blocks per image column).
  */
 int mrstat_plan_inject_grid_stall(mrstat_plan* plan, int32_t block);
 
@@ -398,6 +399,18 @@ int mrstat_set_slice_profile(mrstat_plan* plan, const mrstat_slice_profile* prof
  */
 int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters,
                     void* stream);
+
+/*
+ * Number of iterations the last mrstat_cg_fixed on this plan applied to x: its `iters`
+ * unless an iteration froze the solve (non-positive curvature p.Hp, or a residual that
+ * is exactly zero; the inner solve of Algorithm 6 ends there), in which case x holds the
+ * iterate of the iterations before it.  A caller that times or trusts a fixed-count
+ * solve checks this equals iters.  Synchronises the plan's device.
+ *   applied: host int32 out.
+ * Errors: INVALID_ARG (NULL pointer), NOT_LINEARIZED (no mrstat_cg_fixed has run on
+ * the plan), CUDA.
+ */
+int mrstat_cg_applied(mrstat_plan* plan, int32_t* applied);
 
 /*
  * Inexact Gauss-Newton reconstruction (Algorithm 6) with a trust region.

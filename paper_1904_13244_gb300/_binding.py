@@ -126,6 +126,7 @@ _SIGS = {
     "mrstat_dot": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                    ctypes.c_void_p],
     "mrstat_cg_fixed": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
+    "mrstat_cg_applied": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)],
     "mrstat_gn_default_opts": [ctypes.POINTER(mrstat_gn_opts)],
     "mrstat_gn_solve": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                         ctypes.POINTER(mrstat_gn_opts), ctypes.POINTER(mrstat_gn_report), ctypes.c_void_p],
@@ -358,6 +359,12 @@ def mrstat_cg_fixed(plan, rhs, x, iters, stream=None):
     _check(load().mrstat_cg_fixed(plan, _ptr(rhs, torch.float32, (npar, nv), "rhs"),
                                   _ptr(x, torch.float32, (npar, nv), "x"), int(iters), _stream(stream)),
            "mrstat_cg_fixed")
+
+
+def mrstat_cg_applied(plan) -> int:
+    n = ctypes.c_int32(0)
+    _check(load().mrstat_cg_applied(plan, ctypes.byref(n)), "mrstat_cg_applied")
+    return int(n.value)
 
 
 def mrstat_set_slice_profile(plan, n_iso=None, n_sub=16, sigma=0.2, tbw=4.0, extent=2.0):

@@ -70,8 +70,9 @@ struct Plan {
   int grid_stall_block = -1;   // test hook: this block of those launches withholds an arrival
   float2* cg_jv = nullptr;  // [ntr][nkx]
   double* cg_s = nullptr;   // CG scalars, 4 per iteration
-  int* cg_frozen = nullptr; // CG stop flag
+  int* cg_frozen = nullptr; // CG stop flag: 0, or the index + 1 of the iteration that froze the solve
   int cg_s_cap = 0;         // iterations the scalar buffer holds
+  int cg_last_iters = -1;   // iters of the last mrstat_cg_fixed (-1: none yet)
 
   // Gauss-Newton work space (allocated by the first mrstat_gn_solve)
   bool gn_ready = false;
@@ -266,8 +267,9 @@ cudaError_t launch_dot(const float* a, const float* b, int64_t n, double* partia
                        double* out, cudaStream_t st, const int* gate = nullptr);
 cudaError_t launch_cg_init(const float* rhs, float* x, float* r, float* p, float* q, int64_t n, cudaStream_t st);
 // one Chronopoulos-Gear CG step (see reduce.cu); sk = {delta_k, gamma_k, alpha_k, -} of
-// this iteration, sp the previous iteration's (NULL in the first)
+// this iteration, sp the previous iteration's (NULL in the first); an iteration that
+// freezes the solve stores it + 1 in *frozen
 cudaError_t launch_cg_cg_step(float* x, float* r, float* p, float* q, const float* w, int64_t n, double* sk,
-                              const double* sp, int* frozen, cudaStream_t st);
+                              const double* sp, int* frozen, int it, cudaStream_t st);
 
 }  // namespace mrstat

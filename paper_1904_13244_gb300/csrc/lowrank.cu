@@ -902,7 +902,7 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
 //   the block waits until every block has arrived k + 1 times and adds the parts itself
 //   in block order (the same sums in every block); beta = gamma / gamma_prev,
 //   pq = delta - beta gamma / alpha_prev, alpha = gamma / pq (an iteration with pq <= 0
-//   or gamma = 0 freezes the rest); z = q + beta z, s = w + beta s, p = r + beta p,
+//   or gamma = 0 freezes the rest, and block 0 records where); z = q + beta z, s = w + beta s, p = r + beta p,
 //   x += alpha p, r -= alpha s, w -= alpha z on the block's half; the new w of each half
 //   goes into both blocks' voxel data (a store into the peer and a cluster barrier).
 // Two parity buffers of partials suffice: a block writes part[k mod 2] again only after
@@ -1043,7 +1043,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
                      const float* __restrict__ coefT, const float2* __restrict__ rho,
                      const float* __restrict__ maskf, const float2* __restrict__ roots,
                      const float* __restrict__ UgS, int kmax, int nx, int nv, int R, float scale, int iters,
-                     int stall_block, double* part, unsigned* bar, double* sums, int* err) {
+                     int stall_block, double* part, unsigned* bar, double* sums, int* frozen_at, int* err) {
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
   const int crank = (int)cl.block_rank(), peer = crank ^ 1;
@@ -1137,6 +1137,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   // pq_prev = p.Bp of the previous iteration: beta gamma / alpha_prev = beta^2 pq_prev
   double gam_prev = 0.0, pq_prev = 0.0;
   bool frozen = false;
+  int applied = 0;  // iterations that moved x (thread 0)
   for (int it = 0; it < iters; ++it) {
     FF* pk = reinterpret_cast<FF*>(part) + (size_t)(it & 1) * 2 * G;
     {
@@ -1171,6 +1172,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
           be = (float)beta;
           gam_prev = gamma;
           pq_prev = pq;
+          ++applied;
         } else {
           frozen = true;
         }
@@ -1218,6 +1220,9 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
     // peer has passed the next cluster barrier, i.e. after this read
     if (!ok || !s_ok_peer[it & 1]) break;
   }
+  // every block took the same decisions; block 0 reports where the solve froze (the
+  // iteration index + 1; 0 when all iterations were applied)
+  if (blockIdx.x == 0 && tid == 0) *frozen_at = applied < iters ? applied + 1 : 0;
   if (tid < nh) {
     const int j = (ya + tid) * nx + ix;
 #pragma unroll
@@ -2040,7 +2045,7 @@ static cudaError_t launch_cg_columns_t(Plan* p, const float* rhs, float* x, int 
                                    (const float*)L.coefT, (const float2*)p->rho, (const float*)p->maskf,
                                    (const float2*)p->roots, (const float*)L.UgS, L.ky_count_max, p->nx, p->nv, L.R,
                                    (float)p->nx, iters, p->grid_stall_block, p->red, p->cg_bar, p->cg_s,
-                                   p->dev_err);
+                                   p->cg_frozen, p->dev_err);
 }
 
 static cudaError_t launch_cg_columns(Plan* p, const float* rhs, float* x, int iters, bool launch, cudaStream_t st) {

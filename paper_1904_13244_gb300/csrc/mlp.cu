@@ -323,7 +323,7 @@ mlp_layer_persistent_kernel(const __grid_constant__ CUtensorMap tx, const __grid
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(tmem_slot, PS::kTmemCols);
+  if (warp == 0) tmem_alloc<PS::kTmemCols>(tmem_slot);
   fence_before();
   __syncthreads();
   fence_after();
@@ -460,7 +460,7 @@ mlp_layer_persistent_kernel(const __grid_constant__ CUtensorMap tx, const __grid
   }
   fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, PS::kTmemCols);
+  if (warp == 0) tmem_dealloc<PS::kTmemCols>(tmem);
 }
 
 int blocks_for(int64_t n, int t = 256) {

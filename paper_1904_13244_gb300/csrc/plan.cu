@@ -325,6 +325,8 @@ const char* mrstat_last_error(void) { return g_last_error.c_str(); }
 
 int mrstat_plan_inject_grid_stall(mrstat_plan* plan, int32_t block) {
   if (plan == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan");
+  // the persistent launches have two blocks per image column
+  if (block >= 2 * plan->nx) return fail(MRSTAT_ERR_INVALID_ARG, "stall block outside the persistent grid (2 nx blocks)");
   plan->grid_stall_block = block < 0 ? -1 : block;
   return MRSTAT_OK;
 }
@@ -726,11 +728,15 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
   }
   const int64_t n = (int64_t)plan->npar * plan->nv;
   double* sc = plan->cg_s;
+  plan->cg_last_iters = -1;
   {
     // the low-rank column path runs the whole solve in one persistent launch
     cudaError_t pe;
-    if (lowrank_cg_fixed_persistent(plan, rhs, x, iters, st, &pe))
-      return pe == cudaSuccess ? MRSTAT_OK : cuda_fail(pe, "persistent CG launch");
+    if (lowrank_cg_fixed_persistent(plan, rhs, x, iters, st, &pe)) {
+      if (pe != cudaSuccess) return cuda_fail(pe, "persistent CG launch");
+      plan->cg_last_iters = iters;
+      return MRSTAT_OK;
+    }
   }
   // Chronopoulos-Gear form: the product is applied to the residual, w = B r, with
   // delta = <r, w> and gamma = <r, r> formed in the same pass; one vector kernel then
@@ -748,10 +754,23 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
     {
       Span sp(plan, MRSTAT_K_VECTOR, st);
       e = launch_cg_cg_step(x, plan->cg_r, plan->cg_p, plan->cg_q, plan->cg_w, n, sk, it > 0 ? sk - 4 : nullptr,
-                            plan->cg_frozen, st);
+                            plan->cg_frozen, it, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "CG iteration");
   }
+  plan->cg_last_iters = iters;
+  return MRSTAT_OK;
+}
+
+int mrstat_cg_applied(mrstat_plan* plan, int32_t* applied) {
+  if (plan == nullptr || applied == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or applied");
+  if (plan->cg_last_iters < 0) return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_cg_applied before mrstat_cg_fixed");
+  DeviceGuard g(plan->device);
+  int frozen = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&frozen, plan->cg_frozen, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "CG iteration count");
+  *applied = frozen > 0 ? frozen - 1 : plan->cg_last_iters;
   return MRSTAT_OK;
 }
 

@@ -67,13 +67,14 @@ __global__ void cg_init_kernel(const float* __restrict__ rhs, float* __restrict_
 // In exact arithmetic these are the iterates of textbook CG; the product is applied to r,
 // so the inner products come with it and one vector pass remains.  An iteration with
 // pq <= 0 or gamma == 0 freezes x, r, p and q for the rest (block 0 marks the solve
-// frozen; a block that reads the flag after that reaches the same decision).  Lane 0 of
+// frozen with the iteration index + 1; a block that reads the flag after that reaches the
+// same decision).  Lane 0 of
 // each warp forms the scalars in float64 (GB300's float64 rate makes a per-thread
 // division visible); block 0 keeps alpha for the next iteration in sk[2].
 __global__ void __launch_bounds__(kT)
 cg_cg_step_kernel(float* __restrict__ x, float* __restrict__ r, float* __restrict__ p, float* __restrict__ q,
                   const float* __restrict__ w, int64_t n, int64_t n4, double* __restrict__ sk,
-                  const double* __restrict__ sp, int* __restrict__ frozen) {
+                  const double* __restrict__ sp, int* __restrict__ frozen, int it) {
   pdl_trigger();
   pdl_wait();  // w and the inner products come from the product launch
   const int64_t t0 = blockIdx.x * (int64_t)kT + threadIdx.x, stride = (int64_t)gridDim.x * kT;
@@ -94,14 +95,15 @@ cg_cg_step_kernel(float* __restrict__ x, float* __restrict__ r, float* __restric
       beta = gamma / sp[1];
       pq = delta - beta * gamma / sp[2];
     }
-    apply = !*frozen && pq > 0.0 && gamma > 0.0;
+    const int fz = *frozen;
+    apply = !fz && pq > 0.0 && gamma > 0.0;
     if (apply) {
       al = (float)(gamma / pq);
       be = (float)beta;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       if (apply) sk[2] = gamma / pq;
-      else *frozen = 1;
+      else if (!fz) *frozen = it + 1;
     }
   }
   al = __shfl_sync(0xffffffffu, al, 0);
@@ -156,9 +158,10 @@ cudaError_t launch_cg_init(const float* rhs, float* x, float* r, float* p, float
 }
 
 cudaError_t launch_cg_cg_step(float* x, float* r, float* p, float* q, const float* w, int64_t n, double* sk,
-                              const double* sp, int* frozen, cudaStream_t st) {
+                              const double* sp, int* frozen, int it, cudaStream_t st) {
   const int64_t n4 = aligned16(x) && aligned16(r) && aligned16(p) && aligned16(q) && aligned16(w) ? n / 4 : 0;
-  return launch_pdl(cg_cg_step_kernel, dim3(grid_for(n)), dim3(kT), 0, st, x, r, p, q, w, n, n4, sk, sp, frozen);
+  return launch_pdl(cg_cg_step_kernel, dim3(grid_for(n)), dim3(kT), 0, st, x, r, p, q, w, n, n4, sk, sp, frozen,
+                    it);
 }
 
 }  // namespace mrstat

@@ -68,7 +68,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant_
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(tmem_slot, TS::kTmemCols);
+  if (warp == 0) tmem_alloc<TS::kTmemCols>(tmem_slot);
   fence_before();
   __syncthreads();
   fence_after();
@@ -159,7 +159,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant_
   }
   fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, TS::kTmemCols);
+  if (warp == 0) tmem_dealloc<TS::kTmemCols>(tmem);
 }
 
 // ---------------------------------------------------------------------------
@@ -220,7 +220,7 @@ tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __gri
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(tmem_slot, PS::kTmemCols);
+  if (warp == 0) tmem_alloc<PS::kTmemCols>(tmem_slot);
   fence_before();
   __syncthreads();
   fence_after();
@@ -339,7 +339,7 @@ tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __gri
   }
   fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, PS::kTmemCols);
+  if (warp == 0) tmem_dealloc<PS::kTmemCols>(tmem);
 }
 
 // x (float, rows x cols, row stride ld_src) -> hi, lo (bf16, rows x ldk, zero padded)

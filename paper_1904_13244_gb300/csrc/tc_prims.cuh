@@ -70,15 +70,29 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* ba
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+// tcgen05.alloc takes a column count that is a power of two from 32 to 512; any other
+// count is an invalid operand.  The count is a template argument so that a tile shape
+// with, e.g., 224 accumulator columns fails to compile instead of reaching the GPU.
+template <uint32_t NCOLS>
+struct TmemCols {
+  static_assert(NCOLS >= 32 && NCOLS <= 512 && (NCOLS & (NCOLS - 1)) == 0,
+                "TMEM allocations are a power of two from 32 to 512 columns");
+  static constexpr uint32_t value = NCOLS;
+};
+
+template <uint32_t NCOLS>
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-               "r"(ncols)
+               "r"(TmemCols<NCOLS>::value)
                : "memory");
   asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+template <uint32_t NCOLS>
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+               "r"(TmemCols<NCOLS>::value)
+               : "memory");
 }
 
 __device__ __forceinline__ void fence_before() {

@@ -75,3 +75,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.mrstat_jhw(None, None, None, None) == 1
     assert lib.mrstat_linearize(None, None, None, None, None) == 1
     assert lib.mrstat_plan_destroy(None) == 0
+    assert lib.mrstat_cg_applied(None, None) == 1
+    n = ctypes.c_int32(-1)
+    assert lib.mrstat_cg_applied(None, ctypes.byref(n)) == 1 and n.value == -1
+    assert lib.mrstat_plan_inject_grid_stall(None, 0) == 1

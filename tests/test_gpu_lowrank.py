@@ -266,8 +266,13 @@ def test_persistent_launch_wait_runs_out_and_the_plan_recovers(mr):
             plan.gn_solve(cuda(d, torch.complex64), cuda(alpha), outer_iters=1, inner_iters=5, hessian=1)
         assert e.value.status == 6
         plan.inject_grid_stall(-1)
+        # a block outside the persistent grid (two blocks per image column) is refused
+        with pytest.raises(mr.MrstatError) as e:
+            plan.inject_grid_stall(2 * seq.nx)
+        assert e.value.status == 1
         plan.check()
         plan.lowrank_linearize(cuda(alpha))
         xg = plan.cg_fixed(cuda(b), 1).cpu().numpy()
         plan.check()
+        assert plan.cg_applied() == 1
     assert metrics.relerr(xg, x1) < 1e-5

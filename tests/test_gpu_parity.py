@@ -244,6 +244,27 @@ def brain(mr):
     return seq, ph, alpha, v, w, rows, vox, out
 
 
+@pytest.fixture(scope="module")
+def brain_oracle(brain):
+    """The oracle's s and J.v on the sampled TRs and Re(J^H w) on the sampled voxels of
+    the full 224 x 224 / 1120-TR workload."""
+    seq, ph, alpha, v, w, rows, vox, out = brain
+    sim = bloch.simulate(seq, np.exp(alpha[0]), np.exp(alpha[1]), rows=rows)
+    rho = alpha[2] + 1j * alpha[3]
+    q_s = rho[None, :] * sim["m"]
+    q_j = rho[None, :] * (v[0][None, :] * sim["dm_dlnT1"] + v[1][None, :] * sim["dm_dlnT2"]) \
+        + (v[2] + 1j * v[3])[None, :] * sim["m"]
+    simv = bloch.simulate(seq, np.exp(alpha[0, vox]), np.exp(alpha[1, vox]))
+    W = encoding.encode_adjoint(seq, w, vox)
+    rv = alpha[2, vox] + 1j * alpha[3, vox]
+    g = np.stack([
+        np.real(np.sum(np.conj(rv[None] * simv["dm_dlnT1"]) * W, 0)),
+        np.real(np.sum(np.conj(rv[None] * simv["dm_dlnT2"]) * W, 0)),
+        np.real(np.sum(np.conj(simv["m"]) * W, 0)),
+        np.real(np.sum(np.conj(1j * simv["m"]) * W, 0))])
+    return dict(s=encoding.encode(seq, q_s, rows), jv=encoding.encode(seq, q_j, rows), g=g)
+
+
 def test_full_size_timecourses_sampled_voxels(brain):
     seq, ph, alpha, v, w, rows, vox, out = brain
     sim = bloch.simulate(seq, np.exp(alpha[0, vox]), np.exp(alpha[1, vox]))
@@ -251,28 +272,15 @@ def test_full_size_timecourses_sampled_voxels(brain):
         assert metrics.relerr(out["tc"][c], sim[key].imag) < TOL, key
 
 
-def test_full_size_signal_and_jvp_sampled_trs(brain):
-    seq, ph, alpha, v, w, rows, vox, out = brain
-    sim = bloch.simulate(seq, np.exp(alpha[0]), np.exp(alpha[1]), rows=rows)
-    rho = alpha[2] + 1j * alpha[3]
-    q_s = rho[None, :] * sim["m"]
-    q_j = rho[None, :] * (v[0][None, :] * sim["dm_dlnT1"] + v[1][None, :] * sim["dm_dlnT2"]) \
-        + (v[2] + 1j * v[3])[None, :] * sim["m"]
-    assert metrics.relerr(out["s"], encoding.encode(seq, q_s, rows)) < TOL
-    assert metrics.relerr(out["jv"], encoding.encode(seq, q_j, rows)) < TOL
+def test_full_size_signal_and_jvp_sampled_trs(brain, brain_oracle):
+    out = brain[-1]
+    assert metrics.relerr(out["s"], brain_oracle["s"]) < TOL
+    assert metrics.relerr(out["jv"], brain_oracle["jv"]) < TOL
 
 
-def test_full_size_jhw_sampled_voxels(brain):
-    seq, ph, alpha, v, w, rows, vox, out = brain
-    sim = bloch.simulate(seq, np.exp(alpha[0, vox]), np.exp(alpha[1, vox]))
-    W = encoding.encode_adjoint(seq, w, vox)
-    rho = alpha[2, vox] + 1j * alpha[3, vox]
-    ref = np.stack([
-        np.real(np.sum(np.conj(rho[None] * sim["dm_dlnT1"]) * W, 0)),
-        np.real(np.sum(np.conj(rho[None] * sim["dm_dlnT2"]) * W, 0)),
-        np.real(np.sum(np.conj(sim["m"]) * W, 0)),
-        np.real(np.sum(np.conj(1j * sim["m"]) * W, 0))])
-    assert metrics.relerr(out["g"], ref) < TOL
+def test_full_size_jhw_sampled_voxels(brain, brain_oracle):
+    out = brain[-1]
+    assert metrics.relerr(out["g"], brain_oracle["g"]) < TOL
 
 
 # ---------------------------------------------------------------------------
@@ -303,14 +311,19 @@ def test_split_bf16_products_match_oracle(mr, name):
     assert max(e) < SPLIT_TOL, e
 
 
-def test_split_bf16_full_size_sampled(mr, brain):
+def test_split_bf16_full_size_sampled(mr, brain, brain_oracle):
+    """The split-BF16 form at 224 x 224 / 1120 TRs against the FP64 oracle on the sampled
+    TRs (s, J.v) and voxels (Re(J^H w)), and against the plain FP32 form."""
     seq, ph, alpha, v, w, rows, vox, out = brain
     with mr.Plan(seq, form=mr.MRSTAT_FORM_SPLIT_BF16) as plan:
         a = cuda(alpha)
         plan.linearize(a)
+        s = plan.forward(a).cpu().numpy()[rows]
         jv = plan.jvp(cuda(v)).cpu().numpy()[rows]
         g = plan.jhw(cuda(w, torch.complex64)).cpu().numpy()[:, vox]
         plan.check()
-    # against the plain FP32 outputs of the same inputs (themselves pinned to the oracle)
+    e = [metrics.relerr(s, brain_oracle["s"]), metrics.relerr(jv, brain_oracle["jv"]),
+         metrics.relerr(g, brain_oracle["g"])]
+    assert max(e) < SPLIT_TOL, e
     assert metrics.relerr(jv, out["jv"]) < SPLIT_TOL
     assert metrics.relerr(g, out["g"]) < SPLIT_TOL
