@@ -84,12 +84,20 @@ def parse_args():
     ap.add_argument("--cg-iters", type=int, default=30)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-plan", action="store_true",
+                    help="also run the oracle's full CPU baseline plan (single-threaded and all cores; minutes)")
+    ap.add_argument("--oracle-plan-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--form", default="surrogate", choices=["surrogate", "lowrank", "plain", "split"])
     ap.add_argument("--hidden", type=int, default=256)
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--rank", type=int, default=32)
     ap.add_argument("--no-recon", action="store_true")
     ap.add_argument("--no-shapes", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the split-BF16 (precision form) legs")
+    ap.add_argument("--no-fp64-errors", action="store_true",
+                    help="skip the error of every form against the FP64 oracle on sampled outputs")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-part legs (224x224 and 256x256 with a B1 map)")
     ap.add_argument("--clock-log", default=os.environ.get("MRSTAT_CLOCK_LOG"),
                     help="CSV file for the nvidia-smi clock samples of the timed region "
                          "(default: a file in the system temp directory)")
@@ -129,6 +137,163 @@ def oracle_sample(workload: str, ntr_sample: int, products: int, seed: int = 0, 
         v = v / max(np.linalg.norm(v), 1e-30)
     t2 = time.perf_counter()
     return t1 - t0, (t2 - t1) / max(products, 1), scale
+
+
+def oracle_plan_worker(seeds: int = 3):
+    """The oracle's CPU timings on this process's thread settings (the caller sets
+    OMP_NUM_THREADS and friends before numpy loads): forward, J.v, Re(J^H w) and
+    Re(J^H J) v in full on the 64 x 64 / 320-TR workload; a 10 x 20 Gauss-Newton solve on
+    the 16 x 16 / 64-TR workload (SNR 50), one outer iteration of it on the 64 x 64
+    workload (scaled by 10: a full solve takes minutes); the 224 x 224 /
+    1120-TR linearisation and product on 8 of its TRs, extrapolated linearly in TRs.
+    Medians over `seeds` seeded runs after one warm-up run where the item is short."""
+    from oracle import model, solver
+    res = {}
+
+    def med(fn, n, warm=True):
+        if warm:
+            fn()
+        ts = []
+        for i in range(n):
+            t0 = time.perf_counter()
+            fn(i)
+            ts.append(time.perf_counter() - t0)
+        return float(np.median(ts))
+
+    seq, ph = synth.config("ellipse64")
+    alpha = alpha_of(ph).astype(np.float64)
+    lin = model.linearize(seq, alpha)
+    v = synth.random_params(seq.nv, 1)
+    w = synth.random_kspace(seq.ntr, seq.nkx, 2)
+    res["ellipse64_forward_s"] = med(lambda i=0: model.forward(seq, alpha), seeds)
+    res["ellipse64_linearize_s"] = med(lambda i=0: model.linearize(seq, alpha), seeds)
+    res["ellipse64_jvp_s"] = med(lambda i=0: model.jvp(lin, v), seeds)
+    res["ellipse64_jhw_s"] = med(lambda i=0: model.jhw(lin, w), seeds)
+    res["ellipse64_jhjv_s"] = med(lambda i=0: model.gauss_newton_product(lin, v), seeds)
+
+    def gn(name, outer, inner, snr, n):
+        sq, p = synth.config(name)
+        a = alpha_of(p).astype(np.float64)
+        d = synth.add_noise(model.forward(sq, a), snr, 3)
+
+        def run(i=0):
+            a0, mask = solver.initial_alpha(sq, d, sq.nv, exact=True)
+            solver.gauss_newton(sq, d, a0, mask=mask, opts=solver.GNOptions(outer_iters=outer, inner_iters=inner))
+        return med(run, n, warm=n > 1)
+    res["quad16_gn_10x20_s"] = gn("quad16", 10, 20, 50.0, seeds)
+    # 64 x 64: one outer iteration (with the rho initialisation) timed, scaled by 10
+    res["ellipse64_gn_1x20_s"] = gn("ellipse64", 1, 20, 50.0, 1)
+    res["ellipse64_gn_10x20_s_extrapolated"] = 10 * res["ellipse64_gn_1x20_s"]
+    t_lin, t_prod, scale = oracle_sample("brain224", 8, 1)
+    res["brain224_linearize_s_extrapolated"] = t_lin * scale
+    res["brain224_jhjv_s_extrapolated"] = t_prod * scale
+    res["brain224_note"] = "224 x 224 / 1120 TRs timed on 8 TRs and scaled by 140 (linear in TRs)"
+    return res
+
+
+def fp64_errors(mr, torch, seq, ph, alpha_h, U, net):
+    """Normwise relative error of every form against the FP64 oracle on sampled outputs of
+    the workload, which the oracle computes one by one (this runs the oracle, so it belongs
+    to the cpu_baseline leg): s and J.v on 12 TRs, Re(J^H w) on 64 voxels and Re(J^H J) v on
+    3 image columns (with nkx = nx the readout DFT pair cancels, so a column of the product
+    is nx times the product of that column alone).  The low-rank and surrogate forms are
+    compared with the exact model (their model error included) and, for Re(J^H w) and
+    Re(J^H J) v, with the oracle's projection on the same basis (the low-rank form's
+    arithmetic error; the surrogate's fit error)."""
+    from oracle import bloch, encoding, metrics, model
+    rng = np.random.default_rng(53)
+    rows = np.sort(rng.choice(seq.ntr, 12, replace=False))
+    vox = np.sort(rng.choice(seq.nv, 64, replace=False))
+    cols = [40, seq.nx // 2, seq.nx - 50]
+    alpha = alpha_h.astype(np.float64)
+    v = synth.random_params(seq.nv, 51)
+    w = synth.random_kspace(seq.ntr, seq.nkx, 52)
+    Ud = U.cpu().numpy().astype(np.float64)
+    # oracle: s and J.v on the sampled TRs
+    sim = bloch.simulate(seq, np.exp(alpha[0]), np.exp(alpha[1]), rows=rows)
+    rho = alpha[2] + 1j * alpha[3]
+    ref = {"s": encoding.encode(seq, rho[None, :] * sim["m"], rows),
+           "jv": encoding.encode(seq, rho[None, :] * (v[0][None, :] * sim["dm_dlnT1"] + v[1][None, :] * sim["dm_dlnT2"])
+                                 + (v[2] + 1j * v[3])[None, :] * sim["m"], rows)}
+    del sim
+    # Re(J^H w) on the sampled voxels: exact and projected time courses
+    simv = bloch.simulate(seq, np.exp(alpha[0, vox]), np.exp(alpha[1, vox]))
+    W = encoding.encode_adjoint(seq, w, vox)
+    rv = rho[vox]
+
+    def gdot(m, d1, d2):
+        return np.stack([np.real(np.sum(np.conj(rv[None] * d1) * W, 0)), np.real(np.sum(np.conj(rv[None] * d2) * W, 0)),
+                         np.real(np.sum(np.conj(m) * W, 0)), np.real(np.sum(np.conj(1j * m) * W, 0))])
+    P = Ud @ Ud.T
+    ref["g"] = gdot(simv["m"], simv["dm_dlnT1"], simv["dm_dlnT2"])
+    ref_g_proj = gdot(P @ simv["m"], P @ simv["dm_dlnT1"], P @ simv["dm_dlnT2"])
+    # Re(J^H J) v on the sampled columns
+    v3 = v.reshape(4, seq.ny, seq.nx)
+    h_ref, h_proj = [], []
+    for ix in cols:
+        sub = synth.Sequence(nx=1, ny=seq.ny, nkx=1, tr_ms=seq.tr_ms, te_ms=seq.te_ms, flip_rad=seq.flip_rad,
+                             ky=seq.ky, inversion=seq.inversion, alternate_phase=seq.alternate_phase)
+        a1 = alpha.reshape(4, seq.ny, seq.nx)[:, :, ix]
+        lin = model.linearize(sub, a1)
+        h_ref.append(seq.nx * model.gauss_newton_product(lin, v3[:, :, ix]))
+        h_proj.append(seq.nx * model.gauss_newton_product(model.project_onto_basis(lin, Ud), v3[:, :, ix]))
+    ref["h"] = np.stack(h_ref, -1)
+    ref_h_proj = np.stack(h_proj, -1)
+
+    a_dev = torch.tensor(alpha_h, device="cuda")
+    v_dev = torch.tensor(v.astype(np.float32), device="cuda")
+    w_dev = torch.tensor(w, dtype=torch.complex64, device="cuda")
+
+    def outputs(pl, with_s):
+        o = {}
+        if with_s:
+            o["s"] = pl.forward(a_dev).cpu().numpy()[rows]
+        o["jv"] = pl.jvp(v_dev).cpu().numpy()[rows]
+        o["g"] = pl.jhw(w_dev).cpu().numpy()[:, vox]
+        o["h"] = pl.jhjv(v_dev).cpu().numpy().reshape(4, seq.ny, seq.nx)[:, :, cols]
+        pl.check()
+        return o
+
+    res = {"sample": "12 TRs (s, J.v), 64 voxels (Re(J^H w)), 3 image columns (Re(J^H J) v) of the workload"}
+    for name, form in (("plain", mr.MRSTAT_FORM_PLAIN_FP32), ("split", mr.MRSTAT_FORM_SPLIT_BF16)):
+        pl = mr.Plan(seq, form=form)
+        pl.linearize(a_dev)
+        o = outputs(pl, True)
+        pl.close()
+        res[name] = {k: metrics.relerr(o[k], ref[k]) for k in o}
+    pl = mr.Plan(seq)
+    pl.lowrank_set_basis(U)
+    for name in ("lowrank", "surrogate"):
+        if name == "surrogate":
+            if net is None:
+                continue
+            pl.lowrank_linearize(a_dev, coef=net.infer(a_dev[:2]))
+        else:
+            pl.lowrank_linearize(a_dev)
+        o = outputs(pl, False)
+        res[name] = {k: metrics.relerr(o[k], ref[k]) for k in o}
+        res[name]["g_vs_projected"] = metrics.relerr(o["g"], ref_g_proj)
+        res[name]["h_vs_projected"] = metrics.relerr(o["h"], ref_h_proj)
+    pl.close()
+    return res
+
+
+def run_oracle_plan():
+    """The oracle's CPU baseline plan, single-threaded and on all host cores, each in a
+    fresh interpreter so that the thread settings take effect before numpy loads."""
+    out = {"cores": cpu_cores()}
+    for label, threads in (("one_thread", 1), ("all_cores", cpu_cores())):
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = str(threads)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-plan-worker"], env=env,
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            out[label] = {"error": r.stderr[-500:]}
+            continue
+        out[label] = json.loads(r.stdout.strip().splitlines()[-1])
+        out[label]["threads"] = threads
+    return out
 
 
 def max_over_ranks(x: float, dist=None) -> float:
@@ -195,35 +360,46 @@ def run_reference(args, rank: int):
 # ---------------------------------------------------------------------------
 # learned surrogate: trained on device on exact projections of the Bloch model
 # ---------------------------------------------------------------------------
-def train_surrogate(mr, torch, plan, rank, hidden, steps, n_train=262144, batch=4096, seed=0):
-    """MLP fitted to the plan's projected Bloch model: T1 log-U(100, 6000) ms, T2 log-U(10,
-    3000) ms, B1 = 1; targets from mrstat_lowrank_project_samples.  Returns the network and
-    a summary (training seconds, held-out relative errors of c, dc/dlnT1, dc/dlnT2)."""
-    gen = torch.Generator(device="cuda").manual_seed(seed)
-    rng = np.random.default_rng(seed + 77)
+def training_params(torch, n, seed):
+    """Parameter samples of the learned part: T1 log-U(100, 6000) ms, T2 log-U(10, 3000) ms
+    (the paper's training ranges widened so that CSF does not extrapolate) and B1 U(0.8,
+    1.2); returns (ln T1 / ln T2 [2, n], B1 [n]) on the device."""
+    rng = np.random.default_rng(seed)
+    x = np.stack([rng.uniform(np.log(100), np.log(6000), n), rng.uniform(np.log(10), np.log(3000), n)])
+    b1 = rng.uniform(0.8, 1.2, n)
+    return (torch.tensor(x, dtype=torch.float32, device="cuda"), torch.tensor(b1, dtype=torch.float32, device="cuda"))
 
-    def draw(n):
-        return torch.tensor(np.stack([rng.uniform(np.log(100), np.log(6000), n),
-                                      rng.uniform(np.log(10), np.log(3000), n)]), dtype=torch.float32, device="cuda")
+
+def train_surrogate(mr, torch, plan, rank, hidden, steps, n_train=1 << 20, batch=4096, seed=0):
+    """MLP fitted to the plan's projected Bloch model on n_train samples (T1, T2, B1 drawn
+    by training_params); targets from mrstat_lowrank_project_samples, i.e. the Bloch kernel
+    itself.  Returns the network and a summary (training seconds, held-out relative errors
+    of c, dc/dlnT1, dc/dlnT2 on B1-varied samples and at B1 = 1)."""
+    gen = torch.Generator(device="cuda").manual_seed(seed)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    x = draw(n_train)
-    tgt = plan.lowrank_project_samples(x)
+    x, xb = training_params(torch, n_train, seed + 77)
+    tgt = plan.lowrank_project_samples(x, b1=xb)
     scale = tgt[0].abs().amax(dim=1).clamp_min(1e-6).cpu().numpy()
     net = mr.Surrogate(hidden, rank, (np.log(1000.0), 1.0, np.log(100.0), 1.2, 1.0, 0.2), 0.5, seed=seed)
     net.set_output_scale(scale)
     for it in range(steps):
         idx = torch.randint(0, n_train, (batch,), device="cuda", generator=gen)
         lr = 2e-3 if it < steps * 0.6 else (6e-4 if it < steps * 0.85 else 2e-4)
-        net.train_step(x[:, idx].contiguous(), tgt[:, :, idx].contiguous(), lr)
+        net.train_step(x[:, idx].contiguous(), tgt[:, :, idx].contiguous(), lr, b1=xb[idx].contiguous())
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
-    xt = draw(16384)
-    tt = plan.lowrank_project_samples(xt)
-    pred = net.infer(xt)
-    err = [float(torch.linalg.vector_norm(pred[k] - tt[k]) / torch.linalg.vector_norm(tt[k])) for k in range(3)]
+    del tgt
+    xt, xtb = training_params(torch, 16384, seed + 78)
+
+    def held_out(b1):
+        tt = plan.lowrank_project_samples(xt, b1=b1)
+        pred = net.infer(xt, b1=b1)
+        return {k: float(torch.linalg.vector_norm(pred[i] - tt[i]) / torch.linalg.vector_norm(tt[i]))
+                for i, k in enumerate(("c", "dc_dlnT1", "dc_dlnT2"))}
     return net, {"hidden": hidden, "train_seconds": secs, "train_samples": n_train, "steps": steps,
-                 "batch": batch, "holdout_relerr": {"c": err[0], "dc_dlnT1": err[1], "dc_dlnT2": err[2]}}
+                 "batch": batch, "b1_range": [0.8, 1.2], "holdout_relerr": held_out(xtb),
+                 "holdout_relerr_b1_1": held_out(None)}
 
 
 # ---------------------------------------------------------------------------
@@ -327,6 +503,121 @@ def measured_peak_hbm():
 
 
 # ---------------------------------------------------------------------------
+# reconstructions (Algorithm 6)
+# ---------------------------------------------------------------------------
+def noisy_data(torch, plan, truth, b1, snr=30.0):
+    """d = s(truth) + complex Gaussian noise with ||s|| / ||noise|| = snr (seeded)."""
+    s_true = plan.forward(truth, b1=b1)
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    noise = torch.complex(torch.randn(s_true.shape, generator=gen), torch.randn(s_true.shape, generator=gen))
+    noise = noise.to("cuda").to(torch.complex64)
+    return s_true + noise * (torch.linalg.vector_norm(s_true) / (snr * torch.linalg.vector_norm(noise))), noise
+
+
+def reconstruct(torch, plan, seq, ph, truth, d, b1, runs, rho_kw, profile=None, outer=15, inner=30):
+    """One 15 x 30 Gauss-Newton reconstruction per entry of runs (name, gn options) from
+    T1 = 1000 ms, T2 = 100 ms with the rho initialisation rho_kw and the 0.1 mask; seconds
+    and T1 / T2 / rho NRMSE against the truth over the drawn mask inside the support, and
+    whether each run reaches the "plain" run's T1 and T2 NRMSE:
+    |NRMSE - NRMSE_plain| <= max(0.1 NRMSE_plain, 1e-3)."""
+    out = {}
+    sup = torch.tensor(ph.support.ravel(), device="cuda")
+    for name, kw in runs:
+        a = torch.zeros((4, seq.nv), dtype=torch.float32, device="cuda")
+        mask = torch.zeros(seq.nv, dtype=torch.uint8, device="cuda")
+        if profile == name:
+            plan.gn_solve(d, a.clone(), b1=b1, mask=mask.clone(), outer_iters=outer, inner_iters=inner,
+                          mask_threshold=0.1, **rho_kw, **kw)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = plan.gn_solve(d, a, b1=b1, mask=mask, outer_iters=outer, inner_iters=inner, mask_threshold=0.1,
+                            **rho_kw, **kw)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        if profile == name:
+            torch.cuda.profiler.stop()
+        m = mask.bool() & sup
+
+        def nrmse(x, y):
+            return float(torch.linalg.vector_norm((x - y)[m]) / torch.linalg.vector_norm(y[m]))
+        out[name] = {"seconds": secs, "nrmse_t1": nrmse(torch.exp(a[0]), torch.exp(truth[0])),
+                     "nrmse_t2": nrmse(torch.exp(a[1]), torch.exp(truth[1])),
+                     "nrmse_rho": float(torch.linalg.vector_norm(torch.complex(a[2] - truth[2], a[3] - truth[3])[m])
+                                        / torch.linalg.vector_norm(torch.complex(truth[2], truth[3])[m])),
+                     "f_final": rep["f_final"], "accepted": sum(rep["accepted"]),
+                     "cg_steps": sum(rep["cg_steps"]), "mask_voxels": rep["mask_voxels"]}
+    for name in out:
+        if name != "plain" and "plain" in out:
+            out[name]["equal_nrmse"] = all(abs(out[name][k] - out["plain"][k]) <= max(0.1 * out["plain"][k], 1e-3)
+                                           for k in ("nrmse_t1", "nrmse_t2"))
+    return out
+
+
+def gn_rhs(torch, plan, alpha, b1, seq, rank):
+    """A Gauss-Newton right-hand side: Re(J^H w) of the exact model at alpha for a seeded
+    complex Gaussian k-space vector w, scaled to unit RMS.  It lies in the range of
+    Re(J^H J), so CG solves a consistent system (the background voxels' ln T1 / ln T2 rows,
+    where rho = 0, are in the null space)."""
+    plan.linearize(alpha, b1=b1)
+    w = torch.tensor(synth.random_kspace(seq.ntr, seq.nkx, 100 + rank), dtype=torch.complex64, device="cuda")
+    g = plan.jhw(w)
+    return (g / torch.sqrt(torch.mean(g * g))).contiguous()
+
+
+def learned_part(mr, torch, args, name, rank, iters, timed):
+    """The learned-part form on a workload with a smooth, known B1 map in [0.8, 1.2]: a
+    rank-R basis and the surrogate trained for this sequence on B1-varied samples, then the
+    bench step (linearise + iters CG iterations) with the surrogate's coefficients, with the
+    compressed-exact coefficients (the Bloch recursion projected on the basis) and with the
+    plain FP32 model, and the three 15 x 30 reconstructions (rho initialised by 50 CGLS
+    steps: the exact least-squares form needs B1 = 1)."""
+    seq, ph = synth.config(name, seed=rank, b1_map=True)
+    plan = mr.Plan(seq)
+    train, train_b1 = training_params(torch, 4096, 1000)
+    U, _ = plan.lowrank_basis(train, args.rank, train_b1=train_b1)
+    plan.lowrank_set_basis(U)
+    net, info = train_surrogate(mr, torch, plan, args.rank, args.hidden, args.train_steps)
+    a = torch.tensor(alpha_of(ph), device="cuda")
+    b1 = torch.tensor(ph.b1.ravel().astype(np.float32), device="cuda")
+    rhs = gn_rhs(torch, plan, a, b1, seq, rank)
+    x = torch.empty_like(rhs)
+    coef = torch.empty((3, args.rank, seq.nv), dtype=torch.float32, device="cuda")
+
+    def step_surrogate():
+        net.infer(a[:2], b1=b1, out=coef)
+        plan.lowrank_linearize(a, b1=b1, coef=coef)
+        plan.cg_fixed(rhs, iters, out=x)
+
+    def step_lowrank():
+        plan.lowrank_linearize(a, b1=b1)
+        plan.cg_fixed(rhs, iters, out=x)
+
+    def step_plain():
+        plan.linearize(a, b1=b1)
+        plan.cg_fixed(rhs, iters, out=x)
+    out = {"grid": [seq.nx, seq.ny], "ntr": seq.ntr, "rank": args.rank,
+           "b1": "known map 1 + 0.2 smooth field clipped to [0.8, 1.2]", "surrogate": info}
+    nsteps = max(5, args.steps // 4)
+    for key, st in (("surrogate", step_surrogate), ("lowrank", step_lowrank), ("plain", step_plain)):
+        ms, _, _ = timed(plan, st, nsteps, ())
+        out[key + "_step"] = {"products_per_s": iters / (ms / 1e3), "ms_per_step": ms,
+                              "cg_iterations_applied": plan.cg_applied()}
+    out["surrogate_gain_vs_lowrank"] = out["surrogate_step"]["products_per_s"] / out["lowrank_step"]["products_per_s"]
+    out["surrogate_gain_vs_plain"] = out["surrogate_step"]["products_per_s"] / out["plain_step"]["products_per_s"]
+    if not args.no_recon:
+        truth = a.clone()
+        d, _ = noisy_data(torch, plan, truth, b1)
+        runs = [("plain", dict(hessian=0)), ("lowrank", dict(hessian=1)),
+                ("surrogate", dict(hessian=1, surrogate_iters=10, surrogate=net))]
+        out["recon"] = reconstruct(torch, plan, seq, ph, truth, d, b1, runs, dict(rho_init_iters=50))
+    net.close()
+    plan.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -335,6 +626,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
+    if args.oracle_plan_worker:
+        print(json.dumps(oracle_plan_worker()), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, rank)
         return
@@ -352,22 +646,19 @@ def main():
     seq, ph = synth.config(args.workload, seed=rank)
     iters = args.cg_iters
     alpha_h = alpha_of(ph)
-    rhs_h = synth.random_params(seq.nv, 100 + rank).astype(np.float32)
     form_code = mr.MRSTAT_FORM_SPLIT_BF16 if args.form == "split" else mr.MRSTAT_FORM_PLAIN_FP32
     plan = mr.Plan(seq, form=form_code)
     a_dev = torch.tensor(alpha_h, device="cuda")
-    rhs_dev = torch.tensor(rhs_h, device="cuda")
+    rhs_dev = gn_rhs(torch, plan, a_dev, None, seq, rank)
+    rhs_h = rhs_dev.cpu().numpy()
     x_dev = torch.empty_like(rhs_dev)
     stream = torch.cuda.current_stream()
     basis = None
     net = None
     surrogate_info = None
     if args.form in ("lowrank", "surrogate") or not args.no_recon:
-        rng = np.random.default_rng(1000)
-        train = torch.tensor(np.stack([rng.uniform(np.log(100), np.log(6000), 4096),
-                                       rng.uniform(np.log(10), np.log(3000), 4096)]), dtype=torch.float32,
-                             device="cuda")
-        basis, _ = plan.lowrank_basis(train, args.rank)
+        train, train_b1 = training_params(torch, 4096, 1000)
+        basis, _ = plan.lowrank_basis(train, args.rank, train_b1=train_b1)
         plan.lowrank_set_basis(basis)
     if args.form == "surrogate" or not args.no_recon:
         net, surrogate_info = train_surrogate(mr, torch, plan, args.rank, args.hidden, args.train_steps)
@@ -433,22 +724,44 @@ def main():
         plain = {"value": world * iters / (pms / 1e3), "ms_per_step": pms,
                  "kernel_ms_per_step": {k: pstats[k]["ms"] / max(1, args.steps // 4) for k in all_kernels}}
 
+    # the precision form: the exact model with the readout DFTs as split-BF16 tcgen05
+    # products (s, J.v and Re(J^H w); inside J^H J v the readout DFT pair cancels because
+    # nkx = nx, so its CG products are the plain form's)
+    precision = None
+    if args.form != "split" and not args.no_precision:
+        xplan = mr.Plan(seq, form=mr.MRSTAT_FORM_SPLIT_BF16)
+        nst = max(1, args.steps // 4)
+        xms, xstats, _ = timed(xplan, make_step(xplan, "split"), nst, all_kernels)
+        # the encoding alone: forward (K1 + K2 + split x-DFT) and J^H w (split x-DFT^H + K4)
+        w_dev = torch.tensor(synth.random_kspace(seq.ntr, seq.nkx, 5), dtype=torch.complex64, device="cuda")
+
+        def enc():
+            xplan.forward(a_dev)
+            xplan.jhw(w_dev)
+        ems, estats, _ = timed(xplan, enc, nst, all_kernels)
+        xplan.check()
+        precision = {"value": world * iters / (xms / 1e3), "ms_per_step": xms,
+                     "kernel_ms_per_step": {k: xstats[k]["ms"] / nst for k in all_kernels},
+                     "forward_plus_jhw_ms": ems,
+                     "xdft_launch_ms": estats["xdft"]["ms"] / max(estats["xdft"]["timed"], 1),
+                     "xdft_adj_launch_ms": estats["xdft_adj"]["ms"] / max(estats["xdft_adj"]["timed"], 1),
+                     "xdft_tflops_split": 3 * 2 * seq.ntr * (2 * seq.nkx) * (2 * seq.nx) / 1e12
+                     / (estats["xdft"]["ms"] / max(estats["xdft"]["timed"], 1) / 1e3)}
+        xplan.close()
+
     # the paper's other sequence shapes (Supporting Information S1 / S3): the same step in
     # the low-rank form (coefficients by exact projection), products/s
     shapes = None
     if not args.no_shapes and world == 1:
         shapes = {}
-        rng_s = np.random.default_rng(1000)
-        train_s = torch.tensor(np.stack([rng_s.uniform(np.log(100), np.log(6000), 4096),
-                                         rng_s.uniform(np.log(10), np.log(3000), 4096)]), dtype=torch.float32,
-                               device="cuda")
+        train_s, train_sb1 = training_params(torch, 4096, 1000)
         for name in ("brain224_1792", "const112x88"):
             sseq, sph = synth.config(name, seed=rank)
             splan = mr.Plan(sseq)
             sa = torch.tensor(alpha_of(sph), device="cuda")
-            srhs = torch.tensor(synth.random_params(sseq.nv, 100 + rank).astype(np.float32), device="cuda")
+            srhs = gn_rhs(torch, splan, sa, None, sseq, rank)
             sx = torch.empty_like(srhs)
-            sU, _ = splan.lowrank_basis(train_s, args.rank)
+            sU, _ = splan.lowrank_basis(train_s, args.rank, train_b1=train_sb1)
             splan.lowrank_set_basis(sU)
 
             def sstep(splan=splan, sa=sa, srhs=srhs, sx=sx):
@@ -663,42 +976,23 @@ def main():
     # full reconstructions (Algorithm 6, 15 x 30) with the exact and the low-rank CG matrix
     recon = None
     if not args.no_recon and rank == 0:
-        recon = {}
         truth = torch.tensor(alpha_h, device="cuda")
-        s_true = plan.forward(truth)
-        gen = torch.Generator(device="cpu").manual_seed(7)
-        noise = torch.complex(torch.randn(s_true.shape, generator=gen), torch.randn(s_true.shape, generator=gen))
-        noise = noise.to("cuda").to(torch.complex64)
-        d = s_true + noise * (torch.linalg.vector_norm(s_true) / (30.0 * torch.linalg.vector_norm(noise)))
-        sup = torch.tensor(ph.support.ravel(), device="cuda")
+        d, noise = noisy_data(torch, plan, truth, None)
         runs = [("plain", dict(hessian=0)), ("lowrank", dict(hessian=1))]
         if net is not None:
             runs.append(("surrogate", dict(hessian=1, surrogate_iters=10, surrogate=net)))
-        for name, kw in runs:
-            a = torch.zeros((4, seq.nv), dtype=torch.float32, device="cuda")
-            mask = torch.zeros(seq.nv, dtype=torch.uint8, device="cuda")
-            if args.profile_recon == name:
-                plan.gn_solve(d, a.clone(), mask=mask.clone(), outer_iters=15, inner_iters=30, rho_init_exact=1,
-                              mask_threshold=0.1, **kw)
-                torch.cuda.synchronize()
-                torch.cuda.profiler.start()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rep = plan.gn_solve(d, a, mask=mask, outer_iters=15, inner_iters=30, rho_init_exact=1,
-                                mask_threshold=0.1, **kw)
-            torch.cuda.synchronize()
-            secs = time.perf_counter() - t0
-            if args.profile_recon == name:
-                torch.cuda.profiler.stop()
-            m = (mask.bool() & sup)
-            def nrmse(x, y):
-                return float(torch.linalg.vector_norm((x - y)[m]) / torch.linalg.vector_norm(y[m]))
-            recon[name] = {"seconds": secs, "nrmse_t1": nrmse(torch.exp(a[0]), torch.exp(truth[0])),
-                           "nrmse_t2": nrmse(torch.exp(a[1]), torch.exp(truth[1])),
-                           "nrmse_rho": float(torch.linalg.vector_norm(torch.complex(a[2] - truth[2], a[3] - truth[3])[m])
-                                              / torch.linalg.vector_norm(torch.complex(truth[2], truth[3])[m])),
-                           "f_final": rep["f_final"], "accepted": sum(rep["accepted"]),
-                           "cg_steps": sum(rep["cg_steps"]), "mask_voxels": rep["mask_voxels"]}
+        recon = reconstruct(torch, plan, seq, ph, truth, d, None, runs, dict(rho_init_exact=1),
+                            profile=args.profile_recon)
+        if not args.no_precision:
+            # the precision form's reconstruction: exact model, split-BF16 readout DFTs
+            xplan = mr.Plan(seq, form=mr.MRSTAT_FORM_SPLIT_BF16)
+            recon["split"] = reconstruct(torch, xplan, seq, ph, truth, d, None, [("split", dict(hessian=0))],
+                                         dict(rho_init_exact=1))["split"]
+            xplan.check()
+            xplan.close()
+            recon["split"]["equal_nrmse"] = all(
+                abs(recon["split"][k] - recon["plain"][k]) <= max(0.1 * recon["plain"][k], 1e-3)
+                for k in ("nrmse_t1", "nrmse_t2"))
         # B1 as the fifth unknown (a known map before): brain phantom with a smooth B1 field
         # in [0.8, 1.2], the same noise level, B1 started at 1 with the rho initialisation
         seq_b, ph_b = synth.config(args.workload, seed=rank, b1_map=True)
@@ -728,13 +1022,15 @@ def main():
                                  "settings": "B1 = 1 + 0.2 smooth field in [0.8, 1.2] estimated with T1, T2, rho; "
                                              "15 GN x 30 CG, SNR 30"}
         bplan.close()
-        for name in ("lowrank", "surrogate"):
-            if name in recon:
-                recon[name]["equal_nrmse"] = all(
-                    abs(recon[name][k] - recon["plain"][k]) <= max(0.1 * recon["plain"][k], 1e-3)
-                    for k in ("nrmse_t1", "nrmse_t2"))
         recon["settings"] = ("15 GN x 30 CG, SNR 30, rho the exact least-squares solution at T1 1000 ms / T2 100 ms, mask 0.1; "
                              "surrogate: 10 surrogate + 5 exact iterations, low-rank CG matrix")
+
+    # the learned-part form (surrogate trained on B1-varied samples, known smooth B1 map) at
+    # 224 x 224 / 1120 TRs and 256 x 256 / 1280 TRs: step rates of the surrogate, the
+    # compressed-exact and the plain model, and the three reconstructions
+    learned = None
+    if not args.no_learned and rank == 0 and world == 1:
+        learned = {n: learned_part(mr, torch, args, n, rank, iters, timed) for n in ("brain224", "brain256")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -745,6 +1041,12 @@ def main():
                "sample": f"FP64 NumPy oracle, linearise + 2 J^H J v products on the first {ntr_sample} of {seq.ntr} "
                          f"TRs ({t_lin + 2 * t_prod:.1f} s), extrapolated linearly in TRs to linearise + "
                          f"{iters} products; elementwise NumPy single-threaded, BLAS on all cores"}
+        if args.cpu_plan:
+            cpu["plan"] = run_oracle_plan()
+        if not args.no_fp64_errors and basis is not None:
+            t0 = time.perf_counter()
+            cpu["fp64_errors"] = fp64_errors(mr, torch, seq, ph, alpha_h, basis, net)
+            cpu["fp64_errors"]["oracle_seconds"] = time.perf_counter() - t0
 
     launches = int(sum(stats[k]["launches"] for k in stats))
     if args.form == "surrogate":
@@ -773,9 +1075,9 @@ def main():
                            "form": args.form, "step": f"linearize + {iters} CG iterations (one J^H J v each)",
                            "cg_iters": iters, "l2": l2, "parallelism": f"replicas{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-                "cpu_baseline": cpu, "cg_check": cg_check, "plain": plain,
+                "cpu_baseline": cpu, "cg_check": cg_check, "plain": plain, "precision": precision,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
-                "recon": recon, "surrogate": surrogate_info, "shapes": shapes, "slice_profile": slice_prof,
+                "recon": recon, "learned_part": learned, "surrogate": surrogate_info, "shapes": shapes, "slice_profile": slice_prof,
                 "kernel_ms_per_step": {k: v for k, v in per_step_ms.items()}}
         print(json.dumps(line), flush=True)
     if net is not None:

@@ -108,8 +108,12 @@ def test_bench_cg_on_a_few_columns_matches_oracle(mr):
     seq, ph = synth.config("brain224")
     sub, alpha = columns(seq, ph, list(range(108, 116)))
     U = basis(sub)
-    lin = model.project_onto_basis(model.linearize(sub, alpha), U)
-    b = synth.random_params(sub.nv, 100)
+    exact = model.linearize(sub, alpha)
+    lin = model.project_onto_basis(exact, U)
+    # the bench's right-hand side: Re(J^H w) of the exact model for a seeded k-space w,
+    # unit RMS (a consistent system: rho = 0 voxels' ln T1 / ln T2 rows are in the null space)
+    g = model.jhw(exact, synth.random_kspace(sub.ntr, sub.nkx, 100))
+    b = f32(g / np.sqrt(np.mean(g * g)))
     x_ref, norms = textbook_cg(lambda v: model.gauss_newton_product(lin, v), b, ITERS)
     with mr.Plan(sub) as plan:
         plan.lowrank_set_basis(cuda(U))
@@ -147,11 +151,13 @@ def test_bench_cg_full_size(mr):
     alpha = f32(np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(),
                           ph.rho.imag.ravel()]))
     U = basis(seq)
-    b = synth.random_params(seq.nv, 100)
     with mr.Plan(seq) as plan:
+        plan.linearize(cuda(alpha))
+        g = plan.jhw(cuda(synth.random_kspace(seq.ntr, seq.nkx, 100), torch.complex64))
+        b_dev = (g / torch.sqrt(torch.mean(g * g))).contiguous()
+        b = b_dev.cpu().numpy().astype(np.float64)
         plan.lowrank_set_basis(cuda(U))
         plan.lowrank_linearize(cuda(alpha))
-        b_dev = cuda(b)
         x_gpu = plan.cg_fixed(b_dev, ITERS)
         plan.check()
         assert plan.cg_applied() == ITERS

@@ -162,3 +162,97 @@ def test_training_fits_the_projected_model(mr):
     print(f"surrogate held-out loss {L0:.3e} -> {L1:.3e}; relative errors c {err[0]:.2e} dc1 {err[1]:.2e} dc2 {err[2]:.2e}")
     assert L1 < 0.02 * L0
     assert err[0] < 5e-2
+
+
+def test_b1_map_surrogate_products_match_projected_oracle(mr):
+    """The learned-part form with a known, smooth B1 map (0.8..1.2): a surrogate trained on
+    the device on B1-varied samples gives the coefficients; the low-rank products are those
+    of the oracle model m_j = i U c_j built from exactly those coefficients (3e-5), the
+    compressed-exact products with the same map are the oracle's projected model (3e-5), and
+    the trained surrogate's Gauss-Newton product stays within 10 % of the projected exact
+    one."""
+    seq = synth.make_sequence(24, 64, 5, 7.8, 3.9, seed=4)  # ny = 64: the column path
+    R, hidden, B = 16, 128, 1024
+    train = samples(2000, 21)
+    U = f32(model.time_basis(seq, np.exp(train[0]), np.exp(train[1]), R, b1=train[2])[0])
+    rng = np.random.default_rng(22)
+    alpha = f32(np.stack([rng.uniform(np.log(300), np.log(2500), seq.nv), rng.uniform(np.log(30), np.log(250), seq.nv),
+                          rng.uniform(0.5, 1, seq.nv), rng.uniform(-0.5, 0.5, seq.nv)]))
+    b1 = f32(synth.smooth_b1(seq.nx, seq.ny, 5).ravel())
+    v = synth.random_params(seq.nv, 23)
+    w = synth.random_kspace(seq.ntr, seq.nkx, 24)
+    with mr.Plan(seq) as plan:
+        plan.lowrank_set_basis(cuda(U))
+        x = cuda(samples(32768, 25))
+        tgt = plan.lowrank_project_samples(x[:2].contiguous(), b1=x[2].contiguous())
+        scale = tgt[0].abs().amax(dim=1).clamp_min(1e-6).cpu().numpy()
+        with mr.Surrogate(hidden, R, NORM, 0.5, seed=3) as net:
+            net.set_output_scale(scale)
+            gen = torch.Generator(device="cuda").manual_seed(1)
+            for it in range(3000):
+                idx = torch.randint(0, x.shape[1], (B,), device="cuda", generator=gen)
+                net.train_step(x[:2, idx].contiguous(), tgt[:, :, idx].contiguous(), 3e-3 if it < 2000 else 1e-3,
+                               b1=x[2, idx].contiguous())
+            a, bm = cuda(alpha), cuda(b1)
+            coef = net.infer(a[:2].contiguous(), b1=bm)
+            plan.lowrank_linearize(a, b1=bm, coef=coef)
+            C = coef.cpu().numpy().astype(np.float64)
+            jv = plan.jvp(cuda(v)).cpu().numpy()
+            g = plan.jhw(cuda(w, torch.complex64)).cpu().numpy()
+            h_sur = plan.jhjv(cuda(v)).cpu().numpy()
+            plan.lowrank_linearize(a, b1=bm)
+            h_lr = plan.jhjv(cuda(v)).cpu().numpy()
+            plan.check()
+    lin_net = model.Linearization(seq, alpha, b1, np.ones(seq.nv, bool), 1j * (U @ C[0]), 1j * (U @ C[1]),
+                                  1j * (U @ C[2]), None)
+    assert metrics.relerr(jv, model.jvp(lin_net, v)) < 3e-5
+    assert metrics.relerr(g, model.jhw(lin_net, w)) < 3e-5
+    assert metrics.relerr(h_sur, model.gauss_newton_product(lin_net, v)) < 3e-5
+    lin_proj = model.project_onto_basis(model.linearize(seq, alpha, b1=b1), U)
+    ref = model.gauss_newton_product(lin_proj, v)
+    assert metrics.relerr(h_lr, ref) < 3e-5
+    e_sur = metrics.relerr(h_sur, ref)
+    # the same product with the B1 map ignored (B1 = 1 in the projected model): the map
+    # matters by far more than the surrogate's error
+    e_nob1 = metrics.relerr(model.gauss_newton_product(model.project_onto_basis(model.linearize(seq, alpha), U), v), ref)
+    print(f"surrogate J^H J v vs projected exact with the B1 map: {e_sur:.2e} (B1 map ignored: {e_nob1:.2e})")
+    assert e_sur < 0.1
+    assert e_sur < 0.5 * e_nob1
+
+
+def test_surrogate_linearisation_beats_the_exact_projection(mr):
+    """What the network buys per linearisation at 224 x 224 / 1120 TRs, rank 32: one MLP
+    inference (tcgen05) plus adopting its coefficients against projecting the exact Bloch
+    recursion onto the basis; the products afterwards cost the same.  CUDA-event times of
+    20 back-to-back linearisations each, after a warm-up."""
+    seq, ph = synth.config("brain224")
+    alpha = f32(np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(),
+                          ph.rho.imag.ravel()]))
+    R = 32
+    U = np.linalg.qr(np.random.default_rng(3).standard_normal((seq.ntr, R)))[0]
+    with mr.Plan(seq) as plan, mr.Surrogate(256, R, NORM, 0.5, seed=1) as net:
+        plan.lowrank_set_basis(cuda(f32(U)))
+        a = cuda(alpha)
+        coef = torch.empty((3, R, seq.nv), dtype=torch.float32, device="cuda")
+
+        def surrogate():
+            net.infer(a[:2], out=coef)
+            plan.lowrank_linearize(a, coef=coef)
+
+        def exact():
+            plan.lowrank_linearize(a)
+
+        def ms(fn):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / 20
+        t_sur, t_exact = ms(surrogate), ms(exact)
+        plan.check()
+    print(f"linearisation: surrogate {t_sur:.3f} ms, exact projection {t_exact:.3f} ms ({t_exact / t_sur:.1f}x)")
+    assert t_sur < t_exact / 1.5
