@@ -566,6 +566,47 @@ def gn_rhs(torch, plan, alpha, b1, seq, rank):
     return (g / torch.sqrt(torch.mean(g * g))).contiguous()
 
 
+def differentiation(mr, torch, seq, ph, reps=10):
+    """The differentiation form at the workload's size: s(alpha) as a torch.autograd.Function
+    with the loss 1/2 ||s - d||^2, forward and backward timed with CUDA events (median of
+    reps after a warm-up), with Bloch-state checkpoints every 64 TRs (the backward re-runs
+    the recursion segment by segment) and without (the forward caches the time courses);
+    device memory held by the plan after the forward, and torch's peak over the pass."""
+    from paper_1904_13244_gb300.autograd import signal
+    a0 = torch.tensor(alpha_of(ph), device="cuda")
+    d = torch.zeros((seq.ntr, seq.nkx), dtype=torch.complex64, device="cuda")
+    out = {}
+    for ck in (64, 0):
+        plan = mr.Plan(seq)
+        fw, bw = [], []
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        for i in range(reps + 1):
+            a = a0.clone().requires_grad_(True)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            s = signal(a, plan, checkpoint=ck)
+            loss = 0.5 * torch.sum(torch.abs(s - d) ** 2)
+            e1.record()
+            loss.backward()
+            e2.record()
+            torch.cuda.synchronize()
+            if i > 0:
+                fw.append(e0.elapsed_time(e1))
+                bw.append(e1.elapsed_time(e2))
+            del s, loss
+        plan.check()
+        out[f"checkpoint_{ck}" if ck else "no_checkpoint"] = {
+            "forward_ms": float(np.median(fw)), "backward_ms": float(np.median(bw)),
+            "plan_device_bytes": int(plan.info()["device_bytes"]),
+            "torch_peak_bytes": int(torch.cuda.max_memory_allocated() - base)}
+        plan.close()
+    out["note"] = ("loss 1/2 ||s - d||^2 through paper_1904_13244_gb300.autograd.signal; forward = "
+                   "Bloch recursion + encoding (+ the loss), backward = Re(J^H grad_s)")
+    return out
+
+
 def learned_part(mr, torch, args, name, rank, iters, timed):
     """The learned-part form on a workload with a smooth, known B1 map in [0.8, 1.2]: a
     rank-R basis and the surrogate trained for this sequence on B1-varied samples, then the
@@ -1025,6 +1066,11 @@ def main():
         recon["settings"] = ("15 GN x 30 CG, SNR 30, rho the exact least-squares solution at T1 1000 ms / T2 100 ms, mask 0.1; "
                              "surrogate: 10 surrogate + 5 exact iterations, low-rank CG matrix")
 
+    # the differentiation form (autograd, with and without Bloch-state checkpoints)
+    diff = None
+    if not args.no_shapes and rank == 0 and world == 1:
+        diff = differentiation(mr, torch, seq, ph)
+
     # the learned-part form (surrogate trained on B1-varied samples, known smooth B1 map) at
     # 224 x 224 / 1120 TRs and 256 x 256 / 1280 TRs: step rates of the surrogate, the
     # compressed-exact and the plain model, and the three reconstructions
@@ -1077,7 +1123,7 @@ def main():
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu, "cg_check": cg_check, "plain": plain, "precision": precision,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
-                "recon": recon, "learned_part": learned, "surrogate": surrogate_info, "shapes": shapes, "slice_profile": slice_prof,
+                "recon": recon, "learned_part": learned, "differentiation": diff, "surrogate": surrogate_info, "shapes": shapes, "slice_profile": slice_prof,
                 "kernel_ms_per_step": {k: v for k, v in per_step_ms.items()}}
         print(json.dumps(line), flush=True)
     if net is not None:

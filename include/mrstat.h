@@ -450,6 +450,13 @@ int mrstat_cg_applied(mrstat_plan* plan, int32_t* applied);
  * trust-region ratio stay exact, so the iteration converges to the exact model's
  * solution.
  *
+ * Resuming: the state of a solve between outer iterations is alpha, the mask, the trust
+ * radius and the iteration count.  A call with alpha = the previous call's result, that
+ * call's mask as input (no rho initialisation, mask_threshold = 0), delta0 = its
+ * report->delta_final and iteration_offset = the iterations run so far continues the
+ * solve exactly where it stopped (the surrogate schedule included), so a long
+ * reconstruction can be checkpointed on the host and restarted.
+ *
  * Every CG scalar lives on the device in float64; the host synchronises once per
  * outer iteration to evaluate the trust-region ratio.  Where the CG matrix is the
  * low-rank one (hessian = 1 or the surrogate phase) on a fully sampled readout with
@@ -494,16 +501,22 @@ typedef struct mrstat_gn_opts {
   int32_t hessian;             /* 0: exact Re(J^H J); 1: low-rank per-ky Gram product of
                                   the plan's time basis (mrstat_lowrank_set_basis) for the
                                   CG, with the exact gradient and objective              */
-  int32_t surrogate_iters;     /* 0..outer_iters: the first surrogate_iters outer
-                                  iterations run on the learned surrogate's low-rank
-                                  model (objective, gradient, CG products and the
-                                  trust-region ratio); the rest on the exact model       */
+  int32_t surrogate_iters;     /* 0..iteration_offset + outer_iters: the first
+                                  surrogate_iters outer iterations of the schedule run on
+                                  the learned surrogate's low-rank model (objective,
+                                  gradient, CG products and the trust-region ratio); the
+                                  rest on the exact model                                 */
   const mrstat_mlp* surrogate; /* required when surrogate_iters > 0; its rank must equal
                                   the plan's basis rank                                  */
   double b1_min, b1_max;       /* B1 box when B1 is estimated                           */
   int32_t rho_init_exact;      /* != 0: the rho initialisation is the exact least-squares
                                   solution instead of rho_init_iters CGLS steps (needs
                                   nkx == nx, b1 == NULL and ntr >= ny)                   */
+  int32_t iteration_offset;    /* >= 0: outer iterations already run by earlier calls of a
+                                  solve this call resumes; iteration k of this call is
+                                  iteration iteration_offset + k of the schedule (the
+                                  surrogate phase covers schedule iterations
+                                  0..surrogate_iters-1)                                  */
 } mrstat_gn_opts;
 
 typedef struct mrstat_gn_report {
@@ -518,6 +531,7 @@ typedef struct mrstat_gn_report {
   double ratio[MRSTAT_GN_MAX_OUTER];
   double f_final;
   double seconds;                          /* wall time of the call                 */
+  double delta_final;                      /* trust radius after the last iteration  */
 } mrstat_gn_report;
 
 /* Fill opts with the defaults: 10 x 20 iterations, delta0 from alpha_0, eta = 1e-4,

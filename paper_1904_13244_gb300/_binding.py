@@ -58,7 +58,7 @@ class mrstat_gn_opts(ctypes.Structure):
                 ("t2_init_ms", ctypes.c_double), ("mask_threshold", ctypes.c_double),
                 ("hessian", ctypes.c_int32), ("surrogate_iters", ctypes.c_int32),
                 ("surrogate", ctypes.c_void_p), ("b1_min", ctypes.c_double), ("b1_max", ctypes.c_double),
-                ("rho_init_exact", ctypes.c_int32)]
+                ("rho_init_exact", ctypes.c_int32), ("iteration_offset", ctypes.c_int32)]
 
 
 class mrstat_slice_profile(ctypes.Structure):
@@ -72,7 +72,7 @@ class mrstat_gn_report(ctypes.Structure):
                 ("accepted", ctypes.c_int32 * GN_MAX_OUTER), ("f", ctypes.c_double * GN_MAX_OUTER),
                 ("gnorm", ctypes.c_double * GN_MAX_OUTER), ("delta", ctypes.c_double * GN_MAX_OUTER),
                 ("ratio", ctypes.c_double * GN_MAX_OUTER), ("f_final", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("delta_final", ctypes.c_double)]
 
 
 class mrstat_mlp_config(ctypes.Structure):
@@ -403,7 +403,8 @@ def mrstat_gn_solve(plan, d, alpha, b1=None, mask=None, opts=None, stream=None) 
     return {"iterations": k, "mask_voxels": rep.mask_voxels, "f": list(rep.f[:k]), "gnorm": list(rep.gnorm[:k]),
             "delta": list(rep.delta[:k]), "ratio": list(rep.ratio[:k]), "cg_steps": list(rep.cg_steps[:k]),
             "cg_exit": [CG_EXIT.get(x, str(x)) for x in rep.cg_exit[:k]],
-            "accepted": [bool(x) for x in rep.accepted[:k]], "f_final": rep.f_final, "seconds": rep.seconds}
+            "accepted": [bool(x) for x in rep.accepted[:k]], "f_final": rep.f_final, "seconds": rep.seconds,
+            "delta_final": rep.delta_final}
 
 
 def mrstat_profile_start(plan, kernels=("ycontract", "jhw_dot")):

@@ -7,6 +7,7 @@
 // formed, and once CG has stopped the product kernels return at once through the plan's
 // gate flag.  The host waits
 // once per outer iteration, to evaluate the trust-region ratio in float64.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -721,6 +722,7 @@ void mrstat_gn_default_opts(mrstat_gn_opts* o) {
 
 int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const float* b1, uint8_t* mask,
                     const mrstat_gn_opts* o, mrstat_gn_report* rep, void* stream) {
+  MRSTAT_ABI_RANGE();
   Plan* p = reinterpret_cast<Plan*>(plan_);
   if (p == nullptr || d == nullptr || alpha == nullptr || o == nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, d, alpha or opts");
@@ -747,10 +749,15 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
     return fail(MRSTAT_ERR_UNSUPPORTED, "with the slice profile: exact Hessian, no surrogate, B1 = 1");
   if (o->hessian == 1 && p->lr == nullptr)
     return fail(MRSTAT_ERR_NOT_LINEARIZED, "the low-rank Hessian needs mrstat_lowrank_set_basis first");
-  if (o->surrogate_iters < 0 || o->surrogate_iters > o->outer_iters)
-    return fail(MRSTAT_ERR_INVALID_ARG, "surrogate_iters must lie in 0..outer_iters");
+  if (o->iteration_offset < 0) return fail(MRSTAT_ERR_INVALID_ARG, "iteration_offset must be >= 0");
+  const int k0 = o->iteration_offset;  // schedule index of this call's first iteration
+  if (o->surrogate_iters < 0 || o->surrogate_iters > k0 + o->outer_iters)
+    return fail(MRSTAT_ERR_INVALID_ARG, "surrogate_iters must lie in 0..iteration_offset + outer_iters");
+  // outer iterations of this call that run on the surrogate: schedule iterations below
+  // surrogate_iters
+  const int sur_iters = std::max(0, std::min(o->outer_iters, o->surrogate_iters - k0));
   Mlp* net = nullptr;
-  if (o->surrogate_iters > 0) {
+  if (sur_iters > 0) {
     if (o->surrogate == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "surrogate_iters > 0 needs a surrogate");
     if (p->lr == nullptr)
       return fail(MRSTAT_ERR_NOT_LINEARIZED, "the surrogate phase needs mrstat_lowrank_set_basis first");
@@ -834,7 +841,7 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   };
 
   // -- current point --
-  if (o->surrogate_iters > 0) {
+  if (sur_iters > 0) {
     status = sur_linearize(p->gn_alpha, p->rho, p->lr->coef);
     p->lr->coefT_dirty = true;
     if (status == MRSTAT_OK) status = sur_signal(p->gn_alpha, p->gn_s);
@@ -873,8 +880,8 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
   const float lt2a = (float)std::log(o->t2_min_ms), lt2b = (float)std::log(o->t2_max_ms);
 
   for (int k = 0; k < o->outer_iters; ++k) {
-    const bool sur = k < o->surrogate_iters;
-    if (k > 0 && k == o->surrogate_iters) {
+    const bool sur = k < sur_iters;
+    if (k > 0 && k == sur_iters) {
       // leave the surrogate: exact objective at the current point from here on
       p->lr->active = false;
       status = exact_point();
@@ -953,9 +960,10 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
     }
   }
   local.f_final = f;
+  local.delta_final = delta;
   // the plan's cached linearisation is the one at the returned alpha (mask gn_mask): the
   // exact one, or the surrogate's low-rank one when every iteration used the surrogate
-  if (p->lr) p->lr->active = o->surrogate_iters > 0 && o->surrogate_iters == o->outer_iters;
+  if (p->lr) p->lr->active = sur_iters > 0 && sur_iters == o->outer_iters;
   e = cudaMemcpyAsync(alpha, p->gn_alpha, (size_t)p->npar * nv * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "Gauss-Newton result");

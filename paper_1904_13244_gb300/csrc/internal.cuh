@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -153,6 +154,16 @@ inline cudaError_t dalloc(Plan* p, T** ptr, size_t count) {
 cudaEvent_t pool_event(Plan* p);
 
 // Counts the launches of one kernel class and, while profiling it, brackets them with events.
+// NVTX range over one C-ABI call (header-only NVTX3: a no-op unless a profiler injects
+// itself), so that a timeline shows the library's calls around their kernels.
+struct AbiRange {
+  explicit AbiRange(const char* name) { nvtxRangePushA(name); }
+  ~AbiRange() { nvtxRangePop(); }
+  AbiRange(const AbiRange&) = delete;
+  AbiRange& operator=(const AbiRange&) = delete;
+};
+#define MRSTAT_ABI_RANGE() ::mrstat::AbiRange mrstat_abi_range_(__func__)
+
 struct Span {
   Plan* p;
   int kid;

@@ -74,6 +74,7 @@ using namespace mrstat;
 extern "C" {
 
 int mrstat_lowrank_set_basis(mrstat_plan* plan_, const float* U, int32_t rank, void* stream) {
+  MRSTAT_ABI_RANGE();
   Plan* p = reinterpret_cast<Plan*>(plan_);
   if (p == nullptr || U == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or basis");
   if (p->npar != 4) return fail(MRSTAT_ERR_UNSUPPORTED, "the low-rank form does not estimate B1");
@@ -84,6 +85,7 @@ int mrstat_lowrank_set_basis(mrstat_plan* plan_, const float* U, int32_t rank, v
 
 int mrstat_lowrank_linearize(mrstat_plan* plan_, const float* alpha, const float* b1, const uint8_t* mask,
                              const float* coef, void* stream) {
+  MRSTAT_ABI_RANGE();
   Plan* p = reinterpret_cast<Plan*>(plan_);
   if (p == nullptr || alpha == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or alpha");
   if (p->slice_iso > 0) return fail(MRSTAT_ERR_UNSUPPORTED, "the low-rank forms use the hard-pulse model");
@@ -113,6 +115,7 @@ int mrstat_lowrank_linearize(mrstat_plan* plan_, const float* alpha, const float
 }
 
 int mrstat_lowrank_coefficients(mrstat_plan* plan_, float* coef, void* stream) {
+  MRSTAT_ABI_RANGE();
   Plan* p = reinterpret_cast<Plan*>(plan_);
   if (p == nullptr || coef == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or coef");
   if (p->lr == nullptr || !p->lr->active)
@@ -125,6 +128,7 @@ int mrstat_lowrank_coefficients(mrstat_plan* plan_, float* coef, void* stream) {
 
 int mrstat_lowrank_project_samples(mrstat_plan* plan_, const float* params, const float* b1, int32_t ns,
                                    float* coef, void* stream) {
+  MRSTAT_ABI_RANGE();
   Plan* p = reinterpret_cast<Plan*>(plan_);
   if (p == nullptr || params == nullptr || coef == nullptr || ns < 1)
     return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_lowrank_project_samples");
@@ -154,6 +158,7 @@ int mrstat_lowrank_rank(const mrstat_plan* plan_) {
 
 int mrstat_lowrank_basis(mrstat_plan* plan_, const float* train, const float* train_b1, int32_t ns,
                          int32_t rank, float* U_out, double* sv_out, void* stream) {
+  MRSTAT_ABI_RANGE();
   Plan* p = reinterpret_cast<Plan*>(plan_);
   if (p == nullptr || train == nullptr || U_out == nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, training set or output");

@@ -800,6 +800,7 @@ int mrstat_mlp_set_params(mrstat_mlp* m, const float* host) {
 }
 
 int mrstat_mlp_infer(mrstat_mlp* m, const float* lnT, const float* b1, int32_t n, float* coef, void* stream) {
+  MRSTAT_ABI_RANGE();
   if (m == nullptr || lnT == nullptr || coef == nullptr || n < 1)
     return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_mlp_infer");
   DeviceGuard g(m->device);
@@ -808,6 +809,7 @@ int mrstat_mlp_infer(mrstat_mlp* m, const float* lnT, const float* b1, int32_t n
 
 int mrstat_mlp_train_step(mrstat_mlp* m, const float* lnT, const float* b1, const float* target, int32_t B, float lr,
                           double* loss_out, void* stream) {
+  MRSTAT_ABI_RANGE();
   if (m == nullptr || lnT == nullptr || target == nullptr || B < 1 || !(lr >= 0))
     return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_mlp_train_step");
   DeviceGuard g(m->device);
@@ -825,6 +827,7 @@ int mrstat_mlp_train_step(mrstat_mlp* m, const float* lnT, const float* b1, cons
 
 int mrstat_mlp_loss_grad(mrstat_mlp* m, const float* lnT, const float* b1, const float* target, int32_t B,
                          double* loss_host, float* grad, void* stream) {
+  MRSTAT_ABI_RANGE();
   if (m == nullptr || lnT == nullptr || target == nullptr || B < 1)
     return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_mlp_loss_grad");
   DeviceGuard g(m->device);

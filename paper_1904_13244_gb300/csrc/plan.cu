@@ -332,6 +332,7 @@ int mrstat_plan_inject_grid_stall(mrstat_plan* plan, int32_t block) {
 }
 
 int mrstat_plan_check(mrstat_plan* plan) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan");
   DeviceGuard g(plan->device);
   int flag = 0;
@@ -378,6 +379,7 @@ int mrstat_profile_stop(mrstat_plan* plan, mrstat_kernel_stats* out) {
 }
 
 int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
+  MRSTAT_ABI_RANGE();
   g_last_error.clear();
   if (out == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -518,6 +520,7 @@ int mrstat_plan_create(const mrstat_seq* seq, int32_t form, mrstat_plan** out) {
 }
 
 int mrstat_plan_destroy(mrstat_plan* plan) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr) return MRSTAT_OK;
   DeviceGuard g(plan->device);
   cudaDeviceSynchronize();
@@ -542,6 +545,7 @@ int mrstat_plan_info(const mrstat_plan* plan, mrstat_plan_info_t* info) {
 
 int mrstat_linearize(mrstat_plan* plan, const float* alpha, const float* b1, const uint8_t* mask,
                      void* stream) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr || alpha == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or alpha");
   if (plan->npar == 5 && b1 != nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "B1 is estimated (alpha row 4): pass b1 = NULL");
@@ -559,6 +563,7 @@ int mrstat_linearize(mrstat_plan* plan, const float* alpha, const float* b1, con
 
 int mrstat_forward(mrstat_plan* plan, const float* alpha, const float* b1, const uint8_t* mask,
                    float* s, void* stream) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr || alpha == nullptr || s == nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, alpha or s");
   if (plan->npar == 5 && b1 != nullptr)
@@ -589,6 +594,7 @@ int mrstat_forward(mrstat_plan* plan, const float* alpha, const float* b1, const
 }
 
 int mrstat_jvp(mrstat_plan* plan, const float* v, float* jv, void* stream) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr || v == nullptr || jv == nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, v or jv");
   if (!plan->linearized) return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_jvp before mrstat_linearize");
@@ -598,6 +604,7 @@ int mrstat_jvp(mrstat_plan* plan, const float* v, float* jv, void* stream) {
 }
 
 int mrstat_jhw(mrstat_plan* plan, const float* w, float* gout, void* stream) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr || w == nullptr || gout == nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, w or g");
   if (!plan->linearized) return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_jhw before mrstat_linearize");
@@ -607,6 +614,7 @@ int mrstat_jhw(mrstat_plan* plan, const float* w, float* gout, void* stream) {
 }
 
 int mrstat_timecourses(mrstat_plan* plan, int32_t channel, float* out, void* stream) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr || out == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or out");
   if (channel < 0 || channel >= plan->nch)
     return fail(MRSTAT_ERR_INVALID_ARG, "channel %d not in [0, %d)", channel, plan->nch);
@@ -620,6 +628,7 @@ int mrstat_timecourses(mrstat_plan* plan, int32_t channel, float* out, void* str
 
 int mrstat_dot(mrstat_plan* plan, const float* a, const float* b, int64_t n, double* out,
                void* stream) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr || out == nullptr || n < 0 || (n > 0 && (a == nullptr || b == nullptr)))
     return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_dot");
   DeviceGuard g(plan->device);
@@ -629,6 +638,7 @@ int mrstat_dot(mrstat_plan* plan, const float* a, const float* b, int64_t n, dou
 
 int mrstat_forward_ckpt(mrstat_plan* plan, const float* alpha, const float* b1, const uint8_t* mask,
                         int32_t interval, float* s, void* stream) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr || alpha == nullptr || s == nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, alpha or s");
   if (interval < 4 || interval % 4 != 0)
@@ -682,6 +692,7 @@ int mrstat_forward_ckpt(mrstat_plan* plan, const float* alpha, const float* b1, 
 }
 
 int mrstat_jhw_ckpt(mrstat_plan* plan, const float* w, float* gout, void* stream) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr || w == nullptr || gout == nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, w or g");
   if (!plan->ckpt_ready)
@@ -700,6 +711,7 @@ int mrstat_jhw_ckpt(mrstat_plan* plan, const float* w, float* gout, void* stream
 }
 
 int mrstat_jhjv(mrstat_plan* plan, const float* v, float* out, void* stream) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr || v == nullptr || out == nullptr)
     return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan, v or out");
   if (!plan->linearized) return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_jhjv before a linearisation");
@@ -708,6 +720,7 @@ int mrstat_jhjv(mrstat_plan* plan, const float* v, float* out, void* stream) {
 }
 
 int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters, void* stream) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr || rhs == nullptr || x == nullptr || iters < 0)
     return fail(MRSTAT_ERR_INVALID_ARG, "bad argument to mrstat_cg_fixed");
   if (!plan->linearized) return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_cg_fixed before mrstat_linearize");
@@ -763,6 +776,7 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
 }
 
 int mrstat_cg_applied(mrstat_plan* plan, int32_t* applied) {
+  MRSTAT_ABI_RANGE();
   if (plan == nullptr || applied == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or applied");
   if (plan->cg_last_iters < 0) return fail(MRSTAT_ERR_NOT_LINEARIZED, "mrstat_cg_applied before mrstat_cg_fixed");
   DeviceGuard g(plan->device);

@@ -185,6 +185,7 @@ using namespace mrstat;
 extern "C" {
 
 int mrstat_set_slice_profile(mrstat_plan* plan, const mrstat_slice_profile* prof) {
+  MRSTAT_ABI_RANGE();
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (p == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan");
   DeviceGuard g(p->device);

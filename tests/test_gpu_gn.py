@@ -415,3 +415,35 @@ def test_lowrank_hessian_steihaug_column_path_converges_under_a_mask(mr):
     trial = np.where(mask[None], solver.apply_bounds(a0 + z, solver.GNOptions()), a0)
     assert metrics.relerr(a_gpu - a0, trial - a0) < 1e-3
     assert np.array_equal(a_gpu[:, ~mask], a0[:, ~mask].astype(np.float32))
+
+
+def test_resumed_solve_continues_where_it_stopped(mr, noisy_quad):
+    """Checkpoint and resume on the host: 3 + 3 outer iterations (the second call starts
+    from the first's alpha, its mask, report delta_final and iteration_offset = 3) follow
+    the same trajectory as 6 iterations in one call, also with a surrogate phase of 4
+    iterations that straddles the break."""
+    seq, ph, truth, d, a0 = noisy_quad
+    mask = torch.ones(seq.nv, dtype=torch.uint8, device="cuda")
+    mask[::7] = 0
+    dd = cuda(d, torch.complex64)
+    with mr.Plan(seq) as plan:
+        plan.lowrank_set_basis(_basis(plan, 16))
+        net = _trained_surrogate(mr, plan, 16)
+        for kw in (dict(), dict(hessian=1, surrogate_iters=4, surrogate=net)):
+            a_one = cuda(a0)
+            rep = plan.gn_solve(dd, a_one, mask=mask.clone(), outer_iters=6, inner_iters=15, **kw)
+            a_two = cuda(a0)
+            r1 = plan.gn_solve(dd, a_two, mask=mask.clone(), outer_iters=3, inner_iters=15, **kw)
+            r2 = plan.gn_solve(dd, a_two, mask=mask.clone(), outer_iters=3, inner_iters=15,
+                               delta0=r1["delta_final"], iteration_offset=3, **kw)
+            f_two = r1["f"] + r2["f"]
+            assert np.allclose(f_two, rep["f"], rtol=1e-6), (kw, f_two, rep["f"])
+            assert r1["delta"] + r2["delta"] == pytest.approx(rep["delta"], rel=1e-9)
+            assert r2["delta_final"] == pytest.approx(rep["delta_final"], rel=1e-9)
+            assert r2["f_final"] == pytest.approx(rep["f_final"], rel=1e-6)
+            assert metrics.relerr(a_two.cpu().numpy(), a_one.cpu().numpy()) < 1e-6
+        with pytest.raises(mr.MrstatError) as e:
+            plan.gn_solve(dd, cuda(a0), outer_iters=2, iteration_offset=-1)
+        assert e.value.status == 1
+        plan.check()
+        net.close()
