@@ -82,6 +82,8 @@ def parse_args():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="brain224")
     ap.add_argument("--cg-iters", type=int, default=30)
+    ap.add_argument("--segment", type=int, default=140,
+                    help="TRs per segment of the plain form's recompute variant")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-plan", action="store_true",
@@ -758,12 +760,24 @@ def main():
     # the plain FP32 form on the same inputs, for the comparison the metric asks for
     plain = None
     if args.form != "plain":
+        # the plain FP32 form in both variants, cached time courses and the recompute form
+        # (the recursion re-run inside every product from states every `segment` TRs); the
+        # faster one is the plain form the comparison uses
         pplan = mr.Plan(seq)
-        pms, pstats, _ = timed(pplan, make_step(pplan, "plain"), max(1, args.steps // 4), all_kernels)
-        info = pplan.info()
+        nst = max(1, args.steps // 4)
+        pms, pstats, _ = timed(pplan, make_step(pplan, "plain"), nst, all_kernels)
+        stored = {"value": world * iters / (pms / 1e3), "ms_per_step": pms,
+                  "kernel_ms_per_step": {k: pstats[k]["ms"] / nst for k in all_kernels}}
+        pplan.set_recompute(args.segment)
+        rms, rstats, _ = timed(pplan, make_step(pplan, "plain"), nst, all_kernels)
+        pplan.check()
+        recompute = {"value": world * iters / (rms / 1e3), "ms_per_step": rms, "segment": args.segment,
+                     "kernel_ms_per_step": {k: rstats[k]["ms"] / nst for k in all_kernels},
+                     "cg_iterations_applied": pplan.cg_applied()}
         pplan.close()
-        plain = {"value": world * iters / (pms / 1e3), "ms_per_step": pms,
-                 "kernel_ms_per_step": {k: pstats[k]["ms"] / max(1, args.steps // 4) for k in all_kernels}}
+        best = "recompute" if recompute["value"] > stored["value"] else "stored"
+        plain = dict((recompute if best == "recompute" else stored), variant=best, stored=stored,
+                     recompute=recompute)
 
     # the precision form: the exact model with the readout DFTs as split-BF16 tcgen05
     # products (s, J.v and Re(J^H w); inside J^H J v the readout DFT pair cancels because

@@ -197,6 +197,24 @@ int mrstat_jhw(mrstat_plan* plan, const float* w, float* g, void* stream);
 int mrstat_timecourses(mrstat_plan* plan, int32_t channel, float* out, void* stream);
 
 /*
+ * Recompute form of the exact model.  The paper evaluates every matrix-free product by
+ * running the Bloch simulation again (Algorithms 2 and 4); with segment > 0 the plan does
+ * the same instead of caching the time courses: mrstat_linearize keeps, per voxel, the
+ * relaxation factors and the Bloch state (m_y, m_z and their ln T1 / ln T2 tangents)
+ * before every segment-th TR (6 floats per voxel and segment), and every mrstat_jvp,
+ * mrstat_jhw, mrstat_jhjv and mrstat_cg_fixed product re-runs the recursion from those
+ * states, all segments in parallel, fused with the phase-encode sums (and, for
+ * Re(J^H J) v with nkx == nx, with both of them in one pass).  The results are those of
+ * the cached form up to float32 rounding.  segment = 0 restores the cached time courses.
+ * Either way the cached linearisation is dropped.  Synchronises the plan's device.
+ *   segment: TRs per segment (>= 0; values above ntr mean one segment).
+ * The recompute form needs ny <= 256, B1 known or 1 (not estimated) and hard pulses
+ * (else UNSUPPORTED); mrstat_timecourses and mrstat_gn_solve return UNSUPPORTED while it
+ * is on.  Errors: INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY, CUDA.
+ */
+int mrstat_set_recompute(mrstat_plan* plan, int32_t segment);
+
+/*
  * Checkpointed signal and gradient (differentiation by recomputation).
  *
  * mrstat_forward_ckpt computes s like mrstat_forward and keeps, instead of the time

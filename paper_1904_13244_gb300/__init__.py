@@ -20,7 +20,7 @@ from ._binding import (MrstatError, MRSTAT_FORM_PLAIN_FP32, MRSTAT_FORM_SPLIT_BF
                        mrstat_plan_create, mrstat_plan_destroy, mrstat_plan_info, mrstat_linearize,
                        mrstat_plan_inject_grid_stall,
                        mrstat_forward, mrstat_jvp, mrstat_jhw, mrstat_timecourses, mrstat_dot,
-                       mrstat_cg_fixed, mrstat_cg_applied, mrstat_status_string, mrstat_last_error,
+                       mrstat_cg_fixed, mrstat_cg_applied, mrstat_set_recompute, mrstat_status_string, mrstat_last_error,
                        mrstat_profile_start, mrstat_profile_stop, mrstat_gn_default_opts,
                        mrstat_gn_solve, mrstat_plan_check, mrstat_forward_ckpt, mrstat_jhw_ckpt,
                        mrstat_jhjv, mrstat_lowrank_basis, mrstat_lowrank_set_basis, mrstat_lowrank_linearize,
@@ -185,6 +185,12 @@ class Plan:
         out = self._params(out)
         mrstat_cg_fixed(self._h, rhs, out, iters, stream)
         return out
+
+    def set_recompute(self, segment: int):
+        """segment > 0: re-run the Bloch recursion inside every product from states kept
+        every `segment` TRs (no cached time courses); 0: cached time courses.  Drops the
+        cached linearisation."""
+        mrstat_set_recompute(self._h, segment)
 
     def cg_applied(self) -> int:
         """Iterations the last cg_fixed applied (its iters unless the solve froze);

@@ -127,6 +127,7 @@ _SIGS = {
                    ctypes.c_void_p],
     "mrstat_cg_fixed": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
     "mrstat_cg_applied": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)],
+    "mrstat_set_recompute": [ctypes.c_void_p, ctypes.c_int32],
     "mrstat_gn_default_opts": [ctypes.POINTER(mrstat_gn_opts)],
     "mrstat_gn_solve": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                         ctypes.POINTER(mrstat_gn_opts), ctypes.POINTER(mrstat_gn_report), ctypes.c_void_p],
@@ -359,6 +360,10 @@ def mrstat_cg_fixed(plan, rhs, x, iters, stream=None):
     _check(load().mrstat_cg_fixed(plan, _ptr(rhs, torch.float32, (npar, nv), "rhs"),
                                   _ptr(x, torch.float32, (npar, nv), "x"), int(iters), _stream(stream)),
            "mrstat_cg_fixed")
+
+
+def mrstat_set_recompute(plan, segment):
+    _check(load().mrstat_set_recompute(plan, int(segment)), "mrstat_set_recompute")
 
 
 def mrstat_cg_applied(plan) -> int:

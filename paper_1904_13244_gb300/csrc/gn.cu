@@ -745,6 +745,8 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
     if (o->hessian != 0 || o->surrogate_iters != 0)
       return fail(MRSTAT_ERR_UNSUPPORTED, "the low-rank and surrogate models do not estimate B1");
   }
+  if (p->rc_seg > 0)
+    return fail(MRSTAT_ERR_UNSUPPORTED, "the Gauss-Newton solve uses cached time courses (mrstat_set_recompute 0)");
   if (p->slice_iso > 0 && (o->hessian != 0 || o->surrogate_iters != 0 || b1 != nullptr))
     return fail(MRSTAT_ERR_UNSUPPORTED, "with the slice profile: exact Hessian, no surrogate, B1 = 1");
   if (o->hessian == 1 && p->lr == nullptr)

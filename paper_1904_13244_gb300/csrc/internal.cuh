@@ -105,6 +105,14 @@ struct Plan {
   const uint8_t* ckpt_mask = nullptr;
   bool ckpt_ready = false;
 
+  // recompute form (mrstat_set_recompute): states every rc_seg TRs instead of D
+  int rc_seg = 0, rc_nseg = 0;  // 0: cached time courses
+  float* rc_rlx = nullptr;      // [8][nv] relaxation factors of the linearisation
+  float* rc_ckpt = nullptr;     // [rc_nseg][6][nv] states before each segment
+  float* rc_gpart = nullptr;    // [rc_nseg][4][nv] per-segment gradients
+  float* rc_b1 = nullptr;       // [nv] copy of the linearisation's B1 map
+  bool rc_has_b1 = false;
+
   // kernels of the products return at once while *gate == 0 (nullptr: always run)
   const int* gate = nullptr;
 
@@ -255,6 +263,11 @@ cudaError_t launch_bloch_slice(const Plan& p, const float* alpha, const uint8_t*
 // the same recursion for nv_override voxels laid out [2][nv_override] (ln T1, ln T2)
 cudaError_t launch_bloch_n(const Plan& p, const float* alpha, const float* b1, float4* D, int nv_override,
                            cudaStream_t st);
+// recompute form (fused.cu)
+bool recompute_supported(const Plan& p);
+cudaError_t launch_rc_linearize(const Plan& p, const float* alpha, const float* b1, cudaStream_t st);
+cudaError_t launch_rc_product(const Plan& p, int mode, const float* v, const float2* wt, float* g, cudaStream_t st);
+
 cudaError_t launch_bloch_ckpt(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,
                               int interval, int nseg, float* ckpt, cudaStream_t st);
 cudaError_t launch_segment_jhw(const Plan& p, const float* alpha, const float* b1, const uint8_t* mask,

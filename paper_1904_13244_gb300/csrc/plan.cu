@@ -1,4 +1,5 @@
 // Host side of libmrstat: plan life cycle, per-TR tables and the C entry points.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -44,7 +45,8 @@ void free_plan(Plan* p) {
                   p->cg_jv, p->cg_s, p->cg_frozen, p->D2, p->rho2, p->gn_g, p->gn_z, p->gn_res,
                   p->gn_dir, p->gn_q, p->gn_alpha, p->gn_trial, p->gn_s, p->gn_r, p->gn_st,
                   p->gn_rt, p->gn_jv, p->gn_mask, p->gn_sc, p->gn_si, p->bf_ft_hi, p->bf_ft_lo,
-                  p->bf_fh_hi, p->bf_fh_lo, p->bf_a_hi, p->bf_a_lo, p->bf_w_hi, p->bf_w_lo, p->dev_err, p->ckpt, p->zpart};
+                  p->bf_fh_hi, p->bf_fh_lo, p->bf_a_hi, p->bf_a_lo, p->bf_w_hi, p->bf_w_lo, p->dev_err, p->ckpt, p->zpart,
+                  p->rc_rlx, p->rc_ckpt, p->rc_gpart, p->rc_b1};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
@@ -155,6 +157,14 @@ cudaEvent_t pool_event(Plan* p) {
 
 int do_jvp(Plan* p, const float* v, float2* jv, cudaStream_t st) {
   cudaError_t e;
+  if (p->rc_seg > 0) {
+    {
+      Span sp(p, MRSTAT_K_YCONTRACT, st);
+      e = launch_rc_product(*p, 0, v, nullptr, nullptr, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "recompute J.v launch");
+    return do_xdft(p, p->A, jv, p->gate, st);
+  }
   {
     Span sp(p, MRSTAT_K_VECTOR, st);
     e = launch_prep_jvp(*p, v, st);
@@ -172,6 +182,13 @@ int do_jhw(Plan* p, const float2* w, float* g, cudaStream_t st) {
   const int status = do_xdft_adj(p, w, p->wt, p->gate, st);
   if (status != MRSTAT_OK) return status;
   cudaError_t e;
+  if (p->rc_seg > 0) {
+    {
+      Span sp(p, MRSTAT_K_JHW_DOT, st);
+      e = launch_rc_product(*p, 1, nullptr, p->wt, g, st);
+    }
+    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "recompute J^H w launch");
+  }
   {
     Span sp(p, MRSTAT_K_JHW_DOT, st);
     e = launch_jhw_dot(*p, g, st);
@@ -269,6 +286,15 @@ int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot, 
     if (s != MRSTAT_OK) return s;
     const cudaError_t e = do_dot(p, v, out, (int64_t)p->npar * p->nv, vdot, st);
     return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "dot launch");
+  }
+  if (p->nkx == p->nx && p->rc_seg > 0) {
+    // the simulation, both phase-encode sums and the tangent products in one pass
+    cudaError_t e;
+    {
+      Span sp(p, MRSTAT_K_JHW_DOT, st);
+      e = launch_rc_product(*p, 2, v, nullptr, out, st);
+    }
+    return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "recompute J^H J v launch");
   }
   if (p->nkx == p->nx) {
     cudaError_t e;
@@ -553,6 +579,24 @@ int mrstat_linearize(mrstat_plan* plan, const float* alpha, const float* b1, con
   cudaStream_t st = as_stream(stream);
   plan->linearized = false;
   if (plan->lr) plan->lr->active = false;
+  if (plan->rc_seg > 0) {
+    // recompute form: rho, the mask, the B1 map, relaxation factors and segment states
+    cudaError_t e;
+    {
+      Span sp(plan, MRSTAT_K_VECTOR, st);
+      e = launch_prep_linearize(*plan, alpha, mask, plan->rho, st);
+    }
+    plan->rc_has_b1 = b1 != nullptr;
+    if (e == cudaSuccess && b1 != nullptr)
+      e = cudaMemcpyAsync(plan->rc_b1, b1, (size_t)plan->nv * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {
+      Span sp(plan, MRSTAT_K_BLOCH, st);
+      e = launch_rc_linearize(*plan, alpha, b1, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "recompute linearisation");
+    plan->linearized = true;
+    return MRSTAT_OK;
+  }
   cudaError_t ea = ensure_timecourses(plan);
   if (ea != cudaSuccess) return cuda_fail(ea, "time-course allocation");
   const int status = do_linearize(plan, alpha, b1, mask, plan->D, plan->rho, st);
@@ -618,6 +662,7 @@ int mrstat_timecourses(mrstat_plan* plan, int32_t channel, float* out, void* str
   if (plan == nullptr || out == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or out");
   if (channel < 0 || channel >= plan->nch)
     return fail(MRSTAT_ERR_INVALID_ARG, "channel %d not in [0, %d)", channel, plan->nch);
+  if (plan->rc_seg > 0) return fail(MRSTAT_ERR_UNSUPPORTED, "the recompute form keeps no time courses");
   if (!plan->linearized || plan->D == nullptr || (plan->lr && plan->lr->active))
     return fail(MRSTAT_ERR_NOT_LINEARIZED, "timecourses need an exact mrstat_linearize");
   DeviceGuard g(plan->device);
@@ -772,6 +817,47 @@ int mrstat_cg_fixed(mrstat_plan* plan, const float* rhs, float* x, int32_t iters
     if (e != cudaSuccess) return cuda_fail(e, "CG iteration");
   }
   plan->cg_last_iters = iters;
+  return MRSTAT_OK;
+}
+
+int mrstat_set_recompute(mrstat_plan* plan, int32_t segment) {
+  MRSTAT_ABI_RANGE();
+  if (plan == nullptr || segment < 0) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan or negative segment");
+  if (segment > 0 && !recompute_supported(*plan))
+    return fail(MRSTAT_ERR_UNSUPPORTED, "the recompute form needs ny <= 256, B1 known (npar 4) and hard pulses");
+  DeviceGuard g(plan->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "recompute set-up");
+  auto release = [&](float*& q, size_t count) {
+    if (q) {
+      cudaFree(q);
+      plan->bytes -= (int64_t)(count * sizeof(float));
+      q = nullptr;
+    }
+  };
+  const size_t nv = (size_t)plan->nv;
+  release(plan->rc_rlx, 8 * nv);
+  release(plan->rc_ckpt, (size_t)plan->rc_nseg * 6 * nv);
+  release(plan->rc_gpart, (size_t)plan->rc_nseg * 4 * nv);
+  release(plan->rc_b1, nv);
+  plan->rc_seg = 0;
+  plan->rc_nseg = 0;
+  plan->linearized = false;
+  if (plan->lr) plan->lr->active = false;
+  if (segment == 0) return MRSTAT_OK;
+  const int seg = std::min<int>(segment, plan->ntr);
+  const int nseg = (plan->ntr + seg - 1) / seg;
+  e = dalloc(plan, &plan->rc_rlx, 8 * nv);
+  if (e == cudaSuccess) e = dalloc(plan, &plan->rc_ckpt, (size_t)nseg * 6 * nv);
+  if (e == cudaSuccess) e = dalloc(plan, &plan->rc_gpart, (size_t)nseg * 4 * nv);
+  if (e == cudaSuccess) e = dalloc(plan, &plan->rc_b1, nv);
+  plan->rc_seg = seg;
+  plan->rc_nseg = nseg;
+  if (e != cudaSuccess) {
+    const int s = cuda_fail(e, "recompute work space");
+    mrstat_set_recompute(plan, 0);
+    return s;
+  }
   return MRSTAT_OK;
 }
 
