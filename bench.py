@@ -89,7 +89,7 @@ def parse_args():
     ap.add_argument("--cpu-plan", action="store_true",
                     help="also run the oracle's full CPU baseline plan (single-threaded and all cores; minutes)")
     ap.add_argument("--oracle-plan-worker", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--form", default="surrogate", choices=["surrogate", "lowrank", "plain", "split"])
+    ap.add_argument("--form", default="surrogate", choices=["surrogate", "lowrank", "plain", "recompute", "split"])
     ap.add_argument("--hidden", type=int, default=256)
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--rank", type=int, default=32)
@@ -694,6 +694,8 @@ def main():
     a_dev = torch.tensor(alpha_h, device="cuda")
     rhs_dev = gn_rhs(torch, plan, a_dev, None, seq, rank)
     rhs_h = rhs_dev.cpu().numpy()
+    if args.form == "recompute":
+        plan.set_recompute(args.segment)
     x_dev = torch.empty_like(rhs_dev)
     stream = torch.cuda.current_stream()
     basis = None
@@ -759,7 +761,7 @@ def main():
 
     # the plain FP32 form on the same inputs, for the comparison the metric asks for
     plain = None
-    if args.form != "plain":
+    if args.form not in ("plain", "recompute"):
         # the plain FP32 form in both variants, cached time courses and the recompute form
         # (the recursion re-run inside every product from states every `segment` TRs); the
         # faster one is the plain form the comparison uses
@@ -961,6 +963,12 @@ def main():
     elif lowrank_like:
         gemm_flops = 3 * 2 * (R * ny * (2 * nkx) * (2 * nx) + R * nkx * (2 * ny) * (2 * ny))
         work = {"xdft": (gemm_flops / 2, "tensor"), "xdft_adj": (gemm_flops / 2, "tensor")}
+    elif args.form == "recompute" and full_readout:
+        # one fused launch per product: 86 flops per voxel-TR (the rotation of m and both
+        # tangents 18, two relaxations with the tangents' sources 34, the combination with
+        # v and the phase 15, the adjoint phase and the four tangent products 17, the block
+        # sums 2)
+        work = {"jhw_dot": (86.0 * nv * ntr, "alu")}
     else:
         work = {"jhw_dot": (d_bytes + ntr_pad * nx * 8 + nv * (8 + 4 + 16) + ntr_pad * 4, "hbm"),
                 "ycontract": (d_bytes + nv * 24 + ntr * nx * 8 + ntr_pad * 4, "hbm"),
@@ -1031,6 +1039,8 @@ def main():
     # full reconstructions (Algorithm 6, 15 x 30) with the exact and the low-rank CG matrix
     recon = None
     if not args.no_recon and rank == 0:
+        if args.form == "recompute":
+            plan.set_recompute(0)  # the Gauss-Newton solve keeps cached time courses
         truth = torch.tensor(alpha_h, device="cuda")
         d, noise = noisy_data(torch, plan, truth, None)
         runs = [("plain", dict(hessian=0)), ("lowrank", dict(hessian=1))]
@@ -1119,6 +1129,8 @@ def main():
                                   f"tcgen05 coefficients, {dft}, per-ky Gram J^H J v)",
                      "lowrank": f"low-rank form (rank {R} time basis, {dft}, per-ky Gram J^H J v)",
                      "plain": "plain FP32 form (cached time courses, FP32 readout DFT)",
+                     "recompute": f"plain FP32 form, recompute variant (Bloch recursion re-run in every product "
+                                  f"from states every {args.segment} TRs, fused with the phase-encode sums)",
                      "split": "split-BF16 form (cached time courses, tcgen05 readout DFT)"}[args.form]
         l2 = ("inputs larger than L2 (cached time courses %.0f MB)" % (d_bytes / 1e6) if not lowrank_like
               else "L2 not flushed: the low-rank operands (~%.0f MB) are L2-resident by design; the "

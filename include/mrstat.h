@@ -519,11 +519,12 @@ typedef struct mrstat_gn_opts {
   int32_t hessian;             /* 0: exact Re(J^H J); 1: low-rank per-ky Gram product of
                                   the plan's time basis (mrstat_lowrank_set_basis) for the
                                   CG, with the exact gradient and objective              */
-  int32_t surrogate_iters;     /* 0..iteration_offset + outer_iters: the first
-                                  surrogate_iters outer iterations of the schedule run on
-                                  the learned surrogate's low-rank model (objective,
-                                  gradient, CG products and the trust-region ratio); the
-                                  rest on the exact model                                 */
+  int32_t surrogate_iters;     /* >= 0: the first surrogate_iters outer iterations of the
+                                  schedule run on the learned surrogate's low-rank model
+                                  (objective, gradient, CG products and the trust-region
+                                  ratio); the rest on the exact model.  A call that ends
+                                  inside the surrogate phase returns the surrogate model's
+                                  iterate (a later call with iteration_offset continues) */
   const mrstat_mlp* surrogate; /* required when surrogate_iters > 0; its rank must equal
                                   the plan's basis rank                                  */
   double b1_min, b1_max;       /* B1 box when B1 is estimated                           */

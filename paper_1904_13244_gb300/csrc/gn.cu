@@ -753,8 +753,8 @@ int mrstat_gn_solve(mrstat_plan* plan_, const float* d, float* alpha, const floa
     return fail(MRSTAT_ERR_NOT_LINEARIZED, "the low-rank Hessian needs mrstat_lowrank_set_basis first");
   if (o->iteration_offset < 0) return fail(MRSTAT_ERR_INVALID_ARG, "iteration_offset must be >= 0");
   const int k0 = o->iteration_offset;  // schedule index of this call's first iteration
-  if (o->surrogate_iters < 0 || o->surrogate_iters > k0 + o->outer_iters)
-    return fail(MRSTAT_ERR_INVALID_ARG, "surrogate_iters must lie in 0..iteration_offset + outer_iters");
+  if (o->surrogate_iters < 0 || o->surrogate_iters > (1 << 20))
+    return fail(MRSTAT_ERR_INVALID_ARG, "surrogate_iters must lie in 0..2^20");
   // outer iterations of this call that run on the surrogate: schedule iterations below
   // surrogate_iters
   const int sur_iters = std::max(0, std::min(o->outer_iters, o->surrogate_iters - k0));

@@ -638,7 +638,9 @@ struct ColShared {
 
 // Steps 1-4 of the column product for image column ix (the voxel data in S.vox): on return
 // red4 (this block's half of iy) and rin hold the two parts of the contraction.
-template <int N1>
+// KM > 0 and RCT > 0: kmax == KM and nr == RCT known at compile time (the benchmark's
+// shapes); 0: taken from the arguments.
+template <int N1, int KM = 0, int RCT = 0>
 __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& S, const Fft32Lane& ffw,
                                             const Fft32Lane& ffa, const float* __restrict__ coefT,
                                             const float* __restrict__ UgS, int kmax, int ix, int nx, int R, int r0,
@@ -646,6 +648,10 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
   constexpr int NY = 32 * N1, LD = NY + 1;
+  constexpr int SC = KM > 0 ? KM : 8;              // TR slots per pass of step 2
+  constexpr int RCM = RCT > 0 ? RCT : kColMaxRc;   // basis functions per block, at most
+  const int km = KM > 0 ? KM : kmax;
+  const int nrr = RCT > 0 ? RCT : nr;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int brev = (int)(__brev((unsigned)lane) >> 27);
   const size_t plane = (size_t)nx * NY;
@@ -661,9 +667,9 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
   //    coefficient loads of both issue together and the voxel data is read once; the
   //    second column waits in its own row of hs (in iy order) while the first is
   //    transformed
-  for (int ra = warp; ra < nr; ra += 2 * kColWarps) {
+  for (int ra = warp; ra < nrr; ra += 2 * kColWarps) {
     const int rb = ra + kColWarps;
-    const bool two = rb < nr;
+    const bool two = rb < nrr;
     const float* ca = coefT + (size_t)(r0 + ra) * plane + (size_t)ix * NY;
     const float* cbp = two ? coefT + (size_t)(r0 + rb) * plane + (size_t)ix * NY : ca;
     float2 xa[N1];
@@ -697,48 +703,73 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
     }
   }
   __syncthreads();
-  // 2. per-ky Gram through the TR axis, with the TRs of each ky in slots i < kmax
-  //    (U as UgS[r][i][ky], zero past a ky's TRs; s as [i][ky]): consecutive lanes take
-  //    consecutive ky, so U is read coalesced and s without bank conflicts.
-  //    2a. thread per (i, ky): this block's part of s[i][ky] = sum_q U[i-th TR of ky][q] H_q(ky)
-  for (int e = tid; e < kmax * NY; e += kColThreads) {
-    const int i = e / NY, ky = e - i * NY;
-    float sr = 0.f, si = 0.f;
+  // 2. per-ky Gram through the TR axis, thread per ky: U as UgS[r][i][ky] (the TRs of each
+  //    ky in slots i < kmax, zero past a ky's TRs), so consecutive threads read consecutive
+  //    ky (coalesced); every s and G a thread forms belongs to its own ky, so the phase
+  //    needs no block barrier, only the cluster barrier of the exchange.
+  //    2a. this block's part of s[i][ky] = sum_q U[q][i][ky] H_q(ky), slots in chunks of
+  //        SC, kept in sbuf and stored into the peer's sin
+  for (int ky = tid; ky < NY; ky += kColThreads) {
+    const float* ub = UgS + (size_t)r0 * km * NY + ky;
+    for (int i0 = 0; i0 < km; i0 += SC) {
+      float2 acc[SC];
 #pragma unroll
-    for (int q = 0; q < kColMaxRc; ++q) {  // unrolled: the loads of U issue together
-      if (q < nr) {
-        const float u = __ldg(UgS + ((size_t)(r0 + q) * kmax + i) * NY + ky);
+      for (int i = 0; i < SC; ++i) acc[i] = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int q = 0; q < nrr; ++q) {
         const float2 h = hs[q * LD + ky];
-        sr = fmaf(u, h.x, sr);
-        si = fmaf(u, h.y, si);
+#pragma unroll
+        for (int i = 0; i < SC; ++i) {
+          if (i0 + i < km) {
+            const float u = __ldg(ub + ((size_t)q * km + i0 + i) * NY);
+            acc[i].x = fmaf(u, h.x, acc[i].x);
+            acc[i].y = fmaf(u, h.y, acc[i].y);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < SC; ++i) {
+        if (i0 + i < km) {
+          sbuf[(i0 + i) * NY + ky] = acc[i];
+          sin_peer[(i0 + i) * NY + ky] = acc[i];  // the peer's copy of this block's part
+        }
       }
     }
-    const float2 part = make_float2(sr, si);
-    sbuf[e] = part;
-    sin_peer[e] = part;  // the peer's copy of this block's part
   }
   cl.sync();  // both parts of every s are in both blocks
-  //    2b. warp per r, lane per ky: G_r(ky) = sum_i U[i-th TR of ky][r] s[i][ky], with s the
-  //        sum of the two parts (commutative: the same s in both blocks)
-  for (int rl = warp; rl < nr; rl += kColWarps) {
-    const float* ur = UgS + (size_t)(r0 + rl) * kmax * NY;
+  //    2b. G_r(ky) = sum_i U[r][i][ky] s[i][ky], with s the sum of the two parts
+  //        (commutative: the same s in both blocks), over the slots in chunks of SC; G
+  //        overwrites H_r(ky), which only this thread read
+  for (int ky = tid; ky < NY; ky += kColThreads) {
+    const float* ub = UgS + (size_t)r0 * km * NY + ky;
+    for (int i0 = 0; i0 < km; i0 += SC) {
+      float2 sv[SC];
 #pragma unroll
-    for (int ky = lane; ky < NY; ky += 32) {
-      float2 o = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int i = 0; i < kmax; ++i) {
-        const float u = __ldg(ur + (size_t)i * NY + ky);
-        const float2 sa = sbuf[i * NY + ky], sb = sin[i * NY + ky];
-        const float2 sv = make_float2(sa.x + sb.x, sa.y + sb.y);
-        o.x = fmaf(u, sv.x, o.x);
-        o.y = fmaf(u, sv.y, o.y);
+      for (int i = 0; i < SC; ++i) {
+        sv[i] = make_float2(0.f, 0.f);
+        if (i0 + i < km) {
+          const float2 sa = sbuf[(i0 + i) * NY + ky], sb = sin[(i0 + i) * NY + ky];
+          sv[i] = make_float2(sa.x + sb.x, sa.y + sb.y);
+        }
       }
-      hs[rl * LD + ky] = o;
+#pragma unroll 4
+      for (int r = 0; r < nrr; ++r) {
+        float2 g = i0 == 0 ? make_float2(0.f, 0.f) : hs[r * LD + ky];
+#pragma unroll
+        for (int i = 0; i < SC; ++i) {
+          if (i0 + i < km) {
+            const float u = __ldg(ub + ((size_t)r * km + i0 + i) * NY);
+            g.x = fmaf(u, sv[i].x, g.x);
+            g.y = fmaf(u, sv[i].y, g.y);
+          }
+        }
+        hs[r * LD + ky] = g;
+      }
     }
   }
-  __syncwarp();  // the adjoint below reads only the rows this warp has just written
+  __syncthreads();  // the adjoint below reads whole rows of hs
   // 3. adjoint phase-encode DFT
-  for (int rl = warp; rl < nr; rl += kColWarps) {
+  for (int rl = warp; rl < nrr; rl += kColWarps) {
     float2* x = hs + rl * LD;
     const int i2 = brev;
     float2 z[N1];
@@ -762,8 +793,8 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
     const float rhx = vox[4 * NY + iy], rhy = vox[5 * NY + iy];
     const float* cc = coefT + (size_t)ix * NY + iy;
 #pragma unroll
-    for (int rl = 0; rl < kColMaxRc; ++rl) {
-      if (rl < nr) {
+    for (int rl = 0; rl < RCM; ++rl) {
+      if (rl < nrr) {
         const int r = r0 + rl;
         const float2 pv = hs[rl * LD + iy];
         const float c = cc[(size_t)r * plane];
@@ -785,7 +816,7 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
   cl.sync();  // the peer's part of this block's half has arrived
 }
 
-template <int N1>
+template <int N1, int KM, int RCT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kColThreads, 3)
 lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restrict__ v,
                       const float* __restrict__ coefT, const float2* __restrict__ rho,
@@ -849,7 +880,7 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
       }
       continue;
     }
-    column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ye);
+    column_core<N1, KM, RCT>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ye);
     for (int iy = ya + tid; iy < ye; iy += kColThreads) {
       const int j = iy * nx + ix;
       const float m = maskf[j] * scale;
@@ -1037,7 +1068,7 @@ size_t cg_column_smem_bytes(int ny, int R, int kmax) {
   return column_smem_bytes(ny, R, kmax) + sizeof(float) * ((size_t)ny + 20 * (size_t)hy);
 }
 
-template <int N1>
+template <int N1, int KM, int RCT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kColThreads, 3)
 lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict__ rhs, float* __restrict__ xout,
                      const float* __restrict__ coefT, const float2* __restrict__ rho,
@@ -1111,7 +1142,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   cl.sync();
 
   // w_0 = B r_0 (masked, like every product) becomes the product's input
-  if (inside) column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+  if (inside) column_core<N1, KM, RCT>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
   if (tid < nh) {
     const int iy = ya + tid;
     const float m = mk[iy] * scale;
@@ -1149,7 +1180,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
     }
     // q = B w while the other blocks arrive (not needed in the last iteration)
     const bool prod = inside && it + 1 < iters;
-    if (prod) column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+    if (prod) column_core<N1, KM, RCT>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
     double sums2[2];
     const bool ok = grid_wait_sums<2>(pk, bar, (unsigned)G * (unsigned)(it + 1), err, ws, sums2);
     const double delta = sums2[0], gamma = sums2[1];
@@ -1255,7 +1286,7 @@ size_t st_column_smem_bytes(int ny, int R, int kmax) {
   return column_smem_bytes(ny, R, kmax) + sizeof(float) * ((size_t)ny + 16 * (size_t)hy);
 }
 
-template <int N1>
+template <int N1, int KM, int RCT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kColThreads, 3)
 lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict__ grad,
                            float* __restrict__ zout, const float* __restrict__ coefT,
@@ -1334,7 +1365,7 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
   }
   cl.sync();  // dir of both halves is in both blocks
   // q = B dir_0, then g.g and dir.q
-  if (inside) column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+  if (inside) column_core<N1, KM, RCT>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
   {
     float sg = 0.f, sq = 0.f;
     if (own) {
@@ -1422,7 +1453,7 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
     const bool prod = inside && s_prod;
     float b[3] = {0.f, 0.f, 0.f};
     if (prod) {
-      column_core<N1>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+      column_core<N1, KM, RCT>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
       if (own) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -1978,21 +2009,45 @@ static cudaError_t ensure_coef_columns(Plan* p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int N1>
-static cudaError_t launch_column_t(Plan* p, const float* v, double* vdot, double* vv, float* out, cudaStream_t st) {
+// Shapes with a compiled specialisation of the column kernels (kmax TR slots per ky and
+// R / 2 basis functions per block fixed at compile time): 224 rows with five or eight TRs
+// per phase-encode line and 256 rows with five, rank 32.  Others take the generic kernels.
+enum ColSpec { kSpecGeneric, kSpec7x5, kSpec7x8, kSpec8x5 };
+
+static ColSpec col_spec(const Plan* p) {
+  const LowRank& L = *p->lr;
+  if (L.R != 32) return kSpecGeneric;
+  if (p->ny == 224 && L.ky_count_max == 5) return kSpec7x5;
+  if (p->ny == 224 && L.ky_count_max == 8) return kSpec7x8;
+  if (p->ny == 256 && L.ky_count_max == 5) return kSpec8x5;
+  return kSpecGeneric;
+}
+
+template <int N1, int KM, int RCT>
+static cudaError_t launch_column_k(Plan* p, const float* v, double* vdot, double* vv, float* out, cudaStream_t st) {
   LowRank& L = *p->lr;
   const int nx = p->nx, ny = p->ny, R = L.R;
   const size_t sm = column_smem_bytes(ny, R, L.ky_count_max);
   cudaError_t e =
-      cudaFuncSetAttribute(lr_jhjv_column_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(lr_jhjv_column_kernel<N1, KM, RCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   // two blocks per column (cluster pairs), one float64 partial per block
   const int grid = 2 * std::min(nx, kRedBlocks / 2);
   // programmatic dependent launch: the set-up above the kernel's pdl_wait overlaps the
   // tail of the previous launch in the stream
-  return launch_pdl(lr_jhjv_column_kernel<N1>, dim3(grid), dim3(kColThreads), sm, st, L.dft_small, v, L.coefT,
-                    p->rho, p->maskf, p->roots, L.UgS, L.ky_count_max, nx, ny, p->nv, R, (float)nx, out, p->red,
-                    p->ticket, vdot, vv, p->gate);
+  return launch_pdl(lr_jhjv_column_kernel<N1, KM, RCT>, dim3(grid), dim3(kColThreads), sm, st, L.dft_small, v,
+                    L.coefT, p->rho, p->maskf, p->roots, L.UgS, L.ky_count_max, nx, ny, p->nv, R, (float)nx, out,
+                    p->red, p->ticket, vdot, vv, p->gate);
+}
+
+template <int N1>
+static cudaError_t launch_column_t(Plan* p, const float* v, double* vdot, double* vv, float* out, cudaStream_t st) {
+  switch (col_spec(p)) {
+    case kSpec7x5: return launch_column_k<7, 5, 0>(p, v, vdot, vv, out, st);
+    case kSpec7x8: return launch_column_k<7, 8, 0>(p, v, vdot, vv, out, st);
+    case kSpec8x5: return launch_column_k<8, 5, 0>(p, v, vdot, vv, out, st);
+    default: return launch_column_k<N1, 0, 0>(p, v, vdot, vv, out, st);
+  }
 }
 
 static cudaError_t launch_column(Plan* p, const float* v, double* vdot, double* vv, float* out, cudaStream_t st) {
@@ -2037,15 +2092,25 @@ static cudaError_t launch_persistent_columns(Plan* p, void (*kernel)(KArgs...), 
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <int N1>
-static cudaError_t launch_cg_columns_t(Plan* p, const float* rhs, float* x, int iters, bool launch, cudaStream_t st) {
+template <int N1, int KM, int RCT>
+static cudaError_t launch_cg_columns_k(Plan* p, const float* rhs, float* x, int iters, bool launch, cudaStream_t st) {
   LowRank& L = *p->lr;
   const size_t sm = cg_column_smem_bytes(p->ny, L.R, L.ky_count_max);
-  return launch_persistent_columns(p, lr_cg_columns_kernel<N1>, sm, launch, st, L.dft_small, rhs, x,
+  return launch_persistent_columns(p, lr_cg_columns_kernel<N1, KM, RCT>, sm, launch, st, L.dft_small, rhs, x,
                                    (const float*)L.coefT, (const float2*)p->rho, (const float*)p->maskf,
                                    (const float2*)p->roots, (const float*)L.UgS, L.ky_count_max, p->nx, p->nv, L.R,
                                    (float)p->nx, iters, p->grid_stall_block, p->red, p->cg_bar, p->cg_s,
                                    p->cg_frozen, p->dev_err);
+}
+
+template <int N1>
+static cudaError_t launch_cg_columns_t(Plan* p, const float* rhs, float* x, int iters, bool launch, cudaStream_t st) {
+  switch (col_spec(p)) {
+    case kSpec7x5: return launch_cg_columns_k<7, 5, 0>(p, rhs, x, iters, launch, st);
+    case kSpec7x8: return launch_cg_columns_k<7, 8, 0>(p, rhs, x, iters, launch, st);
+    case kSpec8x5: return launch_cg_columns_k<8, 5, 0>(p, rhs, x, iters, launch, st);
+    default: return launch_cg_columns_k<N1, 0, 0>(p, rhs, x, iters, launch, st);
+  }
 }
 
 static cudaError_t launch_cg_columns(Plan* p, const float* rhs, float* x, int iters, bool launch, cudaStream_t st) {
@@ -2068,16 +2133,27 @@ struct SteihaugArgs {
   int* si;
 };
 
-template <int N1>
-static cudaError_t launch_st_columns_t(Plan* p, const float* g, float* z, const SteihaugArgs& a, bool launch,
+template <int N1, int KM, int RCT>
+static cudaError_t launch_st_columns_k(Plan* p, const float* g, float* z, const SteihaugArgs& a, bool launch,
                                        cudaStream_t st) {
   LowRank& L = *p->lr;
   const size_t sm = st_column_smem_bytes(p->ny, L.R, L.ky_count_max);
-  return launch_persistent_columns(p, lr_steihaug_columns_kernel<N1>, sm, launch, st, L.dft_small, g, z,
+  return launch_persistent_columns(p, lr_steihaug_columns_kernel<N1, KM, RCT>, sm, launch, st, L.dft_small, g, z,
                                    (const float*)L.coefT, (const float2*)p->rho, (const float*)p->maskf,
                                    (const float2*)p->roots, (const float*)L.UgS, L.ky_count_max, p->nx, p->nv, L.R,
                                    (float)p->nx, a.delta, a.rel_tol, a.max_steps, a.sc, a.si, p->grid_stall_block,
                                    p->red, p->cg_bar, p->dev_err);
+}
+
+template <int N1>
+static cudaError_t launch_st_columns_t(Plan* p, const float* g, float* z, const SteihaugArgs& a, bool launch,
+                                       cudaStream_t st) {
+  switch (col_spec(p)) {
+    case kSpec7x5: return launch_st_columns_k<7, 5, 0>(p, g, z, a, launch, st);
+    case kSpec7x8: return launch_st_columns_k<7, 8, 0>(p, g, z, a, launch, st);
+    case kSpec8x5: return launch_st_columns_k<8, 5, 0>(p, g, z, a, launch, st);
+    default: return launch_st_columns_k<N1, 0, 0>(p, g, z, a, launch, st);
+  }
 }
 
 static cudaError_t launch_st_columns(Plan* p, const float* g, float* z, const SteihaugArgs& a, bool launch,

@@ -327,7 +327,7 @@ def test_surrogate_options_are_checked(mr, noisy_quad):
             plan.gn_solve(cuda(d, torch.complex64), cuda(a0), outer_iters=2, surrogate_iters=1)
         assert e.value.status == 1
         with pytest.raises(mr.MrstatError) as e:
-            plan.gn_solve(cuda(d, torch.complex64), cuda(a0), outer_iters=2, surrogate_iters=3)
+            plan.gn_solve(cuda(d, torch.complex64), cuda(a0), outer_iters=2, surrogate_iters=-1)
         assert e.value.status == 1
         with mr.Surrogate(64, 8, (7.0, 1.0, 4.5, 1.2, 1.0, 0.2)) as net:
             with pytest.raises(mr.MrstatError) as e:  # no basis yet
