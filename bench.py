@@ -69,8 +69,10 @@ NCU_TRAFFIC = {
     ("xdft", "0728f575d9d96a3d"): 13670656.0,
     ("xdft_adj", "0728f575d9d96a3d"): 13668608.0,
     # profiles/lr_cg_columns_kernel_brain224.md: one persistent CG launch of 30 products
-    # read 20 934 912 B and wrote 17 152 B (caches flushed before it), per product
-    ("jhw_dot", "7937df7e841037bb"): (20934912.0 + 17152.0) / 30,
+    # read 20 974 592 B and wrote 39 168 B (caches flushed before it), per product
+    ("jhw_dot", "8932e29a79b109c9"): (20974592.0 + 39168.0) / 30,
+    # profiles/rc_product_kernel_brain224.md: one recompute J^H J v read 12 694 528 B
+    ("jhw_dot_rc", "e2a67059450a0ced"): 12694528.0,
 }
 
 
@@ -1023,11 +1025,13 @@ def main():
            "xdft_adj": "tc_gemm.cu", "mlp_infer": "mlp.cu"}
     if lowrank_like:
         src.update({"jhw_dot": "lowrank.cu", "ycontract": "lowrank.cu"})
+    if args.form == "recompute":
+        src.update({"jhw_dot": "fused.cu"})
     if dom == "mlp_infer":
         src["mlp_infer"] = "mlp.cu"
     h = source_hash(os.path.join(ROOT, "paper_1904_13244_gb300", "csrc", src[dom]))
     roofline = roof(dom)
-    roofline["traffic"] = NCU_TRAFFIC.get((dom, h))
+    roofline["traffic"] = NCU_TRAFFIC.get((dom + ("_rc" if args.form == "recompute" else ""), h))
     if column_bytes is not None and dom == "jhw_dot":
         hbm_peak, _ = measured_peak_hbm()
         gbs = column_bytes / (per_launch[dom] / 1e3) / 1e9
