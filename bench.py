@@ -100,6 +100,7 @@ def parse_args():
     ap.add_argument("--no-precision", action="store_true", help="skip the split-BF16 (precision form) legs")
     ap.add_argument("--no-fp64-errors", action="store_true",
                     help="skip the error of every form against the FP64 oracle on sampled outputs")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiation-form leg (autograd)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-part legs (224x224 and 256x256 with a B1 map)")
     ap.add_argument("--clock-log", default=os.environ.get("MRSTAT_CLOCK_LOG"),
@@ -1096,7 +1097,7 @@ def main():
 
     # the differentiation form (autograd, with and without Bloch-state checkpoints)
     diff = None
-    if not args.no_shapes and rank == 0 and world == 1:
+    if not args.no_diff and rank == 0 and world == 1:
         diff = differentiation(mr, torch, seq, ph)
 
     # the learned-part form (surrogate trained on B1-varied samples, known smooth B1 map) at
