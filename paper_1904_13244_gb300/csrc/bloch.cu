@@ -61,19 +61,40 @@ bloch_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
   float by = 0.f, bz = 0.f;   // d m / d ln T2
   float cy = 0.f, cz = 0.f;   // d m / d B1 (NCH = 4)
 
+  // the per-TR rotation data of the next quad is loaded while this quad runs, so the
+  // recursion does not wait on the table loads (the tables hold ntr_pad = 4 nq entries)
+  float2 csn[4];
+  float phin[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    csn[k] = B1MAP ? make_float2(0.f, 0.f) : __ldg(cs + k);
+    phin[k] = (B1MAP || NCH > 3) ? __ldg(phi + k) : 0.f;
+  }
   for (int q = 0; q < nq; ++q) {
+    float2 csq[4];
+    float phq[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      csq[k] = csn[k];
+      phq[k] = phin[k];
+    }
+    if (q + 1 < nq) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!B1MAP) csn[k] = __ldg(cs + 4 * (q + 1) + k);
+        if (B1MAP || NCH > 3) phin[k] = __ldg(phi + 4 * (q + 1) + k);
+      }
+    }
     float o0[4], o1[4], o2[4], o3[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int n = 4 * q + k;
       float c, s;
-      const float phn = (B1MAP || NCH > 3) ? __ldg(phi + n) : 0.f;
+      const float phn = phq[k];
       if (B1MAP) {
         sincosf(phn * bj, &s, &c);
       } else {
-        const float2 t = __ldg(cs + n);
-        c = t.x;
-        s = t.y;
+        c = csq[k].x;
+        s = csq[k].y;
       }
       // rotation about the RF axis
       float ty = c * my + s * mz;
@@ -262,8 +283,19 @@ bloch_ckpt_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
   const float bj = b1map ? b1[j] : 1.f;
   State s{0.f, m0z, 0.f, 0.f, 0.f, 0.f};
   const size_t cstride = (size_t)nv;
+  // the next quad's rotations are fetched while this quad runs (tables hold 4 nq entries)
+  float2 rn[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) rot_cs(cs, phi, b1map, bj, k, rn[k].x, rn[k].y);
   for (int q = 0; q < nq; ++q) {
     const int n0 = 4 * q;
+    float2 rq[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rq[k] = rn[k];
+    if (q + 1 < nq) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) rot_cs(cs, phi, b1map, bj, n0 + 4 + k, rn[k].x, rn[k].y);
+    }
     if (n0 % interval == 0) {
       float* c = ckpt + (size_t)(n0 / interval) * 6 * nv + j;
       c[0] = s.my;
@@ -276,9 +308,7 @@ bloch_ckpt_kernel(const float* __restrict__ alpha, const float* __restrict__ b1,
     float o[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      float c, sn;
-      rot_cs(cs, phi, b1map, bj, n0 + k, c, sn);
-      rotate(s, c, sn);
+      rotate(s, rq[k].x, rq[k].y);
       decay(s, r.x1a, r.x2a, r.d1a, r.d2a);
       o[k] = on ? s.my : 0.f;
       decay(s, r.x1b, r.x2b, r.d1b, r.d2b);
@@ -320,13 +350,24 @@ segment_jhw_kernel(const float* __restrict__ alpha, const float* __restrict__ b1
   const int iy = j / nx, ix = j - iy * nx;
   float z0r = 0.f, z0i = 0.f, z1r = 0.f, z1i = 0.f, z2r = 0.f, z2i = 0.f;
   const int na = seg * interval, ne = min(ntr, na + interval);
+  // the next TR's table entries, k-space row and phase root are loaded while this TR
+  // runs, so the recursion does not wait on them
+  float cn = 1.f, snn = 0.f;
+  if (na < ne) rot_cs(cs, phi, b1map, bj, na, cn, snn);
+  int kyn = na < ne ? __ldg(kyi + na) : 0;
+  float2 wn = na < ne ? __ldg(wt + (size_t)na * nx + ix) : make_float2(0.f, 0.f);
+  float2 en = __ldg(roots + mod_small_b(kyn * iy, ny, inv_ny));
   for (int n = na; n < ne; ++n) {
-    float cc, sn;
-    rot_cs(cs, phi, b1map, bj, n, cc, sn);
+    const float cc = cn, sn = snn;
+    const float2 e = en, w = wn;
+    if (n + 1 < ne) {
+      rot_cs(cs, phi, b1map, bj, n + 1, cn, snn);
+      kyn = __ldg(kyi + n + 1);
+      wn = __ldg(wt + (size_t)(n + 1) * nx + ix);
+      en = __ldg(roots + mod_small_b(kyn * iy, ny, inv_ny));
+    }
     rotate(s, cc, sn);
     decay(s, r.x1a, r.x2a, r.d1a, r.d2a);
-    const float2 e = __ldg(roots + mod_small_b(__ldg(kyi + n) * iy, ny, inv_ny));
-    const float2 w = __ldg(wt + (size_t)n * nx + ix);
     const float ur = fmaf(e.x, w.x, e.y * w.y);
     const float ui = fmaf(e.x, w.y, -e.y * w.x);
     z0r = fmaf(s.my, ur, z0r);
