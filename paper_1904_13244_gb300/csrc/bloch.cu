@@ -350,24 +350,13 @@ segment_jhw_kernel(const float* __restrict__ alpha, const float* __restrict__ b1
   const int iy = j / nx, ix = j - iy * nx;
   float z0r = 0.f, z0i = 0.f, z1r = 0.f, z1i = 0.f, z2r = 0.f, z2i = 0.f;
   const int na = seg * interval, ne = min(ntr, na + interval);
-  // the next TR's table entries, k-space row and phase root are loaded while this TR
-  // runs, so the recursion does not wait on them
-  float cn = 1.f, snn = 0.f;
-  if (na < ne) rot_cs(cs, phi, b1map, bj, na, cn, snn);
-  int kyn = na < ne ? __ldg(kyi + na) : 0;
-  float2 wn = na < ne ? __ldg(wt + (size_t)na * nx + ix) : make_float2(0.f, 0.f);
-  float2 en = __ldg(roots + mod_small_b(kyn * iy, ny, inv_ny));
   for (int n = na; n < ne; ++n) {
-    const float cc = cn, sn = snn;
-    const float2 e = en, w = wn;
-    if (n + 1 < ne) {
-      rot_cs(cs, phi, b1map, bj, n + 1, cn, snn);
-      kyn = __ldg(kyi + n + 1);
-      wn = __ldg(wt + (size_t)(n + 1) * nx + ix);
-      en = __ldg(roots + mod_small_b(kyn * iy, ny, inv_ny));
-    }
+    float cc, sn;
+    rot_cs(cs, phi, b1map, bj, n, cc, sn);
     rotate(s, cc, sn);
     decay(s, r.x1a, r.x2a, r.d1a, r.d2a);
+    const float2 e = __ldg(roots + mod_small_b(__ldg(kyi + n) * iy, ny, inv_ny));
+    const float2 w = __ldg(wt + (size_t)n * nx + ix);
     const float ur = fmaf(e.x, w.x, e.y * w.y);
     const float ui = fmaf(e.x, w.y, -e.y * w.x);
     z0r = fmaf(s.my, ur, z0r);
