@@ -16,9 +16,9 @@
 //             g3 -= m Re b  (Re of conj(dq/dalpha_k) b);
 //   J^H J v:  with nkx = nx the readout DFT pair cancels (F^H F = nx I), so Wt = nx A and
 //             both halves run in one pass: A[n] is formed in the block and used at once.
-// E[ky][iy] = roots[(ky iy) mod ny] is an exact table lookup.  TRs go in chunks of 8: each
-// thread advances its recursion 8 TRs, keeping the three echo values and phases in
-// registers, the block adds the 8 complex sums (a transposing warp reduction, then the
+// E[ky][iy] = roots[(ky iy) mod ny] is an exact table lookup.  TRs go in chunks of kChunk:
+// each thread advances its recursion kChunk TRs, keeping the three echo values and phases
+// in registers, the block adds the kChunk complex sums (a halving warp exchange, then the
 // warps' partials through shared memory), and the gradient terms of the chunk follow.
 // Per-segment gradients go to gpart[s][4][nv]; a second kernel adds the segments.
 #include "internal.cuh"
@@ -26,7 +26,7 @@
 namespace mrstat {
 namespace {
 
-constexpr int kChunk = 8;       // TRs per block reduction
+constexpr int kChunk = 4;       // TRs per block reduction
 constexpr int kMaxRows = 256;   // one thread per row of the column
 
 enum { RC_JV = 0, RC_JHW = 1, RC_JHJV = 2 };
@@ -90,13 +90,12 @@ __device__ __forceinline__ void rc_cs(const float2* cs, const float* phi, const 
   }
 }
 
-// a mod n for 0 <= a < n * n with n <= 2048, by a float reciprocal and one correction
-__device__ __forceinline__ int rc_mod(int a, int n, float inv_n) {
-  int q = __float2int_rz(__int2float_rn(a) * inv_n);
-  int r = a - q * n;
-  r += (r < 0) ? n : 0;
-  r -= (r >= n) ? n : 0;
-  return r;
+// a mod n for 0 <= a < n * n and n <= kMaxRows, with magic = ceil(2^32 / n) (0 for n = 1,
+// where a is 0): the quotient umulhi(a, magic) is exact for every such a and n (the error
+// a (magic - 2^32 / n) / 2^32 < n^2 / 2^32 stays below the gap 1 / n to the next integer;
+// checked exhaustively on the host for n <= 256)
+__device__ __forceinline__ int rc_mod(int a, int n, unsigned magic) {
+  return a - (int)__umulhi((unsigned)a, magic) * n;
 }
 
 // Linearisation: relaxation factors and the state before every seg-th TR, per voxel.
@@ -134,54 +133,40 @@ rc_ckpt_kernel(const float* __restrict__ alpha, const float* __restrict__ b1, co
   }
 }
 
-// Sum of kChunk complex values (v[2k], v[2k+1]) over the 32 lanes of a warp by halving
-// exchanges: after the stages with offsets 16, 8, 4 a lane keeps one complex value, that
-// of chunk slot (lane >> 2) & 7, summed over the lanes it exchanged with; offsets 2 and 1
-// finish the sum.  18 shuffles instead of 80 for eight separate warp sums.
-__device__ __forceinline__ float2 rc_warp_sum8(float (&v)[2 * kChunk], int lane) {
-  // offset 16: keep slots 4..7 (upper lanes) or 0..3
-  {
-    const bool up = lane & 16;
+// Sum of K complex values (v[2k], v[2k+1]) over the 32 lanes of a warp by halving
+// exchanges: at each offset 16, 8, ... a lane sends the half of its values it does not
+// keep and adds the half it receives, until one complex value is left, that of slot
+// (lane / (32 / K)) mod K; the remaining offsets finish the sum.  For K = 8: 18 shuffles
+// instead of 80 for eight separate warp sums.
+template <int K>
+__device__ __forceinline__ float2 rc_warp_sum(float (&v)[2 * K], int lane) {
+  static_assert(K == 1 || K == 2 || K == 4 || K == 8, "chunk of 1, 2, 4 or 8 TRs");
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float send = up ? v[i] : v[i + 8];
-      const float keep = up ? v[i + 8] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-  }
-  {
-    const bool up = lane & 8;
+  for (int n = 2 * K, off = 16; n > 2; n >>= 1, off >>= 1) {
+    const bool up = lane & off;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float send = up ? v[i] : v[i + 4];
-      const float keep = up ? v[i + 4] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-  }
-  {
-    const bool up = lane & 4;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const float send = up ? v[i] : v[i + 2];
-      const float keep = up ? v[i + 2] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    for (int i = 0; i < n / 2; ++i) {
+      const float send = up ? v[i] : v[i + n / 2];
+      const float keep = up ? v[i + n / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
     }
   }
   float re = v[0], im = v[1];
-  re += __shfl_xor_sync(0xffffffffu, re, 2);
-  im += __shfl_xor_sync(0xffffffffu, im, 2);
-  re += __shfl_xor_sync(0xffffffffu, re, 1);
-  im += __shfl_xor_sync(0xffffffffu, im, 1);
+#pragma unroll
+  for (int off = 16 / K; off > 0; off >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, off);
+    im += __shfl_xor_sync(0xffffffffu, im, off);
+  }
   return make_float2(re, im);
 }
 
 // grid (nx, nseg), block = ny rounded up to whole warps (<= kMaxRows)
 template <int MODE>
-__global__ void __launch_bounds__(kMaxRows, 2)
+__global__ void __launch_bounds__(kMaxRows, 3)
 rc_product_kernel(const float* __restrict__ rlx, const float* __restrict__ ckpt, const float2* __restrict__ rho,
                   const float* __restrict__ maskf, const float* __restrict__ b1, const float* __restrict__ v,
                   const float2* __restrict__ cs, const float* __restrict__ phi, const int* __restrict__ kyi,
-                  const float2* __restrict__ roots, int nx, int ny, int nv, int ntr, int seg, float inv_ny,
+                  const float2* __restrict__ roots, int nx, int ny, int nv, int ntr, int seg, unsigned magic,
                   float scale, float2* __restrict__ A, const float2* __restrict__ wt, float* __restrict__ gpart,
                   const int* __restrict__ gate) {
   if (gate != nullptr && *gate == 0) return;
@@ -232,7 +217,7 @@ rc_product_kernel(const float* __restrict__ rlx, const float* __restrict__ ckpt,
         y1[k] = s.ay * m;
         y2[k] = s.by * m;
         // rows past ny (the block's last warp) keep e = 0: their index would leave the table
-        if (row) e[k] = __ldg(roots + rc_mod(__ldg(kyi + n) * iy, ny, inv_ny));
+        if (row) e[k] = __ldg(roots + rc_mod(__ldg(kyi + n) * iy, ny, magic));
         if (MODE != RC_JHW) {
           // q = i u, u = rho t + (v2 + i v3) m_y; p = E q
           const float t = fmaf(v0, y1[k], v1 * y2[k]);
@@ -247,8 +232,9 @@ rc_product_kernel(const float* __restrict__ rlx, const float* __restrict__ ckpt,
     }
     float2 a[kChunk];
     if (MODE != RC_JHW) {
-      const float2 w = rc_warp_sum8(p, lane);
-      if ((lane & 3) == 0) part[warp][(lane >> 2) & 7] = w;
+      const float2 w = rc_warp_sum<kChunk>(p, lane);
+      constexpr int kLanesPerSlot = 32 / kChunk;
+      if ((lane & (kLanesPerSlot - 1)) == 0) part[warp][lane / kLanesPerSlot] = w;
       __syncthreads();
       if (iy < kChunk) {
         float2 t = make_float2(0.f, 0.f);
@@ -320,24 +306,24 @@ cudaError_t launch_rc_product(const Plan& p, int mode, const float* v, const flo
   if (p.nv == 0) return cudaSuccess;
   const int threads = (p.ny + 31) / 32 * 32;
   const dim3 grid(p.nx, p.rc_nseg);
-  const float inv_ny = 1.0f / (float)p.ny;
+  const unsigned magic = p.ny > 1 ? (unsigned)((0x100000000ull + (unsigned)p.ny - 1) / (unsigned)p.ny) : 0u;
   const float scale = mode == RC_JHJV ? (float)p.nx : 1.f;
   const float* b1 = p.rc_has_b1 ? p.rc_b1 : nullptr;
   switch (mode) {
     case RC_JV:
       rc_product_kernel<RC_JV><<<grid, threads, 0, st>>>(p.rc_rlx, p.rc_ckpt, p.rho, p.maskf, b1, v, p.cs, p.phi,
-                                                         p.kyi, p.roots, p.nx, p.ny, p.nv, p.ntr, p.rc_seg, inv_ny,
+                                                         p.kyi, p.roots, p.nx, p.ny, p.nv, p.ntr, p.rc_seg, magic,
                                                          scale, p.A, nullptr, nullptr, p.gate);
       return cudaGetLastError();
     case RC_JHW:
       rc_product_kernel<RC_JHW><<<grid, threads, 0, st>>>(p.rc_rlx, p.rc_ckpt, p.rho, p.maskf, b1, nullptr, p.cs,
                                                           p.phi, p.kyi, p.roots, p.nx, p.ny, p.nv, p.ntr, p.rc_seg,
-                                                          inv_ny, scale, nullptr, wt, p.rc_gpart, p.gate);
+                                                          magic, scale, nullptr, wt, p.rc_gpart, p.gate);
       break;
     default:
       rc_product_kernel<RC_JHJV><<<grid, threads, 0, st>>>(p.rc_rlx, p.rc_ckpt, p.rho, p.maskf, b1, v, p.cs,
                                                            p.phi, p.kyi, p.roots, p.nx, p.ny, p.nv, p.ntr, p.rc_seg,
-                                                           inv_ny, scale, nullptr, nullptr, p.rc_gpart, p.gate);
+                                                           magic, scale, nullptr, nullptr, p.rc_gpart, p.gate);
       break;
   }
   cudaError_t e = cudaGetLastError();

@@ -618,16 +618,23 @@ __global__ void lr_coef_transpose_kernel(const float* __restrict__ coef, int nx,
 constexpr int kColThreads = 256, kColWarps = kColThreads / 32;
 constexpr int kColMaxRc = 16;  // basis functions per block: R <= 32
 
+// TR slots per phase-encode line that the per-line Gram step keeps in registers; with more
+// slots a line's part of s also goes through shared memory (sbuf).
+constexpr int kSlotRegs = 8;
+
+__host__ __device__ inline int sbuf_slots(int kmax) { return kmax > kSlotRegs ? kmax : 0; }
+
 size_t column_smem_bytes(int ny, int R, int kmax) {
   const size_t rc = (size_t)(R + 1) / 2;
-  return sizeof(float2) * ((size_t)ny + rc * (ny + 1) + 2 * (size_t)kmax * ny) + sizeof(float) * 14 * (size_t)ny;
+  return sizeof(float2) * ((size_t)ny + rc * (ny + 1) + (size_t)(kmax + sbuf_slots(kmax)) * ny) +
+         sizeof(float) * 14 * (size_t)ny;
 }
 
 // Shared-memory layout of the column kernels and the peer's exchange buffers.
 struct ColShared {
   float2* rt;      // [NY] w^k
   float2* hs;      // [RC][NY + 1]: H, then G, then P
-  float2* sbuf;    // [kmax][NY] this block's part of s, then s
+  float2* sbuf;    // [kmax][NY] this block's part of s (only with kmax > kSlotRegs)
   float2* sin;     // [kmax][NY] the peer's part (written by it)
   float* vox;      // [6][NY]: v0, v1, m v2, m v3, Re rho, Im rho
   float* red4;     // [4][NY] contraction over this block's r
@@ -640,11 +647,17 @@ struct ColShared {
 // red4 (this block's half of iy) and rin hold the two parts of the contraction.
 // KM > 0 and RCT > 0: kmax == KM and nr == RCT known at compile time (the benchmark's
 // shapes); 0: taken from the arguments.
-template <int N1, int KM = 0, int RCT = 0>
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+// hook: called by every thread right after the block barrier that ends step 1 (the
+// persistent CG finishes its block sums there instead of spending barriers of its own).
+template <int N1, int KM = 0, int RCT = 0, typename Hook = NoHook>
 __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& S, const Fft32Lane& ffw,
                                             const Fft32Lane& ffa, const float* __restrict__ coefT,
                                             const float* __restrict__ UgS, int kmax, int ix, int nx, int R, int r0,
-                                            int nr, int ya, int ye) {
+                                            int nr, int ya, int ye, const Hook& hook = Hook()) {
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
   constexpr int NY = 32 * N1, LD = NY + 1;
@@ -703,69 +716,125 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
     }
   }
   __syncthreads();
+  hook();
   // 2. per-ky Gram through the TR axis, thread per ky: U as UgS[r][i][ky] (the TRs of each
   //    ky in slots i < kmax, zero past a ky's TRs), so consecutive threads read consecutive
   //    ky (coalesced); every s and G a thread forms belongs to its own ky, so the phase
   //    needs no block barrier, only the cluster barrier of the exchange.
-  //    2a. this block's part of s[i][ky] = sum_q U[q][i][ky] H_q(ky), slots in chunks of
-  //        SC, kept in sbuf and stored into the peer's sin
-  for (int ky = tid; ky < NY; ky += kColThreads) {
+  if (km <= SC) {
+    // one pass over the slots: this thread's part of s stays in registers across the
+    // exchange (NY <= kColThreads: at most one line per thread)
+    const int ky = tid;
     const float* ub = UgS + (size_t)r0 * km * NY + ky;
-    for (int i0 = 0; i0 < km; i0 += SC) {
-      float2 acc[SC];
+    float2 acc[SC];
 #pragma unroll
-      for (int i = 0; i < SC; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < SC; ++i) acc[i] = make_float2(0.f, 0.f);
+    //  2a. this block's part of s[i][ky] = sum_q U[q][i][ky] H_q(ky), stored into the peer's sin
+    if (ky < NY) {
 #pragma unroll 4
       for (int q = 0; q < nrr; ++q) {
         const float2 h = hs[q * LD + ky];
 #pragma unroll
         for (int i = 0; i < SC; ++i) {
-          if (i0 + i < km) {
-            const float u = __ldg(ub + ((size_t)q * km + i0 + i) * NY);
+          if (i < km) {
+            const float u = __ldg(ub + ((size_t)q * km + i) * NY);
             acc[i].x = fmaf(u, h.x, acc[i].x);
             acc[i].y = fmaf(u, h.y, acc[i].y);
           }
         }
       }
 #pragma unroll
-      for (int i = 0; i < SC; ++i) {
-        if (i0 + i < km) {
-          sbuf[(i0 + i) * NY + ky] = acc[i];
-          sin_peer[(i0 + i) * NY + ky] = acc[i];  // the peer's copy of this block's part
-        }
-      }
+      for (int i = 0; i < SC; ++i)
+        if (i < km) sin_peer[i * NY + ky] = acc[i];
     }
-  }
-  cl.sync();  // both parts of every s are in both blocks
-  //    2b. G_r(ky) = sum_i U[r][i][ky] s[i][ky], with s the sum of the two parts
-  //        (commutative: the same s in both blocks), over the slots in chunks of SC; G
-  //        overwrites H_r(ky), which only this thread read
-  for (int ky = tid; ky < NY; ky += kColThreads) {
-    const float* ub = UgS + (size_t)r0 * km * NY + ky;
-    for (int i0 = 0; i0 < km; i0 += SC) {
-      float2 sv[SC];
+    cl.sync();  // both parts of every s are in both blocks
+    //  2b. G_r(ky) = sum_i U[r][i][ky] s[i][ky] with s the sum of the two parts
+    //      (commutative: the same s in both blocks); G overwrites H_r(ky), which only this
+    //      thread read
+    if (ky < NY) {
 #pragma unroll
       for (int i = 0; i < SC; ++i) {
-        sv[i] = make_float2(0.f, 0.f);
-        if (i0 + i < km) {
-          const float2 sa = sbuf[(i0 + i) * NY + ky], sb = sin[(i0 + i) * NY + ky];
-          sv[i] = make_float2(sa.x + sb.x, sa.y + sb.y);
+        if (i < km) {
+          const float2 sb = sin[i * NY + ky];
+          acc[i] = make_float2(acc[i].x + sb.x, acc[i].y + sb.y);
         }
       }
 #pragma unroll 4
       for (int r = 0; r < nrr; ++r) {
-        float2 g = i0 == 0 ? make_float2(0.f, 0.f) : hs[r * LD + ky];
+        float2 g = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < SC; ++i) {
-          if (i0 + i < km) {
-            const float u = __ldg(ub + ((size_t)r * km + i0 + i) * NY);
-            g.x = fmaf(u, sv[i].x, g.x);
-            g.y = fmaf(u, sv[i].y, g.y);
+          if (i < km) {
+            const float u = __ldg(ub + ((size_t)r * km + i) * NY);
+            g.x = fmaf(u, acc[i].x, g.x);
+            g.y = fmaf(u, acc[i].y, g.y);
           }
         }
         hs[r * LD + ky] = g;
       }
     }
+  } else {
+    //    2a. this block's part of s[i][ky] = sum_q U[q][i][ky] H_q(ky), slots in chunks of
+    //        SC, kept in sbuf and stored into the peer's sin
+    for (int ky = tid; ky < NY; ky += kColThreads) {
+      const float* ub = UgS + (size_t)r0 * km * NY + ky;
+      for (int i0 = 0; i0 < km; i0 += SC) {
+        float2 acc[SC];
+#pragma unroll
+        for (int i = 0; i < SC; ++i) acc[i] = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int q = 0; q < nrr; ++q) {
+          const float2 h = hs[q * LD + ky];
+#pragma unroll
+          for (int i = 0; i < SC; ++i) {
+            if (i0 + i < km) {
+              const float u = __ldg(ub + ((size_t)q * km + i0 + i) * NY);
+              acc[i].x = fmaf(u, h.x, acc[i].x);
+              acc[i].y = fmaf(u, h.y, acc[i].y);
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < SC; ++i) {
+          if (i0 + i < km) {
+            sbuf[(i0 + i) * NY + ky] = acc[i];
+            sin_peer[(i0 + i) * NY + ky] = acc[i];  // the peer's copy of this block's part
+          }
+        }
+      }
+    }
+    cl.sync();  // both parts of every s are in both blocks
+    //    2b. G_r(ky) = sum_i U[r][i][ky] s[i][ky], with s the sum of the two parts
+    //        (commutative: the same s in both blocks), over the slots in chunks of SC; G
+    //        overwrites H_r(ky), which only this thread read
+    for (int ky = tid; ky < NY; ky += kColThreads) {
+      const float* ub = UgS + (size_t)r0 * km * NY + ky;
+      for (int i0 = 0; i0 < km; i0 += SC) {
+        float2 sv[SC];
+#pragma unroll
+        for (int i = 0; i < SC; ++i) {
+          sv[i] = make_float2(0.f, 0.f);
+          if (i0 + i < km) {
+            const float2 sa = sbuf[(i0 + i) * NY + ky], sb = sin[(i0 + i) * NY + ky];
+            sv[i] = make_float2(sa.x + sb.x, sa.y + sb.y);
+          }
+        }
+#pragma unroll 4
+        for (int r = 0; r < nrr; ++r) {
+          float2 g = i0 == 0 ? make_float2(0.f, 0.f) : hs[r * LD + ky];
+#pragma unroll
+          for (int i = 0; i < SC; ++i) {
+            if (i0 + i < km) {
+              const float u = __ldg(ub + ((size_t)r * km + i0 + i) * NY);
+              g.x = fmaf(u, sv[i].x, g.x);
+              g.y = fmaf(u, sv[i].y, g.y);
+            }
+          }
+          hs[r * LD + ky] = g;
+        }
+      }
+    }
+
   }
   __syncthreads();  // the adjoint below reads whole rows of hs
   // 3. adjoint phase-encode DFT
@@ -834,7 +903,7 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
   float2* rt = fsm;                                      // [NY] w^k
   float2* hs = rt + NY;                                  // [RC][NY + 1]: H, then G, then P
   float2* sbuf = hs + RC * LD;                           // [kmax][NY] this block's part of s, then s
-  float2* sin = sbuf + kmax * NY;                        // [kmax][NY] the peer's part (written by it)
+  float2* sin = sbuf + sbuf_slots(kmax) * NY;            // [kmax][NY] the peer's part (written by it)
   float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // [6][NY]: v0, v1, m v2, m v3, Re rho, Im rho
   float* red4 = vox + 6 * NY;                            // [4][NY] contraction over this block's r
   float* rin = red4 + 4 * NY;                            // [4][NY] the peer's contraction (written by it)
@@ -996,6 +1065,31 @@ __device__ __forceinline__ void block_sums(FF (&v)[NV], FF* ws) {
   __syncthreads();
 }
 
+// The first half of block_sums without a barrier: each warp's sums of its NV values go
+// to ws[k kColWarps + warp]; after the next block barrier warp_finish gives the block sums
+// in lane 0 of warp 0.
+template <int NV>
+__device__ __forceinline__ void warp_partials(FF (&v)[NV], FF* ws) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = ff_add(v[k], ff_shfl_xor(v[k], o));
+    if (lane == 0) ws[k * kColWarps + w] = v[k];
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void warp_finish(FF (&v)[NV], const FF* ws) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    v[k] = lane < kColWarps ? ws[k * kColWarps + lane] : FF{0.f, 0.f};
+#pragma unroll
+    for (int o = kColWarps / 2; o > 0; o >>= 1) v[k] = ff_add(v[k], ff_shfl_xor(v[k], o));
+  }
+}
+
 // Thread 0 stores the block's NV partials (block sums in thread 0) into part[k G + block]
 // and arrives at the grid counter; it does not wait.
 template <int NV>
@@ -1084,7 +1178,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   float2* rt = fsm;
   float2* hs = rt + NY;
   float2* sbuf = hs + RC * LD;
-  float2* sin = sbuf + kmax * NY;
+  float2* sin = sbuf + sbuf_slots(kmax) * NY;
   float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // rows 0..3: the product's input
   float* red4 = vox + 6 * NY;
   float* rin = red4 + 4 * NY;
@@ -1171,16 +1265,27 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   int applied = 0;  // iterations that moved x (thread 0)
   for (int it = 0; it < iters; ++it) {
     FF* pk = reinterpret_cast<FF*>(part) + (size_t)(it & 1) * 2 * G;
-    {
-      // the block's parts of delta and gamma, then arrive (no wait); a block named by the
-      // test hook withholds its first arrival, and every wait runs out
-      FF v[2] = {{sd, 0.f}, {sg, 0.f}};
-      block_sums<2>(v, ws);
-      if (it > 0 || (int)blockIdx.x != stall_block) grid_arrive<2>(pk, bar, v);
-    }
     // q = B w while the other blocks arrive (not needed in the last iteration)
     const bool prod = inside && it + 1 < iters;
-    if (prod) column_core<N1, KM, RCT>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+    // the block's parts of delta and gamma, then arrive (no wait); a block named by the
+    // test hook withholds its first arrival, and every wait runs out.  With a product the
+    // warps' sums are finished by warp 0 after the product's first block barrier.
+    const bool arrive = it > 0 || (int)blockIdx.x != stall_block;
+    FF v[2] = {{sd, 0.f}, {sg, 0.f}};
+    if (prod) {
+      warp_partials<2>(v, ws);
+      auto finish_and_arrive = [&]() {
+        if ((tid >> 5) == 0) {
+          FF b[2];
+          warp_finish<2>(b, ws);
+          if (arrive) grid_arrive<2>(pk, bar, b);
+        }
+      };
+      column_core<N1, KM, RCT>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh, finish_and_arrive);
+    } else {
+      block_sums<2>(v, ws);
+      if (arrive) grid_arrive<2>(pk, bar, v);
+    }
     double sums2[2];
     const bool ok = grid_wait_sums<2>(pk, bar, (unsigned)G * (unsigned)(it + 1), err, ws, sums2);
     const double delta = sums2[0], gamma = sums2[1];
@@ -1304,7 +1409,7 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
   float2* rt = fsm;
   float2* hs = rt + NY;
   float2* sbuf = hs + RC * LD;
-  float2* sin = sbuf + kmax * NY;
+  float2* sin = sbuf + sbuf_slots(kmax) * NY;
   float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // rows 0..3: the product's input
   float* red4 = vox + 6 * NY;
   float* rin = red4 + 4 * NY;
