@@ -93,7 +93,7 @@ __device__ __forceinline__ void rc_cs(const float2* cs, const float* phi, const 
 // a mod n for 0 <= a < n * n and n <= kMaxRows, with magic = ceil(2^32 / n) (0 for n = 1,
 // where a is 0): the quotient umulhi(a, magic) is exact for every such a and n (the error
 // a (magic - 2^32 / n) / 2^32 < n^2 / 2^32 stays below the gap 1 / n to the next integer;
-// checked exhaustively on the host for n <= 256)
+// tests/test_host_arith.py checks this for every n <= 256 and a < n^2)
 __device__ __forceinline__ int rc_mod(int a, int n, unsigned magic) {
   return a - (int)__umulhi((unsigned)a, magic) * n;
 }
