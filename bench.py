@@ -761,6 +761,13 @@ def main():
     ms, stats, clk = timed(plan, step, args.steps, all_kernels, ClockSampler(local, args.clock_log))
     value = world * iters / (ms / 1e3)
     cg_check = check_cg(torch, plan, rhs_dev, x_dev, iters)
+    # what the learned surrogate buys: the same step with the coefficients of the exact
+    # Bloch recursion projected on the basis (the compressed-exact form) on the same inputs
+    compressed_exact = None
+    if args.form == "surrogate":
+        cms, _, _ = timed(plan, make_step(plan, "lowrank"), max(5, args.steps // 4), ())
+        compressed_exact = {"value": world * iters / (cms / 1e3), "ms_per_step": cms,
+                            "surrogate_gain": value / (world * iters / (cms / 1e3))}
 
     # the plain FP32 form on the same inputs, for the comparison the metric asks for
     plain = None
@@ -1152,7 +1159,8 @@ def main():
                            "form": args.form, "step": f"linearize + {iters} CG iterations (one J^H J v each)",
                            "cg_iters": iters, "l2": l2, "parallelism": f"replicas{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-                "cpu_baseline": cpu, "cg_check": cg_check, "plain": plain, "precision": precision,
+                "cpu_baseline": cpu, "cg_check": cg_check, "compressed_exact": compressed_exact, "plain": plain,
+                "precision": precision,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
                 "recon": recon, "learned_part": learned, "differentiation": diff, "surrogate": surrogate_info, "shapes": shapes, "slice_profile": slice_prof,
                 "kernel_ms_per_step": {k: v for k, v in per_step_ms.items()}}
