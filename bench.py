@@ -1130,7 +1130,7 @@ def main():
             cpu["fp64_errors"] = fp64_errors(mr, torch, seq, ph, alpha_h, basis, net)
             cpu["fp64_errors"]["oracle_seconds"] = time.perf_counter() - t0
 
-    launches = int(sum(stats[k]["launches"] for k in stats))
+    launches = int(sum(stats[k]["kernels"] for k in stats))
     if args.form == "surrogate":
         # MLP inference per step: the first layer on the CUDA cores and three fused
         # tensor-core layers (outside the plan's counters)

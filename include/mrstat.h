@@ -582,9 +582,12 @@ typedef enum mrstat_kernel_id {
 } mrstat_kernel_id;
 
 typedef struct mrstat_kernel_stats {
-  int64_t launches[8];       /* indexed by mrstat_kernel_id                          */
+  int64_t launches[8];       /* indexed by mrstat_kernel_id; a persistent CG or
+                                Steihaug launch counts its products                  */
   double ms[8];              /* summed event time of the profiled launches           */
   int64_t timed[8];          /* launches that were bracketed by events               */
+  int64_t kernels[8];        /* kernel launches (a persistent launch counts once, a
+                                call that launches two kernels counts two)            */
 } mrstat_kernel_stats;
 
 int mrstat_profile_start(mrstat_plan* plan, uint32_t kernel_mask);

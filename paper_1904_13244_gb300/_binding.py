@@ -42,7 +42,8 @@ class mrstat_plan_info_t(ctypes.Structure):
 
 
 class mrstat_kernel_stats(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8), ("timed", ctypes.c_int64 * 8)]
+    _fields_ = [("launches", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8), ("timed", ctypes.c_int64 * 8),
+                ("kernels", ctypes.c_int64 * 8)]
 
 
 GN_MAX_OUTER = 64
@@ -422,7 +423,7 @@ def mrstat_profile_start(plan, kernels=("ycontract", "jhw_dot")):
 def mrstat_profile_stop(plan) -> dict:
     st = mrstat_kernel_stats()
     _check(load().mrstat_profile_stop(plan, ctypes.byref(st)), "mrstat_profile_stop")
-    return {name: {"launches": st.launches[i], "ms": st.ms[i], "timed": st.timed[i]}
+    return {name: {"launches": st.launches[i], "ms": st.ms[i], "timed": st.timed[i], "kernels": st.kernels[i]}
             for name, i in KERNEL_IDS.items()}
 
 

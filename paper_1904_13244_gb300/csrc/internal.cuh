@@ -121,6 +121,7 @@ struct Plan {
 
   // tracing
   int64_t launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t kernel_launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   bool prof_on = false;
   uint32_t prof_mask = 0;
   struct Mark {
@@ -178,8 +179,11 @@ struct Span {
   cudaStream_t st;
   int n;
   cudaEvent_t a = nullptr, b = nullptr;
-  Span(Plan* plan, int k, cudaStream_t s, int nlaunch = 1) : p(plan), kid(k), st(s), n(nlaunch) {
+  // nlaunch: launches, or products of a persistent launch, the span counts; nkernels: the
+  // kernel launches it makes (default: nlaunch)
+  Span(Plan* plan, int k, cudaStream_t s, int nlaunch = 1, int nkernels = -1) : p(plan), kid(k), st(s), n(nlaunch) {
     p->launches[kid] += nlaunch;
+    p->kernel_launches[kid] += nkernels < 0 ? nlaunch : nkernels;
     if (p->prof_on && ((p->prof_mask >> kid) & 1u)) {
       a = pool_event(p);
       b = pool_event(p);

@@ -2339,7 +2339,7 @@ bool lowrank_cg_fixed_persistent(Plan* p, const float* rhs, float* x, int iters,
     return true;
   }
   {
-    Span sp(p, MRSTAT_K_JHW_DOT, st, iters);  // one span, counted as `iters` products
+    Span sp(p, MRSTAT_K_JHW_DOT, st, iters, 1);  // one launch, counted as `iters` products
     e = launch_cg_columns(p, rhs, x, iters, true, st);
   }
   if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorInvalidConfiguration || e == cudaErrorNotSupported) {

@@ -184,7 +184,7 @@ int do_jhw(Plan* p, const float2* w, float* g, cudaStream_t st) {
   cudaError_t e;
   if (p->rc_seg > 0) {
     {
-      Span sp(p, MRSTAT_K_JHW_DOT, st);
+      Span sp(p, MRSTAT_K_JHW_DOT, st, 1, 2);  // the product and the segment sum
       e = launch_rc_product(*p, 1, nullptr, p->wt, g, st);
     }
     return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "recompute J^H w launch");
@@ -291,7 +291,7 @@ int do_jhjv(Plan* p, const float* v, float* out, cudaStream_t st, double* vdot, 
     // the simulation, both phase-encode sums and the tangent products in one pass
     cudaError_t e;
     {
-      Span sp(p, MRSTAT_K_JHW_DOT, st);
+      Span sp(p, MRSTAT_K_JHW_DOT, st, 1, 2);  // the product and the segment sum
       e = launch_rc_product(*p, 2, v, nullptr, out, st);
     }
     return e == cudaSuccess ? MRSTAT_OK : cuda_fail(e, "recompute J^H J v launch");
@@ -375,6 +375,7 @@ int mrstat_plan_check(mrstat_plan* plan) {
 int mrstat_profile_start(mrstat_plan* plan, uint32_t kernel_mask) {
   if (plan == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL plan");
   for (int64_t& c : plan->launches) c = 0;
+  for (int64_t& c : plan->kernel_launches) c = 0;
   plan->marks.clear();
   plan->pool_used = 0;
   plan->prof_mask = kernel_mask;
@@ -386,7 +387,10 @@ int mrstat_profile_stop(mrstat_plan* plan, mrstat_kernel_stats* out) {
   if (plan == nullptr || out == nullptr) return fail(MRSTAT_ERR_INVALID_ARG, "NULL argument");
   DeviceGuard g(plan->device);
   std::memset(out, 0, sizeof(*out));
-  for (int k = 0; k < 8; ++k) out->launches[k] = plan->launches[k];
+  for (int k = 0; k < 8; ++k) {
+    out->launches[k] = plan->launches[k];
+    out->kernels[k] = plan->kernel_launches[k];
+  }
   for (const Plan::Mark& m : plan->marks) {
     cudaError_t e = cudaEventSynchronize(m.b);
     float ms = 0.f;
@@ -748,7 +752,7 @@ int mrstat_jhw_ckpt(mrstat_plan* plan, const float* w, float* gout, void* stream
   if (status != MRSTAT_OK) return status;
   cudaError_t e;
   {
-    Span sp(plan, MRSTAT_K_JHW_DOT, st, 2);
+    Span sp(plan, MRSTAT_K_JHW_DOT, st, 1, 2);  // the segment kernel and the segment sum
     e = launch_segment_jhw(*plan, plan->ckpt_alpha, plan->ckpt_b1, plan->ckpt_mask, plan->ckpt_interval,
                            plan->ckpt_nseg, plan->ckpt, plan->zpart, gout, st);
   }

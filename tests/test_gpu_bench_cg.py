@@ -126,7 +126,8 @@ def test_bench_cg_on_a_few_columns_matches_oracle(mr):
         applied = plan.cg_applied()
         x_lpi = jhjv_cg(plan, b_dev, ITERS).cpu().numpy()
         x_gpu = x_gpu.cpu().numpy().astype(np.float64)
-    assert prof["jhw_dot"]["launches"] == ITERS  # one persistent launch carried every product
+    assert prof["jhw_dot"]["launches"] == ITERS  # counted as ITERS products ...
+    assert prof["jhw_dot"]["kernels"] == 1       # ... made by one persistent launch
     assert applied == ITERS
     e_ref = metrics.relerr(x_gpu, x_ref)
     e_lpi = metrics.relerr(x_gpu, x_lpi)
