@@ -69,8 +69,8 @@ NCU_TRAFFIC = {
     ("xdft", "0728f575d9d96a3d"): 13670656.0,
     ("xdft_adj", "0728f575d9d96a3d"): 13668608.0,
     # profiles/lr_cg_columns_kernel_brain224.md: one persistent CG launch of 30 products
-    # read 20 974 592 B and wrote 39 168 B (caches flushed before it), per product
-    ("jhw_dot", "8932e29a79b109c9"): (20974592.0 + 39168.0) / 30,
+    # read 20 977 920 B and wrote 47 360 B (caches flushed before it), per product
+    ("jhw_dot", "ef415ea5c30e16ab"): (20977920.0 + 47360.0) / 30,
     # profiles/rc_product_kernel_brain224.md: one recompute J^H J v read 12 679 936 B
     ("jhw_dot_rc", "d25e8cd46d9baeac"): 12679936.0,
 }
@@ -612,6 +612,41 @@ def differentiation(mr, torch, seq, ph, reps=10):
     return out
 
 
+def plain_products(mr, torch, names=("ellipse64", "brain224"), reps=20):
+    """The plain FP32 form's single products per second (cached time courses): J.v,
+    Re(J^H w) and Re(J^H J) v on the 64 x 64 / 320-TR ellipse workload and on brain224, CUDA
+    events around reps back-to-back calls after a warm-up; the linearisation (K1) timed on
+    its own."""
+    out = {}
+    for name in names:
+        seq, ph = synth.config(name)
+        pl = mr.Plan(seq)
+        a = torch.tensor(alpha_of(ph), device="cuda")
+        v = torch.tensor(synth.random_params(seq.nv, 3).astype(np.float32), device="cuda")
+        w = torch.tensor(synth.random_kspace(seq.ntr, seq.nkx, 4), dtype=torch.complex64, device="cuda")
+        jv = torch.empty((seq.ntr, seq.nkx), dtype=torch.complex64, device="cuda")
+        g = torch.empty((4, seq.nv), dtype=torch.float32, device="cuda")
+        res = {"grid": [seq.nx, seq.ny], "ntr": seq.ntr}
+        for key, fn in (("linearize", lambda: pl.linearize(a)), ("jvp", lambda: pl.jvp(v, out=jv)),
+                        ("jhw", lambda: pl.jhw(w, out=g)), ("jhjv", lambda: pl.jhjv(v, out=g))):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res[key + "_ms"] = ms
+            if key != "linearize":
+                res[key + "_per_s"] = 1e3 / ms
+        pl.check()
+        pl.close()
+        out[name] = res
+    return out
+
+
 def learned_part(mr, torch, args, name, rank, iters, timed):
     """The learned-part form on a workload with a smooth, known B1 map in [0.8, 1.2]: a
     rank-R basis and the surrogate trained for this sequence on B1-varied samples, then the
@@ -1102,6 +1137,11 @@ def main():
         recon["settings"] = ("15 GN x 30 CG, SNR 30, rho the exact least-squares solution at T1 1000 ms / T2 100 ms, mask 0.1; "
                              "surrogate: 10 surrogate + 5 exact iterations, low-rank CG matrix")
 
+    # the plain form's single products at 64 x 64 and 224 x 224
+    products = None
+    if not args.no_shapes and rank == 0 and world == 1:
+        products = plain_products(mr, torch)
+
     # the differentiation form (autograd, with and without Bloch-state checkpoints)
     diff = None
     if not args.no_diff and rank == 0 and world == 1:
@@ -1162,7 +1202,8 @@ def main():
                 "cpu_baseline": cpu, "cg_check": cg_check, "compressed_exact": compressed_exact, "plain": plain,
                 "precision": precision,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
-                "recon": recon, "learned_part": learned, "differentiation": diff, "surrogate": surrogate_info, "shapes": shapes, "slice_profile": slice_prof,
+                "recon": recon, "learned_part": learned, "differentiation": diff, "plain_products": products,
+                "surrogate": surrogate_info, "shapes": shapes, "slice_profile": slice_prof,
                 "kernel_ms_per_step": {k: v for k, v in per_step_ms.items()}}
         print(json.dumps(line), flush=True)
     if net is not None:
