@@ -160,9 +160,27 @@ __device__ __forceinline__ float2 rc_warp_sum(float (&v)[2 * K], int lane) {
   return make_float2(re, im);
 }
 
-// grid (nx, nseg), block = ny rounded up to whole warps (<= kMaxRows)
+// One row's voxel data and running sums in rc_product_kernel.
+struct RcRow {
+  bool on;        // the row exists (rows past ny contribute zeros)
+  int iy, j;
+  float m;        // mask
+  float2 rh;      // rho * mask
+  RcRelax r;
+  RcState s;
+  float bj;
+  float v0, v1, v2, v3;
+  float g0, g1, g2, g3;
+};
+
+// grid (nx, nseg), block = ceil(ny / kRows) rounded up to whole warps; thread t owns rows
+// t + q H, q < kRows, H = ceil(ny / kRows): the recursions of its rows are independent
+// chains (instruction-level parallelism), and the per-TR table loads and the block sums
+// serve all of them.
+constexpr int kRows = 2;
+
 template <int MODE>
-__global__ void __launch_bounds__(kMaxRows, 3)
+__global__ void __launch_bounds__(kMaxRows / kRows, 4)
 rc_product_kernel(const float* __restrict__ rlx, const float* __restrict__ ckpt, const float2* __restrict__ rho,
                   const float* __restrict__ maskf, const float* __restrict__ b1, const float* __restrict__ v,
                   const float2* __restrict__ cs, const float* __restrict__ phi, const int* __restrict__ kyi,
@@ -173,78 +191,95 @@ rc_product_kernel(const float* __restrict__ rlx, const float* __restrict__ ckpt,
   __shared__ float2 part[kMaxRows / 32][kChunk];
   __shared__ float2 asum[kChunk];
   const int ix = blockIdx.x, sg = blockIdx.y;
-  const int iy = threadIdx.x, lane = iy & 31, warp = iy >> 5, nwarps = blockDim.x >> 5;
-  const bool row = iy < ny;
-  const int j = row ? iy * nx + ix : 0;
-  // voxel data (a thread past the last row, or outside the mask, contributes zeros)
-  const float m = row ? maskf[j] : 0.f;
-  const float2 rh = row ? rho[j] : make_float2(0.f, 0.f);  // rho * mask
-  RcRelax r{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  RcState s{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  float bj = 1.f;
-  if (row) {
-    r = {rlx[j], rlx[(size_t)nv + j], rlx[2 * (size_t)nv + j], rlx[3 * (size_t)nv + j],
-         rlx[4 * (size_t)nv + j], rlx[5 * (size_t)nv + j], rlx[6 * (size_t)nv + j], rlx[7 * (size_t)nv + j]};
-    const float* c = ckpt + (size_t)sg * 6 * nv + j;
-    s = {c[0], c[(size_t)nv], c[2 * (size_t)nv], c[3 * (size_t)nv], c[4 * (size_t)nv], c[5 * (size_t)nv]};
-    if (b1 != nullptr) bj = b1[j];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = blockDim.x >> 5;
+  const int H = (ny + kRows - 1) / kRows;
+  RcRow w[kRows];
+#pragma unroll
+  for (int q = 0; q < kRows; ++q) {
+    RcRow& x = w[q];
+    x.iy = t + q * H;
+    x.on = t < H && x.iy < ny;
+    x.j = x.on ? x.iy * nx + ix : 0;
+    x.m = x.on ? maskf[x.j] : 0.f;
+    x.rh = x.on ? rho[x.j] : make_float2(0.f, 0.f);
+    x.r = RcRelax{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    x.s = RcState{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    x.bj = 1.f;
+    x.v0 = x.v1 = x.v2 = x.v3 = 0.f;
+    x.g0 = x.g1 = x.g2 = x.g3 = 0.f;
+    if (x.on) {
+      const int j = x.j;
+      x.r = {rlx[j], rlx[(size_t)nv + j], rlx[2 * (size_t)nv + j], rlx[3 * (size_t)nv + j],
+             rlx[4 * (size_t)nv + j], rlx[5 * (size_t)nv + j], rlx[6 * (size_t)nv + j], rlx[7 * (size_t)nv + j]};
+      const float* c = ckpt + (size_t)sg * 6 * nv + j;
+      x.s = {c[0], c[(size_t)nv], c[2 * (size_t)nv], c[3 * (size_t)nv], c[4 * (size_t)nv], c[5 * (size_t)nv]};
+      if (b1 != nullptr) x.bj = b1[j];
+      if (MODE != RC_JHW) {
+        x.v0 = v[j];
+        x.v1 = v[(size_t)nv + j];
+        x.v2 = v[2 * (size_t)nv + j] * x.m;
+        x.v3 = v[3 * (size_t)nv + j] * x.m;
+      }
+    }
   }
-  float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-  if (MODE != RC_JHW && row) {
-    v0 = v[j];
-    v1 = v[(size_t)nv + j];
-    v2 = v[2 * (size_t)nv + j] * m;
-    v3 = v[3 * (size_t)nv + j] * m;
-  }
-  float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
   const int na = sg * seg, ne = min(ntr, na + seg);
   for (int n0 = na; n0 < ne; n0 += kChunk) {
-    float y0[kChunk], y1[kChunk], y2[kChunk];
-    float2 e[kChunk];
+    float y0[kRows][kChunk], y1[kRows][kChunk], y2[kRows][kChunk];
+    float2 e[kRows][kChunk];
     float p[2 * kChunk];
 #pragma unroll
     for (int k = 0; k < kChunk; ++k) {
       const int n = n0 + k;
-      y0[k] = y1[k] = y2[k] = 0.f;
-      e[k] = make_float2(0.f, 0.f);
       p[2 * k] = p[2 * k + 1] = 0.f;
+#pragma unroll
+      for (int q = 0; q < kRows; ++q) {
+        y0[q][k] = y1[q][k] = y2[q][k] = 0.f;
+        e[q][k] = make_float2(0.f, 0.f);
+      }
       if (n < ne) {  // uniform across the block
-        float cc, sn;
-        rc_cs(cs, phi, b1, bj, n, cc, sn);
-        rc_rotate(s, cc, sn);
-        rc_decay(s, r.x1a, r.x2a, r.d1a, r.d2a);
-        y0[k] = s.my * m;
-        y1[k] = s.ay * m;
-        y2[k] = s.by * m;
-        // rows past ny (the block's last warp) keep e = 0: their index would leave the table
-        if (row) e[k] = __ldg(roots + rc_mod(__ldg(kyi + n) * iy, ny, magic));
-        if (MODE != RC_JHW) {
-          // q = i u, u = rho t + (v2 + i v3) m_y; p = E q
-          const float t = fmaf(v0, y1[k], v1 * y2[k]);
-          const float ur = fmaf(rh.x, t, v2 * y0[k]);
-          const float ui = fmaf(rh.y, t, v3 * y0[k]);
-          const float qr = -ui, qi = ur;
-          p[2 * k] = fmaf(e[k].x, qr, -e[k].y * qi);
-          p[2 * k + 1] = fmaf(e[k].x, qi, e[k].y * qr);
+        float2 csn = make_float2(1.f, 0.f);
+        if (b1 == nullptr) csn = __ldg(cs + n);
+        const int kyn = __ldg(kyi + n);
+#pragma unroll
+        for (int q = 0; q < kRows; ++q) {
+          RcRow& x = w[q];
+          float cc = csn.x, sn = csn.y;
+          if (b1 != nullptr) sincosf(__ldg(phi + n) * x.bj, &sn, &cc);
+          rc_rotate(x.s, cc, sn);
+          rc_decay(x.s, x.r.x1a, x.r.x2a, x.r.d1a, x.r.d2a);
+          y0[q][k] = x.s.my * x.m;
+          y1[q][k] = x.s.ay * x.m;
+          y2[q][k] = x.s.by * x.m;
+          // rows that do not exist keep e = 0: their index would leave the table
+          if (x.on) e[q][k] = __ldg(roots + rc_mod(kyn * x.iy, ny, magic));
+          if (MODE != RC_JHW) {
+            // q = i u, u = rho t + (v2 + i v3) m_y; p += E q (both rows of the thread)
+            const float tt = fmaf(x.v0, y1[q][k], x.v1 * y2[q][k]);
+            const float ur = fmaf(x.rh.x, tt, x.v2 * y0[q][k]);
+            const float ui = fmaf(x.rh.y, tt, x.v3 * y0[q][k]);
+            const float qr = -ui, qi = ur;
+            p[2 * k] += fmaf(e[q][k].x, qr, -e[q][k].y * qi);
+            p[2 * k + 1] += fmaf(e[q][k].x, qi, e[q][k].y * qr);
+          }
+          rc_decay(x.s, x.r.x1b, x.r.x2b, x.r.d1b, x.r.d2b);
         }
-        rc_decay(s, r.x1b, r.x2b, r.d1b, r.d2b);
       }
     }
     float2 a[kChunk];
     if (MODE != RC_JHW) {
-      const float2 w = rc_warp_sum<kChunk>(p, lane);
+      const float2 ws = rc_warp_sum<kChunk>(p, lane);
       constexpr int kLanesPerSlot = 32 / kChunk;
-      if ((lane & (kLanesPerSlot - 1)) == 0) part[warp][lane / kLanesPerSlot] = w;
+      if ((lane & (kLanesPerSlot - 1)) == 0) part[warp][lane / kLanesPerSlot] = ws;
       __syncthreads();
-      if (iy < kChunk) {
-        float2 t = make_float2(0.f, 0.f);
+      if (t < kChunk) {
+        float2 u = make_float2(0.f, 0.f);
         for (int wi = 0; wi < nwarps; ++wi) {
-          const float2 u = part[wi][iy];
-          t.x += u.x;
-          t.y += u.y;
+          const float2 pw = part[wi][t];
+          u.x += pw.x;
+          u.y += pw.y;
         }
-        asum[iy] = t;
-        if (MODE == RC_JV && n0 + iy < ne) A[(size_t)(n0 + iy) * nx + ix] = t;
+        asum[t] = u;
+        if (MODE == RC_JV && n0 + t < ne) A[(size_t)(n0 + t) * nx + ix] = u;
       }
       __syncthreads();
 #pragma unroll
@@ -256,24 +291,33 @@ rc_product_kernel(const float* __restrict__ rlx, const float* __restrict__ ckpt,
     }
     if (MODE != RC_JV) {
 #pragma unroll
-      for (int k = 0; k < kChunk; ++k) {
-        // b = conj(E) a; Re conj(dq/dalpha) b for q = i rho m (tangents) and q = i m (rho)
-        const float br = fmaf(e[k].x, a[k].x, e[k].y * a[k].y);
-        const float bi = fmaf(e[k].x, a[k].y, -e[k].y * a[k].x);
-        const float imcb = fmaf(rh.x, bi, -rh.y * br);
-        g0 = fmaf(y1[k], imcb, g0);
-        g1 = fmaf(y2[k], imcb, g1);
-        g2 = fmaf(y0[k], bi, g2);
-        g3 = fmaf(-y0[k], br, g3);
+      for (int q = 0; q < kRows; ++q) {
+        RcRow& x = w[q];
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) {
+          // b = conj(E) a; Re conj(dq/dalpha) b for q = i rho m (tangents) and q = i m (rho)
+          const float br = fmaf(e[q][k].x, a[k].x, e[q][k].y * a[k].y);
+          const float bi = fmaf(e[q][k].x, a[k].y, -e[q][k].y * a[k].x);
+          const float imcb = fmaf(x.rh.x, bi, -x.rh.y * br);
+          x.g0 = fmaf(y1[q][k], imcb, x.g0);
+          x.g1 = fmaf(y2[q][k], imcb, x.g1);
+          x.g2 = fmaf(y0[q][k], bi, x.g2);
+          x.g3 = fmaf(-y0[q][k], br, x.g3);
+        }
       }
     }
   }
-  if (MODE != RC_JV && row) {
-    float* gp = gpart + (size_t)sg * 4 * nv + j;
-    gp[0] = g0 * scale;
-    gp[(size_t)nv] = g1 * scale;
-    gp[2 * (size_t)nv] = g2 * scale;
-    gp[3 * (size_t)nv] = g3 * scale;
+  if (MODE != RC_JV) {
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
+      const RcRow& x = w[q];
+      if (!x.on) continue;
+      float* gp = gpart + (size_t)sg * 4 * nv + x.j;
+      gp[0] = x.g0 * scale;
+      gp[(size_t)nv] = x.g1 * scale;
+      gp[2 * (size_t)nv] = x.g2 * scale;
+      gp[3 * (size_t)nv] = x.g3 * scale;
+    }
   }
 }
 
@@ -304,7 +348,7 @@ cudaError_t launch_rc_linearize(const Plan& p, const float* alpha, const float* 
 // 2: J^H J v into g (nkx == nx)
 cudaError_t launch_rc_product(const Plan& p, int mode, const float* v, const float2* wt, float* g, cudaStream_t st) {
   if (p.nv == 0) return cudaSuccess;
-  const int threads = (p.ny + 31) / 32 * 32;
+  const int threads = ((p.ny + kRows - 1) / kRows + 31) / 32 * 32;
   const dim3 grid(p.nx, p.rc_nseg);
   const unsigned magic = p.ny > 1 ? (unsigned)((0x100000000ull + (unsigned)p.ny - 1) / (unsigned)p.ny) : 0u;
   const float scale = mode == RC_JHJV ? (float)p.nx : 1.f;
