@@ -71,8 +71,8 @@ NCU_TRAFFIC = {
     # profiles/lr_cg_columns_kernel_brain224.md: one persistent CG launch of 30 products
     # read 20 977 920 B and wrote 47 360 B (caches flushed before it), per product
     ("jhw_dot", "ef415ea5c30e16ab"): (20977920.0 + 47360.0) / 30,
-    # profiles/rc_product_kernel_brain224.md: one recompute J^H J v read 12 679 936 B
-    ("jhw_dot_rc", "d25e8cd46d9baeac"): 12679936.0,
+    # profiles/rc_product_kernel_brain224.md: one recompute J^H J v read 12 698 624 B
+    ("jhw_dot_rc", "43b010ca1597d1da"): 12698624.0,
 }
 
 
