@@ -483,15 +483,14 @@ lr_gram_short_kernel(const float* __restrict__ HT, int ldh, const float* __restr
 }
 
 // ---------------------------------------------------------------------------
-// Phase-encode DFT by factorisation, for ny = 32 N1 (N1 <= 8): with iy = 32 i1 + i2 and
-// ky = k1 + N1 k2 the exponent ky iy (mod ny) splits into N1-point, twiddle and 32-point
-// parts,
-//     X[k1 + N1 k2] = sum_i2 w32^(k2 i2) w^(k1 i2) sum_i1 wN1^(k1 i1) x[32 i1 + i2],
-// with w = exp(-2 pi i / ny), wN1 = w^32 and w32 = w^N1, all read from the exact root
-// table.  A warp holds one column (lane = i2): a dense N1-point DFT per lane, the twiddle,
-// then a 32-point FFT across the lanes (radix-2 decimation in frequency by shuffles; lane
-// L ends with output index bitrev(L)).  The adjoint is the same with conjugate roots in
-// the reverse order.  Everything stays in float32 (no split-BF16 rounding).
+// Phase-encode DFT by factorisation, for ny = 16 M with M = 2 N1 (N1 <= 8): with
+// iy = 16 i1 + i2 and ky = k1 + M k2 (i1, k1 < M; i2, k2 < 16) the exponent ky iy (mod ny)
+// splits into M-point, twiddle and 16-point parts,
+//     X[k1 + M k2] = sum_i2 W16^(k2 i2) w^(k1 i2) sum_i1 wM^(k1 i1) x[16 i1 + i2],
+// with w = exp(-2 pi i / ny), wM = w^16 and W16 = w^M.  The M-point DFT is one radix-2
+// step over two N1-point DFTs, each formed by the symmetries of its matrix; the 16-point
+// DFT is a radix-2 FFT held in one thread's registers.  The adjoint runs the same steps
+// with conjugate roots in the reverse order.  Everything stays in float32.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -499,82 +498,134 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
   return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
 }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
-// In-warp 32-point DFT (lane = input index; the result at lane L is output bitrev(L)),
-// radix-2 decimation in frequency by shuffles, branch-free: at the stage of span h a lane
-// whose bit h is clear keeps v + p, the other p - v times w_(2h)^(pos - h) (pos = lane mod
-// 2h).  The per-lane stage factors are the same for every column a warp transforms, so
-// they are formed once: sign[s] = -1 / +1 and tw[s] for the spans h = 16, 8, 4, 2 (1 for
-// the lanes that keep the sum; span 1 needs none).  CONJ: conjugate roots (the adjoint).
-// rt[k] = w^k with w32 = w^N1.
-struct Fft32Lane {
-  float sg[5];
-  float2 tw[4];
-};
-
-template <bool CONJ>
-__device__ __forceinline__ Fft32Lane fft32_lane(const float2* rt, int n1, int lane) {
-  Fft32Lane f;
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int h = 16 >> s;
-    const int pos = lane & (2 * h - 1);
-    f.sg[s] = pos < h ? 1.f : -1.f;
-    if (s < 4) {
-      float2 w = pos < h ? make_float2(1.f, 0.f) : rt[(pos - h) * (16 / h) * n1];  // w_(2h)^(pos - h)
-      if (CONJ) w.y = -w.y;
-      f.tw[s] = w;
-    }
-  }
-  return f;
-}
-
-__device__ __forceinline__ float2 fft32_warp(float2 v, const Fft32Lane& f) {
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int h = 16 >> s;
-    const float px = __shfl_xor_sync(0xffffffffu, v.x, h);
-    const float py = __shfl_xor_sync(0xffffffffu, v.y, h);
-    v = make_float2(fmaf(f.sg[s], v.x, px), fmaf(f.sg[s], v.y, py));
-    if (s < 4) v = cmul(v, f.tw[s]);
-  }
-  return v;
-}
-
-// Dense N1-point DFT of x by the conjugate symmetry of its matrix (W[N1 - k][i] =
-// conj(W[k][i])): with A_k = sum_i Re W[k][i] x_i and B_k = sum_i Im W[k][i] x_i,
-// X_k = A_k + i B_k and X_(N1 - k) = A_k - i B_k; X_0 is the plain sum, and for even N1
-// X_(N1/2) is the alternating sum.  CONJ: the conjugate matrix (W is symmetric, so this
-// is also its adjoint).
+// N1-point DFT of x (sign -; CONJ: sign +) by the two symmetries of its matrix: with
+// u_i = x_i + x_(N1 - i), d_i = x_i - x_(N1 - i) for 0 < i < N1 / 2,
+//     A_k = x_0 + sum_i cos(2 pi k i / N1) u_i  [+ (-1)^k x_(N1/2) for even N1],
+//     B_k = sum_i sin(2 pi k i / N1) d_i,
+// X_k = A_k - i B_k and X_(N1 - k) = A_k + i B_k (swapped for CONJ); X_0 is the plain
+// sum and, for even N1, X_(N1/2) the alternating one.
 template <int N1, bool CONJ>
-__device__ __forceinline__ void dft_small(const DftSmall& W, const float2 (&x)[N1], float2 (&X)[N1]) {
+__device__ __forceinline__ void dft_n1(const DftSmall& W, const float2 (&x)[N1], float2 (&X)[N1]) {
+  constexpr int P = (N1 - 1) / 2;
+  constexpr bool EVEN = N1 % 2 == 0;
+  float2 u[P + 1], d[P + 1];
+#pragma unroll
+  for (int i = 1; i <= P; ++i) {
+    u[i] = cadd(x[i], x[N1 - i]);
+    d[i] = csub(x[i], x[N1 - i]);
+  }
   float2 s0 = x[0];
 #pragma unroll
-  for (int i = 1; i < N1; ++i) s0 = make_float2(s0.x + x[i].x, s0.y + x[i].y);
+  for (int i = 1; i <= P; ++i) s0 = cadd(s0, u[i]);
+  if (EVEN) s0 = cadd(s0, x[N1 / 2]);
   X[0] = s0;
 #pragma unroll
-  for (int k = 1; 2 * k < N1; ++k) {
+  for (int k = 1; k <= P; ++k) {
     float ax = x[0].x, ay = x[0].y, bx = 0.f, by = 0.f;
-#pragma unroll
-    for (int i = 1; i < N1; ++i) {
-      const float2 w = W.w[k][i];
-      ax = fmaf(w.x, x[i].x, ax);
-      ay = fmaf(w.x, x[i].y, ay);
-      bx = fmaf(w.y, x[i].x, bx);
-      by = fmaf(w.y, x[i].y, by);
+    if (EVEN) {
+      const float sg = (k & 1) ? -1.f : 1.f;
+      ax = fmaf(sg, x[N1 / 2].x, ax);
+      ay = fmaf(sg, x[N1 / 2].y, ay);
     }
-    // A + i B = (ax - by, ay + bx); A - i B = (ax + by, ay - bx)
-    const float2 plus = make_float2(ax - by, ay + bx), minus = make_float2(ax + by, ay - bx);
-    X[k] = CONJ ? minus : plus;
-    X[N1 - k] = CONJ ? plus : minus;
+#pragma unroll
+    for (int i = 1; i <= P; ++i) {
+      const float c = W.c[k - 1][i - 1], s = W.s[k - 1][i - 1];
+      ax = fmaf(c, u[i].x, ax);
+      ay = fmaf(c, u[i].y, ay);
+      bx = fmaf(s, d[i].x, bx);
+      by = fmaf(s, d[i].y, by);
+    }
+    const float2 minus_ib = make_float2(ax + by, ay - bx), plus_ib = make_float2(ax - by, ay + bx);
+    X[k] = CONJ ? plus_ib : minus_ib;
+    X[N1 - k] = CONJ ? minus_ib : plus_ib;
   }
-  if (N1 % 2 == 0) {
+  if (EVEN) {
     float2 a = x[0];
 #pragma unroll
-    for (int i = 1; i < N1; ++i) a = (i & 1) ? make_float2(a.x - x[i].x, a.y - x[i].y) : make_float2(a.x + x[i].x, a.y + x[i].y);
+    for (int i = 1; i <= P; ++i) a = (i & 1) ? csub(a, u[i]) : cadd(a, u[i]);
+    a = ((N1 / 2) & 1) ? csub(a, x[N1 / 2]) : cadd(a, x[N1 / 2]);
     X[N1 / 2] = a;
   }
 }
+
+// M-point DFT (M = 2 N1) by one radix-2 step in time: the N1-point DFTs E of the even and
+// O of the odd samples, Y_k = E_k + wM^k O_k and Y_(k + N1) = E_k - wM^k O_k.
+template <int N1, bool CONJ>
+__device__ __forceinline__ void dft_m(const DftSmall& W, const float2 (&x)[2 * N1], float2 (&Y)[2 * N1]) {
+  float2 xe[N1], xo[N1], E[N1], O[N1];
+#pragma unroll
+  for (int i = 0; i < N1; ++i) {
+    xe[i] = x[2 * i];
+    xo[i] = x[2 * i + 1];
+  }
+  dft_n1<N1, CONJ>(W, xe, E);
+  dft_n1<N1, CONJ>(W, xo, O);
+#pragma unroll
+  for (int k = 0; k < N1; ++k) {
+    const float2 t = k == 0 ? O[0] : (CONJ ? cmulc(O[k], W.wm[k]) : cmul(O[k], W.wm[k]));
+    Y[k] = cadd(E[k], t);
+    Y[k + N1] = csub(E[k], t);
+  }
+}
+
+// z times W16^m = exp(-2 pi i m / 16) (CONJ: exp(+2 pi i m / 16)), 0 <= m < 8; m is a
+// compile-time constant once the callers' loops are unrolled, so the branches fold.
+template <bool CONJ>
+__device__ __forceinline__ float2 tw16(float2 z, int m) {
+  constexpr float C1 = 0.923879532511286756f;  // cos(pi / 8)
+  constexpr float S1 = 0.382683432365089772f;  // sin(pi / 8)
+  constexpr float R2 = 0.707106781186547524f;  // cos(pi / 4)
+  if (m == 0) return z;
+  if (m == 4) return CONJ ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+  if (m == 2 || m == 6) {
+    // (1 -/+ i) / sqrt 2 for m = 2, (-1 -/+ i) / sqrt 2 for m = 6
+    const float p = (z.x + z.y) * R2, q = (z.y - z.x) * R2;
+    if (m == 2) return CONJ ? make_float2(-q, p) : make_float2(p, q);
+    return CONJ ? make_float2(-p, -q) : make_float2(q, -p);
+  }
+  const float c = m == 1 ? C1 : m == 3 ? S1 : m == 5 ? -S1 : -C1;
+  const float s = m == 1 ? S1 : m == 3 ? C1 : m == 5 ? C1 : S1;
+  // forward: (x + i y)(c - i s); CONJ: (x + i y)(c + i s)
+  return CONJ ? make_float2(fmaf(z.x, c, -z.y * s), fmaf(z.y, c, z.x * s))
+              : make_float2(fmaf(z.x, c, z.y * s), fmaf(z.y, c, -z.x * s));
+}
+
+__host__ __device__ constexpr int brev4(int k) {
+  return ((k & 1) << 3) | ((k & 2) << 1) | ((k & 4) >> 1) | ((k & 8) >> 3);
+}
+
+// One radix-2 stage of span H of the 16-point FFT below (H a template argument, so that
+// every index and twiddle is a compile-time constant).
+template <bool CONJ, int H>
+__device__ __forceinline__ void fft16_stage(float2 (&a)[16]) {
+#pragma unroll
+  for (int g = 0; g < 16; g += 2 * H) {
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const float2 u = a[g + j], v = a[g + j + H];
+      a[g + j] = cadd(u, v);
+      a[g + j + H] = tw16<CONJ>(csub(u, v), j * (8 / H));
+    }
+  }
+}
+
+// 16-point DFT in registers, radix-2 decimation in frequency: a in natural order on entry,
+// X_k in a[brev4(k)] on return.
+template <bool CONJ>
+__device__ __forceinline__ void fft16(float2 (&a)[16]) {
+  fft16_stage<CONJ, 8>(a);
+  fft16_stage<CONJ, 4>(a);
+  fft16_stage<CONJ, 2>(a);
+  fft16_stage<CONJ, 1>(a);
+}
+
+// Row stride (complex values) of the per-basis-function rows of the column kernels: the
+// M-point stage stores Z[k1][i2] at 17 k1 + i2, so that the lanes of the 16-point stage
+// (one per (row, k1)) read and write distinct banks.
+__host__ __device__ constexpr int col_row(int ny) { return 17 * (ny / 16); }
 
 // coefT[(k R + r)][ix][iy] = coef[(k R + r)][iy nx + ix]: the coefficients in image-column
 // order, so that a block working on one column ix reads them contiguously (32 x 32 tiles)
@@ -601,13 +652,14 @@ __global__ void lr_coef_transpose_kernel(const float* __restrict__ coef, int nx,
 // (ny = 32 N1); block c of the pair owns the basis functions r in [c RC, (c + 1) RC),
 // RC = ceil(R / 2), and the R columns h_r(iy) never leave shared memory.
 //   0. each block loads the column's voxel data (v and rho);
-//   1. warp w forms h_r(iy) for iy = 32 i1 + lane in registers for its r and applies the
-//      factorised phase-encode DFT -> H_r(ky);
+//   1. warp w owns the rows r = 2w, 2w + 1: lane (r, i2) forms h_r(16 i1 + i2) for i1 < M
+//      in registers, applies the M-point DFT and the twiddle, and lane (r, k1) the
+//      16-point FFT of the factorised phase-encode DFT -> H_r(ky) (warp barriers only);
 //   2. the per-ky Gram through the TR axis: one thread per TR forms the block's part of
 //      s_t = sum_q U[t][q] H_q(ky(t)) and also stores it into the peer; after a cluster
 //      barrier each block adds the two parts (the same sum in both), then one lane per ky
 //      (a warp per r) sums U[t][r] s_t over the TRs of ky;
-//   3. warp w applies the adjoint DFT -> P_r(iy);
+//   3. the same warps apply the adjoint DFT -> P_r(iy);
 //   4. one thread per iy contracts with the tangents over the block's r, keeping the part
 //      for its own half of the column and storing the rest into the peer; after a second
 //      cluster barrier each block adds the two parts for its half, writes g (masked,
@@ -626,14 +678,14 @@ __host__ __device__ inline int sbuf_slots(int kmax) { return kmax > kSlotRegs ? 
 
 size_t column_smem_bytes(int ny, int R, int kmax) {
   const size_t rc = (size_t)(R + 1) / 2;
-  return sizeof(float2) * ((size_t)ny + rc * (ny + 1) + (size_t)(kmax + sbuf_slots(kmax)) * ny) +
+  return sizeof(float2) * ((size_t)ny + rc * col_row(ny) + (size_t)(kmax + sbuf_slots(kmax)) * ny) +
          sizeof(float) * 14 * (size_t)ny;
 }
 
 // Shared-memory layout of the column kernels and the peer's exchange buffers.
 struct ColShared {
   float2* rt;      // [NY] w^k
-  float2* hs;      // [RC][NY + 1]: H, then G, then P
+  float2* hs;      // [RC][col_row(NY)]: Z, H, G, T, P (see column_core)
   float2* sbuf;    // [kmax][NY] this block's part of s (only with kmax > kSlotRegs)
   float2* sin;     // [kmax][NY] the peer's part (written by it)
   float* vox;      // [6][NY]: v0, v1, m v2, m v3, Re rho, Im rho
@@ -654,19 +706,17 @@ struct NoHook {
 // hook: called by every thread right after the block barrier that ends step 1 (the
 // persistent CG finishes its block sums there instead of spending barriers of its own).
 template <int N1, int KM = 0, int RCT = 0, typename Hook = NoHook>
-__device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& S, const Fft32Lane& ffw,
-                                            const Fft32Lane& ffa, const float* __restrict__ coefT,
+__device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& S, const float* __restrict__ coefT,
                                             const float* __restrict__ UgS, int kmax, int ix, int nx, int R, int r0,
                                             int nr, int ya, int ye, const Hook& hook = Hook()) {
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
-  constexpr int NY = 32 * N1, LD = NY + 1;
+  constexpr int NY = 32 * N1, M = 2 * N1, RS = col_row(NY);
   constexpr int SC = KM > 0 ? KM : 8;              // TR slots per pass of step 2
   constexpr int RCM = RCT > 0 ? RCT : kColMaxRc;   // basis functions per block, at most
   const int km = KM > 0 ? KM : kmax;
   const int nrr = RCT > 0 ? RCT : nr;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int brev = (int)(__brev((unsigned)lane) >> 27);
   const size_t plane = (size_t)nx * NY;
   const float2* rt = S.rt;
   float2* hs = S.hs;
@@ -676,45 +726,88 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
   float* red4 = S.red4;
   float2* sin_peer = S.sin_peer;
   float* red4_peer_in = S.rin_peer;
-  // 1. h_r and its phase-encode DFT; warp w takes the pair of local r = w, w + 8: the
-  //    coefficient loads of both issue together and the voxel data is read once; the
-  //    second column waits in its own row of hs (in iy order) while the first is
-  //    transformed
-  for (int ra = warp; ra < nrr; ra += 2 * kColWarps) {
-    const int rb = ra + kColWarps;
-    const bool two = rb < nrr;
-    const float* ca = coefT + (size_t)(r0 + ra) * plane + (size_t)ix * NY;
-    const float* cbp = two ? coefT + (size_t)(r0 + rb) * plane + (size_t)ix * NY : ca;
-    float2 xa[N1];
+  // 1. h_r and its phase-encode DFT.  Warp w owns the rows rl = 2w, 2w + 1 of hs.
+  //    (a) lane (rl = 2w + lane / 16, i2 = lane mod 16) forms x[i1] = h_r(16 i1 + i2) for
+  //        i1 < M, the M-point DFT over i1 and the twiddle w^(k1 i2), and stores
+  //        Z[k1][i2] at 17 k1 + i2 of its row;
+  //    (b) lane (rl = 2w + (lane >= M), k1 = lane mod M) reads Z[k1][.], applies the
+  //        16-point FFT and, once every lane of the warp has read its inputs, stores
+  //        H_r(k1 + M k2) at k1 + M k2 (natural ky order).
+  //    Lanes without a row of their own (rl >= nr, or lane >= 2 M) compute on a clamped
+  //    row and store nothing, so the warp stays converged at its barriers.
+  const int rlast = max(nrr - 1, 0);
+  {
+    const int rl = 2 * warp + (lane >> 4), i2 = lane & 15, rlc = min(rl, rlast);
+    const float* ca = coefT + (size_t)(r0 + rlc) * plane + (size_t)ix * NY;
+    // the coefficients of all M samples are loaded together (one L2 round trip); the
+    // M-point DFT as its radix-2 step: the N1-point DFTs of the even and then of the odd
+    // samples (each formed just before its DFT), then the combination
+    float cf[M], d1[M], d2[M];
 #pragma unroll
-    for (int i1 = 0; i1 < N1; ++i1) {
-      const int iy = 32 * i1 + lane;
-      const float v0 = vox[iy], v1 = vox[NY + iy], v2 = vox[2 * NY + iy], v3 = vox[3 * NY + iy];
-      const float rr = vox[4 * NY + iy], ri = vox[5 * NY + iy];
-      const float c = ca[iy], t = fmaf(v0, ca[(size_t)R * plane + iy], v1 * ca[(size_t)2 * R * plane + iy]);
-      const float d = cbp[iy], u = fmaf(v0, cbp[(size_t)R * plane + iy], v1 * cbp[(size_t)2 * R * plane + iy]);
-      xa[i1] = make_float2(-(ri * t + v3 * c), rr * t + v2 * c);
-      if (two) hs[rb * LD + iy] = make_float2(-(ri * u + v3 * d), rr * u + v2 * d);
+    for (int i1 = 0; i1 < M; ++i1) {
+      const int iy = 16 * i1 + i2;
+      cf[i1] = ca[iy];
+      d1[i1] = ca[(size_t)R * plane + iy];
+      d2[i1] = ca[(size_t)2 * R * plane + iy];
     }
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      if (h == 1) {
-        if (!two) break;
+    float2 E[N1], O[N1];
 #pragma unroll
-        for (int i1 = 0; i1 < N1; ++i1) xa[i1] = hs[rb * LD + 32 * i1 + lane];  // this lane's own stores
-        __syncwarp();  // every lane has its inputs before any output lands in the row
+    for (int par = 0; par < 2; ++par) {
+      float2 x[N1];
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        const int i1 = 2 * i + par, iy = 16 * i1 + i2;
+        const float v0 = vox[iy], v1 = vox[NY + iy], v2 = vox[2 * NY + iy], v3 = vox[3 * NY + iy];
+        const float rr = vox[4 * NY + iy], ri = vox[5 * NY + iy];
+        const float c = cf[i1], t = fmaf(v0, d1[i1], v1 * d2[i1]);
+        x[i] = make_float2(-(ri * t + v3 * c), rr * t + v2 * c);
       }
-      float2 X[N1];
-      dft_small<N1, false>(W, xa, X);
-      const int rl = h == 0 ? ra : rb;
+      if (par == 0) dft_n1<N1, false>(W, x, E);
+      else dft_n1<N1, false>(W, x, O);
+    }
+    float2* row = hs + rl * RS;
+    const bool own = rl < nrr;
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        float2 acc = cmul(X[k1], rt[k1 * lane]);  // k1 lane <= 31 (N1 - 1) < NY
-        acc = fft32_warp(acc, ffw);
-        hs[rl * LD + k1 + N1 * brev] = acc;
+    for (int k = 0; k < N1; ++k) {
+      const float2 t = k == 0 ? O[0] : cmul(O[k], W.wm[k]);
+      const float2 ya = cadd(E[k], t), yb = csub(E[k], t);  // Y_k and Y_(k + N1)
+      const float2 za = k == 0 ? ya : cmul(ya, rt[k * i2]), zb = cmul(yb, rt[(k + N1) * i2]);  // (M - 1) 15 < NY
+      if (own) {
+        row[17 * k + i2] = za;
+        row[17 * (k + N1) + i2] = zb;
       }
     }
   }
+  __syncwarp();
+  {
+    const int rl2 = 2 * warp + (lane >= M ? 1 : 0), k1 = lane >= M ? lane - M : lane;
+    const bool act = lane < 2 * M && rl2 < nrr;
+    const float2* src = hs + min(rl2, rlast) * RS + 17 * (act ? k1 : 0);
+    float2 a[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = src[j];
+    fft16<false>(a);
+    __syncwarp();  // the rows' Z are read before H overwrites them
+    float2* row = hs + rl2 * RS + k1;
+    if (act) {
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) row[M * k2] = a[brev4(k2)];
+    }
+  }
+  // The first batch of step 2a's rows of U, loaded before the barrier so that the L2
+  // latency overlaps the wait (the register path of step 2 only)
+  constexpr int QB = SC <= 5 ? 8 : 4;  // basis functions per batch of U loads in step 2
+  const int kyt = tid;
+  const float* ub = UgS + (size_t)r0 * km * NY + kyt;
+  float u[QB][SC];
+  auto load_u = [&](int q0) {
+#pragma unroll
+    for (int b = 0; b < QB; ++b)
+#pragma unroll
+      for (int i = 0; i < SC; ++i)
+        u[b][i] = (i < km && q0 + b < nrr && kyt < NY) ? __ldg(ub + ((size_t)(q0 + b) * km + i) * NY) : 0.f;
+  };
+  if (km <= SC) load_u(0);
   __syncthreads();
   hook();
   // 2. per-ky Gram through the TR axis, thread per ky: U as UgS[r][i][ky] (the TRs of each
@@ -723,31 +816,39 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
   //    needs no block barrier, only the cluster barrier of the exchange.
   if (km <= SC) {
     // one pass over the slots: this thread's part of s stays in registers across the
-    // exchange (NY <= kColThreads: at most one line per thread)
-    const int ky = tid;
-    const float* ub = UgS + (size_t)r0 * km * NY + ky;
+    // exchange (NY <= kColThreads: at most one line per thread); U in batches of QB rows,
+    // each batch's loads issued together
+    const int ky = kyt;
     float2 acc[SC];
 #pragma unroll
     for (int i = 0; i < SC; ++i) acc[i] = make_float2(0.f, 0.f);
     //  2a. this block's part of s[i][ky] = sum_q U[q][i][ky] H_q(ky), stored into the peer's sin
-    if (ky < NY) {
-#pragma unroll 4
-      for (int q = 0; q < nrr; ++q) {
-        const float2 h = hs[q * LD + ky];
+    for (int q0 = 0; q0 < nrr; q0 += QB) {
+      if (q0 > 0) load_u(q0);
+      if (ky < NY) {
 #pragma unroll
-        for (int i = 0; i < SC; ++i) {
-          if (i < km) {
-            const float u = __ldg(ub + ((size_t)q * km + i) * NY);
-            acc[i].x = fmaf(u, h.x, acc[i].x);
-            acc[i].y = fmaf(u, h.y, acc[i].y);
+        for (int b = 0; b < QB; ++b) {
+          if (q0 + b < nrr) {
+            const float2 h = hs[(q0 + b) * RS + ky];
+#pragma unroll
+            for (int i = 0; i < SC; ++i) {
+              acc[i].x = fmaf(u[b][i], h.x, acc[i].x);
+              acc[i].y = fmaf(u[b][i], h.y, acc[i].y);
+            }
           }
         }
       }
+    }
+    if (ky < NY) {
 #pragma unroll
       for (int i = 0; i < SC; ++i)
         if (i < km) sin_peer[i * NY + ky] = acc[i];
     }
-    cl.sync();  // both parts of every s are in both blocks
+    // both parts of every s are in both blocks after the wait; the first batch of U for
+    // 2b is loaded between the arrival and the wait
+    cl.barrier_arrive();
+    load_u(0);
+    cl.barrier_wait();
     //  2b. G_r(ky) = sum_i U[r][i][ky] s[i][ky] with s the sum of the two parts
     //      (commutative: the same s in both blocks); G overwrites H_r(ky), which only this
     //      thread read
@@ -759,18 +860,22 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
           acc[i] = make_float2(acc[i].x + sb.x, acc[i].y + sb.y);
         }
       }
-#pragma unroll 4
-      for (int r = 0; r < nrr; ++r) {
-        float2 g = make_float2(0.f, 0.f);
+    }
+    for (int q0 = 0; q0 < nrr; q0 += QB) {
+      if (q0 > 0) load_u(q0);
+      if (ky < NY) {
 #pragma unroll
-        for (int i = 0; i < SC; ++i) {
-          if (i < km) {
-            const float u = __ldg(ub + ((size_t)r * km + i) * NY);
-            g.x = fmaf(u, acc[i].x, g.x);
-            g.y = fmaf(u, acc[i].y, g.y);
+        for (int b = 0; b < QB; ++b) {
+          if (q0 + b < nrr) {
+            float2 g = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < SC; ++i) {
+              g.x = fmaf(u[b][i], acc[i].x, g.x);
+              g.y = fmaf(u[b][i], acc[i].y, g.y);
+            }
+            hs[(q0 + b) * RS + ky] = g;
           }
         }
-        hs[r * LD + ky] = g;
       }
     }
   } else {
@@ -784,7 +889,7 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
         for (int i = 0; i < SC; ++i) acc[i] = make_float2(0.f, 0.f);
 #pragma unroll 4
         for (int q = 0; q < nrr; ++q) {
-          const float2 h = hs[q * LD + ky];
+          const float2 h = hs[q * RS + ky];
 #pragma unroll
           for (int i = 0; i < SC; ++i) {
             if (i0 + i < km) {
@@ -821,7 +926,7 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
         }
 #pragma unroll 4
         for (int r = 0; r < nrr; ++r) {
-          float2 g = i0 == 0 ? make_float2(0.f, 0.f) : hs[r * LD + ky];
+          float2 g = i0 == 0 ? make_float2(0.f, 0.f) : hs[r * RS + ky];
 #pragma unroll
           for (int i = 0; i < SC; ++i) {
             if (i0 + i < km) {
@@ -830,57 +935,97 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
               g.y = fmaf(u, sv[i].y, g.y);
             }
           }
-          hs[r * LD + ky] = g;
+          hs[r * RS + ky] = g;
         }
       }
     }
 
   }
   __syncthreads();  // the adjoint below reads whole rows of hs
-  // 3. adjoint phase-encode DFT
-  for (int rl = warp; rl < nrr; rl += kColWarps) {
-    float2* x = hs + rl * LD;
-    const int i2 = brev;
-    float2 z[N1];
+  // 3. adjoint phase-encode DFT on the same rows as step 1, in the reverse order (lanes
+  //    without a row compute on a clamped one and store nothing):
+  //    (a) lane (rl, k1) reads G(k1 + M k2) for k2 < 16, applies the conjugate 16-point FFT
+  //        and stores T[k1][i2] at 17 k1 + i2;
+  //    (b) lane (rl, i2) reads T[k1][i2] for k1 < M, applies the conjugate twiddle and the
+  //        conjugate M-point DFT and stores P_r(16 i1 + i2) at 16 i1 + i2.
+  {
+    const int rl2 = 2 * warp + (lane >= M ? 1 : 0), k1 = lane >= M ? lane - M : lane;
+    const bool act = lane < 2 * M && rl2 < nrr;
+    const float2* src = hs + min(rl2, rlast) * RS + (act ? k1 : 0);
+    float2 a[16];
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) z[k1] = x[k1 + N1 * lane];  // k2 = lane
-    __syncwarp();
+    for (int k2 = 0; k2 < 16; ++k2) a[k2] = src[M * k2];
+    fft16<true>(a);
+    __syncwarp();  // the rows' G are read before T overwrites them
+    float2* row = hs + rl2 * RS + 17 * k1;
+    if (act) {
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) {
-      const float2 t = fft32_warp(z[k1], ffa);  // at i2 = bitrev(lane)
-      z[k1] = cmulc(t, rt[k1 * i2]);
+      for (int j = 0; j < 16; ++j) row[j] = a[brev4(j)];
     }
-    float2 out[N1];
-    dft_small<N1, true>(W, z, out);
-#pragma unroll
-    for (int i1 = 0; i1 < N1; ++i1) x[32 * i1 + i2] = out[i1];
   }
-  __syncthreads();
-  // 4. contraction with the tangents over this block's r, one thread per iy
-  for (int iy = tid; iy < NY; iy += kColThreads) {
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    const float rhx = vox[4 * NY + iy], rhy = vox[5 * NY + iy];
-    const float* cc = coefT + (size_t)ix * NY + iy;
+  __syncwarp();
+  {
+    const int rl = 2 * warp + (lane >> 4), i2 = lane & 15;
+    const float2* src = hs + min(rl, rlast) * RS + i2;
+    float2 z[M];
+    z[0] = src[0];
 #pragma unroll
-    for (int rl = 0; rl < RCM; ++rl) {
-      if (rl < nrr) {
-        const int r = r0 + rl;
-        const float2 pv = hs[rl * LD + iy];
-        const float c = cc[(size_t)r * plane];
-        const float t1 = cc[(size_t)(R + r) * plane], t2 = cc[(size_t)(2 * R + r) * plane];
-        const float imcp = rhx * pv.y - rhy * pv.x;  // Im(conj(rho) P)
-        a0 = fmaf(t1, imcp, a0);
-        a1 = fmaf(t2, imcp, a1);
-        a2 = fmaf(c, pv.y, a2);
-        a3 = fmaf(-c, pv.x, a3);
+    for (int q = 1; q < M; ++q) z[q] = cmulc(src[17 * q], rt[q * i2]);
+    __syncwarp();  // the rows' T are read before P overwrites them
+    float2 out[M];
+    dft_m<N1, true>(W, z, out);
+    float2* row = hs + rl * RS + i2;
+    if (rl < nrr) {
+#pragma unroll
+      for (int i1 = 0; i1 < M; ++i1) row[16 * i1] = out[i1];
+    }
+  }
+  // 4. contraction with the tangents over this block's r, one thread per iy (NY <=
+  //    kColThreads), the coefficients in batches of 8 r whose loads issue together; the
+  //    first batch is loaded before the barrier that ends step 3
+  {
+    constexpr int RB = 8;
+    const int iy = tid;
+    const float* cc = coefT + (size_t)ix * NY + iy;
+    float c4[RB], e1[RB], e2[RB];
+    auto load_c = [&](int rb0) {
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        const bool in = rb0 + b < nrr && iy < NY;
+        const int r = r0 + rb0 + b;
+        c4[b] = in ? cc[(size_t)r * plane] : 0.f;
+        e1[b] = in ? cc[(size_t)(R + r) * plane] : 0.f;
+        e2[b] = in ? cc[(size_t)(2 * R + r) * plane] : 0.f;
+      }
+    };
+    load_c(0);
+    __syncthreads();
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const float rhx = iy < NY ? vox[4 * NY + iy] : 0.f, rhy = iy < NY ? vox[5 * NY + iy] : 0.f;
+    for (int rb0 = 0; rb0 < RCM; rb0 += RB) {
+      if (rb0 > 0) load_c(rb0);
+      if (iy < NY) {
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+          if (rb0 + b < nrr) {
+            const float2 pv = hs[(rb0 + b) * RS + iy];
+            const float imcp = rhx * pv.y - rhy * pv.x;  // Im(conj(rho) P)
+            a0 = fmaf(e1[b], imcp, a0);
+            a1 = fmaf(e2[b], imcp, a1);
+            a2 = fmaf(c4[b], pv.y, a2);
+            a3 = fmaf(-c4[b], pv.x, a3);
+          }
+        }
       }
     }
     // the part for this block's half of the column stays here, the rest goes to the peer
-    float* dst = (iy >= ya && iy < ye) ? red4 : red4_peer_in;
-    dst[iy] = a0;
-    dst[NY + iy] = a1;
-    dst[2 * NY + iy] = a2;
-    dst[3 * NY + iy] = a3;
+    if (iy < NY) {
+      float* dst = (iy >= ya && iy < ye) ? red4 : red4_peer_in;
+      dst[iy] = a0;
+      dst[NY + iy] = a1;
+      dst[2 * NY + iy] = a2;
+      dst[3 * NY + iy] = a3;
+    }
   }
   cl.sync();  // the peer's part of this block's half has arrived
 }
@@ -897,22 +1042,21 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
   const int crank = (int)cl.block_rank(), peer = crank ^ 1;
-  constexpr int NY = 32 * N1, LD = NY + 1;  // the launch passes ny == NY
+  constexpr int NY = 32 * N1, RS = col_row(NY);  // the launch passes ny == NY
   const int RC = (R + 1) / 2, r0 = crank * RC, nr = min(R, r0 + RC) - r0;
   extern __shared__ float2 fsm[];
   float2* rt = fsm;                                      // [NY] w^k
-  float2* hs = rt + NY;                                  // [RC][NY + 1]: H, then G, then P
-  float2* sbuf = hs + RC * LD;                           // [kmax][NY] this block's part of s, then s
+  float2* hs = rt + NY;                                  // [RC][RS] rows of the DFTs
+  float2* sbuf = hs + RC * RS;                           // [kmax][NY] this block's part of s, then s
   float2* sin = sbuf + sbuf_slots(kmax) * NY;            // [kmax][NY] the peer's part (written by it)
   float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // [6][NY]: v0, v1, m v2, m v3, Re rho, Im rho
   float* red4 = vox + 6 * NY;                            // [4][NY] contraction over this block's r
   float* rin = red4 + 4 * NY;                            // [4][NY] the peer's contraction (written by it)
   const ColShared S = {rt, hs, sbuf, sin, vox, red4, rin, cl.map_shared_rank(sin, peer), cl.map_shared_rank(rin, peer)};
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
   const int hy = (NY + 1) / 2, ya = crank * hy, ye = min(NY, ya + hy);  // this block's half of iy
   for (int e = tid; e < NY; e += kColThreads) rt[e] = roots[e];  // plan constants: before the wait
   cl.sync();  // both blocks are running before either stores into the other's shared memory
-  const Fft32Lane ffw = fft32_lane<false>(rt, N1, lane), ffa = fft32_lane<true>(rt, N1, lane);
   red::pdl_wait();  // v, rho, the coefficients and the gate come from earlier launches
   // the gate is written by earlier launches only: both blocks of a cluster take the same
   // branch, so every cluster barrier below is reached by both
@@ -949,7 +1093,7 @@ lr_jhjv_column_kernel(const __grid_constant__ DftSmall W, const float* __restric
       }
       continue;
     }
-    column_core<N1, KM, RCT>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ye);
+    column_core<N1, KM, RCT>(W, S, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ye);
     for (int iy = ya + tid; iy < ye; iy += kColThreads) {
       const int j = iy * nx + ix;
       const float m = maskf[j] * scale;
@@ -1042,6 +1186,31 @@ __device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
   return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
+// Products and quotients of float-float values for the CG scalars (GB300 issues float64
+// at a small fraction of the float32 rate, and a float64 division on one thread sat on the
+// critical path of every iteration): the exact product of two floats by one fused
+// multiply-add (Dekker's TwoProduct), Fast2Sum renormalisation, and a quotient with one
+// correction step (q1 = a / b in float, then q2 from the float-float remainder a - q1 b).
+__device__ __forceinline__ FF ff_fast2sum(float s, float e) {  // |s| >= |e|
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);  // the exact rounding error of a.hi b.hi
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return ff_fast2sum(p, e);
+}
+
+__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, FF{-b.hi, -b.lo}); }
+
+__device__ __forceinline__ FF ff_div(FF a, FF b) {
+  const float q1 = a.hi / b.hi;
+  const FF r = ff_sub(a, ff_mul(b, FF{q1, 0.f}));
+  return ff_fast2sum(q1, r.hi / b.hi);
+}
+
 // Sums of NV values over the block, valid in thread 0 (two block barriers); ws holds
 // NV kColWarps values.
 template <int NV>
@@ -1113,7 +1282,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // part[k G .. (k + 1) G) in block order for each k < NV; the sums are valid in thread 0
 // and the same in every block.  Returns false in a block whose wait ran out.
 template <int NV>
-__device__ bool grid_wait_sums(const FF* part, const unsigned* bar, unsigned target, int* err, FF* ws,
+__device__ __forceinline__ bool grid_wait_sums(const FF* part, const unsigned* bar, unsigned target, int* err, FF* ws,
                                double (&out)[NV]) {
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
@@ -1157,6 +1326,60 @@ __device__ bool grid_wait_sums(const FF* part, const unsigned* bar, unsigned tar
   return s_ok != 0;
 }
 
+// The same wait and sums for warp 0 alone (no block barrier): lane 0 waits, the warp adds
+// the partials in the same order as above (lane l takes blocks l, l + 32, ...; then the
+// butterfly of commutative float-float additions) and every lane of warp 0 holds the sums,
+// the same in every block.  Returns false (in every lane) where the wait ran out.
+template <int NV>
+__device__ __forceinline__ bool grid_wait_sums_w0(const FF* part, const unsigned* bar, unsigned target, int* err,
+                                                  FF (&out)[NV]) {
+  const int lane = threadIdx.x & 31;
+  int ok = 1;
+  if (lane == 0 && ld_acquire(bar) < target) {
+    const uint64_t t0 = col_global_ns();
+    uint32_t spins = 0, ns = 32;
+    while (ld_acquire(bar) < target) {
+      __nanosleep(ns);
+      if (ns < 256) ns <<= 1;
+      if ((++spins & 63u) == 0 && col_global_ns() - t0 > kGridWaitNs) {
+        atomicExch(err, 1);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  __syncwarp();  // lane 0's acquire orders the other lanes' reads after it
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  const int G = gridDim.x;
+  const float2* vp = reinterpret_cast<const float2*>(part);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    // G <= 2 kColThreads = 512 (checked at launch): 16 blocks per lane, loaded together
+    float2 t[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int i = lane + 32 * j;
+      t[j] = i < G ? __ldcg(vp + (size_t)k * G + i) : make_float2(0.f, 0.f);
+    }
+    FF f[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) f[j] = FF{t[j].x, t[j].y};
+    // pairwise: four dependent additions instead of sixteen
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f[j] = ff_add(f[j], f[j + 8]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) f[j] = ff_add(f[j], f[j + 4]);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) f[j] = ff_add(f[j], f[j + 2]);
+    f[0] = ff_add(f[0], f[1]);
+    FF acc = f[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = ff_add(acc, ff_shfl_xor(acc, o));
+    out[k] = acc;
+  }
+  return ok != 0;
+}
+
 size_t cg_column_smem_bytes(int ny, int R, int kmax) {
   const int hy = (ny + 1) / 2;
   return column_smem_bytes(ny, R, kmax) + sizeof(float) * ((size_t)ny + 20 * (size_t)hy);
@@ -1172,12 +1395,12 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
   const int crank = (int)cl.block_rank(), peer = crank ^ 1;
-  constexpr int NY = 32 * N1, LD = NY + 1, HY = (NY + 1) / 2;
+  constexpr int NY = 32 * N1, RS = col_row(NY), HY = (NY + 1) / 2;
   const int RC = (R + 1) / 2, r0 = crank * RC, nr = min(R, r0 + RC) - r0;
   extern __shared__ float2 fsm[];
   float2* rt = fsm;
   float2* hs = rt + NY;
-  float2* sbuf = hs + RC * LD;
+  float2* sbuf = hs + RC * RS;
   float2* sin = sbuf + sbuf_slots(kmax) * NY;
   float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // rows 0..3: the product's input
   float* red4 = vox + 6 * NY;
@@ -1191,7 +1414,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   __shared__ FF ws[2 * kColWarps];
   __shared__ float s_al, s_be;
   __shared__ int s_apply;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
   const int ix = blockIdx.x >> 1;  // one column per cluster
   const int G = gridDim.x;
   const int ya = crank * HY, nh = min(NY, ya + HY) - ya;  // this block's half of iy: ya .. ya + nh
@@ -1202,7 +1425,6 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   float* const cx = cgv + 16 * HY;
   for (int e = tid; e < NY; e += kColThreads) rt[e] = roots[e];
   cl.sync();
-  const Fft32Lane ffw = fft32_lane<false>(rt, N1, lane), ffa = fft32_lane<true>(rt, N1, lane);
 
   // rho and the mask of the whole column; r = rhs and p = s = z = x = 0 on this block's
   // half; the product's input is r (rows 2, 3 masked)
@@ -1236,7 +1458,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   cl.sync();
 
   // w_0 = B r_0 (masked, like every product) becomes the product's input
-  if (inside) column_core<N1, KM, RCT>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+  if (inside) column_core<N1, KM, RCT>(W, S, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
   if (tid < nh) {
     const int iy = ya + tid;
     const float m = mk[iy] * scale;
@@ -1260,9 +1482,12 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
     }
   }
   // pq_prev = p.Bp of the previous iteration: beta gamma / alpha_prev = beta^2 pq_prev
-  double gam_prev = 0.0, pq_prev = 0.0;
+  // (float-float, thread 0)
+  FF gam_prev{0.f, 0.f}, pq_prev{0.f, 0.f};
   bool frozen = false;
   int applied = 0;  // iterations that moved x (thread 0)
+  __shared__ int s_okb;
+  __shared__ FF s_dg[2];  // this iteration's delta and gamma (for the record)
   for (int it = 0; it < iters; ++it) {
     FF* pk = reinterpret_cast<FF*>(part) + (size_t)(it & 1) * 2 * G;
     // q = B w while the other blocks arrive (not needed in the last iteration)
@@ -1281,44 +1506,51 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
           if (arrive) grid_arrive<2>(pk, bar, b);
         }
       };
-      column_core<N1, KM, RCT>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh, finish_and_arrive);
+      column_core<N1, KM, RCT>(W, S, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh, finish_and_arrive);
     } else {
       block_sums<2>(v, ws);
       if (arrive) grid_arrive<2>(pk, bar, v);
     }
-    double sums2[2];
-    const bool ok = grid_wait_sums<2>(pk, bar, (unsigned)G * (unsigned)(it + 1), err, ws, sums2);
-    const double delta = sums2[0], gamma = sums2[1];
-    if (tid == 0) {
-      int apply = 0;
-      float al = 0.f, be = 0.f;
-      if (ok) {
-        if (blockIdx.x == 0) {
-          sums[2 * it] = delta;
-          sums[2 * it + 1] = gamma;
+    // warp 0 waits, sums and decides; the other warps go straight to the block barrier
+    if ((tid >> 5) == 0) {
+      FF sums2[2];
+      const bool okw = grid_wait_sums_w0<2>(pk, bar, (unsigned)G * (unsigned)(it + 1), err, sums2);
+      const FF delta = sums2[0], gamma = sums2[1];
+      if (tid == 0) {
+        s_dg[0] = delta;
+        s_dg[1] = gamma;
+        int apply = 0;
+        float al = 0.f, be = 0.f;
+        if (okw) {
+          FF beta{0.f, 0.f}, pq = delta;
+          if (it > 0) {
+            beta = ff_div(gamma, gam_prev);
+            pq = ff_sub(delta, ff_mul(ff_mul(beta, beta), pq_prev));
+          }
+          apply = !frozen && pq.hi > 0.f && gamma.hi > 0.f;
+          if (apply) {
+            al = ff_div(gamma, pq).hi;
+            be = beta.hi;
+            gam_prev = gamma;
+            pq_prev = pq;
+            ++applied;
+          } else {
+            frozen = true;
+          }
         }
-        double beta = 0.0, pq = delta;
-        if (it > 0) {
-          beta = gamma / gam_prev;
-          pq = delta - beta * beta * pq_prev;
-        }
-        apply = !frozen && pq > 0.0 && gamma > 0.0;
-        if (apply) {
-          al = (float)(gamma / pq);
-          be = (float)beta;
-          gam_prev = gamma;
-          pq_prev = pq;
-          ++applied;
-        } else {
-          frozen = true;
-        }
+        s_apply = apply;
+        s_al = al;
+        s_be = be;
+        s_okb = okw;
+        ok_peer_remote[it & 1] = okw;
       }
-      s_apply = apply;
-      s_al = al;
-      s_be = be;
-      ok_peer_remote[it & 1] = ok;
     }
     __syncthreads();
+    const bool ok = s_okb != 0;
+    if (tid == kColThreads - 1 && ok && blockIdx.x == 0) {  // the record, off warp 0's path
+      sums[2 * it] = (double)s_dg[0].hi + (double)s_dg[0].lo;
+      sums[2 * it + 1] = (double)s_dg[1].hi + (double)s_dg[1].lo;
+    }
     if (s_apply && tid < nh) {
       const int iy = ya + tid;
       const float al = s_al, be = s_be, m = prod ? mk[iy] * scale : 0.f;
@@ -1402,13 +1634,13 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
   const int crank = (int)cl.block_rank(), peer = crank ^ 1;
-  constexpr int NY = 32 * N1, LD = NY + 1, HY = (NY + 1) / 2;
+  constexpr int NY = 32 * N1, RS = col_row(NY), HY = (NY + 1) / 2;
   constexpr int NP = 8;  // partials per block and grid wait, at most
   const int RC = (R + 1) / 2, r0 = crank * RC, nr = min(R, r0 + RC) - r0;
   extern __shared__ float2 fsm[];
   float2* rt = fsm;
   float2* hs = rt + NY;
-  float2* sbuf = hs + RC * LD;
+  float2* sbuf = hs + RC * RS;
   float2* sin = sbuf + sbuf_slots(kmax) * NY;
   float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // rows 0..3: the product's input
   float* red4 = vox + 6 * NY;
@@ -1430,7 +1662,7 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
   __shared__ int lsi[I_COUNT];
   __shared__ int s_ok, s_go, s_cont, s_prod;
   __shared__ float s_c, s_beta;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
   const int ix = blockIdx.x >> 1;  // one column per cluster
   const int G = gridDim.x;
   const int ya = crank * HY, nh = min(NY, ya + HY) - ya;  // this block's half of iy: ya .. ya + nh
@@ -1439,7 +1671,6 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
   unsigned waits = 0;  // grid waits passed; wait n uses part[(n mod 2) NP G ..]
   for (int e = tid; e < NY; e += kColThreads) rt[e] = roots[e];
   cl.sync();  // both blocks run (before any store into the peer) and hold the roots
-  const Fft32Lane ffw = fft32_lane<false>(rt, N1, lane), ffa = fft32_lane<true>(rt, N1, lane);
 
   // rho and the mask of the whole column; res = g, dir = -g, z = 0 on this block's half;
   // the product's input is dir (rows 2, 3 masked)
@@ -1470,7 +1701,7 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
   }
   cl.sync();  // dir of both halves is in both blocks
   // q = B dir_0, then g.g and dir.q
-  if (inside) column_core<N1, KM, RCT>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+  if (inside) column_core<N1, KM, RCT>(W, S, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
   {
     float sg = 0.f, sq = 0.f;
     if (own) {
@@ -1558,7 +1789,7 @@ lr_steihaug_columns_kernel(const __grid_constant__ DftSmall W, const float* __re
     const bool prod = inside && s_prod;
     float b[3] = {0.f, 0.f, 0.f};
     if (prod) {
-      column_core<N1, KM, RCT>(W, S, ffw, ffa, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+      column_core<N1, KM, RCT>(W, S, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
       if (own) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -1831,12 +2062,17 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
       L->fft_y && R <= 2 * kColMaxRc && column_smem_bytes(ny, R, L->ky_count_max) <= (size_t)L->smem_optin;
   if (L->fft_y) {
     const int n1 = ny / 32;
-    for (int a = 0; a < 8; ++a)
-      for (int b = 0; b < 8; ++b) {
-        const double ang = -2.0 * M_PI * (double)((a * b) % n1) / (double)n1;
-        L->dft_small.w[a][b] = (a < n1 && b < n1) ? make_float2((float)std::cos(ang), (float)std::sin(ang))
-                                                  : make_float2(0.f, 0.f);
+    std::memset(&L->dft_small, 0, sizeof(DftSmall));
+    for (int k = 1; 2 * k < n1; ++k)
+      for (int i = 1; 2 * i < n1; ++i) {
+        const double ang = 2.0 * M_PI * (double)((k * i) % n1) / (double)n1;
+        L->dft_small.c[k - 1][i - 1] = (float)std::cos(ang);
+        L->dft_small.s[k - 1][i - 1] = (float)std::sin(ang);
       }
+    for (int k = 0; k < n1; ++k) {
+      const double ang = -2.0 * M_PI * (double)k / (double)(2 * n1);
+      L->dft_small.wm[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
   }
   std::vector<float> M((size_t)ny * R * R, 0.f);
   for (int k = 0; k < ny; ++k)

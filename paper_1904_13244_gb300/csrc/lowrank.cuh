@@ -9,11 +9,14 @@ namespace mrstat {
 
 constexpr int kMaxRank = 32;
 
-// The N1-point DFT matrix wN1^(k1 i1) = w^(32 k1 i1) (N1 <= 8) of the factorised
-// phase-encode DFT, passed to the kernel by value so that its entries are constant-bank
-// operands of the multiply-adds.
+// Constants of the factorised phase-encode DFT (ny = 32 N1, N1 <= 8), passed to the
+// kernels by value so that they are constant-bank operands of the multiply-adds:
+// c[k-1][i-1] = cos(2 pi k i / N1) and s[k-1][i-1] = sin(2 pi k i / N1) for
+// 0 < k, i < N1 / 2 (the N1-point DFT), wm[k] = exp(-2 pi i k / (2 N1)) for k < N1 (the
+// radix-2 step to 2 N1 points).
 struct DftSmall {
-  float2 w[8][8];
+  float c[4][4], s[4][4];
+  float2 wm[8];
 };
 
 struct LowRank {
@@ -49,7 +52,7 @@ struct LowRank {
   bool active = false;             // the plan's current linearisation is this low-rank one
   bool full_readout = false;       // nkx == nx: J^H J v skips the readout DFT pair
   bool fft_y = false;              // ... and ny = 32 N1 (N1 <= 8): the factorised phase-encode DFT applies
-  DftSmall dft_small;              // the N1-point DFT matrix of the factorised path
+  DftSmall dft_small;              // constants of the factorised phase-encode DFT
   bool column_path = false;        // fft_y and the column kernel's shared memory fits
   int sms = 1;                     // SM count (grid of the Gram kernel)
 };
