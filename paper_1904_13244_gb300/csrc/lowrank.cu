@@ -1206,9 +1206,11 @@ __device__ __forceinline__ FF ff_mul(FF a, FF b) {
 __device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, FF{-b.hi, -b.lo}); }
 
 __device__ __forceinline__ FF ff_div(FF a, FF b) {
-  const float q1 = a.hi / b.hi;
+  // q1 needs no correct rounding (the remainder below is exact for any q1 near a / b), so
+  // the fast approximate division serves; q2 corrects it
+  const float q1 = __fdividef(a.hi, b.hi);
   const FF r = ff_sub(a, ff_mul(b, FF{q1, 0.f}));
-  return ff_fast2sum(q1, r.hi / b.hi);
+  return ff_fast2sum(q1, __fdividef(r.hi, b.hi));
 }
 
 // Sums of NV values over the block, valid in thread 0 (two block barriers); ws holds
@@ -1469,18 +1471,24 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
       vox_peer[k * NY + iy] = wv;
     }
   }
+  // the thread's parts of delta = <w, r> and gamma = <r, r> (formed with every update, on
+  // the thread's own elements) and their warp sums, which warp 0 finishes after the
+  // cluster barrier below
+  {
+    float sd = 0.f, sg = 0.f;
+    if (tid < nh) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float r = cr[k * HY + tid];
+        sd = fmaf(r, vox[k * NY + ya + tid], sd);
+        sg = fmaf(r, r, sg);
+      }
+    }
+    FF v[2] = {{sd, 0.f}, {sg, 0.f}};
+    warp_partials<2>(v, ws);
+  }
   cl.sync();
 
-  // the thread's parts of delta = <w, r> and gamma = <r, r> (formed with every update)
-  float sd = 0.f, sg = 0.f;
-  if (tid < nh) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float r = cr[k * HY + tid];
-      sd = fmaf(r, vox[k * NY + ya + tid], sd);
-      sg = fmaf(r, r, sg);
-    }
-  }
   // pq_prev = p.Bp of the previous iteration: beta gamma / alpha_prev = beta^2 pq_prev
   // (float-float, thread 0)
   FF gam_prev{0.f, 0.f}, pq_prev{0.f, 0.f};
@@ -1492,25 +1500,17 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
     FF* pk = reinterpret_cast<FF*>(part) + (size_t)(it & 1) * 2 * G;
     // q = B w while the other blocks arrive (not needed in the last iteration)
     const bool prod = inside && it + 1 < iters;
-    // the block's parts of delta and gamma, then arrive (no wait); a block named by the
-    // test hook withholds its first arrival, and every wait runs out.  With a product the
-    // warps' sums are finished by warp 0 after the product's first block barrier.
+    // warp 0 finishes the block's parts of delta and gamma (the warps' sums, written before
+    // the last cluster barrier) and arrives, before the product: the other blocks' waits
+    // end as early as possible.  A block named by the test hook withholds its first
+    // arrival, and every wait runs out.
     const bool arrive = it > 0 || (int)blockIdx.x != stall_block;
-    FF v[2] = {{sd, 0.f}, {sg, 0.f}};
-    if (prod) {
-      warp_partials<2>(v, ws);
-      auto finish_and_arrive = [&]() {
-        if ((tid >> 5) == 0) {
-          FF b[2];
-          warp_finish<2>(b, ws);
-          if (arrive) grid_arrive<2>(pk, bar, b);
-        }
-      };
-      column_core<N1, KM, RCT>(W, S, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh, finish_and_arrive);
-    } else {
-      block_sums<2>(v, ws);
-      if (arrive) grid_arrive<2>(pk, bar, v);
+    if ((tid >> 5) == 0) {
+      FF b[2];
+      warp_finish<2>(b, ws);
+      if (arrive) grid_arrive<2>(pk, bar, b);
     }
+    if (prod) column_core<N1, KM, RCT>(W, S, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
     // warp 0 waits, sums and decides; the other warps go straight to the block barrier
     if ((tid >> 5) == 0) {
       FF sums2[2];
@@ -1572,16 +1572,19 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
         vox_peer[k * NY + iy] = wn;
       }
     }
-    // the next iteration's parts from r and w as they now stand
-    sd = 0.f;
-    sg = 0.f;
-    if (tid < nh) {
+    // the next iteration's parts from r and w as they now stand, summed over each warp
+    {
+      float sd = 0.f, sg = 0.f;
+      if (tid < nh) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float r = cr[k * HY + tid];
-        sd = fmaf(r, vox[k * NY + ya + tid], sd);
-        sg = fmaf(r, r, sg);
+        for (int k = 0; k < 4; ++k) {
+          const float r = cr[k * HY + tid];
+          sd = fmaf(r, vox[k * NY + ya + tid], sd);
+          sg = fmaf(r, r, sg);
+        }
       }
+      FF v[2] = {{sd, 0.f}, {sg, 0.f}};
+      warp_partials<2>(v, ws);
     }
     cl.sync();  // the new w of both halves is in both blocks; the peer's flag has arrived
     // both blocks of the cluster leave together; the slot is written again only after the
