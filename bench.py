@@ -44,6 +44,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import math
 import json
 import os
 import subprocess
@@ -69,8 +70,8 @@ NCU_TRAFFIC = {
     ("xdft", "0728f575d9d96a3d"): 13670656.0,
     ("xdft_adj", "0728f575d9d96a3d"): 13668608.0,
     # profiles/lr_cg_columns_kernel_brain224.md: one persistent CG launch of 30 products
-    # read 20 977 920 B and wrote 47 360 B (caches flushed before it), per product
-    ("jhw_dot", "ef415ea5c30e16ab"): (20977920.0 + 47360.0) / 30,
+    # read 20 934 656 B and wrote 2 816 B (caches flushed before it), per product
+    ("jhw_dot", "9208322f10858cd6"): (20934656.0 + 2816.0) / 30,
     # profiles/rc_product_kernel_brain224.md: one recompute J^H J v read 12 698 624 B
     ("jhw_dot_rc", "43b010ca1597d1da"): 12698624.0,
 }
@@ -991,11 +992,12 @@ def main():
     fft_y = full_readout and ny % 32 == 0 and ny // 32 <= 8
     if lowrank_like and fft_y and max_trs_per_ky <= 8:
         # the whole product in one kernel per image column (FP32 CUDA cores): count its
-        # arithmetic (h, forward and adjoint factorised DFT, Gram through the TR axis,
-        # contraction) against the FP32-pipe peak; its algorithmic bytes are the
-        # coefficients, v, rho, mask in and g out
-        n1 = ny // 32
-        col_flops = nx * (R * ny * 20 + 2 * R * (256 * n1 * n1 + 992 * n1) + 8 * ntr * R)
+        # arithmetic against the FP32-pipe peak: h and the contraction (20 flops per
+        # basis function and voxel), the forward and adjoint phase-encode DFTs at the
+        # conventional 5 N log2 N flops of a complex N-point FFT (independent of how the
+        # kernel factorises them), the Gram through the TR axis (8 per basis function and
+        # TR); its algorithmic bytes are the coefficients, v, rho, mask in and g out
+        col_flops = nx * (R * ny * 20 + 2 * R * 5 * ny * math.log2(ny) + 8 * ntr * R)
         col_bytes = nv * (12 * R + 16 + 8 + 4 + 16)
         work = {"jhw_dot": (col_flops, "alu")}
         column_bytes = col_bytes
