@@ -41,8 +41,7 @@ struct Plan {
   float* phi = nullptr;     // [ntr_pad] signed flip (radians)
   // slice profile (mrstat_set_slice_profile): 0 isochromats = hard pulses
   int slice_iso = 0, slice_sub = 0;
-  float* slice_w = nullptr;      // [64] sub-pulse weights
-  float2* slice_prec = nullptr;  // [64] (cos, sin) of beta_k at [k] and of -n_sub/2 beta_k at [32 + k]
+  float* slice_rot = nullptr;    // [ntr_pad][32][9] composed pulse of each (TR, isochromat), 3 x 3 column-major
   int* kyi = nullptr;       // [ntr_pad] ky mod ny in [0, ny)
   int* ky_ptr = nullptr;    // [ny + 1] TRs of each ky (CSR over ky_tr)
   int* ky_tr = nullptr;     // [ntr] TR indices grouped by ky, ascending within a ky

@@ -40,7 +40,7 @@ namespace {
 
 void free_plan(Plan* p) {
   if (p == nullptr) return;
-  void* ptrs[] = {p->slice_w, p->slice_prec, p->cs, p->phi, p->kyi, p->ky_ptr, p->ky_tr, p->roots, p->ft, p->fh, p->D, p->rho, p->maskf,
+  void* ptrs[] = {p->slice_rot, p->cs, p->phi, p->kyi, p->ky_ptr, p->ky_tr, p->roots, p->ft, p->fh, p->D, p->rho, p->maskf,
                   p->dfwd, p->cf, p->A, p->wt, p->red, p->ticket, p->cg_r, p->cg_p, p->cg_q, p->cg_w, p->cg_bar,
                   p->cg_jv, p->cg_s, p->cg_frozen, p->D2, p->rho2, p->gn_g, p->gn_z, p->gn_res,
                   p->gn_dir, p->gn_q, p->gn_alpha, p->gn_trial, p->gn_s, p->gn_r, p->gn_st,

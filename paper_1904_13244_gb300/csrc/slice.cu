@@ -13,10 +13,11 @@
 //
 // One lane per isochromat (n_iso a power of two <= 32, 32 / n_iso voxels per warp), the
 // whole 3-vector state and its ln T1 / ln T2 tangents in registers.  The pulse of a
-// (TR, isochromat) pair is the same for every voxel, so each block composes it once per
-// chunk of TRs into a 3 x 3 matrix in shared memory (columns: the basis vectors pushed
-// through pre-winder, sub-steps and rewinder) and its lanes apply it; the per-voxel sum
-// over the isochromats is a segmented shuffle reduction, written as TR quads like K1.
+// (TR, isochromat) pair does not depend on the voxel: mrstat_set_slice_profile composes
+// each one once, in float64 on the host, into a 3 x 3 matrix (columns: the basis vectors
+// pushed through pre-winder, sub-steps and rewinder); each block stages a chunk of TRs'
+// matrices in shared memory and its lanes apply them; the per-voxel sum over the
+// isochromats is a segmented shuffle reduction, written as TR quads like K1.
 #include "internal.cuh"
 
 namespace mrstat {
@@ -28,11 +29,9 @@ constexpr int kSliceMaxSub = 64;
 
 __global__ void __launch_bounds__(kSliceThreads)
 bloch_slice_kernel(const float* __restrict__ alpha, const uint8_t* __restrict__ mask,
-                   const float* __restrict__ phi, const float* __restrict__ wsub, const float2* __restrict__ prec,
-                   int n_iso, int log2_iso, int n_sub, int nv, int nq, float te, float tb, float m0z, int nch,
-                   float4* __restrict__ D) {
-  __shared__ float rot[kSliceChunk * 32 * 9];        // [TR in chunk][isochromat][3 x 3, column-major]
-  __shared__ float2 cs[kSliceChunk * kSliceMaxSub];  // cos / sin of each sub-step's angle
+                   const float* __restrict__ rotg, int n_iso, int log2_iso, int nv, int nq, float te, float tb,
+                   float m0z, int nch, float4* __restrict__ D) {
+  __shared__ float rot[kSliceChunk * 32 * 9];  // [TR in chunk][isochromat][3 x 3, column-major]
   const int tid = threadIdx.x, lane = tid & 31;
   const int k = lane & (n_iso - 1);                              // this lane's isochromat
   const int j = ((blockIdx.x * kSliceThreads + tid) >> 5) * (32 >> log2_iso) + (lane >> log2_iso);
@@ -58,50 +57,16 @@ bloch_slice_kernel(const float* __restrict__ alpha, const uint8_t* __restrict__ 
 
   for (int n0 = 0; n0 < ntr4; n0 += kSliceChunk) {
     __syncthreads();  // the previous chunk's matrices are no longer read
-    // sub-step angles of the chunk's TRs (padded TRs turn by zero)
-    for (int e = tid; e < kSliceChunk * n_sub; e += kSliceThreads) {
-      const int nn = e / n_sub, s = e - nn * n_sub;
-      const int n = n0 + nn;
-      const float ang = n < ntr4 ? __ldg(phi + n) * __ldg(wsub + s) : 0.f;
-      float sn, cn;
-      sincosf(ang, &sn, &cn);
-      cs[e] = make_float2(cn, sn);
-    }
-    __syncthreads();
-    // compose the pulse of each (TR, isochromat) of the chunk: thread e < kSliceChunk n_iso
-    if (tid < kSliceChunk * n_iso) {
-      const int nn = tid >> log2_iso, kk = tid & (n_iso - 1);
-      const float2 pb = prec[kk], ph = prec[32 + kk];  // (cos, sin) of beta_k and of -n_sub/2 beta_k
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float x = c == 0 ? 1.f : 0.f, y = c == 1 ? 1.f : 0.f, z = c == 2 ? 1.f : 0.f;
-        float t = ph.x * x - ph.y * y;  // pre-winder
-        y = ph.y * x + ph.x * y;
-        x = t;
-        for (int s = 0; s < n_sub; ++s) {
-          const float2 r = cs[nn * n_sub + s];
-          t = r.x * y + r.y * z;  // RF sub-pulse (same convention as K1)
-          z = r.x * z - r.y * y;
-          y = t;
-          t = pb.x * x - pb.y * y;  // gradient precession
-          y = pb.y * x + pb.x * y;
-          x = t;
-        }
-        t = ph.x * x - ph.y * y;  // rewinder
-        y = ph.y * x + ph.x * y;
-        x = t;
-        float* R = rot + (nn * 32 + kk) * 9 + 3 * c;
-        R[0] = x;
-        R[1] = y;
-        R[2] = z;
-      }
-    }
+    // the chunk's composed pulses (TRs past the train are never applied)
+    const int nrot = min(kSliceChunk, ntr4 - n0) * 32 * 9;
+    const float* src = rotg + (size_t)n0 * 32 * 9;
+    for (int e = tid; e < nrot; e += kSliceThreads) rot[e] = __ldg(src + e);
     __syncthreads();
     for (int nq4 = 0; nq4 < kSliceChunk; nq4 += 4) {
       if (n0 + nq4 >= ntr4) break;  // ntr4 and the quads are multiples of 4
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int nn = nq4 + u, n = n0 + nn;
+        const int nn = nq4 + u;
         const float* R = rot + (nn * 32 + k) * 9;  // columns R[0..2], R[3..5], R[6..8]
         float r[9];
 #pragma unroll
@@ -172,9 +137,8 @@ cudaError_t launch_bloch_slice(const Plan& p, const float* alpha, const uint8_t*
   const float te = (float)p.te_ms, tb = (float)(p.tr_ms - p.te_ms);
   int log2_iso = 0;
   while ((1 << log2_iso) < p.slice_iso) ++log2_iso;
-  bloch_slice_kernel<<<blocks, kSliceThreads, 0, st>>>(alpha, mask, p.phi, p.slice_w, p.slice_prec, p.slice_iso,
-                                                      log2_iso, p.slice_sub, p.nv, p.nq, te, tb,
-                                                      p.inversion ? -1.f : 1.f, nch, D);
+  bloch_slice_kernel<<<blocks, kSliceThreads, 0, st>>>(alpha, mask, p.slice_rot, p.slice_iso, log2_iso, p.nv,
+                                                      p.nq, te, tb, p.inversion ? -1.f : 1.f, nch, D);
   return cudaGetLastError();
 }
 
@@ -200,8 +164,7 @@ int mrstat_set_slice_profile(mrstat_plan* plan, const mrstat_slice_profile* prof
     return fail(MRSTAT_ERR_INVALID_ARG, "slice profile: n_iso a power of two in 1..32, n_sub in 1..%d, "
                                         "sigma > 0, extent > 0", kSliceMaxSub);
   if (p->npar != 4) return fail(MRSTAT_ERR_UNSUPPORTED, "the slice-profile model has no B1 tangent");
-  // Gaussian sub-pulse weights (sum 1) and the per-isochromat precession factors, in
-  // float64 and rounded once
+  // Gaussian sub-pulse weights (sum 1), in float64
   std::vector<double> w(ns);
   double sum = 0.0;
   for (int s = 0; s < ns; ++s) {
@@ -209,20 +172,44 @@ int mrstat_set_slice_profile(mrstat_plan* plan, const mrstat_slice_profile* prof
     w[s] = std::exp(-x * x / (2.0 * prof->sigma * prof->sigma));
     sum += w[s];
   }
-  std::vector<float> wf(kSliceMaxSub, 0.f);
-  for (int s = 0; s < ns; ++s) wf[s] = (float)(w[s] / sum);
-  std::vector<float2> pr(64, make_float2(1.f, 0.f));
-  for (int k = 0; k < ni; ++k) {
-    const double u = prof->extent * ((k + 0.5) / ni - 0.5);
-    const double beta = 2.0 * M_PI * prof->tbw * u / ns;
-    pr[k] = make_float2((float)std::cos(beta), (float)std::sin(beta));
-    pr[32 + k] = make_float2((float)std::cos(-0.5 * ns * beta), (float)std::sin(-0.5 * ns * beta));
-  }
   cudaError_t e = cudaSuccess;
-  if (p->slice_w == nullptr) e = dalloc(p, &p->slice_w, kSliceMaxSub);
-  if (e == cudaSuccess && p->slice_prec == nullptr) e = dalloc(p, &p->slice_prec, 64);
-  if (e == cudaSuccess) e = cudaMemcpy(p->slice_w, wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(p->slice_prec, pr.data(), pr.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (p->slice_rot == nullptr) e = dalloc(p, &p->slice_rot, (size_t)p->ntr_pad * 32 * 9);
+  // the composed pulse of every (TR, isochromat): pre-winder, then per sub-step the RF
+  // rotation by phi_n w_s about the TR's axis (the hard-pulse kernel's convention) and the
+  // precession by beta_k, then the rewinder; in float64 from the plan's signed flips
+  std::vector<float> phi(p->ntr_pad);
+  if (e == cudaSuccess) e = cudaMemcpy(phi.data(), p->phi, phi.size() * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "slice profile tables");
+  std::vector<float> rot((size_t)p->ntr_pad * 32 * 9, 0.f);
+  for (int n = 0; n < p->ntr_pad; ++n)
+    for (int k = 0; k < ni; ++k) {
+      const double u = prof->extent * ((k + 0.5) / ni - 0.5);
+      const double beta = 2.0 * M_PI * prof->tbw * u / ns, half = -0.5 * ns * beta;
+      const double cb = std::cos(beta), sb = std::sin(beta), ch = std::cos(half), sh = std::sin(half);
+      for (int c = 0; c < 3; ++c) {
+        double x = c == 0, y = c == 1, z = c == 2;
+        double t = ch * x - sh * y;  // pre-winder
+        y = sh * x + ch * y;
+        x = t;
+        for (int s = 0; s < ns; ++s) {
+          const double ang = (double)phi[n] * (w[s] / sum), cn = std::cos(ang), sn = std::sin(ang);
+          t = cn * y + sn * z;  // RF sub-pulse
+          z = cn * z - sn * y;
+          y = t;
+          t = cb * x - sb * y;  // gradient precession
+          y = sb * x + cb * y;
+          x = t;
+        }
+        t = ch * x - sh * y;  // rewinder
+        y = sh * x + ch * y;
+        x = t;
+        float* R = rot.data() + ((size_t)n * 32 + k) * 9 + 3 * c;
+        R[0] = (float)x;
+        R[1] = (float)y;
+        R[2] = (float)z;
+      }
+    }
+  e = cudaMemcpy(p->slice_rot, rot.data(), rot.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "slice profile tables");
   p->slice_iso = ni;
   p->slice_sub = ns;
