@@ -67,11 +67,14 @@ def test_time_basis_matches_numpy_svd(mr):
 
 
 # nkx == nx from the third case on: J^H J v takes the path without the readout DFT pair;
-# ny = 32 N1 (64, 96, 224, 256, 32) takes the factorised phase-encode DFT on top, the
-# whole product in one kernel per image column (the last case has 10 TRs per ky)
+# ny = 32 N1 for every N1 = 1 .. 8 (32, 64, 96, 128, 160, 192, 224, 256) takes the
+# factorised phase-encode DFT on top (a 2 N1-point DFT from two N1-point DFTs, then a
+# 16-point FFT), the whole product in one kernel per image column (the 32-row case has
+# 10 TRs per ky)
 @pytest.mark.parametrize("case", [(40, 24, 5, 6, 48, 16), (33, 17, 3, 3, 30, 8), (64, 64, 5, 0, 64, 32),
                                   (36, 20, 3, 2, 36, 24), (1, 12, 2, 1, 1, 8), (24, 96, 2, 3, 24, 16),
-                                  (8, 224, 1, 0, 8, 8), (13, 256, 1, 1, 13, 24), (16, 32, 10, 0, 16, 8)])
+                                  (8, 224, 1, 0, 8, 8), (13, 256, 1, 1, 13, 24), (16, 32, 10, 0, 16, 8),
+                                  (6, 128, 1, 0, 6, 8), (5, 160, 1, 1, 5, 16), (4, 192, 1, 2, 4, 24)])
 def test_lowrank_products_match_projected_oracle(mr, case):
     nx, ny, fills, extra, nkx, R = case
     seq = synth.make_sequence(nx, ny, fills, 7.8, 3.9, seed=5, nkx=nkx, extra_trs=extra)
