@@ -1382,13 +1382,20 @@ __device__ __forceinline__ bool grid_wait_sums_w0(const FF* part, const unsigned
   return ok != 0;
 }
 
-size_t cg_column_smem_bytes(int ny, int R, int kmax) {
-  const int hy = (ny + 1) / 2;
-  return column_smem_bytes(ny, R, kmax) + sizeof(float) * ((size_t)ny + 20 * (size_t)hy);
+// Shared memory of the persistent fixed-count CG with cpc image columns per cluster: the
+// column kernel's, then per column the mask and the CG vectors (and, for the second
+// column on, its own product input and rho rows and its product q = B w).
+size_t cg_column_smem_bytes(int ny, int R, int kmax, int cpc = 1) {
+  const size_t hy = (size_t)(ny + 1) / 2;
+  return column_smem_bytes(ny, R, kmax) + sizeof(float) * ((size_t)ny + 20 * hy) +
+         (size_t)(cpc - 1) * sizeof(float) * (6 * (size_t)ny + ny + 20 * hy + 4 * hy);
 }
 
-template <int N1, int KM, int RCT>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kColThreads, 3)
+// CPC image columns per cluster (1, or 2 where the grid of one cluster per column does
+// not fit at once: every column's CG state stays in shared memory, the products of the
+// cluster's columns run one after the other, and the grid-wide sums add all of them).
+template <int N1, int KM, int RCT, int CPC>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kColThreads, CPC == 1 ? 3 : 2)
 lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict__ rhs, float* __restrict__ xout,
                      const float* __restrict__ coefT, const float2* __restrict__ rho,
                      const float* __restrict__ maskf, const float2* __restrict__ roots,
@@ -1404,89 +1411,145 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   float2* hs = rt + NY;
   float2* sbuf = hs + RC * RS;
   float2* sin = sbuf + sbuf_slots(kmax) * NY;
-  float* vox = reinterpret_cast<float*>(sin + kmax * NY);  // rows 0..3: the product's input
-  float* red4 = vox + 6 * NY;
+  float* vox0 = reinterpret_cast<float*>(sin + kmax * NY);  // rows 0..3: the product's input
+  float* red4 = vox0 + 6 * NY;
   float* rin = red4 + 4 * NY;
-  float* mk = rin + 4 * NY;      // [NY] mask of the column
-  float* cgv = mk + NY;          // [5 vectors r, p, s, z, x][4 rows][HY] this block's half
-  const ColShared S = {rt, hs, sbuf, sin, vox, red4, rin, cl.map_shared_rank(sin, peer), cl.map_shared_rank(rin, peer)};
-  float* vox_peer = cl.map_shared_rank(vox, peer);
+  // per column c: vox[c] [6][NY] (w and rho), mk[c] [NY], cgv[c] [5 vectors r, p, s, z, x]
+  // [4 rows][HY] of this block's half, and (c >= 1) qv[c] [4][HY], its product q = B w
+  float* vox[CPC];
+  float* mk[CPC];
+  float* cgv[CPC];
+  float* qv[CPC];
+  {
+    float* q = rin + 4 * NY;
+#pragma unroll
+    for (int c = 0; c < CPC; ++c) {
+      if (c > 0) {
+        vox[c] = q;
+        q += 6 * NY;
+      } else {
+        vox[c] = vox0;
+      }
+      mk[c] = q;
+      q += NY;
+      cgv[c] = q;
+      q += 20 * HY;
+      if (c > 0) {
+        qv[c] = q;
+        q += 4 * HY;
+      } else {
+        qv[c] = nullptr;
+      }
+    }
+  }
+  float2* const sin_peer = cl.map_shared_rank(sin, peer);
+  float* const rin_peer = cl.map_shared_rank(rin, peer);
   __shared__ int s_ok_peer[2];  // written by the peer, slot it mod 2 in iteration it
   int* ok_peer_remote = cl.map_shared_rank(s_ok_peer, peer);
   __shared__ FF ws[2 * kColWarps];
   __shared__ float s_al, s_be;
   __shared__ int s_apply;
   const int tid = threadIdx.x;
-  const int ix = blockIdx.x >> 1;  // one column per cluster
+  const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;  // column c of this cluster: cid + c ncl
   const int G = gridDim.x;
   const int ya = crank * HY, nh = min(NY, ya + HY) - ya;  // this block's half of iy: ya .. ya + nh
-  float* const cr = cgv;
-  float* const cp = cgv + 4 * HY;
-  float* const cs = cgv + 8 * HY;
-  float* const cz = cgv + 12 * HY;
-  float* const cx = cgv + 16 * HY;
   for (int e = tid; e < NY; e += kColThreads) rt[e] = roots[e];
   cl.sync();
 
-  // rho and the mask of the whole column; r = rhs and p = s = z = x = 0 on this block's
+  // rho and the mask of each whole column; r = rhs and p = s = z = x = 0 on this block's
   // half; the product's input is r (rows 2, 3 masked)
-  int inside = 0;
-  for (int iy = tid; iy < NY; iy += kColThreads) {
-    const int j = iy * nx + ix;
-    const float2 rh = rho[j];
-    const float m = maskf[j];
-    vox[4 * NY + iy] = rh.x;
-    vox[5 * NY + iy] = rh.y;
-    mk[iy] = m;
-    inside |= m != 0.f;
-  }
-  inside = __syncthreads_or(inside);  // the same column in both blocks: the same answer
-  if (tid < nh) {
-    const int iy = ya + tid, j = iy * nx + ix;
-    const float m = mk[iy];
+  bool inside[CPC];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float r = rhs[(size_t)k * nv + j];
-      cr[k * HY + tid] = r;
-      cp[k * HY + tid] = 0.f;
-      cs[k * HY + tid] = 0.f;
-      cz[k * HY + tid] = 0.f;
-      cx[k * HY + tid] = 0.f;
-      const float vv = k >= 2 ? r * m : r;
-      vox[k * NY + iy] = vv;
-      vox_peer[k * NY + iy] = vv;
+  for (int c = 0; c < CPC; ++c) {
+    const int ix = cid + c * ncl;
+    int in = 0;
+    if (ix < nx) {
+      for (int iy = tid; iy < NY; iy += kColThreads) {
+        const int j = iy * nx + ix;
+        const float2 rh = rho[j];
+        const float m = maskf[j];
+        vox[c][4 * NY + iy] = rh.x;
+        vox[c][5 * NY + iy] = rh.y;
+        mk[c][iy] = m;
+        in |= m != 0.f;
+      }
+    }
+    inside[c] = __syncthreads_or(in) != 0;  // the same column in both blocks: the same answer
+    float* const cg = cgv[c];
+    float* const vp = cl.map_shared_rank(vox[c], peer);
+    if (tid < nh) {
+      const int iy = ya + tid, j = iy * nx + ix;
+      const float m = ix < nx ? mk[c][iy] : 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float r = ix < nx ? rhs[(size_t)k * nv + j] : 0.f;
+        cg[k * HY + tid] = r;
+        cg[(4 + k) * HY + tid] = 0.f;
+        cg[(8 + k) * HY + tid] = 0.f;
+        cg[(12 + k) * HY + tid] = 0.f;
+        cg[(16 + k) * HY + tid] = 0.f;
+        const float vv = k >= 2 ? r * m : r;
+        vox[c][k * NY + iy] = vv;
+        vp[k * NY + iy] = vv;
+      }
     }
   }
   cl.sync();
 
-  // w_0 = B r_0 (masked, like every product) becomes the product's input
-  if (inside) column_core<N1, KM, RCT>(W, S, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
-  if (tid < nh) {
-    const int iy = ya + tid;
-    const float m = mk[iy] * scale;
+  // the product q = B w of column c (masked, like every product), into qv[c] for c >= 1
+  auto product = [&](int c) {
+    const ColShared S = {rt, hs, sbuf, sin, vox[c], red4, rin, sin_peer, rin_peer};
+    column_core<N1, KM, RCT>(W, S, coefT, UgS, kmax, cid + c * ncl, nx, R, r0, nr, ya, ya + nh);
+    if (c > 0 && tid < nh) {
+      const int iy = ya + tid;
+      const float m = mk[c][iy] * scale;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float wv = inside ? (red4[k * NY + iy] + rin[k * NY + iy]) * m : 0.f;
-      vox[k * NY + iy] = wv;
-      vox_peer[k * NY + iy] = wv;
+      for (int k = 0; k < 4; ++k) qv[c][k * HY + tid] = (red4[k * NY + iy] + rin[k * NY + iy]) * m;
+    }
+  };
+  // column c's q at this thread's element (k, iy): column 0 reads the product's output
+  // in place (its product is the last of an iteration), the others their copy
+  auto qval = [&](int c, int k, int iy) {
+    return c == 0 ? (red4[k * NY + iy] + rin[k * NY + iy]) * (mk[0][iy] * scale) : qv[c][k * HY + (iy - ya)];
+  };
+
+  // w_0 = B r_0 becomes the product's input
+#pragma unroll
+  for (int c = CPC - 1; c >= 0; --c)
+    if (inside[c]) product(c);
+#pragma unroll
+  for (int c = 0; c < CPC; ++c) {
+    float* const vp = cl.map_shared_rank(vox[c], peer);
+    if (tid < nh) {
+      const int iy = ya + tid;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float wv = inside[c] ? qval(c, k, iy) : 0.f;
+        vox[c][k * NY + iy] = wv;
+        vp[k * NY + iy] = wv;
+      }
     }
   }
-  // the thread's parts of delta = <w, r> and gamma = <r, r> (formed with every update, on
-  // the thread's own elements) and their warp sums, which warp 0 finishes after the
-  // cluster barrier below
-  {
+  // the thread's parts of delta = <w, r> and gamma = <r, r> over the cluster's columns
+  // (formed with every update, on the thread's own elements) and their warp sums, which
+  // warp 0 finishes after the cluster barrier below
+  auto partials = [&]() {
     float sd = 0.f, sg = 0.f;
     if (tid < nh) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float r = cr[k * HY + tid];
-        sd = fmaf(r, vox[k * NY + ya + tid], sd);
-        sg = fmaf(r, r, sg);
+      for (int c = 0; c < CPC; ++c) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float r = cgv[c][k * HY + tid];
+          sd = fmaf(r, vox[c][k * NY + ya + tid], sd);
+          sg = fmaf(r, r, sg);
+        }
       }
     }
     FF v[2] = {{sd, 0.f}, {sg, 0.f}};
     warp_partials<2>(v, ws);
-  }
+  };
+  partials();
   cl.sync();
 
   // pq_prev = p.Bp of the previous iteration: beta gamma / alpha_prev = beta^2 pq_prev
@@ -1499,7 +1562,7 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   for (int it = 0; it < iters; ++it) {
     FF* pk = reinterpret_cast<FF*>(part) + (size_t)(it & 1) * 2 * G;
     // q = B w while the other blocks arrive (not needed in the last iteration)
-    const bool prod = inside && it + 1 < iters;
+    const bool more = it + 1 < iters;
     // warp 0 finishes the block's parts of delta and gamma (the warps' sums, written before
     // the last cluster barrier) and arrives, before the product: the other blocks' waits
     // end as early as possible.  A block named by the test hook withholds its first
@@ -1510,7 +1573,10 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
       warp_finish<2>(b, ws);
       if (arrive) grid_arrive<2>(pk, bar, b);
     }
-    if (prod) column_core<N1, KM, RCT>(W, S, coefT, UgS, kmax, ix, nx, R, r0, nr, ya, ya + nh);
+    // the products, column 0 last (the update reads its output in place)
+#pragma unroll
+    for (int c = CPC - 1; c >= 0; --c)
+      if (inside[c] && more) product(c);
     // warp 0 waits, sums and decides; the other warps go straight to the block barrier
     if ((tid >> 5) == 0) {
       FF sums2[2];
@@ -1553,39 +1619,33 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
     }
     if (s_apply && tid < nh) {
       const int iy = ya + tid;
-      const float al = s_al, be = s_be, m = prod ? mk[iy] * scale : 0.f;
+      const float al = s_al, be = s_be;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int e = k * HY + tid;
-        const float wv = vox[k * NY + iy];
-        const float qv = prod ? (red4[k * NY + iy] + rin[k * NY + iy]) * m : 0.f;  // q = B w
-        const float zv = fmaf(be, cz[e], qv);
-        const float sv = fmaf(be, cs[e], wv);
-        const float pv = fmaf(be, cp[e], cr[e]);
-        cz[e] = zv;
-        cs[e] = sv;
-        cp[e] = pv;
-        cx[e] = fmaf(al, pv, cx[e]);
-        cr[e] = fmaf(-al, sv, cr[e]);
-        const float wn = fmaf(-al, zv, wv);
-        vox[k * NY + iy] = wn;
-        vox_peer[k * NY + iy] = wn;
+      for (int c = 0; c < CPC; ++c) {
+        float* const cg = cgv[c];
+        float* const vp = cl.map_shared_rank(vox[c], peer);
+        const bool pc = inside[c] && more;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int e = k * HY + tid;
+          const float wv = vox[c][k * NY + iy];
+          const float q = pc ? qval(c, k, iy) : 0.f;  // q = B w
+          const float zv = fmaf(be, cg[12 * HY + e], q);
+          const float sv = fmaf(be, cg[8 * HY + e], wv);
+          const float pv = fmaf(be, cg[4 * HY + e], cg[e]);
+          cg[12 * HY + e] = zv;
+          cg[8 * HY + e] = sv;
+          cg[4 * HY + e] = pv;
+          cg[16 * HY + e] = fmaf(al, pv, cg[16 * HY + e]);
+          cg[e] = fmaf(-al, sv, cg[e]);
+          const float wn = fmaf(-al, zv, wv);
+          vox[c][k * NY + iy] = wn;
+          vp[k * NY + iy] = wn;
+        }
       }
     }
     // the next iteration's parts from r and w as they now stand, summed over each warp
-    {
-      float sd = 0.f, sg = 0.f;
-      if (tid < nh) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float r = cr[k * HY + tid];
-          sd = fmaf(r, vox[k * NY + ya + tid], sd);
-          sg = fmaf(r, r, sg);
-        }
-      }
-      FF v[2] = {{sd, 0.f}, {sg, 0.f}};
-      warp_partials<2>(v, ws);
-    }
+    partials();
     cl.sync();  // the new w of both halves is in both blocks; the peer's flag has arrived
     // both blocks of the cluster leave together; the slot is written again only after the
     // peer has passed the next cluster barrier, i.e. after this read
@@ -1594,10 +1654,14 @@ lr_cg_columns_kernel(const __grid_constant__ DftSmall W, const float* __restrict
   // every block took the same decisions; block 0 reports where the solve froze (the
   // iteration index + 1; 0 when all iterations were applied)
   if (blockIdx.x == 0 && tid == 0) *frozen_at = applied < iters ? applied + 1 : 0;
-  if (tid < nh) {
-    const int j = (ya + tid) * nx + ix;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) xout[(size_t)k * nv + j] = cx[k * HY + tid];
+  for (int c = 0; c < CPC; ++c) {
+    const int ix = cid + c * ncl;
+    if (tid < nh && ix < nx) {
+      const int j = (ya + tid) * nx + ix;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) xout[(size_t)k * nv + j] = cgv[c][(16 + k) * HY + tid];
+    }
   }
 }
 
@@ -2410,12 +2474,12 @@ static cudaError_t launch_column(Plan* p, const float* v, double* vdot, double* 
 // A persistent column kernel: one cluster of two blocks per image column, all resident at
 // once (cooperative launch).  With launch = false only checks that every cluster fits.
 template <typename... KArgs, typename... Args>
-static cudaError_t launch_persistent_columns(Plan* p, void (*kernel)(KArgs...), size_t sm, bool launch,
+static cudaError_t launch_persistent_columns(Plan* p, void (*kernel)(KArgs...), size_t sm, int clusters, bool launch,
                                              cudaStream_t st, Args... args) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * p->nx);
+  cfg.gridDim = dim3(2 * clusters);
   cfg.blockDim = dim3(kColThreads);
   cfg.dynamicSmemBytes = sm;
   cfg.stream = st;
@@ -2424,7 +2488,7 @@ static cudaError_t launch_persistent_columns(Plan* p, void (*kernel)(KArgs...), 
     int max_clusters = 0;
     e = cudaOccupancyMaxActiveClusters(&max_clusters, kernel, &cfg);
     if (e != cudaSuccess) return e;
-    return max_clusters >= p->nx ? cudaSuccess : cudaErrorCooperativeLaunchTooLarge;
+    return max_clusters >= clusters ? cudaSuccess : cudaErrorCooperativeLaunchTooLarge;
   }
   e = cudaMemsetAsync(p->cg_bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
@@ -2439,12 +2503,24 @@ static cudaError_t launch_persistent_columns(Plan* p, void (*kernel)(KArgs...), 
 template <int N1, int KM, int RCT>
 static cudaError_t launch_cg_columns_k(Plan* p, const float* rhs, float* x, int iters, bool launch, cudaStream_t st) {
   LowRank& L = *p->lr;
-  const size_t sm = cg_column_smem_bytes(p->ny, L.R, L.ky_count_max);
-  return launch_persistent_columns(p, lr_cg_columns_kernel<N1, KM, RCT>, sm, launch, st, L.dft_small, rhs, x,
-                                   (const float*)L.coefT, (const float2*)p->rho, (const float*)p->maskf,
-                                   (const float2*)p->roots, (const float*)L.UgS, L.ky_count_max, p->nx, p->nv, L.R,
-                                   (float)p->nx, iters, p->grid_stall_block, p->red, p->cg_bar, p->cg_s,
-                                   p->cg_frozen, p->dev_err);
+  // one cluster per image column when all of them fit at once, else two columns per cluster
+  auto go = [&](auto kernel, int cpc, bool now) {
+    const size_t sm = cg_column_smem_bytes(p->ny, L.R, L.ky_count_max, cpc);
+    return launch_persistent_columns(p, kernel, sm, (p->nx + cpc - 1) / cpc, now, st, L.dft_small, rhs, x,
+                                     (const float*)L.coefT, (const float2*)p->rho, (const float*)p->maskf,
+                                     (const float2*)p->roots, (const float*)L.UgS, L.ky_count_max, p->nx, p->nv,
+                                     L.R, (float)p->nx, iters, p->grid_stall_block, p->red, p->cg_bar, p->cg_s,
+                                     p->cg_frozen, p->dev_err);
+  };
+  cudaError_t e = go(lr_cg_columns_kernel<N1, KM, RCT, 1>, 1, false);
+  if (e == cudaSuccess) return launch ? go(lr_cg_columns_kernel<N1, KM, RCT, 1>, 1, true) : e;
+  if constexpr (KM > 0) {  // two columns per cluster: compiled for the specialised shapes only
+    cudaGetLastError();
+    e = go(lr_cg_columns_kernel<N1, KM, RCT, 2>, 2, false);
+    if (e != cudaSuccess || !launch) return e;
+    return go(lr_cg_columns_kernel<N1, KM, RCT, 2>, 2, true);
+  }
+  return e;
 }
 
 template <int N1>
@@ -2482,7 +2558,7 @@ static cudaError_t launch_st_columns_k(Plan* p, const float* g, float* z, const 
                                        cudaStream_t st) {
   LowRank& L = *p->lr;
   const size_t sm = st_column_smem_bytes(p->ny, L.R, L.ky_count_max);
-  return launch_persistent_columns(p, lr_steihaug_columns_kernel<N1, KM, RCT>, sm, launch, st, L.dft_small, g, z,
+  return launch_persistent_columns(p, lr_steihaug_columns_kernel<N1, KM, RCT>, sm, p->nx, launch, st, L.dft_small, g, z,
                                    (const float*)L.coefT, (const float2*)p->rho, (const float*)p->maskf,
                                    (const float2*)p->roots, (const float*)L.UgS, L.ky_count_max, p->nx, p->nv, L.R,
                                    (float)p->nx, a.delta, a.rel_tol, a.max_steps, a.sc, a.si, p->grid_stall_block,

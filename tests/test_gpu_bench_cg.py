@@ -187,3 +187,46 @@ def test_bench_cg_full_size(mr):
         res = np.linalg.norm(b3[:, :, ix] - bx)
         res_lpi = np.linalg.norm(b3[:, :, ix] - seq.nx * model.gauss_newton_product(lin, l3[:, :, ix]))
         assert res < 1.2 * res_lpi + 1e-4 * np.linalg.norm(b3[:, :, ix]), (ix, res, res_lpi)
+
+
+def test_two_columns_per_cluster_full_size(mr):
+    """256 x 256 with 1280 TRs: one cluster per image column (512 blocks) does not fit at
+    once, so the persistent launch gives each cluster two columns (ix and ix + 128; their
+    CG vectors stay in shared memory, the products run one after the other).  One launch
+    for all 30 products, against the product-by-product CG, and its residual on sampled
+    columns of both kinds through the one-column oracle."""
+    seq, ph = synth.config("brain256")
+    alpha = f32(np.stack([np.log(ph.t1_ms.ravel()), np.log(ph.t2_ms.ravel()), ph.rho.real.ravel(),
+                          ph.rho.imag.ravel()]))
+    U = basis(seq)
+    with mr.Plan(seq) as plan:
+        plan.linearize(cuda(alpha))
+        g = plan.jhw(cuda(synth.random_kspace(seq.ntr, seq.nkx, 101), torch.complex64))
+        b_dev = (g / torch.sqrt(torch.mean(g * g))).contiguous()
+        b = b_dev.cpu().numpy().astype(np.float64)
+        plan.lowrank_set_basis(cuda(U))
+        plan.lowrank_linearize(cuda(alpha))
+        plan.profile_start(kernels=("jhw_dot",))
+        x_gpu = plan.cg_fixed(b_dev, ITERS)
+        prof = plan.profile_stop()
+        plan.check()
+        assert plan.cg_applied() == ITERS
+        x_lpi = jhjv_cg(plan, b_dev, ITERS)
+        bx_gpu = plan.jhjv(x_gpu).cpu().numpy().astype(np.float64)
+        e_lpi = float(torch.linalg.vector_norm(x_gpu.double() - x_lpi) / torch.linalg.vector_norm(x_lpi))
+        x_gpu = x_gpu.cpu().numpy().astype(np.float64)
+        x_lpi = x_lpi.cpu().numpy()
+    assert prof["jhw_dot"]["kernels"] == 1 and prof["jhw_dot"]["launches"] == ITERS
+    assert e_lpi < 2e-3, e_lpi
+    x3 = x_gpu.reshape(4, seq.ny, seq.nx)
+    l3 = x_lpi.reshape(4, seq.ny, seq.nx)
+    b3 = b.reshape(4, seq.ny, seq.nx)
+    bx3 = bx_gpu.reshape(4, seq.ny, seq.nx)
+    for ix in (60, 190):  # a first and a second column of a cluster
+        sub, a1 = columns(seq, ph, [ix])
+        lin = model.project_onto_basis(model.linearize(sub, a1), U)
+        bx = seq.nx * model.gauss_newton_product(lin, x3[:, :, ix])
+        assert metrics.relerr(bx3[:, :, ix], bx) < 1e-4, ix
+        res = np.linalg.norm(b3[:, :, ix] - bx)
+        res_lpi = np.linalg.norm(b3[:, :, ix] - seq.nx * model.gauss_newton_product(lin, l3[:, :, ix]))
+        assert res < 1.2 * res_lpi + 1e-4 * np.linalg.norm(b3[:, :, ix]), (ix, res, res_lpi)
