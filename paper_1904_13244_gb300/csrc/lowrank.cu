@@ -655,15 +655,18 @@ __global__ void lr_coef_transpose_kernel(const float* __restrict__ coef, int nx,
 //   1. warp w owns the rows r = 2w, 2w + 1: lane (r, i2) forms h_r(16 i1 + i2) for i1 < M
 //      in registers, applies the M-point DFT and the twiddle, and lane (r, k1) the
 //      16-point FFT of the factorised phase-encode DFT -> H_r(ky) (warp barriers only);
-//   2. the per-ky Gram through the TR axis: one thread per TR forms the block's part of
-//      s_t = sum_q U[t][q] H_q(ky(t)) and also stores it into the peer; after a cluster
-//      barrier each block adds the two parts (the same sum in both), then one lane per ky
-//      (a warp per r) sums U[t][r] s_t over the TRs of ky;
+//   2. the per-ky Gram through the TR axis, one thread per phase-encode line ky: it forms
+//      the block's part of s_t = sum_q U[t][q] H_q(ky) for the TRs t of its line and
+//      stores it into the peer; after a cluster barrier it adds the peer's part (the same
+//      sum in both blocks) and forms G_r(ky) = sum_t U[t][r] s_t for the block's r (the
+//      rows of U in batches of eight basis functions whose loads issue together, each
+//      pass's first batch before the barrier that precedes it);
 //   3. the same warps apply the adjoint DFT -> P_r(iy);
-//   4. one thread per iy contracts with the tangents over the block's r, keeping the part
-//      for its own half of the column and storing the rest into the peer; after a second
-//      cluster barrier each block adds the two parts for its half, writes g (masked,
-//      times nx) and its part of <v, g>; the last block adds the parts.
+//   4. one thread per iy contracts with the tangents over the block's r (coefficients in
+//      two batches, the first loaded before step 3's barrier), keeping the part for its
+//      own half of the column and storing the rest into the peer; after a second cluster
+//      barrier each block adds the two parts for its half, writes g (masked, times nx)
+//      and its part of <v, g>; the last block adds the parts.
 // Two blocks per column (448 for 224 columns, three per SM) balance the SMs better than
 // one block of twice the size (224 blocks on 152 SMs).
 // ---------------------------------------------------------------------------
