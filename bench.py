@@ -70,8 +70,8 @@ NCU_TRAFFIC = {
     ("xdft", "0728f575d9d96a3d"): 13670656.0,
     ("xdft_adj", "0728f575d9d96a3d"): 13668608.0,
     # profiles/lr_cg_columns_kernel_brain224.md: one persistent CG launch of 30 products
-    # read 20 934 656 B and wrote 2 816 B (caches flushed before it), per product
-    ("jhw_dot", "9208322f10858cd6"): (20934656.0 + 2816.0) / 30,
+    # read 21 394 176 B and wrote 3 072 B (caches flushed before it), per product
+    ("jhw_dot", "5dfb75d55030b8ff"): (21394176.0 + 3072.0) / 30,
     # profiles/rc_product_kernel_brain224.md: one recompute J^H J v read 12 698 624 B
     ("jhw_dot_rc", "43b010ca1597d1da"): 12698624.0,
 }
