@@ -702,16 +702,10 @@ struct ColShared {
 // red4 (this block's half of iy) and rin hold the two parts of the contraction.
 // KM > 0 and RCT > 0: kmax == KM and nr == RCT known at compile time (the benchmark's
 // shapes); 0: taken from the arguments.
-struct NoHook {
-  __device__ __forceinline__ void operator()() const {}
-};
-
-// hook: called by every thread right after the block barrier that ends step 1 (the
-// persistent CG finishes its block sums there instead of spending barriers of its own).
-template <int N1, int KM = 0, int RCT = 0, typename Hook = NoHook>
+template <int N1, int KM = 0, int RCT = 0>
 __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& S, const float* __restrict__ coefT,
                                             const float* __restrict__ UgS, int kmax, int ix, int nx, int R, int r0,
-                                            int nr, int ya, int ye, const Hook& hook = Hook()) {
+                                            int nr, int ya, int ye) {
   namespace cgp = cooperative_groups;
   cgp::cluster_group cl = cgp::this_cluster();
   constexpr int NY = 32 * N1, M = 2 * N1, RS = col_row(NY);
@@ -812,7 +806,6 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
   };
   if (km <= SC) load_u(0);
   __syncthreads();
-  hook();
   // 2. per-ky Gram through the TR axis, thread per ky: U as UgS[r][i][ky] (the TRs of each
   //    ky in slots i < kmax, zero past a ky's TRs), so consecutive threads read consecutive
   //    ky (coalesced); every s and G a thread forms belongs to its own ky, so the phase
