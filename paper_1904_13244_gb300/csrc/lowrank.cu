@@ -798,11 +798,36 @@ __device__ __forceinline__ void column_core(const DftSmall& W, const ColShared& 
   const float* ub = UgS + (size_t)r0 * km * NY + kyt;
   float u[QB][SC];
   auto load_u = [&](int q0) {
+    if constexpr (KM >= 4 && KM <= 8) {
+      // the slot planes (UgS is then the plan's UgQ): one 16-byte load for slots 0-3 and
+      // one 4- or 16-byte load for the rest, per basis function
+      const float4* p0 = reinterpret_cast<const float4*>(UgS) + (size_t)r0 * NY + kyt;
+      const float4* p1 = reinterpret_cast<const float4*>(UgS) + (size_t)R * NY + (size_t)r0 * NY + kyt;
+      const float* p1f = UgS + (size_t)4 * R * NY + (size_t)r0 * NY + kyt;  // plane 1 of floats (KM = 5)
 #pragma unroll
-    for (int b = 0; b < QB; ++b)
+      for (int b = 0; b < QB; ++b) {
+        const bool in = q0 + b < nrr && kyt < NY;
+        const float4 a = in ? __ldg(p0 + (size_t)(q0 + b) * NY) : make_float4(0.f, 0.f, 0.f, 0.f);
+        u[b][0] = a.x;
+        u[b][1] = a.y;
+        u[b][2] = a.z;
+        u[b][3] = a.w;
+        if constexpr (KM == 5) {
+          u[b][4] = in ? __ldg(p1f + (size_t)(q0 + b) * NY) : 0.f;
+        } else if constexpr (KM > 5) {
+          const float4 c = in ? __ldg(p1 + (size_t)(q0 + b) * NY) : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-      for (int i = 0; i < SC; ++i)
-        u[b][i] = (i < km && q0 + b < nrr && kyt < NY) ? __ldg(ub + ((size_t)(q0 + b) * km + i) * NY) : 0.f;
+          for (int i = 4; i < KM; ++i) u[b][i] = cv[i - 4];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < QB; ++b)
+#pragma unroll
+        for (int i = 0; i < SC; ++i)
+          u[b][i] = (i < km && q0 + b < nrr && kyt < NY) ? __ldg(ub + ((size_t)(q0 + b) * km + i) * NY) : 0.f;
+    }
   };
   if (km <= SC) load_u(0);
   __syncthreads();
@@ -2043,7 +2068,7 @@ cudaError_t lowrank_project(const Plan& p, const LowRank& L, const float* alpha,
 
 void lowrank_free(LowRank* L) {
   if (L == nullptr) return;
-  void* ptrs[] = {L->U, L->Ug, L->UgT, L->UgS, L->kyof, L->Mky, L->kyptr, L->kytr, L->coef, L->coef2, L->gpart, L->coefT, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
+  void* ptrs[] = {L->U, L->Ug, L->UgT, L->UgS, L->UgQ, L->kyof, L->Mky, L->kyptr, L->kytr, L->coef, L->coef2, L->gpart, L->coefT, L->a1_hi, L->a1_lo, L->a23_hi, L->a23_lo,
                   L->a4_hi, L->a4_lo, L->by_hi, L->by_lo, L->bya_hi, L->bya_lo, L->X1, L->H, L->Y3, L->P};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -2114,6 +2139,18 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   for (int k = 0; k < ny; ++k)
     for (int t = ptr[k]; t < ptr[k + 1]; ++t)
       for (int r = 0; r < R; ++r) UgS[((size_t)r * kmax + (t - ptr[k])) * ny + k] = Uh[(size_t)trs[t] * R + r];
+  // the same in slot planes for the specialised column kernels (kmax <= 8): slots 0-3 as
+  // float4 [R][ny], then slot 4 as float [R][ny] (kmax 5) or slots 4-7 as float4 [R][ny]
+  const int w1 = kmax <= 4 ? 0 : (kmax == 5 ? 1 : 4);
+  std::vector<float> UgQ(kmax <= 8 ? (size_t)R * ny * (4 + w1) : 0, 0.f);
+  if (kmax <= 8)
+    for (int r = 0; r < R; ++r)
+      for (int k = 0; k < ny; ++k)
+        for (int i = 0; i < kmax; ++i) {
+          const float v = UgS[((size_t)r * kmax + i) * ny + k];
+          if (i < 4) UgQ[((size_t)r * ny + k) * 4 + i] = v;
+          else UgQ[(size_t)R * ny * 4 + ((size_t)r * ny + k) * w1 + (i - 4)] = v;
+        }
   // the cancelled readout DFT pair needs nkx == nx; the Gram kernel keeps a ky tile's rows of U
   // in shared memory
   L->full_readout = p->nkx == p->nx && (size_t)L->gram_rows_max * (R + 1) * sizeof(float) <= (size_t)L->smem_optin;
@@ -2177,6 +2214,7 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   chk(cudaMalloc(&L->Ug, (size_t)ntr * R * sizeof(float)));
   chk(cudaMalloc(&L->UgT, (size_t)ntr * R * sizeof(float)));
   chk(cudaMalloc(&L->UgS, std::max<size_t>(UgS.size(), 1) * sizeof(float)));
+  chk(cudaMalloc(&L->UgQ, std::max<size_t>(UgQ.size(), 4) * sizeof(float)));
   chk(cudaMalloc(&L->kyof, (size_t)ntr * sizeof(int)));
   chk(cudaMalloc(&L->Mky, M.size() * sizeof(float)));
   chk(cudaMalloc(&L->kyptr, ptr.size() * sizeof(int)));
@@ -2208,6 +2246,7 @@ int lowrank_setup(Plan* p, const float* U_dev, int R, cudaStream_t st) {
   chk(cudaMemcpy(L->Ug, Ug.data(), Ug.size() * sizeof(float), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->UgT, UgT.data(), UgT.size() * sizeof(float), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->UgS, UgS.data(), UgS.size() * sizeof(float), cudaMemcpyHostToDevice));
+  if (!UgQ.empty()) chk(cudaMemcpy(L->UgQ, UgQ.data(), UgQ.size() * sizeof(float), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->kyof, kyof.data(), kyof.size() * sizeof(int), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->kyptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(L->kytr, trs.data(), trs.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -2440,7 +2479,7 @@ static cudaError_t launch_column_k(Plan* p, const float* v, double* vdot, double
   // programmatic dependent launch: the set-up above the kernel's pdl_wait overlaps the
   // tail of the previous launch in the stream
   return launch_pdl(lr_jhjv_column_kernel<N1, KM, RCT>, dim3(grid), dim3(kColThreads), sm, st, L.dft_small, v,
-                    L.coefT, p->rho, p->maskf, p->roots, L.UgS, L.ky_count_max, nx, ny, p->nv, R, (float)nx, out,
+                    L.coefT, p->rho, p->maskf, p->roots, KM > 0 ? L.UgQ : L.UgS, L.ky_count_max, nx, ny, p->nv, R, (float)nx, out,
                     p->red, p->ticket, vdot, vv, p->gate);
 }
 
@@ -2504,7 +2543,7 @@ static cudaError_t launch_cg_columns_k(Plan* p, const float* rhs, float* x, int 
     const size_t sm = cg_column_smem_bytes(p->ny, L.R, L.ky_count_max, cpc);
     return launch_persistent_columns(p, kernel, sm, (p->nx + cpc - 1) / cpc, now, st, L.dft_small, rhs, x,
                                      (const float*)L.coefT, (const float2*)p->rho, (const float*)p->maskf,
-                                     (const float2*)p->roots, (const float*)L.UgS, L.ky_count_max, p->nx, p->nv,
+                                     (const float2*)p->roots, (const float*)(KM > 0 ? L.UgQ : L.UgS), L.ky_count_max, p->nx, p->nv,
                                      L.R, (float)p->nx, iters, p->grid_stall_block, p->red, p->cg_bar, p->cg_s,
                                      p->cg_frozen, p->dev_err);
   };
@@ -2556,7 +2595,7 @@ static cudaError_t launch_st_columns_k(Plan* p, const float* g, float* z, const 
   const size_t sm = st_column_smem_bytes(p->ny, L.R, L.ky_count_max);
   return launch_persistent_columns(p, lr_steihaug_columns_kernel<N1, KM, RCT>, sm, p->nx, launch, st, L.dft_small, g, z,
                                    (const float*)L.coefT, (const float2*)p->rho, (const float*)p->maskf,
-                                   (const float2*)p->roots, (const float*)L.UgS, L.ky_count_max, p->nx, p->nv, L.R,
+                                   (const float2*)p->roots, (const float*)(KM > 0 ? L.UgQ : L.UgS), L.ky_count_max, p->nx, p->nv, L.R,
                                    (float)p->nx, a.delta, a.rel_tol, a.max_steps, a.sc, a.si, p->grid_stall_block,
                                    p->red, p->cg_bar, p->dev_err);
 }

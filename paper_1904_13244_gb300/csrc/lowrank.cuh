@@ -26,6 +26,8 @@ struct LowRank {
   float* Ug = nullptr;             // [ntr][R] rows of U in ky order (the order of kytr)
   float* UgT = nullptr;            // [R][ntr] the same, transposed
   float* UgS = nullptr;            // [R][ky_count_max][ny]: the i-th TR of ky at [r][i][ky], else 0
+  float* UgQ = nullptr;            // the same for ky_count_max <= 8 in planes of slots: float4 [R][ny] of
+                                   // slots 0-3, then slot 4 as float [R][ny] (5 slots) or slots 4-7 as float4
   int* kyof = nullptr;             // [ntr] ky of each TR in that order
   int gram_rows_max = 0;           // most TRs of any 32 consecutive ky values
   int ky_count_max = 0;            // most TRs of any single ky value
