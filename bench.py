@@ -70,8 +70,8 @@ NCU_TRAFFIC = {
     ("xdft", "0728f575d9d96a3d"): 13670656.0,
     ("xdft_adj", "0728f575d9d96a3d"): 13668608.0,
     # profiles/lr_cg_columns_kernel_brain224.md: one persistent CG launch of 30 products
-    # read 21 400 832 B and wrote 512 B (caches flushed before it), per product
-    ("jhw_dot", "623d6d92b1b7d3f2"): (21400832.0 + 512.0) / 30,
+    # read 20 971 520 B and wrote 0 B (caches flushed before it), per product
+    ("jhw_dot", "4ac33d5f5257c6e2"): (20971520.0 + 0.0) / 30,
     # profiles/rc_product_kernel_brain224.md: one recompute J^H J v read 12 698 624 B
     ("jhw_dot_rc", "43b010ca1597d1da"): 12698624.0,
 }
