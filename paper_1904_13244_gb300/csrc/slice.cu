@@ -92,16 +92,24 @@ bloch_slice_kernel(const float* __restrict__ alpha, const uint8_t* __restrict__ 
         m[0] = fmaf(x2a, m[0], m[0]);
         m[1] = fmaf(x2a, m[1], m[1]);
         m[2] = fmaf(x1a, zm1, m[2]);
-        // echo: the mean of m_y (and tangents) over the voxel's isochromats
-        float sy = m[1], sa = a[1], sb = b[1];
-        for (int o = n_iso >> 1; o > 0; o >>= 1) {
-          sy += __shfl_xor_sync(0xffffffffu, sy, o);
-          sa += __shfl_xor_sync(0xffffffffu, sa, o);
-          sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        // echo: the mean of m_y (and tangents) over the voxel's isochromats; with 32
+        // isochromats (one voxel per warp) the quad's twelve sums are formed together after
+        // the quad, otherwise per TR here
+        if (n_iso == 32) {
+          o0[u] = m[1];
+          o1[u] = a[1];
+          o2[u] = b[1];
+        } else {
+          float sy = m[1], sa = a[1], sb = b[1];
+          for (int o = n_iso >> 1; o > 0; o >>= 1) {
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+          }
+          o0[u] = sy * inv_iso;
+          o1[u] = sa * inv_iso;
+          o2[u] = sb * inv_iso;
         }
-        o0[u] = sy * inv_iso;
-        o1[u] = sa * inv_iso;
-        o2[u] = sb * inv_iso;
         // decay over TR - TE
         zm1 = m[2] - 1.f;
         a[0] = fmaf(x2b, a[0], a[0]);
@@ -114,7 +122,44 @@ bloch_slice_kernel(const float* __restrict__ alpha, const uint8_t* __restrict__ 
         m[1] = fmaf(x2b, m[1], m[1]);
         m[2] = fmaf(x1b, zm1, m[2]);
       }
-      if (k == 0 && live) {  // one float4 per channel and TR quad, as K1 stores them
+      if (n_iso == 32) {
+        // the quad's twelve sums v[3 u + channel] over the warp's lanes, by halving: after
+        // the exchanges across lane bits 4 and 3, lane group g = lane / 8 holds TR u = g's
+        // three values, summed over its partners; a butterfly over the low three lane bits
+        // completes them (18 shuffles for the quad instead of 60)
+        float v[12];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          v[3 * u] = o0[u];
+          v[3 * u + 1] = o1[u];
+          v[3 * u + 2] = o2[u];
+        }
+        const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0;
+        float w[6], x[3];
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+          const float send = h4 ? v[e] : v[6 + e], keep = h4 ? v[6 + e] : v[e];
+          w[e] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          const float send = h3 ? w[e] : w[3 + e], keep = h3 ? w[3 + e] : w[e];
+          x[e] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+          for (int e = 0; e < 3; ++e) x[e] += __shfl_xor_sync(0xffffffffu, x[e], o);
+        if ((lane & 7) == 0 && live) {  // TR u of the quad: one float of each channel's float4
+          const int u = lane >> 3;
+          const size_t q = (size_t)((n0 + nq4) >> 2) * nv + j;
+          __stcs(reinterpret_cast<float*>(D + q) + u, on ? x[0] * inv_iso : 0.f);
+          if (nch > 1) {
+            __stcs(reinterpret_cast<float*>(D + cstride + q) + u, on ? x[1] * inv_iso : 0.f);
+            __stcs(reinterpret_cast<float*>(D + 2 * cstride + q) + u, on ? x[2] * inv_iso : 0.f);
+          }
+        }
+      } else if (k == 0 && live) {  // one float4 per channel and TR quad, as K1 stores them
         const size_t q = (size_t)((n0 + nq4) >> 2) * nv + j;
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         __stcs(D + q, on ? make_float4(o0[0], o0[1], o0[2], o0[3]) : z4);
